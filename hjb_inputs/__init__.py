@@ -1,0 +1,260 @@
+"""Seeded synthetic problem data for the 2-D stochastic minimum-time problem.
+
+This module is shared by the FP64 oracle tests, the GPU tests and ``bench.py``.
+It holds only the *data* of a problem instance -- grid geometry, speed field,
+target / obstacle mask, the boundary sectors Gamma_p and the discretised
+control set -- never any step of the solution method (no interpolation, no
+value iteration, no synthesis, no labelling).  Both the oracle and the CUDA
+path receive these arrays as inputs.
+
+Conventions (shared by every consumer):
+  * n nodes per side on [-1, 1]^2, dx = 2/(n-1), node (i, j) sits at
+    (-1 + i*dx, -1 + j*dx); arrays are row-major with i fastest, k = j*n + i.
+  * speed: float32 (n*n), the scalar c(x) of the dynamics f(x, a) = c(x) a
+    (Section 5, dynamics B).
+  * drift: optional float32 (n*n*2), interleaved (bx, by), the control-free
+    part b(x) of f(x, a) = b(x) + c(x) a (dynamics A and C of Section 5).
+  * mask: uint8 (n*n): 0 free, 1 target (u = g = 0), 2 obstacle.
+  * sector: int8 (n*n): the boundary subset Gamma_p a target node belongs
+    to (0..N_P-1), -1 for every other node.
+  * controls: float64 (N_A, 2): the points discretising the control set A.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+MASK_FREE = 0
+MASK_TARGET = 1
+MASK_OBSTACLE = 2
+
+
+def node_coords(n: int) -> Tuple[np.ndarray, float]:
+    """1-D node coordinates of the uniform grid on [-1, 1] and its step dx."""
+    if n < 3:
+        raise ValueError("n must be >= 3")
+    dx = 2.0 / (n - 1)
+    # (2i - (n-1)) / (n-1) is exactly antisymmetric about the centre node, so
+    # symmetric data (discs, even speed fields) stay bit-symmetric.
+    i = np.arange(n, dtype=np.float64)
+    return (2.0 * i - (n - 1)) / (n - 1), dx
+
+
+def mesh(n: int) -> Tuple[np.ndarray, np.ndarray]:
+    """2-D coordinate arrays X1, X2 of shape (n, n) indexed [j, i]."""
+    x, _ = node_coords(n)
+    X1, X2 = np.meshgrid(x, x, indexing="xy")
+    return X1, X2
+
+
+def control_set(n_controls: int, phase: float = 0.0) -> np.ndarray:
+    """N_A unit directions a_j = (cos(2 pi j/N_A + phase), sin(...)), float64 (N_A, 2)."""
+    if n_controls < 1:
+        raise ValueError("n_controls must be >= 1")
+    t = 2.0 * math.pi * np.arange(n_controls, dtype=np.float64) / n_controls + phase
+    return np.stack([np.cos(t), np.sin(t)], axis=1)
+
+
+# ----------------------------------------------------------------- speed fields
+
+def speed_constant(n: int, c: float = 1.0) -> np.ndarray:
+    return np.full(n * n, c, dtype=np.float32)
+
+
+def speed_sine(n: int, amplitude: float = 0.5, freq: float = 2.0 * math.pi) -> np.ndarray:
+    """c(x) = 1 + 0.5 sin(2 pi x1) sin(2 pi x2), evaluated in FP64, stored FP32."""
+    X1, X2 = mesh(n)
+    c = 1.0 + amplitude * np.sin(freq * X1) * np.sin(freq * X2)
+    return c.astype(np.float32).reshape(-1)
+
+
+def speed_halfplane(n: int, c_left: float = 1.0, c_right: float = 2.0) -> np.ndarray:
+    """c(x) = c_left + (c_right - c_left) * chi{x1 >= 0} (Section 5, Table 0 case B)."""
+    X1, _ = mesh(n)
+    c = np.where(X1 >= 0.0, c_right, c_left)
+    return c.astype(np.float32).reshape(-1)
+
+
+def speed_fourier(n: int, rng: np.random.Generator, n_modes: int = 8,
+                  lo: float = 0.2, hi: float = 1.8) -> np.ndarray:
+    """Random Fourier speed field: clip(1 + 0.5 sum_m A_m cos(pi(k1 x1 + k2 x2) + phi_m), lo, hi).
+
+    A_m ~ U[-1, 1], k1, k2 ~ U{1..4}, phi_m ~ U[0, 2 pi), all from ``rng``.
+    """
+    X1, X2 = mesh(n)
+    amp = rng.uniform(-1.0, 1.0, n_modes)
+    k1 = rng.integers(1, 5, n_modes)
+    k2 = rng.integers(1, 5, n_modes)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_modes)
+    s = np.zeros_like(X1)
+    for m in range(n_modes):
+        s += amp[m] * np.cos(math.pi * (k1[m] * X1 + k2[m] * X2) + phi[m])
+    c = np.clip(1.0 + 0.5 * s, lo, hi)
+    return c.astype(np.float32).reshape(-1)
+
+
+# ------------------------------------------------------------- masks / sectors
+
+def disc_target(n: int, centres: Sequence[Tuple[float, float]],
+                radii: Sequence[float]) -> np.ndarray:
+    """mask with 1 on nodes inside any closed disc |x - c| <= r, 0 elsewhere."""
+    X1, X2 = mesh(n)
+    m = np.zeros((n, n), dtype=bool)
+    for (cx, cy), r in zip(centres, radii):
+        m |= (X1 - cx) ** 2 + (X2 - cy) ** 2 <= r * r
+    return m.astype(np.uint8).reshape(-1)
+
+
+def square_boundary_target(n: int) -> np.ndarray:
+    """mask with 1 on the nodes of the boundary of the square (exit problem)."""
+    m = np.zeros((n, n), dtype=np.uint8)
+    m[0, :] = m[-1, :] = m[:, 0] = m[:, -1] = 1
+    return m.reshape(-1)
+
+
+def add_rect_obstacles(n: int, mask: np.ndarray,
+                       rects: Sequence[Tuple[float, float, float, float]]) -> np.ndarray:
+    """Mark nodes inside axis-aligned rectangles (x0, y0, x1, y1) as obstacles (2),
+    leaving target nodes untouched."""
+    X1, X2 = mesh(n)
+    out = mask.copy().reshape(n, n)
+    for (x0, y0, x1, y1) in rects:
+        inside = (X1 >= x0) & (X1 <= x1) & (X2 >= y0) & (X2 <= y1)
+        out[inside & (out == MASK_FREE)] = MASK_OBSTACLE
+    return out.reshape(-1)
+
+
+def sectors_about_centres(n: int, mask: np.ndarray,
+                          centres: Sequence[Tuple[float, float]],
+                          n_patches: int) -> np.ndarray:
+    """Split the target nodes into N_P angular sectors about the nearest disc centre.
+
+    sector = floor(N_P * (atan2(y - cy, x - cx) + pi) / (2 pi)) mod N_P on target
+    nodes, -1 elsewhere.  This is the partition of the target boundary into the
+    subsets Gamma_p from which the patches are grown.
+    """
+    X1, X2 = mesh(n)
+    sec = np.full((n, n), -1, dtype=np.int8)
+    tgt = mask.reshape(n, n) == MASK_TARGET
+    cs = np.asarray(centres, dtype=np.float64).reshape(-1, 2)
+    d2 = np.stack([(X1 - c[0]) ** 2 + (X2 - c[1]) ** 2 for c in cs], axis=0)
+    near = np.argmin(d2, axis=0)
+    cx = cs[near, 0]
+    cy = cs[near, 1]
+    ang = np.arctan2(X2 - cy, X1 - cx)
+    s = np.floor(n_patches * (ang + math.pi) / (2.0 * math.pi)).astype(np.int64) % n_patches
+    sec[tgt] = s[tgt].astype(np.int8)
+    return sec.reshape(-1)
+
+
+def sectors_square_sides(n: int, mask: np.ndarray) -> np.ndarray:
+    """Sectors 0..3 = bottom, right, top, left side of the square (corners go to
+    the first side listed that contains them); -1 on non-target nodes."""
+    sec = np.full((n, n), -1, dtype=np.int8)
+    sec[:, 0] = 3
+    sec[-1, :] = 2
+    sec[:, -1] = 1
+    sec[0, :] = 0
+    sec[mask.reshape(n, n) != MASK_TARGET] = -1
+    return sec.reshape(-1)
+
+
+# ----------------------------------------------------------------- instances
+
+@dataclasses.dataclass
+class Instance:
+    """One problem instance: the statement's data plus the discretisation knobs."""
+    n: int
+    controls: np.ndarray            # float64 (N_A, 2)
+    speed: np.ndarray               # float32 (n*n)
+    mask: np.ndarray                # uint8 (n*n)
+    sector: np.ndarray              # int8 (n*n)
+    h: float = 0.0                  # <= 0 means h = dx
+    lam: float = 1.0                # discount rate lambda
+    sigma: float = 0.0              # diffusion, displacement sqrt(2h)*sigma per axis
+    coarse_n: int = 0               # 0: no coarse grid
+    n_patches: int = 1
+    cost: float = 1.0               # running cost l
+    drift: Optional[np.ndarray] = None   # float32 (n*n*2) or None
+    name: str = ""
+
+    @property
+    def dx(self) -> float:
+        return 2.0 / (self.n - 1)
+
+    @property
+    def h_eff(self) -> float:
+        return self.h if self.h > 0 else self.dx
+
+    @property
+    def n_controls(self) -> int:
+        return int(self.controls.shape[0])
+
+
+def disc_instance(n: int, sigma: float, *, n_controls: int = 32, lam: float = 1.0,
+                  speed: Optional[np.ndarray] = None, radius: float = 0.1,
+                  centre: Tuple[float, float] = (0.0, 0.0), coarse_n: int = 0,
+                  n_patches: int = 16, h: float = 0.0, name: str = "") -> Instance:
+    """Discounted problem with one target disc and projected (reflecting) outer boundary."""
+    mask = disc_target(n, [centre], [radius])
+    sec = sectors_about_centres(n, mask, [centre], n_patches)
+    if speed is None:
+        speed = speed_constant(n, 1.0)
+    return Instance(n=n, controls=control_set(n_controls), speed=speed, mask=mask,
+                    sector=sec, h=h, lam=lam, sigma=sigma, coarse_n=coarse_n,
+                    n_patches=n_patches, name=name)
+
+
+def plain_101() -> Instance:
+    """The plain full-grid FP64 workload: 101^2 grid (dx = 0.02), c = 1, sigma = 0.05,
+    lambda = 1, h = dx, 32 controls, target disc |x| <= 0.1."""
+    return disc_instance(101, 0.05, n_controls=32, lam=1.0, n_patches=16,
+                         name="plain-101x101-sigma0.05")
+
+
+def patchy_1025(sigma: float, n: int = 1025, coarse_n: int = 129,
+                n_patches: int = 16) -> Instance:
+    """The patchy workload: c = 1 + 0.5 sin(2 pi x1) sin(2 pi x2), target disc |x| <= 0.1,
+    32 controls, lambda = 1, h = dx, coarse 129^2, 16 sectors.  Smaller n (with
+    (n-1) divisible by (coarse_n-1)) gives the same workload at test sizes."""
+    return disc_instance(n, sigma, n_controls=32, lam=1.0, speed=speed_sine(n),
+                         coarse_n=coarse_n, n_patches=n_patches,
+                         name=f"patchy-{n}x{n}-sigma{sigma:g}")
+
+
+def batched_instance(seed: int, n: Optional[int] = None) -> Instance:
+    """One instance of the many-instance workload: n ~ U{65..513} (odd),
+    random Fourier speed clipped to [0.2, 1.8], 1-3 target discs of radius
+    0.05-0.15, sigma ~ U[0, 0.1], lambda ~ U[0.5, 2], 32 controls, 4-16 patches."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    if n is None:
+        n = int(rng.integers(32, 257)) * 2 + 1
+    speed = speed_fourier(n, rng)
+    k = int(rng.integers(1, 4))
+    centres = [tuple(rng.uniform(-0.7, 0.7, 2)) for _ in range(k)]
+    radii = list(rng.uniform(0.05, 0.15, k))
+    mask = disc_target(n, centres, radii)
+    n_p = int(rng.integers(4, 17))
+    sec = sectors_about_centres(n, mask, centres, n_p)
+    sigma = float(rng.uniform(0.0, 0.1))
+    lam = float(rng.uniform(0.5, 2.0))
+    coarse = min(129, (n - 1) // 4 + 1)
+    while (n - 1) % (coarse - 1) != 0:
+        coarse -= 1
+    return Instance(n=n, controls=control_set(32), speed=speed, mask=mask, sector=sec,
+                    lam=lam, sigma=sigma, coarse_n=coarse, n_patches=n_p,
+                    name=f"batched-seed{seed}-n{n}")
+
+
+def random_values(n: int, seed: int, lo: float = 0.0, hi: float = 1.0,
+                  mask: Optional[np.ndarray] = None) -> np.ndarray:
+    """A seeded random value field (float64, n*n) for operator-level tests; target
+    nodes are set to 0 when a mask is given."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    u = rng.uniform(lo, hi, n * n)
+    if mask is not None:
+        u[mask == MASK_TARGET] = 0.0
+    return u

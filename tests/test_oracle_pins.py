@@ -1,0 +1,557 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names the passage of the paper (Cacace & Falcone) or the piece of
+mathematics that fixes the expected value:
+  * exact discrete solutions of on-grid cases, built here by index arithmetic
+    only (BFS shortest paths; dense policy iteration; brute-force policy
+    enumeration) -- these never call an interpolation routine;
+  * the sigma = 0 closed form (gauge distance of the control polygon);
+  * invariants of the scheme (monotonicity, beta-contraction, bounds, D4
+    symmetry, equality of the SLscheme2 / SLscheme3 fixed points);
+  * the paper's own worked counts (Section 5.1, Table 0).
+"""
+import collections
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import hjb_inputs as hi
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+# ----------------------------------------------------------------- helpers
+
+def bfs_steps(n, mask):
+    """4-neighbour graph distance (in steps) from every node to the target set."""
+    dist = np.full(n * n, -1, dtype=np.int64)
+    q = collections.deque()
+    for k in np.flatnonzero(mask == hi.MASK_TARGET):
+        dist[k] = 0
+        q.append(int(k))
+    while q:
+        k = q.popleft()
+        i, j = k % n, k // n
+        for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            ii, jj = i + di, j + dj
+            if 0 <= ii < n and 0 <= jj < n:
+                kk = jj * n + ii
+                if dist[kk] < 0 and mask[kk] == hi.MASK_FREE:
+                    dist[kk] = dist[k] + 1
+                    q.append(kk)
+    return dist
+
+
+AXIS = [(1, 0), (0, 1), (-1, 0), (0, -1)]   # directions of control_set(4): angles 0, pi/2, pi, 3pi/2
+
+
+def ongrid_transitions(n, mask, cells_per_step, d_cells):
+    """Markov-chain transition matrices P_m (dense, N x N) of the scheme when every
+    point lands on a grid node: axis controls, integer displacement c*h/dx and
+    integer diffusion displacement d.  Points leaving the square are projected
+    (coordinate clamp).  Built from indices only."""
+    N = n * n
+    Ps = []
+    for (ax, ay) in AXIS:
+        P = np.zeros((N, N))
+        for k in range(N):
+            if mask[k] != hi.MASK_FREE:
+                continue
+            i, j = k % n, k // n
+            c = int(cells_per_step[k])
+            fx, fy = i + c * ax, j + c * ay
+            pts = [(fx + d_cells, fy), (fx - d_cells, fy), (fx, fy + d_cells), (fx, fy - d_cells)]
+            for (px, py) in pts:
+                px = min(max(px, 0), n - 1)
+                py = min(max(py, 0), n - 1)
+                P[k, py * n + px] += 0.25
+        Ps.append(P)
+    return Ps
+
+
+def policy_iteration(Ps, mask, beta, h):
+    """Howard's policy iteration on the MDP u = min_m (beta P_m u + h) on free nodes,
+    u = 0 on targets.  Exact up to the dense solve's rounding."""
+    free = np.flatnonzero(mask == hi.MASK_FREE)
+    N = mask.size
+    pol = np.zeros(N, dtype=np.int64)
+    for _ in range(200):
+        A = np.eye(free.size)
+        rhs = np.full(free.size, h)
+        Pp = np.stack([Ps[pol[k]][k] for k in free])     # rows of the policy's matrix
+        A -= beta * Pp[:, free]
+        uf = np.linalg.solve(A, rhs)
+        u = np.zeros(N)
+        u[free] = uf
+        q = np.stack([beta * (P @ u) + h for P in Ps], axis=1)[free]
+        best = q.min(axis=1)
+        cur = q[np.arange(free.size), pol[free]]
+        improve = cur > best + 1e-13
+        if not improve.any():
+            return u
+        newpol = pol.copy()
+        newpol[free[improve]] = np.argmin(q[improve], axis=1)
+        pol = newpol
+    raise AssertionError("policy iteration did not terminate")
+
+
+def gauge_polygon(v1, v2, n_controls):
+    """Gauge of the convex hull of the unit directions at angles 2 pi j/N_A: the
+    maximum over the edge normals (2m+1) pi/N_A of (v . n_e) / cos(pi/N_A)."""
+    ang = (2.0 * np.arange(n_controls) + 1.0) * math.pi / n_controls
+    proj = v1[..., None] * np.cos(ang) + v2[..., None] * np.sin(ang)
+    return proj.max(axis=-1) / math.cos(math.pi / n_controls)
+
+
+def gauge_distance_to_disc(x1, x2, r, n_controls):
+    """min over the circle |y| = r of gauge(y - x): travel time to the disc with
+    unit speed and the relaxed control polygon (dense sampling + local refinement)."""
+    th = np.linspace(0, 2 * math.pi, 721)[:-1]
+    vals = gauge_polygon(r * np.cos(th)[None, :] - x1[:, None],
+                         r * np.sin(th)[None, :] - x2[:, None], n_controls)
+    t0 = th[np.argmin(vals, axis=1)]
+    lo, hi_ = t0 - 2 * math.pi / 720, t0 + 2 * math.pi / 720
+    g = (math.sqrt(5) - 1) / 2
+    f = lambda t: gauge_polygon(r * np.cos(t) - x1, r * np.sin(t) - x2, n_controls)
+    a, b = lo, hi_
+    for _ in range(60):
+        c1 = b - g * (b - a)
+        c2 = a + g * (b - a)
+        m = f(c1) < f(c2)
+        b = np.where(m, c2, b)
+        a = np.where(m, a, c1)
+    return np.minimum(f(0.5 * (a + b)), vals.min(axis=1))
+
+
+def axis_problem(n, speed_cells, sigma_cells, lam=1.0, mask=None):
+    """Problem whose points all land on nodes: h = dx, 4 axis controls,
+    c = speed_cells (integer), sigma with sqrt(2h) sigma = sigma_cells * dx."""
+    dx = 2.0 / (n - 1)
+    sigma = sigma_cells * dx / math.sqrt(2.0 * dx)
+    if mask is None:
+        mask = hi.disc_target(n, [(0.0, 0.0)], [0.3])
+    return oracle.Problem(n, hi.control_set(4), speed_cells.astype(np.float32), mask,
+                          h=dx, lam=lam, sigma=sigma)
+
+
+# ------------------------------------------------------------------- pins
+
+def test_bfs_exact_solution_axis_controls():
+    """sigma = 0, c = 1, h = dx, four axis controls: every foot is a neighbour node,
+    so the scheme is the discounted shortest-path recursion u = min_nbr beta u + h
+    whose solution is h (1 - beta^D)/(1 - beta), D = BFS distance to the target."""
+    n = 21
+    mask = hi.disc_target(n, [(0.3, -0.2)], [0.25])
+    P = axis_problem(n, np.ones(n * n), 0.0, lam=1.0, mask=mask)
+    u, sweeps, _ = P.solve(tol=1e-14)
+    assert sweeps > 0
+    D = bfs_steps(n, mask)
+    assert (D >= 0).all()
+    expect = P.h * (1.0 - P.beta ** D) / (1.0 - P.beta)
+    np.testing.assert_allclose(u, expect, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [2, 3])
+def test_policy_iteration_exact_ongrid_mdp(scheme):
+    """Drift 1 or 2 cells (c = 1 + chi{x1 >= 0}, the speed of Table 0) and a
+    diffusion displacement of exactly one cell: the scheme is a finite MDP whose
+    transition matrices are built here from indices.  Policy iteration gives its
+    exact solution; both the original and the modified scheme reach it."""
+    n = 17
+    cells = np.where(hi.mesh(n)[0].ravel() >= 0.0, 2.0, 1.0)
+    mask = hi.disc_target(n, [(-0.25, 0.1)], [0.3])
+    P = axis_problem(n, cells, 1.0, lam=0.7, mask=mask)
+    Ps = ongrid_transitions(n, mask, cells, 1)
+    exact = policy_iteration(Ps, mask, P.beta, P.h)
+    u, sweeps, _ = P.solve(tol=1e-15, scheme=scheme)
+    assert sweeps > 0
+    np.testing.assert_allclose(u, exact, rtol=0, atol=1e-12)
+
+
+def test_brute_force_policy_enumeration_tiny():
+    """On a 4x4 grid with six free nodes the optimal value is the componentwise
+    minimum over all 4^6 stationary policies of the policy values."""
+    n = 4
+    mask = np.ones(n * n, dtype=np.uint8)
+    free_nodes = [5, 6, 9, 10, 1, 14]
+    mask[free_nodes] = 0
+    cells = np.ones(n * n)
+    P = axis_problem(n, cells, 1.0, lam=0.5, mask=mask)
+    Ps = ongrid_transitions(n, mask, cells, 1)
+    free = np.array(sorted(free_nodes))
+    best = np.full(free.size, np.inf)
+    for pol in itertools.product(range(4), repeat=free.size):
+        Pp = np.stack([Ps[m][k] for m, k in zip(pol, free)])[:, free]
+        uf = np.linalg.solve(np.eye(free.size) - P.beta * Pp, np.full(free.size, P.h))
+        best = np.minimum(best, uf)
+    u, _, _ = P.solve(tol=1e-15)
+    np.testing.assert_allclose(u[free], best, rtol=0, atol=1e-12)
+
+
+def test_sigma0_converges_to_gauge_closed_form():
+    """sigma = 0, c = 1: as dx -> 0 the discrete value tends to (1 - e^{-lambda T})/lambda,
+    T the travel time to the disc with the relaxed control polygon (gauge distance).
+    The error shrinks with dx and stays within 0.5% + O(dx) of the Euclidean form."""
+    errs = []
+    for n in (51, 101, 201):
+        inst = hi.disc_instance(n, 0.0, n_controls=32, lam=1.0)
+        P = oracle.Problem.from_instance(inst)
+        X1, X2 = hi.mesh(n)
+        x1, x2 = X1.ravel(), X2.ravel()
+        rr = np.hypot(x1, x2)
+        order = np.argsort(rr, kind="stable")
+        u, sweeps, _ = P.solve(scheme=3, order=order, tol=1e-12)
+        assert sweeps > 0
+        sel = rr >= 0.25
+        T = gauge_distance_to_disc(x1[sel], x2[sel], 0.1, 32)
+        exact = (1.0 - np.exp(-T)) / 1.0
+        errs.append(np.abs(u[sel] - exact).max())
+        eucl = 1.0 - np.exp(-(rr[sel] - 0.1))
+        assert np.abs(u[sel] - eucl).max() <= 0.006 + 2.0 * P.dx
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] / errs[2] >= 2.5
+    assert errs[2] < 0.02
+
+
+def test_affine_field_is_reproduced_exactly():
+    """Q1 reproduces affine functions and the four Markov-chain points are
+    symmetric about the foot, so for u(x) = a0 + a1 x1 + a2 x2 the original scheme
+    gives min_m beta u(x + h f_m) + h l exactly wherever no point is projected."""
+    n = 33
+    rng = np.random.default_rng(7)
+    ctr = rng.normal(size=(9, 2))
+    speed = rng.uniform(0.2, 1.5, n * n).astype(np.float32)
+    drift = rng.uniform(-0.3, 0.3, (n * n, 2)).astype(np.float32)
+    mask = np.zeros(n * n, dtype=np.uint8)
+    P = oracle.Problem(n, ctr, speed, mask, lam=0.8, sigma=0.07, cost=1.3, drift=drift)
+    X1, X2 = hi.mesh(n)
+    x1, x2 = X1.ravel(), X2.ravel()
+    a0, a1, a2 = 0.4, -0.7, 0.25
+    u = a0 + a1 * x1 + a2 * x2
+    out, am, _ = P.apply(u, scheme=2)
+    fx = speed[:, None].astype(np.float64) * ctr[None, :, 0] + drift[:, 0:1]
+    fy = speed[:, None].astype(np.float64) * ctr[None, :, 1] + drift[:, 1:2]
+    q = P.beta * (a0 + a1 * (x1[:, None] + P.h * fx) + a2 * (x2[:, None] + P.h * fy)) + P.h * P.cost
+    reach = np.abs(P.h * np.sqrt(fx ** 2 + fy ** 2)).max() + math.sqrt(2 * P.h) * P.sigma
+    inner = (np.abs(x1) < 1 - reach - 1e-9) & (np.abs(x2) < 1 - reach - 1e-9)
+    assert inner.sum() > 100
+    np.testing.assert_allclose(out[inner], q[inner].min(axis=1), rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(am[inner], q[inner].argmin(axis=1))
+
+
+def test_modified_and_original_schemes_share_the_fixed_point():
+    """Section 3: the explicit form (eq. SLexplicit) has the same solution as the
+    implicit one (eq. SLimplicit); the modified scheme needs fewer sweeps."""
+    inst = hi.disc_instance(41, 0.08, n_controls=16, lam=1.0, speed=hi.speed_sine(41))
+    P = oracle.Problem.from_instance(inst)
+    u2, s2, _ = P.solve(scheme=2, tol=1e-14)
+    u3, s3, _ = P.solve(scheme=3, tol=1e-14)
+    assert s2 > 0 and s3 > 0
+    np.testing.assert_allclose(u3, u2, rtol=0, atol=1e-12)
+    assert s3 < s2
+    assert P.residual(u3) < 1e-13
+
+
+def test_monotone_contraction_and_bounds():
+    """The scheme is a convex combination of node values plus h l, discounted by
+    beta: u <= v implies Tu <= Tv, ||Tu - Tv|| <= beta ||u - v||, and the solution
+    lies in [0, h l/(1 - beta)].  Iterates from 0 increase, from u_max decrease."""
+    inst = hi.disc_instance(31, 0.06, n_controls=16, lam=2.0, speed=hi.speed_sine(31))
+    P = oracle.Problem.from_instance(inst)
+    rng = np.random.default_rng(3)
+    for scheme in (2, 3):
+        for _ in range(4):
+            u = P.fix_nonfree(rng.uniform(0, P.u_max, P.N))
+            v = P.fix_nonfree(u + rng.uniform(0, 0.3, P.N))
+            tu = P.apply(u, scheme)[0]
+            tv = P.apply(v, scheme)[0]
+            assert (tu <= tv + 1e-15).all()
+            w = P.fix_nonfree(rng.uniform(0, P.u_max, P.N))
+            tw = P.apply(w, scheme)[0]
+            free = P.mask == 0
+            assert np.abs(tu - tw)[free].max() <= P.beta * np.abs(u - w)[free].max() + 1e-15
+    u = np.zeros(P.N)
+    for _ in range(30):
+        nu = P.apply(u, 3)[0]
+        assert (nu >= u - 1e-15).all()
+        u = nu
+    u = P.fix_nonfree(np.full(P.N, P.u_max))
+    for _ in range(30):
+        nu = P.apply(u, 3)[0]
+        assert (nu <= u + 1e-15).all()
+        u = nu
+    us, _, _ = P.solve(tol=1e-14)
+    assert us.min() >= 0 and us.max() <= P.u_max + 1e-12
+
+
+def test_d4_symmetry():
+    """D4-symmetric data (even speed, disc at the centre, 8 | N_A) give a D4-symmetric
+    solution."""
+    n = 41
+    X1, X2 = hi.mesh(n)
+    speed = (1.0 + 0.3 * np.cos(math.pi * X1) * np.cos(math.pi * X2)).astype(np.float32).ravel()
+    inst = hi.disc_instance(n, 0.05, n_controls=32, lam=1.0, speed=speed, radius=0.2)
+    P = oracle.Problem.from_instance(inst)
+    u, _, _ = P.solve(tol=1e-14)
+    U = u.reshape(n, n)
+    for V in (U.T, U[::-1, :], U[:, ::-1], np.rot90(U)):
+        np.testing.assert_allclose(V, U, rtol=0, atol=1e-12)
+
+
+def _paper_mode(n, controls, speed, sigma, h, drift=None):
+    mask = hi.square_boundary_target(n)
+    return oracle.Problem(n, controls, speed, mask, h=h, lam=0.0, sigma=sigma, drift=drift,
+                          u_obstacle=1e6), mask
+
+
+def _left_to_right_top_to_bottom(n):
+    return np.array([j * n + i for j in range(n - 1, -1, -1) for i in range(n)], dtype=np.int64)
+
+
+def test_paper_case_a_single_pass():
+    """Section 5.1, Table 0 row A (eps = 0): with the self-dependency removed and nodes
+    processed left to right, the advection b . grad u = 1 with inflow on the left
+    converges in one sweep plus the checking sweep to the exact affine solution
+    u = x1 + 1, while the original scheme needs over a hundred sweeps.  Reading of
+    the sign: the paper's information enters from the left, i.e. the foot is
+    x_i - h b, realised here with drift -b."""
+    gold = json.load(open(GOLDEN))["table0"]["rows"][0]
+    n = 50
+    dx = 2.0 / (n - 1)
+    drift = np.zeros((n * n, 2), np.float32)
+    drift[:, 0] = -1.0
+    P, mask = _paper_mode(n, np.array([[1.0, 0.0]]), hi.speed_constant(n, 0.0), 0.0, dx / 2, drift)
+    order = _left_to_right_top_to_bottom(n)
+    u0 = np.full(n * n, 1e6)
+    u3, s3, _ = P.solve(u0, scheme=3, order=order, tol=1e-10)
+    u2, s2, _ = P.solve(u0, scheme=2, order=order, tol=1e-10, max_sweeps=5000)
+    x1 = hi.mesh(n)[0].ravel()
+    free = mask == 0
+    assert s3 == gold["sl3"] == 2
+    np.testing.assert_allclose(u3[free], x1[free] + 1.0, rtol=0, atol=1e-12)
+    assert s2 > 50 * s3
+
+
+def test_paper_table0_counts():
+    """Section 5.1, Table 0: the modified scheme needs far fewer sweeps than the
+    original in every row; for the eps = 0 rows of dynamics B the counts match the
+    paper's (26 and 33) to within two sweeps.  h = alpha dx / f_min with
+    alpha = 1/(1+Upsilon) (Section 4.1); the paper does not state h or the
+    tolerance, which is why only eps = 0 rows are compared in absolute terms."""
+    rows = json.load(open(GOLDEN))["table0"]["rows"]
+    n = 50
+    dx = 2.0 / (n - 1)
+    ctr16 = hi.control_set(16)
+    order = _left_to_right_top_to_bottom(n)
+    u0 = np.full(n * n, 1e6)
+    eps_sigma = {0.0: 0.0, 0.01: 0.1}
+    X1, X2 = hi.mesh(n)
+    rr = np.hypot(X1, X2)
+    rr[rr == 0] = 1.0
+    th = math.pi / 4
+    den = 1.0 + X1 ** 2 + X2 ** 2
+    zb = np.stack([((math.cos(th) * X1 - math.sin(th) * X2) / rr / den).ravel(),
+                   ((math.sin(th) * X1 + math.cos(th) * X2) / rr / den).ravel()], 1).astype(np.float32)
+    zc = (0.5 / den).astype(np.float32).ravel()
+    adrift = np.zeros((n * n, 2), np.float32)
+    adrift[:, 0] = -1.0
+    for row in rows:
+        sig = eps_sigma[row["eps"]]
+        if row["eq"] == "A":
+            P, _ = _paper_mode(n, np.array([[1.0, 0.0]]), hi.speed_constant(n, 0.0), sig, dx / 2, adrift)
+        elif row["dynamics"] == "c=1":
+            P, _ = _paper_mode(n, ctr16, hi.speed_constant(n, 1.0), sig, dx / 2)
+        elif row["eq"] == "B":
+            P, _ = _paper_mode(n, ctr16, hi.speed_halfplane(n), sig, dx / 3)
+        else:
+            P, _ = _paper_mode(n, ctr16, zc, sig, 0.1 * dx / (1.0 / 6.0), zb)
+        _, s2, _ = P.solve(u0, scheme=2, order=order, tol=1e-6, max_sweeps=5000)
+        _, s3, _ = P.solve(u0, scheme=3, order=order, tol=1e-6, max_sweeps=5000)
+        assert 0 < s3 and 0 < s2
+        assert s2 >= 1.8 * s3, row
+        if row["eq"] == "B" and row["eps"] == 0.0:
+            assert abs(s3 - row["sl3"]) <= 2, (row, s3)
+
+
+def test_coarse_grid_data_and_interpolation():
+    """Section 2: G_c nests in G; Q1 interpolation of u_c reproduces any bilinear
+    function exactly on G."""
+    n, nc = 33, 9
+    mask = hi.disc_target(n, [(0.0, 0.0)], [0.05])
+    speed = hi.speed_sine(n)
+    sc, mc = oracle.coarse_data(n, nc, speed, mask)
+    r = (n - 1) // (nc - 1)
+    S = speed.reshape(n, n)
+    np.testing.assert_array_equal(sc.reshape(nc, nc), S[::r, ::r])
+    # the small disc holds only the centre fine node; the centre coarse node
+    # sits on it, so exactly one coarse target
+    assert mask.sum() == 1 and mc.sum() == 1 and mc.reshape(nc, nc)[nc // 2, nc // 2] == 1
+    Xc1, Xc2 = hi.mesh(nc)
+    uc = (0.3 + 0.2 * Xc1 - 0.5 * Xc2 + 0.7 * Xc1 * Xc2).ravel()
+    uh = oracle.interp_coarse(nc, uc, n, np.zeros(n * n, np.uint8), 9.0)
+    X1, X2 = hi.mesh(n)
+    np.testing.assert_allclose(uh, (0.3 + 0.2 * X1 - 0.5 * X2 + 0.7 * X1 * X2).ravel(), atol=1e-14)
+    with pytest.raises(ValueError):
+        oracle.coarse_data(33, 10, speed, mask)
+
+
+def test_coarse_target_window_keeps_small_targets():
+    """A target that misses every coarse node still marks the nearest coarse node."""
+    n, nc = 65, 17
+    mask = hi.disc_target(n, [(0.05, 0.05)], [0.03])
+    assert mask.sum() >= 1
+    _, mc = oracle.coarse_data(n, nc, hi.speed_constant(n), mask)
+    assert mc.sum() >= 1
+
+
+def test_synthesis_follows_steepest_descent_of_affine_field():
+    """eq. discrete-synthesis on an affine u_hat: beta u_hat(x + h c a) + h l is smallest
+    for the control most opposed to grad u_hat (ties to the lowest index)."""
+    n = 29
+    ctr = hi.control_set(24)
+    mask = np.zeros(n * n, np.uint8)
+    P = oracle.Problem(n, ctr, hi.speed_constant(n, 0.8), mask, lam=1.0)
+    X1, X2 = hi.mesh(n)
+    g = np.array([0.6, -0.35])
+    uh = (1.0 + g[0] * X1 + g[1] * X2).ravel()
+    a = P.synthesis(uh)
+    expect = int(np.argmin(ctr @ g))
+    x1, x2 = X1.ravel(), X2.ravel()
+    inner = (np.abs(x1) < 1 - 2 * P.h) & (np.abs(x2) < 1 - 2 * P.h)
+    assert (a[inner] == expect).all()
+
+
+def test_labels_hand_built_rows():
+    """Section 4.3, eq. discrete-advection read winner-take-all.  Target column
+    i = 4 on a 9x9 grid with sector = row index; every other node steers
+    horizontally toward it with a one-cell step, so each node's patch is its row."""
+    n = 9
+    mask = np.zeros((n, n), np.uint8)
+    mask[:, 4] = 1
+    sector = np.full((n, n), -1, np.int8)
+    sector[:, 4] = np.arange(n)
+    ctr = hi.control_set(4)             # 0: east, 1: north, 2: west, 3: south
+    a = np.where(np.arange(n)[None, :] < 4, 0, 2).astype(np.uint8).repeat(n, 0)
+    a[:, 4] = 255
+    P = oracle.Problem(n, ctr, hi.speed_constant(n, 1.0), mask.ravel(), h=0.0)
+    succ = P.successors(a.ravel())
+    lab = P.labels(succ, sector.ravel(), n)
+    np.testing.assert_array_equal(lab.reshape(n, n), np.arange(n)[:, None].repeat(n, 1))
+
+
+def test_labels_cycles_selfloops_obstacles_and_ties():
+    """Chains that end in a cycle, in a zero-speed self-loop or at an obstacle are
+    'leftover' (label N_P).  Half-cell steps round back onto the node itself, so the
+    second-heaviest vertex is taken (the node cannot inform itself): an east step of
+    half a cell goes to the east neighbour; a diagonal half step has equal weights
+    on its two axis neighbours and goes to the lower linear index."""
+    n = 7
+    N = n * n
+    mask = np.zeros(N, np.uint8)
+    mask[0] = 1
+    mask[6] = 2
+    sector = np.full(N, -1, np.int8)
+    sector[0] = 3
+    ctr = np.array([[1.0, 0.0], [-1.0, 0.0], [math.sqrt(0.5), math.sqrt(0.5)], [0.0, -1.0]])
+    speed = np.ones(N, np.float32)
+    a = np.full(N, 1, np.uint8)                  # everyone steps west one cell
+    a[0] = a[6] = 255
+    k_a, k_b = 3 * n + 3, 3 * n + 4              # two nodes pointing at each other
+    a[k_a], a[k_b] = 0, 1
+    k_self = 5 * n + 5
+    speed[k_self] = 0.0                          # zero speed: foot on the node itself
+    a[5] = 0                                     # node (5,0) steps east onto the obstacle (6,0)
+    P = oracle.Problem(n, ctr, speed, mask)
+    succ = P.successors(a)
+    lab = P.labels(succ, sector, 4)
+    assert succ[k_a] == k_b and succ[k_b] == k_a
+    assert lab[k_a] == 4 and lab[k_b] == 4 and lab[3 * n + 5] == 4
+    assert succ[k_self] == k_self and lab[k_self] == 4
+    assert lab[5] == 4
+    assert lab[1] == 3 and lab[4] == 3          # row 0 west of the obstacle reaches the target
+    half = oracle.Problem(n, ctr, speed, mask, h=(2.0 / (n - 1)) / 2)
+    a2 = np.zeros(N, np.uint8)
+    k = 2 * n + 2
+    s = half.successors(a2)
+    assert s[k] == k + 1
+    a2[:] = 2
+    s = half.successors(a2)
+    assert s[k] == k + 1                         # tie between k+1 and k+n -> lower index
+
+
+def test_band_keys_follow_travel_time():
+    """Bands on the travel-time scale T = -log(1 - lambda u)/lambda, the inverse of
+    u = (1 - e^{-lambda T})/lambda."""
+    lam, width = 1.5, 0.01
+    b = np.arange(0, 200)
+    u = (1.0 - np.exp(-lam * (b + 0.5) * width)) / lam
+    keys = oracle.band_keys(u, np.zeros(u.size, np.uint8), lam, width, 1 << 20)
+    np.testing.assert_array_equal(keys, b)
+    keys0 = oracle.band_keys((b + 0.5) * width, np.zeros(u.size, np.uint8), 0.0, width, 50)
+    np.testing.assert_array_equal(keys0, np.minimum(b, 49))
+
+
+def test_argmin_ties_go_to_lowest_control():
+    """Duplicated controls give exactly tied candidates in the min of eq. SLscheme3 and
+    of eq. discrete-synthesis; the tie goes to the lowest index (a reading: the paper
+    compares candidates directly and names no tie rule)."""
+    n = 21
+    base = hi.control_set(8)
+    ctr = np.concatenate([base[3:4], base, base])          # control 0 duplicates control 4, etc.
+    inst = hi.disc_instance(n, 0.05, n_controls=8, lam=1.0, speed=hi.speed_sine(n))
+    P = oracle.Problem(n, ctr, inst.speed, inst.mask, lam=1.0, sigma=0.05)
+    u, _, _ = P.solve(tol=1e-13)
+    _, am, _ = P.apply(u, 3)
+    free = inst.mask == 0
+    assert (am[free] <= 8).all()
+    # the winner among the duplicated copies is always the first copy
+    dup = am[free] >= 1
+    assert not (am[free][dup] == 9).any()
+    a = P.synthesis(u)
+    assert (a[free] <= 8).all()
+
+
+def test_synthesis_values_on_affine_field():
+    """The synthesis objective beta u_hat(x + h c a_m) + h l is exact on an affine u_hat."""
+    n = 25
+    ctr = hi.control_set(12)
+    mask = np.zeros(n * n, np.uint8)
+    P = oracle.Problem(n, ctr, hi.speed_constant(n, 0.9), mask, lam=1.3, cost=0.7)
+    X1, X2 = hi.mesh(n)
+    uh = (0.5 + 0.3 * X1 - 0.2 * X2).ravel()
+    k = (n // 2) * n + n // 2 + 3
+    vals = P.synthesis_values(uh, np.array([k]))[0]
+    x1, x2 = X1.ravel()[k], X2.ravel()[k]
+    c = float(np.float32(0.9))                             # the speed is stored in FP32
+    exp = P.beta * (0.5 + 0.3 * (x1 + P.h * c * ctr[:, 0]) - 0.2 * (x2 + P.h * c * ctr[:, 1])) + P.h * 0.7
+    np.testing.assert_allclose(vals, exp, rtol=0, atol=1e-14)
+
+
+def test_successor_weight_rules():
+    """Winner-take-all successor: (a) a foot exactly between two vertices (equal Q1
+    weights) goes to the lower index; (b) when the heaviest vertex is the node itself,
+    the second-heaviest is the neighbour along the axis whose fraction is closer to 1/2:
+    for a step (0.3, 0.1) the weights of (i+1, j) and (i, j+1) are 0.27 and 0.07."""
+    n = 11
+    N = n * n
+    mask = np.zeros(N, np.uint8)
+    dx = 2.0 / (n - 1)
+    k = 5 * n + 5
+    a = np.zeros(N, np.uint8)
+    # (a) foot at i + 1.5: vertices i+1 and i+2 weigh 1/2 each -> i+1
+    P = oracle.Problem(n, np.array([[1.0, 0.0]]), hi.speed_constant(n, 1.5), mask, h=dx)
+    assert P.successors(a)[k] == k + 1
+    # same on the y axis: foot at j + 1.5 -> (i, j+1)
+    P = oracle.Problem(n, np.array([[0.0, 1.0]]), hi.speed_constant(n, 1.5), mask, h=dx)
+    assert P.successors(a)[k] == k + n
+    # (b) step (0.3, 0.1) rounds onto the node itself -> east neighbour
+    P = oracle.Problem(n, np.array([[0.6, 0.2]]), hi.speed_constant(n, 1.0), mask, h=dx / 2)
+    assert P.successors(a)[k] == k + 1
+    # step (0.1, -0.3): rounds onto itself, y fraction is closer to 1/2 -> south neighbour
+    P = oracle.Problem(n, np.array([[0.2, -0.6]]), hi.speed_constant(n, 1.0), mask, h=dx / 2)
+    assert P.successors(a)[k] == k - n
