@@ -1,0 +1,267 @@
+/*
+ * hjb.h -- C ABI of the GB300 (sm_103a) solver for the 2-D second-order HJB
+ * equation of a stochastic minimum-time problem, discretised by the
+ * Markov-chain semi-Lagrangian scheme without self-dependency and solved inside
+ * the patchy (dynamic) domain decomposition of Cacace & Falcone, "A dynamic
+ * domain decomposition for a class of second order semi-linear equations".
+ *
+ * Problem (Section 3, eqs. HJB2 and SDE, with a discount):
+ *     dX = f(X, a) dt + sigma dW,   f(x, a) = b(x) + c(x) a,   l = const,
+ *     u = 0 on the target, value = E[ int_0^tau e^{-lambda t} l dt ].
+ * Scheme (Section 3, eq. SLscheme3; 2-D isotropic form of Section 4.1):
+ *     for every free node x_i and control a in the discrete set A,
+ *       x_{i,k}^{a,s} = x_i + h f(x_i, a) + s sqrt(2h) sigma e_k   (k = 1,2, s = +-1),
+ *       u(x_i) = min_a ( beta Lambda1'(a) + h l ) / ( 1 - beta Lambda0(a) ),
+ *     with Q1 interpolation, beta = 1/(1 + lambda h), points projected onto the
+ *     square, Lambda0 the self weights and Lambda1' the rest (eq. self-dependency).
+ *
+ * Grid: n nodes per side on [-1,1]^2, dx = 2/(n-1); node (i, j) sits at
+ * (-1 + i dx, -1 + j dx) and every per-node array is row-major with i fastest:
+ * element k = j*n + i.
+ *
+ * Call order (Section 4.3, the patchy algorithm):
+ *   hjb_create_problem  -> hjb_coarse_solve -> hjb_build_patches -> hjb_solve_patches
+ *   hjb_solve_full (plain full-grid value iteration, the static comparator) may be
+ *   called at any time after creation.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: HJB_OK (0) or a negative HJB_ERR_* code.  The library never
+ *     aborts the process; hjb_last_error() gives a one-line message for the
+ *     calling thread.  After HJB_ERR_CUDA the problem must be destroyed.
+ *   - Host pointers are plain host memory (pageable or pinned); the library
+ *     copies inputs at the call and writes outputs into caller-owned buffers
+ *     before returning.  The library owns every device buffer it allocates.
+ *   - All device work of a problem runs on the stream given at creation (NULL:
+ *     a stream the library creates).  Entry points that return host data
+ *     synchronise that stream.
+ *   - A problem object may be used by one host thread at a time.
+ */
+#ifndef HJB_H
+#define HJB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HJB_OK                  0
+#define HJB_ERR_INVALID_ARG    -1   /* bad size, NULL pointer, NaN/Inf input, non-nesting grids */
+#define HJB_ERR_CUDA           -2   /* a CUDA runtime call failed                               */
+#define HJB_ERR_OOM            -3   /* device allocation failed                                 */
+#define HJB_ERR_STATE          -4   /* call out of order (e.g. solve_patches before build)      */
+#define HJB_ERR_NOT_CONVERGED  -5   /* sweep/pass cap reached; the state is valid               */
+#define HJB_ERR_TIMEOUT        -6   /* a device-side wait hit its time limit; state is valid   */
+
+#define HJB_MASK_FREE      0
+#define HJB_MASK_TARGET    1
+#define HJB_MASK_OBSTACLE  2
+
+#define HJB_MAX_CONTROLS 255
+#define HJB_MAX_PATCHES  126
+
+typedef struct hjb_problem hjb_problem;
+
+/* Problem description (Section 3 data, Section 4.3 initialisation). */
+typedef struct {
+    int32_t n;            /* nodes per side of the fine grid G, 3 <= n <= 16385             */
+    int32_t n_controls;   /* N_A: points discretising the control set, 1..255              */
+    double  h;            /* time step; <= 0 selects h = dx                                  */
+    double  lambda;       /* discount rate >= 0; beta = 1/(1 + lambda h)                     */
+    double  sigma;        /* diffusion >= 0; points at +-sqrt(2h) sigma e_k                  */
+    double  cost;         /* running cost l > 0 (constant)                                   */
+    int32_t coarse_n;     /* nodes per side of the coarse grid G_c; (n-1) % (coarse_n-1) == 0;
+                             0 = no coarse grid (coarse_solve / build_patches unavailable)    */
+    int32_t n_patches;    /* N_P: number of boundary subsets Gamma_p, 1..126                 */
+    int32_t scheme;       /* 3: modified scheme SLscheme3 (default), 2: original SLscheme2   */
+    double  band_width;   /* width of the causal bands in units of h (<= 0: 1.0)             */
+    int32_t band_window;  /* passes > 0 revisit a group of bands if a group within this many
+                             bands changed by more than the tolerance (<= 0: 8)               */
+    int32_t band_group;   /* consecutive bands per grid-wide wave (<= 0: 1)                   */
+    int32_t wave_warps;   /* warps of the band-wave kernel = nodes in flight; <= 0: every
+                             co-resident warp                                                  */
+    int32_t resort_passes;/* after each of the first k FP32 passes, re-sort the free nodes by
+                             the current value instead of u_hat (0: never)                    */
+    int32_t reserved;     /* must be 0                                                        */
+} hjb_desc;
+
+/* Per-call statistics; every field is written by the call that receives it. */
+typedef struct {
+    int32_t sweeps;                /* full sweeps (solve_full, coarse_solve) or passes (solve_patches) */
+    int32_t status;                /* the call's return code                                     */
+    int64_t node_updates;          /* free-node scheme evaluations performed                     */
+    int64_t node_control_updates;  /* node_updates x N_A                                          */
+    double  residual;              /* FP64 sup-residual ||T u - u||_inf (eq. SLscheme2), or -1    */
+    double  increment;             /* last sup-increment of the iteration                        */
+    double  ms_total;              /* device time of the call (CUDA events)                      */
+    double  ms_stage[8];           /* per-stage device time, see each entry point                */
+    int32_t fp32_passes;           /* solve_patches / solve_full: passes (sweeps) in FP32         */
+    int32_t fp64_passes;           /* passes (sweeps) in FP64                                     */
+} hjb_stats;
+
+/* Regime of the upwind diffusion-ball condition (Section 4.1, eqs. upper-bound,
+ * lower-bound, upper-alpha, lower-alpha, hyperbolicity) for a problem with speed
+ * range [f_min, f_max] and diffusion eps (paper's notation; eps = sigma^2 here). */
+typedef struct {
+    double upsilon;      /* f_max / f_min                                     */
+    double omega;        /* f_min / (2 eps)                                    */
+    double alpha_lower;  /* 1/(omega dx)                      (eq. lower-alpha) */
+    double alpha_upper;  /* 1/Upsilon - (sqrt(1+4 omega dx Upsilon)-1)/(2 omega dx Upsilon^2) (eq. upper-alpha) */
+    double alpha;        /* 1/(1+Upsilon), the choice valid whenever the condition holds */
+    double tau_dx;       /* dx/(1+Upsilon): the condition is 1/omega < tau_dx (eq. hyperbolicity) */
+    double eps_threshold;/* eps below which the condition holds: f_min dx / (2 (1+Upsilon)) */
+    double h;            /* alpha dx / f_min                                    */
+    int32_t holds;       /* 1 if 1/omega < tau_dx                               */
+    int32_t upper_ok;    /* h f_max + sqrt(2 eps h) < dx at h   (eq. upper-bound) */
+    int32_t lower_ok;    /* h f_min - sqrt(2 eps h) > 0 at h    (eq. lower-bound) */
+    int32_t reach_cells; /* ceil((h f_max + sqrt(2 eps h)) / dx): interpolation reach */
+} hjb_regime_info;
+
+/* hjb_regime -- host-only, no GPU needed.  Section 4.1.  dx > 0, 0 < f_min <= f_max,
+ * eps >= 0 (eps = 0: omega = +inf, the condition holds).  Returns HJB_OK or
+ * HJB_ERR_INVALID_ARG. */
+int hjb_regime(double dx, double f_min, double f_max, double eps, hjb_regime_info* out);
+
+/* hjb_create_problem -- Section 4.3 "Initialization": builds G (and G_c when
+ * desc->coarse_n > 0), uploads the data and the control set.
+ *   speed    : host float[n*n], c(x) >= 0 (finite).
+ *   mask     : host uint8[n*n], HJB_MASK_*; target nodes hold u = g = 0, obstacle
+ *              nodes hold l/(lambda) + h l (the value of never reaching the target).
+ *   sector   : host int8[n*n], the boundary subset Gamma_p of each target node
+ *              (0..n_patches-1) or -1; may be NULL when no patches are built.
+ *   controls : host double[2*n_controls], a_m = (controls[2m], controls[2m+1]).
+ *   drift    : host float[2*n*n] interleaved (b_x, b_y) or NULL (b = 0).
+ *   cuda_stream : a cudaStream_t owned by the caller, or NULL.
+ *   out      : receives the new problem (NULL on failure).
+ * Errors: HJB_ERR_INVALID_ARG (sizes, NULL, NaN/Inf, lambda = 0 with obstacles,
+ * non-nesting coarse grid), HJB_ERR_OOM, HJB_ERR_CUDA.  The initial value is
+ * u = 0 on free nodes. */
+int hjb_create_problem(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                       const int8_t* sector, const double* controls, const float* drift,
+                       void* cuda_stream, hjb_problem** out);
+
+/* hjb_create_problem_device -- as hjb_create_problem, but speed, mask, sector and
+ * drift are DEVICE pointers (e.g. torch CUDA tensors' data_ptr) on the current
+ * device; they are copied device-to-device on cuda_stream.  controls stays a host
+ * pointer. */
+int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                              const int8_t* sector, const double* controls,
+                              const float* drift, void* cuda_stream, hjb_problem** out);
+
+/* hjb_coarse_solve -- Section 4.3 "Pre-computation", first item: starting from
+ * u_c^0 = l(1/lambda + h) off the target (the paper's "very big value"), iterate
+ * SLscheme3 with sigma = 0 on G_c until the sup-increment is <= tol_c.  G_c is
+ * nested in G: coarse node (I,J) is fine node (rI, rJ), r = (n-1)/(coarse_n-1);
+ * its speed is the fine speed there; it is a target when a fine target node lies
+ * within r/2 fine cells in both axes, else an obstacle when its fine node is one.
+ * Time step h_c = h r.  ms_stage[0] = coarse solve.
+ * Errors: HJB_ERR_STATE (no coarse grid), HJB_ERR_NOT_CONVERGED (max_sweeps). */
+int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats* stats);
+
+/* hjb_build_patches -- Section 4.3 "Pre-computation", remaining items:
+ *   u_hat = Q1 interpolation of u_c on G (also the initial value of the fine
+ *           iteration: "starting from u_hat");
+ *   a*    = argmin_a beta u_hat(x_i + h f(x_i,a)) + h l  (eq. discrete-synthesis),
+ *           ties to the lowest control index;
+ *   labels: winner-take-all reading of eq. discrete-advection -- each free node
+ *           takes the patch at the end of its successor chain, the successor being
+ *           the heaviest Q1 vertex of the foot x_i + h f(x_i, a*) other than x_i
+ *           (foot computed by a fixed FP32 operation sequence); chains ending in a
+ *           cycle or at an obstacle get label n_patches ("leftover");
+ *   order : free nodes grouped by (causal band, patch), bands by increasing
+ *           travel time T(u_hat) = -log(1 - lambda u_hat)/lambda (Section 4.2).
+ * ms_stage: [0] interpolation, [1] synthesis + band keys, [2] successors + labels,
+ * [3] ordering.  Errors: HJB_ERR_STATE (coarse_solve not run). */
+int hjb_build_patches(hjb_problem* p, hjb_stats* stats);
+
+/* hjb_set_feedback -- replace a* by the caller's host uint8[n*n] (values < N_A on
+ * free nodes, ignored elsewhere) and recompute successors, labels and ordering
+ * from it (the band keys keep u_hat).  Requires build_patches. */
+int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
+
+/* hjb_solve_patches -- Section 4.3 "Computation": from the current value (u_hat
+ * after build_patches), iterate SLscheme3 (with sigma) in place on the single
+ * shared array (sharp interfaces: the transmission condition is the identity),
+ * visiting the bands in increasing order, band_group bands per grid-wide wave
+ * (nodes of a wave taken in sorted order by the wave_warps warps in flight);
+ * passes after the first skip groups whose neighbourhood did not change.  FP32 until a
+ * pass's sup-increment is <= tol32; then, if tol64 > 0, FP64 passes until the
+ * FP64 sup-residual ||T2 u - u|| is <= tol64.  max_passes caps each phase.
+ * ms_stage: [0] FP32 passes, [1] promotion + residuals, [2] FP64 passes.
+ * Errors: HJB_ERR_STATE (build_patches not run), HJB_ERR_NOT_CONVERGED,
+ * HJB_ERR_TIMEOUT (a grid-wide wait exceeded its limit). */
+int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_passes,
+                      hjb_stats* stats);
+
+/* hjb_solve_full -- plain full-grid Jacobi value iteration (the static comparator
+ * of Section 5.4, without decomposition or ordering): from u = 0, u <- T u on every
+ * free node until the sup-increment is <= tol, in FP32 (precision = 32) or FP64
+ * (precision = 64).  For precision 32 and tol64 > 0, FP64 Jacobi sweeps follow
+ * until the FP64 sup-increment (= residual) is <= tol64.  max_sweeps caps each
+ * phase.  ms_stage: [0] FP32 sweeps, [1] FP64 sweeps. */
+int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64,
+                   int32_t max_sweeps, hjb_stats* stats);
+
+/* hjb_apply_operator -- one application of the scheme operator to a caller's
+ * value: out = T u on free nodes (u on the others), and argmin = the minimising
+ * control (-1 on non-free nodes; may be NULL).  precision 32 or 64, scheme 2 or 3.
+ * u, out: host double[n*n].  Used to check the operator itself at any size. */
+int hjb_apply_operator(hjb_problem* p, int32_t precision, int32_t scheme, const double* u,
+                       double* out, int32_t* argmin);
+
+/* hjb_residual -- FP64 sup-residual ||T2 u - u||_inf of the current value. */
+int hjb_residual(hjb_problem* p, double* residual);
+
+/* hjb_set_value -- warm start / resume: the current value becomes host double[n*n]
+ * (non-free nodes are reset to their fixed values).  Both precisions are set. */
+int hjb_set_value(hjb_problem* p, const double* u);
+
+/* hjb_get_value -- the current value (FP64 copy when the last solve ended in
+ * FP64, else FP32 widened) into host double[n*n].  Merge of Section 4.3 is
+ * implicit: all patches share one array. */
+int hjb_get_value(hjb_problem* p, double* u_out);
+
+/* hjb_get_coarse_value -- u_c into host double[coarse_n^2]. */
+int hjb_get_coarse_value(hjb_problem* p, double* uc_out);
+
+/* hjb_get_uhat -- u_hat (FP32 widened) into host double[n*n]. */
+int hjb_get_uhat(hjb_problem* p, double* uhat_out);
+
+/* hjb_get_feedback -- a* into host uint8[n*n] (255 on non-free nodes). */
+int hjb_get_feedback(hjb_problem* p, uint8_t* a_out);
+
+/* hjb_get_successors -- successor of each node into host int32[n*n] (self on
+ * non-free nodes). */
+int hjb_get_successors(hjb_problem* p, int32_t* succ_out);
+
+/* hjb_get_labels -- patch label of each node into host int8[n*n]: 0..N_P-1, or
+ * N_P for leftover / obstacle nodes; target nodes carry their sector. */
+int hjb_get_labels(hjb_problem* p, int8_t* label_out);
+
+/* hjb_get_order -- the ordering: band key of each node into host int32[n*n] (-1
+ * on non-free nodes, may be NULL), the node list into host int32[n_free] (may be
+ * NULL), the band offsets into host int32[n_bands+1] (may be NULL).  *n_free and
+ * *n_bands receive the sizes (may be NULL). */
+int hjb_get_order(hjb_problem* p, int32_t* keys_out, int32_t* order_out,
+                  int32_t* band_off_out, int32_t* n_free, int32_t* n_bands);
+
+/* hjb_device_info -- SM count and the number of co-resident blocks the band-wave
+ * kernel runs with (FP32 and FP64), for reporting. */
+int hjb_device_info(hjb_problem* p, int32_t* num_sms, int32_t* wave_blocks32,
+                    int32_t* wave_blocks64);
+
+/* hjb_destroy -- frees every device buffer and the stream the library created.
+ * NULL is ignored. */
+void hjb_destroy(hjb_problem* p);
+
+/* hjb_status_string -- static text for a return code. */
+const char* hjb_status_string(int code);
+
+/* hjb_last_error -- message of the last failure on the calling thread ("" if none). */
+const char* hjb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJB_H */

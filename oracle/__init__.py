@@ -31,6 +31,9 @@ def lib():
         L.orc_node_update.restype = ctypes.c_double
         L.orc_node_update.argtypes = [P(_Problem), P(ctypes.c_double), ctypes.c_int64,
                                       ctypes.c_int, P(ctypes.c_int32)]
+        L.orc_node_candidates.restype = None
+        L.orc_node_candidates.argtypes = [P(_Problem), P(ctypes.c_double), ctypes.c_int64,
+                                          ctypes.c_int, P(ctypes.c_double)]
         L.orc_fix_nonfree.restype = None
         L.orc_fix_nonfree.argtypes = [P(_Problem), P(ctypes.c_double)]
         L.orc_apply.restype = ctypes.c_double
@@ -135,6 +138,17 @@ class Problem:
         v = lib().orc_node_update(ctypes.byref(self._s), _ptr(u, ctypes.c_double), int(k),
                                   scheme, ctypes.byref(am))
         return v, am.value
+
+    def node_candidates(self, u: np.ndarray, nodes: np.ndarray, scheme: int = 3) -> np.ndarray:
+        """Every control's candidate value at the listed free nodes: (len(nodes), N_A)."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.empty((len(nodes), self.controls.shape[0]))
+        row = np.empty(self.controls.shape[0])
+        for t, k in enumerate(nodes):
+            lib().orc_node_candidates(ctypes.byref(self._s), _ptr(u, ctypes.c_double), int(k),
+                                      scheme, _ptr(row, ctypes.c_double))
+            out[t] = row
+        return out
 
     def fix_nonfree(self, u: np.ndarray) -> np.ndarray:
         u = np.array(u, dtype=np.float64, copy=True)

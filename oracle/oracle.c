@@ -166,6 +166,35 @@ double orc_node_update(const orc_problem *P, const double *u, int64_t k, int sch
     return best;
 }
 
+/* Every control's candidate value at free node k (the quantities the min of
+ * eq. SLscheme2 / SLscheme3 compares), vals[m] for m < N_A.  Used to judge
+ * whether a minimiser chosen elsewhere is a valid one at a near-tie. */
+void orc_node_candidates(const orc_problem *P, const double *u, int64_t k, int scheme,
+                         double *vals)
+{
+    static const double dirs[4][2] = {{1.0, 0.0}, {-1.0, 0.0}, {0.0, 1.0}, {0.0, -1.0}};
+    const double dx = orc_dx(P);
+    const double beta = orc_beta(P);
+    const double d = sqrt(2.0 * P->h) * P->sigma / dx;
+    for (int m = 0; m < P->n_controls; m++) {
+        double xi, eta;
+        foot(P, k, m, &xi, &eta);
+        double lam1 = 0.0, lam0 = 0.0;
+        for (int p = 0; p < 4; p++) {
+            double e, s;
+            q1_split(u, P->n, xi + d * dirs[p][0], eta + d * dirs[p][1], k, &e, &s);
+            lam1 += 0.25 * e;
+            lam0 += 0.25 * s;
+        }
+        if (scheme == 3) {
+            double den = 1.0 - beta * lam0;
+            vals[m] = den > 0.0 ? (beta * lam1 + P->h * P->cost) / den : INFINITY;
+        } else {
+            vals[m] = beta * (lam1 + lam0 * u[k]) + P->h * P->cost;
+        }
+    }
+}
+
 /* Values held on non-free nodes: u = g = 0 on the target, u_obstacle on obstacles. */
 void orc_fix_nonfree(const orc_problem *P, double *u)
 {

@@ -1,0 +1,212 @@
+"""GB300 (sm_103a) solver for the Markov-chain semi-Lagrangian value iteration of
+the 2-D second-order HJB equation inside the patchy domain decomposition
+(Cacace & Falcone, "A dynamic domain decomposition for a class of second order
+semi-linear equations").
+
+The compute path is the CUDA library behind the C ABI of ``include/hjb.h``;
+this package is its thin binding.  Names follow the C entry points:
+
+    p = Problem(desc_fields..., speed, mask, sector, controls)
+    p.coarse_solve(); p.build_patches(); stats = p.solve_patches(tol32, tol64)
+    u = p.get_value()
+
+PyTorch, when used, only supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, Desc, HJBError, RegimeInfo, Stats, check,
+                   header_functions, lib)
+
+__all__ = ["Problem", "HJBError", "regime", "lib", "header_functions", "HJB_ERR_NOT_CONVERGED"]
+
+
+def _c(a: np.ndarray, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def regime(dx: float, f_min: float, f_max: float, eps: float) -> dict:
+    """Upwind diffusion-ball regime (Section 4.1): Upsilon, omega, alpha bounds,
+    tau_dx, the threshold on eps and whether the condition holds.  Host only."""
+    out = RegimeInfo()
+    check(lib().hjb_regime(dx, f_min, f_max, eps, ctypes.byref(out)), "hjb_regime")
+    return {f: getattr(out, f) for f, _ in out._fields_}
+
+
+class Problem:
+    """One problem instance on the GPU (wraps an ``hjb_problem*``)."""
+
+    def __init__(self, n: int, controls: np.ndarray, speed: np.ndarray, mask: np.ndarray,
+                 sector: Optional[np.ndarray] = None, *, h: float = 0.0, lam: float = 1.0,
+                 sigma: float = 0.0, cost: float = 1.0, coarse_n: int = 0, n_patches: int = 1,
+                 scheme: int = 3, band_width: float = 1.0, band_window: int = 8,
+                 band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
+                 drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False):
+        self._h = None
+        self.n = int(n)
+        self.N = self.n * self.n
+        self.controls = _c(controls, np.float64).reshape(-1, 2)
+        self.n_controls = self.controls.shape[0]
+        self.coarse_n = int(coarse_n)
+        self.n_patches = int(n_patches)
+        d = Desc()
+        d.n, d.n_controls, d.h, d.lam, d.sigma, d.cost = (self.n, self.n_controls, float(h),
+                                                         float(lam), float(sigma), float(cost))
+        d.coarse_n, d.n_patches, d.scheme = self.coarse_n, self.n_patches, int(scheme)
+        d.band_width, d.band_window = float(band_width), int(band_window)
+        d.band_group, d.wave_warps, d.resort_passes = int(band_group), int(wave_warps), int(resort_passes)
+        self.desc = d
+        st = None
+        if stream is not None:
+            st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        handle = ctypes.c_void_p()
+        if device_inputs:
+            # torch CUDA tensors (or raw device pointers as ints)
+            ptr = lambda t: None if t is None else ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr())
+            rc = lib().hjb_create_problem_device(ctypes.byref(d), ptr(speed), ptr(mask), ptr(sector),
+                                                 _p(self.controls), ptr(drift), st,
+                                                 ctypes.byref(handle))
+        else:
+            self._speed = _c(speed, np.float32).reshape(-1)
+            self._mask = _c(mask, np.uint8).reshape(-1)
+            self._sector = None if sector is None else _c(sector, np.int8).reshape(-1)
+            self._drift = None if drift is None else _c(drift, np.float32).reshape(-1)
+            if self._speed.size != self.N or self._mask.size != self.N:
+                raise ValueError("speed and mask must have n*n entries")
+            rc = lib().hjb_create_problem(ctypes.byref(d), _p(self._speed), _p(self._mask),
+                                          _p(self._sector), _p(self.controls), _p(self._drift), st,
+                                          ctypes.byref(handle))
+        check(rc, "hjb_create_problem")
+        self._h = handle
+
+    @classmethod
+    def from_instance(cls, inst, **kw) -> "Problem":
+        args = dict(h=inst.h, lam=inst.lam, sigma=inst.sigma, cost=inst.cost,
+                    coarse_n=inst.coarse_n, n_patches=inst.n_patches, drift=inst.drift)
+        args.update(kw)
+        return cls(inst.n, inst.controls, inst.speed, inst.mask, inst.sector, **args)
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().hjb_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ----------------------------------------------------------- solve steps
+    @staticmethod
+    def _ret(rc: int, st: Stats, where: str, check_conv: bool) -> dict:
+        if rc == HJB_ERR_NOT_CONVERGED and not check_conv:
+            return st.as_dict()
+        check(rc, where)
+        return st.as_dict()
+
+    def coarse_solve(self, tol_c: float = 1e-6, max_sweeps: int = 100000,
+                     check_conv: bool = True) -> dict:
+        st = Stats()
+        rc = lib().hjb_coarse_solve(self._h, tol_c, max_sweeps, ctypes.byref(st))
+        return self._ret(rc, st, "hjb_coarse_solve", check_conv)
+
+    def build_patches(self) -> dict:
+        st = Stats()
+        check(lib().hjb_build_patches(self._h, ctypes.byref(st)), "hjb_build_patches")
+        return st.as_dict()
+
+    def set_feedback(self, a: np.ndarray) -> None:
+        a = _c(a, np.uint8).reshape(-1)
+        check(lib().hjb_set_feedback(self._h, _p(a)), "hjb_set_feedback")
+
+    def solve_patches(self, tol32: float = 5e-7, tol64: float = 1e-6, max_passes: int = 10000,
+                      check_conv: bool = True) -> dict:
+        st = Stats()
+        rc = lib().hjb_solve_patches(self._h, tol32, tol64, max_passes, ctypes.byref(st))
+        return self._ret(rc, st, "hjb_solve_patches", check_conv)
+
+    def solve_full(self, precision: int = 32, tol: float = 5e-7, tol64: float = 1e-6,
+                   max_sweeps: int = 200000, check_conv: bool = True) -> dict:
+        st = Stats()
+        rc = lib().hjb_solve_full(self._h, precision, tol, tol64, max_sweeps, ctypes.byref(st))
+        return self._ret(rc, st, "hjb_solve_full", check_conv)
+
+    def apply_operator(self, u: np.ndarray, precision: int = 64, scheme: int = 3):
+        u = _c(u, np.float64).reshape(-1)
+        out = np.empty(self.N)
+        am = np.empty(self.N, np.int32)
+        check(lib().hjb_apply_operator(self._h, precision, scheme, _p(u), _p(out), _p(am)),
+              "hjb_apply_operator")
+        return out, am
+
+    def residual(self) -> float:
+        r = ctypes.c_double()
+        check(lib().hjb_residual(self._h, ctypes.byref(r)), "hjb_residual")
+        return r.value
+
+    # -------------------------------------------------------------- state
+    def set_value(self, u: np.ndarray) -> None:
+        u = _c(u, np.float64).reshape(-1)
+        check(lib().hjb_set_value(self._h, _p(u)), "hjb_set_value")
+
+    def get_value(self) -> np.ndarray:
+        out = np.empty(self.N)
+        check(lib().hjb_get_value(self._h, _p(out)), "hjb_get_value")
+        return out
+
+    def get_coarse_value(self) -> np.ndarray:
+        out = np.empty(self.coarse_n * self.coarse_n)
+        check(lib().hjb_get_coarse_value(self._h, _p(out)), "hjb_get_coarse_value")
+        return out
+
+    def get_uhat(self) -> np.ndarray:
+        out = np.empty(self.N)
+        check(lib().hjb_get_uhat(self._h, _p(out)), "hjb_get_uhat")
+        return out
+
+    def get_feedback(self) -> np.ndarray:
+        out = np.empty(self.N, np.uint8)
+        check(lib().hjb_get_feedback(self._h, _p(out)), "hjb_get_feedback")
+        return out
+
+    def get_successors(self) -> np.ndarray:
+        out = np.empty(self.N, np.int32)
+        check(lib().hjb_get_successors(self._h, _p(out)), "hjb_get_successors")
+        return out
+
+    def get_labels(self) -> np.ndarray:
+        out = np.empty(self.N, np.int8)
+        check(lib().hjb_get_labels(self._h, _p(out)), "hjb_get_labels")
+        return out
+
+    def get_order(self):
+        nf, nb = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().hjb_get_order(self._h, None, None, None, ctypes.byref(nf), ctypes.byref(nb)),
+              "hjb_get_order")
+        keys = np.empty(self.N, np.int32)
+        order = np.empty(nf.value, np.int32)
+        off = np.empty(nb.value + 1, np.int32)
+        check(lib().hjb_get_order(self._h, _p(keys), _p(order), _p(off), None, None), "hjb_get_order")
+        return keys, order, off
+
+    def device_info(self) -> dict:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().hjb_device_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+              "hjb_device_info")
+        return {"num_sms": a.value, "wave_blocks32": b.value, "wave_blocks64": c.value}

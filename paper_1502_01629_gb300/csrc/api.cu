@@ -1,0 +1,1099 @@
+// C ABI of the solver (declared in include/hjb.h): problem construction and
+// device memory, the patchy call sequence of Section 4.3 (coarse solve ->
+// pre-computation -> band-ordered patch solve with FP64 polish), the plain
+// full-grid comparator, the regime helper of Section 4.1 and the getters.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hjb.h"
+#include "hjb_kernels.h"
+
+using namespace hjb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? HJB_ERR_OOM : HJB_ERR_CUDA,         \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr int kBandCap = 1 << 20;
+constexpr unsigned long long kTimeoutNs = 4000000000ull;   // grid-wide wait limit: 4 s
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+// Device allocation released at scope exit (test-path temporaries only).
+struct DevBuf {
+    void* ptr = nullptr;
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&ptr, bytes); }
+    ~DevBuf() {
+        if (ptr) cudaFree(ptr);
+    }
+};
+
+// Stage timer on the problem's stream.
+struct Timer {
+    cudaEvent_t ev[10];
+    int n = 0;
+    cudaStream_t st;
+    explicit Timer(cudaStream_t s) : st(s) {
+        for (auto& e : ev) cudaEventCreate(&e);
+    }
+    ~Timer() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
+    void mark() {
+        if (n < 10) cudaEventRecord(ev[n++], st);
+    }
+    // elapsed ms between marks a and b (after a stream sync)
+    double ms(int a, int b) {
+        float t = 0.0f;
+        if (a < n && b < n && cudaEventSynchronize(ev[b]) == cudaSuccess)
+            cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return (double)t;
+    }
+};
+
+void clear_stats(hjb_stats* s) {
+    if (!s) return;
+    std::memset(s, 0, sizeof(*s));
+    s->residual = -1.0;
+}
+
+}  // namespace
+
+struct hjb_problem {
+    hjb_desc desc{};
+    int n = 0, N = 0, na = 0, nc = 0, r = 0, np = 1;
+    double dx = 0, h = 0, beta = 0, hl = 0, uob = 0, sigma = 0, lambda = 0;
+    double reach = 0;     // max |h f| / dx + d, cells
+    int halo = 1;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 0;
+    bool has_drift = false;
+
+    // fine data
+    float* speed = nullptr;
+    float2* drift = nullptr;
+    uint8_t* mask = nullptr;
+    int8_t* sector = nullptr;
+    float2* ctrl32 = nullptr;
+    double2* ctrl64 = nullptr;
+    // values
+    float* u32 = nullptr;
+    float* u32b = nullptr;
+    double* u64 = nullptr;
+    double* u64b = nullptr;
+    bool value_f64 = false;
+    // coarse grid
+    float* speed_c = nullptr;
+    float2* drift_c = nullptr;
+    uint8_t* mask_c = nullptr;
+    float* uc = nullptr;
+    double hc = 0, beta_c = 0, hl_c = 0, uob_c = 0;
+    // pre-computation
+    float* uhat = nullptr;
+    uint8_t* a = nullptr;
+    int32_t* succ = nullptr;
+    int32_t* jump_a = nullptr;
+    int32_t* jump_b = nullptr;
+    int8_t* label = nullptr;
+    int32_t* key = nullptr;
+    int32_t* order = nullptr;
+    int32_t* bin_count = nullptr;
+    int32_t* bin_off = nullptr;
+    int32_t* band_off = nullptr;
+    unsigned int* inc_bits = nullptr;
+    int n_bands = 0, n_free = 0, bins_cap = 0, bands_cap = 0;
+    long long n_free_total = 0;   // free nodes of G
+    bool coarse_done = false, built = false;
+    // scratch
+    void* scratch = nullptr;      // small device scalars
+    void* host_pinned = nullptr;  // small pinned host scalars
+    unsigned int* inc_hist32 = nullptr;
+    unsigned long long* inc_hist64 = nullptr;
+    int hist_cap = 0;
+    int wave_blocks32 = 0, wave_blocks64 = 0;
+
+    GridView fine_view() const {
+        GridView g{};
+        g.n = n;
+        g.na = na;
+        g.speed = speed;
+        g.drift = has_drift ? drift : nullptr;
+        g.mask = mask;
+        g.ctrl32 = ctrl32;
+        g.ctrl64 = ctrl64;
+        const double s = h / dx;
+        const double d = std::sqrt(2.0 * h) * sigma / dx;
+        g.s32 = (float)s;
+        g.s64 = s;
+        g.d32 = (float)d;
+        g.d64 = d;
+        g.beta32 = (float)beta;
+        g.beta64 = beta;
+        g.hl32 = (float)hl;
+        g.hl64 = hl;
+        g.uob32 = (float)uob;
+        g.uob64 = uob;
+        return g;
+    }
+    GridView coarse_view() const {
+        GridView g{};
+        g.n = nc;
+        g.na = na;
+        g.speed = speed_c;
+        g.drift = has_drift ? drift_c : nullptr;
+        g.mask = mask_c;
+        g.ctrl32 = ctrl32;
+        g.ctrl64 = ctrl64;
+        const double dxc = 2.0 / (nc - 1);
+        const double s = hc / dxc;
+        g.s32 = (float)s;
+        g.s64 = s;
+        g.d32 = 0.0f;
+        g.d64 = 0.0;
+        g.beta32 = (float)beta_c;
+        g.beta64 = beta_c;
+        g.hl32 = (float)hl_c;
+        g.hl64 = hl_c;
+        g.uob32 = (float)uob_c;
+        g.uob64 = uob_c;
+        return g;
+    }
+};
+
+namespace {
+
+struct Scalars {
+    unsigned int inc32;
+    int max_key;
+    unsigned long long inc64;
+    CoarseResult coarse;
+    WaveResult wave;
+    GridSync sync;
+};
+
+Scalars* dscal(hjb_problem* p) { return reinterpret_cast<Scalars*>(p->scratch); }
+Scalars* hscal(hjb_problem* p) { return reinterpret_cast<Scalars*>(p->host_pinned); }
+
+int validate_desc(const hjb_desc* d) {
+    if (!d) return fail(HJB_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n < 3 || d->n > 16385) return fail(HJB_ERR_INVALID_ARG, "n=%d out of range [3,16385]", d->n);
+    if (d->n_controls < 1 || d->n_controls > HJB_MAX_CONTROLS)
+        return fail(HJB_ERR_INVALID_ARG, "n_controls=%d out of range", d->n_controls);
+    if (!(d->lambda >= 0.0) || !std::isfinite(d->lambda)) return fail(HJB_ERR_INVALID_ARG, "bad lambda");
+    if (!(d->sigma >= 0.0) || !std::isfinite(d->sigma)) return fail(HJB_ERR_INVALID_ARG, "bad sigma");
+    if (!(d->cost > 0.0) || !std::isfinite(d->cost)) return fail(HJB_ERR_INVALID_ARG, "cost must be > 0");
+    if (!std::isfinite(d->h)) return fail(HJB_ERR_INVALID_ARG, "bad h");
+    if (d->scheme != 2 && d->scheme != 3 && d->scheme != 0)
+        return fail(HJB_ERR_INVALID_ARG, "scheme must be 2 or 3");
+    if (d->n_patches < 1 || d->n_patches > HJB_MAX_PATCHES)
+        return fail(HJB_ERR_INVALID_ARG, "n_patches=%d out of range", d->n_patches);
+    if (d->coarse_n != 0) {
+        if (d->coarse_n < 3 || d->coarse_n > d->n || (d->n - 1) % (d->coarse_n - 1) != 0)
+            return fail(HJB_ERR_INVALID_ARG, "coarse_n=%d does not nest in n=%d", d->coarse_n, d->n);
+    }
+    if (!std::isfinite(d->band_width)) return fail(HJB_ERR_INVALID_ARG, "bad band_width");
+    if (d->resort_passes < 0) return fail(HJB_ERR_INVALID_ARG, "resort_passes must be >= 0");
+    if (d->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "reserved field must be 0");
+    return HJB_OK;
+}
+
+int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                  const int8_t* sector, const double* controls, const float* drift,
+                  void* cuda_stream, hjb_problem** out, bool device_inputs) {
+    g_last_error.clear();
+    if (!out) return fail(HJB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = validate_desc(desc);
+    if (rc) return rc;
+    if (!speed || !mask || !controls) return fail(HJB_ERR_INVALID_ARG, "speed, mask and controls are required");
+    const int n = desc->n;
+    const size_t N = (size_t)n * n;
+    const int na = desc->n_controls;
+
+    double amax = 0.0;
+    for (int m = 0; m < na; ++m) {
+        if (!std::isfinite(controls[2 * m]) || !std::isfinite(controls[2 * m + 1]))
+            return fail(HJB_ERR_INVALID_ARG, "control %d is not finite", m);
+        amax = std::fmax(amax, std::hypot(controls[2 * m], controls[2 * m + 1]));
+    }
+
+    // host-side validation of the per-node inputs (copied back for device inputs)
+    std::vector<float> hs;
+    std::vector<uint8_t> hm;
+    std::vector<int8_t> hsec;
+    std::vector<float> hd;
+    const float* s_h = speed;
+    const uint8_t* m_h = mask;
+    const int8_t* sec_h = sector;
+    const float* d_h = drift;
+    if (device_inputs) {
+        hs.resize(N);
+        hm.resize(N);
+        CU(cudaMemcpy(hs.data(), speed, N * sizeof(float), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hm.data(), mask, N, cudaMemcpyDeviceToHost));
+        s_h = hs.data();
+        m_h = hm.data();
+        if (sector) {
+            hsec.resize(N);
+            CU(cudaMemcpy(hsec.data(), sector, N, cudaMemcpyDeviceToHost));
+            sec_h = hsec.data();
+        }
+        if (drift) {
+            hd.resize(2 * N);
+            CU(cudaMemcpy(hd.data(), drift, 2 * N * sizeof(float), cudaMemcpyDeviceToHost));
+            d_h = hd.data();
+        }
+    }
+    double cmax = 0.0, bmax = 0.0;
+    long long n_free_total = 0;
+    bool any_obstacle = false, any_target = false;
+    for (size_t k = 0; k < N; ++k) {
+        if (!std::isfinite(s_h[k]) || s_h[k] < 0.0f) return fail(HJB_ERR_INVALID_ARG, "speed[%zu] invalid", k);
+        if (m_h[k] > HJB_MASK_OBSTACLE) return fail(HJB_ERR_INVALID_ARG, "mask[%zu]=%d invalid", k, m_h[k]);
+        any_obstacle |= (m_h[k] == HJB_MASK_OBSTACLE);
+        any_target |= (m_h[k] == HJB_MASK_TARGET);
+        if (m_h[k] == HJB_MASK_FREE) {
+            cmax = std::fmax(cmax, (double)s_h[k]);
+            ++n_free_total;
+        }
+        if (sec_h && m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
+            return fail(HJB_ERR_INVALID_ARG, "sector[%zu]=%d >= n_patches", k, sec_h[k]);
+        if (d_h) {
+            if (!std::isfinite(d_h[2 * k]) || !std::isfinite(d_h[2 * k + 1]))
+                return fail(HJB_ERR_INVALID_ARG, "drift[%zu] not finite", k);
+            if (m_h[k] == HJB_MASK_FREE)
+                bmax = std::fmax(bmax, std::hypot((double)d_h[2 * k], (double)d_h[2 * k + 1]));
+        }
+    }
+    (void)any_target;
+    if (any_obstacle && desc->lambda <= 0.0)
+        return fail(HJB_ERR_INVALID_ARG, "obstacles need lambda > 0 (their value is l/lambda + h l)");
+
+    hjb_problem* p = new hjb_problem();
+    p->desc = *desc;
+    if (p->desc.scheme == 0) p->desc.scheme = 3;
+    if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
+    if (p->desc.band_window <= 0) p->desc.band_window = 8;
+    if (p->desc.band_group <= 0) p->desc.band_group = 1;
+    p->n = n;
+    p->N = (int)N;
+    p->na = na;
+    p->np = desc->n_patches;
+    p->dx = 2.0 / (n - 1);
+    p->h = desc->h > 0.0 ? desc->h : p->dx;
+    p->lambda = desc->lambda;
+    p->sigma = desc->sigma;
+    p->beta = 1.0 / (1.0 + p->lambda * p->h);
+    p->hl = p->h * desc->cost;
+    p->uob = p->lambda > 0.0 ? p->hl / (1.0 - p->beta) : 1e6;
+    p->has_drift = drift != nullptr;
+    p->n_free_total = n_free_total;
+    p->reach = (p->h * (cmax * amax + bmax) + std::sqrt(2.0 * p->h) * p->sigma) / p->dx;
+    p->halo = sweep_halo(p->reach);
+    if (p->halo > 64) {
+        delete p;
+        return fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach);
+    }
+    auto bail = [&](int code) {
+        hjb_destroy(p);
+        return code;
+    };
+#define CUP(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? HJB_ERR_OOM : HJB_ERR_CUDA, \
+                             "%s failed: %s", #call, cudaGetErrorString(e_)));           \
+    } while (0)
+
+    CUP(cudaGetDevice(&p->device));
+    CUP(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (cuda_stream) {
+        p->st = (cudaStream_t)cuda_stream;
+    } else {
+        CUP(cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUP(cudaMalloc(&p->speed, N * sizeof(float)));
+    CUP(cudaMalloc(&p->mask, N));
+    CUP(cudaMalloc(&p->sector, N));
+    CUP(cudaMemcpyAsync(p->speed, speed, N * sizeof(float), kind, p->st));
+    CUP(cudaMemcpyAsync(p->mask, mask, N, kind, p->st));
+    if (sector) {
+        CUP(cudaMemcpyAsync(p->sector, sector, N, kind, p->st));
+    } else {
+        CUP(cudaMemsetAsync(p->sector, 0xff, N, p->st));
+    }
+    if (drift) {
+        CUP(cudaMalloc(&p->drift, N * sizeof(float2)));
+        CUP(cudaMemcpyAsync(p->drift, drift, N * sizeof(float2), kind, p->st));
+    }
+    {
+        std::vector<float2> c32(na);
+        std::vector<double2> c64(na);
+        for (int m = 0; m < na; ++m) {
+            c32[m] = make_float2((float)controls[2 * m], (float)controls[2 * m + 1]);
+            c64[m] = make_double2(controls[2 * m], controls[2 * m + 1]);
+        }
+        CUP(cudaMalloc(&p->ctrl32, na * sizeof(float2)));
+        CUP(cudaMalloc(&p->ctrl64, na * sizeof(double2)));
+        CUP(cudaMemcpy(p->ctrl32, c32.data(), na * sizeof(float2), cudaMemcpyHostToDevice));
+        CUP(cudaMemcpy(p->ctrl64, c64.data(), na * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+    CUP(cudaMalloc(&p->u32, N * sizeof(float)));
+    CUP(cudaMalloc(&p->u32b, N * sizeof(float)));
+    CUP(cudaMalloc(&p->u64, N * sizeof(double)));
+    CUP(cudaMalloc(&p->u64b, N * sizeof(double)));
+    CUP(cudaMalloc(&p->scratch, sizeof(Scalars)));
+    CUP(cudaMemsetAsync(p->scratch, 0, sizeof(Scalars), p->st));
+    CUP(cudaMallocHost(&p->host_pinned, sizeof(Scalars)));
+    CUP(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, p->u64, p->uob, p->st));
+
+    if (desc->coarse_n > 0) {
+        const int nc = desc->coarse_n;
+        p->nc = nc;
+        p->r = (n - 1) / (nc - 1);
+        p->hc = p->h * p->r;
+        p->beta_c = 1.0 / (1.0 + p->lambda * p->hc);
+        p->hl_c = p->hc * desc->cost;
+        p->uob_c = p->lambda > 0.0 ? p->hl_c / (1.0 - p->beta_c) : 1e6;
+        if (coarse_solve_smem(nc, na) > 227 * 1024) {
+            return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d too large for one block's shared memory", nc));
+        }
+        const size_t Nc = (size_t)nc * nc;
+        CUP(cudaMalloc(&p->speed_c, Nc * sizeof(float)));
+        CUP(cudaMalloc(&p->mask_c, Nc));
+        CUP(cudaMalloc(&p->uc, Nc * sizeof(float)));
+        if (drift) CUP(cudaMalloc(&p->drift_c, Nc * sizeof(float2)));
+        CUP(launch_coarse_data(n, nc, p->speed, p->drift, p->mask, p->speed_c, p->drift_c,
+                               p->mask_c, p->st));
+        CUP(cudaMalloc(&p->uhat, N * sizeof(float)));
+        CUP(cudaMalloc(&p->a, N));
+        CUP(cudaMalloc(&p->succ, N * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->jump_a, N * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->jump_b, N * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->label, N));
+        CUP(cudaMalloc(&p->key, N * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->order, N * sizeof(int32_t)));
+    }
+    const bool sig = p->sigma > 0.0;
+    p->wave_blocks32 = std::max(1, wave_blocks_per_sm(false, sig, na)) * p->num_sms;
+    p->wave_blocks64 = std::max(1, wave_blocks_per_sm(true, sig, na)) * p->num_sms;
+    CUP(cudaStreamSynchronize(p->st));
+#undef CUP
+    *out = p;
+    return HJB_OK;
+}
+
+int ensure_hist(hjb_problem* p, int cap) {
+    if (p->hist_cap >= cap) return HJB_OK;
+    dfree(p->inc_hist32);
+    dfree(p->inc_hist64);
+    CU(cudaMalloc(&p->inc_hist32, sizeof(unsigned int) * (size_t)cap));
+    CU(cudaMalloc(&p->inc_hist64, sizeof(unsigned long long) * (size_t)cap));
+    p->hist_cap = cap;
+    return HJB_OK;
+}
+
+// Plain Jacobi sweeps u <- T u (double buffered) until the sup-increment of a
+// sweep is <= tol; the increment of every sweep lands in inc_hist, checked on
+// the host every kCheck sweeps.  Returns the sweeps done in *sweeps and the
+// last increment in *last; the result is in buf[0].
+template <typename T>
+int jacobi_loop(hjb_problem* p, T* buf0, T* buf1, double tol, int max_sweeps, int* sweeps,
+                double* last, bool* converged);
+
+template <>
+int jacobi_loop<float>(hjb_problem* p, float* buf0, float* buf1, double tol, int max_sweeps,
+                       int* sweeps, double* last, bool* converged) {
+    constexpr int kCheck = 8;
+    int rc = ensure_hist(p, max_sweeps + kCheck);
+    if (rc) return rc;
+    CU(cudaMemsetAsync(p->inc_hist32, 0, sizeof(unsigned int) * (size_t)(max_sweeps + kCheck), p->st));
+    const GridView g = p->fine_view();
+    const bool sig = p->sigma > 0.0;
+    std::vector<unsigned int> h(kCheck);
+    float* cur = buf0;
+    float* nxt = buf1;
+    int s = 0;
+    *converged = false;
+    *last = -1.0;
+    while (s < max_sweeps) {
+        const int chunk = std::min(kCheck, max_sweeps - s);
+        for (int c = 0; c < chunk; ++c) {
+            CU(launch_sweep_f32(g, sig, p->desc.scheme, p->halo, cur, nxt, nullptr,
+                                p->inc_hist32 + s + c, p->st));
+            std::swap(cur, nxt);
+        }
+        CU(cudaMemcpyAsync(h.data(), p->inc_hist32 + s, sizeof(unsigned int) * chunk,
+                           cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+        s += chunk;
+        float v = 0.0f;
+        std::memcpy(&v, &h[chunk - 1], sizeof(float));
+        *last = v;
+        if (v <= tol) {
+            *converged = true;
+            break;
+        }
+    }
+    if (cur != buf0) CU(cudaMemcpyAsync(buf0, cur, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, p->st));
+    *sweeps = s;
+    return HJB_OK;
+}
+
+template <>
+int jacobi_loop<double>(hjb_problem* p, double* buf0, double* buf1, double tol, int max_sweeps,
+                        int* sweeps, double* last, bool* converged) {
+    constexpr int kCheck = 8;
+    int rc = ensure_hist(p, max_sweeps + kCheck);
+    if (rc) return rc;
+    CU(cudaMemsetAsync(p->inc_hist64, 0, sizeof(unsigned long long) * (size_t)(max_sweeps + kCheck), p->st));
+    const GridView g = p->fine_view();
+    const bool sig = p->sigma > 0.0;
+    std::vector<unsigned long long> h(kCheck);
+    double* cur = buf0;
+    double* nxt = buf1;
+    int s = 0;
+    *converged = false;
+    *last = -1.0;
+    while (s < max_sweeps) {
+        const int chunk = std::min(kCheck, max_sweeps - s);
+        for (int c = 0; c < chunk; ++c) {
+            CU(launch_sweep_f64(g, sig, p->desc.scheme, p->halo, cur, nxt, nullptr,
+                                p->inc_hist64 + s + c, p->st));
+            std::swap(cur, nxt);
+        }
+        CU(cudaMemcpyAsync(h.data(), p->inc_hist64 + s, sizeof(unsigned long long) * chunk,
+                           cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+        s += chunk;
+        double v = 0.0;
+        std::memcpy(&v, &h[chunk - 1], sizeof(double));
+        *last = v;
+        if (v <= tol) {
+            *converged = true;
+            break;
+        }
+    }
+    if (cur != buf0) CU(cudaMemcpyAsync(buf0, cur, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, p->st));
+    *sweeps = s;
+    return HJB_OK;
+}
+
+// FP64 sup-residual ||T2 u - u|| of u64.
+int residual64(hjb_problem* p, double* out) {
+    Scalars* ds = dscal(p);
+    CU(cudaMemsetAsync(&ds->inc64, 0, sizeof(unsigned long long), p->st));
+    CU(launch_sweep_f64(p->fine_view(), p->sigma > 0.0, 2, p->halo, p->u64, nullptr, nullptr,
+                        &ds->inc64, p->st));
+    unsigned long long bits = 0;
+    CU(cudaMemcpyAsync(&hscal(p)->inc64, &ds->inc64, sizeof(bits), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    bits = hscal(p)->inc64;
+    std::memcpy(out, &bits, sizeof(double));
+    return HJB_OK;
+}
+
+// Band-ordered passes on u32 (f64 = false) or u64 (f64 = true).
+int run_waves(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out) {
+    Scalars* ds = dscal(p);
+    CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
+    CU(cudaMemsetAsync(&ds->sync, 0, sizeof(GridSync), p->st));
+    WaveArgs a{};
+    a.g = p->fine_view();
+    a.scheme = p->desc.scheme;
+    a.order = p->order;
+    a.band_off = p->band_off;
+    a.n_bands = p->n_bands;
+    a.group = p->desc.band_group;
+    a.n_groups = (p->n_bands + a.group - 1) / a.group;
+    a.window = std::max(1, (p->desc.band_window + a.group - 1) / a.group);
+    a.tol = (float)tol;
+    a.max_passes = max_passes;
+    a.inc_bits = p->inc_bits;
+    a.sync = &ds->sync;
+    a.res = &ds->wave;
+    a.timeout_ns = kTimeoutNs;
+    const bool sig = p->sigma > 0.0;
+    int blocks = f64 ? p->wave_blocks64 : p->wave_blocks32;
+    if (p->desc.wave_warps > 0) {
+        const int want = (p->desc.wave_warps + wave_threads() / 32 - 1) / (wave_threads() / 32);
+        blocks = std::max(1, std::min(blocks, want));
+    }
+    if (f64) {
+        CU(launch_waves_f64(a, p->u64, sig, blocks, p->st));
+    } else {
+        CU(launch_waves_f32(a, p->u32, sig, blocks, p->st));
+    }
+    CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    *out = hscal(p)->wave;
+    if (hscal(p)->sync.err != 0)
+        return fail(hscal(p)->sync.err, "band-wave kernel: a grid-wide wait exceeded its limit");
+    return HJB_OK;
+}
+
+int rebuild_order(hjb_problem* p) {
+    // successors -> labels -> (band, patch) ordering, from p->a and p->key
+    const GridView g = p->fine_view();
+    CU(launch_successors(g, p->a, p->succ, p->st));
+    CU(launch_labels(p->N, p->succ, p->mask, p->sector, p->np, p->jump_a, p->jump_b, p->label, p->st));
+    const int bins = p->n_bands * (p->np + 1);
+    if (bins > p->bins_cap) {
+        dfree(p->bin_count);
+        dfree(p->bin_off);
+        CU(cudaMalloc(&p->bin_count, sizeof(int32_t) * (size_t)bins));
+        CU(cudaMalloc(&p->bin_off, sizeof(int32_t) * (size_t)(bins + 1)));
+        p->bins_cap = bins;
+    }
+    if (p->n_bands > p->bands_cap) {
+        dfree(p->band_off);
+        dfree(p->inc_bits);
+        CU(cudaMalloc(&p->band_off, sizeof(int32_t) * (size_t)(p->n_bands + 1)));
+        CU(cudaMalloc(&p->inc_bits, sizeof(unsigned int) * 2 * (size_t)p->n_bands));
+        p->bands_cap = p->n_bands;
+    }
+    CU(cudaMemsetAsync(p->inc_bits, 0, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
+    CU(launch_order(p->N, p->key, p->label, p->mask, p->np, p->n_bands, p->bin_count, p->bin_off,
+                    p->order, p->band_off, p->st));
+    return HJB_OK;
+}
+
+// Re-sort the free nodes by the current FP32 value (keys from u32, labels kept).
+int resort_by_value(hjb_problem* p) {
+    Scalars* ds = dscal(p);
+    CU(cudaMemsetAsync(&ds->max_key, 0, sizeof(int), p->st));
+    CU(launch_keys_from_values(p->N, p->mask, p->u32, (float)p->lambda,
+                               (float)(p->desc.band_width * p->h), kBandCap, p->key, &ds->max_key,
+                               p->st));
+    CU(cudaMemcpyAsync(&hscal(p)->max_key, &ds->max_key, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    p->n_bands = hscal(p)->max_key + 1;
+    const int bins = p->n_bands * (p->np + 1);
+    if (bins > p->bins_cap) {
+        dfree(p->bin_count);
+        dfree(p->bin_off);
+        CU(cudaMalloc(&p->bin_count, sizeof(int32_t) * (size_t)bins));
+        CU(cudaMalloc(&p->bin_off, sizeof(int32_t) * (size_t)(bins + 1)));
+        p->bins_cap = bins;
+    }
+    if (p->n_bands > p->bands_cap) {
+        dfree(p->band_off);
+        dfree(p->inc_bits);
+        CU(cudaMalloc(&p->band_off, sizeof(int32_t) * (size_t)(p->n_bands + 1)));
+        CU(cudaMalloc(&p->inc_bits, sizeof(unsigned int) * 2 * (size_t)p->n_bands));
+        p->bands_cap = p->n_bands;
+    }
+    CU(cudaMemsetAsync(p->inc_bits, 0, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
+    CU(launch_order(p->N, p->key, p->label, p->mask, p->np, p->n_bands, p->bin_count, p->bin_off,
+                    p->order, p->band_off, p->st));
+    return HJB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hjb_status_string(int code) {
+    switch (code) {
+        case HJB_OK: return "ok";
+        case HJB_ERR_INVALID_ARG: return "invalid argument";
+        case HJB_ERR_CUDA: return "CUDA error";
+        case HJB_ERR_OOM: return "out of device memory";
+        case HJB_ERR_STATE: return "call out of order";
+        case HJB_ERR_NOT_CONVERGED: return "not converged (iteration cap reached)";
+        case HJB_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* hjb_last_error(void) { return g_last_error.c_str(); }
+
+int hjb_regime(double dx, double f_min, double f_max, double eps, hjb_regime_info* out) {
+    if (!out || !(dx > 0.0) || !(f_min > 0.0) || !(f_max >= f_min) || !(eps >= 0.0))
+        return fail(HJB_ERR_INVALID_ARG, "hjb_regime: need dx>0, 0<f_min<=f_max, eps>=0");
+    hjb_regime_info r{};
+    r.upsilon = f_max / f_min;
+    r.tau_dx = dx / (1.0 + r.upsilon);
+    r.alpha = 1.0 / (1.0 + r.upsilon);
+    r.eps_threshold = f_min * dx / (2.0 * (1.0 + r.upsilon));
+    if (eps > 0.0) {
+        r.omega = f_min / (2.0 * eps);
+        const double q = r.omega * dx;
+        r.alpha_lower = 1.0 / q;
+        r.alpha_upper = 1.0 / r.upsilon - (std::sqrt(1.0 + 4.0 * q * r.upsilon) - 1.0) /
+                                              (2.0 * q * r.upsilon * r.upsilon);
+        r.holds = (1.0 / r.omega < r.tau_dx) ? 1 : 0;
+    } else {
+        r.omega = INFINITY;
+        r.alpha_lower = 0.0;
+        r.alpha_upper = 1.0 / r.upsilon;
+        r.holds = 1;
+    }
+    r.h = r.alpha * dx / f_min;
+    const double diff = std::sqrt(2.0 * eps * r.h);
+    r.upper_ok = (r.h * f_max + diff < dx) ? 1 : 0;
+    r.lower_ok = (r.h * f_min - diff > 0.0) ? 1 : 0;
+    r.reach_cells = (int)std::ceil((r.h * f_max + diff) / dx);
+    *out = r;
+    return HJB_OK;
+}
+
+int hjb_create_problem(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                       const int8_t* sector, const double* controls, const float* drift,
+                       void* cuda_stream, hjb_problem** out) {
+    return create_common(desc, speed, mask, sector, controls, drift, cuda_stream, out, false);
+}
+
+int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                              const int8_t* sector, const double* controls, const float* drift,
+                              void* cuda_stream, hjb_problem** out) {
+    return create_common(desc, speed, mask, sector, controls, drift, cuda_stream, out, true);
+}
+
+void hjb_destroy(hjb_problem* p) {
+    if (!p) return;
+    if (p->st) cudaStreamSynchronize(p->st);
+    dfree(p->speed); dfree(p->drift); dfree(p->mask); dfree(p->sector);
+    dfree(p->ctrl32); dfree(p->ctrl64);
+    dfree(p->u32); dfree(p->u32b); dfree(p->u64); dfree(p->u64b);
+    dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc);
+    dfree(p->uhat); dfree(p->a); dfree(p->succ); dfree(p->jump_a); dfree(p->jump_b);
+    dfree(p->label); dfree(p->key); dfree(p->order); dfree(p->bin_count); dfree(p->bin_off);
+    dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
+    if (p->scratch) cudaFree(p->scratch);
+    if (p->host_pinned) cudaFreeHost(p->host_pinned);
+    if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+    delete p;
+}
+
+int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats* stats) {
+    g_last_error.clear();
+    clear_stats(stats);
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "problem is NULL");
+    if (p->nc == 0) return fail(HJB_ERR_STATE, "problem has no coarse grid");
+    if (!(tol_c > 0.0) || max_sweeps < 1) return fail(HJB_ERR_INVALID_ARG, "bad tol_c / max_sweeps");
+    Timer tm(p->st);
+    tm.mark();
+    Scalars* ds = dscal(p);
+    CU(launch_coarse_solve(p->coarse_view(), (float)p->uob_c, (float)tol_c, max_sweeps, p->uc,
+                           &ds->coarse, p->st));
+    tm.mark();
+    CU(cudaMemcpyAsync(&hscal(p)->coarse, &ds->coarse, sizeof(CoarseResult), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    const CoarseResult cr = hscal(p)->coarse;
+    p->coarse_done = true;
+    p->built = false;
+    int rc = cr.sweeps > 0 ? HJB_OK : HJB_ERR_NOT_CONVERGED;
+    if (stats) {
+        stats->sweeps = cr.sweeps > 0 ? cr.sweeps : -cr.sweeps;
+        stats->increment = cr.increment;
+        stats->ms_total = tm.ms(0, 1);
+        stats->ms_stage[0] = stats->ms_total;
+        stats->node_updates = (long long)stats->sweeps * (long long)p->nc * p->nc;
+        stats->node_control_updates = stats->node_updates * p->na;
+        stats->status = rc;
+    }
+    if (rc) fail(rc, "coarse solve did not reach tol_c in %d sweeps", max_sweeps);
+    return rc;
+}
+
+int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
+    g_last_error.clear();
+    clear_stats(stats);
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->coarse_done) return fail(HJB_ERR_STATE, "hjb_coarse_solve has not run");
+    Timer tm(p->st);
+    Scalars* ds = dscal(p);
+    const GridView g = p->fine_view();
+    tm.mark();
+    CU(launch_interp(p->nc, p->uc, p->n, p->mask, (float)p->uob, p->uhat, p->st));
+    tm.mark();
+    CU(cudaMemsetAsync(&ds->max_key, 0, sizeof(int), p->st));
+    const double band_w = p->desc.band_width * p->h;
+    CU(launch_synthesis(g, p->uhat, (float)p->lambda, (float)band_w, kBandCap, p->a, p->key,
+                        &ds->max_key, p->st));
+    CU(cudaMemcpyAsync(&hscal(p)->max_key, &ds->max_key, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    tm.mark();
+    p->n_bands = hscal(p)->max_key + 1;
+    int rc = rebuild_order(p);
+    if (rc) return rc;
+    tm.mark();
+    // the fine iteration starts from u_hat
+    CU(cudaMemcpyAsync(p->u32, p->uhat, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, p->st));
+    CU(launch_fix_nonfree(p->N, p->mask, (float)p->uob, p->uob, p->u32, nullptr, p->st));
+    p->value_f64 = false;
+    int32_t nfree = 0;
+    CU(cudaMemcpyAsync(&nfree, p->band_off + p->n_bands, sizeof(int32_t), cudaMemcpyDeviceToHost, p->st));
+    tm.mark();
+    CU(cudaStreamSynchronize(p->st));
+    p->n_free = nfree;
+    p->built = true;
+    if (stats) {
+        stats->ms_stage[0] = tm.ms(0, 1);
+        stats->ms_stage[1] = tm.ms(1, 2);
+        stats->ms_stage[3] = tm.ms(2, 3);
+        stats->ms_total = tm.ms(0, 4);
+        stats->sweeps = p->n_bands;
+        stats->status = HJB_OK;
+    }
+    return HJB_OK;
+}
+
+int hjb_set_feedback(hjb_problem* p, const uint8_t* a) {
+    g_last_error.clear();
+    if (!p || !a) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    std::vector<uint8_t> m(p->N);
+    CU(cudaMemcpy(m.data(), p->mask, p->N, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> clean(a, a + p->N);
+    for (int k = 0; k < p->N; ++k) {
+        if (m[k] == HJB_MASK_FREE) {
+            if (clean[k] >= p->na) return fail(HJB_ERR_INVALID_ARG, "a[%d]=%d >= n_controls", k, clean[k]);
+        } else {
+            clean[k] = 255;
+        }
+    }
+    CU(cudaMemcpyAsync(p->a, clean.data(), p->N, cudaMemcpyHostToDevice, p->st));
+    int rc = rebuild_order(p);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(p->st));
+    return HJB_OK;
+}
+
+int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_passes,
+                      hjb_stats* stats) {
+    g_last_error.clear();
+    clear_stats(stats);
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    if (!(tol32 > 0.0) || max_passes < 1 || !(tol64 >= 0.0))
+        return fail(HJB_ERR_INVALID_ARG, "bad tolerances / max_passes");
+    Timer tm(p->st);
+    tm.mark();
+    WaveResult w32{}, w64{};
+    int rc = HJB_OK;
+    if (p->value_f64) {
+        CU(launch_demote(p->N, p->u64, p->u32, p->st));
+        p->value_f64 = false;
+    }
+    {
+        // optional single passes followed by a re-sort by the current value
+        int done = 0;
+        unsigned long long nodes = 0;
+        WaveResult w{};
+        w.converged = 0;
+        for (int r = 0; r < p->desc.resort_passes && done < max_passes && !w.converged; ++r) {
+            rc = run_waves(p, false, tol32, 1, &w);
+            if (rc) return rc;
+            done += w.passes;
+            nodes += w.nodes;
+            if (!w.converged) {
+                rc = resort_by_value(p);
+                if (rc) return rc;
+            }
+        }
+        if (!w.converged && done < max_passes) {
+            rc = run_waves(p, false, tol32, max_passes - done, &w);
+            if (rc) return rc;
+            done += w.passes;
+            nodes += w.nodes;
+        }
+        w32 = w;
+        w32.passes = done;
+        w32.nodes = nodes;
+    }
+    tm.mark();
+    if (!w32.converged) rc = HJB_ERR_NOT_CONVERGED;
+    double res = -1.0;
+    double ms_promote = 0.0, ms64 = 0.0;
+    unsigned long long nodes64 = 0;
+    int passes64 = 0;
+    double last = w32.last_increment;
+    if (tol64 > 0.0 && rc == HJB_OK) {
+        Timer t2(p->st);
+        t2.mark();
+        CU(launch_promote(p->N, p->u32, p->u64, p->st));
+        p->value_f64 = true;
+        int r2 = residual64(p, &res);
+        if (r2) return r2;
+        t2.mark();
+        ms_promote += t2.ms(0, 1);
+        double tol_pass = tol64;
+        while (res > tol64 && passes64 < max_passes) {
+            Timer t3(p->st);
+            t3.mark();
+            r2 = run_waves(p, true, tol_pass, max_passes - passes64, &w64);
+            if (r2) return r2;
+            t3.mark();
+            passes64 += w64.passes;
+            nodes64 += w64.nodes;
+            last = w64.last_increment;
+            r2 = residual64(p, &res);
+            if (r2) return r2;
+            t3.mark();
+            ms64 += t3.ms(0, 1);
+            ms_promote += t3.ms(1, 2);
+            tol_pass *= 0.25;
+        }
+        if (res > tol64) rc = HJB_ERR_NOT_CONVERGED;
+    }
+    if (stats) {
+        stats->fp32_passes = w32.passes;
+        stats->fp64_passes = passes64;
+        stats->sweeps = w32.passes + passes64;
+        stats->node_updates = (long long)(w32.nodes + nodes64);
+        stats->node_control_updates = stats->node_updates * p->na;
+        stats->residual = res;
+        stats->increment = last;
+        stats->ms_stage[0] = tm.ms(0, 1);
+        stats->ms_stage[1] = ms_promote;
+        stats->ms_stage[2] = ms64;
+        stats->ms_total = stats->ms_stage[0] + ms_promote + ms64;
+        stats->status = rc;
+    }
+    if (rc) fail(rc, "patch solve did not converge (FP32 passes %d, FP64 passes %d, residual %.3e)",
+                 w32.passes, passes64, res);
+    return rc;
+}
+
+int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64, int32_t max_sweeps,
+                   hjb_stats* stats) {
+    g_last_error.clear();
+    clear_stats(stats);
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "problem is NULL");
+    if ((precision != 32 && precision != 64) || !(tol > 0.0) || max_sweeps < 1 || !(tol64 >= 0.0))
+        return fail(HJB_ERR_INVALID_ARG, "bad precision / tolerance / max_sweeps");
+    Timer tm(p->st);
+    int rc = HJB_OK;
+    int s32 = 0, s64 = 0;
+    double last = -1.0, res = -1.0;
+    bool conv = false;
+    tm.mark();
+    if (precision == 32) {
+        CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, nullptr, p->uob, p->st));
+        CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32b, nullptr, p->uob, p->st));
+        rc = jacobi_loop<float>(p, p->u32, p->u32b, tol, max_sweeps, &s32, &last, &conv);
+        if (rc) return rc;
+        p->value_f64 = false;
+        if (!conv) rc = HJB_ERR_NOT_CONVERGED;
+    }
+    tm.mark();
+    if (precision == 64 || (tol64 > 0.0 && rc == HJB_OK)) {
+        if (precision == 64) {
+            CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, nullptr, p->u64, p->uob, p->st));
+        } else {
+            CU(launch_promote(p->N, p->u32, p->u64, p->st));
+        }
+        CU(cudaMemcpyAsync(p->u64b, p->u64, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, p->st));
+        const double t = precision == 64 ? tol : tol64;
+        int r2 = jacobi_loop<double>(p, p->u64, p->u64b, t, max_sweeps, &s64, &last, &conv);
+        if (r2) return r2;
+        p->value_f64 = true;
+        rc = conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
+        r2 = residual64(p, &res);
+        if (r2) return r2;
+    }
+    tm.mark();
+    CU(cudaStreamSynchronize(p->st));
+    if (stats) {
+        stats->fp32_passes = s32;
+        stats->fp64_passes = s64;
+        stats->sweeps = s32 + s64;
+        stats->node_updates = (long long)(s32 + s64) * p->n_free_total;
+        stats->node_control_updates = stats->node_updates * p->na;
+        stats->residual = res;
+        stats->increment = last;
+        stats->ms_stage[0] = tm.ms(0, 1);
+        stats->ms_stage[1] = tm.ms(1, 2);
+        stats->ms_total = tm.ms(0, 2);
+        stats->status = rc;
+    }
+    if (rc) fail(rc, "full-grid iteration did not converge in %d sweeps", max_sweeps);
+    return rc;
+}
+
+int hjb_apply_operator(hjb_problem* p, int32_t precision, int32_t scheme, const double* u,
+                       double* out, int32_t* argmin) {
+    g_last_error.clear();
+    if (!p || !u || !out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if ((precision != 32 && precision != 64) || (scheme != 2 && scheme != 3))
+        return fail(HJB_ERR_INVALID_ARG, "precision must be 32/64 and scheme 2/3");
+    const size_t N = p->N;
+    DevBuf d_arg, din, dout;
+    if (argmin) CU(d_arg.alloc(N * sizeof(int32_t)));
+    Scalars* ds = dscal(p);
+    const GridView g = p->fine_view();
+    const bool sig = p->sigma > 0.0;
+    if (precision == 64) {
+        CU(din.alloc(N * sizeof(double)));
+        CU(dout.alloc(N * sizeof(double)));
+        CU(cudaMemcpyAsync(din.ptr, u, N * sizeof(double), cudaMemcpyHostToDevice, p->st));
+        CU(launch_sweep_f64(g, sig, scheme, p->halo, (const double*)din.ptr, (double*)dout.ptr,
+                            (int32_t*)d_arg.ptr, &ds->inc64, p->st));
+        CU(cudaMemcpyAsync(out, dout.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+    } else {
+        std::vector<float> h32(N);
+        for (size_t k = 0; k < N; ++k) h32[k] = (float)u[k];
+        CU(din.alloc(N * sizeof(float)));
+        CU(dout.alloc(N * sizeof(float)));
+        CU(cudaMemcpyAsync(din.ptr, h32.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->st));
+        CU(launch_sweep_f32(g, sig, scheme, p->halo, (const float*)din.ptr, (float*)dout.ptr,
+                            (int32_t*)d_arg.ptr, &ds->inc32, p->st));
+        CU(cudaMemcpyAsync(h32.data(), dout.ptr, N * sizeof(float), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+        for (size_t k = 0; k < N; ++k) out[k] = (double)h32[k];
+    }
+    if (argmin) {
+        CU(cudaMemcpyAsync(argmin, d_arg.ptr, N * sizeof(int32_t), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+    }
+    return HJB_OK;
+}
+
+int hjb_residual(hjb_problem* p, double* residual) {
+    g_last_error.clear();
+    if (!p || !residual) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->value_f64) {
+        CU(launch_promote(p->N, p->u32, p->u64, p->st));
+    }
+    return residual64(p, residual);
+}
+
+int hjb_set_value(hjb_problem* p, const double* u) {
+    g_last_error.clear();
+    if (!p || !u) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < p->N; ++k)
+        if (!std::isfinite(u[k])) return fail(HJB_ERR_INVALID_ARG, "u[%d] not finite", k);
+    std::vector<float> h32(p->N);
+    for (int k = 0; k < p->N; ++k) h32[k] = (float)u[k];
+    CU(cudaMemcpyAsync(p->u64, u, sizeof(double) * p->N, cudaMemcpyHostToDevice, p->st));
+    CU(cudaMemcpyAsync(p->u32, h32.data(), sizeof(float) * p->N, cudaMemcpyHostToDevice, p->st));
+    CU(launch_fix_nonfree(p->N, p->mask, (float)p->uob, p->uob, p->u32, p->u64, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    p->value_f64 = false;
+    return HJB_OK;
+}
+
+int hjb_get_value(hjb_problem* p, double* u_out) {
+    g_last_error.clear();
+    if (!p || !u_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (p->value_f64) {
+        CU(cudaMemcpyAsync(u_out, p->u64, sizeof(double) * p->N, cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+    } else {
+        std::vector<float> h(p->N);
+        CU(cudaMemcpyAsync(h.data(), p->u32, sizeof(float) * p->N, cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+        for (int k = 0; k < p->N; ++k) u_out[k] = (double)h[k];
+    }
+    return HJB_OK;
+}
+
+int hjb_get_coarse_value(hjb_problem* p, double* uc_out) {
+    g_last_error.clear();
+    if (!p || !uc_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->coarse_done) return fail(HJB_ERR_STATE, "hjb_coarse_solve has not run");
+    std::vector<float> h((size_t)p->nc * p->nc);
+    CU(cudaMemcpyAsync(h.data(), p->uc, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    for (size_t k = 0; k < h.size(); ++k) uc_out[k] = (double)h[k];
+    return HJB_OK;
+}
+
+int hjb_get_uhat(hjb_problem* p, double* uhat_out) {
+    g_last_error.clear();
+    if (!p || !uhat_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    std::vector<float> h(p->N);
+    CU(cudaMemcpyAsync(h.data(), p->uhat, sizeof(float) * p->N, cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    for (int k = 0; k < p->N; ++k) uhat_out[k] = (double)h[k];
+    return HJB_OK;
+}
+
+int hjb_get_feedback(hjb_problem* p, uint8_t* a_out) {
+    g_last_error.clear();
+    if (!p || !a_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    CU(cudaMemcpyAsync(a_out, p->a, p->N, cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    return HJB_OK;
+}
+
+int hjb_get_successors(hjb_problem* p, int32_t* succ_out) {
+    g_last_error.clear();
+    if (!p || !succ_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    CU(cudaMemcpyAsync(succ_out, p->succ, sizeof(int32_t) * p->N, cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    return HJB_OK;
+}
+
+int hjb_get_labels(hjb_problem* p, int8_t* label_out) {
+    g_last_error.clear();
+    if (!p || !label_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    CU(cudaMemcpyAsync(label_out, p->label, p->N, cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    return HJB_OK;
+}
+
+int hjb_get_order(hjb_problem* p, int32_t* keys_out, int32_t* order_out, int32_t* band_off_out,
+                  int32_t* n_free, int32_t* n_bands) {
+    g_last_error.clear();
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    if (keys_out) CU(cudaMemcpyAsync(keys_out, p->key, sizeof(int32_t) * p->N, cudaMemcpyDeviceToHost, p->st));
+    if (order_out) CU(cudaMemcpyAsync(order_out, p->order, sizeof(int32_t) * p->n_free, cudaMemcpyDeviceToHost, p->st));
+    if (band_off_out)
+        CU(cudaMemcpyAsync(band_off_out, p->band_off, sizeof(int32_t) * (p->n_bands + 1), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    if (n_free) *n_free = p->n_free;
+    if (n_bands) *n_bands = p->n_bands;
+    return HJB_OK;
+}
+
+int hjb_device_info(hjb_problem* p, int32_t* num_sms, int32_t* wave_blocks32, int32_t* wave_blocks64) {
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (num_sms) *num_sms = p->num_sms;
+    if (wave_blocks32) *wave_blocks32 = p->wave_blocks32;
+    if (wave_blocks64) *wave_blocks64 = p->wave_blocks64;
+    return HJB_OK;
+}
+
+}  // extern "C"

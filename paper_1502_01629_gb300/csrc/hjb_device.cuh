@@ -1,0 +1,291 @@
+// Device-side building blocks of the solver: the per-control evaluation of the
+// Markov-chain semi-Lagrangian scheme (Cacace & Falcone, Section 3, eqs.
+// SLscheme2 / SLscheme3 and the 2-D isotropic form of Section 4.1), the
+// warp-level argmin over controls, block reductions and the bounded grid-wide
+// barrier used by the persistent band-wave kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hjb.h"
+
+namespace hjb {
+
+constexpr int kFree = HJB_MASK_FREE;
+constexpr int kTarget = HJB_MASK_TARGET;
+constexpr int kObstacle = HJB_MASK_OBSTACLE;
+
+// Everything a kernel needs to evaluate the scheme on one grid, by value.
+struct GridView {
+    int n;                  // nodes per side
+    int na;                 // number of controls
+    const float* speed;     // c(x), n*n
+    const float2* drift;    // b(x), n*n, or nullptr
+    const uint8_t* mask;    // n*n
+    const float2* ctrl32;   // a_m in FP32
+    const double2* ctrl64;  // a_m in FP64
+    float s32;   double s64;     // h / dx
+    float d32;   double d64;     // sqrt(2h) sigma / dx: diffusion offset in cells
+    float beta32; double beta64; // 1 / (1 + lambda h)
+    float hl32;  double hl64;    // h * l
+    float uob32; double uob64;   // value held on obstacle nodes
+};
+
+template <typename T> struct RealOf;
+template <> struct RealOf<float> {
+    using V2 = float2;
+    __device__ static float s(const GridView& g) { return g.s32; }
+    __device__ static float d(const GridView& g) { return g.d32; }
+    __device__ static float beta(const GridView& g) { return g.beta32; }
+    __device__ static float hl(const GridView& g) { return g.hl32; }
+    __device__ static float uob(const GridView& g) { return g.uob32; }
+    __device__ static float2 ctrl(const GridView& g, int m) { return g.ctrl32[m]; }
+};
+template <> struct RealOf<double> {
+    using V2 = double2;
+    __device__ static double s(const GridView& g) { return g.s64; }
+    __device__ static double d(const GridView& g) { return g.d64; }
+    __device__ static double beta(const GridView& g) { return g.beta64; }
+    __device__ static double hl(const GridView& g) { return g.hl64; }
+    __device__ static double uob(const GridView& g) { return g.uob64; }
+    __device__ static double2 ctrl(const GridView& g, int m) { return g.ctrl64[m]; }
+};
+
+// One axis of a point's Q1 cell, relative to the node: the point sits at offset
+// `d` (grid units) from node index i.  The projection onto the square clamps the
+// absolute coordinate to [0, n-1]; the cell is floor(), capped at n-2 so that a
+// point on the last grid line uses the last cell with fraction 1.  Working with
+// the small offset keeps the fraction exact in FP32 at any grid size.
+// `sw` is the Q1 weight of node i along this axis (0 if i is not a vertex).
+template <typename T>
+struct Axis {
+    int off;
+    T fr;
+    T sw;
+};
+
+template <typename T>
+__device__ __forceinline__ Axis<T> axis_cell(T d, int i, int n) {
+    const T lo = (T)(-i);
+    const T hi = (T)(n - 1 - i);
+    d = fmin(fmax(d, lo), hi);
+    T fl = floor(d);
+    int off = (int)fl;
+    const int cap = n - 2 - i;
+    if (off > cap) {
+        off = cap;
+        fl = (T)cap;
+    }
+    Axis<T> a;
+    a.off = off;
+    a.fr = d - fl;
+    a.sw = (off == 0) ? (T(1) - a.fr) : ((off == -1) ? a.fr : T(0));
+    return a;
+}
+
+// Q1 value at the point whose axis cells are ax, ay, relative to the node's
+// value uk: sum_v lambda_v (u_v - uk).  The weights sum to one, so this is the
+// interpolated value minus uk; forming it from differences keeps the rounding
+// proportional to the (small) differences, and the node itself, if it is a
+// vertex, contributes exactly zero.  U(dx, dy) returns u at node (i+dx, j+dy).
+template <typename T, typename Acc>
+__device__ __forceinline__ T bilinear_rel(const Axis<T>& ax, const Axis<T>& ay, T uk, const Acc& U) {
+    const T v00 = U(ax.off, ay.off);
+    const T v10 = U(ax.off + 1, ay.off);
+    const T v01 = U(ax.off, ay.off + 1);
+    const T v11 = U(ax.off + 1, ay.off + 1);
+    const T a = fma(ax.fr, v10 - v00, v00 - uk);
+    const T b = fma(ax.fr, v11 - v01, v01 - uk);
+    return fma(ay.fr, b - a, a);
+}
+
+// For one control: Sd = (1/2d) sum_{k,s} (I[u](x_{i,k}^{a,s}) - u_i) and
+// L = (1/2d) sum_{k,s} lambda_{i0,k}^{a,s} (the self weight, Lambda0 of eq.
+// SLimplicit).  SIG = false: sigma = 0, the four points coincide with the foot.
+template <typename T, bool SIG, typename Acc>
+__device__ __forceinline__ void control_terms(const GridView& g, int i, int j, T fx, T fy, T uk,
+                                              const Acc& U, T& Sd, T& L) {
+    const int n = g.n;
+    if (SIG) {
+        const T d = RealOf<T>::d(g);
+        const Axis<T> xm = axis_cell<T>(fx - d, i, n);
+        const Axis<T> x0 = axis_cell<T>(fx, i, n);
+        const Axis<T> xp = axis_cell<T>(fx + d, i, n);
+        const Axis<T> ym = axis_cell<T>(fy - d, j, n);
+        const Axis<T> y0 = axis_cell<T>(fy, j, n);
+        const Axis<T> yp = axis_cell<T>(fy + d, j, n);
+        Sd = (bilinear_rel<T>(xp, y0, uk, U) + bilinear_rel<T>(xm, y0, uk, U)) +
+             (bilinear_rel<T>(x0, yp, uk, U) + bilinear_rel<T>(x0, ym, uk, U));
+        L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
+        Sd *= T(0.25);
+        L *= T(0.25);
+    } else {
+        const Axis<T> x0 = axis_cell<T>(fx, i, n);
+        const Axis<T> y0 = axis_cell<T>(fy, j, n);
+        Sd = bilinear_rel<T>(x0, y0, uk, U);
+        L = x0.sw * y0.sw;
+    }
+}
+
+// Candidates of the min, written as increments over the node's value uk.
+// With Sd and L as above and c0 = h l - (1 - beta) uk,
+//   scheme 3 (eq. SLscheme3 with the discount):
+//       (beta (S - L uk) + h l) / (1 - beta L) - uk = (beta Sd + c0) / (1 - beta L),
+//   scheme 2 (eq. SLscheme2):
+//       beta S + h l - uk = beta Sd + c0,
+// so each candidate is a fraction N/D (D > 0) and candidates are compared by
+// cross-multiplication; the new value is uk + N*/D*.
+template <typename T>
+__device__ __forceinline__ bool better(T na, T da, int ma, T nb, T db, int mb) {
+    const T l = na * db, r = nb * da;
+    return (l < r) || (l == r && ma < mb);
+}
+
+// Evaluate every control handled by this thread (m = m0, m0+stride, ...) for
+// node (i, j) with value uk, speed c, drift (bx, by); returns the best
+// increment as a fraction N/D and its control index (ties: lowest index).
+template <typename T, bool SIG, typename CtrlFn, typename Acc>
+__device__ __forceinline__ void best_over_controls(const GridView& g, int scheme, int i, int j,
+                                                   T uk, T c, T bx, T by, int m0, int stride,
+                                                   const CtrlFn& ctrl, const Acc& U,
+                                                   T& bestN, T& bestD, int& bestM) {
+    const T s = RealOf<T>::s(g);
+    const T beta = RealOf<T>::beta(g);
+    const T c0 = fma(-(T(1) - beta), uk, RealOf<T>::hl(g));
+    bestN = T(INFINITY);
+    bestD = T(1);
+    bestM = 0x7fffffff;
+    for (int m = m0; m < g.na; m += stride) {
+        const auto a = ctrl(m);
+        const T fx = s * fma(c, (T)a.x, bx);
+        const T fy = s * fma(c, (T)a.y, by);
+        T Sd, L;
+        control_terms<T, SIG>(g, i, j, fx, fy, uk, U, Sd, L);
+        T N = fma(beta, Sd, c0);
+        T D = T(1);
+        if (scheme == 3) {
+            D = fma(-beta, L, T(1));
+            if (!(D > T(0))) {
+                N = T(INFINITY);
+                D = T(1);
+            }
+        }
+        if (N * bestD < bestN * D) {
+            bestN = N;
+            bestD = D;
+            bestM = m;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_argmin(T& N, T& D, int& M) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const T oN = __shfl_xor_sync(0xffffffffu, N, off);
+        const T oD = __shfl_xor_sync(0xffffffffu, D, off);
+        const int oM = __shfl_xor_sync(0xffffffffu, M, off);
+        if (better<T>(oN, oD, oM, N, D, M)) {
+            N = oN;
+            D = oD;
+            M = oM;
+        }
+    }
+}
+
+// ------------------------------------------------------------- reductions
+
+// Non-negative floats compare like their bit patterns as unsigned integers.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned int* addr, float v) {
+    if (v > 0.0f) atomicMax(addr, __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+    if (v > 0.0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// Block-wide max of a non-negative value; valid in thread 0.  blockDim.x*y <= 1024.
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* scratch32) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    v = warp_max(v);
+    __syncthreads();
+    if ((tid & 31) == 0) scratch32[tid >> 5] = v;
+    __syncthreads();
+    T r = T(0);
+    if (tid < 32) {
+        r = (tid < (nt + 31) / 32) ? scratch32[tid] : T(0);
+        r = warp_max(r);
+    }
+    return r;
+}
+
+// ------------------------------------------------------------ grid barrier
+
+// State of the grid-wide barrier of a cooperative (co-resident) launch.
+struct GridSync {
+    unsigned int count;
+    unsigned int gen;
+    int err;          // 0, or a negative HJB_ERR_* code set by any block
+    int pad;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Sense-free generation barrier.  Every wait is bounded by `timeout_ns` of
+// global time; on expiry the block records HJB_ERR_TIMEOUT and every block
+// leaves at its next barrier.  Returns false when the grid must stop.
+// Requires all blocks to be co-resident (cudaLaunchCooperativeKernel).
+__device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int nblocks,
+                                          unsigned long long timeout_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned int g = ld_acquire_u32(&gs->gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&gs->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(&gs->gen) == g) {
+                if (ld_relaxed_s32(&gs->err) != 0) break;
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicCAS(&gs->err, 0, HJB_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ld_relaxed_s32(&gs->err) == 0;
+}
+
+}  // namespace hjb

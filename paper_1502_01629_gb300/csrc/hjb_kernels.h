@@ -1,0 +1,97 @@
+// Host-side launch wrappers of the solver's kernels (one translation unit per
+// group), called by the C ABI in api.cu.  All launches go to the given stream
+// and return the cudaError_t of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hjb_device.cuh"
+
+namespace hjb {
+
+// ---------------------------------------------------------------- sweep.cu
+// Halo (cells) a tile needs so that every Q1 vertex of every point lies inside.
+int sweep_halo(double reach_cells);
+
+// One full-grid application of the scheme: uout = T uin on free nodes (uin
+// copied elsewhere); argmin (nullable) gets the minimising control; the block
+// maxima of |T uin - uin| over free nodes are folded into *incmax (bit pattern
+// of a non-negative float / double).  uout may be nullptr (residual only).
+cudaError_t launch_sweep_f32(const GridView& g, bool sig, int scheme, int halo, const float* uin,
+                             float* uout, int32_t* argmin, unsigned int* incmax, cudaStream_t st);
+cudaError_t launch_sweep_f64(const GridView& g, bool sig, int scheme, int halo, const double* uin,
+                             double* uout, int32_t* argmin, unsigned long long* incmax,
+                             cudaStream_t st);
+
+// ------------------------------------------------------------ precompute.cu
+struct CoarseResult {
+    int sweeps;
+    float increment;
+};
+
+cudaError_t launch_coarse_data(int n, int nc, const float* speed, const float2* drift,
+                               const uint8_t* mask, float* speed_c, float2* drift_c,
+                               uint8_t* mask_c, cudaStream_t st);
+// Whole coarse grid in one block's shared memory; returns an error when nc is
+// too large for shared memory.
+cudaError_t launch_coarse_solve(const GridView& gc, float u_start, float tol, int max_sweeps,
+                                float* uc, CoarseResult* res, cudaStream_t st);
+size_t coarse_solve_smem(int nc, int na);
+cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, float u_obst,
+                          float* uhat, cudaStream_t st);
+cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda, float band_w,
+                             int band_cap, uint8_t* a, int32_t* key, int* max_key, cudaStream_t st);
+// Band key from the current value (re-sorting), same mapping as the synthesis.
+cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, float lambda,
+                                    float band_w, int band_cap, int32_t* key, int* max_key,
+                                    cudaStream_t st);
+cudaError_t launch_successors(const GridView& g, const uint8_t* a, int32_t* succ, cudaStream_t st);
+cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const int8_t* sector,
+                          int n_patches, int32_t* jump_a, int32_t* jump_b, int8_t* label,
+                          cudaStream_t st);
+cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const uint8_t* mask,
+                         int n_patches, int n_bands, int32_t* bin_count, int32_t* bin_off,
+                         int32_t* order, int32_t* band_off, cudaStream_t st);
+cudaError_t launch_promote(int N, const float* u32, double* u64, cudaStream_t st);
+cudaError_t launch_demote(int N, const double* u64, float* u32, cudaStream_t st);
+cudaError_t launch_init_values(int N, const uint8_t* mask, float free_val, float uob,
+                               float* u32, double* u64, double uob64, cudaStream_t st);
+cudaError_t launch_fix_nonfree(int N, const uint8_t* mask, float uob, double uob64, float* u32,
+                               double* u64, cudaStream_t st);
+
+// ---------------------------------------------------------------- waves.cu
+struct WaveResult {
+    int passes;          // passes completed
+    int converged;       // 1 if a pass met the tolerance
+    unsigned long long nodes;   // free-node updates performed
+    float last_increment;       // sup-increment of the last pass
+    int pad;
+};
+
+struct WaveArgs {
+    GridView g;
+    int scheme;
+    const int32_t* order;     // free nodes grouped by band
+    const int32_t* band_off;  // n_bands + 1
+    int n_bands;
+    int group;                // bands per wave
+    int n_groups;             // ceil(n_bands / group)
+    int window;               // activity window, in groups
+    float tol;                // sup-increment tolerance of a pass
+    int max_passes;
+    unsigned int* inc_bits;   // 2 * n_groups, per-group max increment (float bits)
+    GridSync* sync;
+    WaveResult* res;
+    unsigned long long timeout_ns;
+};
+
+// Persistent cooperative kernel: max_passes passes of band-ordered waves over
+// u (FP32 or FP64) in place.  blocks = co-resident block count.
+cudaError_t launch_waves_f32(const WaveArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
+cudaError_t launch_waves_f64(const WaveArgs& a, double* u, bool sig, int blocks, cudaStream_t st);
+int wave_blocks_per_sm(bool f64, bool sig, int na);
+int wave_threads();
+size_t wave_smem(bool f64, int na);
+
+}  // namespace hjb

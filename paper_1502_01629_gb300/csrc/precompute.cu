@@ -1,0 +1,481 @@
+// Pre-computation of the patchy decomposition (Cacace & Falcone, Section 4.3):
+// coarse grid data and coarse solve (sigma = 0), Q1 interpolation u_hat,
+// feedback synthesis (eq. discrete-synthesis) with the causal band keys
+// (Section 4.2), winner-take-all transport successors (eq. discrete-advection),
+// labels by pointer jumping and the (band, patch) ordering of the free nodes.
+#include <cmath>
+
+#include "hjb_kernels.h"
+
+namespace hjb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- coarse grid
+// Coarse node (I,J) is fine node (rI, rJ).  It is a target when some fine target
+// node lies within r/2 fine cells in both axes, else an obstacle if its fine
+// node is one.  Speed and drift are the fine ones there.
+__global__ void k_coarse_data(int n, int nc, const float* __restrict__ speed,
+                              const float2* __restrict__ drift, const uint8_t* __restrict__ mask,
+                              float* speed_c, float2* drift_c, uint8_t* mask_c) {
+    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc >= nc * nc) return;
+    const int r = (n - 1) / (nc - 1);
+    const int hw = r / 2;
+    const int I = kc % nc, J = kc / nc;
+    const size_t kf = (size_t)(r * J) * n + (size_t)(r * I);
+    speed_c[kc] = speed[kf];
+    if (drift_c) drift_c[kc] = drift[kf];
+    bool tgt = false;
+    for (int dj = -hw; dj <= hw && !tgt; ++dj) {
+        const int fj = r * J + dj;
+        if (fj < 0 || fj >= n) continue;
+        for (int di = -hw; di <= hw; ++di) {
+            const int fi = r * I + di;
+            if (fi < 0 || fi >= n) continue;
+            if (mask[(size_t)fj * n + fi] == kTarget) {
+                tgt = true;
+                break;
+            }
+        }
+    }
+    mask_c[kc] = tgt ? kTarget : (mask[kf] == kObstacle ? kObstacle : kFree);
+}
+
+// Coarse solve: eq. SLscheme3 with sigma = 0 on G_c, iterated in place in one
+// block's shared memory (updates inside a sweep see the newest values, as in
+// the paper's Gauss-Seidel), alternating the visiting direction between
+// sweeps, until the sup-increment of a sweep is <= tol.
+__global__ void __launch_bounds__(1024)
+k_coarse_solve(GridView g, float u_start, float tol, int max_sweeps, float* uc,
+               CoarseResult* res) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* sctrl = reinterpret_cast<float2*>(smem);
+    const size_t ctrl_bytes = ((size_t)g.na * sizeof(float2) + 15) & ~(size_t)15;
+    float* su = reinterpret_cast<float*>(smem + ctrl_bytes);
+    __shared__ float red[32];
+    __shared__ float s_inc;
+    const int n = g.n;
+    const int N = n * n;
+    const int tid = threadIdx.x;
+    for (int m = tid; m < g.na; m += blockDim.x) sctrl[m] = g.ctrl32[m];
+    for (int k = tid; k < N; k += blockDim.x) {
+        const int mk = g.mask[k];
+        su[k] = (mk == kFree) ? u_start : (mk == kTarget ? 0.0f : g.uob32);
+    }
+    __syncthreads();
+    int s = 0;
+    float inc = 0.0f;
+    for (s = 0; s < max_sweeps; ++s) {
+        float lmax = 0.0f;
+        const bool rev = (s & 1) != 0;
+        for (int t = tid; t < N; t += blockDim.x) {
+            const int k = rev ? (N - 1 - t) : t;
+            if (g.mask[k] != kFree) continue;
+            const int i = k % n, j = k / n;
+            const float uk = su[k];
+            const float c = g.speed[k];
+            float bx = 0.0f, by = 0.0f;
+            if (g.drift) {
+                const float2 b = g.drift[k];
+                bx = b.x;
+                by = b.y;
+            }
+            const volatile float* base = su + k;
+            auto U = [&](int dx, int dy) { return (float)base[dy * n + dx]; };
+            auto C = [&](int m) { return sctrl[m]; };
+            float Nn, D;
+            int M;
+            best_over_controls<float, false>(g, 3, i, j, uk, c, bx, by, 0, 1, C, U, Nn, D, M);
+            const float du = Nn / D;
+            su[k] = uk + du;
+            lmax = fmaxf(lmax, fabsf(du));
+        }
+        const float bm = block_max<float>(lmax, red);
+        if (tid == 0) s_inc = bm;
+        __syncthreads();
+        inc = s_inc;
+        if (inc <= tol) {
+            ++s;
+            break;
+        }
+    }
+    for (int k = tid; k < N; k += blockDim.x) uc[k] = su[k];
+    if (tid == 0) {
+        res->sweeps = (inc <= tol) ? s : -s;
+        res->increment = inc;
+    }
+}
+
+// u_hat: Q1 interpolation of u_c at the fine nodes (nested grids, ratio r).
+__global__ void k_interp(int nc, const float* __restrict__ uc, int n,
+                         const uint8_t* __restrict__ mask, float u_obst, float* uhat) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n * n) return;
+    const int i = (int)(k % n), j = (int)(k / n);
+    const int mk = mask[k];
+    if (mk != kFree) {
+        uhat[k] = (mk == kTarget) ? 0.0f : u_obst;
+        return;
+    }
+    const int r = (n - 1) / (nc - 1);
+    const int cx = min(i / r, nc - 2), cy = min(j / r, nc - 2);
+    const float fx = (float)(i - cx * r) / (float)r;
+    const float fy = (float)(j - cy * r) / (float)r;
+    const float* b = uc + (size_t)cy * nc + cx;
+    const float a0 = fmaf(fx, b[1] - b[0], b[0]);
+    const float a1 = fmaf(fx, b[nc + 1] - b[nc], b[nc]);
+    uhat[k] = fmaf(fy, a1 - a0, a0);
+}
+
+// Synthesis a*(x_i) = argmin_a beta u_hat(x_i + h f(x_i, a)) + h l (sigma = 0,
+// self vertex included, ties to the lowest index) and the causal band key
+// floor(T(u_hat)/w), T(u) = -log(1 - lambda u)/lambda (lambda u clipped at 1 - 1e-6).
+__global__ void k_synthesis(GridView g, const float* __restrict__ uhat, float lambda, float band_w,
+                            int band_cap, uint8_t* a_out, int32_t* key, int* max_key) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* sctrl = reinterpret_cast<float2*>(smem);
+    const int n = g.n;
+    for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = g.ctrl32[m];
+    __syncthreads();
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int kk = -1;
+    if (k < (size_t)n * n) {
+        if (g.mask[k] != kFree) {
+            a_out[k] = 255;
+            key[k] = -1;
+        } else {
+            const int i = (int)(k % n), j = (int)(k / n);
+            const float c = g.speed[k];
+            float bx = 0.0f, by = 0.0f;
+            if (g.drift) {
+                const float2 b = g.drift[k];
+                bx = b.x;
+                by = b.y;
+            }
+            const float* base = uhat + k;
+            auto U = [&](int dx, int dy) { return __ldg(base + (ptrdiff_t)dy * n + dx); };
+            auto C = [&](int m) { return sctrl[m]; };
+            float Nn, D;
+            int M;
+            best_over_controls<float, false>(g, 2, i, j, 0.0f, c, bx, by, 0, 1, C, U, Nn, D, M);
+            a_out[k] = (uint8_t)M;
+            float u = fmaxf(uhat[k], 0.0f);
+            float T;
+            if (lambda > 0.0f) {
+                const float lu = fminf(lambda * u, 1.0f - 1e-6f);
+                T = -log1pf(-lu) / lambda;
+            } else {
+                T = u;
+            }
+            kk = min((int)floorf(T / band_w), band_cap - 1);
+            key[k] = kk;
+        }
+    }
+    // block max of the keys -> one atomic per warp
+    int wm = kk;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, off));
+    if ((threadIdx.x & 31) == 0 && wm >= 0) atomicMax(max_key, wm);
+}
+
+// Band key of the current value (same mapping as in k_synthesis).
+__global__ void k_keys_from_values(int N, const uint8_t* __restrict__ mask,
+                                   const float* __restrict__ u, float lambda, float band_w,
+                                   int band_cap, int32_t* key, int* max_key) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int kk = -1;
+    if (k < N) {
+        if (mask[k] != kFree) {
+            key[k] = -1;
+        } else {
+            const float v = fmaxf(u[k], 0.0f);
+            float T;
+            if (lambda > 0.0f) {
+                const float lu = fminf(lambda * v, 1.0f - 1e-6f);
+                T = -log1pf(-lu) / lambda;
+            } else {
+                T = v;
+            }
+            kk = min((int)floorf(T / band_w), band_cap - 1);
+            key[k] = kk;
+        }
+    }
+    int wm = kk;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, off));
+    if ((threadIdx.x & 31) == 0 && wm >= 0) atomicMax(max_key, wm);
+}
+
+// Successor of each free node (winner-take-all transport step of eq.
+// discrete-advection).  The foot uses the prescribed IEEE FP32 sequence
+//   t = c*ax; t = t + bx; t = s*t; xi = (float)i + t    (round-to-nearest, no FMA)
+// so that the result is bit-reproducible on any IEEE machine; the heaviest Q1
+// vertex rounds each coordinate (0.5 rounds down); if it is the node itself the
+// neighbour along the axis whose fraction is closer to 1/2 is taken (equal:
+// lower linear index); a foot exactly on the node is a self-loop.
+__global__ void k_successors(GridView g, const uint8_t* __restrict__ a, int32_t* succ) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = g.n;
+    if (k >= (size_t)n * n) return;
+    if (g.mask[k] != kFree) {
+        succ[k] = (int32_t)k;
+        return;
+    }
+    const int i = (int)(k % n), j = (int)(k / n);
+    const int m = a[k];
+    const float2 ctrl = g.ctrl32[min(m, g.na - 1)];
+    const float c = g.speed[k];
+    float bx = 0.0f, by = 0.0f;
+    if (g.drift) {
+        const float2 b = g.drift[k];
+        bx = b.x;
+        by = b.y;
+    }
+    const float s = g.s32;
+    float tx = __fmul_rn(c, ctrl.x);
+    tx = __fadd_rn(tx, bx);
+    tx = __fmul_rn(s, tx);
+    float ty = __fmul_rn(c, ctrl.y);
+    ty = __fadd_rn(ty, by);
+    ty = __fmul_rn(s, ty);
+    const float top = (float)(n - 1);
+    float xi = __fadd_rn((float)i, tx);
+    float eta = __fadd_rn((float)j, ty);
+    xi = fminf(fmaxf(xi, 0.0f), top);
+    eta = fminf(fmaxf(eta, 0.0f), top);
+    int cx = (int)floorf(xi), cy = (int)floorf(eta);
+    cx = min(cx, n - 2);
+    cy = min(cy, n - 2);
+    const float fx = __fsub_rn(xi, (float)cx);
+    const float fy = __fsub_rn(eta, (float)cy);
+    const int vx = cx + (fx > 0.5f ? 1 : 0);
+    const int vy = cy + (fy > 0.5f ? 1 : 0);
+    int32_t out;
+    if (vx == i && vy == j) {
+        if (xi == (float)i && eta == (float)j) {
+            out = (int32_t)k;
+        } else {
+            const float ex = fabsf(__fsub_rn(fx, 0.5f));
+            const float ey = fabsf(__fsub_rn(fy, 0.5f));
+            const int ox = (vx == cx) ? cx + 1 : cx;
+            const int oy = (vy == cy) ? cy + 1 : cy;
+            const int32_t kx = vy * n + ox;
+            const int32_t ky = oy * n + vx;
+            out = (ex < ey) ? kx : ((ey < ex) ? ky : min(kx, ky));
+        }
+    } else {
+        out = vy * n + vx;
+    }
+    succ[k] = out;
+}
+
+// Pointer jumping: out[k] = in[in[k]].
+__global__ void k_jump(int N, const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) out[k] = in[in[k]];
+}
+
+// After enough jumps every pointer sits on its chain's terminal (a non-free
+// node) or inside a cycle of free nodes.
+__global__ void k_label_from_end(int N, const int32_t* __restrict__ end,
+                                 const uint8_t* __restrict__ mask, const int8_t* __restrict__ sector,
+                                 int n_patches, int8_t* label) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int t = end[k];
+    int8_t lab = (int8_t)n_patches;
+    if (mask[t] == kTarget && sector && sector[t] >= 0) lab = sector[t];
+    label[k] = lab;
+}
+
+// ------------------------------------------------------------------ ordering
+// Bin of a free node = band * (N_P + 1) + label; counting sort by bin.
+__global__ void k_hist(int N, const int32_t* __restrict__ key, const int8_t* __restrict__ label,
+                       const uint8_t* __restrict__ mask, int stride, int32_t* count) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N || mask[k] != kFree) return;
+    atomicAdd(&count[key[k] * stride + label[k]], 1);
+}
+
+// Exclusive scan of count[0..nb) into off[0..nb], one block.
+__global__ void __launch_bounds__(1024) k_scan(int nb, const int32_t* __restrict__ count,
+                                               int32_t* off) {
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(t * per, nb), b1 = min(b0 + per, nb);
+    int32_t s = 0;
+    for (int b = b0; b < b1; ++b) s += count[b];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < blockDim.x; o <<= 1) {
+        int32_t v = (t >= o) ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = (t == 0) ? 0 : part[t - 1];
+    for (int b = b0; b < b1; ++b) {
+        off[b] = run;
+        run += count[b];
+    }
+    if (t == blockDim.x - 1) off[nb] = part[t];
+}
+
+__global__ void k_scatter(int N, const int32_t* __restrict__ key, const int8_t* __restrict__ label,
+                          const uint8_t* __restrict__ mask, int stride, int32_t* cursor,
+                          int32_t* order) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N || mask[k] != kFree) return;
+    const int pos = atomicAdd(&cursor[key[k] * stride + label[k]], 1);
+    order[pos] = k;
+}
+
+__global__ void k_band_off(int n_bands, int stride, const int32_t* __restrict__ bin_off,
+                           int32_t* band_off) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b <= n_bands) band_off[b] = bin_off[b * stride];
+}
+
+__global__ void k_promote(int N, const float* __restrict__ a, double* b) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) b[k] = (double)a[k];
+}
+
+__global__ void k_demote(int N, const double* __restrict__ a, float* b) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) b[k] = (float)a[k];
+}
+
+__global__ void k_init_values(int N, const uint8_t* __restrict__ mask, float free_val, float uob,
+                              float* u32, double* u64, double uob64) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int mk = mask[k];
+    if (u32) u32[k] = (mk == kFree) ? free_val : (mk == kTarget ? 0.0f : uob);
+    if (u64) u64[k] = (mk == kFree) ? (double)free_val : (mk == kTarget ? 0.0 : uob64);
+}
+
+__global__ void k_fix_nonfree(int N, const uint8_t* __restrict__ mask, float uob, double uob64,
+                              float* u32, double* u64) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int mk = mask[k];
+    if (mk == kFree) return;
+    if (u32) u32[k] = (mk == kTarget) ? 0.0f : uob;
+    if (u64) u64[k] = (mk == kTarget) ? 0.0 : uob64;
+}
+
+}  // namespace
+
+cudaError_t launch_coarse_data(int n, int nc, const float* speed, const float2* drift,
+                               const uint8_t* mask, float* speed_c, float2* drift_c,
+                               uint8_t* mask_c, cudaStream_t st) {
+    k_coarse_data<<<blocks_for((long long)nc * nc), kThreads, 0, st>>>(n, nc, speed, drift, mask,
+                                                                         speed_c, drift_c, mask_c);
+    return cudaGetLastError();
+}
+
+size_t coarse_solve_smem(int nc, int na) {
+    return (((size_t)na * sizeof(float2) + 15) & ~(size_t)15) + (size_t)nc * nc * sizeof(float);
+}
+
+cudaError_t launch_coarse_solve(const GridView& gc, float u_start, float tol, int max_sweeps,
+                                float* uc, CoarseResult* res, cudaStream_t st) {
+    const size_t smem = coarse_solve_smem(gc.n, gc.na);
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_coarse_solve<<<1, 1024, smem, st>>>(gc, u_start, tol, max_sweeps, uc, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, float u_obst,
+                          float* uhat, cudaStream_t st) {
+    k_interp<<<blocks_for((long long)n * n), kThreads, 0, st>>>(nc, uc, n, mask, u_obst, uhat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda, float band_w,
+                             int band_cap, uint8_t* a, int32_t* key, int* max_key, cudaStream_t st) {
+    const size_t smem = (size_t)g.na * sizeof(float2);
+    k_synthesis<<<blocks_for((long long)g.n * g.n), kThreads, smem, st>>>(g, uhat, lambda, band_w,
+                                                                          band_cap, a, key, max_key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, float lambda,
+                                    float band_w, int band_cap, int32_t* key, int* max_key,
+                                    cudaStream_t st) {
+    k_keys_from_values<<<blocks_for(N), kThreads, 0, st>>>(N, mask, u, lambda, band_w, band_cap,
+                                                             key, max_key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_successors(const GridView& g, const uint8_t* a, int32_t* succ, cudaStream_t st) {
+    k_successors<<<blocks_for((long long)g.n * g.n), kThreads, 0, st>>>(g, a, succ);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const int8_t* sector,
+                          int n_patches, int32_t* jump_a, int32_t* jump_b, int8_t* label,
+                          cudaStream_t st) {
+    // 2^rounds >= N: every chain has reached its end or a cycle.
+    int rounds = 1;
+    while ((1LL << rounds) < (long long)N) ++rounds;
+    const int32_t* in = succ;
+    int32_t* bufs[2] = {jump_a, jump_b};
+    for (int r = 0; r < rounds; ++r) {
+        int32_t* out = bufs[r & 1];
+        k_jump<<<blocks_for(N), kThreads, 0, st>>>(N, in, out);
+        in = out;
+    }
+    k_label_from_end<<<blocks_for(N), kThreads, 0, st>>>(N, in, mask, sector, n_patches, label);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const uint8_t* mask,
+                         int n_patches, int n_bands, int32_t* bin_count, int32_t* bin_off,
+                         int32_t* order, int32_t* band_off, cudaStream_t st) {
+    const int stride = n_patches + 1;
+    const int nb = n_bands * stride;
+    cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * (size_t)nb, st);
+    if (e != cudaSuccess) return e;
+    k_hist<<<blocks_for(N), kThreads, 0, st>>>(N, key, label, mask, stride, bin_count);
+    k_scan<<<1, 1024, 0, st>>>(nb, bin_count, bin_off);
+    // bin_count becomes the scatter cursor
+    e = cudaMemcpyAsync(bin_count, bin_off, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<blocks_for(N), kThreads, 0, st>>>(N, key, label, mask, stride, bin_count, order);
+    k_band_off<<<blocks_for(n_bands + 1), kThreads, 0, st>>>(n_bands, stride, bin_off, band_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_promote(int N, const float* u32, double* u64, cudaStream_t st) {
+    k_promote<<<blocks_for(N), kThreads, 0, st>>>(N, u32, u64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_demote(int N, const double* u64, float* u32, cudaStream_t st) {
+    k_demote<<<blocks_for(N), kThreads, 0, st>>>(N, u64, u32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_values(int N, const uint8_t* mask, float free_val, float uob, float* u32,
+                               double* u64, double uob64, cudaStream_t st) {
+    k_init_values<<<blocks_for(N), kThreads, 0, st>>>(N, mask, free_val, uob, u32, u64, uob64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix_nonfree(int N, const uint8_t* mask, float uob, double uob64, float* u32,
+                               double* u64, cudaStream_t st) {
+    k_fix_nonfree<<<blocks_for(N), kThreads, 0, st>>>(N, mask, uob, uob64, u32, u64);
+    return cudaGetLastError();
+}
+
+}  // namespace hjb

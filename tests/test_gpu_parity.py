@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs come from ``hjb_inputs`` (seeded, synthetic, shaped like the paper's 2-D
+tests); expected values come from ``oracle`` only.  Tolerances:
+  * FP64 operator / solutions: 1e-12 per application, 1e-10 after the FP64
+    polish (the FP64 gate);
+  * FP32 operator: 2e-6 (a handful of FP32 roundings on values <= ~1);
+  * FP32 solutions: 1e-5 * max(1, |u|_inf) (the FP32 gate);
+  * integer outputs (successors, labels) bit-exact given the same a*;
+  * argmins: exact where the oracle's best candidate is unique by more than
+    the arithmetic's error, otherwise the chosen candidate must be within it.
+"""
+import numpy as np
+import pytest
+
+import hjb_inputs as hi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the -m gpu tests")
+    from paper_1502_01629_gb300 import build
+    build.build()
+
+
+def P_gpu(inst, **kw):
+    from paper_1502_01629_gb300 import Problem
+    return Problem.from_instance(inst, **kw)
+
+
+def instance_variants():
+    n = 37
+    out = []
+    out.append(("disc-s0", hi.disc_instance(n, 0.0, n_controls=32, speed=hi.speed_sine(n))))
+    out.append(("disc-s005", hi.disc_instance(n, 0.05, n_controls=32, speed=hi.speed_sine(n))))
+    inst = hi.disc_instance(101, 0.1, n_controls=33, speed=hi.speed_sine(101), lam=0.7)
+    out.append(("n101-na33-s01", inst))
+    inst = hi.disc_instance(150, 0.02, n_controls=64, speed=hi.speed_sine(150), lam=2.0)
+    out.append(("n150-na64", inst))
+    rng = np.random.default_rng(5)
+    inst = hi.disc_instance(45, 0.03, n_controls=16, speed=hi.speed_fourier(45, rng))
+    inst.drift = rng.uniform(-0.4, 0.4, 2 * 45 * 45).astype(np.float32)
+    inst.mask = hi.add_rect_obstacles(45, inst.mask, [(0.3, 0.3, 0.6, 0.5)])
+    out.append(("drift-obstacle", inst))
+    inst = hi.disc_instance(20, 0.2, n_controls=1, speed=hi.speed_constant(20, 0.3))
+    out.append(("na1-bigsigma", inst))
+    return out
+
+
+VARIANTS = instance_variants()
+
+
+@pytest.mark.parametrize("name,inst", VARIANTS, ids=[v[0] for v in VARIANTS])
+@pytest.mark.parametrize("scheme", [3, 2])
+def test_operator_parity_fp64(name, inst, scheme):
+    """One application of eq. SLscheme3 / SLscheme2 to a seeded random value field."""
+    O = oracle.Problem.from_instance(inst)
+    u = O.fix_nonfree(hi.random_values(inst.n, 11, 0.0, O.u_max, inst.mask))
+    exp, am_o, _ = O.apply(u, scheme)
+    with P_gpu(inst) as G:
+        got, am_g = G.apply_operator(u, precision=64, scheme=scheme)
+    np.testing.assert_allclose(got, exp, rtol=0, atol=1e-12)
+    _check_argmin(O, u, scheme, am_g, am_o, inst.mask, 1e-11)
+
+
+@pytest.mark.parametrize("name,inst", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_operator_parity_fp32(name, inst):
+    O = oracle.Problem.from_instance(inst)
+    u = O.fix_nonfree(hi.random_values(inst.n, 12, 0.0, O.u_max, inst.mask))
+    u = u.astype(np.float32).astype(np.float64)        # the FP32 path sees FP32 inputs
+    exp, am_o, _ = O.apply(u, 3)
+    with P_gpu(inst) as G:
+        got, am_g = G.apply_operator(u, precision=32, scheme=3)
+    np.testing.assert_allclose(got, exp, rtol=0, atol=2e-6 * max(1.0, O.u_max))
+    _check_argmin(O, u, 3, am_g, am_o, inst.mask, 4e-6 * max(1.0, O.u_max))
+
+
+def _check_argmin(O, u, scheme, am_g, am_o, mask, tol):
+    free = np.flatnonzero(mask == 0)
+    assert (am_g[mask != 0] == -1).all()
+    diff = free[am_g[free] != am_o[free]]
+    if diff.size:
+        vals = O.node_candidates(u, diff, scheme)
+        best = vals.min(axis=1)
+        chosen = vals[np.arange(diff.size), am_g[diff]]
+        assert (chosen - best <= tol).all(), (chosen - best).max()
+    assert diff.size <= max(3, free.size // 100)
+
+
+def test_plain_full_grid_fp64_matches_oracle():
+    """The plain FP64 workload (101^2, sigma = 0.05, 32 controls): Jacobi from u = 0
+    to a sup-increment of 1e-8, then to 1e-13 for the 1e-10 gate."""
+    inst = hi.plain_101()
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(scheme=3, tol=1e-14)
+    u_jac, sweeps_or, _ = O.solve(scheme=3, method="jacobi", tol=1e-8)
+    with P_gpu(inst) as G:
+        st = G.solve_full(precision=64, tol=1e-8, tol64=0.0)
+        assert abs(st["sweeps"] - sweeps_or) <= 8          # checked every 8 sweeps
+        u8 = G.get_value()
+        assert np.abs(u8 - u_ref).max() <= 1e-8 / (1.0 - O.beta)
+        st = G.solve_full(precision=64, tol=1e-13, tol64=0.0)
+        u = G.get_value()
+        assert st["residual"] <= 1e-13
+    np.testing.assert_allclose(u, u_ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("sigma", [0.0, 0.02, 0.1])
+def test_full_grid_fp32_then_fp64(sigma):
+    inst = hi.patchy_1025(sigma, n=129, coarse_n=17)
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(scheme=3, tol=1e-14)
+    with P_gpu(inst) as G:
+        st = G.solve_full(precision=32, tol=3e-7, tol64=0.0)
+        u32 = G.get_value()
+        assert np.abs(u32 - u_ref).max() <= 1e-5 * max(1.0, np.abs(u_ref).max())
+        st = G.solve_full(precision=32, tol=3e-7, tol64=1e-13)
+        assert st["residual"] <= 1e-12
+        u = G.get_value()
+    np.testing.assert_allclose(u, u_ref, rtol=0, atol=1e-10)
+
+
+def _oracle_pipeline(inst, tol_c=1e-9):
+    return oracle.patchy_precompute(inst, tol_c=tol_c)
+
+
+@pytest.mark.parametrize("sigma", [0.0, 0.02, 0.1])
+def test_patchy_pipeline_small(sigma):
+    """Coarse solve, u_hat, a*, labels, ordering and the band-ordered solve on the
+    patchy workload at 257^2 (coarse 33^2), against the oracle."""
+    inst = hi.patchy_1025(sigma, n=257, coarse_n=33)
+    O = oracle.Problem.from_instance(inst)
+    ref = _oracle_pipeline(inst)
+    with P_gpu(inst) as G:
+        cs = G.coarse_solve(tol_c=1e-7)
+        uc = G.get_coarse_value()
+        # FP32 coarse iteration stopped at 1e-7: error <= 1e-7 / (1 - beta_c) + rounding
+        bc = ref["coarse"].beta
+        assert np.abs(uc - ref["uc"]).max() <= 2e-7 / (1 - bc) + 1e-5
+        G.build_patches()
+        uh = G.get_uhat()
+        assert np.abs(uh - ref["uhat"]).max() <= 2e-7 / (1 - bc) + 1e-5
+        # synthesis: the chosen control is a minimiser of the oracle's objective up
+        # to the difference of the two u_hat
+        a = G.get_feedback()
+        free = np.flatnonzero(inst.mask == 0)
+        assert (a[inst.mask != 0] == 255).all()
+        diff = free[a[free] != ref["a"][free]]
+        assert diff.size <= free.size // 50
+        if diff.size:
+            vals = O.synthesis_values(ref["uhat"], diff)
+            chosen = vals[np.arange(diff.size), a[diff]]
+            assert (chosen - vals.min(axis=1) <= 4e-5).all()
+        # labels bit-exact given the oracle's a*
+        G.set_feedback(ref["a"])
+        np.testing.assert_array_equal(G.get_successors(), ref["succ"])
+        lab = G.get_labels()
+        np.testing.assert_array_equal(lab, ref["labels"])
+        keys, order, off = G.get_order()
+        # ordering: a permutation of the free nodes, grouped by nondecreasing band
+        assert np.array_equal(np.sort(order), free)
+        kk = keys[order]
+        assert (np.diff(kk) >= 0).all()
+        for b in range(len(off) - 1):
+            assert (kk[off[b]:off[b + 1]] == b).all()
+        key_or = oracle.band_keys(ref["uhat"], inst.mask, inst.lam, O.h, 1 << 20)
+        assert (np.abs(keys[free] - key_or[free]) <= 1).all()
+        assert (keys[free] == key_or[free]).mean() > 0.99
+        # within a band the nodes are grouped by patch
+        for b in range(0, len(off) - 1, max(1, (len(off) - 1) // 20)):
+            seg = lab[order[off[b]:off[b + 1]]]
+            assert (np.diff(seg.astype(int)) >= 0).all()
+        # solve: FP32 phase, then FP64 polish
+        st = G.solve_patches(tol32=3e-7, tol64=0.0)
+        u32 = G.get_value()
+        u_ref, _, _ = O.solve(scheme=3, order=np.argsort(ref["uhat"], kind="stable"), tol=1e-14)
+        assert np.abs(u32 - u_ref).max() <= 1e-5 * max(1.0, np.abs(u_ref).max())
+        st = G.solve_patches(tol32=3e-7, tol64=1e-12)
+        assert st["residual"] <= 1e-12
+        u = G.get_value()
+    np.testing.assert_allclose(u, u_ref, rtol=0, atol=1e-10)
+
+
+def test_paper_mode_case_a_on_gpu():
+    """Section 5.1, Case A (b = (1,0) read with inflow on the left, eps = 0,
+    undiscounted, exit through the boundary): the solution is u = x1 + 1."""
+    n = 50
+    dx = 2.0 / (n - 1)
+    mask = hi.square_boundary_target(n)
+    drift = np.zeros((n * n, 2), np.float32)
+    drift[:, 0] = -1.0
+    inst = hi.Instance(n=n, controls=np.array([[1.0, 0.0]]), speed=hi.speed_constant(n, 0.0),
+                       mask=mask, sector=hi.sectors_square_sides(n, mask), h=dx / 2, lam=0.0,
+                       sigma=0.0, drift=drift.reshape(-1), n_patches=4)
+    with P_gpu(inst) as G:
+        G.solve_full(precision=64, tol=1e-13, tol64=0.0)
+        u = G.get_value()
+    x1 = hi.mesh(n)[0].ravel()
+    free = mask == 0
+    np.testing.assert_allclose(u[free], x1[free] + 1.0, rtol=0, atol=1e-10)
+
+
+def test_edge_cases_tiny_and_all_target():
+    # smallest grid: 3x3 with one free node
+    n = 3
+    mask = np.ones(9, np.uint8)
+    mask[4] = 0
+    inst = hi.Instance(n=n, controls=hi.control_set(8), speed=hi.speed_constant(n), mask=mask,
+                       sector=np.where(mask == 1, 0, -1).astype(np.int8), sigma=0.3, lam=1.0,
+                       coarse_n=3, n_patches=1)
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(tol=1e-15)
+    with P_gpu(inst) as G:
+        G.solve_full(precision=64, tol=1e-14, tol64=0.0)
+        np.testing.assert_allclose(G.get_value(), u_ref, atol=1e-12)
+        G.coarse_solve(tol_c=1e-7)
+        G.build_patches()
+        G.solve_patches(tol32=1e-7, tol64=1e-13)
+        np.testing.assert_allclose(G.get_value(), u_ref, atol=1e-10)
+    # every node a target: nothing to update
+    inst = hi.Instance(n=5, controls=hi.control_set(4), speed=hi.speed_constant(5),
+                       mask=np.ones(25, np.uint8), sector=np.zeros(25, np.int8), coarse_n=3)
+    with P_gpu(inst) as G:
+        G.coarse_solve()
+        G.build_patches()
+        G.solve_patches(tol32=1e-7, tol64=1e-12)
+        assert (G.get_value() == 0).all()
+        G.solve_full(precision=32, tol=1e-7, tol64=1e-12)
+
+
+def test_warm_start_and_state_errors():
+    from paper_1502_01629_gb300 import HJBError
+    inst = hi.patchy_1025(0.02, n=65, coarse_n=17)
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(tol=1e-14)
+    with P_gpu(inst) as G:
+        with pytest.raises(HJBError):
+            G.build_patches()                   # coarse_solve has not run
+        with pytest.raises(HJBError):
+            G.solve_patches()
+        G.coarse_solve()
+        G.build_patches()
+        # resume from a perturbed copy of the solution: same fixed point
+        G.set_value(u_ref + 0.01 * (inst.mask == 0))
+        G.solve_patches(tol32=1e-7, tol64=1e-13)
+        np.testing.assert_allclose(G.get_value(), u_ref, atol=1e-10)
+        assert G.residual() <= 1e-12
