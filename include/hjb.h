@@ -97,6 +97,9 @@ typedef struct {
     double  ms_stage[8];           /* per-stage device time, see each entry point                */
     int32_t fp32_passes;           /* solve_patches / solve_full: passes (sweeps) in FP32         */
     int32_t fp64_passes;           /* passes (sweeps) in FP64                                     */
+    int64_t fp64_node_updates;     /* the part of node_updates done in FP64                       */
+    int32_t residual_evals;        /* FP64 residual evaluations (full-grid operator applications) */
+    int32_t pad;
 } hjb_stats;
 
 /* Regime of the upwind diffusion-ball condition (Section 4.1, eqs. upper-bound,
@@ -150,7 +153,9 @@ int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const ui
 
 /* hjb_coarse_solve -- Section 4.3 "Pre-computation", first item: starting from
  * u_c^0 = l(1/lambda + h) off the target (the paper's "very big value"), iterate
- * SLscheme3 with sigma = 0 on G_c until the sup-increment is <= tol_c.  G_c is
+ * SLscheme3 with sigma = 0 on G_c (full-grid Jacobi sweeps, the paper's
+ * "standard (static) domain decomposition" of the coarse solve taken to one node
+ * per thread) until the sup-increment is <= tol_c.  G_c is
  * nested in G: coarse node (I,J) is fine node (rI, rJ), r = (n-1)/(coarse_n-1);
  * its speed is the fine speed there; it is a target when a fine target node lies
  * within r/2 fine cells in both axes, else an obstacle when its fine node is one.
@@ -259,6 +264,10 @@ const char* hjb_status_string(int code);
 
 /* hjb_last_error -- message of the last failure on the calling thread ("" if none). */
 const char* hjb_last_error(void);
+
+/* hjb_kernel_launches -- number of CUDA kernels this library has launched since it
+ * was loaded (all problems, all threads); a reporting aid for benchmarks. */
+long long hjb_kernel_launches(void);
 
 #ifdef __cplusplus
 }

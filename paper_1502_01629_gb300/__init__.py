@@ -22,7 +22,7 @@ import numpy as np
 from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, Desc, HJBError, RegimeInfo, Stats, check,
                    header_functions, lib)
 
-__all__ = ["Problem", "HJBError", "regime", "lib", "header_functions", "HJB_ERR_NOT_CONVERGED"]
+__all__ = ["Problem", "HJBError", "regime", "kernel_launches", "lib", "header_functions", "HJB_ERR_NOT_CONVERGED"]
 
 
 def _c(a: np.ndarray, dtype) -> np.ndarray:
@@ -31,6 +31,11 @@ def _c(a: np.ndarray, dtype) -> np.ndarray:
 
 def _p(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched since it was loaded."""
+    return int(lib().hjb_kernel_launches())
 
 
 def regime(dx: float, f_min: float, f_max: float, eps: float) -> dict:

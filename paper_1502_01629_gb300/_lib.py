@@ -38,7 +38,9 @@ class Stats(ctypes.Structure):
                 ("node_updates", ctypes.c_int64), ("node_control_updates", ctypes.c_int64),
                 ("residual", ctypes.c_double), ("increment", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_stage", ctypes.c_double * 8),
-                ("fp32_passes", ctypes.c_int32), ("fp64_passes", ctypes.c_int32)]
+                ("fp32_passes", ctypes.c_int32), ("fp64_passes", ctypes.c_int32),
+                ("fp64_node_updates", ctypes.c_int64), ("residual_evals", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "ms_stage"}
@@ -86,6 +88,7 @@ _SIGNATURES = {
     "hjb_destroy": (None, [_P]),
     "hjb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hjb_last_error": (ctypes.c_char_p, []),
+    "hjb_kernel_launches": (ctypes.c_longlong, []),
 }
 
 _LIB = None

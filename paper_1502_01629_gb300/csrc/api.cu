@@ -3,6 +3,7 @@
 // pre-computation -> band-ordered patch solve with FP64 polish), the plain
 // full-grid comparator, the regime helper of Section 4.1 and the getters.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,6 +16,14 @@
 #include "hjb_kernels.h"
 
 using namespace hjb;
+
+namespace hjb {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hjb
 
 namespace {
 
@@ -116,6 +125,8 @@ struct hjb_problem {
     float2* drift_c = nullptr;
     uint8_t* mask_c = nullptr;
     float* uc = nullptr;
+    float* uc_b = nullptr;
+    int halo_c = 1;
     double hc = 0, beta_c = 0, hl_c = 0, uob_c = 0;
     // pre-computation
     float* uhat = nullptr;
@@ -387,13 +398,12 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         p->beta_c = 1.0 / (1.0 + p->lambda * p->hc);
         p->hl_c = p->hc * desc->cost;
         p->uob_c = p->lambda > 0.0 ? p->hl_c / (1.0 - p->beta_c) : 1e6;
-        if (coarse_solve_smem(nc, na) > 227 * 1024) {
-            return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d too large for one block's shared memory", nc));
-        }
+        p->halo_c = sweep_halo(p->h * (cmax * amax + bmax) / p->dx);
         const size_t Nc = (size_t)nc * nc;
         CUP(cudaMalloc(&p->speed_c, Nc * sizeof(float)));
         CUP(cudaMalloc(&p->mask_c, Nc));
         CUP(cudaMalloc(&p->uc, Nc * sizeof(float)));
+        CUP(cudaMalloc(&p->uc_b, Nc * sizeof(float)));
         if (drift) CUP(cudaMalloc(&p->drift_c, Nc * sizeof(float2)));
         CUP(launch_coarse_data(n, nc, p->speed, p->drift, p->mask, p->speed_c, p->drift_c,
                                p->mask_c, p->st));
@@ -429,86 +439,75 @@ int ensure_hist(hjb_problem* p, int cap) {
 // sweep is <= tol; the increment of every sweep lands in inc_hist, checked on
 // the host every kCheck sweeps.  Returns the sweeps done in *sweeps and the
 // last increment in *last; the result is in buf[0].
-template <typename T>
-int jacobi_loop(hjb_problem* p, T* buf0, T* buf1, double tol, int max_sweeps, int* sweeps,
-                double* last, bool* converged);
-
-template <>
-int jacobi_loop<float>(hjb_problem* p, float* buf0, float* buf1, double tol, int max_sweeps,
-                       int* sweeps, double* last, bool* converged) {
+// Plain Jacobi sweeps u <- T u (double buffered) on the grid `g` until the
+// sup-increment of a sweep is <= tol; the increment of every sweep lands in
+// inc_hist, checked on the host every kCheck sweeps.  Returns the sweeps done
+// in *sweeps and the last increment in *last; the result is in buf0.
+template <typename T, typename Bits, typename Launch>
+int jacobi_loop_impl(hjb_problem* p, Bits* hist, T* buf0, T* buf1, int N, double tol,
+                     int max_sweeps, int* sweeps, double* last, bool* converged,
+                     const Launch& launch) {
     constexpr int kCheck = 8;
-    int rc = ensure_hist(p, max_sweeps + kCheck);
-    if (rc) return rc;
-    CU(cudaMemsetAsync(p->inc_hist32, 0, sizeof(unsigned int) * (size_t)(max_sweeps + kCheck), p->st));
-    const GridView g = p->fine_view();
-    const bool sig = p->sigma > 0.0;
-    std::vector<unsigned int> h(kCheck);
-    float* cur = buf0;
-    float* nxt = buf1;
+    CU(cudaMemsetAsync(hist, 0, sizeof(Bits) * (size_t)(max_sweeps + kCheck), p->st));
+    std::vector<Bits> h(kCheck);
+    T* cur = buf0;
+    T* nxt = buf1;
     int s = 0;
     *converged = false;
     *last = -1.0;
     while (s < max_sweeps) {
         const int chunk = std::min(kCheck, max_sweeps - s);
         for (int c = 0; c < chunk; ++c) {
-            CU(launch_sweep_f32(g, sig, p->desc.scheme, p->halo, cur, nxt, nullptr,
-                                p->inc_hist32 + s + c, p->st));
+            CU(launch(cur, nxt, hist + s + c));
             std::swap(cur, nxt);
         }
-        CU(cudaMemcpyAsync(h.data(), p->inc_hist32 + s, sizeof(unsigned int) * chunk,
-                           cudaMemcpyDeviceToHost, p->st));
+        CU(cudaMemcpyAsync(h.data(), hist + s, sizeof(Bits) * chunk, cudaMemcpyDeviceToHost, p->st));
         CU(cudaStreamSynchronize(p->st));
         s += chunk;
-        float v = 0.0f;
-        std::memcpy(&v, &h[chunk - 1], sizeof(float));
-        *last = v;
-        if (v <= tol) {
-            *converged = true;
-            break;
+        // first sweep of the chunk that met the tolerance
+        for (int c = 0; c < chunk; ++c) {
+            T v;
+            std::memcpy(&v, &h[c], sizeof(T));
+            *last = (double)v;
+            if ((double)v <= tol) {
+                *converged = true;
+                break;
+            }
         }
+        if (*converged) break;
     }
-    if (cur != buf0) CU(cudaMemcpyAsync(buf0, cur, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, p->st));
+    if (cur != buf0) CU(cudaMemcpyAsync(buf0, cur, sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, p->st));
     *sweeps = s;
     return HJB_OK;
 }
 
-template <>
-int jacobi_loop<double>(hjb_problem* p, double* buf0, double* buf1, double tol, int max_sweeps,
-                        int* sweeps, double* last, bool* converged) {
-    constexpr int kCheck = 8;
-    int rc = ensure_hist(p, max_sweeps + kCheck);
+int jacobi32(hjb_problem* p, const GridView& g, int halo, float* buf0, float* buf1, double tol,
+             int max_sweeps, int* sweeps, double* last, bool* converged) {
+    int rc = ensure_hist(p, max_sweeps + 8);
     if (rc) return rc;
-    CU(cudaMemsetAsync(p->inc_hist64, 0, sizeof(unsigned long long) * (size_t)(max_sweeps + kCheck), p->st));
+    const bool sig = g.d64 > 0.0;
+    const int scheme = p->desc.scheme;
+    return jacobi_loop_impl<float>(p, p->inc_hist32, buf0, buf1, g.n * g.n, tol, max_sweeps, sweeps,
+                                   last, converged,
+                                   [&](const float* a, float* b, unsigned int* inc) {
+                                       return launch_sweep_f32(g, sig, scheme, halo, a, b, nullptr,
+                                                               inc, p->st);
+                                   });
+}
+
+int jacobi64(hjb_problem* p, double* buf0, double* buf1, double tol, int max_sweeps, int* sweeps,
+             double* last, bool* converged) {
+    int rc = ensure_hist(p, max_sweeps + 8);
+    if (rc) return rc;
     const GridView g = p->fine_view();
     const bool sig = p->sigma > 0.0;
-    std::vector<unsigned long long> h(kCheck);
-    double* cur = buf0;
-    double* nxt = buf1;
-    int s = 0;
-    *converged = false;
-    *last = -1.0;
-    while (s < max_sweeps) {
-        const int chunk = std::min(kCheck, max_sweeps - s);
-        for (int c = 0; c < chunk; ++c) {
-            CU(launch_sweep_f64(g, sig, p->desc.scheme, p->halo, cur, nxt, nullptr,
-                                p->inc_hist64 + s + c, p->st));
-            std::swap(cur, nxt);
-        }
-        CU(cudaMemcpyAsync(h.data(), p->inc_hist64 + s, sizeof(unsigned long long) * chunk,
-                           cudaMemcpyDeviceToHost, p->st));
-        CU(cudaStreamSynchronize(p->st));
-        s += chunk;
-        double v = 0.0;
-        std::memcpy(&v, &h[chunk - 1], sizeof(double));
-        *last = v;
-        if (v <= tol) {
-            *converged = true;
-            break;
-        }
-    }
-    if (cur != buf0) CU(cudaMemcpyAsync(buf0, cur, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, p->st));
-    *sweeps = s;
-    return HJB_OK;
+    const int scheme = p->desc.scheme;
+    return jacobi_loop_impl<double>(p, p->inc_hist64, buf0, buf1, p->N, tol, max_sweeps, sweeps,
+                                    last, converged,
+                                    [&](const double* a, double* b, unsigned long long* inc) {
+                                        return launch_sweep_f64(g, sig, scheme, p->halo, a, b,
+                                                                nullptr, inc, p->st);
+                                    });
 }
 
 // FP64 sup-residual ||T2 u - u|| of u64.
@@ -641,6 +640,8 @@ const char* hjb_status_string(int code) {
 
 const char* hjb_last_error(void) { return g_last_error.c_str(); }
 
+long long hjb_kernel_launches(void) { return hjb::launches(); }
+
 int hjb_regime(double dx, double f_min, double f_max, double eps, hjb_regime_info* out) {
     if (!out || !(dx > 0.0) || !(f_min > 0.0) || !(f_max >= f_min) || !(eps >= 0.0))
         return fail(HJB_ERR_INVALID_ARG, "hjb_regime: need dx>0, 0<f_min<=f_max, eps>=0");
@@ -689,7 +690,7 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->speed); dfree(p->drift); dfree(p->mask); dfree(p->sector);
     dfree(p->ctrl32); dfree(p->ctrl64);
     dfree(p->u32); dfree(p->u32b); dfree(p->u64); dfree(p->u64b);
-    dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc);
+    dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc); dfree(p->uc_b);
     dfree(p->uhat); dfree(p->a); dfree(p->succ); dfree(p->jump_a); dfree(p->jump_b);
     dfree(p->label); dfree(p->key); dfree(p->order); dfree(p->bin_count); dfree(p->bin_off);
     dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
@@ -707,13 +708,20 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     if (!(tol_c > 0.0) || max_sweeps < 1) return fail(HJB_ERR_INVALID_ARG, "bad tol_c / max_sweeps");
     Timer tm(p->st);
     tm.mark();
-    Scalars* ds = dscal(p);
-    CU(launch_coarse_solve(p->coarse_view(), (float)p->uob_c, (float)tol_c, max_sweeps, p->uc,
-                           &ds->coarse, p->st));
+    const GridView gc = p->coarse_view();
+    const int Nc = p->nc * p->nc;
+    CU(launch_init_values(Nc, p->mask_c, (float)p->uob_c, (float)p->uob_c, p->uc, nullptr, p->uob_c, p->st));
+    CU(launch_init_values(Nc, p->mask_c, (float)p->uob_c, (float)p->uob_c, p->uc_b, nullptr, p->uob_c, p->st));
+    int sweeps = 0;
+    double last = -1.0;
+    bool conv = false;
+    int rcj = jacobi32(p, gc, p->halo_c, p->uc, p->uc_b, tol_c, max_sweeps, &sweeps, &last, &conv);
+    if (rcj) return rcj;
     tm.mark();
-    CU(cudaMemcpyAsync(&hscal(p)->coarse, &ds->coarse, sizeof(CoarseResult), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
-    const CoarseResult cr = hscal(p)->coarse;
+    CoarseResult cr;
+    cr.sweeps = conv ? sweeps : -sweeps;
+    cr.increment = (float)last;
     p->coarse_done = true;
     p->built = false;
     int rc = cr.sweeps > 0 ? HJB_OK : HJB_ERR_NOT_CONVERGED;
@@ -842,6 +850,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
     double ms_promote = 0.0, ms64 = 0.0;
     unsigned long long nodes64 = 0;
     int passes64 = 0;
+    int n_res = 0;
     double last = w32.last_increment;
     if (tol64 > 0.0 && rc == HJB_OK) {
         Timer t2(p->st);
@@ -850,6 +859,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         p->value_f64 = true;
         int r2 = residual64(p, &res);
         if (r2) return r2;
+        ++n_res;
         t2.mark();
         ms_promote += t2.ms(0, 1);
         double tol_pass = tol64;
@@ -864,6 +874,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
             last = w64.last_increment;
             r2 = residual64(p, &res);
             if (r2) return r2;
+            ++n_res;
             t3.mark();
             ms64 += t3.ms(0, 1);
             ms_promote += t3.ms(1, 2);
@@ -877,6 +888,8 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         stats->sweeps = w32.passes + passes64;
         stats->node_updates = (long long)(w32.nodes + nodes64);
         stats->node_control_updates = stats->node_updates * p->na;
+        stats->fp64_node_updates = (long long)nodes64;
+        stats->residual_evals = n_res;
         stats->residual = res;
         stats->increment = last;
         stats->ms_stage[0] = tm.ms(0, 1);
@@ -906,26 +919,34 @@ int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64, 
     if (precision == 32) {
         CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, nullptr, p->uob, p->st));
         CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32b, nullptr, p->uob, p->st));
-        rc = jacobi_loop<float>(p, p->u32, p->u32b, tol, max_sweeps, &s32, &last, &conv);
+        rc = jacobi32(p, p->fine_view(), p->halo, p->u32, p->u32b, tol, max_sweeps, &s32, &last, &conv);
         if (rc) return rc;
         p->value_f64 = false;
         if (!conv) rc = HJB_ERR_NOT_CONVERGED;
     }
     tm.mark();
     if (precision == 64 || (tol64 > 0.0 && rc == HJB_OK)) {
+        bool need = true;
         if (precision == 64) {
             CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, nullptr, p->u64, p->uob, p->st));
         } else {
+            // FP64 sweeps only if the FP32 result misses the FP64 residual tolerance
             CU(launch_promote(p->N, p->u32, p->u64, p->st));
+            int r2 = residual64(p, &res);
+            if (r2) return r2;
+            p->value_f64 = true;
+            need = res > tol64;
         }
-        CU(cudaMemcpyAsync(p->u64b, p->u64, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, p->st));
-        const double t = precision == 64 ? tol : tol64;
-        int r2 = jacobi_loop<double>(p, p->u64, p->u64b, t, max_sweeps, &s64, &last, &conv);
-        if (r2) return r2;
-        p->value_f64 = true;
-        rc = conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
-        r2 = residual64(p, &res);
-        if (r2) return r2;
+        if (need) {
+            CU(cudaMemcpyAsync(p->u64b, p->u64, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, p->st));
+            const double t = precision == 64 ? tol : tol64;
+            int r2 = jacobi64(p, p->u64, p->u64b, t, max_sweeps, &s64, &last, &conv);
+            if (r2) return r2;
+            p->value_f64 = true;
+            rc = conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
+            r2 = residual64(p, &res);
+            if (r2) return r2;
+        }
     }
     tm.mark();
     CU(cudaStreamSynchronize(p->st));
@@ -935,6 +956,8 @@ int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64, 
         stats->sweeps = s32 + s64;
         stats->node_updates = (long long)(s32 + s64) * p->n_free_total;
         stats->node_control_updates = stats->node_updates * p->na;
+        stats->fp64_node_updates = (long long)s64 * p->n_free_total;
+        stats->residual_evals = (precision == 32 && tol64 > 0.0 ? 1 : 0) + (s64 > 0 ? 1 : 0);
         stats->residual = res;
         stats->increment = last;
         stats->ms_stage[0] = tm.ms(0, 1);

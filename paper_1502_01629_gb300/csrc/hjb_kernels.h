@@ -10,6 +10,10 @@
 
 namespace hjb {
 
+// Number of kernels this library has launched (all threads), for reporting.
+void count_launches(long long k);
+long long launches();
+
 // ---------------------------------------------------------------- sweep.cu
 // Halo (cells) a tile needs so that every Q1 vertex of every point lies inside.
 int sweep_halo(double reach_cells);
@@ -33,11 +37,6 @@ struct CoarseResult {
 cudaError_t launch_coarse_data(int n, int nc, const float* speed, const float2* drift,
                                const uint8_t* mask, float* speed_c, float2* drift_c,
                                uint8_t* mask_c, cudaStream_t st);
-// Whole coarse grid in one block's shared memory; returns an error when nc is
-// too large for shared memory.
-cudaError_t launch_coarse_solve(const GridView& gc, float u_start, float tol, int max_sweeps,
-                                float* uc, CoarseResult* res, cudaStream_t st);
-size_t coarse_solve_smem(int nc, int na);
 cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, float u_obst,
                           float* uhat, cudaStream_t st);
 cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda, float band_w,

@@ -1,5 +1,5 @@
 // Pre-computation of the patchy decomposition (Cacace & Falcone, Section 4.3):
-// coarse grid data and coarse solve (sigma = 0), Q1 interpolation u_hat,
+// coarse grid data, Q1 interpolation u_hat,
 // feedback synthesis (eq. discrete-synthesis) with the causal band keys
 // (Section 4.2), winner-take-all transport successors (eq. discrete-advection),
 // labels by pointer jumping and the (band, patch) ordering of the free nodes.
@@ -44,71 +44,6 @@ __global__ void k_coarse_data(int n, int nc, const float* __restrict__ speed,
         }
     }
     mask_c[kc] = tgt ? kTarget : (mask[kf] == kObstacle ? kObstacle : kFree);
-}
-
-// Coarse solve: eq. SLscheme3 with sigma = 0 on G_c, iterated in place in one
-// block's shared memory (updates inside a sweep see the newest values, as in
-// the paper's Gauss-Seidel), alternating the visiting direction between
-// sweeps, until the sup-increment of a sweep is <= tol.
-__global__ void __launch_bounds__(1024)
-k_coarse_solve(GridView g, float u_start, float tol, int max_sweeps, float* uc,
-               CoarseResult* res) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float2* sctrl = reinterpret_cast<float2*>(smem);
-    const size_t ctrl_bytes = ((size_t)g.na * sizeof(float2) + 15) & ~(size_t)15;
-    float* su = reinterpret_cast<float*>(smem + ctrl_bytes);
-    __shared__ float red[32];
-    __shared__ float s_inc;
-    const int n = g.n;
-    const int N = n * n;
-    const int tid = threadIdx.x;
-    for (int m = tid; m < g.na; m += blockDim.x) sctrl[m] = g.ctrl32[m];
-    for (int k = tid; k < N; k += blockDim.x) {
-        const int mk = g.mask[k];
-        su[k] = (mk == kFree) ? u_start : (mk == kTarget ? 0.0f : g.uob32);
-    }
-    __syncthreads();
-    int s = 0;
-    float inc = 0.0f;
-    for (s = 0; s < max_sweeps; ++s) {
-        float lmax = 0.0f;
-        const bool rev = (s & 1) != 0;
-        for (int t = tid; t < N; t += blockDim.x) {
-            const int k = rev ? (N - 1 - t) : t;
-            if (g.mask[k] != kFree) continue;
-            const int i = k % n, j = k / n;
-            const float uk = su[k];
-            const float c = g.speed[k];
-            float bx = 0.0f, by = 0.0f;
-            if (g.drift) {
-                const float2 b = g.drift[k];
-                bx = b.x;
-                by = b.y;
-            }
-            const volatile float* base = su + k;
-            auto U = [&](int dx, int dy) { return (float)base[dy * n + dx]; };
-            auto C = [&](int m) { return sctrl[m]; };
-            float Nn, D;
-            int M;
-            best_over_controls<float, false>(g, 3, i, j, uk, c, bx, by, 0, 1, C, U, Nn, D, M);
-            const float du = Nn / D;
-            su[k] = uk + du;
-            lmax = fmaxf(lmax, fabsf(du));
-        }
-        const float bm = block_max<float>(lmax, red);
-        if (tid == 0) s_inc = bm;
-        __syncthreads();
-        inc = s_inc;
-        if (inc <= tol) {
-            ++s;
-            break;
-        }
-    }
-    for (int k = tid; k < N; k += blockDim.x) uc[k] = su[k];
-    if (tid == 0) {
-        res->sweeps = (inc <= tol) ? s : -s;
-        res->increment = inc;
-    }
 }
 
 // u_hat: Q1 interpolation of u_c at the fine nodes (nested grids, ratio r).
@@ -376,27 +311,15 @@ __global__ void k_fix_nonfree(int N, const uint8_t* __restrict__ mask, float uob
 cudaError_t launch_coarse_data(int n, int nc, const float* speed, const float2* drift,
                                const uint8_t* mask, float* speed_c, float2* drift_c,
                                uint8_t* mask_c, cudaStream_t st) {
+    count_launches(1);
     k_coarse_data<<<blocks_for((long long)nc * nc), kThreads, 0, st>>>(n, nc, speed, drift, mask,
                                                                          speed_c, drift_c, mask_c);
     return cudaGetLastError();
 }
 
-size_t coarse_solve_smem(int nc, int na) {
-    return (((size_t)na * sizeof(float2) + 15) & ~(size_t)15) + (size_t)nc * nc * sizeof(float);
-}
-
-cudaError_t launch_coarse_solve(const GridView& gc, float u_start, float tol, int max_sweeps,
-                                float* uc, CoarseResult* res, cudaStream_t st) {
-    const size_t smem = coarse_solve_smem(gc.n, gc.na);
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    k_coarse_solve<<<1, 1024, smem, st>>>(gc, u_start, tol, max_sweeps, uc, res);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, float u_obst,
                           float* uhat, cudaStream_t st) {
+    count_launches(1);
     k_interp<<<blocks_for((long long)n * n), kThreads, 0, st>>>(nc, uc, n, mask, u_obst, uhat);
     return cudaGetLastError();
 }
@@ -404,6 +327,7 @@ cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, f
 cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda, float band_w,
                              int band_cap, uint8_t* a, int32_t* key, int* max_key, cudaStream_t st) {
     const size_t smem = (size_t)g.na * sizeof(float2);
+    count_launches(1);
     k_synthesis<<<blocks_for((long long)g.n * g.n), kThreads, smem, st>>>(g, uhat, lambda, band_w,
                                                                           band_cap, a, key, max_key);
     return cudaGetLastError();
@@ -412,12 +336,14 @@ cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda,
 cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, float lambda,
                                     float band_w, int band_cap, int32_t* key, int* max_key,
                                     cudaStream_t st) {
+    count_launches(1);
     k_keys_from_values<<<blocks_for(N), kThreads, 0, st>>>(N, mask, u, lambda, band_w, band_cap,
                                                              key, max_key);
     return cudaGetLastError();
 }
 
 cudaError_t launch_successors(const GridView& g, const uint8_t* a, int32_t* succ, cudaStream_t st) {
+    count_launches(1);
     k_successors<<<blocks_for((long long)g.n * g.n), kThreads, 0, st>>>(g, a, succ);
     return cudaGetLastError();
 }
@@ -432,9 +358,11 @@ cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const
     int32_t* bufs[2] = {jump_a, jump_b};
     for (int r = 0; r < rounds; ++r) {
         int32_t* out = bufs[r & 1];
+        count_launches(1);
         k_jump<<<blocks_for(N), kThreads, 0, st>>>(N, in, out);
         in = out;
     }
+    count_launches(1);
     k_label_from_end<<<blocks_for(N), kThreads, 0, st>>>(N, in, mask, sector, n_patches, label);
     return cudaGetLastError();
 }
@@ -446,34 +374,42 @@ cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const u
     const int nb = n_bands * stride;
     cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * (size_t)nb, st);
     if (e != cudaSuccess) return e;
+    count_launches(1);
     k_hist<<<blocks_for(N), kThreads, 0, st>>>(N, key, label, mask, stride, bin_count);
+    count_launches(1);
     k_scan<<<1, 1024, 0, st>>>(nb, bin_count, bin_off);
     // bin_count becomes the scatter cursor
     e = cudaMemcpyAsync(bin_count, bin_off, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
+    count_launches(1);
     k_scatter<<<blocks_for(N), kThreads, 0, st>>>(N, key, label, mask, stride, bin_count, order);
+    count_launches(1);
     k_band_off<<<blocks_for(n_bands + 1), kThreads, 0, st>>>(n_bands, stride, bin_off, band_off);
     return cudaGetLastError();
 }
 
 cudaError_t launch_promote(int N, const float* u32, double* u64, cudaStream_t st) {
+    count_launches(1);
     k_promote<<<blocks_for(N), kThreads, 0, st>>>(N, u32, u64);
     return cudaGetLastError();
 }
 
 cudaError_t launch_demote(int N, const double* u64, float* u32, cudaStream_t st) {
+    count_launches(1);
     k_demote<<<blocks_for(N), kThreads, 0, st>>>(N, u64, u32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_values(int N, const uint8_t* mask, float free_val, float uob, float* u32,
                                double* u64, double uob64, cudaStream_t st) {
+    count_launches(1);
     k_init_values<<<blocks_for(N), kThreads, 0, st>>>(N, mask, free_val, uob, u32, u64, uob64);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fix_nonfree(int N, const uint8_t* mask, float uob, double uob64, float* u32,
                                double* u64, cudaStream_t st) {
+    count_launches(1);
     k_fix_nonfree<<<blocks_for(N), kThreads, 0, st>>>(N, mask, uob, uob64, u32, u64);
     return cudaGetLastError();
 }

@@ -103,6 +103,7 @@ cudaError_t launch_sweep_impl(const GridView& g, int scheme, int R, const T* uin
     }
     dim3 block(kTileX, kBlockY);
     dim3 grid((g.n + kTileX - 1) / kTileX, (g.n + kTileY - 1) / kTileY);
+    count_launches(1);
     kern<<<grid, block, smem, st>>>(g, scheme, R, uin, uout, argmin, incmax);
     return cudaGetLastError();
 }

@@ -152,6 +152,7 @@ cudaError_t launch_impl(const WaveArgs& a, T* u, int blocks, cudaStream_t st) {
     using V2 = typename RealOf<T>::V2;
     const size_t smem = (size_t)a.g.na * sizeof(V2);
     void* args[] = {(void*)&a, (void*)&u};
+    count_launches(1);
     return cudaLaunchCooperativeKernel((const void*)k_waves<T, SIG>, dim3(blocks),
                                        dim3(kWaveThreads), args, smem, st);
 }
