@@ -255,6 +255,31 @@ int hjb_get_order(hjb_problem* p, int32_t* keys_out, int32_t* order_out,
 int hjb_device_info(hjb_problem* p, int32_t* num_sms, int32_t* wave_blocks32,
                     int32_t* wave_blocks64);
 
+/* hjb_residual_noalloc -- the FP64 sup-residual ||T2 u - u||_inf of hjb_residual,
+ * for a value field the caller holds, computed without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory where they need the residual -- a loop with a latency
+ * budget (cudaMalloc/cudaFree may synchronise the device) or a process whose device
+ * memory is wholly owned by another allocator (a caching pool, a fixed budget).
+ *   desc     : host; uses n, n_controls, h, lambda, sigma, cost (no coarse grid).
+ *   speed, mask, drift (nullable), u : DEVICE arrays with the layouts of
+ *              hjb_create_problem (u: double[n*n]); controls: DEVICE double[2*n_controls]
+ *              (16-byte aligned); residual_out: DEVICE double[1] (written by the call).
+ *   cuda_stream: the stream the work is queued on (NULL: the legacy default stream);
+ *              the call returns before the result is ready.
+ * Scratch: one partial maximum per 32x16-node tile, held in a fixed device array of
+ * 65536 doubles (512 KiB) that every GPU loading the library keeps until exit; grids
+ * with more tiles (n above 5760 in general) are rejected with HJB_ERR_INVALID_ARG.
+ * Every call overwrites the partials it reads, so nothing needs clearing, but all
+ * calls share the one array: calls whose work overlaps on the GPU race.  The first
+ * call on a device resolves the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: HJB_ERR_INVALID_ARG (NULL pointers, sizes, misalignment), HJB_ERR_CUDA. */
+int hjb_residual_noalloc(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                         const float* drift, const double* controls, const double* u,
+                         double* residual_out, void* cuda_stream);
+
 /* hjb_destroy -- frees every device buffer and the stream the library created.
  * NULL is ignored. */
 void hjb_destroy(hjb_problem* p);

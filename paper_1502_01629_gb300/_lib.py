@@ -89,6 +89,8 @@ _SIGNATURES = {
     "hjb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hjb_last_error": (ctypes.c_char_p, []),
     "hjb_kernel_launches": (ctypes.c_longlong, []),
+    "hjb_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc), _PTR, _PTR, _PTR, _PTR, _PTR, _PTR,
+                                            _PTR]),
 }
 
 _LIB = None
