@@ -77,11 +77,14 @@ typedef struct {
     double  band_width;   /* width of the causal bands in units of h (<= 0: 1.0)             */
     int32_t band_window;  /* passes > 0 revisit a group of bands if a group within this many
                              bands changed by more than the tolerance (<= 0: 8)               */
-    int32_t band_group;   /* consecutive bands per grid-wide wave (<= 0: 1)                   */
-    int32_t wave_warps;   /* warps of the band-wave kernel = nodes in flight; <= 0: every
-                             co-resident warp                                                  */
+    int32_t band_group;   /* band schedule: consecutive bands per grid-wide wave (<= 0: 1)    */
+    int32_t wave_warps;   /* band schedule: warps in flight (<= 0: every co-resident warp)    */
     int32_t resort_passes;/* after each of the first k FP32 passes, re-sort the free nodes by
                              the current value instead of u_hat (0: never)                    */
+    int32_t schedule;     /* patch-solve schedule: 0 tile-pipelined (default), 1 band waves   */
+    int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: 8)                   */
+    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 4)         */
+    int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
     int32_t reserved;     /* must be 0                                                        */
 } hjb_desc;
 
@@ -187,9 +190,15 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
 /* hjb_solve_patches -- Section 4.3 "Computation": from the current value (u_hat
  * after build_patches), iterate SLscheme3 (with sigma) in place on the single
  * shared array (sharp interfaces: the transmission condition is the identity),
- * visiting the bands in increasing order, band_group bands per grid-wide wave
- * (nodes of a wave taken in sorted order by the wave_warps warps in flight);
- * passes after the first skip groups whose neighbourhood did not change.  FP32 until a
+ * following the causal bands.  Schedule 0 (tile-pipelined): 16x16-node tiles
+ * staged in shared memory, each tile's nodes visited in band order, tiles grouped
+ * into waves by their lowest band and run on a cyclic schedule of period D (one
+ * grid-wide barrier per step); tiles whose neighbourhood did not change are
+ * skipped; converged when no tile visited in the last D steps changed by more
+ * than the tolerance ("passes" in the stats count pipeline steps).  Schedule 1
+ * (band waves): band_group bands per grid-wide wave, nodes taken in sorted order
+ * by the wave_warps warps in flight; passes after the first skip groups whose
+ * neighbourhood did not change.  FP32 until a
  * pass's sup-increment is <= tol32; then, if tol64 > 0, FP64 passes until the
  * FP64 sup-residual ||T2 u - u|| is <= tol64.  max_passes caps each phase.
  * ms_stage: [0] FP32 passes, [1] promotion + residuals, [2] FP64 passes.

@@ -30,7 +30,9 @@ class Desc(ctypes.Structure):
                 ("n_patches", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("band_width", ctypes.c_double), ("band_window", ctypes.c_int32),
                 ("band_group", ctypes.c_int32), ("wave_warps", ctypes.c_int32),
-                ("resort_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("resort_passes", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("tile_waves", ctypes.c_int32), ("tile_period", ctypes.c_int32),
+                ("local_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

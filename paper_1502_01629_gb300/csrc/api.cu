@@ -142,6 +142,22 @@ struct hjb_problem {
     int32_t* band_off = nullptr;
     unsigned int* inc_bits = nullptr;
     int n_bands = 0, n_free = 0, bins_cap = 0, bands_cap = 0;
+    // tile schedule
+    int ntx = 0, nt = 0, n_waves = 0, sched_cap = 0;
+    int32_t* tile_min = nullptr;
+    int32_t* tile_wave = nullptr;
+    int32_t* tile_key = nullptr;
+    int32_t* tile_list = nullptr;
+    unsigned int* tile_inc = nullptr;
+    int32_t* tile_key2 = nullptr;
+    int32_t* tile_nodes = nullptr;
+    int32_t* tile_bin_count = nullptr;
+    int32_t* tile_bin_off = nullptr;
+    int32_t* sched_count = nullptr;
+    int32_t* sched_off = nullptr;
+    int32_t* res_off = nullptr;
+    unsigned int* step_inc = nullptr;
+    int tile_blocks32 = 0, tile_blocks64 = 0;
     long long n_free_total = 0;   // free nodes of G
     bool coarse_done = false, built = false;
     // scratch
@@ -233,6 +249,7 @@ int validate_desc(const hjb_desc* d) {
     }
     if (!std::isfinite(d->band_width)) return fail(HJB_ERR_INVALID_ARG, "bad band_width");
     if (d->resort_passes < 0) return fail(HJB_ERR_INVALID_ARG, "resort_passes must be >= 0");
+    if (d->schedule != 0 && d->schedule != 1) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0 or 1");
     if (d->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "reserved field must be 0");
     return HJB_OK;
 }
@@ -315,6 +332,9 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
     if (p->desc.band_group <= 0) p->desc.band_group = 1;
+    if (p->desc.tile_waves <= 0) p->desc.tile_waves = 8;
+    if (p->desc.tile_period <= 1) p->desc.tile_period = 4;
+    if (p->desc.local_sweeps <= 0) p->desc.local_sweeps = 1;
     p->n = n;
     p->N = (int)N;
     p->na = na;
@@ -415,8 +435,24 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMalloc(&p->label, N));
         CUP(cudaMalloc(&p->key, N * sizeof(int32_t)));
         CUP(cudaMalloc(&p->order, N * sizeof(int32_t)));
+        p->ntx = (n + kTileSize - 1) / kTileSize;
+        p->nt = p->ntx * p->ntx;
+        const size_t nt = p->nt;
+        CUP(cudaMalloc(&p->tile_min, nt * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_wave, nt * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_key, nt * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_list, nt * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_inc, nt * sizeof(unsigned int)));
+        CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_bin_count, nt * kLocalBands * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->tile_bin_off, (nt * kLocalBands + 1) * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->res_off, (p->desc.tile_period + 1) * sizeof(int32_t)));
+        CUP(cudaMalloc(&p->step_inc, 2 * p->desc.tile_period * sizeof(unsigned int)));
     }
     const bool sig = p->sigma > 0.0;
+    p->tile_blocks32 = std::max(1, tile_blocks_per_sm(false, sig, na, p->halo)) * p->num_sms;
+    p->tile_blocks64 = std::max(1, tile_blocks_per_sm(true, sig, na, p->halo)) * p->num_sms;
     p->wave_blocks32 = std::max(1, wave_blocks_per_sm(false, sig, na)) * p->num_sms;
     p->wave_blocks64 = std::max(1, wave_blocks_per_sm(true, sig, na)) * p->num_sms;
     CUP(cudaStreamSynchronize(p->st));
@@ -590,6 +626,84 @@ int rebuild_order(hjb_problem* p) {
     return HJB_OK;
 }
 
+// Tile schedule from the band keys: nodes sorted by (tile, local band), tiles
+// grouped into waves by their lowest band and sorted by (wave mod D, wave).
+int build_tiles(hjb_problem* p) {
+    const int B = p->desc.tile_waves, D = p->desc.tile_period;
+    CU(cudaMemsetAsync(p->tile_min, 0x7f, sizeof(int32_t) * (size_t)p->nt, p->st));
+    CU(launch_tile_min(p->n, p->ntx, p->key, p->mask, p->tile_min, p->st));
+    CU(launch_tile_node_keys(p->n, p->ntx, p->key, p->mask, p->tile_min, p->tile_key2, p->st));
+    CU(launch_counting_sort(p->N, p->tile_key2, p->nt * kLocalBands, p->tile_bin_count,
+                            p->tile_bin_off, p->tile_nodes, p->st));
+    p->n_waves = (std::max(p->n_bands, 1) - 1) / B + 1;
+    const int bins = D * p->n_waves;
+    if (bins > p->sched_cap) {
+        dfree(p->sched_count);
+        dfree(p->sched_off);
+        CU(cudaMalloc(&p->sched_count, sizeof(int32_t) * (size_t)bins));
+        CU(cudaMalloc(&p->sched_off, sizeof(int32_t) * (size_t)(bins + 1)));
+        p->sched_cap = bins;
+    }
+    CU(launch_tile_waves(p->nt, p->tile_min, B, D, p->n_waves, p->tile_wave, p->tile_key,
+                         p->tile_inc, p->st));
+    CU(launch_counting_sort(p->nt, p->tile_key, bins, p->sched_count, p->sched_off, p->tile_list,
+                            p->st));
+    CU(launch_strided_gather(D, p->n_waves, p->sched_off, p->res_off, p->st));
+    return HJB_OK;
+}
+
+// Tile-pipelined passes on u32 (f64 = false) or u64 (f64 = true).
+int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out) {
+    Scalars* ds = dscal(p);
+    const int B = p->desc.tile_waves, D = p->desc.tile_period;
+    CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
+    CU(cudaMemsetAsync(&ds->sync, 0, sizeof(GridSync), p->st));
+    CU(cudaMemsetAsync(p->step_inc, 0, sizeof(unsigned int) * 2 * D, p->st));
+    // every tile with free nodes starts as changed
+    CU(launch_tile_waves(p->nt, p->tile_min, B, D, p->n_waves, p->tile_wave, p->tile_key,
+                         p->tile_inc, p->st));
+    TileArgs a{};
+    a.g = p->fine_view();
+    a.scheme = p->desc.scheme;
+    a.halo = p->halo;
+    a.nodes = p->tile_nodes;
+    a.bin_off = p->tile_bin_off;
+    a.tile_list = p->tile_list;
+    a.res_off = p->res_off;
+    a.tile_wave = p->tile_wave;
+    a.tile_inc = p->tile_inc;
+    a.step_inc = p->step_inc;
+    a.ntx = p->ntx;
+    a.nty = p->ntx;
+    a.n_waves = p->n_waves;
+    a.period = D;
+    a.local_sweeps = p->desc.local_sweeps;
+    a.max_steps = p->n_waves + max_passes * D;
+    a.tol = (float)tol;
+    a.sync = &ds->sync;
+    a.res = &ds->wave;
+    a.timeout_ns = kTimeoutNs;
+    const bool sig = p->sigma > 0.0;
+    if (f64) {
+        CU(launch_tiles_f64(a, p->u64, sig, p->tile_blocks64, p->st));
+    } else {
+        CU(launch_tiles_f32(a, p->u32, sig, p->tile_blocks32, p->st));
+    }
+    CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    *out = hscal(p)->wave;
+    if (hscal(p)->sync.err != 0)
+        return fail(hscal(p)->sync.err, "tile kernel: a grid-wide wait exceeded its limit");
+    return HJB_OK;
+}
+
+// One solve phase with the selected schedule.
+int run_phase(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out) {
+    return p->desc.schedule == 0 ? run_tiles(p, f64, tol, max_passes, out)
+                                 : run_waves(p, f64, tol, max_passes, out);
+}
+
 // Re-sort the free nodes by the current FP32 value (keys from u32, labels kept).
 int resort_by_value(hjb_problem* p) {
     Scalars* ds = dscal(p);
@@ -618,7 +732,7 @@ int resort_by_value(hjb_problem* p) {
     CU(cudaMemsetAsync(p->inc_bits, 0, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
     CU(launch_order(p->N, p->key, p->label, p->mask, p->np, p->n_bands, p->bin_count, p->bin_off,
                     p->order, p->band_off, p->st));
-    return HJB_OK;
+    return build_tiles(p);
 }
 
 }  // namespace
@@ -694,6 +808,10 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->uhat); dfree(p->a); dfree(p->succ); dfree(p->jump_a); dfree(p->jump_b);
     dfree(p->label); dfree(p->key); dfree(p->order); dfree(p->bin_count); dfree(p->bin_off);
     dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
+    dfree(p->tile_min); dfree(p->tile_wave); dfree(p->tile_key); dfree(p->tile_list);
+    dfree(p->tile_inc); dfree(p->tile_key2); dfree(p->tile_nodes); dfree(p->tile_bin_count);
+    dfree(p->tile_bin_off); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
+    dfree(p->step_inc);
     if (p->scratch) cudaFree(p->scratch);
     if (p->host_pinned) cudaFreeHost(p->host_pinned);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
@@ -758,6 +876,8 @@ int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
     tm.mark();
     p->n_bands = hscal(p)->max_key + 1;
     int rc = rebuild_order(p);
+    if (rc) return rc;
+    rc = build_tiles(p);
     if (rc) return rc;
     tm.mark();
     // the fine iteration starts from u_hat
@@ -825,7 +945,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         WaveResult w{};
         w.converged = 0;
         for (int r = 0; r < p->desc.resort_passes && done < max_passes && !w.converged; ++r) {
-            rc = run_waves(p, false, tol32, 1, &w);
+            rc = run_phase(p, false, tol32, 1, &w);
             if (rc) return rc;
             done += w.passes;
             nodes += w.nodes;
@@ -835,7 +955,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
             }
         }
         if (!w.converged && done < max_passes) {
-            rc = run_waves(p, false, tol32, max_passes - done, &w);
+            rc = run_phase(p, false, tol32, max_passes - done, &w);
             if (rc) return rc;
             done += w.passes;
             nodes += w.nodes;
@@ -866,7 +986,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         while (res > tol64 && passes64 < max_passes) {
             Timer t3(p->st);
             t3.mark();
-            r2 = run_waves(p, true, tol_pass, max_passes - passes64, &w64);
+            r2 = run_phase(p, true, tol_pass, max_passes - passes64, &w64);
             if (r2) return r2;
             t3.mark();
             passes64 += w64.passes;

@@ -49,6 +49,14 @@ cudaError_t launch_successors(const GridView& g, const uint8_t* a, int32_t* succ
 cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const int8_t* sector,
                           int n_patches, int32_t* jump_a, int32_t* jump_b, int8_t* label,
                           cudaStream_t st);
+// Counting sort of the indices k with key[k] >= 0 by key (nbins bins):
+// off[0..nbins] = bin offsets, order = indices grouped by bin (order inside a bin
+// is unspecified).  count is scratch of nbins entries.
+cudaError_t launch_counting_sort(int N, const int32_t* key, int nbins, int32_t* count,
+                                 int32_t* off, int32_t* order, cudaStream_t st);
+// out[b] = off[b * stride] for b = 0..nb (inclusive).
+cudaError_t launch_strided_gather(int nb, int stride, const int32_t* off, int32_t* out,
+                                  cudaStream_t st);
 cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const uint8_t* mask,
                          int n_patches, int n_bands, int32_t* bin_count, int32_t* bin_off,
                          int32_t* order, int32_t* band_off, cudaStream_t st);
@@ -92,5 +100,44 @@ cudaError_t launch_waves_f64(const WaveArgs& a, double* u, bool sig, int blocks,
 int wave_blocks_per_sm(bool f64, bool sig, int na);
 int wave_threads();
 size_t wave_smem(bool f64, int na);
+
+// ---------------------------------------------------------------- tiles.cu
+constexpr int kTileSize = 16;     // tile edge in nodes
+constexpr int kLocalBands = 64;   // band slots per tile (the last one takes the rest)
+
+struct TileArgs {
+    GridView g;
+    int scheme;
+    int halo;                  // cells staged around the tile
+    const int32_t* nodes;      // free nodes sorted by (tile, local band)
+    const int32_t* bin_off;    // n_tiles * kLocalBands + 1
+    const int32_t* tile_list;  // tiles sorted by (wave mod period, wave)
+    const int32_t* res_off;    // period + 1
+    const int32_t* tile_wave;  // wave of each tile
+    unsigned int* tile_inc;    // max increment of each tile's last visit (float bits)
+    unsigned int* step_inc;    // ring of 2 * period per-step maxima (float bits)
+    int ntx, nty;              // tiles per row / column
+    int n_waves;
+    int period;                // D
+    int local_sweeps;
+    int max_steps;
+    float tol;
+    GridSync* sync;
+    WaveResult* res;
+    unsigned long long timeout_ns;
+};
+
+size_t tile_smem(bool f64, int na, int halo);
+int tile_blocks_per_sm(bool f64, bool sig, int na, int halo);
+int tile_threads();
+cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
+cudaError_t launch_tiles_f64(const TileArgs& a, double* u, bool sig, int blocks, cudaStream_t st);
+cudaError_t launch_tile_min(int n, int ntx, const int32_t* key, const uint8_t* mask, int* tile_min,
+                            cudaStream_t st);
+cudaError_t launch_tile_node_keys(int n, int ntx, const int32_t* key, const uint8_t* mask,
+                                  const int* tile_min, int32_t* key2, cudaStream_t st);
+cudaError_t launch_tile_waves(int nt, const int* tile_min, int band_group, int D, int n_waves,
+                              int32_t* tile_wave, int32_t* tile_key, unsigned int* tile_inc,
+                              cudaStream_t st);
 
 }  // namespace hjb

@@ -271,6 +271,22 @@ __global__ void k_scatter(int N, const int32_t* __restrict__ key, const int8_t* 
     order[pos] = k;
 }
 
+__global__ void k_hist_key(int N, const int32_t* __restrict__ key, int32_t* count) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int b = key[k];
+    if (b >= 0) atomicAdd(&count[b], 1);
+}
+
+__global__ void k_scatter_key(int N, const int32_t* __restrict__ key, int32_t* cursor,
+                              int32_t* order) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int b = key[k];
+    if (b < 0) return;
+    order[atomicAdd(&cursor[b], 1)] = k;
+}
+
 __global__ void k_band_off(int n_bands, int stride, const int32_t* __restrict__ bin_off,
                            int32_t* band_off) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -385,6 +401,26 @@ cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const u
     k_scatter<<<blocks_for(N), kThreads, 0, st>>>(N, key, label, mask, stride, bin_count, order);
     count_launches(1);
     k_band_off<<<blocks_for(n_bands + 1), kThreads, 0, st>>>(n_bands, stride, bin_off, band_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counting_sort(int N, const int32_t* key, int nbins, int32_t* count,
+                                 int32_t* off, int32_t* order, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * (size_t)nbins, st);
+    if (e != cudaSuccess) return e;
+    count_launches(3);
+    k_hist_key<<<blocks_for(N), kThreads, 0, st>>>(N, key, count);
+    k_scan<<<1, 1024, 0, st>>>(nbins, count, off);
+    e = cudaMemcpyAsync(count, off, sizeof(int32_t) * (size_t)nbins, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_scatter_key<<<blocks_for(N), kThreads, 0, st>>>(N, key, count, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strided_gather(int nb, int stride, const int32_t* off, int32_t* out,
+                                  cudaStream_t st) {
+    count_launches(1);
+    k_band_off<<<blocks_for(nb + 1), kThreads, 0, st>>>(nb, stride, off, out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,304 @@
+// Tile-pipelined causal patch solve (Cacace & Falcone, Section 4.3
+// "Computation", with the ordering of Section 4.2).
+//
+// The grid is cut into 16x16-node tiles.  Inside a tile the free nodes are
+// visited in causal-band order (bands of T(u_hat), as in the band ordering of
+// the patches), one thread block per tile with the tile and a halo of u staged
+// in shared memory, so consecutive bands are separated only by __syncthreads.
+// Tiles are grouped into waves by their lowest band (wave q = floor(b_min / B))
+// and scheduled cyclically: at step s every wave q <= s with q = s (mod D) is
+// processed, then a grid-wide barrier.  Each tile is therefore visited once per
+// D steps, always right after the wave upwind of it, and a new ordered pass
+// enters the pipeline every D steps; about n_tiles / D tiles run per step.
+// A tile is skipped when neither it nor any of its 8 neighbours changed by more
+// than the tolerance at their last visit (a fast-marching-like active set).
+// The solve stops when no tile visited during the last D steps changed by more
+// than the tolerance.  All patches share one array (sharp interfaces), so the
+// transmission condition is the identity; values written by other blocks are
+// read through L2 (ld.global.cg).
+#include "hjb_kernels.h"
+
+namespace hjb {
+
+namespace {
+
+constexpr int kTS = kTileSize;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ float ld_l2(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_l2(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ void st_l2(float* p, float v) { __stcg(p, v); }
+__device__ __forceinline__ void st_l2(double* p, double v) { __stcg(p, v); }
+__device__ __forceinline__ float inc_to_float(float v) { return v; }
+__device__ __forceinline__ float inc_to_float(double v) { return __double2float_ru(v); }
+
+template <typename T, bool SIG>
+__global__ void __launch_bounds__(kThreads)
+k_tiles(TileArgs a, T* u) {
+    using V2 = typename RealOf<T>::V2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GridView& g = a.g;
+    const int n = g.n;
+    const int R = a.halo;
+    const int W = kTS + 2 * R;
+    V2* sctrl = reinterpret_cast<V2*>(smem);
+    const size_t ctrl_bytes = ((size_t)g.na * sizeof(V2) + 15) & ~(size_t)15;
+    int* soff = reinterpret_cast<int*>(smem + ctrl_bytes);                  // kLocalBands + 1
+    T* su = reinterpret_cast<T*>(smem + ctrl_bytes + (((kLocalBands + 1) * sizeof(int) + 15) & ~(size_t)15));
+    __shared__ float red[32];
+    __shared__ int s_flag;
+    __shared__ unsigned long long s_nodes;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const unsigned int nblocks = gridDim.x;
+    const unsigned int tol_bits = __float_as_uint(a.tol);
+    for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(g, m);
+    if (threadIdx.x == 0) s_nodes = 0ull;
+    __syncthreads();
+    auto C = [&](int m) { return sctrl[m]; };
+
+    const int D = a.period;
+    const int ring = 2 * D;
+    int step = 0;
+    int converged = 0;
+    float last_max = 0.0f;
+    bool ok = true;
+    for (step = 0; step < a.max_steps; ++step) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.step_inc[(step + 1) % ring] = 0u;
+        const int r = step % D;
+        const int lbeg = a.res_off[r];
+        const int lend = a.res_off[r + 1];
+        float bmax = 0.0f;
+        for (int idx = lbeg + (int)blockIdx.x; idx < lend; idx += gridDim.x) {
+            const int t = a.tile_list[idx];
+            if (a.tile_wave[t] > step) break;       // entries are sorted by wave
+            const int tcx = t % a.ntx, tcy = t / a.ntx;
+            // activity: this tile or a neighbour changed by more than tol at its last visit
+            if (threadIdx.x == 0) s_flag = 0;
+            __syncthreads();
+            if (threadIdx.x < 9) {
+                const int nx = tcx + (int)(threadIdx.x % 3) - 1;
+                const int ny = tcy + (int)(threadIdx.x / 3) - 1;
+                if (nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty &&
+                    __ldcg(a.tile_inc + ny * a.ntx + nx) > tol_bits)
+                    s_flag = 1;
+            }
+            __syncthreads();
+            if (!s_flag) continue;
+            // stage the tile + halo
+            const int gx0 = tcx * kTS - R, gy0 = tcy * kTS - R;
+            for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+                const int ey = e / W, ex = e - ey * W;
+                const int gx = min(max(gx0 + ex, 0), n - 1);
+                const int gy = min(max(gy0 + ey, 0), n - 1);
+                su[e] = ld_l2(u + (size_t)gy * n + gx);
+            }
+            for (int e = threadIdx.x; e <= kLocalBands; e += blockDim.x)
+                soff[e] = a.bin_off[(size_t)t * kLocalBands + e];
+            __syncthreads();
+            float tmax = 0.0f;
+            unsigned long long cnt = 0;
+            for (int sw = 0; sw < a.local_sweeps; ++sw) {
+                for (int lb = 0; lb < kLocalBands; ++lb) {
+                    const int b0 = soff[lb], b1 = soff[lb + 1];
+                    if (b0 == b1) continue;
+                    for (int q = b0 + warp; q < b1; q += kWarps) {
+                        const int k = a.nodes[q];
+                        const int i = k % n, j = k / n;
+                        const int lx = i - gx0, ly = j - gy0;
+                        T* base = su + ly * W + lx;
+                        const T uk = base[0];
+                        const T c = (T)g.speed[k];
+                        T bx = T(0), by = T(0);
+                        if (g.drift) {
+                            const float2 bb = g.drift[k];
+                            bx = (T)bb.x;
+                            by = (T)bb.y;
+                        }
+                        auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
+                        T N, Dn;
+                        int M;
+                        best_over_controls<T, SIG>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C, U,
+                                                   N, Dn, M);
+                        warp_argmin<T>(N, Dn, M);
+                        const T du = N / Dn;
+                        __syncwarp();
+                        if (lane == 0) {
+                            base[0] = uk + du;
+                            ++cnt;
+                        }
+                        tmax = fmaxf(tmax, inc_to_float(fabs(du)));
+                    }
+                    __syncthreads();
+                }
+            }
+            // write back the tile's free nodes
+            for (int e = threadIdx.x; e < kTS * kTS; e += blockDim.x) {
+                const int i = tcx * kTS + (e % kTS), j = tcy * kTS + (e / kTS);
+                if (i >= n || j >= n) continue;
+                const size_t k = (size_t)j * n + i;
+                if (g.mask[k] != kFree) continue;
+                st_l2(u + k, su[(j - gy0) * W + (i - gx0)]);
+            }
+            if (lane == 0 && cnt) atomicAdd(&s_nodes, cnt);
+            const float tm = block_max<float>(tmax, red);
+            if (threadIdx.x == 0) {
+                __stcg(a.tile_inc + t, __float_as_uint(tm));
+                bmax = fmaxf(bmax, tm);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && bmax > 0.0f) atomicMax(a.step_inc + step % ring, __float_as_uint(bmax));
+        ok = grid_sync(a.sync, nblocks, a.timeout_ns);
+        if (!ok) break;
+        // convergence: no tile visited in the last D steps (after every wave
+        // has been reached) changed by more than tol
+        if (step >= a.n_waves - 1 + D) {
+            if (threadIdx.x == 0) {
+                float m = 0.0f;
+                for (int d = 0; d < D; ++d)
+                    m = fmaxf(m, __uint_as_float(__ldcg(a.step_inc + (step - d) % ring)));
+                last_max = m;
+                s_flag = (m <= a.tol) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_flag) {
+                converged = 1;
+                ++step;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.res->nodes, s_nodes);
+        if (blockIdx.x == 0) {
+            a.res->passes = step;
+            a.res->converged = converged;
+            a.res->last_increment = last_max;
+        }
+    }
+}
+
+template <typename T, bool SIG>
+cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
+    const size_t smem = tile_smem(sizeof(T) == 8, a.g.na, a.halo);
+    auto kern = k_tiles<T, SIG>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {(void*)&a, (void*)&u};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kThreads), args, smem, st);
+}
+
+template <typename T, bool SIG>
+int blocks_per_sm_impl(int na, int halo) {
+    const size_t smem = tile_smem(sizeof(T) == 8, na, halo);
+    auto kern = k_tiles<T, SIG>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem);
+    return nb;
+}
+
+// ------------------------------------------------------------ schedule prep
+// lowest band of each tile's free nodes
+__global__ void k_tile_min(int n, int ntx, const int32_t* __restrict__ key,
+                           const uint8_t* __restrict__ mask, int* tile_min) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n * n || mask[k] != kFree) return;
+    const int i = (int)(k % n), j = (int)(k / n);
+    atomicMin(tile_min + (j / kTS) * ntx + (i / kTS), key[k]);
+}
+
+// bin of a free node: tile * kLocalBands + (band - tile's lowest band), capped
+__global__ void k_tile_node_keys(int n, int ntx, const int32_t* __restrict__ key,
+                                 const uint8_t* __restrict__ mask, const int* __restrict__ tile_min,
+                                 int32_t* key2) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n * n) return;
+    if (mask[k] != kFree) {
+        key2[k] = -1;
+        return;
+    }
+    const int i = (int)(k % n), j = (int)(k / n);
+    const int t = (j / kTS) * ntx + (i / kTS);
+    key2[k] = t * kLocalBands + min(key[k] - tile_min[t], kLocalBands - 1);
+}
+
+// wave of each tile and its bin in the cyclic schedule: (wave mod D) * n_waves + wave
+// (tile_inc starts "changed" for tiles with free nodes, "quiet" for the others)
+__global__ void k_tile_waves(int nt, const int* __restrict__ tile_min, int band_group, int D,
+                             int n_waves, int32_t* tile_wave, int32_t* tile_key,
+                             unsigned int* tile_inc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int bm = tile_min[t];
+    if (bm >= 0x7f7f7f7f) {          // no free node (tile_min keeps its fill value)
+        tile_wave[t] = 0x7fffffff;
+        tile_key[t] = -1;
+        tile_inc[t] = 0u;
+        return;
+    }
+    const int q = bm / band_group;
+    tile_wave[t] = q;
+    tile_key[t] = (q % D) * n_waves + q;
+    tile_inc[t] = 0x7f7fffffu;       // FLT_MAX: visit at least once
+}
+
+}  // namespace
+
+size_t tile_smem(bool f64, int na, int halo) {
+    const size_t v2 = f64 ? sizeof(double2) : sizeof(float2);
+    const size_t ctrl = ((size_t)na * v2 + 15) & ~(size_t)15;
+    const size_t off = (((size_t)kLocalBands + 1) * sizeof(int) + 15) & ~(size_t)15;
+    const size_t w = (size_t)(kTileSize + 2 * halo);
+    return ctrl + off + w * w * (f64 ? sizeof(double) : sizeof(float));
+}
+
+int tile_blocks_per_sm(bool f64, bool sig, int na, int halo) {
+    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo) : blocks_per_sm_impl<double, false>(na, halo);
+    return sig ? blocks_per_sm_impl<float, true>(na, halo) : blocks_per_sm_impl<float, false>(na, halo);
+}
+
+int tile_threads() { return kThreads; }
+
+cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st) {
+    return sig ? launch_impl<float, true>(a, u, blocks, st) : launch_impl<float, false>(a, u, blocks, st);
+}
+
+cudaError_t launch_tiles_f64(const TileArgs& a, double* u, bool sig, int blocks, cudaStream_t st) {
+    return sig ? launch_impl<double, true>(a, u, blocks, st) : launch_impl<double, false>(a, u, blocks, st);
+}
+
+cudaError_t launch_tile_min(int n, int ntx, const int32_t* key, const uint8_t* mask, int* tile_min,
+                            cudaStream_t st) {
+    const long long N = (long long)n * n;
+    count_launches(1);
+    k_tile_min<<<(int)((N + 255) / 256), 256, 0, st>>>(n, ntx, key, mask, tile_min);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_node_keys(int n, int ntx, const int32_t* key, const uint8_t* mask,
+                                  const int* tile_min, int32_t* key2, cudaStream_t st) {
+    const long long N = (long long)n * n;
+    count_launches(1);
+    k_tile_node_keys<<<(int)((N + 255) / 256), 256, 0, st>>>(n, ntx, key, mask, tile_min, key2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_waves(int nt, const int* tile_min, int band_group, int D, int n_waves,
+                              int32_t* tile_wave, int32_t* tile_key, unsigned int* tile_inc,
+                              cudaStream_t st) {
+    count_launches(1);
+    k_tile_waves<<<(nt + 255) / 256, 256, 0, st>>>(nt, tile_min, band_group, D, n_waves, tile_wave,
+                                                    tile_key, tile_inc);
+    return cudaGetLastError();
+}
+
+}  // namespace hjb
