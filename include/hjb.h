@@ -81,7 +81,8 @@ typedef struct {
     int32_t wave_warps;   /* band schedule: warps in flight (<= 0: every co-resident warp)    */
     int32_t resort_passes;/* after each of the first k FP32 passes, re-sort the free nodes by
                              the current value instead of u_hat (0: never)                    */
-    int32_t schedule;     /* patch-solve schedule: 0 tile-pipelined (default), 1 band waves   */
+    int32_t schedule;     /* patch-solve schedule: 0 warp tiles (default), 1 band waves,
+                             2 block tiles                                                    */
     int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: 8)                   */
     int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 4)         */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
@@ -190,12 +191,14 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
 /* hjb_solve_patches -- Section 4.3 "Computation": from the current value (u_hat
  * after build_patches), iterate SLscheme3 (with sigma) in place on the single
  * shared array (sharp interfaces: the transmission condition is the identity),
- * following the causal bands.  Schedule 0 (tile-pipelined): 16x16-node tiles
- * staged in shared memory, each tile's nodes visited in band order, tiles grouped
- * into waves by their lowest band and run on a cyclic schedule of period D (one
- * grid-wide barrier per step); tiles whose neighbourhood did not change are
- * skipped; converged when no tile visited in the last D steps changed by more
- * than the tolerance ("passes" in the stats count pipeline steps).  Schedule 1
+ * following the causal bands.  Schedules 0 and 2 (tile-pipelined): tiles staged
+ * in shared memory -- 0: one warp per 8x8 tile visiting the tile's nodes one by
+ * one in increasing u_hat; 2: one block per 16x16 tile visiting its bands in
+ * order -- tiles grouped into waves by their lowest band and run on a cyclic
+ * schedule of period D (one grid-wide barrier per step); tiles whose
+ * neighbourhood did not change are skipped; converged when no tile visited in
+ * the last D steps changed by more than the tolerance ("passes" in the stats
+ * count pipeline steps).  Schedule 1
  * (band waves): band_group bands per grid-wide wave, nodes taken in sorted order
  * by the wave_warps warps in flight; passes after the first skip groups whose
  * neighbourhood did not change.  FP32 until a

@@ -153,6 +153,8 @@ struct hjb_problem {
     int32_t* tile_nodes = nullptr;
     int32_t* tile_bin_count = nullptr;
     int32_t* tile_bin_off = nullptr;
+    int32_t* wt_nodes = nullptr;
+    int32_t* wt_count = nullptr;
     int32_t* sched_count = nullptr;
     int32_t* sched_off = nullptr;
     int32_t* res_off = nullptr;
@@ -249,7 +251,7 @@ int validate_desc(const hjb_desc* d) {
     }
     if (!std::isfinite(d->band_width)) return fail(HJB_ERR_INVALID_ARG, "bad band_width");
     if (d->resort_passes < 0) return fail(HJB_ERR_INVALID_ARG, "resort_passes must be >= 0");
-    if (d->schedule != 0 && d->schedule != 1) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0 or 1");
+    if (d->schedule < 0 || d->schedule > 2) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0, 1 or 2");
     if (d->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "reserved field must be 0");
     return HJB_OK;
 }
@@ -354,6 +356,13 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         delete p;
         return fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach);
     }
+    if (p->desc.schedule != 1 && p->desc.coarse_n > 0 &&
+        tile_smem(true, desc->n_controls, p->halo, p->desc.schedule == 0) > 200 * 1024) {
+        delete p;
+        return fail(HJB_ERR_INVALID_ARG,
+                    "interpolation reach %.1f cells is too large for the tile schedules "
+                    "(shared memory); use schedule 1", p->reach);
+    }
     auto bail = [&](int code) {
         hjb_destroy(p);
         return code;
@@ -435,7 +444,9 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMalloc(&p->label, N));
         CUP(cudaMalloc(&p->key, N * sizeof(int32_t)));
         CUP(cudaMalloc(&p->order, N * sizeof(int32_t)));
-        p->ntx = (n + kTileSize - 1) / kTileSize;
+        const bool warp_tiles = p->desc.schedule == 0;
+        const int ts = warp_tiles ? kWarpTile : kTileSize;
+        p->ntx = (n + ts - 1) / ts;
         p->nt = p->ntx * p->ntx;
         const size_t nt = p->nt;
         CUP(cudaMalloc(&p->tile_min, nt * sizeof(int32_t)));
@@ -443,16 +454,24 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMalloc(&p->tile_key, nt * sizeof(int32_t)));
         CUP(cudaMalloc(&p->tile_list, nt * sizeof(int32_t)));
         CUP(cudaMalloc(&p->tile_inc, nt * sizeof(unsigned int)));
-        CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_bin_count, nt * kLocalBands * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_bin_off, (nt * kLocalBands + 1) * sizeof(int32_t)));
+        if (warp_tiles) {
+            CUP(cudaMalloc(&p->wt_nodes, nt * kWarpTileNodes * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->wt_count, nt * sizeof(int32_t)));
+        } else {
+            CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->tile_bin_count, nt * kLocalBands * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->tile_bin_off, (nt * kLocalBands + 1) * sizeof(int32_t)));
+        }
         CUP(cudaMalloc(&p->res_off, (p->desc.tile_period + 1) * sizeof(int32_t)));
         CUP(cudaMalloc(&p->step_inc, 2 * p->desc.tile_period * sizeof(unsigned int)));
     }
     const bool sig = p->sigma > 0.0;
-    p->tile_blocks32 = std::max(1, tile_blocks_per_sm(false, sig, na, p->halo)) * p->num_sms;
-    p->tile_blocks64 = std::max(1, tile_blocks_per_sm(true, sig, na, p->halo)) * p->num_sms;
+    {
+        const bool wt = p->desc.schedule == 0;
+        p->tile_blocks32 = std::max(1, tile_blocks_per_sm(false, sig, na, p->halo, wt)) * p->num_sms;
+        p->tile_blocks64 = std::max(1, tile_blocks_per_sm(true, sig, na, p->halo, wt)) * p->num_sms;
+    }
     p->wave_blocks32 = std::max(1, wave_blocks_per_sm(false, sig, na)) * p->num_sms;
     p->wave_blocks64 = std::max(1, wave_blocks_per_sm(true, sig, na)) * p->num_sms;
     CUP(cudaStreamSynchronize(p->st));
@@ -628,13 +647,21 @@ int rebuild_order(hjb_problem* p) {
 
 // Tile schedule from the band keys: nodes sorted by (tile, local band), tiles
 // grouped into waves by their lowest band and sorted by (wave mod D, wave).
-int build_tiles(hjb_problem* p) {
+int build_tiles(hjb_problem* p, const float* key_val) {
+    if (p->desc.schedule == 1) return HJB_OK;     // band waves need no tiles
     const int B = p->desc.tile_waves, D = p->desc.tile_period;
-    CU(cudaMemsetAsync(p->tile_min, 0x7f, sizeof(int32_t) * (size_t)p->nt, p->st));
-    CU(launch_tile_min(p->n, p->ntx, p->key, p->mask, p->tile_min, p->st));
-    CU(launch_tile_node_keys(p->n, p->ntx, p->key, p->mask, p->tile_min, p->tile_key2, p->st));
-    CU(launch_counting_sort(p->N, p->tile_key2, p->nt * kLocalBands, p->tile_bin_count,
-                            p->tile_bin_off, p->tile_nodes, p->st));
+    if (p->desc.schedule == 0) {
+        // warp tiles: per-tile exact order by the key value (u_hat or current value)
+        CU(launch_wtile_build(p->n, p->ntx, p->nt, key_val, p->mask, (float)p->lambda,
+                              (float)(p->desc.band_width * p->h), kBandCap, p->wt_nodes,
+                              p->wt_count, p->tile_min, p->st));
+    } else {
+        CU(cudaMemsetAsync(p->tile_min, 0x7f, sizeof(int32_t) * (size_t)p->nt, p->st));
+        CU(launch_tile_min(p->n, p->ntx, p->key, p->mask, p->tile_min, p->st));
+        CU(launch_tile_node_keys(p->n, p->ntx, p->key, p->mask, p->tile_min, p->tile_key2, p->st));
+        CU(launch_counting_sort(p->N, p->tile_key2, p->nt * kLocalBands, p->tile_bin_count,
+                                p->tile_bin_off, p->tile_nodes, p->st));
+    }
     p->n_waves = (std::max(p->n_bands, 1) - 1) / B + 1;
     const int bins = D * p->n_waves;
     if (bins > p->sched_cap) {
@@ -666,8 +693,10 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.g = p->fine_view();
     a.scheme = p->desc.scheme;
     a.halo = p->halo;
-    a.nodes = p->tile_nodes;
+    a.warp_tiles = p->desc.schedule == 0 ? 1 : 0;
+    a.nodes = a.warp_tiles ? p->wt_nodes : p->tile_nodes;
     a.bin_off = p->tile_bin_off;
+    a.wt_count = p->wt_count;
     a.tile_list = p->tile_list;
     a.res_off = p->res_off;
     a.tile_wave = p->tile_wave;
@@ -700,8 +729,8 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
 
 // One solve phase with the selected schedule.
 int run_phase(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out) {
-    return p->desc.schedule == 0 ? run_tiles(p, f64, tol, max_passes, out)
-                                 : run_waves(p, f64, tol, max_passes, out);
+    return p->desc.schedule == 1 ? run_waves(p, f64, tol, max_passes, out)
+                                 : run_tiles(p, f64, tol, max_passes, out);
 }
 
 // Re-sort the free nodes by the current FP32 value (keys from u32, labels kept).
@@ -732,7 +761,7 @@ int resort_by_value(hjb_problem* p) {
     CU(cudaMemsetAsync(p->inc_bits, 0, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
     CU(launch_order(p->N, p->key, p->label, p->mask, p->np, p->n_bands, p->bin_count, p->bin_off,
                     p->order, p->band_off, p->st));
-    return build_tiles(p);
+    return build_tiles(p, p->u32);
 }
 
 }  // namespace
@@ -810,7 +839,7 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
     dfree(p->tile_min); dfree(p->tile_wave); dfree(p->tile_key); dfree(p->tile_list);
     dfree(p->tile_inc); dfree(p->tile_key2); dfree(p->tile_nodes); dfree(p->tile_bin_count);
-    dfree(p->tile_bin_off); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
+    dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
     dfree(p->step_inc);
     if (p->scratch) cudaFree(p->scratch);
     if (p->host_pinned) cudaFreeHost(p->host_pinned);
@@ -877,7 +906,7 @@ int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
     p->n_bands = hscal(p)->max_key + 1;
     int rc = rebuild_order(p);
     if (rc) return rc;
-    rc = build_tiles(p);
+    rc = build_tiles(p, p->uhat);
     if (rc) return rc;
     tm.mark();
     // the fine iteration starts from u_hat

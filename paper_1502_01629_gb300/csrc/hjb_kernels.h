@@ -102,15 +102,20 @@ int wave_threads();
 size_t wave_smem(bool f64, int na);
 
 // ---------------------------------------------------------------- tiles.cu
-constexpr int kTileSize = 16;     // tile edge in nodes
-constexpr int kLocalBands = 64;   // band slots per tile (the last one takes the rest)
+constexpr int kTileSize = 16;     // tile edge in nodes (block tiles)
+constexpr int kLocalBands = 64;   // band slots per block tile (the last one takes the rest)
+constexpr int kWarpTile = 8;      // tile edge in nodes (warp tiles)
+constexpr int kWarpTileNodes = kWarpTile * kWarpTile;
 
 struct TileArgs {
     GridView g;
     int scheme;
     int halo;                  // cells staged around the tile
-    const int32_t* nodes;      // free nodes sorted by (tile, local band)
-    const int32_t* bin_off;    // n_tiles * kLocalBands + 1
+    int warp_tiles;            // 1: one warp per 8x8 tile, 0: one block per 16x16 tile
+    const int32_t* nodes;      // block tiles: free nodes sorted by (tile, local band);
+                               // warp tiles: 64 slots per tile, sorted by u_hat
+    const int32_t* bin_off;    // block tiles: n_tiles * kLocalBands + 1
+    const int32_t* wt_count;   // warp tiles: free nodes per tile
     const int32_t* tile_list;  // tiles sorted by (wave mod period, wave)
     const int32_t* res_off;    // period + 1
     const int32_t* tile_wave;  // wave of each tile
@@ -127,8 +132,11 @@ struct TileArgs {
     unsigned long long timeout_ns;
 };
 
-size_t tile_smem(bool f64, int na, int halo);
-int tile_blocks_per_sm(bool f64, bool sig, int na, int halo);
+size_t tile_smem(bool f64, int na, int halo, bool warp_tiles);
+int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, bool warp_tiles);
+cudaError_t launch_wtile_build(int n, int ntx, int nt, const float* key_val, const uint8_t* mask,
+                               float lambda, float band_w, int band_cap, int32_t* nodes,
+                               int32_t* count, int* tile_min, cudaStream_t st);
 int tile_threads();
 cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
 cudaError_t launch_tiles_f64(const TileArgs& a, double* u, bool sig, int blocks, cudaStream_t st);

@@ -182,10 +182,249 @@ k_tiles(TileArgs a, T* u) {
     }
 }
 
+// ------------------------------------------------- one warp per 8x8 tile
+// Each warp owns one tile per visit: it stages the tile and its halo in its own
+// slice of shared memory and updates the tile's free nodes one after another in
+// increasing u_hat (the Gauss-Seidel order of Section 4.2 restricted to the
+// tile), its lanes spread over the controls.  Warps never wait for each other
+// inside a step.
+template <typename T, bool SIG>
+__global__ void __launch_bounds__(kThreads)
+k_wtiles(TileArgs a, T* u) {
+    using V2 = typename RealOf<T>::V2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GridView& g = a.g;
+    const int n = g.n;
+    const int R = a.halo;
+    const int W = kWarpTile + 2 * R;
+    V2* sctrl = reinterpret_cast<V2*>(smem);
+    const size_t ctrl_bytes = ((size_t)g.na * sizeof(V2) + 15) & ~(size_t)15;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T* su = reinterpret_cast<T*>(smem + ctrl_bytes) + (size_t)warp * W * W;
+    __shared__ float red[32];
+    __shared__ int s_flag;
+    __shared__ unsigned long long s_nodes;
+
+    const unsigned int nblocks = gridDim.x;
+    const unsigned int tol_bits = __float_as_uint(a.tol);
+    const int gw = blockIdx.x * kWarps + warp;
+    const int nw = gridDim.x * kWarps;
+    for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(g, m);
+    if (threadIdx.x == 0) s_nodes = 0ull;
+    __syncthreads();
+    auto C = [&](int m) { return sctrl[m]; };
+
+    const int D = a.period;
+    const int ring = 2 * D;
+    int step = 0;
+    int converged = 0;
+    float last_max = 0.0f;
+    bool ok = true;
+    unsigned long long cnt = 0;
+    for (step = 0; step < a.max_steps; ++step) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.step_inc[(step + 1) % ring] = 0u;
+        const int r = step % D;
+        const int lbeg = a.res_off[r];
+        const int lend = a.res_off[r + 1];
+        float wmax = 0.0f;
+        for (int idx = lbeg + gw; idx < lend; idx += nw) {
+            const int t = a.tile_list[idx];
+            if (a.tile_wave[t] > step) break;       // entries are sorted by wave
+            const int tcx = t % a.ntx, tcy = t / a.ntx;
+            bool act = false;
+            if (lane < 9) {
+                const int nx = tcx + lane % 3 - 1, ny = tcy + lane / 3 - 1;
+                act = nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty &&
+                      __ldcg(a.tile_inc + ny * a.ntx + nx) > tol_bits;
+            }
+            if (!__any_sync(0xffffffffu, act)) continue;
+            const int gx0 = tcx * kWarpTile - R, gy0 = tcy * kWarpTile - R;
+            for (int e = lane; e < W * W; e += 32) {
+                const int ey = e / W, ex = e - ey * W;
+                const int gx = min(max(gx0 + ex, 0), n - 1);
+                const int gy = min(max(gy0 + ey, 0), n - 1);
+                su[e] = ld_l2(u + (size_t)gy * n + gx);
+            }
+            const int nn = a.wt_count[t];
+            const int* tn = a.nodes + (size_t)t * kWarpTileNodes;
+            const int k0 = lane < nn ? tn[lane] : 0;
+            const int k1 = lane + 32 < nn ? tn[lane + 32] : 0;
+            const float c0 = lane < nn ? g.speed[k0] : 0.0f;
+            const float c1 = lane + 32 < nn ? g.speed[k1] : 0.0f;
+            __syncwarp();
+            float tmax = 0.0f;
+            for (int sw = 0; sw < a.local_sweeps; ++sw) {
+                for (int q = 0; q < nn; ++q) {
+                    const int k = __shfl_sync(0xffffffffu, q < 32 ? k0 : k1, q & 31);
+                    const T c = (T)__shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
+                    const int i = k % n, j = k / n;
+                    T* base = su + (j - gy0) * W + (i - gx0);
+                    const T uk = base[0];
+                    T bx = T(0), by = T(0);
+                    if (g.drift) {
+                        const float2 bb = g.drift[k];
+                        bx = (T)bb.x;
+                        by = (T)bb.y;
+                    }
+                    auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
+                    T N, Dn;
+                    int M;
+                    best_over_controls<T, SIG>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C, U, N,
+                                               Dn, M);
+                    warp_argmin<T>(N, Dn, M);
+                    const T du = N / Dn;
+                    if (lane == 0) base[0] = uk + du;
+                    __syncwarp();
+                    tmax = fmaxf(tmax, inc_to_float(fabs(du)));
+                }
+            }
+            // write back this tile's free nodes
+            if (lane < nn) {
+                const int i = k0 % n, j = k0 / n;
+                st_l2(u + k0, su[(j - gy0) * W + (i - gx0)]);
+            }
+            if (lane + 32 < nn) {
+                const int i = k1 % n, j = k1 / n;
+                st_l2(u + k1, su[(j - gy0) * W + (i - gx0)]);
+            }
+            if (lane == 0) {
+                __stcg(a.tile_inc + t, __float_as_uint(tmax));
+                cnt += (unsigned long long)nn * a.local_sweeps;
+            }
+            wmax = fmaxf(wmax, tmax);
+            __syncwarp();
+        }
+        const float bm = block_max<float>(wmax, red);
+        if (threadIdx.x == 0 && bm > 0.0f) atomicMax(a.step_inc + step % ring, __float_as_uint(bm));
+        ok = grid_sync(a.sync, nblocks, a.timeout_ns);
+        if (!ok) break;
+        if (step >= a.n_waves - 1 + D) {
+            if (threadIdx.x == 0) {
+                float m = 0.0f;
+                for (int d = 0; d < D; ++d)
+                    m = fmaxf(m, __uint_as_float(__ldcg(a.step_inc + (step - d) % ring)));
+                last_max = m;
+                s_flag = (m <= a.tol) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_flag) {
+                converged = 1;
+                ++step;
+                break;
+            }
+        }
+    }
+    if (lane == 0 && cnt) atomicAdd(&s_nodes, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.res->nodes, s_nodes);
+        if (blockIdx.x == 0) {
+            a.res->passes = step;
+            a.res->converged = converged;
+            a.res->last_increment = last_max;
+        }
+    }
+}
+
+// Build of the 8x8 warp tiles: one warp per tile gathers the tile's free nodes,
+// sorts them by the key (u_hat, or the current value when re-sorting) with a
+// 64-element bitonic sort held two per lane, writes them to slots
+// t*64 .. t*64+count-1, and records the band of the smallest key (the tile's wave
+// is derived from it).
+__global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ key_val,
+                              const uint8_t* __restrict__ mask, float lambda, float band_w,
+                              int band_cap, int32_t* nodes, int32_t* count, int* tile_min) {
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;
+    const int tcx = t % ntx, tcy = t / ntx;
+    // lane holds tile cells lane and lane + 32 (row-major 8x8)
+    float kv[2];
+    int kn[2];
+    for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        const int i = tcx * kWarpTile + (e & 7), j = tcy * kWarpTile + (e >> 3);
+        kv[h] = INFINITY;
+        kn[h] = -1;
+        if (i < n && j < n) {
+            const int k = j * n + i;
+            if (mask[k] == kFree) {
+                kv[h] = key_val[k];
+                kn[h] = k;
+            }
+        }
+    }
+    // bitonic sort of 64 (key, node) pairs; element e = lane + 32*h
+    for (int size = 2; size <= 64; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int h = 0; h < 2; ++h) {
+                const int e = lane + 32 * h;
+                const int partner = e ^ stride;
+                float pv;
+                int pn;
+                if (stride == 32) {
+                    pv = kv[1 - h];
+                    pn = kn[1 - h];
+                } else {
+                    pv = __shfl_xor_sync(0xffffffffu, kv[h], stride);
+                    pn = __shfl_xor_sync(0xffffffffu, kn[h], stride);
+                }
+                const bool up = ((e & size) == 0);
+                const bool lower = e < partner;
+                // keep the smaller in the lower slot for an ascending block
+                const bool mine_first = (kv[h] < pv) || (kv[h] == pv && kn[h] <= pn);
+                const bool keep_mine = (lower == up) ? mine_first : !mine_first;
+                if (stride == 32) {
+                    // both halves of the lane exchange at once below
+                } else if (!keep_mine) {
+                    kv[h] = pv;
+                    kn[h] = pn;
+                }
+            }
+            if (stride == 32) {
+                // element e (h=0) pairs with e+32 (h=1) in the same lane
+                const bool up = ((lane & size) == 0);
+                const bool first_le = (kv[0] < kv[1]) || (kv[0] == kv[1] && kn[0] <= kn[1]);
+                if (up != first_le) {
+                    const float tv = kv[0];
+                    kv[0] = kv[1];
+                    kv[1] = tv;
+                    const int tn = kn[0];
+                    kn[0] = kn[1];
+                    kn[1] = tn;
+                }
+            }
+        }
+    }
+    const unsigned m0 = __ballot_sync(0xffffffffu, kn[0] >= 0);
+    const unsigned m1 = __ballot_sync(0xffffffffu, kn[1] >= 0);
+    const int cnt = __popc(m0) + __popc(m1);
+    // empty slots (INFINITY) sort last, so the first cnt elements are the nodes
+    if (lane < cnt) nodes[(size_t)t * kWarpTileNodes + lane] = kn[0];
+    if (lane + 32 < cnt) nodes[(size_t)t * kWarpTileNodes + lane + 32] = kn[1];
+    if (lane == 0) {
+        count[t] = cnt;
+        int bm = 0x7f7f7f7f;
+        if (cnt > 0) {
+            const float v = fmaxf(kv[0], 0.0f);
+            float T;
+            if (lambda > 0.0f) {
+                const float lu = fminf(lambda * v, 1.0f - 1e-6f);
+                T = -log1pf(-lu) / lambda;
+            } else {
+                T = v;
+            }
+            bm = min((int)floorf(T / band_w), band_cap - 1);
+        }
+        tile_min[t] = bm;
+    }
+}
+
 template <typename T, bool SIG>
 cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
-    const size_t smem = tile_smem(sizeof(T) == 8, a.g.na, a.halo);
-    auto kern = k_tiles<T, SIG>;
+    const size_t smem = tile_smem(sizeof(T) == 8, a.g.na, a.halo, a.warp_tiles);
+    auto kern = a.warp_tiles ? k_wtiles<T, SIG> : k_tiles<T, SIG>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -196,9 +435,9 @@ cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
 }
 
 template <typename T, bool SIG>
-int blocks_per_sm_impl(int na, int halo) {
-    const size_t smem = tile_smem(sizeof(T) == 8, na, halo);
-    auto kern = k_tiles<T, SIG>;
+int blocks_per_sm_impl(int na, int halo, bool warp_tiles) {
+    const size_t smem = tile_smem(sizeof(T) == 8, na, halo, warp_tiles);
+    auto kern = warp_tiles ? k_wtiles<T, SIG> : k_tiles<T, SIG>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
@@ -253,17 +492,35 @@ __global__ void k_tile_waves(int nt, const int* __restrict__ tile_min, int band_
 
 }  // namespace
 
-size_t tile_smem(bool f64, int na, int halo) {
+size_t tile_smem(bool f64, int na, int halo, bool warp_tiles) {
     const size_t v2 = f64 ? sizeof(double2) : sizeof(float2);
     const size_t ctrl = ((size_t)na * v2 + 15) & ~(size_t)15;
+    const size_t rs = f64 ? sizeof(double) : sizeof(float);
+    if (warp_tiles) {
+        const size_t w = (size_t)(kWarpTile + 2 * halo);
+        return ctrl + (size_t)kWarps * w * w * rs;
+    }
     const size_t off = (((size_t)kLocalBands + 1) * sizeof(int) + 15) & ~(size_t)15;
     const size_t w = (size_t)(kTileSize + 2 * halo);
-    return ctrl + off + w * w * (f64 ? sizeof(double) : sizeof(float));
+    return ctrl + off + w * w * rs;
 }
 
-int tile_blocks_per_sm(bool f64, bool sig, int na, int halo) {
-    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo) : blocks_per_sm_impl<double, false>(na, halo);
-    return sig ? blocks_per_sm_impl<float, true>(na, halo) : blocks_per_sm_impl<float, false>(na, halo);
+int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, bool warp_tiles) {
+    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo, warp_tiles)
+                        : blocks_per_sm_impl<double, false>(na, halo, warp_tiles);
+    return sig ? blocks_per_sm_impl<float, true>(na, halo, warp_tiles)
+               : blocks_per_sm_impl<float, false>(na, halo, warp_tiles);
+}
+
+cudaError_t launch_wtile_build(int n, int ntx, int nt, const float* key_val, const uint8_t* mask,
+                               float lambda, float band_w, int band_cap, int32_t* nodes,
+                               int32_t* count, int* tile_min, cudaStream_t st) {
+    count_launches(1);
+    const long long threads = (long long)nt * 32;
+    k_wtile_build<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, lambda,
+                                                                 band_w, band_cap, nodes, count,
+                                                                 tile_min);
+    return cudaGetLastError();
 }
 
 int tile_threads() { return kThreads; }
