@@ -83,8 +83,8 @@ typedef struct {
                              the current value instead of u_hat (0: never)                    */
     int32_t schedule;     /* patch-solve schedule: 0 warp tiles (default), 1 band waves,
                              2 block tiles                                                    */
-    int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: 8)                   */
-    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 4)         */
+    int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: 3)                   */
+    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 2)         */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
     int32_t reserved;     /* must be 0                                                        */
 } hjb_desc;

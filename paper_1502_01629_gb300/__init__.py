@@ -54,7 +54,7 @@ class Problem:
                  sigma: float = 0.0, cost: float = 1.0, coarse_n: int = 0, n_patches: int = 1,
                  scheme: int = 3, band_width: float = 1.0, band_window: int = 8,
                  band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
-                 schedule: int = 0, tile_waves: int = 8, tile_period: int = 4,
+                 schedule: int = 0, tile_waves: int = 3, tile_period: int = 2,
                  local_sweeps: int = 1,
                  drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False):
         self._h = None

@@ -54,10 +54,13 @@ template <> struct RealOf<double> {
 
 // One axis of a point's Q1 cell, relative to the node: the point sits at offset
 // `d` (grid units) from node index i.  The projection onto the square clamps the
-// absolute coordinate to [0, n-1]; the cell is floor(), capped at n-2 so that a
-// point on the last grid line uses the last cell with fraction 1.  Working with
-// the small offset keeps the fraction exact in FP32 at any grid size.
-// `sw` is the Q1 weight of node i along this axis (0 if i is not a vertex).
+// absolute coordinate to [0, n-1], i.e. the offset to [lo, hi] = [-i, n-1-i];
+// the cell is floor(), capped at hi - 1 so that a point on the last grid line
+// uses the last cell with fraction 1.  Working with the small offset keeps the
+// fraction exact in FP32 at any grid size.  `sw` is the Q1 weight of node i
+// along this axis: the hat function max(0, 1 - |d|) of the clamped offset (it
+// equals 1 - fr when the cell starts at the node, fr when it ends there, 0
+// otherwise).
 template <typename T>
 struct Axis {
     int off;
@@ -65,22 +68,33 @@ struct Axis {
     T sw;
 };
 
+// Clamp bounds of the offsets around one node, computed once per node.
 template <typename T>
-__device__ __forceinline__ Axis<T> axis_cell(T d, int i, int n) {
-    const T lo = (T)(-i);
-    const T hi = (T)(n - 1 - i);
+struct NodeBox {
+    T lox, hix, capx;   // capx = hix - 1
+    T loy, hiy, capy;
+};
+
+template <typename T>
+__device__ __forceinline__ NodeBox<T> node_box(int i, int j, int n) {
+    NodeBox<T> b;
+    b.lox = (T)(-i);
+    b.hix = (T)(n - 1 - i);
+    b.capx = b.hix - T(1);
+    b.loy = (T)(-j);
+    b.hiy = (T)(n - 1 - j);
+    b.capy = b.hiy - T(1);
+    return b;
+}
+
+template <typename T>
+__device__ __forceinline__ Axis<T> axis_cell(T d, T lo, T hi, T cap) {
     d = fmin(fmax(d, lo), hi);
-    T fl = floor(d);
-    int off = (int)fl;
-    const int cap = n - 2 - i;
-    if (off > cap) {
-        off = cap;
-        fl = (T)cap;
-    }
+    const T fl = fmin(floor(d), cap);
     Axis<T> a;
-    a.off = off;
+    a.off = (int)fl;
     a.fr = d - fl;
-    a.sw = (off == 0) ? (T(1) - a.fr) : ((off == -1) ? a.fr : T(0));
+    a.sw = fmax(T(1) - fabs(d), T(0));
     return a;
 }
 
@@ -104,25 +118,24 @@ __device__ __forceinline__ T bilinear_rel(const Axis<T>& ax, const Axis<T>& ay, 
 // L = (1/2d) sum_{k,s} lambda_{i0,k}^{a,s} (the self weight, Lambda0 of eq.
 // SLimplicit).  SIG = false: sigma = 0, the four points coincide with the foot.
 template <typename T, bool SIG, typename Acc>
-__device__ __forceinline__ void control_terms(const GridView& g, int i, int j, T fx, T fy, T uk,
-                                              const Acc& U, T& Sd, T& L) {
-    const int n = g.n;
+__device__ __forceinline__ void control_terms(const GridView& g, const NodeBox<T>& bx, T fx, T fy,
+                                              T uk, const Acc& U, T& Sd, T& L) {
     if (SIG) {
         const T d = RealOf<T>::d(g);
-        const Axis<T> xm = axis_cell<T>(fx - d, i, n);
-        const Axis<T> x0 = axis_cell<T>(fx, i, n);
-        const Axis<T> xp = axis_cell<T>(fx + d, i, n);
-        const Axis<T> ym = axis_cell<T>(fy - d, j, n);
-        const Axis<T> y0 = axis_cell<T>(fy, j, n);
-        const Axis<T> yp = axis_cell<T>(fy + d, j, n);
+        const Axis<T> xm = axis_cell<T>(fx - d, bx.lox, bx.hix, bx.capx);
+        const Axis<T> x0 = axis_cell<T>(fx, bx.lox, bx.hix, bx.capx);
+        const Axis<T> xp = axis_cell<T>(fx + d, bx.lox, bx.hix, bx.capx);
+        const Axis<T> ym = axis_cell<T>(fy - d, bx.loy, bx.hiy, bx.capy);
+        const Axis<T> y0 = axis_cell<T>(fy, bx.loy, bx.hiy, bx.capy);
+        const Axis<T> yp = axis_cell<T>(fy + d, bx.loy, bx.hiy, bx.capy);
         Sd = (bilinear_rel<T>(xp, y0, uk, U) + bilinear_rel<T>(xm, y0, uk, U)) +
              (bilinear_rel<T>(x0, yp, uk, U) + bilinear_rel<T>(x0, ym, uk, U));
         L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
         Sd *= T(0.25);
         L *= T(0.25);
     } else {
-        const Axis<T> x0 = axis_cell<T>(fx, i, n);
-        const Axis<T> y0 = axis_cell<T>(fy, j, n);
+        const Axis<T> x0 = axis_cell<T>(fx, bx.lox, bx.hix, bx.capx);
+        const Axis<T> y0 = axis_cell<T>(fy, bx.loy, bx.hiy, bx.capy);
         Sd = bilinear_rel<T>(x0, y0, uk, U);
         L = x0.sw * y0.sw;
     }
@@ -153,6 +166,7 @@ __device__ __forceinline__ void best_over_controls(const GridView& g, int scheme
     const T s = RealOf<T>::s(g);
     const T beta = RealOf<T>::beta(g);
     const T c0 = fma(-(T(1) - beta), uk, RealOf<T>::hl(g));
+    const NodeBox<T> box = node_box<T>(i, j, g.n);
     bestN = T(INFINITY);
     bestD = T(1);
     bestM = 0x7fffffff;
@@ -161,7 +175,7 @@ __device__ __forceinline__ void best_over_controls(const GridView& g, int scheme
         const T fx = s * fma(c, (T)a.x, bx);
         const T fy = s * fma(c, (T)a.y, by);
         T Sd, L;
-        control_terms<T, SIG>(g, i, j, fx, fy, uk, U, Sd, L);
+        control_terms<T, SIG>(g, box, fx, fy, uk, U, Sd, L);
         T N = fma(beta, Sd, c0);
         T D = T(1);
         if (scheme == 3) {
@@ -192,6 +206,26 @@ __device__ __forceinline__ void warp_argmin(T& N, T& D, int& M) {
             M = oM;
         }
     }
+}
+
+// Warp min of the candidates (FP32): each lane turns its best fraction into a
+// value N/D, the warp takes the min of the values with redux.sync on
+// order-preserving bit patterns, then the lowest control index among the lanes
+// holding that value.  Returns the min value (the increment); M gets its control.
+__device__ __forceinline__ unsigned int order_key(float v) {
+    const unsigned int b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_val(unsigned int k) {
+    return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+}
+__device__ __forceinline__ float warp_min_increment(float N, float D, int& M) {
+    const float v = (M == 0x7fffffff) ? INFINITY : __fdividef(N, D);
+    const unsigned int key = order_key(v);
+    const unsigned int kmin = __reduce_min_sync(0xffffffffu, key);
+    const unsigned int mc = (key == kmin) ? (unsigned int)M : 0xffffffffu;
+    M = (int)__reduce_min_sync(0xffffffffu, mc);
+    return order_val(kmin);
 }
 
 // ------------------------------------------------------------- reductions

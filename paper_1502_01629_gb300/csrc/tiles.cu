@@ -248,18 +248,23 @@ k_wtiles(TileArgs a, T* u) {
             }
             const int nn = a.wt_count[t];
             const int* tn = a.nodes + (size_t)t * kWarpTileNodes;
-            const int k0 = lane < nn ? tn[lane] : 0;
-            const int k1 = lane + 32 < nn ? tn[lane + 32] : 0;
+            // tile-local indices e (row-major 8x8) of the nodes, in visiting order
+            const int e0 = lane < nn ? tn[lane] : 0;
+            const int e1 = lane + 32 < nn ? tn[lane + 32] : 0;
+            const int bi = tcx * kWarpTile, bj = tcy * kWarpTile;
+            const int k0 = (bj + (e0 >> 3)) * n + bi + (e0 & 7);
+            const int k1 = (bj + (e1 >> 3)) * n + bi + (e1 & 7);
             const float c0 = lane < nn ? g.speed[k0] : 0.0f;
             const float c1 = lane + 32 < nn ? g.speed[k1] : 0.0f;
             __syncwarp();
             float tmax = 0.0f;
             for (int sw = 0; sw < a.local_sweeps; ++sw) {
                 for (int q = 0; q < nn; ++q) {
-                    const int k = __shfl_sync(0xffffffffu, q < 32 ? k0 : k1, q & 31);
+                    const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
                     const T c = (T)__shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
-                    const int i = k % n, j = k / n;
-                    T* base = su + (j - gy0) * W + (i - gx0);
+                    const int i = bi + (e & 7), j = bj + (e >> 3);
+                    const int k = j * n + i;
+                    T* base = su + (R + (e >> 3)) * W + (R + (e & 7));
                     const T uk = base[0];
                     T bx = T(0), by = T(0);
                     if (g.drift) {
@@ -272,22 +277,21 @@ k_wtiles(TileArgs a, T* u) {
                     int M;
                     best_over_controls<T, SIG>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C, U, N,
                                                Dn, M);
-                    warp_argmin<T>(N, Dn, M);
-                    const T du = N / Dn;
+                    T du;
+                    if constexpr (sizeof(T) == 4) {
+                        du = warp_min_increment(N, Dn, M);
+                    } else {
+                        warp_argmin<T>(N, Dn, M);
+                        du = N / Dn;
+                    }
                     if (lane == 0) base[0] = uk + du;
                     __syncwarp();
                     tmax = fmaxf(tmax, inc_to_float(fabs(du)));
                 }
             }
             // write back this tile's free nodes
-            if (lane < nn) {
-                const int i = k0 % n, j = k0 / n;
-                st_l2(u + k0, su[(j - gy0) * W + (i - gx0)]);
-            }
-            if (lane + 32 < nn) {
-                const int i = k1 % n, j = k1 / n;
-                st_l2(u + k1, su[(j - gy0) * W + (i - gx0)]);
-            }
+            if (lane < nn) st_l2(u + k0, su[(R + (e0 >> 3)) * W + (R + (e0 & 7))]);
+            if (lane + 32 < nn) st_l2(u + k1, su[(R + (e1 >> 3)) * W + (R + (e1 & 7))]);
             if (lane == 0) {
                 __stcg(a.tile_inc + t, __float_as_uint(tmax));
                 cnt += (unsigned long long)nn * a.local_sweeps;
@@ -401,8 +405,10 @@ __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ 
     const unsigned m1 = __ballot_sync(0xffffffffu, kn[1] >= 0);
     const int cnt = __popc(m0) + __popc(m1);
     // empty slots (INFINITY) sort last, so the first cnt elements are the nodes
-    if (lane < cnt) nodes[(size_t)t * kWarpTileNodes + lane] = kn[0];
-    if (lane + 32 < cnt) nodes[(size_t)t * kWarpTileNodes + lane + 32] = kn[1];
+    // store tile-local indices e = (j - 8 tcy) * 8 + (i - 8 tcx)
+    auto local = [&](int k) { return ((k / n) - tcy * kWarpTile) * kWarpTile + (k % n) - tcx * kWarpTile; };
+    if (lane < cnt) nodes[(size_t)t * kWarpTileNodes + lane] = local(kn[0]);
+    if (lane + 32 < cnt) nodes[(size_t)t * kWarpTileNodes + lane + 32] = local(kn[1]);
     if (lane == 0) {
         count[t] = cnt;
         int bm = 0x7f7f7f7f;
