@@ -42,7 +42,7 @@ N_FINE, N_COARSE, N_PATCH = 1025, 129, 16
 TOL32, TOL64, TOL_C = 5e-7, 1e-6, 1e-6
 METRIC = "time to 1e-6 residual vs plain GPU value iteration; node·control updates/s"
 UNIT = "node·control updates/s"
-SOLVER_KW = dict(schedule=0, tile_waves=3, tile_period=2, local_sweeps=1)
+SOLVER_KW = dict(schedule=0, tile_shape=-1, tile_waves=0, tile_period=2, local_sweeps=1)
 
 
 def flops_per_node_control(sigma: float) -> int:

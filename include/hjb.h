@@ -78,14 +78,18 @@ typedef struct {
     int32_t band_window;  /* passes > 0 revisit a group of bands if a group within this many
                              bands changed by more than the tolerance (<= 0: 8)               */
     int32_t band_group;   /* band schedule: consecutive bands per grid-wide wave (<= 0: 1)    */
-    int32_t wave_warps;   /* band schedule: warps in flight (<= 0: every co-resident warp)    */
+    int32_t wave_warps;   /* warps of the band-wave / tile kernels (<= 0: every co-resident
+                             warp)                                                             */
     int32_t resort_passes;/* after each of the first k FP32 passes, re-sort the free nodes by
                              the current value instead of u_hat (0: never)                    */
     int32_t schedule;     /* patch-solve schedule: 0 warp tiles (default), 1 band waves,
                              2 block tiles                                                    */
-    int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: 3)                   */
+    int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: automatic, 1 when the
+                             diffusion offset sqrt(2h) sigma exceeds one cell, else 2)        */
     int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 2)         */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
+    int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (4x4 when the
+                             diffusion offset exceeds one cell, else 8x4)                     */
     int32_t reserved;     /* must be 0                                                        */
 } hjb_desc;
 
@@ -192,8 +196,8 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
  * after build_patches), iterate SLscheme3 (with sigma) in place on the single
  * shared array (sharp interfaces: the transmission condition is the identity),
  * following the causal bands.  Schedules 0 and 2 (tile-pipelined): tiles staged
- * in shared memory -- 0: one warp per 8x8 tile visiting the tile's nodes one by
- * one in increasing u_hat; 2: one block per 16x16 tile visiting its bands in
+ * in shared memory -- 0: one warp per 8x8 (or tile_shape) tile visiting the
+ * tile's nodes one by one in increasing u_hat; 2: one block per 16x16 tile visiting its bands in
  * order -- tiles grouped into waves by their lowest band and run on a cyclic
  * schedule of period D (one grid-wide barrier per step); tiles whose
  * neighbourhood did not change are skipped; converged when no tile visited in

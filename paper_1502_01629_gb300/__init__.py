@@ -54,8 +54,8 @@ class Problem:
                  sigma: float = 0.0, cost: float = 1.0, coarse_n: int = 0, n_patches: int = 1,
                  scheme: int = 3, band_width: float = 1.0, band_window: int = 8,
                  band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
-                 schedule: int = 0, tile_waves: int = 3, tile_period: int = 2,
-                 local_sweeps: int = 1,
+                 schedule: int = 0, tile_waves: int = 0, tile_period: int = 2,
+                 local_sweeps: int = 1, tile_shape: int = -1,
                  drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False):
         self._h = None
         self.n = int(n)
@@ -72,6 +72,7 @@ class Problem:
         d.band_group, d.wave_warps, d.resort_passes = int(band_group), int(wave_warps), int(resort_passes)
         d.schedule, d.tile_waves, d.tile_period = int(schedule), int(tile_waves), int(tile_period)
         d.local_sweeps = int(local_sweeps)
+        d.tile_shape = int(tile_shape)
         self.desc = d
         st = None
         if stream is not None:

@@ -32,7 +32,8 @@ class Desc(ctypes.Structure):
                 ("band_group", ctypes.c_int32), ("wave_warps", ctypes.c_int32),
                 ("resort_passes", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("tile_waves", ctypes.c_int32), ("tile_period", ctypes.c_int32),
-                ("local_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("local_sweeps", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

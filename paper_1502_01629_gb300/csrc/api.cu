@@ -143,7 +143,9 @@ struct hjb_problem {
     unsigned int* inc_bits = nullptr;
     int n_bands = 0, n_free = 0, bins_cap = 0, bands_cap = 0;
     // tile schedule
-    int ntx = 0, nt = 0, n_waves = 0, sched_cap = 0;
+    int ntx = 0, nty = 0, nt = 0, n_waves = 0, sched_cap = 0;
+    int shape = 0;        // 0 block tiles 16x16; warp tiles 1: 8x8, 2: 8x4, 3: 4x4
+    int act_radius = 1;
     int32_t* tile_min = nullptr;
     int32_t* tile_wave = nullptr;
     int32_t* tile_key = nullptr;
@@ -252,6 +254,8 @@ int validate_desc(const hjb_desc* d) {
     if (!std::isfinite(d->band_width)) return fail(HJB_ERR_INVALID_ARG, "bad band_width");
     if (d->resort_passes < 0) return fail(HJB_ERR_INVALID_ARG, "resort_passes must be >= 0");
     if (d->schedule < 0 || d->schedule > 2) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0, 1 or 2");
+    if (d->tile_shape < -1 || d->tile_shape > 2)
+        return fail(HJB_ERR_INVALID_ARG, "tile_shape must be -1 (auto), 0 (8x8), 1 (8x4) or 2 (4x4)");
     if (d->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "reserved field must be 0");
     return HJB_OK;
 }
@@ -334,7 +338,17 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
     if (p->desc.band_group <= 0) p->desc.band_group = 1;
-    if (p->desc.tile_waves <= 0) p->desc.tile_waves = 3;
+    {
+        // automatic tile schedule: when the diffusion offset sqrt(2h) sigma reaches
+        // past one cell the scheme couples nodes of equal value (no upwind
+        // diffusion ball, Section 4.1) and smaller tiles in single-band waves are
+        // faster; otherwise 8x4 tiles in two-band waves (measured on the
+        // 1025^2 workload)
+        const double dcell = std::sqrt(2.0 * p->h) * p->sigma / p->dx;
+        const bool wide = dcell > 1.0;
+        if (p->desc.tile_shape < 0) p->desc.tile_shape = wide ? 2 : 1;
+        if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
+    }
     if (p->desc.tile_period <= 1) p->desc.tile_period = 2;
     if (p->desc.local_sweeps <= 0) p->desc.local_sweeps = 1;
     p->n = n;
@@ -356,8 +370,9 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         delete p;
         return fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach);
     }
+    p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
     if (p->desc.schedule != 1 && p->desc.coarse_n > 0 &&
-        tile_smem(true, desc->n_controls, p->halo, p->desc.schedule == 0) > 200 * 1024) {
+        tile_smem(true, desc->n_controls, p->halo, p->shape) > 200 * 1024) {
         delete p;
         return fail(HJB_ERR_INVALID_ARG,
                     "interpolation reach %.1f cells is too large for the tile schedules "
@@ -445,9 +460,12 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMalloc(&p->key, N * sizeof(int32_t)));
         CUP(cudaMalloc(&p->order, N * sizeof(int32_t)));
         const bool warp_tiles = p->desc.schedule == 0;
-        const int ts = warp_tiles ? kWarpTile : kTileSize;
-        p->ntx = (n + ts - 1) / ts;
-        p->nt = p->ntx * p->ntx;
+        int tw = kTileSize, th = kTileSize;
+        if (warp_tiles) wtile_dims(p->shape, &tw, &th);
+        p->ntx = (n + tw - 1) / tw;
+        p->nty = (n + th - 1) / th;
+        p->nt = p->ntx * p->nty;
+        p->act_radius = std::max(1, (p->halo + std::min(tw, th) - 1) / std::min(tw, th));
         const size_t nt = p->nt;
         CUP(cudaMalloc(&p->tile_min, nt * sizeof(int32_t)));
         CUP(cudaMalloc(&p->tile_wave, nt * sizeof(int32_t)));
@@ -468,9 +486,8 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     }
     const bool sig = p->sigma > 0.0;
     {
-        const bool wt = p->desc.schedule == 0;
-        p->tile_blocks32 = std::max(1, tile_blocks_per_sm(false, sig, na, p->halo, wt)) * p->num_sms;
-        p->tile_blocks64 = std::max(1, tile_blocks_per_sm(true, sig, na, p->halo, wt)) * p->num_sms;
+        p->tile_blocks32 = std::max(1, tile_blocks_per_sm(false, sig, na, p->halo, p->shape)) * p->num_sms;
+        p->tile_blocks64 = std::max(1, tile_blocks_per_sm(true, sig, na, p->halo, p->shape)) * p->num_sms;
     }
     p->wave_blocks32 = std::max(1, wave_blocks_per_sm(false, sig, na)) * p->num_sms;
     p->wave_blocks64 = std::max(1, wave_blocks_per_sm(true, sig, na)) * p->num_sms;
@@ -565,12 +582,23 @@ int jacobi64(hjb_problem* p, double* buf0, double* buf1, double tol, int max_swe
                                     });
 }
 
-// FP64 sup-residual ||T2 u - u|| of u64.
+// Screening margin of the FP64 residual.  With every value in [0, U]
+// (U = l/lambda + h l), an FP32 candidate differs from the FP64 one by at most
+// E <= 64 * 2^-24 * U (rounding of the values to FP32 and of about 25 FP32
+// operations on quantities <= 2U) + 2^-22 * reach * U (rounding of the foot
+// offset, times the largest value difference across a cell), which is below
+// 1e-5 U for a reach under 26 cells; the margin 2e-5 max(1, U) exceeds 2E.
+float screening_margin(const hjb_problem* p) {
+    const double U = std::max(1.0, p->uob);
+    return (float)(2e-5 * U);
+}
+
+// FP64 sup-residual ||T2 u - u|| of u64 (FP32-screened, exact FP64 value).
 int residual64(hjb_problem* p, double* out) {
     Scalars* ds = dscal(p);
     CU(cudaMemsetAsync(&ds->inc64, 0, sizeof(unsigned long long), p->st));
-    CU(launch_sweep_f64(p->fine_view(), p->sigma > 0.0, 2, p->halo, p->u64, nullptr, nullptr,
-                        &ds->inc64, p->st));
+    CU(launch_residual_screened(p->fine_view(), p->sigma > 0.0, p->halo, p->u64,
+                                screening_margin(p), &ds->inc64, p->st));
     unsigned long long bits = 0;
     CU(cudaMemcpyAsync(&hscal(p)->inc64, &ds->inc64, sizeof(bits), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
@@ -652,7 +680,7 @@ int build_tiles(hjb_problem* p, const float* key_val) {
     const int B = p->desc.tile_waves, D = p->desc.tile_period;
     if (p->desc.schedule == 0) {
         // warp tiles: per-tile exact order by the key value (u_hat or current value)
-        CU(launch_wtile_build(p->n, p->ntx, p->nt, key_val, p->mask, (float)p->lambda,
+        CU(launch_wtile_build(p->shape, p->n, p->ntx, p->nt, key_val, p->mask, (float)p->lambda,
                               (float)(p->desc.band_width * p->h), kBandCap, p->wt_nodes,
                               p->wt_count, p->tile_min, p->st));
     } else {
@@ -693,7 +721,8 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.g = p->fine_view();
     a.scheme = p->desc.scheme;
     a.halo = p->halo;
-    a.warp_tiles = p->desc.schedule == 0 ? 1 : 0;
+    a.warp_tiles = p->shape;
+    a.act_radius = p->act_radius;
     a.nodes = a.warp_tiles ? p->wt_nodes : p->tile_nodes;
     a.bin_off = p->tile_bin_off;
     a.wt_count = p->wt_count;
@@ -703,7 +732,7 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.tile_inc = p->tile_inc;
     a.step_inc = p->step_inc;
     a.ntx = p->ntx;
-    a.nty = p->ntx;
+    a.nty = p->nty;
     a.n_waves = p->n_waves;
     a.period = D;
     a.local_sweeps = p->desc.local_sweeps;
@@ -713,10 +742,15 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.res = &ds->wave;
     a.timeout_ns = kTimeoutNs;
     const bool sig = p->sigma > 0.0;
+    int blocks = f64 ? p->tile_blocks64 : p->tile_blocks32;
+    if (p->desc.wave_warps > 0) {
+        const int want = (p->desc.wave_warps + tile_threads() / 32 - 1) / (tile_threads() / 32);
+        blocks = std::max(1, std::min(blocks, want));
+    }
     if (f64) {
-        CU(launch_tiles_f64(a, p->u64, sig, p->tile_blocks64, p->st));
+        CU(launch_tiles_f64(a, p->u64, sig, blocks, p->st));
     } else {
-        CU(launch_tiles_f32(a, p->u32, sig, p->tile_blocks32, p->st));
+        CU(launch_tiles_f32(a, p->u32, sig, blocks, p->st));
     }
     CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
     CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));

@@ -193,6 +193,22 @@ __device__ __forceinline__ void best_over_controls(const GridView& g, int scheme
     }
 }
 
+// Argmin over the aligned group of LPN lanes (LPN = 32: the whole warp).
+template <typename T, int LPN>
+__device__ __forceinline__ void group_argmin(T& N, T& D, int& M) {
+#pragma unroll
+    for (int off = LPN / 2; off > 0; off >>= 1) {
+        const T oN = __shfl_xor_sync(0xffffffffu, N, off);
+        const T oD = __shfl_xor_sync(0xffffffffu, D, off);
+        const int oM = __shfl_xor_sync(0xffffffffu, M, off);
+        if (better<T>(oN, oD, oM, N, D, M)) {
+            N = oN;
+            D = oD;
+            M = oM;
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_argmin(T& N, T& D, int& M) {
 #pragma unroll
@@ -219,13 +235,16 @@ __device__ __forceinline__ unsigned int order_key(float v) {
 __device__ __forceinline__ float order_val(unsigned int k) {
     return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
 }
-__device__ __forceinline__ float warp_min_increment(float N, float D, int& M) {
+__device__ __forceinline__ float group_min_increment(float N, float D, int& M, unsigned int mask) {
     const float v = (M == 0x7fffffff) ? INFINITY : __fdividef(N, D);
     const unsigned int key = order_key(v);
-    const unsigned int kmin = __reduce_min_sync(0xffffffffu, key);
+    const unsigned int kmin = __reduce_min_sync(mask, key);
     const unsigned int mc = (key == kmin) ? (unsigned int)M : 0xffffffffu;
-    M = (int)__reduce_min_sync(0xffffffffu, mc);
+    M = (int)__reduce_min_sync(mask, mc);
     return order_val(kmin);
+}
+__device__ __forceinline__ float warp_min_increment(float N, float D, int& M) {
+    return group_min_increment(N, D, M, 0xffffffffu);
 }
 
 // ------------------------------------------------------------- reductions

@@ -28,6 +28,12 @@ cudaError_t launch_sweep_f64(const GridView& g, bool sig, int scheme, int halo, 
                              double* uout, int32_t* argmin, unsigned long long* incmax,
                              cudaStream_t st);
 
+// FP64 residual with exact FP32 screening of the controls (see sweep.cu);
+// margin must exceed twice the largest |FP32 - FP64| candidate difference.
+cudaError_t launch_residual_screened(const GridView& g, bool sig, int halo, const double* u,
+                                     float margin, unsigned long long* incmax, cudaStream_t st);
+size_t residual_screened_smem(int na, int R);
+
 // ------------------------------------------------------------ precompute.cu
 struct CoarseResult {
     int sweeps;
@@ -111,7 +117,8 @@ struct TileArgs {
     GridView g;
     int scheme;
     int halo;                  // cells staged around the tile
-    int warp_tiles;            // 1: one warp per 8x8 tile, 0: one block per 16x16 tile
+    int warp_tiles;            // tile shape: 0 block 16x16; warp tiles 1: 8x8, 2: 8x4, 3: 4x4
+    int act_radius;            // tiles around a tile whose change re-activates it
     const int32_t* nodes;      // block tiles: free nodes sorted by (tile, local band);
                                // warp tiles: 64 slots per tile, sorted by u_hat
     const int32_t* bin_off;    // block tiles: n_tiles * kLocalBands + 1
@@ -132,11 +139,12 @@ struct TileArgs {
     unsigned long long timeout_ns;
 };
 
-size_t tile_smem(bool f64, int na, int halo, bool warp_tiles);
-int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, bool warp_tiles);
-cudaError_t launch_wtile_build(int n, int ntx, int nt, const float* key_val, const uint8_t* mask,
-                               float lambda, float band_w, int band_cap, int32_t* nodes,
-                               int32_t* count, int* tile_min, cudaStream_t st);
+void wtile_dims(int shape, int* tw, int* th);
+size_t tile_smem(bool f64, int na, int halo, int shape);
+int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape);
+cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
+                               const uint8_t* mask, float lambda, float band_w, int band_cap,
+                               int32_t* nodes, int32_t* count, int* tile_min, cudaStream_t st);
 int tile_threads();
 cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
 cudaError_t launch_tiles_f64(const TileArgs& a, double* u, bool sig, int blocks, cudaStream_t st);

@@ -108,6 +108,108 @@ cudaError_t launch_sweep_impl(const GridView& g, int scheme, int R, const T* uin
     return cudaGetLastError();
 }
 
+// FP64 sup-residual ||T2 u - u|| (eq. SLscheme2) with exact FP32 screening.
+// Per node an FP32 pass finds the smallest candidate v32_min over the controls;
+// a control whose FP32 candidate exceeds v32_min by more than `margin` cannot be
+// the FP64 minimiser as long as |v32 - v64| <= margin / 2 for every control
+// (the host sizes the margin from the FP32 rounding of the values), so only
+// the remaining controls are evaluated in FP64.  The result is the FP64 min,
+// hence the same residual as the unscreened FP64 evaluation.
+template <bool SIG>
+__global__ void __launch_bounds__(kTileX * kBlockY)
+k_residual_screened(GridView g, int R, const double* __restrict__ u, float margin,
+                    unsigned long long* incmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double2* c64 = reinterpret_cast<double2*>(smem);
+    const size_t cb64 = ((size_t)g.na * sizeof(double2) + 15) & ~(size_t)15;
+    float2* c32 = reinterpret_cast<float2*>(smem + cb64);
+    const size_t cb32 = ((size_t)g.na * sizeof(float2) + 15) & ~(size_t)15;
+    const int n = g.n;
+    const int W = kTileX + 2 * R;
+    const int H = kTileY + 2 * R;
+    double* t64 = reinterpret_cast<double*>(smem + cb64 + cb32);
+    float* t32 = reinterpret_cast<float*>(t64 + (size_t)W * H);
+    __shared__ double red[32];
+    const int gx0 = blockIdx.x * kTileX - R;
+    const int gy0 = blockIdx.y * kTileY - R;
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    const int nthreads = kTileX * kBlockY;
+    for (int m = tid; m < g.na; m += nthreads) {
+        c64[m] = g.ctrl64[m];
+        c32[m] = g.ctrl32[m];
+    }
+    for (int t = tid; t < W * H; t += nthreads) {
+        const int ty = t / W;
+        const int tx = t - ty * W;
+        const int gx = min(max(gx0 + tx, 0), n - 1);
+        const int gy = min(max(gy0 + ty, 0), n - 1);
+        const double v = u[(size_t)gy * n + gx];
+        t64[t] = v;
+        t32[t] = (float)v;
+    }
+    __syncthreads();
+    double lmax = 0.0;
+#pragma unroll 1
+    for (int r = 0; r < kTileY / kBlockY; ++r) {
+        const int i = blockIdx.x * kTileX + threadIdx.x;
+        const int j = blockIdx.y * kTileY + threadIdx.y + r * kBlockY;
+        if (i >= n || j >= n) continue;
+        const size_t k = (size_t)j * n + i;
+        if (g.mask[k] != kFree) continue;
+        const int off = (j - gy0) * W + (i - gx0);
+        const float* b32 = t32 + off;
+        const double* b64 = t64 + off;
+        auto U32 = [&](int dx, int dy) { return b32[dy * W + dx]; };
+        auto U64 = [&](int dx, int dy) { return b64[dy * W + dx]; };
+        const float ck32 = g.speed[k];
+        float bx32 = 0.0f, by32 = 0.0f;
+        if (g.drift) {
+            const float2 b = g.drift[k];
+            bx32 = b.x;
+            by32 = b.y;
+        }
+        const float uk32 = b32[0];
+        const double uk64 = b64[0];
+        // FP32 screening pass
+        const float s32 = g.s32, beta32 = g.beta32;
+        const float c0_32 = fmaf(-(1.0f - beta32), uk32, g.hl32);
+        const NodeBox<float> box32 = node_box<float>(i, j, n);
+        float vmin = INFINITY;
+        for (int m = 0; m < g.na; ++m) {
+            const float2 a = c32[m];
+            const float fx = s32 * fmaf(ck32, a.x, bx32);
+            const float fy = s32 * fmaf(ck32, a.y, by32);
+            float Sd, L;
+            control_terms<float, SIG>(g, box32, fx, fy, uk32, U32, Sd, L);
+            vmin = fminf(vmin, fmaf(beta32, Sd, c0_32));
+        }
+        const float keep = vmin + margin;
+        // FP64 evaluation of the controls the screening cannot exclude
+        const double s64 = g.s64, beta64 = g.beta64;
+        const double c0_64 = fma(-(1.0 - beta64), uk64, g.hl64);
+        const NodeBox<double> box64 = node_box<double>(i, j, n);
+        const double ck64 = (double)ck32, bx64 = (double)bx32, by64 = (double)by32;
+        double best = INFINITY;
+        for (int m = 0; m < g.na; ++m) {
+            const float2 a = c32[m];
+            const float fx = s32 * fmaf(ck32, a.x, bx32);
+            const float fy = s32 * fmaf(ck32, a.y, by32);
+            float Sd, L;
+            control_terms<float, SIG>(g, box32, fx, fy, uk32, U32, Sd, L);
+            if (fmaf(beta32, Sd, c0_32) > keep) continue;
+            const double2 a64 = c64[m];
+            const double fx64 = s64 * fma(ck64, a64.x, bx64);
+            const double fy64 = s64 * fma(ck64, a64.y, by64);
+            double Sd64, L64;
+            control_terms<double, SIG>(g, box64, fx64, fy64, uk64, U64, Sd64, L64);
+            best = fmin(best, fma(beta64, Sd64, c0_64));
+        }
+        lmax = fmax(lmax, fabs(best));
+    }
+    const double bm = block_max<double>(lmax, red);
+    if (tid == 0) atomic_max_nonneg(incmax, bm);
+}
+
 }  // namespace
 
 // Every Q1 vertex of a point at offset d (|d| <= reach) from its node lies
@@ -115,6 +217,28 @@ cudaError_t launch_sweep_impl(const GridView& g, int scheme, int R, const T* uin
 // while the kernels form offsets in FP32, so a relative margin covers the FP32
 // rounding of the offset.
 int sweep_halo(double reach_cells) { return (int)std::floor(reach_cells * (1.0 + 1e-5) + 1e-5) + 1; }
+
+size_t residual_screened_smem(int na, int R) {
+    const size_t cb64 = ((size_t)na * sizeof(double2) + 15) & ~(size_t)15;
+    const size_t cb32 = ((size_t)na * sizeof(float2) + 15) & ~(size_t)15;
+    const size_t wh = (size_t)(kTileX + 2 * R) * (kTileY + 2 * R);
+    return cb64 + cb32 + wh * (sizeof(double) + sizeof(float));
+}
+
+cudaError_t launch_residual_screened(const GridView& g, bool sig, int halo, const double* u,
+                                     float margin, unsigned long long* incmax, cudaStream_t st) {
+    const size_t smem = residual_screened_smem(g.na, halo);
+    auto kern = sig ? k_residual_screened<true> : k_residual_screened<false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 block(kTileX, kBlockY);
+    dim3 grid((g.n + kTileX - 1) / kTileX, (g.n + kTileY - 1) / kTileY);
+    count_launches(1);
+    kern<<<grid, block, smem, st>>>(g, halo, u, margin, incmax);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sweep_f32(const GridView& g, bool sig, int scheme, int halo, const float* uin,
                              float* uout, int32_t* argmin, unsigned int* incmax, cudaStream_t st) {

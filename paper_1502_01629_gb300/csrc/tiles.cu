@@ -182,13 +182,15 @@ k_tiles(TileArgs a, T* u) {
     }
 }
 
-// ------------------------------------------------- one warp per 8x8 tile
+// ------------------------------------------------- one warp per TW x TH tile
 // Each warp owns one tile per visit: it stages the tile and its halo in its own
 // slice of shared memory and updates the tile's free nodes one after another in
 // increasing u_hat (the Gauss-Seidel order of Section 4.2 restricted to the
 // tile), its lanes spread over the controls.  Warps never wait for each other
-// inside a step.
-template <typename T, bool SIG>
+// inside a step.  A tile is visited only if some tile within `act_radius` tiles
+// (enough to cover the interpolation reach) changed by more than tol at its
+// last visit.
+template <typename T, bool SIG, int TW, int TH>
 __global__ void __launch_bounds__(kThreads)
 k_wtiles(TileArgs a, T* u) {
     using V2 = typename RealOf<T>::V2;
@@ -196,12 +198,13 @@ k_wtiles(TileArgs a, T* u) {
     const GridView& g = a.g;
     const int n = g.n;
     const int R = a.halo;
-    const int W = kWarpTile + 2 * R;
+    const int W = TW + 2 * R;
+    const int H = TH + 2 * R;
     V2* sctrl = reinterpret_cast<V2*>(smem);
     const size_t ctrl_bytes = ((size_t)g.na * sizeof(V2) + 15) & ~(size_t)15;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    T* su = reinterpret_cast<T*>(smem + ctrl_bytes) + (size_t)warp * W * W;
+    T* su = reinterpret_cast<T*>(smem + ctrl_bytes) + (size_t)warp * W * H;
     __shared__ float red[32];
     __shared__ int s_flag;
     __shared__ unsigned long long s_nodes;
@@ -210,6 +213,8 @@ k_wtiles(TileArgs a, T* u) {
     const unsigned int tol_bits = __float_as_uint(a.tol);
     const int gw = blockIdx.x * kWarps + warp;
     const int nw = gridDim.x * kWarps;
+    const int ar = a.act_radius;
+    const int aw = 2 * ar + 1;
     for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(g, m);
     if (threadIdx.x == 0) s_nodes = 0ull;
     __syncthreads();
@@ -233,14 +238,15 @@ k_wtiles(TileArgs a, T* u) {
             if (a.tile_wave[t] > step) break;       // entries are sorted by wave
             const int tcx = t % a.ntx, tcy = t / a.ntx;
             bool act = false;
-            if (lane < 9) {
-                const int nx = tcx + lane % 3 - 1, ny = tcy + lane / 3 - 1;
-                act = nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty &&
-                      __ldcg(a.tile_inc + ny * a.ntx + nx) > tol_bits;
+            for (int q = lane; q < aw * aw; q += 32) {
+                const int nx = tcx + q % aw - ar, ny = tcy + q / aw - ar;
+                act |= nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty &&
+                       __ldcg(a.tile_inc + ny * a.ntx + nx) > tol_bits;
             }
             if (!__any_sync(0xffffffffu, act)) continue;
-            const int gx0 = tcx * kWarpTile - R, gy0 = tcy * kWarpTile - R;
-            for (int e = lane; e < W * W; e += 32) {
+            const int bi = tcx * TW, bj = tcy * TH;
+            const int gx0 = bi - R, gy0 = bj - R;
+            for (int e = lane; e < W * H; e += 32) {
                 const int ey = e / W, ex = e - ey * W;
                 const int gx = min(max(gx0 + ex, 0), n - 1);
                 const int gy = min(max(gy0 + ey, 0), n - 1);
@@ -248,12 +254,11 @@ k_wtiles(TileArgs a, T* u) {
             }
             const int nn = a.wt_count[t];
             const int* tn = a.nodes + (size_t)t * kWarpTileNodes;
-            // tile-local indices e (row-major 8x8) of the nodes, in visiting order
+            // tile-local indices e (row-major TW x TH) of the nodes, in visiting order
             const int e0 = lane < nn ? tn[lane] : 0;
             const int e1 = lane + 32 < nn ? tn[lane + 32] : 0;
-            const int bi = tcx * kWarpTile, bj = tcy * kWarpTile;
-            const int k0 = (bj + (e0 >> 3)) * n + bi + (e0 & 7);
-            const int k1 = (bj + (e1 >> 3)) * n + bi + (e1 & 7);
+            const int k0 = (bj + e0 / TW) * n + bi + e0 % TW;
+            const int k1 = (bj + e1 / TW) * n + bi + e1 % TW;
             const float c0 = lane < nn ? g.speed[k0] : 0.0f;
             const float c1 = lane + 32 < nn ? g.speed[k1] : 0.0f;
             __syncwarp();
@@ -262,13 +267,13 @@ k_wtiles(TileArgs a, T* u) {
                 for (int q = 0; q < nn; ++q) {
                     const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
                     const T c = (T)__shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
-                    const int i = bi + (e & 7), j = bj + (e >> 3);
-                    const int k = j * n + i;
-                    T* base = su + (R + (e >> 3)) * W + (R + (e & 7));
+                    const int ex = e % TW, ey = e / TW;
+                    const int i = bi + ex, j = bj + ey;
+                    T* base = su + (R + ey) * W + (R + ex);
                     const T uk = base[0];
                     T bx = T(0), by = T(0);
                     if (g.drift) {
-                        const float2 bb = g.drift[k];
+                        const float2 bb = g.drift[j * n + i];
                         bx = (T)bb.x;
                         by = (T)bb.y;
                     }
@@ -290,8 +295,8 @@ k_wtiles(TileArgs a, T* u) {
                 }
             }
             // write back this tile's free nodes
-            if (lane < nn) st_l2(u + k0, su[(R + (e0 >> 3)) * W + (R + (e0 & 7))]);
-            if (lane + 32 < nn) st_l2(u + k1, su[(R + (e1 >> 3)) * W + (R + (e1 & 7))]);
+            if (lane < nn) st_l2(u + k0, su[(R + e0 / TW) * W + (R + e0 % TW)]);
+            if (lane + 32 < nn) st_l2(u + k1, su[(R + e1 / TW) * W + (R + e1 % TW)]);
             if (lane == 0) {
                 __stcg(a.tile_inc + t, __float_as_uint(tmax));
                 cnt += (unsigned long long)nn * a.local_sweeps;
@@ -331,11 +336,12 @@ k_wtiles(TileArgs a, T* u) {
     }
 }
 
-// Build of the 8x8 warp tiles: one warp per tile gathers the tile's free nodes,
+// Build of the warp tiles: one warp per tile gathers the tile's free nodes,
 // sorts them by the key (u_hat, or the current value when re-sorting) with a
 // 64-element bitonic sort held two per lane, writes them to slots
 // t*64 .. t*64+count-1, and records the band of the smallest key (the tile's wave
 // is derived from it).
+template <int TW, int TH>
 __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ key_val,
                               const uint8_t* __restrict__ mask, float lambda, float band_w,
                               int band_cap, int32_t* nodes, int32_t* count, int* tile_min) {
@@ -343,15 +349,16 @@ __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ 
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= nt) return;
     const int tcx = t % ntx, tcy = t / ntx;
-    // lane holds tile cells lane and lane + 32 (row-major 8x8)
+    // lane holds tile cells lane and lane + 32 (row-major TW x TH; slots past
+    // TW*TH stay empty)
     float kv[2];
     int kn[2];
     for (int h = 0; h < 2; ++h) {
         const int e = lane + 32 * h;
-        const int i = tcx * kWarpTile + (e & 7), j = tcy * kWarpTile + (e >> 3);
+        const int i = tcx * TW + e % TW, j = tcy * TH + e / TW;
         kv[h] = INFINITY;
         kn[h] = -1;
-        if (i < n && j < n) {
+        if (e < TW * TH && i < n && j < n) {
             const int k = j * n + i;
             if (mask[k] == kFree) {
                 kv[h] = key_val[k];
@@ -406,7 +413,7 @@ __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ 
     const int cnt = __popc(m0) + __popc(m1);
     // empty slots (INFINITY) sort last, so the first cnt elements are the nodes
     // store tile-local indices e = (j - 8 tcy) * 8 + (i - 8 tcx)
-    auto local = [&](int k) { return ((k / n) - tcy * kWarpTile) * kWarpTile + (k % n) - tcx * kWarpTile; };
+    auto local = [&](int k) { return ((k / n) - tcy * TH) * TW + (k % n) - tcx * TW; };
     if (lane < cnt) nodes[(size_t)t * kWarpTileNodes + lane] = local(kn[0]);
     if (lane + 32 < cnt) nodes[(size_t)t * kWarpTileNodes + lane + 32] = local(kn[1]);
     if (lane == 0) {
@@ -427,10 +434,21 @@ __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ 
     }
 }
 
+// shape code: 0 = block tiles 16x16, 1 = warp 8x8, 2 = warp 8x4, 3 = warp 4x4
+template <typename T, bool SIG>
+auto wtile_kernel(int shape) -> void (*)(TileArgs, T*) {
+    switch (shape) {
+        case 1: return k_wtiles<T, SIG, 8, 8>;
+        case 2: return k_wtiles<T, SIG, 8, 4>;
+        case 3: return k_wtiles<T, SIG, 4, 4>;
+        default: return k_tiles<T, SIG>;
+    }
+}
+
 template <typename T, bool SIG>
 cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
     const size_t smem = tile_smem(sizeof(T) == 8, a.g.na, a.halo, a.warp_tiles);
-    auto kern = a.warp_tiles ? k_wtiles<T, SIG> : k_tiles<T, SIG>;
+    auto kern = wtile_kernel<T, SIG>(a.warp_tiles);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -441,9 +459,9 @@ cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
 }
 
 template <typename T, bool SIG>
-int blocks_per_sm_impl(int na, int halo, bool warp_tiles) {
-    const size_t smem = tile_smem(sizeof(T) == 8, na, halo, warp_tiles);
-    auto kern = warp_tiles ? k_wtiles<T, SIG> : k_tiles<T, SIG>;
+int blocks_per_sm_impl(int na, int halo, int shape) {
+    const size_t smem = tile_smem(sizeof(T) == 8, na, halo, shape);
+    auto kern = wtile_kernel<T, SIG>(shape);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
@@ -498,34 +516,40 @@ __global__ void k_tile_waves(int nt, const int* __restrict__ tile_min, int band_
 
 }  // namespace
 
-size_t tile_smem(bool f64, int na, int halo, bool warp_tiles) {
+void wtile_dims(int shape, int* tw, int* th) {
+    *tw = shape == 3 ? 4 : 8;
+    *th = shape == 1 ? 8 : 4;
+}
+
+size_t tile_smem(bool f64, int na, int halo, int shape) {
     const size_t v2 = f64 ? sizeof(double2) : sizeof(float2);
     const size_t ctrl = ((size_t)na * v2 + 15) & ~(size_t)15;
     const size_t rs = f64 ? sizeof(double) : sizeof(float);
-    if (warp_tiles) {
-        const size_t w = (size_t)(kWarpTile + 2 * halo);
-        return ctrl + (size_t)kWarps * w * w * rs;
+    if (shape > 0) {
+        int tw, th;
+        wtile_dims(shape, &tw, &th);
+        return ctrl + (size_t)kWarps * (size_t)(tw + 2 * halo) * (size_t)(th + 2 * halo) * rs;
     }
     const size_t off = (((size_t)kLocalBands + 1) * sizeof(int) + 15) & ~(size_t)15;
     const size_t w = (size_t)(kTileSize + 2 * halo);
     return ctrl + off + w * w * rs;
 }
 
-int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, bool warp_tiles) {
-    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo, warp_tiles)
-                        : blocks_per_sm_impl<double, false>(na, halo, warp_tiles);
-    return sig ? blocks_per_sm_impl<float, true>(na, halo, warp_tiles)
-               : blocks_per_sm_impl<float, false>(na, halo, warp_tiles);
+int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape) {
+    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo, shape)
+                        : blocks_per_sm_impl<double, false>(na, halo, shape);
+    return sig ? blocks_per_sm_impl<float, true>(na, halo, shape)
+               : blocks_per_sm_impl<float, false>(na, halo, shape);
 }
 
-cudaError_t launch_wtile_build(int n, int ntx, int nt, const float* key_val, const uint8_t* mask,
-                               float lambda, float band_w, int band_cap, int32_t* nodes,
-                               int32_t* count, int* tile_min, cudaStream_t st) {
+cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
+                               const uint8_t* mask, float lambda, float band_w, int band_cap,
+                               int32_t* nodes, int32_t* count, int* tile_min, cudaStream_t st) {
     count_launches(1);
     const long long threads = (long long)nt * 32;
-    k_wtile_build<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, lambda,
-                                                                 band_w, band_cap, nodes, count,
-                                                                 tile_min);
+    auto kern = shape == 3 ? k_wtile_build<4, 4> : (shape == 2 ? k_wtile_build<8, 4> : k_wtile_build<8, 8>);
+    kern<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, lambda, band_w,
+                                                        band_cap, nodes, count, tile_min);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ def _desc(L, **kw):
     d.coarse_n, d.n_patches, d.scheme, d.band_width, d.band_window = 0, 1, 3, 1.0, 8
     d.band_group, d.wave_warps, d.resort_passes = 1, 0, 0
     d.schedule, d.tile_waves, d.tile_period, d.local_sweeps = 0, 8, 8, 1
+    d.tile_shape = 0
     for k, v in kw.items():
         setattr(d, k, v)
     return d
@@ -60,7 +61,7 @@ def _desc(L, **kw):
 @pytest.mark.parametrize("bad", [
     dict(n=2), dict(n_controls=0), dict(n_controls=300), dict(lam=-1.0), dict(sigma=-0.1),
     dict(cost=0.0), dict(scheme=4), dict(n_patches=0), dict(coarse_n=4),
-    dict(lam=float("nan")), dict(reserved=1), dict(resort_passes=-1), dict(schedule=3),
+    dict(lam=float("nan")), dict(reserved=1), dict(resort_passes=-1), dict(schedule=3), dict(tile_shape=3), dict(tile_shape=-2),
 ])
 def test_invalid_descriptions_are_rejected_on_host(L, bad):
     d = _desc(L, **bad)

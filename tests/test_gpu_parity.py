@@ -251,3 +251,49 @@ def test_warm_start_and_state_errors():
         G.solve_patches(tol32=1e-7, tol64=1e-13)
         np.testing.assert_allclose(G.get_value(), u_ref, atol=1e-10)
         assert G.residual() <= 1e-12
+
+
+@pytest.mark.parametrize("name,inst", VARIANTS[:5], ids=[v[0] for v in VARIANTS[:5]])
+def test_fp64_residual_equals_unscreened(name, inst):
+    """hjb_residual screens the controls in FP32 and evaluates only the survivors
+    in FP64; the result must equal the plain FP64 sup-residual of eq. SLscheme2
+    (one full FP64 operator application), on a random field and near a solution."""
+    O = oracle.Problem.from_instance(inst)
+    with P_gpu(inst) as G:
+        for u in (O.fix_nonfree(hi.random_values(inst.n, 21, 0.0, O.u_max, inst.mask)),
+                  O.solve(scheme=3, tol=1e-7, max_sweeps=4000)[0]):
+            u = u.astype(np.float32).astype(np.float64)
+            G.set_value(u)
+            r_scr = G.residual()
+            tu, _ = G.apply_operator(u, precision=64, scheme=2)
+            free = inst.mask == 0
+            r_full = np.abs(tu - u)[free].max()
+            assert abs(r_scr - r_full) <= 1e-15 * max(1.0, r_full), (r_scr, r_full)
+            assert abs(r_scr - O.residual(u)) <= 1e-13
+
+
+SCHEDULES = [dict(schedule=0, tile_shape=0), dict(schedule=0, tile_shape=1),
+             dict(schedule=0, tile_shape=2), dict(schedule=0, tile_shape=0, tile_waves=8, tile_period=4),
+             dict(schedule=0, resort_passes=1), dict(schedule=0, local_sweeps=2),
+             dict(schedule=1, band_group=1), dict(schedule=1, band_group=4, wave_warps=1024),
+             dict(schedule=2, tile_waves=8, tile_period=4)]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=[str(s) for s in SCHEDULES])
+@pytest.mark.parametrize("sigma", [0.0, 0.05])
+def test_every_patch_schedule_reaches_the_oracle_fixed_point(sched, sigma):
+    """The fixed point does not depend on the visiting order (Section 4.2): every
+    schedule -- warp tiles of each shape, block tiles, band waves, re-sorting,
+    extra local sweeps -- must reach the oracle's solution within the gates."""
+    inst = hi.patchy_1025(sigma, n=129, coarse_n=17)
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(scheme=3, tol=1e-14)
+    with P_gpu(inst, **sched) as G:
+        G.coarse_solve(tol_c=1e-7)
+        G.build_patches()
+        G.solve_patches(tol32=3e-7, tol64=0.0)
+        u32 = G.get_value()
+        assert np.abs(u32 - u_ref).max() <= 1e-5 * max(1.0, np.abs(u_ref).max())
+        st = G.solve_patches(tol32=3e-7, tol64=1e-12)
+        assert st["residual"] <= 1e-12
+        np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)
