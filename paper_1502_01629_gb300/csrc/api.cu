@@ -338,17 +338,6 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
     if (p->desc.band_group <= 0) p->desc.band_group = 1;
-    {
-        // automatic tile schedule: when the diffusion offset sqrt(2h) sigma reaches
-        // past one cell the scheme couples nodes of equal value (no upwind
-        // diffusion ball, Section 4.1) and smaller tiles in single-band waves are
-        // faster; otherwise 8x4 tiles in two-band waves (measured on the
-        // 1025^2 workload)
-        const double dcell = std::sqrt(2.0 * p->h) * p->sigma / p->dx;
-        const bool wide = dcell > 1.0;
-        if (p->desc.tile_shape < 0) p->desc.tile_shape = wide ? 2 : 1;
-        if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
-    }
     if (p->desc.tile_period <= 1) p->desc.tile_period = 2;
     if (p->desc.local_sweeps <= 0) p->desc.local_sweeps = 1;
     p->n = n;
@@ -369,6 +358,17 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->halo > 64) {
         delete p;
         return fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach);
+    }
+    {
+        // automatic tile schedule: when the diffusion offset sqrt(2h) sigma reaches
+        // past one cell the scheme couples nodes of equal value (no upwind
+        // diffusion ball, Section 4.1) and smaller tiles in single-band waves are
+        // faster; otherwise 8x4 tiles in two-band waves (measured on the
+        // 1025^2 workload)
+        const double dcell = std::sqrt(2.0 * p->h) * p->sigma / p->dx;
+        const bool wide = dcell > 1.0;
+        if (p->desc.tile_shape < 0) p->desc.tile_shape = wide ? 2 : 1;
+        if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
     }
     p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
     if (p->desc.schedule != 1 && p->desc.coarse_n > 0 &&
