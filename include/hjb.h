@@ -161,9 +161,10 @@ int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const ui
 
 /* hjb_coarse_solve -- Section 4.3 "Pre-computation", first item: starting from
  * u_c^0 = l(1/lambda + h) off the target (the paper's "very big value"), iterate
- * SLscheme3 with sigma = 0 on G_c (full-grid Jacobi sweeps, the paper's
- * "standard (static) domain decomposition" of the coarse solve taken to one node
- * per thread) until the sup-increment is <= tol_c.  G_c is
+ * SLscheme3 with sigma = 0 on G_c (whole-grid in-place sweeps in one cooperative
+ * launch, a warp per node -- the paper's "standard (static) domain decomposition"
+ * of the coarse solve taken to one node per warp) until the sup-increment of a
+ * sweep is <= tol_c.  G_c is
  * nested in G: coarse node (I,J) is fine node (rI, rJ), r = (n-1)/(coarse_n-1);
  * its speed is the fine speed there; it is a target when a fine target node lies
  * within r/2 fine cells in both axes, else an obstacle when its fine node is one.

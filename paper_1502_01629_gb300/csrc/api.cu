@@ -125,8 +125,6 @@ struct hjb_problem {
     float2* drift_c = nullptr;
     uint8_t* mask_c = nullptr;
     float* uc = nullptr;
-    float* uc_b = nullptr;
-    int halo_c = 1;
     double hc = 0, beta_c = 0, hl_c = 0, uob_c = 0;
     // pre-computation
     float* uhat = nullptr;
@@ -223,6 +221,7 @@ struct hjb_problem {
 namespace {
 
 struct Scalars {
+    unsigned int relax_inc[3];
     unsigned int inc32;
     int max_key;
     unsigned long long inc64;
@@ -442,12 +441,13 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         p->beta_c = 1.0 / (1.0 + p->lambda * p->hc);
         p->hl_c = p->hc * desc->cost;
         p->uob_c = p->lambda > 0.0 ? p->hl_c / (1.0 - p->beta_c) : 1e6;
-        p->halo_c = sweep_halo(p->h * (cmax * amax + bmax) / p->dx);
         const size_t Nc = (size_t)nc * nc;
+        if (grid_relax_smem(nc, na) > 200 * 1024)
+            return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d too large for the coarse solve "
+                                                  "(its field must fit in shared memory)", nc));
         CUP(cudaMalloc(&p->speed_c, Nc * sizeof(float)));
         CUP(cudaMalloc(&p->mask_c, Nc));
         CUP(cudaMalloc(&p->uc, Nc * sizeof(float)));
-        CUP(cudaMalloc(&p->uc_b, Nc * sizeof(float)));
         if (drift) CUP(cudaMalloc(&p->drift_c, Nc * sizeof(float2)));
         CUP(launch_coarse_data(n, nc, p->speed, p->drift, p->mask, p->speed_c, p->drift_c,
                                p->mask_c, p->st));
@@ -744,7 +744,8 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     const bool sig = p->sigma > 0.0;
     int blocks = f64 ? p->tile_blocks64 : p->tile_blocks32;
     if (p->desc.wave_warps > 0) {
-        const int want = (p->desc.wave_warps + tile_threads() / 32 - 1) / (tile_threads() / 32);
+        const int wpb = tile_threads(f64, p->shape) / 32;
+        const int want = (p->desc.wave_warps + wpb - 1) / wpb;
         blocks = std::max(1, std::min(blocks, want));
     }
     if (f64) {
@@ -867,7 +868,7 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->speed); dfree(p->drift); dfree(p->mask); dfree(p->sector);
     dfree(p->ctrl32); dfree(p->ctrl64);
     dfree(p->u32); dfree(p->u32b); dfree(p->u64); dfree(p->u64b);
-    dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc); dfree(p->uc_b);
+    dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc);
     dfree(p->uhat); dfree(p->a); dfree(p->succ); dfree(p->jump_a); dfree(p->jump_b);
     dfree(p->label); dfree(p->key); dfree(p->order); dfree(p->bin_count); dfree(p->bin_off);
     dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
@@ -892,14 +893,34 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     const GridView gc = p->coarse_view();
     const int Nc = p->nc * p->nc;
     CU(launch_init_values(Nc, p->mask_c, (float)p->uob_c, (float)p->uob_c, p->uc, nullptr, p->uob_c, p->st));
-    CU(launch_init_values(Nc, p->mask_c, (float)p->uob_c, (float)p->uob_c, p->uc_b, nullptr, p->uob_c, p->st));
-    int sweeps = 0;
-    double last = -1.0;
-    bool conv = false;
-    int rcj = jacobi32(p, gc, p->halo_c, p->uc, p->uc_b, tol_c, max_sweeps, &sweeps, &last, &conv);
-    if (rcj) return rcj;
+    // one cooperative launch: in-place sweeps until the sup-increment is <= tol_c
+    Scalars* ds = dscal(p);
+    CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
+    CU(cudaMemsetAsync(&ds->sync, 0, sizeof(GridSync), p->st));
+    CU(cudaMemsetAsync(ds->relax_inc, 0, sizeof(ds->relax_inc), p->st));
+    RelaxArgs ra{};
+    ra.g = gc;
+    ra.tol = (float)tol_c;
+    ra.max_sweeps = max_sweeps;
+    ra.sweep_inc = ds->relax_inc;
+    ra.sync = &ds->sync;
+    ra.res = &ds->wave;
+    ra.timeout_ns = kTimeoutNs;
+    {
+        // one block per SM, but not more warps than coarse nodes
+        const int warps = grid_relax_threads() / 32;
+        const int blocks = std::max(1, std::min(p->num_sms, (Nc + warps - 1) / warps));
+        CU(launch_grid_relax(ra, p->uc, false, blocks, p->st));
+    }
     tm.mark();
+    CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
+    CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
+    if (hscal(p)->sync.err != 0)
+        return fail(hscal(p)->sync.err, "coarse solve: a grid-wide wait exceeded its limit");
+    const int sweeps = hscal(p)->wave.passes;
+    const double last = hscal(p)->wave.last_increment;
+    const bool conv = hscal(p)->wave.converged != 0;
     CoarseResult cr;
     cr.sweeps = conv ? sweeps : -sweeps;
     cr.increment = (float)last;

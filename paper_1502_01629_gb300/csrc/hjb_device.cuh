@@ -283,12 +283,16 @@ __device__ __forceinline__ T block_max(T v, T* scratch32) {
 
 // ------------------------------------------------------------ grid barrier
 
-// State of the grid-wide barrier of a cooperative (co-resident) launch.
+// State of the grid-wide barrier of a cooperative (co-resident) launch.  Blocks
+// arrive on one of kSyncGroups group counters (each on its own 128-byte line);
+// the last arriver of a group arrives on the top counter.
+constexpr int kSyncGroups = 16;
 struct GridSync {
     unsigned int count;
     unsigned int gen;
     int err;          // 0, or a negative HJB_ERR_* code set by any block
-    int pad;
+    int pad[29];
+    unsigned int group[kSyncGroups * 32];
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -309,22 +313,31 @@ __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
     return v;
 }
 
-// Sense-free generation barrier.  Every wait is bounded by `timeout_ns` of
-// global time; on expiry the block records HJB_ERR_TIMEOUT and every block
-// leaves at its next barrier.  Returns false when the grid must stop.
-// Requires all blocks to be co-resident (cudaLaunchCooperativeKernel).
+// Two-level generation barrier.  Every wait is bounded by `timeout_ns` of global
+// time; on expiry the block records HJB_ERR_TIMEOUT and every block leaves at
+// its next barrier.  Returns false when the grid must stop.  Requires all
+// blocks to be co-resident (cudaLaunchCooperativeKernel).
 __device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int nblocks,
                                           unsigned long long timeout_ns) {
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned int G = nblocks < (unsigned int)kSyncGroups ? nblocks : (unsigned int)kSyncGroups;
+        const unsigned int my = blockIdx.x % G;
+        const unsigned int members = nblocks / G + (my < nblocks % G ? 1u : 0u);
         const unsigned int g = ld_acquire_u32(&gs->gen);
         __threadfence();
-        const unsigned int arrived = atomicAdd(&gs->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&gs->count, 0u);
+        bool release = false;
+        if (atomicAdd(&gs->group[my * 32], 1u) == members - 1) {
+            atomicExch(&gs->group[my * 32], 0u);
             __threadfence();
-            atomicAdd(&gs->gen, 1u);
-        } else {
+            if (atomicAdd(&gs->count, 1u) == G - 1) {
+                atomicExch(&gs->count, 0u);
+                __threadfence();
+                atomicAdd(&gs->gen, 1u);
+                release = true;
+            }
+        }
+        if (!release) {
             const unsigned long long t0 = global_ns();
             while (ld_acquire_u32(&gs->gen) == g) {
                 if (ld_relaxed_s32(&gs->err) != 0) break;

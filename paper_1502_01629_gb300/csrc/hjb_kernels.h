@@ -99,6 +99,21 @@ struct WaveArgs {
     unsigned long long timeout_ns;
 };
 
+// Whole-grid in-place relaxation in one cooperative launch (coarse solve).
+struct RelaxArgs {
+    GridView g;
+    float tol;
+    int max_sweeps;
+    unsigned int* sweep_inc;  // ring of 3 per-sweep maxima (float bits), zeroed by the host
+    GridSync* sync;
+    WaveResult* res;
+    unsigned long long timeout_ns;
+};
+// One block per SM; the n x n field must fit in shared memory (grid_relax_smem).
+cudaError_t launch_grid_relax(const RelaxArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
+size_t grid_relax_smem(int n, int na);
+int grid_relax_threads();
+
 // Persistent cooperative kernel: max_passes passes of band-ordered waves over
 // u (FP32 or FP64) in place.  blocks = co-resident block count.
 cudaError_t launch_waves_f32(const WaveArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
@@ -145,7 +160,7 @@ int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape);
 cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
                                const uint8_t* mask, float lambda, float band_w, int band_cap,
                                int32_t* nodes, int32_t* count, int* tile_min, cudaStream_t st);
-int tile_threads();
+int tile_threads(bool f64, int shape);
 cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
 cudaError_t launch_tiles_f64(const TileArgs& a, double* u, bool sig, int blocks, cudaStream_t st);
 cudaError_t launch_tile_min(int n, int ntx, const int32_t* key, const uint8_t* mask, int* tile_min,

@@ -26,6 +26,14 @@ constexpr int kTS = kTileSize;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+// Block size of the warp-tile kernel: one 1024-thread block per SM in FP32 (a
+// cheaper grid barrier), 256 threads in FP64 (more registers per thread).
+template <typename T>
+struct WTBlock {
+    static constexpr int threads = sizeof(T) == 4 ? 1024 : 256;
+    static constexpr int warps = threads / 32;
+};
+
 __device__ __forceinline__ float ld_l2(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_l2(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ void st_l2(float* p, float v) { __stcg(p, v); }
@@ -191,8 +199,9 @@ k_tiles(TileArgs a, T* u) {
 // (enough to cover the interpolation reach) changed by more than tol at its
 // last visit.
 template <typename T, bool SIG, int TW, int TH>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(WTBlock<T>::threads)
 k_wtiles(TileArgs a, T* u) {
+    constexpr int kWarpsW = WTBlock<T>::warps;
     using V2 = typename RealOf<T>::V2;
     extern __shared__ __align__(16) unsigned char smem[];
     const GridView& g = a.g;
@@ -211,8 +220,9 @@ k_wtiles(TileArgs a, T* u) {
 
     const unsigned int nblocks = gridDim.x;
     const unsigned int tol_bits = __float_as_uint(a.tol);
-    const int gw = blockIdx.x * kWarps + warp;
-    const int nw = gridDim.x * kWarps;
+    // consecutive tiles of a step go to different blocks (SMs) first
+    const int gw = warp * gridDim.x + blockIdx.x;
+    const int nw = gridDim.x * kWarpsW;
     const int ar = a.act_radius;
     const int aw = 2 * ar + 1;
     for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(g, m);
@@ -455,7 +465,8 @@ cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
     }
     void* args[] = {(void*)&a, (void*)&u};
     count_launches(1);
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kThreads), args, smem, st);
+    const int threads = a.warp_tiles ? WTBlock<T>::threads : kThreads;
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), args, smem, st);
 }
 
 template <typename T, bool SIG>
@@ -465,7 +476,7 @@ int blocks_per_sm_impl(int na, int halo, int shape) {
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, shape ? WTBlock<T>::threads : kThreads, smem);
     return nb;
 }
 
@@ -528,7 +539,8 @@ size_t tile_smem(bool f64, int na, int halo, int shape) {
     if (shape > 0) {
         int tw, th;
         wtile_dims(shape, &tw, &th);
-        return ctrl + (size_t)kWarps * (size_t)(tw + 2 * halo) * (size_t)(th + 2 * halo) * rs;
+        const size_t warps = f64 ? WTBlock<double>::warps : WTBlock<float>::warps;
+        return ctrl + warps * (size_t)(tw + 2 * halo) * (size_t)(th + 2 * halo) * rs;
     }
     const size_t off = (((size_t)kLocalBands + 1) * sizeof(int) + 15) & ~(size_t)15;
     const size_t w = (size_t)(kTileSize + 2 * halo);
@@ -553,7 +565,10 @@ cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* k
     return cudaGetLastError();
 }
 
-int tile_threads() { return kThreads; }
+int tile_threads(bool f64, int shape) {
+    if (!shape) return kThreads;
+    return f64 ? WTBlock<double>::threads : WTBlock<float>::threads;
+}
 
 cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st) {
     return sig ? launch_impl<float, true>(a, u, blocks, st) : launch_impl<float, false>(a, u, blocks, st);

@@ -46,7 +46,8 @@ k_waves(WaveArgs a, T* u) {
     const int n = g.n;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * kWarps + warp;
+    // consecutive nodes of a wave go to different blocks (SMs) first
+    const int gw = warp * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * kWarps;
     const unsigned int nblocks = gridDim.x;
     const unsigned int tol_bits = __float_as_uint(a.tol);
@@ -147,6 +148,82 @@ k_waves(WaveArgs a, T* u) {
     }
 }
 
+// Whole-grid relaxation in one cooperative launch (used for the coarse solve,
+// Section 4.3): at the start of every sweep each block copies the whole value
+// field into its shared memory (the coarse grid is small), then updates its
+// share of the free nodes from that copy -- a warp per node, lanes over the
+// controls -- and writes them back; the node order alternates between
+// row-major and reverse; a grid barrier closes each sweep and the loop stops
+// once a sweep's sup-increment is <= tol.  One block of kRelaxThreads per SM.
+constexpr int kRelaxThreads = 1024;
+constexpr int kRelaxWarps = kRelaxThreads / 32;
+
+template <bool SIG>
+__global__ void __launch_bounds__(kRelaxThreads)
+k_grid_relax(RelaxArgs a, float* u) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GridView& g = a.g;
+    const int n = g.n;
+    const int N = n * n;
+    float2* sctrl = reinterpret_cast<float2*>(smem);
+    float* su = reinterpret_cast<float*>(smem + (((size_t)g.na * sizeof(float2) + 15) & ~(size_t)15));
+    __shared__ float red[32];
+    __shared__ int s_flag;
+    const int lane = threadIdx.x & 31;
+    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int nw = gridDim.x * kRelaxWarps;
+    for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = g.ctrl32[m];
+    auto C = [&](int m) { return sctrl[m]; };
+    int s = 0;
+    int converged = 0;
+    float last = 0.0f;
+    for (s = 0; s < a.max_sweeps; ++s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.sweep_inc[(s + 1) % 3] = 0u;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) su[k] = __ldcg(u + k);
+        __syncthreads();
+        float lmax = 0.0f;
+        for (int t = gw; t < N; t += nw) {
+            const int k = (s & 1) ? (N - 1 - t) : t;
+            if (g.mask[k] != kFree) continue;
+            const int i = k % n, j = k / n;
+            const float uk = su[k];
+            const float c = g.speed[k];
+            float bx = 0.0f, by = 0.0f;
+            if (g.drift) {
+                const float2 bb = g.drift[k];
+                bx = bb.x;
+                by = bb.y;
+            }
+            const float* base = su + k;
+            auto U = [&](int dx, int dy) { return base[dy * n + dx]; };
+            float Nn, D;
+            int M;
+            best_over_controls<float, SIG>(g, 3, i, j, uk, c, bx, by, lane, 32, C, U, Nn, D, M);
+            const float du = warp_min_increment(Nn, D, M);
+            if (lane == 0) __stcg(u + k, uk + du);
+            lmax = fmaxf(lmax, fabsf(du));
+        }
+        const float bm = block_max<float>(lmax, red);
+        if (threadIdx.x == 0 && bm > 0.0f) atomicMax(a.sweep_inc + s % 3, __float_as_uint(bm));
+        if (!grid_sync(a.sync, gridDim.x, a.timeout_ns)) break;
+        if (threadIdx.x == 0) {
+            last = __uint_as_float(__ldcg(a.sweep_inc + s % 3));
+            s_flag = last <= a.tol ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_flag) {
+            converged = 1;
+            ++s;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.res->passes = s;
+        a.res->converged = converged;
+        a.res->last_increment = last;
+    }
+}
+
 template <typename T, bool SIG>
 cudaError_t launch_impl(const WaveArgs& a, T* u, int blocks, cudaStream_t st) {
     using V2 = typename RealOf<T>::V2;
@@ -169,6 +246,22 @@ int blocks_per_sm_impl(int na) {
 }  // namespace
 
 int wave_threads() { return kWaveThreads; }
+
+size_t grid_relax_smem(int n, int na) {
+    return (((size_t)na * sizeof(float2) + 15) & ~(size_t)15) + (size_t)n * n * sizeof(float);
+}
+
+cudaError_t launch_grid_relax(const RelaxArgs& a, float* u, bool sig, int blocks, cudaStream_t st) {
+    const size_t smem = grid_relax_smem(a.g.n, a.g.na);
+    const void* kern = sig ? (const void*)k_grid_relax<true> : (const void*)k_grid_relax<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a, (void*)&u};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(kRelaxThreads), args, smem, st);
+}
+
+int grid_relax_threads() { return kRelaxThreads; }
 
 size_t wave_smem(bool f64, int na) { return (size_t)na * (f64 ? sizeof(double2) : sizeof(float2)); }
 
