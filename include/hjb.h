@@ -88,7 +88,7 @@ typedef struct {
                              diffusion offset sqrt(2h) sigma exceeds one cell, else 2)        */
     int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 2)         */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
-    int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (4x4 when the
+    int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (8x8 when the
                              diffusion offset exceeds one cell, else 8x4)                     */
     int32_t reserved;     /* must be 0                                                        */
 } hjb_desc;
@@ -200,10 +200,12 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
  * in shared memory -- 0: one warp per 8x8 (or tile_shape) tile visiting the
  * tile's nodes one by one in increasing u_hat; 2: one block per 16x16 tile visiting its bands in
  * order -- tiles grouped into waves by their lowest band and run on a cyclic
- * schedule of period D (one grid-wide barrier per step); tiles whose
- * neighbourhood did not change are skipped; converged when no tile visited in
- * the last D steps changed by more than the tolerance ("passes" in the stats
- * count pipeline steps).  Schedule 1
+ * schedule of period D (one grid-wide barrier per step).  Schedule 0 visits a
+ * tile at its wave and afterwards only when a tile within the interpolation
+ * reach changed by more than the tolerance (per-step tile queues); schedule 2
+ * skips tiles whose neighbourhood did not change.  Converged when no tile
+ * visited in the last D steps changed by more than the tolerance ("passes" in
+ * the stats count pipeline steps).  Schedule 1
  * (band waves): band_group bands per grid-wide wave, nodes taken in sorted order
  * by the wave_warps warps in flight; passes after the first skip groups whose
  * neighbourhood did not change.  FP32 until a

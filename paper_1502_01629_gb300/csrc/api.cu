@@ -155,6 +155,10 @@ struct hjb_problem {
     int32_t* tile_bin_off = nullptr;
     int32_t* wt_nodes = nullptr;
     int32_t* wt_count = nullptr;
+    float* wt_speed = nullptr;     // speed per node slot (warp tiles)
+    int32_t* wt_stamp = nullptr;   // per-tile queue stamps (warp tiles)
+    int32_t* wt_queue = nullptr;   // (tile_period + 2) x nt queued tiles
+    int32_t* wt_qcount = nullptr;  // tile_period + 2 queue lengths
     int32_t* sched_count = nullptr;
     int32_t* sched_off = nullptr;
     int32_t* res_off = nullptr;
@@ -361,12 +365,12 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     {
         // automatic tile schedule: when the diffusion offset sqrt(2h) sigma reaches
         // past one cell the scheme couples nodes of equal value (no upwind
-        // diffusion ball, Section 4.1) and smaller tiles in single-band waves are
+        // diffusion ball, Section 4.1) and 8x8 tiles in single-band waves are
         // faster; otherwise 8x4 tiles in two-band waves (measured on the
         // 1025^2 workload)
         const double dcell = std::sqrt(2.0 * p->h) * p->sigma / p->dx;
         const bool wide = dcell > 1.0;
-        if (p->desc.tile_shape < 0) p->desc.tile_shape = wide ? 2 : 1;
+        if (p->desc.tile_shape < 0) p->desc.tile_shape = wide ? 0 : 1;
         if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
     }
     p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
@@ -474,7 +478,11 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMalloc(&p->tile_inc, nt * sizeof(unsigned int)));
         if (warp_tiles) {
             CUP(cudaMalloc(&p->wt_nodes, nt * kWarpTileNodes * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->wt_speed, nt * kWarpTileNodes * sizeof(float)));
             CUP(cudaMalloc(&p->wt_count, nt * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->wt_stamp, nt * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->wt_queue, (p->desc.tile_period + 2) * nt * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->wt_qcount, (p->desc.tile_period + 2) * sizeof(int32_t)));
         } else {
             CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
             CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
@@ -673,16 +681,18 @@ int rebuild_order(hjb_problem* p) {
     return HJB_OK;
 }
 
-// Tile schedule from the band keys: nodes sorted by (tile, local band), tiles
-// grouped into waves by their lowest band and sorted by (wave mod D, wave).
+// Tile schedule from the band keys.  Warp tiles: nodes of each tile sorted by
+// the key value, tiles grouped into waves by their lowest band and sorted by
+// wave.  Block tiles: nodes sorted by (tile, local band), tiles sorted by
+// (wave mod D, wave).
 int build_tiles(hjb_problem* p, const float* key_val) {
     if (p->desc.schedule == 1) return HJB_OK;     // band waves need no tiles
     const int B = p->desc.tile_waves, D = p->desc.tile_period;
     if (p->desc.schedule == 0) {
         // warp tiles: per-tile exact order by the key value (u_hat or current value)
-        CU(launch_wtile_build(p->shape, p->n, p->ntx, p->nt, key_val, p->mask, (float)p->lambda,
-                              (float)(p->desc.band_width * p->h), kBandCap, p->wt_nodes,
-                              p->wt_count, p->tile_min, p->st));
+        CU(launch_wtile_build(p->shape, p->n, p->ntx, p->nt, key_val, p->mask, p->speed,
+                              (float)p->lambda, (float)(p->desc.band_width * p->h), kBandCap, p->wt_nodes,
+                              p->wt_speed, p->wt_count, p->tile_min, p->st));
     } else {
         CU(cudaMemsetAsync(p->tile_min, 0x7f, sizeof(int32_t) * (size_t)p->nt, p->st));
         CU(launch_tile_min(p->n, p->ntx, p->key, p->mask, p->tile_min, p->st));
@@ -691,7 +701,10 @@ int build_tiles(hjb_problem* p, const float* key_val) {
                                 p->tile_bin_off, p->tile_nodes, p->st));
     }
     p->n_waves = (std::max(p->n_bands, 1) - 1) / B + 1;
-    const int bins = D * p->n_waves;
+    // warp tiles: sorted by wave alone (sched_off = wave offsets); block tiles:
+    // by (wave mod D, wave)
+    const int Dk = p->desc.schedule == 0 ? 1 : D;
+    const int bins = Dk * p->n_waves;
     if (bins > p->sched_cap) {
         dfree(p->sched_count);
         dfree(p->sched_off);
@@ -699,11 +712,12 @@ int build_tiles(hjb_problem* p, const float* key_val) {
         CU(cudaMalloc(&p->sched_off, sizeof(int32_t) * (size_t)(bins + 1)));
         p->sched_cap = bins;
     }
-    CU(launch_tile_waves(p->nt, p->tile_min, B, D, p->n_waves, p->tile_wave, p->tile_key,
+    CU(launch_tile_waves(p->nt, p->tile_min, B, Dk, p->n_waves, p->tile_wave, p->tile_key,
                          p->tile_inc, p->st));
     CU(launch_counting_sort(p->nt, p->tile_key, bins, p->sched_count, p->sched_off, p->tile_list,
                             p->st));
-    CU(launch_strided_gather(D, p->n_waves, p->sched_off, p->res_off, p->st));
+    if (p->desc.schedule != 0)
+        CU(launch_strided_gather(D, p->n_waves, p->sched_off, p->res_off, p->st));
     return HJB_OK;
 }
 
@@ -714,9 +728,15 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
     CU(cudaMemsetAsync(&ds->sync, 0, sizeof(GridSync), p->st));
     CU(cudaMemsetAsync(p->step_inc, 0, sizeof(unsigned int) * 2 * D, p->st));
-    // every tile with free nodes starts as changed
-    CU(launch_tile_waves(p->nt, p->tile_min, B, D, p->n_waves, p->tile_wave, p->tile_key,
-                         p->tile_inc, p->st));
+    if (p->desc.schedule == 0) {
+        // empty queues; no tile is queued for a step up to its own wave
+        CU(cudaMemsetAsync(p->wt_qcount, 0, sizeof(int32_t) * (D + 2), p->st));
+        CU(launch_tile_stamps(p->nt, p->tile_wave, p->wt_stamp, p->st));
+    } else {
+        // every tile with free nodes starts as changed
+        CU(launch_tile_waves(p->nt, p->tile_min, B, D, p->n_waves, p->tile_wave, p->tile_key,
+                             p->tile_inc, p->st));
+    }
     TileArgs a{};
     a.g = p->fine_view();
     a.scheme = p->desc.scheme;
@@ -730,6 +750,12 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.res_off = p->res_off;
     a.tile_wave = p->tile_wave;
     a.tile_inc = p->tile_inc;
+    a.wave_off = p->sched_off;
+    a.slot_speed = p->wt_speed;
+    a.stamp = p->wt_stamp;
+    a.queue = p->wt_queue;
+    a.qcount = p->wt_qcount;
+    a.nt = p->nt;
     a.step_inc = p->step_inc;
     a.ntx = p->ntx;
     a.nty = p->nty;
@@ -757,8 +783,10 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
     *out = hscal(p)->wave;
+    if (hscal(p)->sync.err == HJB_ERR_TIMEOUT)
+        return fail(HJB_ERR_TIMEOUT, "tile kernel: a grid-wide wait exceeded its limit");
     if (hscal(p)->sync.err != 0)
-        return fail(hscal(p)->sync.err, "tile kernel: a grid-wide wait exceeded its limit");
+        return fail(hscal(p)->sync.err, "tile kernel: tile queue overflow (internal error)");
     return HJB_OK;
 }
 
@@ -874,7 +902,8 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
     dfree(p->tile_min); dfree(p->tile_wave); dfree(p->tile_key); dfree(p->tile_list);
     dfree(p->tile_inc); dfree(p->tile_key2); dfree(p->tile_nodes); dfree(p->tile_bin_count);
-    dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
+    dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->wt_speed);
+    dfree(p->wt_stamp); dfree(p->wt_queue); dfree(p->wt_qcount); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
     dfree(p->step_inc);
     if (p->scratch) cudaFree(p->scratch);
     if (p->host_pinned) cudaFreeHost(p->host_pinned);

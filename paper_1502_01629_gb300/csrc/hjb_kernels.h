@@ -138,10 +138,16 @@ struct TileArgs {
                                // warp tiles: 64 slots per tile, sorted by u_hat
     const int32_t* bin_off;    // block tiles: n_tiles * kLocalBands + 1
     const int32_t* wt_count;   // warp tiles: free nodes per tile
-    const int32_t* tile_list;  // tiles sorted by (wave mod period, wave)
-    const int32_t* res_off;    // period + 1
+    const int32_t* tile_list;  // block tiles: sorted by (wave mod period, wave); warp tiles: by wave
+    const int32_t* res_off;    // block tiles: period + 1
+    const int32_t* wave_off;   // warp tiles: n_waves + 1 offsets into tile_list
     const int32_t* tile_wave;  // wave of each tile
-    unsigned int* tile_inc;    // max increment of each tile's last visit (float bits)
+    unsigned int* tile_inc;    // block tiles: max increment of each tile's last visit (float bits)
+    const float* slot_speed;   // warp tiles: speed of each node slot (64 per tile)
+    int32_t* stamp;            // warp tiles: last step each tile was queued for
+    int32_t* queue;            // warp tiles: (period + 2) x nt queued tiles
+    int32_t* qcount;           // warp tiles: period + 2 queue lengths
+    int nt;                    // number of tiles
     unsigned int* step_inc;    // ring of 2 * period per-step maxima (float bits)
     int ntx, nty;              // tiles per row / column
     int n_waves;
@@ -158,8 +164,11 @@ void wtile_dims(int shape, int* tw, int* th);
 size_t tile_smem(bool f64, int na, int halo, int shape);
 int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape);
 cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
-                               const uint8_t* mask, float lambda, float band_w, int band_cap,
-                               int32_t* nodes, int32_t* count, int* tile_min, cudaStream_t st);
+                               const uint8_t* mask, const float* speed, float lambda, float band_w,
+                               int band_cap, int32_t* nodes, float* slot_speed, int32_t* count,
+                               int* tile_min, cudaStream_t st);
+// stamp[t] = tile_wave[t] (a tile is never queued for a step up to its first visit)
+cudaError_t launch_tile_stamps(int nt, const int32_t* tile_wave, int32_t* stamp, cudaStream_t st);
 int tile_threads(bool f64, int shape);
 cudaError_t launch_tiles_f32(const TileArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
 cudaError_t launch_tiles_f64(const TileArgs& a, double* u, bool sig, int blocks, cudaStream_t st);

@@ -195,9 +195,17 @@ k_tiles(TileArgs a, T* u) {
 // slice of shared memory and updates the tile's free nodes one after another in
 // increasing u_hat (the Gauss-Seidel order of Section 4.2 restricted to the
 // tile), its lanes spread over the controls.  Warps never wait for each other
-// inside a step.  A tile is visited only if some tile within `act_radius` tiles
-// (enough to cover the interpolation reach) changed by more than tol at its
-// last visit.
+// inside a step.
+//
+// Work of step s: the tiles of wave s (first visit, a contiguous range of the
+// wave-sorted tile list) and the tiles queued for step s.  A tile whose visit
+// changed some node by more than tol queues every tile within `act_radius`
+// tiles (enough to cover the interpolation reach) for that tile's next step
+// s' > s with s' = wave (mod D); a per-tile stamp (the last step it was queued
+// for, initially its own wave) keeps each tile at most once in a step's queue.
+// The queues form a ring of D + 2 slots: slot s is read in step s, filled during
+// steps s - D .. s - 1 and cleared in step s + 1.  The solve stops once every
+// wave has had its first visit and the queues of the next D steps are empty.
 template <typename T, bool SIG, int TW, int TH>
 __global__ void __launch_bounds__(WTBlock<T>::threads)
 k_wtiles(TileArgs a, T* u) {
@@ -219,18 +227,19 @@ k_wtiles(TileArgs a, T* u) {
     __shared__ unsigned long long s_nodes;
 
     const unsigned int nblocks = gridDim.x;
-    const unsigned int tol_bits = __float_as_uint(a.tol);
     // consecutive tiles of a step go to different blocks (SMs) first
     const int gw = warp * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * kWarpsW;
     const int ar = a.act_radius;
     const int aw = 2 * ar + 1;
+    const int nnb = aw * aw;
     for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(g, m);
     if (threadIdx.x == 0) s_nodes = 0ull;
     __syncthreads();
     auto C = [&](int m) { return sctrl[m]; };
 
     const int D = a.period;
+    const int QS = D + 2;
     const int ring = 2 * D;
     int step = 0;
     int converged = 0;
@@ -238,22 +247,22 @@ k_wtiles(TileArgs a, T* u) {
     bool ok = true;
     unsigned long long cnt = 0;
     for (step = 0; step < a.max_steps; ++step) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.step_inc[(step + 1) % ring] = 0u;
-        const int r = step % D;
-        const int lbeg = a.res_off[r];
-        const int lend = a.res_off[r + 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.step_inc[(step + 1) % ring] = 0u;
+            if (step >= 1) a.qcount[(step - 1) % QS] = 0;   // slot of step s - 1 = s + D + 1
+        }
+        const int slot = step % QS;
+        int fbeg = 0, fn = 0;
+        if (step < a.n_waves) {
+            fbeg = a.wave_off[step];
+            fn = a.wave_off[step + 1] - fbeg;
+        }
+        const int total = fn + min(__ldcg(a.qcount + slot), a.nt);
+        const int32_t* queue = a.queue + (size_t)slot * a.nt;
         float wmax = 0.0f;
-        for (int idx = lbeg + gw; idx < lend; idx += nw) {
-            const int t = a.tile_list[idx];
-            if (a.tile_wave[t] > step) break;       // entries are sorted by wave
+        for (int idx = gw; idx < total; idx += nw) {
+            const int t = idx < fn ? a.tile_list[fbeg + idx] : __ldcg(queue + (idx - fn));
             const int tcx = t % a.ntx, tcy = t / a.ntx;
-            bool act = false;
-            for (int q = lane; q < aw * aw; q += 32) {
-                const int nx = tcx + q % aw - ar, ny = tcy + q / aw - ar;
-                act |= nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty &&
-                       __ldcg(a.tile_inc + ny * a.ntx + nx) > tol_bits;
-            }
-            if (!__any_sync(0xffffffffu, act)) continue;
             const int bi = tcx * TW, bj = tcy * TH;
             const int gx0 = bi - R, gy0 = bj - R;
             for (int e = lane; e < W * H; e += 32) {
@@ -264,15 +273,26 @@ k_wtiles(TileArgs a, T* u) {
             }
             const int nn = a.wt_count[t];
             const int* tn = a.nodes + (size_t)t * kWarpTileNodes;
+            const float* tsp = a.slot_speed + (size_t)t * kWarpTileNodes;
             // tile-local indices e (row-major TW x TH) of the nodes, in visiting order
             const int e0 = lane < nn ? tn[lane] : 0;
             const int e1 = lane + 32 < nn ? tn[lane + 32] : 0;
-            const int k0 = (bj + e0 / TW) * n + bi + e0 % TW;
-            const int k1 = (bj + e1 / TW) * n + bi + e1 % TW;
-            const float c0 = lane < nn ? g.speed[k0] : 0.0f;
-            const float c1 = lane + 32 < nn ? g.speed[k1] : 0.0f;
+            const float c0 = lane < nn ? tsp[lane] : 0.0f;
+            const float c1 = lane + 32 < nn ? tsp[lane + 32] : 0.0f;
+            // this lane's neighbour tile (lane < nnb): its wave decides the step it
+            // would be queued for; -1 = none
+            int nbw = -1;
+            if (lane < nnb) {
+                const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
+                if (nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty) {
+                    const int w = a.tile_wave[ny * a.ntx + nx];
+                    if (w <= step) nbw = w;
+                }
+            }
             __syncwarp();
             float tmax = 0.0f;
+            int old = 0x7fffffff;    // stamp before this visit claimed the neighbour
+            bool claimed = false;
             for (int sw = 0; sw < a.local_sweeps; ++sw) {
                 for (int q = 0; q < nn; ++q) {
                     const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
@@ -302,15 +322,51 @@ k_wtiles(TileArgs a, T* u) {
                     if (lane == 0) base[0] = uk + du;
                     __syncwarp();
                     tmax = fmaxf(tmax, inc_to_float(fabs(du)));
+                    if (!claimed && tmax > a.tol) {
+                        // claim the neighbours now; the queue slots are taken after
+                        // the visit, so the atomics overlap the remaining nodes
+                        claimed = true;
+                        if (nbw >= 0) {
+                            const int tgt = step + 1 + ((nbw - step - 1) % D + D) % D;
+                            const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
+                            old = atomicMax(a.stamp + ny * a.ntx + nx, tgt);
+                        }
+                    }
                 }
             }
             // write back this tile's free nodes
-            if (lane < nn) st_l2(u + k0, su[(R + e0 / TW) * W + (R + e0 % TW)]);
-            if (lane + 32 < nn) st_l2(u + k1, su[(R + e1 / TW) * W + (R + e1 % TW)]);
-            if (lane == 0) {
-                __stcg(a.tile_inc + t, __float_as_uint(tmax));
-                cnt += (unsigned long long)nn * a.local_sweeps;
+            if (lane < nn) st_l2(u + (size_t)(bj + e0 / TW) * n + bi + e0 % TW,
+                                 su[(R + e0 / TW) * W + (R + e0 % TW)]);
+            if (lane + 32 < nn) st_l2(u + (size_t)(bj + e1 / TW) * n + bi + e1 % TW,
+                                      su[(R + e1 / TW) * W + (R + e1 % TW)]);
+            if (claimed) {
+                // lanes 0..31 claimed above; tiles past the 32nd neighbour (radius > 2)
+                // are claimed here
+                for (int q = lane; q < nnb; q += 32) {
+                    const int nx = tcx + q % aw - ar, ny = tcy + q / aw - ar;
+                    int w = -1;
+                    if (q == lane) {
+                        w = nbw;
+                    } else if (nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty) {
+                        const int ww = a.tile_wave[ny * a.ntx + nx];
+                        if (ww <= step) w = ww;
+                    }
+                    if (w < 0) continue;
+                    const int tt = ny * a.ntx + nx;
+                    const int tgt = step + 1 + ((w - step - 1) % D + D) % D;
+                    const int prev = q == lane ? old : atomicMax(a.stamp + tt, tgt);
+                    if (prev < tgt) {
+                        const int qs = tgt % QS;
+                        const int pos = atomicAdd(a.qcount + qs, 1);
+                        if (pos < a.nt) {
+                            __stcg(a.queue + (size_t)qs * a.nt + pos, tt);
+                        } else {
+                            atomicCAS(&a.sync->err, 0, HJB_ERR_CUDA);   // cannot happen
+                        }
+                    }
+                }
             }
+            if (lane == 0) cnt += (unsigned long long)nn * a.local_sweeps;
             wmax = fmaxf(wmax, tmax);
             __syncwarp();
         }
@@ -318,13 +374,15 @@ k_wtiles(TileArgs a, T* u) {
         if (threadIdx.x == 0 && bm > 0.0f) atomicMax(a.step_inc + step % ring, __float_as_uint(bm));
         ok = grid_sync(a.sync, nblocks, a.timeout_ns);
         if (!ok) break;
-        if (step >= a.n_waves - 1 + D) {
+        if (step >= a.n_waves - 1) {
             if (threadIdx.x == 0) {
+                int pending = 0;
+                for (int d = 1; d <= D; ++d) pending += __ldcg(a.qcount + (step + d) % QS);
                 float m = 0.0f;
-                for (int d = 0; d < D; ++d)
+                for (int d = 0; d < D && d <= step; ++d)
                     m = fmaxf(m, __uint_as_float(__ldcg(a.step_inc + (step - d) % ring)));
                 last_max = m;
-                s_flag = (m <= a.tol) ? 1 : 0;
+                s_flag = pending == 0 ? 1 : 0;
             }
             __syncthreads();
             if (s_flag) {
@@ -353,8 +411,9 @@ k_wtiles(TileArgs a, T* u) {
 // is derived from it).
 template <int TW, int TH>
 __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ key_val,
-                              const uint8_t* __restrict__ mask, float lambda, float band_w,
-                              int band_cap, int32_t* nodes, int32_t* count, int* tile_min) {
+                              const uint8_t* __restrict__ mask, const float* __restrict__ speed,
+                              float lambda, float band_w, int band_cap, int32_t* nodes,
+                              float* slot_speed, int32_t* count, int* tile_min) {
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= nt) return;
@@ -424,8 +483,15 @@ __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ 
     // empty slots (INFINITY) sort last, so the first cnt elements are the nodes
     // store tile-local indices e = (j - 8 tcy) * 8 + (i - 8 tcx)
     auto local = [&](int k) { return ((k / n) - tcy * TH) * TW + (k % n) - tcx * TW; };
-    if (lane < cnt) nodes[(size_t)t * kWarpTileNodes + lane] = local(kn[0]);
-    if (lane + 32 < cnt) nodes[(size_t)t * kWarpTileNodes + lane + 32] = local(kn[1]);
+    const size_t sb = (size_t)t * kWarpTileNodes;
+    if (lane < cnt) {
+        nodes[sb + lane] = local(kn[0]);
+        slot_speed[sb + lane] = speed[kn[0]];
+    }
+    if (lane + 32 < cnt) {
+        nodes[sb + lane + 32] = local(kn[1]);
+        slot_speed[sb + lane + 32] = speed[kn[1]];
+    }
     if (lane == 0) {
         count[t] = cnt;
         int bm = 0x7f7f7f7f;
@@ -519,10 +585,15 @@ __global__ void k_tile_waves(int nt, const int* __restrict__ tile_min, int band_
         tile_inc[t] = 0u;
         return;
     }
-    const int q = bm / band_group;
+    const int q = min(bm / band_group, n_waves - 1);
     tile_wave[t] = q;
     tile_key[t] = (q % D) * n_waves + q;
     tile_inc[t] = 0x7f7fffffu;       // FLT_MAX: visit at least once
+}
+
+__global__ void k_tile_stamps(int nt, const int32_t* __restrict__ tile_wave, int32_t* stamp) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) stamp[t] = tile_wave[t];
 }
 
 }  // namespace
@@ -555,13 +626,21 @@ int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape) {
 }
 
 cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
-                               const uint8_t* mask, float lambda, float band_w, int band_cap,
-                               int32_t* nodes, int32_t* count, int* tile_min, cudaStream_t st) {
+                               const uint8_t* mask, const float* speed, float lambda, float band_w,
+                               int band_cap, int32_t* nodes, float* slot_speed, int32_t* count,
+                               int* tile_min, cudaStream_t st) {
     count_launches(1);
     const long long threads = (long long)nt * 32;
     auto kern = shape == 3 ? k_wtile_build<4, 4> : (shape == 2 ? k_wtile_build<8, 4> : k_wtile_build<8, 8>);
-    kern<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, lambda, band_w,
-                                                        band_cap, nodes, count, tile_min);
+    kern<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, speed, lambda,
+                                                        band_w, band_cap, nodes, slot_speed, count,
+                                                        tile_min);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_stamps(int nt, const int32_t* tile_wave, int32_t* stamp, cudaStream_t st) {
+    count_launches(1);
+    k_tile_stamps<<<(nt + 255) / 256, 256, 0, st>>>(nt, tile_wave, stamp);
     return cudaGetLastError();
 }
 
