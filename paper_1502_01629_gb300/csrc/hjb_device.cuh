@@ -33,6 +33,10 @@ struct GridView {
 };
 
 template <typename T> struct RealOf;
+template <typename T> struct V2Of_;
+template <> struct V2Of_<float> { using type = float2; };
+template <> struct V2Of_<double> { using type = double2; };
+template <typename T> using V2Of = typename V2Of_<T>::type;
 template <> struct RealOf<float> {
     using V2 = float2;
     __device__ static float s(const GridView& g) { return g.s32; }
@@ -87,14 +91,45 @@ __device__ __forceinline__ NodeBox<T> node_box(int i, int j, int n) {
     return b;
 }
 
-template <typename T>
+// CLAMP = false: the caller guarantees lo < d < hi and floor(d) <= cap (the node
+// lies at least the interpolation reach inside the grid), so the projection is
+// the identity and is skipped.
+template <typename T, bool CLAMP = true>
 __device__ __forceinline__ Axis<T> axis_cell(T d, T lo, T hi, T cap) {
-    d = fmin(fmax(d, lo), hi);
-    const T fl = fmin(floor(d), cap);
+    if (CLAMP) d = fmin(fmax(d, lo), hi);
+    T fl = floor(d);
+    if (CLAMP) fl = fmin(fl, cap);
     Axis<T> a;
     a.off = (int)fl;
     a.fr = d - fl;
     a.sw = fmax(T(1) - fabs(d), T(0));
+    return a;
+}
+
+// FP32: floor by rounding.  Adding 1.5 * 2^23 with rounding toward -infinity
+// leaves floor(d) in the low mantissa bits of the sum (its ulp is 1) for
+// |d| < 2^22; the integer is read from the bits and floor(d) as a float is the
+// sum minus 1.5 * 2^23 (exact).  Same results as floor() and a conversion,
+// computed on the FMA and integer pipes instead of the conversion unit.
+template <>
+__device__ __forceinline__ Axis<float> axis_cell<float, true>(float d, float lo, float hi, float cap) {
+    constexpr float kRound = 12582912.0f;            // 1.5 * 2^23
+    d = fminf(fmaxf(d, lo), hi);
+    const float t = fminf(__fadd_rd(d, kRound), cap + kRound);
+    Axis<float> a;
+    a.off = __float_as_int(t) - 0x4B400000;          // bits of 1.5 * 2^23
+    a.fr = d - (t - kRound);
+    a.sw = fmaxf(1.0f - fabsf(d), 0.0f);
+    return a;
+}
+template <>
+__device__ __forceinline__ Axis<float> axis_cell<float, false>(float d, float, float, float) {
+    constexpr float kRound = 12582912.0f;
+    const float t = __fadd_rd(d, kRound);
+    Axis<float> a;
+    a.off = __float_as_int(t) - 0x4B400000;
+    a.fr = d - (t - kRound);
+    a.sw = fmaxf(1.0f - fabsf(d), 0.0f);
     return a;
 }
 
@@ -114,30 +149,41 @@ __device__ __forceinline__ T bilinear_rel(const Axis<T>& ax, const Axis<T>& ay, 
     return fma(ay.fr, b - a, a);
 }
 
-// For one control: Sd = (1/2d) sum_{k,s} (I[u](x_{i,k}^{a,s}) - u_i) and
-// L = (1/2d) sum_{k,s} lambda_{i0,k}^{a,s} (the self weight, Lambda0 of eq.
-// SLimplicit).  SIG = false: sigma = 0, the four points coincide with the foot.
-template <typename T, bool SIG, typename Acc>
-__device__ __forceinline__ void control_terms(const GridView& g, const NodeBox<T>& bx, T fx, T fy,
-                                              T uk, const Acc& U, T& Sd, T& L) {
+// For one control: Sd4 = sum_{k,s} (I[u](x_{i,k}^{a,s}) - u_i) and
+// L4 = sum_{k,s} lambda_{i0,k}^{a,s} (four times the self weight Lambda0 of eq.
+// SLimplicit; the 1/2d = 1/4 is applied by the caller).  SIG = false: sigma = 0,
+// the four points coincide with the foot (Sd4, L4 are then the single point's
+// terms, already "averaged").
+template <typename T, bool SIG, bool CLAMP, typename Acc>
+__device__ __forceinline__ void control_terms4(const GridView& g, const NodeBox<T>& bx, T fx, T fy,
+                                               T uk, const Acc& U, T& Sd, T& L) {
     if (SIG) {
         const T d = RealOf<T>::d(g);
-        const Axis<T> xm = axis_cell<T>(fx - d, bx.lox, bx.hix, bx.capx);
-        const Axis<T> x0 = axis_cell<T>(fx, bx.lox, bx.hix, bx.capx);
-        const Axis<T> xp = axis_cell<T>(fx + d, bx.lox, bx.hix, bx.capx);
-        const Axis<T> ym = axis_cell<T>(fy - d, bx.loy, bx.hiy, bx.capy);
-        const Axis<T> y0 = axis_cell<T>(fy, bx.loy, bx.hiy, bx.capy);
-        const Axis<T> yp = axis_cell<T>(fy + d, bx.loy, bx.hiy, bx.capy);
+        const Axis<T> xm = axis_cell<T, CLAMP>(fx - d, bx.lox, bx.hix, bx.capx);
+        const Axis<T> x0 = axis_cell<T, CLAMP>(fx, bx.lox, bx.hix, bx.capx);
+        const Axis<T> xp = axis_cell<T, CLAMP>(fx + d, bx.lox, bx.hix, bx.capx);
+        const Axis<T> ym = axis_cell<T, CLAMP>(fy - d, bx.loy, bx.hiy, bx.capy);
+        const Axis<T> y0 = axis_cell<T, CLAMP>(fy, bx.loy, bx.hiy, bx.capy);
+        const Axis<T> yp = axis_cell<T, CLAMP>(fy + d, bx.loy, bx.hiy, bx.capy);
         Sd = (bilinear_rel<T>(xp, y0, uk, U) + bilinear_rel<T>(xm, y0, uk, U)) +
              (bilinear_rel<T>(x0, yp, uk, U) + bilinear_rel<T>(x0, ym, uk, U));
         L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
-        Sd *= T(0.25);
-        L *= T(0.25);
     } else {
-        const Axis<T> x0 = axis_cell<T>(fx, bx.lox, bx.hix, bx.capx);
-        const Axis<T> y0 = axis_cell<T>(fy, bx.loy, bx.hiy, bx.capy);
+        const Axis<T> x0 = axis_cell<T, CLAMP>(fx, bx.lox, bx.hix, bx.capx);
+        const Axis<T> y0 = axis_cell<T, CLAMP>(fy, bx.loy, bx.hiy, bx.capy);
         Sd = bilinear_rel<T>(x0, y0, uk, U);
         L = x0.sw * y0.sw;
+    }
+}
+
+// Sd and L with the 1/2d = 1/4 applied (for callers that need the terms).
+template <typename T, bool SIG, bool CLAMP = true, typename Acc>
+__device__ __forceinline__ void control_terms(const GridView& g, const NodeBox<T>& bx, T fx, T fy,
+                                              T uk, const Acc& U, T& Sd, T& L) {
+    control_terms4<T, SIG, CLAMP>(g, bx, fx, fy, uk, U, Sd, L);
+    if (SIG) {
+        Sd *= T(0.25);
+        L *= T(0.25);
     }
 }
 
@@ -148,43 +194,60 @@ __device__ __forceinline__ void control_terms(const GridView& g, const NodeBox<T
 //   scheme 2 (eq. SLscheme2):
 //       beta S + h l - uk = beta Sd + c0,
 // so each candidate is a fraction N/D (D > 0) and candidates are compared by
-// cross-multiplication; the new value is uk + N*/D*.
+// cross-multiplication; the new value is uk + N*/D*.  With sigma > 0 the 1/4 is
+// folded into beta (beta/4 times the four-point sums; a power-of-two scaling,
+// so the products are the same numbers).
 template <typename T>
 __device__ __forceinline__ bool better(T na, T da, int ma, T nb, T db, int mb) {
     const T l = na * db, r = nb * da;
     return (l < r) || (l == r && ma < mb);
 }
 
+template <typename T, bool SIG, bool CLAMP, typename Acc>
+__device__ __forceinline__ void candidate(const GridView& g, int scheme, const NodeBox<T>& box, T s,
+                                          T bq, T c0, T uk, T c, T bx, T by, const V2Of<T>& a,
+                                          const Acc& U, T& N, T& D) {
+    const T fx = s * fma(c, (T)a.x, bx);
+    const T fy = s * fma(c, (T)a.y, by);
+    T Sd, L;
+    control_terms4<T, SIG, CLAMP>(g, box, fx, fy, uk, U, Sd, L);
+    N = fma(bq, Sd, c0);
+    D = T(1);
+    if (scheme == 3) {
+        D = fma(-bq, L, T(1));
+        if (!(D > T(0))) {
+            N = T(INFINITY);
+            D = T(1);
+        }
+    }
+}
+
 // Evaluate every control handled by this thread (m = m0, m0+stride, ...) for
 // node (i, j) with value uk, speed c, drift (bx, by); returns the best
 // increment as a fraction N/D and its control index (ties: lowest index).
-template <typename T, bool SIG, typename CtrlFn, typename Acc>
+template <typename T, bool SIG, bool CLAMP = true, typename CtrlFn, typename Acc>
 __device__ __forceinline__ void best_over_controls(const GridView& g, int scheme, int i, int j,
                                                    T uk, T c, T bx, T by, int m0, int stride,
                                                    const CtrlFn& ctrl, const Acc& U,
                                                    T& bestN, T& bestD, int& bestM) {
     const T s = RealOf<T>::s(g);
     const T beta = RealOf<T>::beta(g);
+    const T bq = SIG ? beta * T(0.25) : beta;
     const T c0 = fma(-(T(1) - beta), uk, RealOf<T>::hl(g));
     const NodeBox<T> box = node_box<T>(i, j, g.n);
     bestN = T(INFINITY);
     bestD = T(1);
     bestM = 0x7fffffff;
-    for (int m = m0; m < g.na; m += stride) {
-        const auto a = ctrl(m);
-        const T fx = s * fma(c, (T)a.x, bx);
-        const T fy = s * fma(c, (T)a.y, by);
-        T Sd, L;
-        control_terms<T, SIG>(g, box, fx, fy, uk, U, Sd, L);
-        T N = fma(beta, Sd, c0);
-        T D = T(1);
-        if (scheme == 3) {
-            D = fma(-beta, L, T(1));
-            if (!(D > T(0))) {
-                N = T(INFINITY);
-                D = T(1);
-            }
-        }
+    int m = m0;
+    if (m < g.na) {
+        // first control: taken without comparison
+        candidate<T, SIG, CLAMP>(g, scheme, box, s, bq, c0, uk, c, bx, by, ctrl(m), U, bestN, bestD);
+        bestM = bestN < T(INFINITY) ? m : 0x7fffffff;   // an excluded candidate is not taken
+        m += stride;
+    }
+    for (; m < g.na; m += stride) {
+        T N, D;
+        candidate<T, SIG, CLAMP>(g, scheme, box, s, bq, c0, uk, c, bx, by, ctrl(m), U, N, D);
         if (N * bestD < bestN * D) {
             bestN = N;
             bestD = D;

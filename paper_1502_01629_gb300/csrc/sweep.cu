@@ -51,6 +51,9 @@ k_sweep_tile(GridView g, int scheme, int R, const T* __restrict__ uin, T* __rest
     }
     __syncthreads();
 
+    // staged window inside the grid: every point of every node stays inside the
+    // square, so the projection is skipped
+    const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + W <= n && gy0 + H <= n;
     T lmax = T(0);
 #pragma unroll 1
     for (int r = 0; r < kTileY / kBlockY; ++r) {
@@ -76,7 +79,10 @@ k_sweep_tile(GridView g, int scheme, int R, const T* __restrict__ uin, T* __rest
             auto C = [&](int m) { return sctrl[m]; };
             T N, D;
             int M;
-            best_over_controls<T, SIG>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
+            if (interior)
+                best_over_controls<T, SIG, false>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
+            else
+                best_over_controls<T, SIG, true>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
             const T du = N / D;
             out = uk + du;
             am = M;

@@ -16,6 +16,8 @@
 // than the tolerance.  All patches share one array (sharp interfaces), so the
 // transmission condition is the identity; values written by other blocks are
 // read through L2 (ld.global.cg).
+#include <type_traits>
+
 #include "hjb_kernels.h"
 
 namespace hjb {
@@ -293,7 +295,11 @@ k_wtiles(TileArgs a, T* u) {
             float tmax = 0.0f;
             int old = 0x7fffffff;    // stamp before this visit claimed the neighbour
             bool claimed = false;
-            for (int sw = 0; sw < a.local_sweeps; ++sw) {
+            // staged window inside the grid: the projection is the identity
+            const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + W <= n && gy0 + H <= n;
+            auto visit = [&](auto clamp_tag) {
+              constexpr bool CL = decltype(clamp_tag)::value;
+              for (int sw = 0; sw < a.local_sweeps; ++sw) {
                 for (int q = 0; q < nn; ++q) {
                     const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
                     const T c = (T)__shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
@@ -310,8 +316,8 @@ k_wtiles(TileArgs a, T* u) {
                     auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
                     T N, Dn;
                     int M;
-                    best_over_controls<T, SIG>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C, U, N,
-                                               Dn, M);
+                    best_over_controls<T, SIG, CL>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C,
+                                                   U, N, Dn, M);
                     T du;
                     if constexpr (sizeof(T) == 4) {
                         du = warp_min_increment(N, Dn, M);
@@ -333,7 +339,12 @@ k_wtiles(TileArgs a, T* u) {
                         }
                     }
                 }
-            }
+              }
+            };
+            if (interior)
+                visit(std::false_type{});
+            else
+                visit(std::true_type{});
             // write back this tile's free nodes
             if (lane < nn) st_l2(u + (size_t)(bj + e0 / TW) * n + bi + e0 % TW,
                                  su[(R + e0 / TW) * W + (R + e0 % TW)]);
