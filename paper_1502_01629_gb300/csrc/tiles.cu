@@ -192,6 +192,65 @@ k_tiles(TileArgs a, T* u) {
     }
 }
 
+// ------------------------------------------- FP32 node-control geometry
+// Everything of one node-control candidate that does not depend on u: the
+// shared-memory index of the first vertex of each point's Q1 cell, the cell
+// fractions and the reciprocal of the denominator D = 1 - beta L (scheme 3;
+// -1 marks an excluded candidate, D <= 0).  Split out so the geometry of the
+// next node can be formed while the current node's gathers, warp reduction and
+// store are in flight.  Same arithmetic as control_terms4 and candidate().
+template <bool SIG>
+struct Geo32 {
+    int o[SIG ? 4 : 1];       // SIG: (xp, y0), (xm, y0), (x0, yp), (x0, ym)
+    float fx[SIG ? 3 : 1];    // SIG: xp, xm, x0
+    float fy[SIG ? 3 : 1];    // SIG: y0, yp, ym
+    float rD;
+};
+
+template <bool SIG, bool CLAMP>
+__device__ __forceinline__ Geo32<SIG> geo32(const GridView& g, int scheme, float s, float bq, int i,
+                                            int j, int kb, int W, float c, float2 a) {
+    Geo32<SIG> r;
+    const NodeBox<float> box = node_box<float>(i, j, g.n);
+    const float fx = s * (c * a.x);
+    const float fy = s * (c * a.y);
+    float L;
+    if constexpr (SIG) {
+        const float d = g.d32;
+        const Axis<float> xm = axis_cell<float, CLAMP>(fx - d, box.lox, box.hix, box.capx);
+        const Axis<float> x0 = axis_cell<float, CLAMP>(fx, box.lox, box.hix, box.capx);
+        const Axis<float> xp = axis_cell<float, CLAMP>(fx + d, box.lox, box.hix, box.capx);
+        const Axis<float> ym = axis_cell<float, CLAMP>(fy - d, box.loy, box.hiy, box.capy);
+        const Axis<float> y0 = axis_cell<float, CLAMP>(fy, box.loy, box.hiy, box.capy);
+        const Axis<float> yp = axis_cell<float, CLAMP>(fy + d, box.loy, box.hiy, box.capy);
+        r.o[0] = kb + y0.off * W + xp.off;
+        r.o[1] = kb + y0.off * W + xm.off;
+        r.o[2] = kb + yp.off * W + x0.off;
+        r.o[3] = kb + ym.off * W + x0.off;
+        r.fx[0] = xp.fr; r.fx[1] = xm.fr; r.fx[2] = x0.fr;
+        r.fy[0] = y0.fr; r.fy[1] = yp.fr; r.fy[2] = ym.fr;
+        L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
+    } else {
+        const Axis<float> x0 = axis_cell<float, CLAMP>(fx, box.lox, box.hix, box.capx);
+        const Axis<float> y0 = axis_cell<float, CLAMP>(fy, box.loy, box.hiy, box.capy);
+        r.o[0] = kb + y0.off * W + x0.off;
+        r.fx[0] = x0.fr;
+        r.fy[0] = y0.fr;
+        L = x0.sw * y0.sw;
+    }
+    const float D = scheme == 3 ? fmaf(-bq, L, 1.0f) : 1.0f;
+    r.rD = D > 0.0f ? __frcp_rn(D) : -1.0f;
+    return r;
+}
+
+// Q1 value at a point minus uk from the vertex block at su[o] (row stride W).
+__device__ __forceinline__ float bil32(const float* su, int o, int W, float frx, float fry, float uk) {
+    const float v00 = su[o], v10 = su[o + 1], v01 = su[o + W], v11 = su[o + W + 1];
+    const float a = fmaf(frx, v10 - v00, v00 - uk);
+    const float b = fmaf(frx, v11 - v01, v01 - uk);
+    return fmaf(fry, b - a, a);
+}
+
 // ------------------------------------------------- one warp per TW x TH tile
 // Each warp owns one tile per visit: it stages the tile and its halo in its own
 // slice of shared memory and updates the tile's free nodes one after another in
@@ -341,10 +400,74 @@ k_wtiles(TileArgs a, T* u) {
                 }
               }
             };
-            if (interior)
-                visit(std::false_type{});
-            else
-                visit(std::true_type{});
+            // FP32, no drift, at most one control per lane: the geometry of node
+            // q + 1 is formed during node q (software pipelining)
+            auto visit32 = [&](auto clamp_tag) {
+              constexpr bool CL = decltype(clamp_tag)::value;
+              const float s = g.s32, beta = g.beta32, hl = g.hl32;
+              const float bq = SIG ? beta * 0.25f : beta;
+              const float omb = 1.0f - beta;
+              const bool has = lane < g.na;
+              const float2 ac = has ? g.ctrl32[lane] : make_float2(0.0f, 0.0f);
+              auto node_geo = [&](int q, int& kb) {
+                  const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
+                  const float c = __shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
+                  const int ex = e % TW, ey = e / TW;
+                  kb = (R + ey) * W + (R + ex);
+                  return geo32<SIG, CL>(g, a.scheme, s, bq, bi + ex, bj + ey, kb, W, c, ac);
+              };
+              float* sf = reinterpret_cast<float*>(su);
+              for (int sw = 0; sw < a.local_sweeps; ++sw) {
+                int kbn;
+                Geo32<SIG> gn = node_geo(0, kbn);
+                for (int q = 0; q < nn; ++q) {
+                    const Geo32<SIG> gc = gn;
+                    const int kb = kbn;
+                    gn = node_geo(min(q + 1, nn - 1), kbn);
+                    const float uk = sf[kb];
+                    const float cc0 = fmaf(-omb, uk, hl);
+                    float Sd;
+                    if constexpr (SIG) {
+                        Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
+                              bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
+                             (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
+                              bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
+                    } else {
+                        Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
+                    }
+                    const float N = fmaf(bq, Sd, cc0);
+                    const float v = (has && gc.rD > 0.0f) ? N * gc.rD : INFINITY;
+                    const float du = order_val(__reduce_min_sync(0xffffffffu, order_key(v)));
+                    if (lane == 0) sf[kb] = uk + du;
+                    __syncwarp();
+                    tmax = fmaxf(tmax, fabsf(du));
+                    if (!claimed && tmax > a.tol) {
+                        claimed = true;
+                        if (nbw >= 0) {
+                            const int tgt = step + 1 + ((nbw - step - 1) % D + D) % D;
+                            const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
+                            old = atomicMax(a.stamp + ny * a.ntx + nx, tgt);
+                        }
+                    }
+                }
+              }
+            };
+            bool piped = false;
+            if constexpr (sizeof(T) == 4) {
+                if (g.drift == nullptr && g.na <= 32) {
+                    piped = true;
+                    if (interior)
+                        visit32(std::false_type{});
+                    else
+                        visit32(std::true_type{});
+                }
+            }
+            if (!piped) {
+                if (interior)
+                    visit(std::false_type{});
+                else
+                    visit(std::true_type{});
+            }
             // write back this tile's free nodes
             if (lane < nn) st_l2(u + (size_t)(bj + e0 / TW) * n + bi + e0 % TW,
                                  su[(R + e0 / TW) * W + (R + e0 % TW)]);
