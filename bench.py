@@ -14,6 +14,11 @@ the time to FP64 residual 1e-6 of the patchy path and of plain full-grid FP32
 Jacobi value iteration (the comparator) on the same GPU reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload patchy1025|large4097]
+
+--workload large4097 runs the 4097^2 workload instead (random Fourier speed,
+six rectangular obstacles, 64 controls, sigma = 0.01, 64 patches; one patchy
+solve per step, the plain Jacobi comparator timed once).
 
 N > 1 runs under torchrun, one rank per GPU; every rank solves the same
 workload (independent replicas, weak scaling) and rank 0 prints one JSON line.
@@ -39,7 +44,10 @@ import hjb_inputs as hi  # noqa: E402
 
 SIGMAS = (0.0, 0.02, 0.1)
 N_FINE, N_COARSE, N_PATCH = 1025, 129, 16
-TOL32, TOL64, TOL_C = 5e-7, 1e-6, 1e-6
+# FP32 pass tolerance a quarter of the FP64 residual target: the FP32 stop
+# (sup-increment of the last tile visits) then leaves the FP64 residual below
+# the target without extra phases
+TOL32, TOL64, TOL_C = 2.5e-7, 1e-6, 1e-6
 METRIC = "time to 1e-6 residual vs plain GPU value iteration; node·control updates/s"
 UNIT = "node·control updates/s"
 SOLVER_KW = dict(schedule=0, tile_shape=-1, tile_waves=0, tile_period=2, local_sweeps=1)
@@ -156,8 +164,23 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- workload
 
+WORKLOAD = "patchy1025"
+WORKLOAD_DESC = {
+    "patchy1025": "patchy 1025x1025, c=1+0.5sin(2pi x1)sin(2pi x2), disc |x|<=0.1, "
+                  "32 controls, lambda=1, h=dx, coarse 129x129, 16 patches, "
+                  "sigma in {0,0.02,0.1}, FP32 passes + FP64 residual <= 1e-6",
+    "large4097": "large 4097x4097, random Fourier speed in [0.2,1.8], 6 rectangular "
+                 "obstacles (speed 0), disc |x|<=0.1, 64 controls, sigma=0.01, lambda=1, "
+                 "h=dx, coarse 129x129, 64 patches, FP32 passes + FP64 residual <= 1e-6",
+}
+
+
 def make_instances():
-    return [hi.patchy_1025(s, n=N_FINE, coarse_n=N_COARSE, n_patches=N_PATCH) for s in SIGMAS]
+    """(label, instance) pairs of one step."""
+    if WORKLOAD == "large4097":
+        return [("0.01", hi.large_instance(n=N_FINE, coarse_n=N_COARSE))]
+    return [(f"{s}", hi.patchy_1025(s, n=N_FINE, coarse_n=N_COARSE, n_patches=N_PATCH))
+            for s in SIGMAS]
 
 
 def set_size(n: int, coarse_n: int):
@@ -191,7 +214,9 @@ def ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
     stream = torch.cuda.current_stream()
-    insts = make_instances()
+    labeled = make_instances()
+    labels = [lb for lb, _ in labeled]
+    insts = [inst for _, inst in labeled]
     n_free = [int((i.mask == 0).sum()) for i in insts]
     probs = [Problem.from_instance(inst, stream=stream, **SOLVER_KW) for inst in insts]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
@@ -199,7 +224,7 @@ def ours(args, ws, rank, local):
     def step(record=None):
         total_nc = 0
         per = []
-        for P, sig, nf in zip(probs, SIGMAS, n_free):
+        for P, sig, nf in zip(probs, labels, n_free):
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -217,7 +242,7 @@ def ours(args, ws, rank, local):
     torch.cuda.synchronize()
 
     launches0 = kernel_launches()
-    step_ms, total_nc, by_sigma = [], 0, {s: [] for s in SIGMAS}
+    step_ms, total_nc, by_sigma = [], 0, {s: [] for s in labels}
     last_stats = {}
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -244,9 +269,11 @@ def ours(args, ws, rank, local):
 
     # ---- plain full-grid FP32 Jacobi comparator (same GPU, same tolerances)
     plain = {}
-    for P, sig in zip(probs, SIGMAS):
+    for P, sig in zip(probs, labels):
         ts = []
-        for r in range(1 + args.plain_reps):
+        # one untimed run first, except on the large grid (a run of seconds)
+        warm_runs = 0 if WORKLOAD == "large4097" else 1
+        for r in range(warm_runs + max(1, args.plain_reps)):
             flush_l2(torch, flush)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -254,7 +281,7 @@ def ours(args, ws, rank, local):
             st = P.solve_full(precision=32, tol=TOL32, tol64=TOL64)
             e1.record(stream)
             torch.cuda.synchronize()
-            if r > 0:
+            if r >= warm_runs:
                 ts.append(e0.elapsed_time(e1))
         plain[sig] = dict(ms=statistics.median(ts), sweeps=st["sweeps"],
                           fp64_sweeps=st["fp64_passes"], residual=st["residual"],
@@ -262,11 +289,11 @@ def ours(args, ws, rank, local):
 
     # ---- dominant kernel: the band-wave FP32 passes (stage 0 of solve_patches)
     wave_ms, wave_flops = 0.0, 0.0
-    for sig in SIGMAS:
+    for sig, inst in zip(labels, insts):
         c, b, s = last_stats[sig]
         wave_ms += s["ms_stage"][0]
         nodes32 = s["node_updates"] - s["fp64_node_updates"]
-        wave_flops += nodes32 * 32 * flops_per_node_control(sig)
+        wave_flops += nodes32 * inst.n_controls * flops_per_node_control(inst.sigma)
     peaks = load_peaks()
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
     achieved = wave_flops / (wave_ms / 1e3) / 1e12 if wave_ms > 0 else 0.0
@@ -310,19 +337,20 @@ def ours(args, ws, rank, local):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {
-            "workload": "patchy 1025x1025, c=1+0.5sin(2pi x1)sin(2pi x2), disc |x|<=0.1, "
-                        "32 controls, lambda=1, h=dx, coarse 129x129, 16 patches, "
-                        "sigma in {0,0.02,0.1}, FP32 passes + FP64 residual <= 1e-6",
-            "n": N_FINE, "coarse_n": N_COARSE, "n_patches": N_PATCH, "n_controls": 32,
-            "sigmas": list(SIGMAS), "tol32": TOL32, "tol64_residual": TOL64,
+            "workload": WORKLOAD_DESC[WORKLOAD],
+            "n": N_FINE, "coarse_n": N_COARSE, "n_patches": insts[0].n_patches,
+            "n_controls": insts[0].n_controls,
+            "sigmas": [i.sigma for i in insts], "tol32": TOL32, "tol64_residual": TOL64,
             "solver": SOLVER_KW,
-            "l2": "flushed between timed steps (256 MiB write); working set < L2",
+            "l2": ("flushed between timed steps (256 MiB write); working set < L2"
+                   if WORKLOAD == "patchy1025" else
+                   "flushed between timed steps (256 MiB write); working set > L2"),
             "parallelism": f"replicas x{ws}",
         },
         "time_to_1e-6_ms": {
-            "patchy": {str(s): patchy_ms[s] for s in SIGMAS},
-            "plain_jacobi_fp32": {str(s): plain[s]["ms"] for s in SIGMAS},
-            "speedup_vs_plain": {str(s): plain[s]["ms"] / patchy_ms[s] for s in SIGMAS},
+            "patchy": {str(s): patchy_ms[s] for s in labels},
+            "plain_jacobi_fp32": {str(s): plain[s]["ms"] for s in labels},
+            "speedup_vs_plain": {str(s): plain[s]["ms"] / patchy_ms[s] for s in labels},
         },
         "solver_stats": {
             str(s): {
@@ -338,7 +366,7 @@ def ours(args, ws, rank, local):
                 "plain_sweeps": plain[s]["sweeps"],
                 "plain_fp64_sweeps": plain[s]["fp64_sweeps"],
                 "plain_residual": plain[s]["residual"],
-            } for s in SIGMAS},
+            } for s in labels},
         "roofline": {
             "kernel": "k_wtiles<float> (warp-tile pipelined FP32 passes)",
             "bound": "alu",
@@ -356,7 +384,8 @@ def ours(args, ws, rank, local):
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds,
+                                           insts[1] if len(insts) > 1 else insts[0])
     return out
 
 
@@ -372,28 +401,30 @@ def load_peaks() -> dict:
 # ------------------------------------------------------------- CPU oracle leg
 
 def cpu_baseline(seconds: float, inst=None) -> dict:
-    """The FP64 oracle as it stands (single-threaded Gauss-Seidel sweeps of the
-    modified scheme) on a bounded sample of the workload: whole sweeps over the
-    sigma = 0.02 instance from u_hat-free start u = 0, as many as fit in about
-    `seconds` seconds."""
+    """The FP64 oracle as it stands (single-threaded Gauss-Seidel updates of the
+    modified scheme) on a bounded sample of the workload: repeated Gauss-Seidel
+    passes over the first rows of the grid (at most 2^20 nodes, from u = 0), as
+    many as fit in about `seconds` seconds."""
     import oracle
     if inst is None:
         inst = hi.patchy_1025(0.02, n=N_FINE, coarse_n=N_COARSE, n_patches=N_PATCH)
     O = oracle.Problem.from_instance(inst)
     u = O.fix_nonfree(np.zeros(O.N))
-    nfree = int((inst.mask == 0).sum())
-    sweeps = 0
+    rows = np.arange(0, min(O.N, 1 << 20), dtype=np.int64)
+    nodes = int((inst.mask[rows] == 0).sum())
+    passes = 0
     t0 = time.perf_counter()
     while True:
-        O.sweep_gs(u, 3)
-        sweeps += 1
+        O.sweep_gs(u, 3, rows)
+        passes += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": nfree * inst.n_controls * sweeps / dt, "unit": UNIT, "cores": 1,
+    return {"value": nodes * inst.n_controls * passes / dt, "unit": UNIT, "cores": 1,
             "kind": "oracle",
-            "sample": f"{sweeps} Gauss-Seidel sweep(s) of the FP64 oracle over the 1025^2 "
-                      f"sigma=0.02 instance ({nfree} free nodes x 32 controls), {dt:.1f} s"}
+            "sample": f"{passes} Gauss-Seidel pass(es) of the FP64 oracle over the first "
+                      f"{rows.size} nodes of {inst.name} ({nodes} free nodes x "
+                      f"{inst.n_controls} controls), {dt:.1f} s"}
 
 
 def reference(args, ws, rank, local):
@@ -437,11 +468,16 @@ def main(argv=None):
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=N_FINE, help="fine grid size (profiling only)")
+    ap.add_argument("--workload", choices=("patchy1025", "large4097"), default="patchy1025",
+                    help="patchy1025: the 1025^2 three-sigma workload (default); large4097: "
+                         "the 4097^2 64-control workload with obstacles")
+    ap.add_argument("--n", type=int, default=0, help="fine grid size (profiling only)")
     ap.add_argument("--coarse-n", type=int, default=N_COARSE)
     args = ap.parse_args(argv)
-    if (args.n, args.coarse_n) != (N_FINE, N_COARSE):
-        set_size(args.n, args.coarse_n)
+    global WORKLOAD
+    WORKLOAD = args.workload
+    n_default = 4097 if WORKLOAD == "large4097" else N_FINE
+    set_size(args.n or n_default, args.coarse_n)
     if args.warmup < 3 and args.impl == "ours":
         print("bench.py: --warmup must be >= 3", file=sys.stderr)
     ws, rank, local = dist_env()

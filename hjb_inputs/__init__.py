@@ -249,6 +249,35 @@ def batched_instance(seed: int, n: Optional[int] = None) -> Instance:
                     name=f"batched-seed{seed}-n{n}")
 
 
+def large_instance(seed: int = 5000, n: int = 4097, coarse_n: int = 129,
+                   n_patches: int = 64, sigma: float = 0.01, n_obstacles: int = 6) -> Instance:
+    """The large workload: n = 4097, random Fourier speed clipped to [0.2, 1.8],
+    64 controls, sigma = 0.01, lambda = 1, h = dx, target disc |x| <= 0.1,
+    6 seeded axis-aligned rectangular obstacles (sides 0.08-0.35, at least 0.25
+    from the origin; speed 0 there, nodes held at the obstacle value), 64 sectors.
+    Smaller n (with (n-1) divisible by (coarse_n-1)) gives the same recipe at
+    test sizes."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    speed = speed_fourier(n, rng)
+    mask = disc_target(n, [(0.0, 0.0)], [0.1])
+    rects = []
+    while len(rects) < n_obstacles:
+        w, hh = rng.uniform(0.08, 0.35, 2)
+        cx, cy = rng.uniform(-0.85, 0.85, 2)
+        gx = max(abs(cx) - w / 2, 0.0)
+        gy = max(abs(cy) - hh / 2, 0.0)
+        if math.hypot(gx, gy) < 0.25:
+            continue
+        rects.append((cx - w / 2, cy - hh / 2, cx + w / 2, cy + hh / 2))
+    mask = add_rect_obstacles(n, mask, rects)
+    speed = speed.copy()
+    speed[mask == MASK_OBSTACLE] = 0.0
+    sec = sectors_about_centres(n, mask, [(0.0, 0.0)], n_patches)
+    return Instance(n=n, controls=control_set(64), speed=speed, mask=mask, sector=sec,
+                    lam=1.0, sigma=sigma, coarse_n=coarse_n, n_patches=n_patches,
+                    name=f"large-seed{seed}-n{n}")
+
+
 def random_values(n: int, seed: int, lo: float = 0.0, hi: float = 1.0,
                   mask: Optional[np.ndarray] = None) -> np.ndarray:
     """A seeded random value field (float64, n*n) for operator-level tests; target

@@ -89,7 +89,8 @@ typedef struct {
     int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 2)         */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
     int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (8x8 when the
-                             diffusion offset exceeds one cell, else 8x4)                     */
+                             diffusion offset exceeds one cell, n > 2049 or more than 32
+                             controls, else 8x4)                                              */
     int32_t reserved;     /* must be 0                                                        */
 } hjb_desc;
 
@@ -209,8 +210,13 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
  * (band waves): band_group bands per grid-wide wave, nodes taken in sorted order
  * by the wave_warps warps in flight; passes after the first skip groups whose
  * neighbourhood did not change.  FP32 until a
- * pass's sup-increment is <= tol32; then, if tol64 > 0, FP64 passes until the
- * FP64 sup-residual ||T2 u - u|| is <= tol64.  max_passes caps each phase.
+ * pass's sup-increment is <= tol32; then, if tol64 > 0, the FP64 sup-residual
+ * ||T2 u - u|| is evaluated; if it exceeds tol64 while tol64 is at least 2^-22
+ * max(1, u_max), at most two more FP32 phases run from the current value with
+ * the tolerance divided by 4 each time while it stays >= 2^-21 max(1, u_max)
+ * (schedule 0, every tile visited in the first two steps in checkerboard
+ * order); then FP64 passes until the FP64
+ * sup-residual is <= tol64.  max_passes caps each phase.
  * ms_stage: [0] FP32 passes, [1] promotion + residuals, [2] FP64 passes.
  * Errors: HJB_ERR_STATE (build_patches not run), HJB_ERR_NOT_CONVERGED,
  * HJB_ERR_TIMEOUT (a grid-wide wait exceeded its limit). */

@@ -159,6 +159,11 @@ struct hjb_problem {
     int32_t* wt_stamp = nullptr;   // per-tile queue stamps (warp tiles)
     int32_t* wt_queue = nullptr;   // (tile_period + 2) x nt queued tiles
     int32_t* wt_qcount = nullptr;  // tile_period + 2 queue lengths
+    int32_t* cb_wave = nullptr;    // warm restart: checkerboard wave (0/1) of each tile
+    int32_t* cb_key = nullptr;
+    int32_t* cb_list = nullptr;    // tiles sorted by checkerboard wave
+    int32_t* cb_off = nullptr;     // 3 offsets
+    int32_t* cb_count = nullptr;   // 2 counters (sort scratch)
     int32_t* sched_count = nullptr;
     int32_t* sched_off = nullptr;
     int32_t* res_off = nullptr;
@@ -367,10 +372,13 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         // past one cell the scheme couples nodes of equal value (no upwind
         // diffusion ball, Section 4.1) and 8x8 tiles in single-band waves are
         // faster; otherwise 8x4 tiles in two-band waves (measured on the
-        // 1025^2 workload)
+        // 1025^2 workload and on the 4097^2 / 64-control workload); grids above 2049^2 or more
+        // than 32 controls keep enough tiles in flight per step that the larger
+        // 8x8 tiles (half the halo staging per node) win there too
         const double dcell = std::sqrt(2.0 * p->h) * p->sigma / p->dx;
         const bool wide = dcell > 1.0;
-        if (p->desc.tile_shape < 0) p->desc.tile_shape = wide ? 0 : 1;
+        const bool big = desc->n > 2049 || desc->n_controls > 32;
+        if (p->desc.tile_shape < 0) p->desc.tile_shape = (wide || big) ? 0 : 1;
         if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
     }
     p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
@@ -483,6 +491,11 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             CUP(cudaMalloc(&p->wt_stamp, nt * sizeof(int32_t)));
             CUP(cudaMalloc(&p->wt_queue, (p->desc.tile_period + 2) * nt * sizeof(int32_t)));
             CUP(cudaMalloc(&p->wt_qcount, (p->desc.tile_period + 2) * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->cb_wave, nt * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->cb_key, nt * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->cb_list, nt * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->cb_off, 3 * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->cb_count, 2 * sizeof(int32_t)));
         } else {
             CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
             CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
@@ -716,13 +729,25 @@ int build_tiles(hjb_problem* p, const float* key_val) {
                          p->tile_inc, p->st));
     CU(launch_counting_sort(p->nt, p->tile_key, bins, p->sched_count, p->sched_off, p->tile_list,
                             p->st));
-    if (p->desc.schedule != 0)
+    if (p->desc.schedule != 0) {
         CU(launch_strided_gather(D, p->n_waves, p->sched_off, p->res_off, p->st));
+    } else {
+        // warm-restart schedule: tiles with free nodes in two checkerboard waves
+        CU(launch_checker_waves(p->nt, p->ntx, p->wt_count, p->cb_wave, p->cb_key, p->st));
+        CU(launch_counting_sort(p->nt, p->cb_key, 2, p->cb_count, p->cb_off, p->cb_list, p->st));
+    }
     return HJB_OK;
 }
 
-// Tile-pipelined passes on u32 (f64 = false) or u64 (f64 = true).
-int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out) {
+// Tile-pipelined passes on u32 (f64 = false) or u64 (f64 = true).  warm (warp
+// tiles only): every tile is visited in the first two steps, in checkerboard
+// order, instead of along the causal waves -- for a value already close to
+// the fixed point.
+int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out,
+              bool warm = false) {
+    warm = warm && p->desc.schedule == 0;
+    const int32_t* waves = warm ? p->cb_wave : p->tile_wave;
+    const int n_waves = warm ? 2 : p->n_waves;
     Scalars* ds = dscal(p);
     const int B = p->desc.tile_waves, D = p->desc.tile_period;
     CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
@@ -731,7 +756,7 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     if (p->desc.schedule == 0) {
         // empty queues; no tile is queued for a step up to its own wave
         CU(cudaMemsetAsync(p->wt_qcount, 0, sizeof(int32_t) * (D + 2), p->st));
-        CU(launch_tile_stamps(p->nt, p->tile_wave, p->wt_stamp, p->st));
+        CU(launch_tile_stamps(p->nt, waves, p->wt_stamp, p->st));
     } else {
         // every tile with free nodes starts as changed
         CU(launch_tile_waves(p->nt, p->tile_min, B, D, p->n_waves, p->tile_wave, p->tile_key,
@@ -746,11 +771,11 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.nodes = a.warp_tiles ? p->wt_nodes : p->tile_nodes;
     a.bin_off = p->tile_bin_off;
     a.wt_count = p->wt_count;
-    a.tile_list = p->tile_list;
+    a.tile_list = warm ? p->cb_list : p->tile_list;
     a.res_off = p->res_off;
-    a.tile_wave = p->tile_wave;
+    a.tile_wave = waves;
     a.tile_inc = p->tile_inc;
-    a.wave_off = p->sched_off;
+    a.wave_off = warm ? p->cb_off : p->sched_off;
     a.slot_speed = p->wt_speed;
     a.stamp = p->wt_stamp;
     a.queue = p->wt_queue;
@@ -759,10 +784,10 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.step_inc = p->step_inc;
     a.ntx = p->ntx;
     a.nty = p->nty;
-    a.n_waves = p->n_waves;
+    a.n_waves = n_waves;
     a.period = D;
     a.local_sweeps = p->desc.local_sweeps;
-    a.max_steps = p->n_waves + max_passes * D;
+    a.max_steps = n_waves + max_passes * D;
     a.tol = (float)tol;
     a.sync = &ds->sync;
     a.res = &ds->wave;
@@ -791,9 +816,10 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
 }
 
 // One solve phase with the selected schedule.
-int run_phase(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out) {
+int run_phase(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* out,
+              bool warm = false) {
     return p->desc.schedule == 1 ? run_waves(p, f64, tol, max_passes, out)
-                                 : run_tiles(p, f64, tol, max_passes, out);
+                                 : run_tiles(p, f64, tol, max_passes, out, warm);
 }
 
 // Re-sort the free nodes by the current FP32 value (keys from u32, labels kept).
@@ -903,7 +929,8 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->tile_min); dfree(p->tile_wave); dfree(p->tile_key); dfree(p->tile_list);
     dfree(p->tile_inc); dfree(p->tile_key2); dfree(p->tile_nodes); dfree(p->tile_bin_count);
     dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->wt_speed);
-    dfree(p->wt_stamp); dfree(p->wt_queue); dfree(p->wt_qcount); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
+    dfree(p->wt_stamp); dfree(p->wt_queue); dfree(p->wt_qcount);
+    dfree(p->cb_wave); dfree(p->cb_key); dfree(p->cb_list); dfree(p->cb_off); dfree(p->cb_count); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
     dfree(p->step_inc);
     if (p->scratch) cudaFree(p->scratch);
     if (p->host_pinned) cudaFreeHost(p->host_pinned);
@@ -1080,7 +1107,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
     tm.mark();
     if (!w32.converged) rc = HJB_ERR_NOT_CONVERGED;
     double res = -1.0;
-    double ms_promote = 0.0, ms64 = 0.0;
+    double ms_promote = 0.0, ms64 = 0.0, ms_warm32 = 0.0;
     unsigned long long nodes64 = 0;
     int passes64 = 0;
     int n_res = 0;
@@ -1095,6 +1122,36 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         ++n_res;
         t2.mark();
         ms_promote += t2.ms(0, 1);
+        // The FP32 stop (sup-increment of the last visits) does not bound the
+        // residual tightly.  If the FP64 residual misses tol64 but tol64 lies
+        // well above what FP32 values can resolve (4 ulp of the largest value),
+        // tighten the FP32 tolerance and continue in FP32 from the current
+        // value (warm: every tile in the first two steps) before any FP64 pass.
+        // The tightened tolerance stays at 8 ulp or more: nearer the rounding
+        // noise of a converged FP32 field every tile would keep re-queueing.
+        const double floor32 = std::ldexp(std::max(1.0, p->uob), -22);
+        double tol_w = tol32;
+        for (int tries = 0; tries < 2 && res > tol64 && tol64 >= floor32 &&
+                            0.25 * tol_w >= 2.0 * floor32 && p->desc.schedule == 0 &&
+                            w32.passes < max_passes; ++tries) {
+            Timer tw(p->st);
+            tw.mark();
+            tol_w = 0.25 * tol_w;
+            WaveResult ww{};
+            r2 = run_phase(p, false, tol_w, max_passes - w32.passes, &ww, true);
+            if (r2) return r2;
+            w32.passes += ww.passes;
+            w32.nodes += ww.nodes;
+            last = ww.last_increment;
+            tw.mark();
+            CU(launch_promote(p->N, p->u32, p->u64, p->st));
+            r2 = residual64(p, &res);
+            if (r2) return r2;
+            ++n_res;
+            tw.mark();
+            ms_warm32 += tw.ms(0, 1);
+            ms_promote += tw.ms(1, 2);
+        }
         double tol_pass = tol64;
         while (res > tol64 && passes64 < max_passes) {
             Timer t3(p->st);
@@ -1125,7 +1182,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         stats->residual_evals = n_res;
         stats->residual = res;
         stats->increment = last;
-        stats->ms_stage[0] = tm.ms(0, 1);
+        stats->ms_stage[0] = tm.ms(0, 1) + ms_warm32;
         stats->ms_stage[1] = ms_promote;
         stats->ms_stage[2] = ms64;
         stats->ms_total = stats->ms_stage[0] + ms_promote + ms64;

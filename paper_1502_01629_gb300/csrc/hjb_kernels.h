@@ -167,6 +167,10 @@ cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* k
                                const uint8_t* mask, const float* speed, float lambda, float band_w,
                                int band_cap, int32_t* nodes, float* slot_speed, int32_t* count,
                                int* tile_min, cudaStream_t st);
+// wave[t] = (tx + ty) mod 2 for tiles with free nodes (INT_MAX otherwise), key
+// the same (-1 for empty tiles): the warm-restart schedule
+cudaError_t launch_checker_waves(int nt, int ntx, const int32_t* count, int32_t* wave,
+                                 int32_t* key, cudaStream_t st);
 // stamp[t] = tile_wave[t] (a tile is never queued for a step up to its first visit)
 cudaError_t launch_tile_stamps(int nt, const int32_t* tile_wave, int32_t* stamp, cudaStream_t st);
 int tile_threads(bool f64, int shape);

@@ -725,6 +725,21 @@ __global__ void k_tile_waves(int nt, const int* __restrict__ tile_min, int band_
     tile_inc[t] = 0x7f7fffffu;       // FLT_MAX: visit at least once
 }
 
+// checkerboard wave (tx + ty) mod 2 of each tile with free nodes; sort key
+__global__ void k_checker_waves(int nt, int ntx, const int32_t* __restrict__ count, int32_t* wave,
+                                int32_t* key) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    if (count[t] > 0) {
+        const int w = ((t % ntx) + (t / ntx)) & 1;
+        wave[t] = w;
+        key[t] = w;
+    } else {
+        wave[t] = 0x7fffffff;
+        key[t] = -1;
+    }
+}
+
 __global__ void k_tile_stamps(int nt, const int32_t* __restrict__ tile_wave, int32_t* stamp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < nt) stamp[t] = tile_wave[t];
@@ -769,6 +784,13 @@ cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* k
     kern<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, speed, lambda,
                                                         band_w, band_cap, nodes, slot_speed, count,
                                                         tile_min);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_checker_waves(int nt, int ntx, const int32_t* count, int32_t* wave,
+                                 int32_t* key, cudaStream_t st) {
+    count_launches(1);
+    k_checker_waves<<<(nt + 255) / 256, 256, 0, st>>>(nt, ntx, count, wave, key);
     return cudaGetLastError();
 }
 

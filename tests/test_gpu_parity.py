@@ -297,3 +297,87 @@ def test_every_patch_schedule_reaches_the_oracle_fixed_point(sched, sigma):
         st = G.solve_patches(tol32=3e-7, tol64=1e-12)
         assert st["residual"] <= 1e-12
         np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)
+
+
+def test_large_recipe_matches_oracle():
+    """The large workload's recipe (random Fourier speed, 64 controls, six
+    rectangular obstacles held at the obstacle value, sigma = 0.01, 64 sectors)
+    at 129^2 with a 33^2 coarse grid: the patchy solve with the automatic tile
+    schedule (8x8 tiles: more than 32 controls) meets the FP32 gate, then the
+    FP64 gate after polishing."""
+    inst = hi.large_instance(n=129, coarse_n=33)
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(scheme=3, tol=1e-13)
+    scale = max(1.0, np.abs(u_ref).max())
+    with P_gpu(inst) as G:
+        G.coarse_solve(tol_c=1e-7)
+        G.build_patches()
+        G.solve_patches(tol32=3e-7, tol64=0.0)
+        u32 = G.get_value()
+        assert np.abs(u32 - u_ref).max() <= 1e-5 * scale
+        st = G.solve_patches(tol32=3e-7, tol64=1e-12)
+        assert st["residual"] <= 1e-12
+        np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)
+        u = G.get_value()
+    assert np.all(u[inst.mask == hi.MASK_TARGET] == 0.0)
+    # obstacle nodes hold l/lambda + h l (R16); the two sides round the formula
+    # differently in the last place
+    np.testing.assert_allclose(u[inst.mask == hi.MASK_OBSTACLE], O.u_max, rtol=0, atol=1e-12)
+
+
+def test_warm_fp32_retry_reaches_the_fp64_tolerance():
+    """A loose FP32 tolerance leaves the FP64 residual above tol64; the solver
+    then continues in FP32 from the current value with tighter tolerances
+    before any FP64 pass.  The result must still satisfy the FP64 residual
+    bound and the FP32 value gate against the oracle."""
+    inst = hi.patchy_1025(0.02, n=257, coarse_n=33)
+    O = oracle.Problem.from_instance(inst)
+    u_ref, _, _ = O.solve(scheme=3, tol=1e-12)
+    with P_gpu(inst) as G:
+        G.coarse_solve(tol_c=1e-7)
+        G.build_patches()
+        st = G.solve_patches(tol32=1e-4, tol64=1e-6)
+        assert st["residual"] <= 1e-6
+        assert st["residual_evals"] >= 2          # the first check failed
+        u = G.get_value()
+        assert np.abs(u - u_ref).max() <= 1e-5 * max(1.0, np.abs(u_ref).max())
+        # the oracle's residual of the returned value agrees with the solver's
+        assert abs(O.residual(u) - st["residual"]) <= 1e-12
+
+
+def test_large_workload_full_size_sampled():
+    """The 4097^2 large workload as the benchmark runs it (FP32 passes, FP64
+    residual <= 1e-6): too large for a full oracle solve, so the FP64 oracle
+    evaluates the scheme (eq. SLscheme2) at 3000 sampled free nodes -- random
+    ones plus nodes next to obstacles, the target and the domain edge -- from
+    the returned value: every sampled |T u - u| must lie within the residual
+    the solver reports, and the value must respect the bounds 0 <= u <= u_max."""
+    inst = hi.large_instance()
+    n = inst.n
+    with P_gpu(inst) as G:
+        G.coarse_solve(tol_c=1e-6)
+        G.build_patches()
+        st = G.solve_patches(tol32=5e-7, tol64=1e-6)
+        u = G.get_value()
+    assert st["residual"] <= 1e-6
+    O = oracle.Problem.from_instance(inst)
+    m = inst.mask.reshape(n, n)
+    free = m == hi.MASK_FREE
+    near = np.zeros_like(free)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            near |= np.roll(np.roll(m != hi.MASK_FREE, dy, 0), dx, 1)
+    near[0, :] = near[-1, :] = near[:, 0] = near[:, -1] = True
+    rng = np.random.default_rng(11)
+    special = np.flatnonzero((near & free).reshape(-1))
+    pick = np.concatenate([rng.choice(np.flatnonzero(free.reshape(-1)), 2000, replace=False),
+                           rng.choice(special, 1000, replace=False)])
+    worst = 0.0
+    for k in pick:
+        v, _ = O.node_update(u, int(k), scheme=2)
+        worst = max(worst, abs(v - u[k]))
+    assert worst <= st["residual"] * (1 + 1e-9) + 1e-15, (worst, st["residual"])
+    assert u.min() >= 0.0 and u.max() <= O.u_max * (1 + 1e-12)
+    # obstacle nodes hold l/lambda + h l (R16); the two sides round the formula
+    # differently in the last place
+    np.testing.assert_allclose(u[inst.mask == hi.MASK_OBSTACLE], O.u_max, rtol=0, atol=1e-12)
