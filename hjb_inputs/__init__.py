@@ -226,12 +226,13 @@ def patchy_1025(sigma: float, n: int = 1025, coarse_n: int = 129,
 
 
 def batched_instance(seed: int, n: Optional[int] = None) -> Instance:
-    """One instance of the many-instance workload: n ~ U{65..513} (odd),
+    """One instance of the many-instance workload: n = 8k + 1 with k ~ U{8..64}
+    (65 <= n <= 513, so the coarse grid (n-1)/4 + 1 nests with ratio 4),
     random Fourier speed clipped to [0.2, 1.8], 1-3 target discs of radius
     0.05-0.15, sigma ~ U[0, 0.1], lambda ~ U[0.5, 2], 32 controls, 4-16 patches."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     if n is None:
-        n = int(rng.integers(32, 257)) * 2 + 1
+        n = int(rng.integers(8, 65)) * 8 + 1
     speed = speed_fourier(n, rng)
     k = int(rng.integers(1, 4))
     centres = [tuple(rng.uniform(-0.7, 0.7, 2)) for _ in range(k)]

@@ -319,6 +319,96 @@ const char* hjb_last_error(void);
  * was loaded (all problems, all threads); a reporting aid for benchmarks. */
 long long hjb_kernel_launches(void);
 
+/* FP32 tolerances (tol_c, tol32 and the FP32 Jacobi tolerance) below half an FP32
+ * ulp of the largest value, 1.01 * 2^-23 * max(1, u_max), are raised to it: at the
+ * FP32 fixed point each node's increment can be that large, so a smaller
+ * tolerance could stall until the pass cap.  u_max = l/lambda + h l (the coarse
+ * grid's h_c for tol_c). */
+
+/* ===================================================================== batches
+ * Many independent problems solved together: the patchy pipeline of Section 4.3
+ * (coarse solve -> interpolation -> synthesis -> labels -> ordering -> patch
+ * solve -> FP64 residual / polish) with every stage one launch over all the
+ * instances, and the patch solve one persistent launch whose steps carry the
+ * tiles of every instance.  Each instance has its own grid size, speed, mask,
+ * sectors, h, lambda, sigma, coarse grid and patch count; the control set, the
+ * scheme and the running cost l are shared.  No drift field. */
+typedef struct hjb_batch hjb_batch;
+
+typedef struct {
+    int32_t n;            /* nodes per side, 9..16385                                      */
+    int32_t coarse_n;     /* coarse nodes per side, >= 5, (n-1) % (coarse_n-1) == 0       */
+    int32_t n_patches;    /* sectors Gamma_p, 1..HJB_MAX_PATCHES                           */
+    int32_t reserved;     /* must be 0                                                     */
+    double h;             /* time step (<= 0: h = dx)                                      */
+    double lambda;        /* discount rate, > 0                                            */
+    double sigma;         /* diffusion (>= 0)                                              */
+} hjb_batch_inst;
+
+typedef struct {
+    int32_t n_controls;   /* shared control set, 1..HJB_MAX_CONTROLS                        */
+    int32_t scheme;       /* 3 (SLscheme3, default when 0) or 2                            */
+    int32_t tile_shape;   /* warp tiles: 0 8x8, 1 8x4, 2 4x4, -1: 8x4 until tuned          */
+    int32_t tile_waves;   /* bands per tile wave B (<= 0: 2 until tuned)                   */
+    int32_t tile_period;  /* period D of the tile schedule (<= 1: 2)                       */
+    int32_t reserved;     /* must be 0                                                     */
+    double cost;          /* running cost l (> 0)                                          */
+    double band_width;    /* causal band width in units of h (<= 0: 1)                    */
+} hjb_batch_desc;
+
+/* hjb_batch_create -- copies `count` instances to the device.  speed, mask and
+ * sector are the instances' n*n arrays (row-major, i fastest) concatenated in
+ * instance order; sector may be NULL (every target node in sector 0);
+ * controls: n_controls (a_x, a_y) pairs.  Ownership as hjb_create_problem.
+ * Errors: HJB_ERR_INVALID_ARG (count < 1, a bad instance: its index is in
+ * hjb_last_error), HJB_ERR_OOM, HJB_ERR_CUDA. */
+int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst* insts,
+                     const float* speed, const uint8_t* mask, const int8_t* sector,
+                     const double* controls, void* cuda_stream, hjb_batch** out);
+
+/* hjb_batch_solve -- the whole patchy pipeline for every instance: coarse solves
+ * until the sup-increment is <= tol_c, pre-computation, FP32 warp-tile passes
+ * until no tile changes by more than tol32, the FP64 sup-residual ||T2 u - u||
+ * of every instance, then FP64 passes for the instances above tol64 (if tol64 >
+ * 0).  residuals (nullable, count doubles) receives each instance's final FP64
+ * residual.  stats: node_updates / node_control_updates over all stages,
+ * residual = the largest, fp32_passes = pipeline steps; ms_stage: [0] FP32
+ * passes, [1] residuals, [2] FP64 passes, [3] coarse solves, [4] pre-computation.
+ * Errors: HJB_ERR_NOT_CONVERGED (a cap was hit; values valid), HJB_ERR_TIMEOUT. */
+int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int32_t max_passes,
+                    hjb_stats* stats, double* residuals);
+
+/* hjb_batch_solve_full -- the plain comparator for every instance: full-grid FP32
+ * Jacobi sweeps from u = 0 (one launch per sweep over the instances not yet
+ * converged) until an instance's sup-increment is <= tol32, then its FP64
+ * residual; instances above tol64 continue with the tolerance divided by 4 (at
+ * most 3 times).  Same outputs as hjb_batch_solve; fp32_passes = sweeps of the
+ * slowest instance. */
+int hjb_batch_solve_full(hjb_batch* b, double tol32, double tol64, int32_t max_sweeps,
+                         hjb_stats* stats, double* residuals);
+
+/* hjb_batch_autotune -- runs the pre-computation once, then the FP32 patch solve
+ * for each candidate schedule (tile shapes 8x8, 8x4, 4x4 x bands per wave 1, 2),
+ * times each with CUDA events and keeps the fastest for later solves.  ms_out
+ * (nullable, 6 doubles) gets the candidates' times in that order; shape_out /
+ * waves_out (nullable) the choice. */
+int hjb_batch_autotune(hjb_batch* b, double tol_c, double tol32, int32_t* shape_out,
+                       int32_t* waves_out, double* ms_out);
+
+/* hjb_batch_get_value -- instance `index`'s current value (n*n doubles). */
+int hjb_batch_get_value(const hjb_batch* b, int32_t index, double* u_out);
+
+/* hjb_batch_get_feedback / hjb_batch_get_labels -- instance `index`'s a*
+ * (255 on non-free nodes) and patch labels after a solve. */
+int hjb_batch_get_feedback(const hjb_batch* b, int32_t index, uint8_t* a_out);
+int hjb_batch_get_labels(const hjb_batch* b, int32_t index, int8_t* label_out);
+
+/* hjb_batch_get_uhat -- instance `index`'s interpolated coarse value u_hat. */
+int hjb_batch_get_uhat(const hjb_batch* b, int32_t index, float* uhat_out);
+
+/* hjb_batch_destroy -- frees the batch; NULL is ignored. */
+void hjb_batch_destroy(hjb_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

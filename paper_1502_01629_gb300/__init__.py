@@ -19,10 +19,11 @@ from typing import Optional
 
 import numpy as np
 
-from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, Desc, HJBError, RegimeInfo, Stats, check,
-                   header_functions, lib)
+from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, BatchDesc, BatchInst, Desc, HJBError, RegimeInfo,
+                   Stats, check, header_functions, lib)
 
-__all__ = ["Problem", "HJBError", "regime", "kernel_launches", "lib", "header_functions", "HJB_ERR_NOT_CONVERGED"]
+__all__ = ["Problem", "Batch", "HJBError", "regime", "kernel_launches", "lib", "header_functions",
+           "HJB_ERR_NOT_CONVERGED"]
 
 
 def _c(a: np.ndarray, dtype) -> np.ndarray:
@@ -220,3 +221,109 @@ class Problem:
         check(lib().hjb_device_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
               "hjb_device_info")
         return {"num_sms": a.value, "wave_blocks32": b.value, "wave_blocks64": c.value}
+
+
+class Batch:
+    """Many independent problems solved together (wraps an ``hjb_batch*``).
+
+    ``instances`` are objects with the fields of ``hjb_inputs.Instance`` (n,
+    speed, mask, sector, h, lam, sigma, coarse_n, n_patches); they share the
+    control set ``controls``, the running cost and the scheme."""
+
+    def __init__(self, instances, controls: np.ndarray, *, cost: float = 1.0, scheme: int = 3,
+                 tile_shape: int = -1, tile_waves: int = 0, tile_period: int = 2,
+                 band_width: float = 1.0, stream=None):
+        self._h = None
+        insts = list(instances)
+        self.count = len(insts)
+        self.ns = [int(x.n) for x in insts]
+        arr = (BatchInst * self.count)()
+        for i, x in enumerate(insts):
+            arr[i].n, arr[i].coarse_n, arr[i].n_patches, arr[i].reserved = x.n, x.coarse_n, x.n_patches, 0
+            arr[i].h, arr[i].lam, arr[i].sigma = x.h, x.lam, x.sigma
+        d = BatchDesc()
+        controls = _c(controls, np.float64).reshape(-1, 2)
+        d.n_controls, d.scheme, d.tile_shape = controls.shape[0], scheme, tile_shape
+        d.tile_waves, d.tile_period, d.reserved = tile_waves, tile_period, 0
+        d.cost, d.band_width = cost, band_width
+        speed = _c(np.concatenate([np.asarray(x.speed).reshape(-1) for x in insts]), np.float32)
+        mask = _c(np.concatenate([np.asarray(x.mask).reshape(-1) for x in insts]), np.uint8)
+        sector = _c(np.concatenate([np.asarray(x.sector).reshape(-1) for x in insts]), np.int8)
+        h = ctypes.c_void_p()
+        st = None
+        if stream is not None:
+            st = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+        check(lib().hjb_batch_create(ctypes.byref(d), self.count, ctypes.cast(arr, ctypes.c_void_p),
+                                     _p(speed), _p(mask), _p(sector), _p(controls), st,
+                                     ctypes.byref(h)), "hjb_batch_create")
+        self._h = h
+
+    @classmethod
+    def from_instances(cls, insts, **kw) -> "Batch":
+        return cls(insts, insts[0].controls, cost=insts[0].cost, **kw)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().hjb_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, tol_c: float = 1e-6, tol32: float = 2.5e-7, tol64: float = 1e-6,
+              max_passes: int = 100000, check_conv: bool = True):
+        """The patchy pipeline for every instance; returns (stats, residuals)."""
+        st = Stats()
+        res = np.empty(self.count)
+        rc = lib().hjb_batch_solve(self._h, tol_c, tol32, tol64, max_passes, ctypes.byref(st), _p(res))
+        if not (rc == HJB_ERR_NOT_CONVERGED and not check_conv):
+            check(rc, "hjb_batch_solve")
+        return st.as_dict(), res
+
+    def solve_full(self, tol32: float = 2.5e-7, tol64: float = 1e-6, max_sweeps: int = 200000,
+                   check_conv: bool = True):
+        """The plain full-grid Jacobi comparator for every instance."""
+        st = Stats()
+        res = np.empty(self.count)
+        rc = lib().hjb_batch_solve_full(self._h, tol32, tol64, max_sweeps, ctypes.byref(st), _p(res))
+        if not (rc == HJB_ERR_NOT_CONVERGED and not check_conv):
+            check(rc, "hjb_batch_solve_full")
+        return st.as_dict(), res
+
+    def autotune(self, tol_c: float = 1e-6, tol32: float = 2.5e-7) -> dict:
+        """Time the candidate tile schedules; returns the choice and the times."""
+        shape, waves = ctypes.c_int32(), ctypes.c_int32()
+        ms = np.zeros(6)
+        check(lib().hjb_batch_autotune(self._h, tol_c, tol32, ctypes.byref(shape), ctypes.byref(waves),
+                                       _p(ms)), "hjb_batch_autotune")
+        names = [f"{s}/B{b}" for s in ("8x8", "8x4", "4x4") for b in (1, 2)]
+        return {"tile_shape": shape.value, "tile_waves": waves.value, "ms": dict(zip(names, ms.tolist()))}
+
+    def get_value(self, index: int) -> np.ndarray:
+        out = np.empty(self.ns[index] ** 2)
+        check(lib().hjb_batch_get_value(self._h, index, _p(out)), "hjb_batch_get_value")
+        return out
+
+    def get_feedback(self, index: int) -> np.ndarray:
+        out = np.empty(self.ns[index] ** 2, np.uint8)
+        check(lib().hjb_batch_get_feedback(self._h, index, _p(out)), "hjb_batch_get_feedback")
+        return out
+
+    def get_labels(self, index: int) -> np.ndarray:
+        out = np.empty(self.ns[index] ** 2, np.int8)
+        check(lib().hjb_batch_get_labels(self._h, index, _p(out)), "hjb_batch_get_labels")
+        return out
+
+    def get_uhat(self, index: int) -> np.ndarray:
+        out = np.empty(self.ns[index] ** 2, np.float32)
+        check(lib().hjb_batch_get_uhat(self._h, index, _p(out)), "hjb_batch_get_uhat")
+        return out

@@ -60,6 +60,19 @@ class RegimeInfo(ctypes.Structure):
                 ("lower_ok", ctypes.c_int32), ("reach_cells", ctypes.c_int32)]
 
 
+class BatchInst(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("coarse_n", ctypes.c_int32), ("n_patches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("h", ctypes.c_double), ("lam", ctypes.c_double),
+                ("sigma", ctypes.c_double)]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_controls", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("tile_shape", ctypes.c_int32), ("tile_waves", ctypes.c_int32),
+                ("tile_period", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cost", ctypes.c_double), ("band_width", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _D = ctypes.c_double
@@ -94,6 +107,16 @@ _SIGNATURES = {
     "hjb_kernel_launches": (ctypes.c_longlong, []),
     "hjb_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc), _PTR, _PTR, _PTR, _PTR, _PTR, _PTR,
                                             _PTR]),
+    "hjb_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _PTR, _PTR, _PTR, _PTR, _PTR,
+                                        _PTR, ctypes.POINTER(_P)]),
+    "hjb_batch_solve": (ctypes.c_int, [_P, _D, _D, _D, _I32, ctypes.POINTER(Stats), _PTR]),
+    "hjb_batch_solve_full": (ctypes.c_int, [_P, _D, _D, _I32, ctypes.POINTER(Stats), _PTR]),
+    "hjb_batch_autotune": (ctypes.c_int, [_P, _D, _D, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _PTR]),
+    "hjb_batch_get_value": (ctypes.c_int, [_P, _I32, _PTR]),
+    "hjb_batch_get_feedback": (ctypes.c_int, [_P, _I32, _PTR]),
+    "hjb_batch_get_labels": (ctypes.c_int, [_P, _I32, _PTR]),
+    "hjb_batch_get_uhat": (ctypes.c_int, [_P, _I32, _PTR]),
+    "hjb_batch_destroy": (None, [_P]),
 }
 
 _LIB = None

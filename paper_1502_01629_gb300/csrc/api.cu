@@ -39,6 +39,18 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+}  // namespace
+
+namespace hjb {
+int set_last_error(int code, const char* msg) {
+    g_last_error = msg ? msg : "";
+    return code;
+}
+void clear_last_error() { g_last_error.clear(); }
+}  // namespace hjb
+
+namespace {
+
 #define CU(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
@@ -47,8 +59,6 @@ int fail(int code, const char* fmt, ...) {
                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-constexpr int kBandCap = 1 << 20;
-constexpr unsigned long long kTimeoutNs = 4000000000ull;   // grid-wide wait limit: 4 s
 
 template <typename T>
 void dfree(T*& p) {
@@ -164,6 +174,8 @@ struct hjb_problem {
     int32_t* cb_list = nullptr;    // tiles sorted by checkerboard wave
     int32_t* cb_off = nullptr;     // 3 offsets
     int32_t* cb_count = nullptr;   // 2 counters (sort scratch)
+    TileInst* tinst = nullptr;     // warp tiles: the problem as a one-instance batch (device)
+    int max_wh = 0;                // (TW + 2R)(TH + 2R)
     int32_t* sched_count = nullptr;
     int32_t* sched_off = nullptr;
     int32_t* res_off = nullptr;
@@ -221,8 +233,8 @@ struct hjb_problem {
         g.beta64 = beta_c;
         g.hl32 = (float)hl_c;
         g.hl64 = hl_c;
-        g.uob32 = (float)uob_c;
-        g.uob64 = uob_c;
+        g.uob32 = (float)uob;     // obstacles hold the fine scheme's value on both grids
+        g.uob64 = uob;
         return g;
     }
 };
@@ -496,6 +508,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             CUP(cudaMalloc(&p->cb_list, nt * sizeof(int32_t)));
             CUP(cudaMalloc(&p->cb_off, 3 * sizeof(int32_t)));
             CUP(cudaMalloc(&p->cb_count, 2 * sizeof(int32_t)));
+            CUP(cudaMalloc(&p->tinst, sizeof(TileInst)));
         } else {
             CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
             CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
@@ -509,6 +522,25 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     {
         p->tile_blocks32 = std::max(1, tile_blocks_per_sm(false, sig, na, p->halo, p->shape)) * p->num_sms;
         p->tile_blocks64 = std::max(1, tile_blocks_per_sm(true, sig, na, p->halo, p->shape)) * p->num_sms;
+    }
+    if (p->tinst) {
+        // the problem as a one-instance batch of the warp-tile kernel
+        int tw, th;
+        wtile_dims(p->shape, &tw, &th);
+        TileInst ti{};
+        ti.g = p->fine_view();
+        ti.u32 = p->u32;
+        ti.u64 = p->u64;
+        ti.uhat = p->uhat;
+        ti.lambda = (float)p->lambda;
+        ti.band_w = (float)(p->desc.band_width * p->h);
+        ti.R = p->halo;
+        ti.ntx = p->ntx;
+        ti.nty = p->nty;
+        ti.tile_off = 0;
+        ti.act_radius = p->act_radius;
+        p->max_wh = (tw + 2 * p->halo) * (th + 2 * p->halo);
+        CUP(cudaMemcpyAsync(p->tinst, &ti, sizeof(ti), cudaMemcpyHostToDevice, p->st));
     }
     p->wave_blocks32 = std::max(1, wave_blocks_per_sm(false, sig, na)) * p->num_sms;
     p->wave_blocks64 = std::max(1, wave_blocks_per_sm(true, sig, na)) * p->num_sms;
@@ -703,9 +735,8 @@ int build_tiles(hjb_problem* p, const float* key_val) {
     const int B = p->desc.tile_waves, D = p->desc.tile_period;
     if (p->desc.schedule == 0) {
         // warp tiles: per-tile exact order by the key value (u_hat or current value)
-        CU(launch_wtile_build(p->shape, p->n, p->ntx, p->nt, key_val, p->mask, p->speed,
-                              (float)p->lambda, (float)(p->desc.band_width * p->h), kBandCap, p->wt_nodes,
-                              p->wt_speed, p->wt_count, p->tile_min, p->st));
+        CU(launch_wtile_build(p->shape, p->tinst, nullptr, p->nt, key_val == p->u32, kBandCap,
+                              p->wt_nodes, p->wt_speed, p->wt_count, p->tile_min, p->st));
     } else {
         CU(cudaMemsetAsync(p->tile_min, 0x7f, sizeof(int32_t) * (size_t)p->nt, p->st));
         CU(launch_tile_min(p->n, p->ntx, p->key, p->mask, p->tile_min, p->st));
@@ -733,7 +764,7 @@ int build_tiles(hjb_problem* p, const float* key_val) {
         CU(launch_strided_gather(D, p->n_waves, p->sched_off, p->res_off, p->st));
     } else {
         // warm-restart schedule: tiles with free nodes in two checkerboard waves
-        CU(launch_checker_waves(p->nt, p->ntx, p->wt_count, p->cb_wave, p->cb_key, p->st));
+        CU(launch_checker_waves(p->tinst, nullptr, p->nt, p->wt_count, p->cb_wave, p->cb_key, p->st));
         CU(launch_counting_sort(p->nt, p->cb_key, 2, p->cb_count, p->cb_off, p->cb_list, p->st));
     }
     return HJB_OK;
@@ -792,6 +823,10 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.sync = &ds->sync;
     a.res = &ds->wave;
     a.timeout_ns = kTimeoutNs;
+    a.insts = p->tinst;
+    a.tile_inst = nullptr;
+    a.inst_active = nullptr;
+    a.max_wh = p->max_wh;
     const bool sig = p->sigma > 0.0;
     int blocks = f64 ? p->tile_blocks64 : p->tile_blocks32;
     if (p->desc.wave_warps > 0) {
@@ -799,7 +834,9 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
         const int want = (p->desc.wave_warps + wpb - 1) / wpb;
         blocks = std::max(1, std::min(blocks, want));
     }
-    if (f64) {
+    if (p->desc.schedule == 0) {
+        CU(launch_wtiles(a, f64, sig, blocks, p->st));
+    } else if (f64) {
         CU(launch_tiles_f64(a, p->u64, sig, blocks, p->st));
     } else {
         CU(launch_tiles_f32(a, p->u32, sig, blocks, p->st));
@@ -930,7 +967,8 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->tile_inc); dfree(p->tile_key2); dfree(p->tile_nodes); dfree(p->tile_bin_count);
     dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->wt_speed);
     dfree(p->wt_stamp); dfree(p->wt_queue); dfree(p->wt_qcount);
-    dfree(p->cb_wave); dfree(p->cb_key); dfree(p->cb_list); dfree(p->cb_off); dfree(p->cb_count); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
+    dfree(p->cb_wave); dfree(p->cb_key); dfree(p->cb_list); dfree(p->cb_off); dfree(p->cb_count);
+    dfree(p->tinst); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
     dfree(p->step_inc);
     if (p->scratch) cudaFree(p->scratch);
     if (p->host_pinned) cudaFreeHost(p->host_pinned);
@@ -948,7 +986,7 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     tm.mark();
     const GridView gc = p->coarse_view();
     const int Nc = p->nc * p->nc;
-    CU(launch_init_values(Nc, p->mask_c, (float)p->uob_c, (float)p->uob_c, p->uc, nullptr, p->uob_c, p->st));
+    CU(launch_init_values(Nc, p->mask_c, (float)p->uob_c, (float)p->uob, p->uc, nullptr, p->uob, p->st));
     // one cooperative launch: in-place sweeps until the sup-increment is <= tol_c
     Scalars* ds = dscal(p);
     CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
@@ -956,7 +994,7 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     CU(cudaMemsetAsync(ds->relax_inc, 0, sizeof(ds->relax_inc), p->st));
     RelaxArgs ra{};
     ra.g = gc;
-    ra.tol = (float)tol_c;
+    ra.tol = (float)std::max(tol_c, fp32_tol_floor(p->uob_c));
     ra.max_sweeps = max_sweeps;
     ra.sweep_inc = ds->relax_inc;
     ra.sync = &ds->sync;
@@ -1070,6 +1108,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
     if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
     if (!(tol32 > 0.0) || max_passes < 1 || !(tol64 >= 0.0))
         return fail(HJB_ERR_INVALID_ARG, "bad tolerances / max_passes");
+    tol32 = std::max(tol32, fp32_tol_floor(p->uob));
     Timer tm(p->st);
     tm.mark();
     WaveResult w32{}, w64{};
@@ -1209,7 +1248,8 @@ int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64, 
     if (precision == 32) {
         CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, nullptr, p->uob, p->st));
         CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32b, nullptr, p->uob, p->st));
-        rc = jacobi32(p, p->fine_view(), p->halo, p->u32, p->u32b, tol, max_sweeps, &s32, &last, &conv);
+        rc = jacobi32(p, p->fine_view(), p->halo, p->u32, p->u32b, std::max(tol, fp32_tol_floor(p->uob)),
+                      max_sweeps, &s32, &last, &conv);
         if (rc) return rc;
         p->value_f64 = false;
         if (!conv) rc = HJB_ERR_NOT_CONVERGED;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <stdint.h>
 
 #include "hjb_device.cuh"
@@ -13,6 +14,19 @@ namespace hjb {
 // Number of kernels this library has launched (all threads), for reporting.
 void count_launches(long long k);
 long long launches();
+
+// Error text returned by hjb_last_error (calling thread).
+int set_last_error(int code, const char* msg);
+void clear_last_error();
+
+// Smallest FP32 sup-increment tolerance an FP32 iteration can meet: half an
+// ulp of the largest value (with 1% to spare).  At the FP32 fixed point every
+// node's increment is at most half an ulp of its value (a larger one would
+// change it), so a tolerance below this could stall short of it.
+inline double fp32_tol_floor(double umax) { return 1.01 * std::ldexp(umax > 1.0 ? umax : 1.0, -23); }
+
+constexpr int kBandCap = 1 << 20;                          // causal bands per problem
+constexpr unsigned long long kTimeoutNs = 4000000000ull;   // grid-wide wait limit: 4 s
 
 // ---------------------------------------------------------------- sweep.cu
 // Halo (cells) a tile needs so that every Q1 vertex of every point lies inside.
@@ -55,6 +69,10 @@ cudaError_t launch_successors(const GridView& g, const uint8_t* a, int32_t* succ
 cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const int8_t* sector,
                           int n_patches, int32_t* jump_a, int32_t* jump_b, int8_t* label,
                           cudaStream_t st);
+// `rounds` pointer-jumping passes out[k] = in[in[k]] starting from succ over N
+// nodes, alternating between jump_a and jump_b; *result = the last output.
+cudaError_t launch_pointer_jumps(long long N, const int32_t* succ, int rounds, int32_t* jump_a,
+                                 int32_t* jump_b, const int32_t** result, cudaStream_t st);
 // Counting sort of the indices k with key[k] >= 0 by key (nbins bins):
 // off[0..nbins] = bin offsets, order = indices grouped by bin (order inside a bin
 // is unspecified).  count is scratch of nbins entries.
@@ -128,6 +146,21 @@ constexpr int kLocalBands = 64;   // band slots per block tile (the last one tak
 constexpr int kWarpTile = 8;      // tile edge in nodes (warp tiles)
 constexpr int kWarpTileNodes = kWarpTile * kWarpTile;
 
+// Per-instance data of the warp-tile kernel; a single problem is a batch of one.
+struct TileInst {
+    GridView g;          // grid, speed, mask, controls (shared by a batch) and scheme constants
+    float* u32;          // the instance's values (n*n)
+    double* u64;
+    const float* uhat;   // the coarse-grid interpolant (tile build key)
+    float lambda;        // band map: band = floor(T(u) / band_w), T(u) = -log(1 - lambda u)/lambda
+    float band_w;
+    int R;               // halo cells staged around a tile
+    int ntx, nty;        // tiles per row / column
+    int tile_off;        // global index of the instance's tile 0
+    int act_radius;      // tiles around a tile whose change re-queues it
+    int pad;
+};
+
 struct TileArgs {
     GridView g;
     int scheme;
@@ -147,7 +180,11 @@ struct TileArgs {
     int32_t* stamp;            // warp tiles: last step each tile was queued for
     int32_t* queue;            // warp tiles: (period + 2) x nt queued tiles
     int32_t* qcount;           // warp tiles: period + 2 queue lengths
-    int nt;                    // number of tiles
+    int nt;                    // number of tiles (all instances)
+    const TileInst* insts;     // warp tiles: per-instance data
+    const int32_t* tile_inst;  // warp tiles: instance of each tile (nullptr: all instance 0)
+    const uint8_t* inst_active;// warp tiles: first visits only for instances flagged 1 (nullable)
+    int max_wh;                // warp tiles: largest (TW + 2R)(TH + 2R) over the instances
     unsigned int* step_inc;    // ring of 2 * period per-step maxima (float bits)
     int ntx, nty;              // tiles per row / column
     int n_waves;
@@ -162,15 +199,22 @@ struct TileArgs {
 
 void wtile_dims(int shape, int* tw, int* th);
 size_t tile_smem(bool f64, int na, int halo, int shape);
+// launch of the warp-tile kernel with the slices sized by a.max_wh
+size_t wtile_smem(bool f64, int na, int max_wh);
 int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape);
-cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
-                               const uint8_t* mask, const float* speed, float lambda, float band_w,
-                               int band_cap, int32_t* nodes, float* slot_speed, int32_t* count,
-                               int* tile_min, cudaStream_t st);
-// wave[t] = (tx + ty) mod 2 for tiles with free nodes (INT_MAX otherwise), key
-// the same (-1 for empty tiles): the warm-restart schedule
-cudaError_t launch_checker_waves(int nt, int ntx, const int32_t* count, int32_t* wave,
-                                 int32_t* key, cudaStream_t st);
+// Warp-tile build over nt tiles of the instances (tile_inst: instance of each
+// tile, nullptr = all instance 0); key = u32 (re-sorting) or u_hat.
+cudaError_t launch_wtile_build(int shape, const TileInst* insts, const int32_t* tile_inst, int nt,
+                               bool key_u32, int band_cap, int32_t* nodes, float* slot_speed,
+                               int32_t* count, int* tile_min, cudaStream_t st);
+// wave[t] = (tx + ty) mod 2 (tile coordinates within its instance) for tiles with
+// free nodes (INT_MAX otherwise), key the same (-1 for empty tiles): the
+// warm-restart schedule
+cudaError_t launch_checker_waves(const TileInst* insts, const int32_t* tile_inst, int nt,
+                                 const int32_t* count, int32_t* wave, int32_t* key, cudaStream_t st);
+// The warp-tile kernel (shape 1..3) over a.insts / a.tile_inst.
+cudaError_t launch_wtiles(const TileArgs& a, bool f64, bool sig, int blocks, cudaStream_t st);
+int wtile_blocks_per_sm(bool f64, bool sig, int na, int max_wh, int shape);
 // stamp[t] = tile_wave[t] (a tile is never queued for a step up to its first visit)
 cudaError_t launch_tile_stamps(int nt, const int32_t* tile_wave, int32_t* stamp, cudaStream_t st);
 int tile_threads(bool f64, int shape);

@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "hjb_kernels.h"
+#include "precompute_device.cuh"
 
 namespace hjb {
 
@@ -16,34 +17,12 @@ constexpr int kThreads = 256;
 inline int blocks_for(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- coarse grid
-// Coarse node (I,J) is fine node (rI, rJ).  It is a target when some fine target
-// node lies within r/2 fine cells in both axes, else an obstacle if its fine
-// node is one.  Speed and drift are the fine ones there.
 __global__ void k_coarse_data(int n, int nc, const float* __restrict__ speed,
                               const float2* __restrict__ drift, const uint8_t* __restrict__ mask,
                               float* speed_c, float2* drift_c, uint8_t* mask_c) {
     const int kc = blockIdx.x * blockDim.x + threadIdx.x;
     if (kc >= nc * nc) return;
-    const int r = (n - 1) / (nc - 1);
-    const int hw = r / 2;
-    const int I = kc % nc, J = kc / nc;
-    const size_t kf = (size_t)(r * J) * n + (size_t)(r * I);
-    speed_c[kc] = speed[kf];
-    if (drift_c) drift_c[kc] = drift[kf];
-    bool tgt = false;
-    for (int dj = -hw; dj <= hw && !tgt; ++dj) {
-        const int fj = r * J + dj;
-        if (fj < 0 || fj >= n) continue;
-        for (int di = -hw; di <= hw; ++di) {
-            const int fi = r * I + di;
-            if (fi < 0 || fi >= n) continue;
-            if (mask[(size_t)fj * n + fi] == kTarget) {
-                tgt = true;
-                break;
-            }
-        }
-    }
-    mask_c[kc] = tgt ? kTarget : (mask[kf] == kObstacle ? kObstacle : kFree);
+    coarse_data_node(kc, n, nc, speed, drift, mask, speed_c, drift_c, mask_c);
 }
 
 // u_hat: Q1 interpolation of u_c at the fine nodes (nested grids, ratio r).
@@ -51,25 +30,11 @@ __global__ void k_interp(int nc, const float* __restrict__ uc, int n,
                          const uint8_t* __restrict__ mask, float u_obst, float* uhat) {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (size_t)n * n) return;
-    const int i = (int)(k % n), j = (int)(k / n);
-    const int mk = mask[k];
-    if (mk != kFree) {
-        uhat[k] = (mk == kTarget) ? 0.0f : u_obst;
-        return;
-    }
-    const int r = (n - 1) / (nc - 1);
-    const int cx = min(i / r, nc - 2), cy = min(j / r, nc - 2);
-    const float fx = (float)(i - cx * r) / (float)r;
-    const float fy = (float)(j - cy * r) / (float)r;
-    const float* b = uc + (size_t)cy * nc + cx;
-    const float a0 = fmaf(fx, b[1] - b[0], b[0]);
-    const float a1 = fmaf(fx, b[nc + 1] - b[nc], b[nc]);
-    uhat[k] = fmaf(fy, a1 - a0, a0);
+    uhat[k] = interp_node(k, nc, uc, n, mask, u_obst);
 }
 
-// Synthesis a*(x_i) = argmin_a beta u_hat(x_i + h f(x_i, a)) + h l (sigma = 0,
-// self vertex included, ties to the lowest index) and the causal band key
-// floor(T(u_hat)/w), T(u) = -log(1 - lambda u)/lambda (lambda u clipped at 1 - 1e-6).
+// Synthesis a* and the causal band key of every free node; the largest key is
+// folded into *max_key.
 __global__ void k_synthesis(GridView g, const float* __restrict__ uhat, float lambda, float band_w,
                             int band_cap, uint8_t* a_out, int32_t* key, int* max_key) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -84,30 +49,9 @@ __global__ void k_synthesis(GridView g, const float* __restrict__ uhat, float la
             a_out[k] = 255;
             key[k] = -1;
         } else {
-            const int i = (int)(k % n), j = (int)(k / n);
-            const float c = g.speed[k];
-            float bx = 0.0f, by = 0.0f;
-            if (g.drift) {
-                const float2 b = g.drift[k];
-                bx = b.x;
-                by = b.y;
-            }
-            const float* base = uhat + k;
-            auto U = [&](int dx, int dy) { return __ldg(base + (ptrdiff_t)dy * n + dx); };
             auto C = [&](int m) { return sctrl[m]; };
-            float Nn, D;
-            int M;
-            best_over_controls<float, false>(g, 2, i, j, 0.0f, c, bx, by, 0, 1, C, U, Nn, D, M);
-            a_out[k] = (uint8_t)M;
-            float u = fmaxf(uhat[k], 0.0f);
-            float T;
-            if (lambda > 0.0f) {
-                const float lu = fminf(lambda * u, 1.0f - 1e-6f);
-                T = -log1pf(-lu) / lambda;
-            } else {
-                T = u;
-            }
-            kk = min((int)floorf(T / band_w), band_cap - 1);
+            a_out[k] = (uint8_t)synthesis_node(g, k, uhat, C);
+            kk = band_of(uhat[k], lambda, band_w, band_cap);
             key[k] = kk;
         }
     }
@@ -128,15 +72,7 @@ __global__ void k_keys_from_values(int N, const uint8_t* __restrict__ mask,
         if (mask[k] != kFree) {
             key[k] = -1;
         } else {
-            const float v = fmaxf(u[k], 0.0f);
-            float T;
-            if (lambda > 0.0f) {
-                const float lu = fminf(lambda * v, 1.0f - 1e-6f);
-                T = -log1pf(-lu) / lambda;
-            } else {
-                T = v;
-            }
-            kk = min((int)floorf(T / band_w), band_cap - 1);
+            kk = band_of(u[k], lambda, band_w, band_cap);
             key[k] = kk;
         }
     }
@@ -146,67 +82,12 @@ __global__ void k_keys_from_values(int N, const uint8_t* __restrict__ mask,
     if ((threadIdx.x & 31) == 0 && wm >= 0) atomicMax(max_key, wm);
 }
 
-// Successor of each free node (winner-take-all transport step of eq.
-// discrete-advection).  The foot uses the prescribed IEEE FP32 sequence
-//   t = c*ax; t = t + bx; t = s*t; xi = (float)i + t    (round-to-nearest, no FMA)
-// so that the result is bit-reproducible on any IEEE machine; the heaviest Q1
-// vertex rounds each coordinate (0.5 rounds down); if it is the node itself the
-// neighbour along the axis whose fraction is closer to 1/2 is taken (equal:
-// lower linear index); a foot exactly on the node is a self-loop.
+// Successor of each free node (non-free nodes point to themselves).
 __global__ void k_successors(GridView g, const uint8_t* __restrict__ a, int32_t* succ) {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = g.n;
     if (k >= (size_t)n * n) return;
-    if (g.mask[k] != kFree) {
-        succ[k] = (int32_t)k;
-        return;
-    }
-    const int i = (int)(k % n), j = (int)(k / n);
-    const int m = a[k];
-    const float2 ctrl = g.ctrl32[min(m, g.na - 1)];
-    const float c = g.speed[k];
-    float bx = 0.0f, by = 0.0f;
-    if (g.drift) {
-        const float2 b = g.drift[k];
-        bx = b.x;
-        by = b.y;
-    }
-    const float s = g.s32;
-    float tx = __fmul_rn(c, ctrl.x);
-    tx = __fadd_rn(tx, bx);
-    tx = __fmul_rn(s, tx);
-    float ty = __fmul_rn(c, ctrl.y);
-    ty = __fadd_rn(ty, by);
-    ty = __fmul_rn(s, ty);
-    const float top = (float)(n - 1);
-    float xi = __fadd_rn((float)i, tx);
-    float eta = __fadd_rn((float)j, ty);
-    xi = fminf(fmaxf(xi, 0.0f), top);
-    eta = fminf(fmaxf(eta, 0.0f), top);
-    int cx = (int)floorf(xi), cy = (int)floorf(eta);
-    cx = min(cx, n - 2);
-    cy = min(cy, n - 2);
-    const float fx = __fsub_rn(xi, (float)cx);
-    const float fy = __fsub_rn(eta, (float)cy);
-    const int vx = cx + (fx > 0.5f ? 1 : 0);
-    const int vy = cy + (fy > 0.5f ? 1 : 0);
-    int32_t out;
-    if (vx == i && vy == j) {
-        if (xi == (float)i && eta == (float)j) {
-            out = (int32_t)k;
-        } else {
-            const float ex = fabsf(__fsub_rn(fx, 0.5f));
-            const float ey = fabsf(__fsub_rn(fy, 0.5f));
-            const int ox = (vx == cx) ? cx + 1 : cx;
-            const int oy = (vy == cy) ? cy + 1 : cy;
-            const int32_t kx = vy * n + ox;
-            const int32_t ky = oy * n + vx;
-            out = (ex < ey) ? kx : ((ey < ex) ? ky : min(kx, ky));
-        }
-    } else {
-        out = vy * n + vx;
-    }
-    succ[k] = out;
+    succ[k] = g.mask[k] != kFree ? (int32_t)k : successor_node(g, k, a[k]);
 }
 
 // Pointer jumping: out[k] = in[in[k]].
@@ -380,6 +261,20 @@ cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const
     }
     count_launches(1);
     k_label_from_end<<<blocks_for(N), kThreads, 0, st>>>(N, in, mask, sector, n_patches, label);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pointer_jumps(long long N, const int32_t* succ, int rounds, int32_t* jump_a,
+                                 int32_t* jump_b, const int32_t** result, cudaStream_t st) {
+    const int32_t* in = succ;
+    int32_t* bufs[2] = {jump_a, jump_b};
+    for (int r = 0; r < rounds; ++r) {
+        int32_t* out = bufs[r & 1];
+        count_launches(1);
+        k_jump<<<blocks_for(N), kThreads, 0, st>>>((int)N, in, out);
+        in = out;
+    }
+    *result = in;
     return cudaGetLastError();
 }
 

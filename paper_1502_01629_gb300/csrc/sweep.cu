@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "hjb_kernels.h"
+#include "sweep_device.cuh"
 
 namespace hjb {
 
@@ -67,23 +68,11 @@ k_sweep_tile(GridView g, int scheme, int R, const T* __restrict__ uin, T* __rest
         T out = uk;
         int am = -1;
         if (g.mask[k] == kFree) {
-            const T c = (T)g.speed[k];
-            T bx = T(0), by = T(0);
-            if (g.drift) {
-                const float2 b = g.drift[k];
-                bx = (T)b.x;
-                by = (T)b.y;
-            }
             const T* base = tile + ly * W + lx;
-            auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
             auto C = [&](int m) { return sctrl[m]; };
-            T N, D;
             int M;
-            if (interior)
-                best_over_controls<T, SIG, false>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
-            else
-                best_over_controls<T, SIG, true>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
-            const T du = N / D;
+            const T du = interior ? node_increment<T, SIG, false>(g, scheme, i, j, k, base, W, C, M)
+                                  : node_increment<T, SIG, true>(g, scheme, i, j, k, base, W, C, M);
             out = uk + du;
             am = M;
             lmax = fmax(lmax, fabs(du));
@@ -163,54 +152,7 @@ k_residual_screened(GridView g, int R, const double* __restrict__ u, float margi
         const size_t k = (size_t)j * n + i;
         if (g.mask[k] != kFree) continue;
         const int off = (j - gy0) * W + (i - gx0);
-        const float* b32 = t32 + off;
-        const double* b64 = t64 + off;
-        auto U32 = [&](int dx, int dy) { return b32[dy * W + dx]; };
-        auto U64 = [&](int dx, int dy) { return b64[dy * W + dx]; };
-        const float ck32 = g.speed[k];
-        float bx32 = 0.0f, by32 = 0.0f;
-        if (g.drift) {
-            const float2 b = g.drift[k];
-            bx32 = b.x;
-            by32 = b.y;
-        }
-        const float uk32 = b32[0];
-        const double uk64 = b64[0];
-        // FP32 screening pass
-        const float s32 = g.s32, beta32 = g.beta32;
-        const float c0_32 = fmaf(-(1.0f - beta32), uk32, g.hl32);
-        const NodeBox<float> box32 = node_box<float>(i, j, n);
-        float vmin = INFINITY;
-        for (int m = 0; m < g.na; ++m) {
-            const float2 a = c32[m];
-            const float fx = s32 * fmaf(ck32, a.x, bx32);
-            const float fy = s32 * fmaf(ck32, a.y, by32);
-            float Sd, L;
-            control_terms<float, SIG>(g, box32, fx, fy, uk32, U32, Sd, L);
-            vmin = fminf(vmin, fmaf(beta32, Sd, c0_32));
-        }
-        const float keep = vmin + margin;
-        // FP64 evaluation of the controls the screening cannot exclude
-        const double s64 = g.s64, beta64 = g.beta64;
-        const double c0_64 = fma(-(1.0 - beta64), uk64, g.hl64);
-        const NodeBox<double> box64 = node_box<double>(i, j, n);
-        const double ck64 = (double)ck32, bx64 = (double)bx32, by64 = (double)by32;
-        double best = INFINITY;
-        for (int m = 0; m < g.na; ++m) {
-            const float2 a = c32[m];
-            const float fx = s32 * fmaf(ck32, a.x, bx32);
-            const float fy = s32 * fmaf(ck32, a.y, by32);
-            float Sd, L;
-            control_terms<float, SIG>(g, box32, fx, fy, uk32, U32, Sd, L);
-            if (fmaf(beta32, Sd, c0_32) > keep) continue;
-            const double2 a64 = c64[m];
-            const double fx64 = s64 * fma(ck64, a64.x, bx64);
-            const double fy64 = s64 * fma(ck64, a64.y, by64);
-            double Sd64, L64;
-            control_terms<double, SIG>(g, box64, fx64, fy64, uk64, U64, Sd64, L64);
-            best = fmin(best, fma(beta64, Sd64, c0_64));
-        }
-        lmax = fmax(lmax, fabs(best));
+        lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin));
     }
     const double bm = block_max<double>(lmax, red);
     if (tid == 0) atomic_max_nonneg(incmax, bm);

@@ -28,11 +28,12 @@ constexpr int kTS = kTileSize;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-// Block size of the warp-tile kernel: one 1024-thread block per SM in FP32 (a
-// cheaper grid barrier), 256 threads in FP64 (more registers per thread).
+// Block size of the warp-tile kernel: one 768-thread block per SM in FP32 (a
+// cheap grid barrier; 85 registers a thread hold the pipelined node loop
+// without spilling), 256 threads in FP64 (more registers per thread).
 template <typename T>
 struct WTBlock {
-    static constexpr int threads = sizeof(T) == 4 ? 1024 : 256;
+    static constexpr int threads = sizeof(T) == 4 ? 768 : 256;
     static constexpr int warps = threads / 32;
 };
 
@@ -269,20 +270,16 @@ __device__ __forceinline__ float bil32(const float* su, int o, int W, float frx,
 // wave has had its first visit and the queues of the next D steps are empty.
 template <typename T, bool SIG, int TW, int TH>
 __global__ void __launch_bounds__(WTBlock<T>::threads)
-k_wtiles(TileArgs a, T* u) {
+k_wtiles(TileArgs a) {
     constexpr int kWarpsW = WTBlock<T>::warps;
     using V2 = typename RealOf<T>::V2;
     extern __shared__ __align__(16) unsigned char smem[];
-    const GridView& g = a.g;
-    const int n = g.n;
-    const int R = a.halo;
-    const int W = TW + 2 * R;
-    const int H = TH + 2 * R;
+    const int na = a.insts[0].g.na;           // one control set for every instance
     V2* sctrl = reinterpret_cast<V2*>(smem);
-    const size_t ctrl_bytes = ((size_t)g.na * sizeof(V2) + 15) & ~(size_t)15;
+    const size_t ctrl_bytes = ((size_t)na * sizeof(V2) + 15) & ~(size_t)15;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    T* su = reinterpret_cast<T*>(smem + ctrl_bytes) + (size_t)warp * W * H;
+    T* su = reinterpret_cast<T*>(smem + ctrl_bytes) + (size_t)warp * a.max_wh;
     __shared__ float red[32];
     __shared__ int s_flag;
     __shared__ unsigned long long s_nodes;
@@ -291,10 +288,7 @@ k_wtiles(TileArgs a, T* u) {
     // consecutive tiles of a step go to different blocks (SMs) first
     const int gw = warp * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * kWarpsW;
-    const int ar = a.act_radius;
-    const int aw = 2 * ar + 1;
-    const int nnb = aw * aw;
-    for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(g, m);
+    for (int m = threadIdx.x; m < na; m += blockDim.x) sctrl[m] = RealOf<T>::ctrl(a.insts[0].g, m);
     if (threadIdx.x == 0) s_nodes = 0ull;
     __syncthreads();
     auto C = [&](int m) { return sctrl[m]; };
@@ -323,7 +317,21 @@ k_wtiles(TileArgs a, T* u) {
         float wmax = 0.0f;
         for (int idx = gw; idx < total; idx += nw) {
             const int t = idx < fn ? a.tile_list[fbeg + idx] : __ldcg(queue + (idx - fn));
-            const int tcx = t % a.ntx, tcy = t / a.ntx;
+            const int b = a.tile_inst ? a.tile_inst[t] : 0;
+            if (a.inst_active && !a.inst_active[b]) continue;
+            const TileInst& I = a.insts[b];
+            const GridView& g = I.g;
+            const int n = g.n;
+            const int R = I.R;
+            const int W = TW + 2 * R;
+            const int H = TH + 2 * R;
+            T* u;
+            if constexpr (sizeof(T) == 4) u = I.u32; else u = I.u64;
+            const int ar = I.act_radius;
+            const int aw = 2 * ar + 1;
+            const int nnb = aw * aw;
+            const int tl = t - I.tile_off;
+            const int tcx = tl % I.ntx, tcy = tl / I.ntx;
             const int bi = tcx * TW, bj = tcy * TH;
             const int gx0 = bi - R, gy0 = bj - R;
             for (int e = lane; e < W * H; e += 32) {
@@ -345,8 +353,8 @@ k_wtiles(TileArgs a, T* u) {
             int nbw = -1;
             if (lane < nnb) {
                 const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
-                if (nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty) {
-                    const int w = a.tile_wave[ny * a.ntx + nx];
+                if (nx >= 0 && ny >= 0 && nx < I.ntx && ny < I.nty) {
+                    const int w = a.tile_wave[I.tile_off + ny * I.ntx + nx];
                     if (w <= step) nbw = w;
                 }
             }
@@ -354,6 +362,17 @@ k_wtiles(TileArgs a, T* u) {
             float tmax = 0.0f;
             int old = 0x7fffffff;    // stamp before this visit claimed the neighbour
             bool claimed = false;
+            auto claim = [&]() {
+                // claim the neighbours as soon as the tile has changed; the queue
+                // slots are taken after the visit, so the atomics overlap the
+                // remaining nodes
+                claimed = true;
+                if (nbw >= 0) {
+                    const int tgt = step + 1 + ((nbw - step - 1) % D + D) % D;
+                    const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
+                    old = atomicMax(a.stamp + I.tile_off + ny * I.ntx + nx, tgt);
+                }
+            };
             // staged window inside the grid: the projection is the identity
             const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + W <= n && gy0 + H <= n;
             auto visit = [&](auto clamp_tag) {
@@ -387,16 +406,7 @@ k_wtiles(TileArgs a, T* u) {
                     if (lane == 0) base[0] = uk + du;
                     __syncwarp();
                     tmax = fmaxf(tmax, inc_to_float(fabs(du)));
-                    if (!claimed && tmax > a.tol) {
-                        // claim the neighbours now; the queue slots are taken after
-                        // the visit, so the atomics overlap the remaining nodes
-                        claimed = true;
-                        if (nbw >= 0) {
-                            const int tgt = step + 1 + ((nbw - step - 1) % D + D) % D;
-                            const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
-                            old = atomicMax(a.stamp + ny * a.ntx + nx, tgt);
-                        }
-                    }
+                    if (!claimed && tmax > a.tol) claim();
                 }
               }
             };
@@ -407,7 +417,7 @@ k_wtiles(TileArgs a, T* u) {
               const float s = g.s32, beta = g.beta32, hl = g.hl32;
               const float bq = SIG ? beta * 0.25f : beta;
               const float omb = 1.0f - beta;
-              const bool has = lane < g.na;
+              const bool has = lane < na;
               const float2 ac = has ? g.ctrl32[lane] : make_float2(0.0f, 0.0f);
               auto node_geo = [&](int q, int& kb) {
                   const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
@@ -441,20 +451,13 @@ k_wtiles(TileArgs a, T* u) {
                     if (lane == 0) sf[kb] = uk + du;
                     __syncwarp();
                     tmax = fmaxf(tmax, fabsf(du));
-                    if (!claimed && tmax > a.tol) {
-                        claimed = true;
-                        if (nbw >= 0) {
-                            const int tgt = step + 1 + ((nbw - step - 1) % D + D) % D;
-                            const int nx = tcx + lane % aw - ar, ny = tcy + lane / aw - ar;
-                            old = atomicMax(a.stamp + ny * a.ntx + nx, tgt);
-                        }
-                    }
+                    if (!claimed && tmax > a.tol) claim();
                 }
               }
             };
             bool piped = false;
             if constexpr (sizeof(T) == 4) {
-                if (g.drift == nullptr && g.na <= 32) {
+                if (g.drift == nullptr && na <= 32) {
                     piped = true;
                     if (interior)
                         visit32(std::false_type{});
@@ -481,12 +484,12 @@ k_wtiles(TileArgs a, T* u) {
                     int w = -1;
                     if (q == lane) {
                         w = nbw;
-                    } else if (nx >= 0 && ny >= 0 && nx < a.ntx && ny < a.nty) {
-                        const int ww = a.tile_wave[ny * a.ntx + nx];
+                    } else if (nx >= 0 && ny >= 0 && nx < I.ntx && ny < I.nty) {
+                        const int ww = a.tile_wave[I.tile_off + ny * I.ntx + nx];
                         if (ww <= step) w = ww;
                     }
                     if (w < 0) continue;
-                    const int tt = ny * a.ntx + nx;
+                    const int tt = I.tile_off + ny * I.ntx + nx;
                     const int tgt = step + 1 + ((w - step - 1) % D + D) % D;
                     const int prev = q == lane ? old : atomicMax(a.stamp + tt, tgt);
                     if (prev < tgt) {
@@ -544,14 +547,20 @@ k_wtiles(TileArgs a, T* u) {
 // t*64 .. t*64+count-1, and records the band of the smallest key (the tile's wave
 // is derived from it).
 template <int TW, int TH>
-__global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ key_val,
-                              const uint8_t* __restrict__ mask, const float* __restrict__ speed,
-                              float lambda, float band_w, int band_cap, int32_t* nodes,
+__global__ void k_wtile_build(const TileInst* __restrict__ insts, const int32_t* __restrict__ tile_inst,
+                              int nt, bool key_u32, int band_cap, int32_t* nodes,
                               float* slot_speed, int32_t* count, int* tile_min) {
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= nt) return;
-    const int tcx = t % ntx, tcy = t / ntx;
+    const TileInst& I = insts[tile_inst ? tile_inst[t] : 0];
+    const int n = I.g.n;
+    const float* key_val = key_u32 ? I.u32 : I.uhat;
+    const uint8_t* mask = I.g.mask;
+    const float* speed = I.g.speed;
+    const float lambda = I.lambda, band_w = I.band_w;
+    const int tl = t - I.tile_off;
+    const int tcx = tl % I.ntx, tcy = tl / I.ntx;
     // lane holds tile cells lane and lane + 32 (row-major TW x TH; slots past
     // TW*TH stay empty)
     float kv[2];
@@ -644,39 +653,63 @@ __global__ void k_wtile_build(int n, int ntx, int nt, const float* __restrict__ 
     }
 }
 
-// shape code: 0 = block tiles 16x16, 1 = warp 8x8, 2 = warp 8x4, 3 = warp 4x4
+// shape code: 1 = warp 8x8, 2 = warp 8x4, 3 = warp 4x4
 template <typename T, bool SIG>
-auto wtile_kernel(int shape) -> void (*)(TileArgs, T*) {
+auto wtile_kernel(int shape) -> void (*)(TileArgs) {
     switch (shape) {
-        case 1: return k_wtiles<T, SIG, 8, 8>;
         case 2: return k_wtiles<T, SIG, 8, 4>;
         case 3: return k_wtiles<T, SIG, 4, 4>;
-        default: return k_tiles<T, SIG>;
+        default: return k_wtiles<T, SIG, 8, 8>;
     }
 }
 
 template <typename T, bool SIG>
-cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
-    const size_t smem = tile_smem(sizeof(T) == 8, a.g.na, a.halo, a.warp_tiles);
+cudaError_t launch_wtiles_impl(const TileArgs& a, int blocks, cudaStream_t st) {
+    const size_t smem = wtile_smem(sizeof(T) == 8, a.g.na, a.max_wh);
     auto kern = wtile_kernel<T, SIG>(a.warp_tiles);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {(void*)&a};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(WTBlock<T>::threads),
+                                       args, smem, st);
+}
+
+template <typename T, bool SIG>
+int wtile_blocks_per_sm_impl(int na, int max_wh, int shape) {
+    const size_t smem = wtile_smem(sizeof(T) == 8, na, max_wh);
+    auto kern = wtile_kernel<T, SIG>(shape);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, WTBlock<T>::threads, smem);
+    return nb;
+}
+
+// block tiles (16x16, one block per tile)
+template <typename T, bool SIG>
+cudaError_t launch_impl(const TileArgs& a, T* u, int blocks, cudaStream_t st) {
+    const size_t smem = tile_smem(sizeof(T) == 8, a.g.na, a.halo, 0);
+    auto kern = k_tiles<T, SIG>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     void* args[] = {(void*)&a, (void*)&u};
     count_launches(1);
-    const int threads = a.warp_tiles ? WTBlock<T>::threads : kThreads;
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), args, smem, st);
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kThreads), args, smem, st);
 }
 
 template <typename T, bool SIG>
-int blocks_per_sm_impl(int na, int halo, int shape) {
-    const size_t smem = tile_smem(sizeof(T) == 8, na, halo, shape);
-    auto kern = wtile_kernel<T, SIG>(shape);
+int blocks_per_sm_impl(int na, int halo) {
+    const size_t smem = tile_smem(sizeof(T) == 8, na, halo, 0);
+    auto kern = k_tiles<T, SIG>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, shape ? WTBlock<T>::threads : kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem);
     return nb;
 }
 
@@ -726,12 +759,15 @@ __global__ void k_tile_waves(int nt, const int* __restrict__ tile_min, int band_
 }
 
 // checkerboard wave (tx + ty) mod 2 of each tile with free nodes; sort key
-__global__ void k_checker_waves(int nt, int ntx, const int32_t* __restrict__ count, int32_t* wave,
-                                int32_t* key) {
+__global__ void k_checker_waves(const TileInst* __restrict__ insts,
+                                const int32_t* __restrict__ tile_inst, int nt,
+                                const int32_t* __restrict__ count, int32_t* wave, int32_t* key) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     if (count[t] > 0) {
-        const int w = ((t % ntx) + (t / ntx)) & 1;
+        const TileInst& I = insts[tile_inst ? tile_inst[t] : 0];
+        const int tl = t - I.tile_off;
+        const int w = ((tl % I.ntx) + (tl / I.ntx)) & 1;
         wave[t] = w;
         key[t] = w;
     } else {
@@ -752,45 +788,68 @@ void wtile_dims(int shape, int* tw, int* th) {
     *th = shape == 1 ? 8 : 4;
 }
 
-size_t tile_smem(bool f64, int na, int halo, int shape) {
+size_t wtile_smem(bool f64, int na, int max_wh) {
     const size_t v2 = f64 ? sizeof(double2) : sizeof(float2);
     const size_t ctrl = ((size_t)na * v2 + 15) & ~(size_t)15;
     const size_t rs = f64 ? sizeof(double) : sizeof(float);
+    const size_t warps = f64 ? WTBlock<double>::warps : WTBlock<float>::warps;
+    return ctrl + warps * (size_t)max_wh * rs;
+}
+
+size_t tile_smem(bool f64, int na, int halo, int shape) {
     if (shape > 0) {
         int tw, th;
         wtile_dims(shape, &tw, &th);
-        const size_t warps = f64 ? WTBlock<double>::warps : WTBlock<float>::warps;
-        return ctrl + warps * (size_t)(tw + 2 * halo) * (size_t)(th + 2 * halo) * rs;
+        return wtile_smem(f64, na, (tw + 2 * halo) * (th + 2 * halo));
     }
+    const size_t v2 = f64 ? sizeof(double2) : sizeof(float2);
+    const size_t ctrl = ((size_t)na * v2 + 15) & ~(size_t)15;
+    const size_t rs = f64 ? sizeof(double) : sizeof(float);
     const size_t off = (((size_t)kLocalBands + 1) * sizeof(int) + 15) & ~(size_t)15;
     const size_t w = (size_t)(kTileSize + 2 * halo);
     return ctrl + off + w * w * rs;
 }
 
 int tile_blocks_per_sm(bool f64, bool sig, int na, int halo, int shape) {
-    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo, shape)
-                        : blocks_per_sm_impl<double, false>(na, halo, shape);
-    return sig ? blocks_per_sm_impl<float, true>(na, halo, shape)
-               : blocks_per_sm_impl<float, false>(na, halo, shape);
+    if (shape > 0) {
+        int tw, th;
+        wtile_dims(shape, &tw, &th);
+        return wtile_blocks_per_sm(f64, sig, na, (tw + 2 * halo) * (th + 2 * halo), shape);
+    }
+    if (f64) return sig ? blocks_per_sm_impl<double, true>(na, halo)
+                        : blocks_per_sm_impl<double, false>(na, halo);
+    return sig ? blocks_per_sm_impl<float, true>(na, halo) : blocks_per_sm_impl<float, false>(na, halo);
 }
 
-cudaError_t launch_wtile_build(int shape, int n, int ntx, int nt, const float* key_val,
-                               const uint8_t* mask, const float* speed, float lambda, float band_w,
-                               int band_cap, int32_t* nodes, float* slot_speed, int32_t* count,
-                               int* tile_min, cudaStream_t st) {
+int wtile_blocks_per_sm(bool f64, bool sig, int na, int max_wh, int shape) {
+    if (f64) return sig ? wtile_blocks_per_sm_impl<double, true>(na, max_wh, shape)
+                        : wtile_blocks_per_sm_impl<double, false>(na, max_wh, shape);
+    return sig ? wtile_blocks_per_sm_impl<float, true>(na, max_wh, shape)
+               : wtile_blocks_per_sm_impl<float, false>(na, max_wh, shape);
+}
+
+cudaError_t launch_wtiles(const TileArgs& a, bool f64, bool sig, int blocks, cudaStream_t st) {
+    if (f64) return sig ? launch_wtiles_impl<double, true>(a, blocks, st)
+                        : launch_wtiles_impl<double, false>(a, blocks, st);
+    return sig ? launch_wtiles_impl<float, true>(a, blocks, st)
+               : launch_wtiles_impl<float, false>(a, blocks, st);
+}
+
+cudaError_t launch_wtile_build(int shape, const TileInst* insts, const int32_t* tile_inst, int nt,
+                               bool key_u32, int band_cap, int32_t* nodes, float* slot_speed,
+                               int32_t* count, int* tile_min, cudaStream_t st) {
     count_launches(1);
     const long long threads = (long long)nt * 32;
     auto kern = shape == 3 ? k_wtile_build<4, 4> : (shape == 2 ? k_wtile_build<8, 4> : k_wtile_build<8, 8>);
-    kern<<<(int)((threads + 255) / 256), 256, 0, st>>>(n, ntx, nt, key_val, mask, speed, lambda,
-                                                        band_w, band_cap, nodes, slot_speed, count,
-                                                        tile_min);
+    kern<<<(int)((threads + 255) / 256), 256, 0, st>>>(insts, tile_inst, nt, key_u32, band_cap,
+                                                        nodes, slot_speed, count, tile_min);
     return cudaGetLastError();
 }
 
-cudaError_t launch_checker_waves(int nt, int ntx, const int32_t* count, int32_t* wave,
-                                 int32_t* key, cudaStream_t st) {
+cudaError_t launch_checker_waves(const TileInst* insts, const int32_t* tile_inst, int nt,
+                                 const int32_t* count, int32_t* wave, int32_t* key, cudaStream_t st) {
     count_launches(1);
-    k_checker_waves<<<(nt + 255) / 256, 256, 0, st>>>(nt, ntx, count, wave, key);
+    k_checker_waves<<<(nt + 255) / 256, 256, 0, st>>>(insts, tile_inst, nt, count, wave, key);
     return cudaGetLastError();
 }
 
