@@ -374,6 +374,9 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
  * residual.  stats: node_updates / node_control_updates over all stages,
  * residual = the largest, fp32_passes = pipeline steps; ms_stage: [0] FP32
  * passes, [1] residuals, [2] FP64 passes, [3] coarse solves, [4] pre-computation.
+ * An instance above tol64 first gets at most two more FP32 phases (tolerance /4
+ * each, while above the FP32 floor), then FP64 passes; both start warm (that
+ * instance's tiles visited once in checkerboard order, then the queues).
  * Errors: HJB_ERR_NOT_CONVERGED (a cap was hit; values valid), HJB_ERR_TIMEOUT. */
 int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int32_t max_passes,
                     hjb_stats* stats, double* residuals);

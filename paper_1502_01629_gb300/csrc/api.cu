@@ -175,6 +175,10 @@ struct hjb_problem {
     int32_t* cb_off = nullptr;     // 3 offsets
     int32_t* cb_count = nullptr;   // 2 counters (sort scratch)
     TileInst* tinst = nullptr;     // warp tiles: the problem as a one-instance batch (device)
+    int32_t* rank_flags = nullptr; // dense-wave scratch (n_bands + 1)
+    int32_t* rank_scan = nullptr;
+    int32_t* rank_boff = nullptr;  // {0, n_bands}
+    int rank_cap = 0;
     int max_wh = 0;                // (TW + 2R)(TH + 2R)
     int32_t* sched_count = nullptr;
     int32_t* sched_off = nullptr;
@@ -245,6 +249,7 @@ struct Scalars {
     unsigned int relax_inc[3];
     unsigned int inc32;
     int max_key;
+    int n_waves;
     unsigned long long inc64;
     CoarseResult coarse;
     WaveResult wave;
@@ -509,6 +514,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             CUP(cudaMalloc(&p->cb_off, 3 * sizeof(int32_t)));
             CUP(cudaMalloc(&p->cb_count, 2 * sizeof(int32_t)));
             CUP(cudaMalloc(&p->tinst, sizeof(TileInst)));
+            CUP(cudaMalloc(&p->rank_boff, 2 * sizeof(int32_t)));
         } else {
             CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
             CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
@@ -745,6 +751,25 @@ int build_tiles(hjb_problem* p, const float* key_val) {
                                 p->tile_bin_off, p->tile_nodes, p->st));
     }
     p->n_waves = (std::max(p->n_bands, 1) - 1) / B + 1;
+    if (p->desc.schedule == 0) {
+        // dense waves: rank of each tile's lowest band among the distinct ones
+        const int S = std::max(p->n_bands, 1);
+        if (S + 1 > p->rank_cap) {
+            dfree(p->rank_flags);
+            dfree(p->rank_scan);
+            CU(cudaMalloc(&p->rank_flags, sizeof(int32_t) * (size_t)(S + 1)));
+            CU(cudaMalloc(&p->rank_scan, sizeof(int32_t) * (size_t)(S + 1)));
+            p->rank_cap = S + 1;
+        }
+        const int32_t boff[2] = {0, S};
+        CU(cudaMemcpyAsync(p->rank_boff, boff, sizeof(boff), cudaMemcpyHostToDevice, p->st));
+        Scalars* ds = dscal(p);
+        CU(launch_dense_waves(p->nt, p->tile_min, nullptr, 1, p->rank_boff, S, B, p->rank_flags,
+                              p->rank_scan, p->tile_wave, p->tile_key, &ds->n_waves, p->st));
+        CU(cudaMemcpyAsync(&hscal(p)->n_waves, &ds->n_waves, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+        p->n_waves = std::max(1, hscal(p)->n_waves);
+    }
     // warp tiles: sorted by wave alone (sched_off = wave offsets); block tiles:
     // by (wave mod D, wave)
     const int Dk = p->desc.schedule == 0 ? 1 : D;
@@ -756,8 +781,9 @@ int build_tiles(hjb_problem* p, const float* key_val) {
         CU(cudaMalloc(&p->sched_off, sizeof(int32_t) * (size_t)(bins + 1)));
         p->sched_cap = bins;
     }
-    CU(launch_tile_waves(p->nt, p->tile_min, B, Dk, p->n_waves, p->tile_wave, p->tile_key,
-                         p->tile_inc, p->st));
+    if (p->desc.schedule != 0)
+        CU(launch_tile_waves(p->nt, p->tile_min, B, Dk, p->n_waves, p->tile_wave, p->tile_key,
+                             p->tile_inc, p->st));
     CU(launch_counting_sort(p->nt, p->tile_key, bins, p->sched_count, p->sched_off, p->tile_list,
                             p->st));
     if (p->desc.schedule != 0) {
@@ -968,7 +994,7 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->wt_speed);
     dfree(p->wt_stamp); dfree(p->wt_queue); dfree(p->wt_qcount);
     dfree(p->cb_wave); dfree(p->cb_key); dfree(p->cb_list); dfree(p->cb_off); dfree(p->cb_count);
-    dfree(p->tinst); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
+    dfree(p->tinst); dfree(p->rank_flags); dfree(p->rank_scan); dfree(p->rank_boff); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
     dfree(p->step_inc);
     if (p->scratch) cudaFree(p->scratch);
     if (p->host_pinned) cudaFreeHost(p->host_pinned);

@@ -424,6 +424,16 @@ struct hjb_batch {
     int32_t* sched_off = nullptr;
     int sched_cap = 0;
     int n_waves = 1;
+    int32_t* cb_wave = nullptr;          // warm restart: checkerboard waves
+    int32_t* cb_key = nullptr;
+    int32_t* cb_list = nullptr;
+    int32_t* cb_off = nullptr;
+    int32_t* cb_count = nullptr;
+    int32_t* rank_flags = nullptr;       // dense-wave scratch
+    int32_t* rank_scan = nullptr;
+    int32_t* rank_boff = nullptr;        // count + 1
+    int* n_waves_dev = nullptr;
+    int rank_cap = 0;
     int max_wh = 0;
     int max_R = 0;
     int tiles_shape = 0;         // shape the tile arrays were built for (0: none)
@@ -840,6 +850,11 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     BCUP(dalloc(b->tile_inc, ntc));
     BCUP(dalloc(b->stamp, ntc));
     BCUP(dalloc(b->queue, ntc * (size_t)(b->D + 2)));
+    BCUP(dalloc(b->cb_wave, ntc));
+    BCUP(dalloc(b->cb_key, ntc));
+    BCUP(dalloc(b->cb_list, ntc));
+    BCUP(dalloc(b->cb_off, 3));
+    BCUP(dalloc(b->cb_count, 2));
     BCUP(dalloc(b->qcount, b->D + 2));
     BCUP(dalloc(b->step_inc, 2 * b->D));
     // per-instance scalars
@@ -852,6 +867,8 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     BCUP(dalloc(b->inc_bits, count));
     BCUP(dalloc(b->j_sweeps, count));
     BCUP(dalloc(b->n_active, 1));
+    BCUP(dalloc(b->rank_boff, count + 1));
+    BCUP(dalloc(b->n_waves_dev, 1));
     BCUP(dalloc(b->sync, 1));
     BCUP(dalloc(b->wres, 1));
     BCUP(cudaMallocHost((void**)&b->h_wres, sizeof(WaveResult)));
@@ -895,7 +912,8 @@ void hjb_batch_destroy(hjb_batch* b) {
     dfree(b->queue); dfree(b->qcount); dfree(b->step_inc); dfree(b->sched_count); dfree(b->sched_off);
     dfree(b->max_key); dfree(b->c_sweeps); dfree(b->c_inc); dfree(b->res_bits); dfree(b->margin);
     dfree(b->active); dfree(b->inc_bits); dfree(b->j_sweeps); dfree(b->n_active); dfree(b->sync);
-    dfree(b->wres);
+    dfree(b->cb_wave); dfree(b->cb_key); dfree(b->cb_list); dfree(b->cb_off); dfree(b->cb_count);
+    dfree(b->wres); dfree(b->rank_flags); dfree(b->rank_scan); dfree(b->rank_boff); dfree(b->n_waves_dev);
     if (b->h_wres) cudaFreeHost(b->h_wres);
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     delete b;
@@ -966,9 +984,26 @@ int stage_tiles(hjb_batch* b) {
     BCU(launch_wtile_build(b->shape, b->dtile, b->tile_inst, b->NT, false, kBandCap, b->wt_nodes,
                            b->wt_speed, b->wt_count, b->tile_min, b->st));
     BCU(cudaStreamSynchronize(b->st));
-    int kmax = 0;
-    for (int v : mk) kmax = std::max(kmax, v);
-    b->n_waves = kmax / b->B + 1;
+    // dense waves: per instance, rank of each tile's lowest band among the
+    // distinct ones (no step waits on a band no tile starts at)
+    std::vector<int32_t> boff(b->count + 1, 0);
+    for (int i = 0; i < b->count; ++i) boff[i + 1] = boff[i] + std::max(mk[i], 0) + 1;
+    const int S = boff[b->count];
+    if (S + 1 > b->rank_cap) {
+        dfree(b->rank_flags);
+        dfree(b->rank_scan);
+        BCU(dalloc(b->rank_flags, (size_t)S + 1));
+        BCU(dalloc(b->rank_scan, (size_t)S + 1));
+        b->rank_cap = S + 1;
+    }
+    BCU(cudaMemcpyAsync(b->rank_boff, boff.data(), sizeof(int32_t) * (b->count + 1), cudaMemcpyHostToDevice,
+                        b->st));
+    BCU(launch_dense_waves(b->NT, b->tile_min, b->tile_inst, b->count, b->rank_boff, S, b->B,
+                           b->rank_flags, b->rank_scan, b->tile_wave, b->tile_key, b->n_waves_dev, b->st));
+    int nw = 1;
+    BCU(cudaMemcpyAsync(&nw, b->n_waves_dev, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    BCU(cudaStreamSynchronize(b->st));
+    b->n_waves = std::max(1, nw);
     if (b->n_waves > b->sched_cap) {
         dfree(b->sched_count);
         dfree(b->sched_off);
@@ -976,41 +1011,46 @@ int stage_tiles(hjb_batch* b) {
         BCU(dalloc(b->sched_off, b->n_waves + 1));
         b->sched_cap = b->n_waves;
     }
-    BCU(launch_tile_waves(b->NT, b->tile_min, b->B, 1, b->n_waves, b->tile_wave, b->tile_key,
-                          b->tile_inc, b->st));
     BCU(launch_counting_sort(b->NT, b->tile_key, b->n_waves, b->sched_count, b->sched_off, b->tile_list,
                              b->st));
+    // warm-restart schedule: every tile with free nodes in two checkerboard waves
+    BCU(launch_checker_waves(b->dtile, b->tile_inst, b->NT, b->wt_count, b->cb_wave, b->cb_key, b->st));
+    BCU(launch_counting_sort(b->NT, b->cb_key, 2, b->cb_count, b->cb_off, b->cb_list, b->st));
     b->built = true;
     return HJB_OK;
 }
 
 // persistent warp-tile passes over every instance (f64: u64, only the instances
-// flagged in b->active when use_active)
-int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_active, WaveResult* out) {
+// flagged in b->active when use_active); warm: every tile visited in the first
+// two steps in checkerboard order instead of along the causal waves
+int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_active, WaveResult* out,
+                 bool warm = false) {
+    const int32_t* waves = warm ? b->cb_wave : b->tile_wave;
+    const int n_waves = warm ? 2 : b->n_waves;
     BCU(cudaMemsetAsync(b->wres, 0, sizeof(WaveResult), b->st));
     BCU(cudaMemsetAsync(b->sync, 0, sizeof(GridSync), b->st));
     BCU(cudaMemsetAsync(b->step_inc, 0, sizeof(unsigned int) * 2 * b->D, b->st));
     BCU(cudaMemsetAsync(b->qcount, 0, sizeof(int32_t) * (b->D + 2), b->st));
-    BCU(launch_tile_stamps(b->NT, b->tile_wave, b->stamp, b->st));
+    BCU(launch_tile_stamps(b->NT, waves, b->stamp, b->st));
     TileArgs a{};
     a.g = b->hinst[0].g;
     a.scheme = b->scheme;
     a.warp_tiles = b->shape;
     a.nodes = b->wt_nodes;
     a.wt_count = b->wt_count;
-    a.tile_list = b->tile_list;
-    a.wave_off = b->sched_off;
-    a.tile_wave = b->tile_wave;
+    a.tile_list = warm ? b->cb_list : b->tile_list;
+    a.wave_off = warm ? b->cb_off : b->sched_off;
+    a.tile_wave = waves;
     a.slot_speed = b->wt_speed;
     a.stamp = b->stamp;
     a.queue = b->queue;
     a.qcount = b->qcount;
     a.nt = b->NT;
     a.step_inc = b->step_inc;
-    a.n_waves = b->n_waves;
+    a.n_waves = n_waves;
     a.period = b->D;
     a.local_sweeps = 1;
-    a.max_steps = b->n_waves + max_passes * b->D;
+    a.max_steps = n_waves + max_passes * b->D;
     a.tol = (float)tol;
     a.sync = b->sync;
     a.res = b->wres;
@@ -1126,7 +1166,37 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
         if (rc) return rc;
         ++n_res;
         ms_res += t.stop();
-        // FP64 passes for the instances above tol64
+        // instances above tol64 first continue in FP32 from their current value
+        // with tighter tolerances (warm: every tile of theirs visited once, then
+        // the queues), as far as FP32 can resolve tol64
+        double tol_w = tol32;
+        for (int tries = 0; tries < 2 && 0.25 * tol_w >= fp32_tol_floor(umax); ++tries) {
+            std::vector<uint8_t> act(b->count);
+            int n_act = 0;
+            for (int i = 0; i < b->count; ++i) {
+                act[i] = res[i] > tol64 && tol64 >= 4.0 * fp32_tol_floor(b->uob[i]);
+                n_act += act[i];
+            }
+            if (n_act == 0) break;
+            tol_w *= 0.25;
+            BCU(cudaMemcpyAsync(b->active, act.data(), b->count, cudaMemcpyHostToDevice, b->st));
+            BTimer tw(b->st);
+            WaveResult ww{};
+            rc = stage_passes(b, false, tol_w, max_passes, true, &ww, true);
+            if (rc) return rc;
+            w32.passes += ww.passes;
+            w32.nodes += ww.nodes;
+            ms32 += tw.stop();
+            BTimer tr(b->st);
+            count_launches(1);
+            k_b_promote<<<b->nfblk, kBT, 0, b->st>>>(b->dinst, b->fblk, b->u32, b->u32, nullptr, b->u64);
+            BCU(cudaGetLastError());
+            rc = stage_residual(b, true, res);
+            if (rc) return rc;
+            ++n_res;
+            ms_res += tr.stop();
+        }
+        // FP64 passes for the instances still above tol64
         double tol_pass = tol64;
         for (int round = 0; round < 4; ++round) {
             std::vector<uint8_t> act(b->count);
@@ -1139,7 +1209,8 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
             BCU(cudaMemcpyAsync(b->active, act.data(), b->count, cudaMemcpyHostToDevice, b->st));
             BTimer t2(b->st);
             WaveResult w64{};
-            rc = stage_passes(b, true, tol_pass, max_passes - passes64, true, &w64);
+            // warm: the instances' values are close to the fixed point already
+            rc = stage_passes(b, true, tol_pass, max_passes - passes64, true, &w64, true);
             if (rc) return rc;
             passes64 += w64.passes;
             nodes64 += w64.nodes;

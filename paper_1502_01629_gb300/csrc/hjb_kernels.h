@@ -78,6 +78,8 @@ cudaError_t launch_pointer_jumps(long long N, const int32_t* succ, int rounds, i
 // is unspecified).  count is scratch of nbins entries.
 cudaError_t launch_counting_sort(int N, const int32_t* key, int nbins, int32_t* count,
                                  int32_t* off, int32_t* order, cudaStream_t st);
+// out[0..n] = exclusive prefix sums of in[0..n) (one block).
+cudaError_t launch_exclusive_scan(int n, const int32_t* in, int32_t* out, cudaStream_t st);
 // out[b] = off[b * stride] for b = 0..nb (inclusive).
 cudaError_t launch_strided_gather(int nb, int stride, const int32_t* off, int32_t* out,
                                   cudaStream_t st);
@@ -215,6 +217,15 @@ cudaError_t launch_checker_waves(const TileInst* insts, const int32_t* tile_inst
 // The warp-tile kernel (shape 1..3) over a.insts / a.tile_inst.
 cudaError_t launch_wtiles(const TileArgs& a, bool f64, bool sig, int blocks, cudaStream_t st);
 int wtile_blocks_per_sm(bool f64, bool sig, int na, int max_wh, int shape);
+// Dense tile waves (warp tiles): within each instance the distinct lowest bands
+// of its tiles are ranked in increasing order and wave = rank / band_group, so
+// no step waits on a band no tile starts at.  band_off[b] = first slot of
+// instance b in the flag array (nb instances, band_off[nb] = S slots); flags and
+// scan are scratch of S + 1 ints; *n_waves (device) receives the largest wave + 1.
+cudaError_t launch_dense_waves(int nt, const int* tile_min, const int32_t* tile_inst, int nb,
+                               const int32_t* band_off, int S, int band_group, int32_t* flags,
+                               int32_t* scan, int32_t* tile_wave, int32_t* tile_key, int* n_waves,
+                               cudaStream_t st);
 // stamp[t] = tile_wave[t] (a tile is never queued for a step up to its first visit)
 cudaError_t launch_tile_stamps(int nt, const int32_t* tile_wave, int32_t* stamp, cudaStream_t st);
 int tile_threads(bool f64, int shape);

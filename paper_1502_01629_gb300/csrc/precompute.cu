@@ -278,6 +278,12 @@ cudaError_t launch_pointer_jumps(long long N, const int32_t* succ, int rounds, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_exclusive_scan(int n, const int32_t* in, int32_t* out, cudaStream_t st) {
+    count_launches(1);
+    k_scan<<<1, 1024, 0, st>>>(n, in, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const uint8_t* mask,
                          int n_patches, int n_bands, int32_t* bin_count, int32_t* bin_off,
                          int32_t* order, int32_t* band_off, cudaStream_t st) {

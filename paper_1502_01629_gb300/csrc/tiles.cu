@@ -776,6 +776,39 @@ __global__ void k_checker_waves(const TileInst* __restrict__ insts,
     }
 }
 
+// flags[band_off[b] + lowest band of tile] = 1 for every tile with free nodes
+__global__ void k_mark_bands(int nt, const int* __restrict__ tile_min,
+                             const int32_t* __restrict__ tile_inst, const int32_t* __restrict__ band_off,
+                             int32_t* flags) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int bm = tile_min[t];
+    if (bm >= 0x7f7f7f7f) return;
+    const int b = tile_inst ? tile_inst[t] : 0;
+    flags[band_off[b] + bm] = 1;
+}
+
+// wave = rank of the tile's lowest band among its instance's distinct ones / B
+__global__ void k_rank_waves(int nt, const int* __restrict__ tile_min,
+                             const int32_t* __restrict__ tile_inst, const int32_t* __restrict__ band_off,
+                             const int32_t* __restrict__ scan, int band_group, int32_t* tile_wave,
+                             int32_t* tile_key, int* n_waves) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int bm = tile_min[t];
+    if (bm >= 0x7f7f7f7f) {
+        tile_wave[t] = 0x7fffffff;
+        tile_key[t] = -1;
+        return;
+    }
+    const int b = tile_inst ? tile_inst[t] : 0;
+    const int rank = scan[band_off[b] + bm] - scan[band_off[b]];
+    const int q = rank / band_group;
+    tile_wave[t] = q;
+    tile_key[t] = q;
+    atomicMax(n_waves, q + 1);
+}
+
 __global__ void k_tile_stamps(int nt, const int32_t* __restrict__ tile_wave, int32_t* stamp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < nt) stamp[t] = tile_wave[t];
@@ -850,6 +883,25 @@ cudaError_t launch_checker_waves(const TileInst* insts, const int32_t* tile_inst
                                  const int32_t* count, int32_t* wave, int32_t* key, cudaStream_t st) {
     count_launches(1);
     k_checker_waves<<<(nt + 255) / 256, 256, 0, st>>>(insts, tile_inst, nt, count, wave, key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_waves(int nt, const int* tile_min, const int32_t* tile_inst, int nb,
+                               const int32_t* band_off, int S, int band_group, int32_t* flags,
+                               int32_t* scan, int32_t* tile_wave, int32_t* tile_key, int* n_waves,
+                               cudaStream_t st) {
+    (void)nb;
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * (size_t)(S + 1), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(n_waves, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_mark_bands<<<(nt + 255) / 256, 256, 0, st>>>(nt, tile_min, tile_inst, band_off, flags);
+    e = launch_exclusive_scan(S, flags, scan, st);   // scan[0..S]
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_rank_waves<<<(nt + 255) / 256, 256, 0, st>>>(nt, tile_min, tile_inst, band_off, scan, band_group,
+                                                    tile_wave, tile_key, n_waves);
     return cudaGetLastError();
 }
 
