@@ -14,11 +14,13 @@ the time to FP64 residual 1e-6 of the patchy path and of plain full-grid FP32
 Jacobi value iteration (the comparator) on the same GPU reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload patchy1025|large4097]
+                    [--workload patchy1025|large4097|batched512]
 
 --workload large4097 runs the 4097^2 workload instead (random Fourier speed,
 six rectangular obstacles, 64 controls, sigma = 0.01, 64 patches; one patchy
-solve per step, the plain Jacobi comparator timed once).
+solve per step, the plain Jacobi comparator timed once).  --workload
+batched512 solves 512 independent instances (n 65..513) as one batch per step
+against the batched plain Jacobi comparator.
 
 N > 1 runs under torchrun, one rank per GPU; every rank solves the same
 workload (independent replicas, weak scaling) and rank 0 prints one JSON line.
@@ -51,6 +53,12 @@ TOL32, TOL64, TOL_C = 2.5e-7, 1e-6, 1e-6
 METRIC = "time to 1e-6 residual vs plain GPU value iteration; node·control updates/s"
 UNIT = "node·control updates/s"
 SOLVER_KW = dict(schedule=0, tile_shape=-1, tile_waves=0, tile_period=2, local_sweeps=1)
+BATCH_COUNT = 512
+# DRAM bytes (read + write) per launch of the warp-tile kernel on the 1025^2
+# workload, mean of the three launches of a step, from one ncu capture of this
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum); None for the other
+# workloads (not captured)
+WTILES_DRAM_BYTES_1025 = 14.49e6
 
 
 def flops_per_node_control(sigma: float) -> int:
@@ -374,7 +382,8 @@ def ours(args, ws, rank, local):
             "peak": fp32_peak,
             "unit": "TFLOP/s",
             "frac": achieved / fp32_peak,
-            "traffic": None,
+            "traffic": WTILES_DRAM_BYTES_1025 if (WORKLOAD == "patchy1025" and N_FINE == 1025) else None,
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (MEASURED_PEAKS.json)",
         },
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -399,6 +408,130 @@ def load_peaks() -> dict:
 
 
 # ------------------------------------------------------------- CPU oracle leg
+
+def ours_batched(args, ws, rank, local):
+    """The many-instance workload: 512 independent problems (n = 8k + 1 in
+    65..513, random Fourier speeds, 1-3 target discs, sigma ~ U[0, 0.1], lambda
+    ~ U[0.5, 2], 32 controls, 4-16 patches) solved as one batch; the plain
+    comparator is the batched full-grid FP32 Jacobi on the same GPU."""
+    import torch
+    from paper_1502_01629_gb300 import Batch, kernel_launches
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    stream = torch.cuda.current_stream()
+    insts = [hi.batched_instance(1000 + k) for k in range(BATCH_COUNT)]
+    n_free = sum(int((i.mask == 0).sum()) for i in insts)
+    B = Batch.from_instances(insts, stream=stream)
+    tune = B.autotune(tol_c=TOL_C, tol32=TOL32)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+
+    def solve():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, res = B.solve(tol_c=TOL_C, tol32=TOL32, tol64=TOL64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st, res
+
+    for _ in range(args.warmup):
+        solve()
+        flush_l2(torch, flush)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = kernel_launches()
+    step_ms, total_nc = [], 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(torch, flush)
+            ms, st, res = solve()
+            step_ms.append(ms)
+            total_nc += st["node_control_updates"]
+    launches = kernel_launches() - launches0
+    barrier(ws)
+    clocks = clk.summary()
+    time_s_max = reduce_max(sum(step_ms) / 1e3, ws, device)
+    value = reduce_sum(float(total_nc), ws, device) / time_s_max
+    # plain batched Jacobi comparator (seconds: one untimed start-up is not needed)
+    plain_ms = []
+    for _ in range(max(1, args.plain_reps)):
+        flush_l2(torch, flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pst, pres = B.solve_full(tol32=TOL32, tol64=TOL64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    # dominant kernel: the warp-tile FP32 passes
+    nodes32 = st["node_updates"] - st["fp64_node_updates"]
+    # every instance takes the sigma > 0 path of the kernel
+    sig_nodes = nodes32 * 32 * flops_per_node_control(0.05)
+    peaks = load_peaks()
+    fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    achieved = sig_nodes / (st["ms_stage"][0] / 1e3) / 1e12
+    # end to end through the C ABI with host buffers: create (H2D), solve, get_value (D2H)
+    e2e_ms, e2e_nc = [], 0
+    h2d = sum(i.speed.nbytes + i.mask.nbytes + i.sector.nbytes for i in insts) + insts[0].controls.nbytes
+    d2h = sum(i.n * i.n * 8 for i in insts)
+    for r in range(args.e2e_reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with Batch.from_instances(insts, stream=stream, tile_shape=tune["tile_shape"],
+                                  tile_waves=tune["tile_waves"]) as BB:
+            est, _ = BB.solve(tol_c=TOL_C, tol32=TOL32, tol64=TOL64)
+            for k in range(len(insts)):
+                BB.get_value(k)
+        torch.cuda.synchronize()
+        if r > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_nc += est["node_control_updates"]
+    e2e_value = e2e_nc / (sum(e2e_ms) / 1e3) if e2e_ms else None
+    B.close()
+    if rank != 0:
+        return None
+    patchy = statistics.median(step_ms)
+    plain = statistics.median(plain_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {
+            "workload": f"batched {BATCH_COUNT} instances, n=8k+1 in 65..513, random Fourier speed "
+                        "in [0.2,1.8], 1-3 discs r 0.05-0.15, sigma~U[0,0.1], lambda~U[0.5,2], "
+                        "32 controls, 4-16 patches, coarse (n-1)/4+1, FP32 passes + FP64 residual <= 1e-6",
+            "instances": BATCH_COUNT, "nodes": sum(i.n * i.n for i in insts), "free_nodes": n_free,
+            "tol32": TOL32, "tol64_residual": TOL64, "autotune": tune,
+            "l2": "flushed between timed steps (256 MiB write); working set > L2",
+            "parallelism": f"replicas x{ws}",
+        },
+        "time_to_1e-6_ms": {"patchy_batch": patchy, "plain_jacobi_fp32_batch": plain,
+                            "speedup_vs_plain": plain / patchy},
+        "solver_stats": {"steps": st["fp32_passes"], "node_updates": st["node_updates"],
+                         "fp64_node_updates": st["fp64_node_updates"], "residual_max": float(res.max()),
+                         "ms_fp32_passes": st["ms_stage"][0], "ms_residuals": st["ms_stage"][1],
+                         "ms_fp64": st["ms_stage"][2], "ms_coarse": st["ms_stage"][3],
+                         "ms_precompute": st["ms_stage"][4], "plain_sweeps": pst["sweeps"],
+                         "plain_residual_max": float(pres.max())},
+        "roofline": {"kernel": "k_wtiles<float> (warp-tile FP32 passes, all instances)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (MEASURED_PEAKS.json)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": statistics.median(e2e_ms) if e2e_ms else None,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        big = max(insts, key=lambda i: i.n)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, big)
+    return out
+
 
 def cpu_baseline(seconds: float, inst=None) -> dict:
     """The FP64 oracle as it stands (single-threaded Gauss-Seidel updates of the
@@ -468,9 +601,11 @@ def main(argv=None):
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("patchy1025", "large4097"), default="patchy1025",
+    ap.add_argument("--workload", choices=("patchy1025", "large4097", "batched512"),
+                    default="patchy1025",
                     help="patchy1025: the 1025^2 three-sigma workload (default); large4097: "
-                         "the 4097^2 64-control workload with obstacles")
+                         "the 4097^2 64-control workload with obstacles; batched512: 512 "
+                         "independent instances of 65^2..513^2 solved as one batch")
     ap.add_argument("--n", type=int, default=0, help="fine grid size (profiling only)")
     ap.add_argument("--coarse-n", type=int, default=N_COARSE)
     args = ap.parse_args(argv)
@@ -481,7 +616,12 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         print("bench.py: --warmup must be >= 3", file=sys.stderr)
     ws, rank, local = dist_env()
-    out = reference(args, ws, rank, local) if args.impl == "reference" else ours(args, ws, rank, local)
+    if args.impl == "reference":
+        out = reference(args, ws, rank, local)
+    elif WORKLOAD == "batched512":
+        out = ours_batched(args, ws, rank, local)
+    else:
+        out = ours(args, ws, rank, local)
     if out is not None:
         print(json.dumps(out), flush=True)
     if ws > 1 and args.impl == "ours":

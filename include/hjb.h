@@ -371,8 +371,10 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
  * until no tile changes by more than tol32, the FP64 sup-residual ||T2 u - u||
  * of every instance, then FP64 passes for the instances above tol64 (if tol64 >
  * 0).  residuals (nullable, count doubles) receives each instance's final FP64
- * residual.  stats: node_updates / node_control_updates over all stages,
- * residual = the largest, fp32_passes = pipeline steps; ms_stage: [0] FP32
+ * residual.  stats: node_updates = fine-grid updates of the FP32 and FP64
+ * passes, node_control_updates = every scheme evaluation (coarse sweeps, fine
+ * passes, residuals) times n_controls, residual = the largest, fp32_passes =
+ * pipeline steps; ms_stage: [0] FP32
  * passes, [1] residuals, [2] FP64 passes, [3] coarse solves, [4] pre-computation.
  * An instance above tol64 first gets at most two more FP32 phases (tolerance /4
  * each, while above the FP32 floor), then FP64 passes; both start warm (that

@@ -1237,9 +1237,9 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
         stats->sweeps = w32.passes + passes64;
         stats->fp32_passes = w32.passes;
         stats->fp64_passes = passes64;
-        stats->node_updates = nodes_c + (long long)w32.nodes + (long long)nodes64;
+        stats->node_updates = (long long)w32.nodes + (long long)nodes64;
         stats->fp64_node_updates = (long long)nodes64;
-        stats->node_control_updates = (stats->node_updates + (long long)n_res * nf) * b->na;
+        stats->node_control_updates = (nodes_c + stats->node_updates + (long long)n_res * nf) * b->na;
         stats->residual_evals = n_res;
         stats->residual = tol64 > 0.0 ? rmax : -1.0;
         stats->increment = w32.last_increment;
