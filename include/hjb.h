@@ -414,6 +414,72 @@ int hjb_batch_get_uhat(const hjb_batch* b, int32_t index, float* uhat_out);
 /* hjb_batch_destroy -- frees the batch; NULL is ignored. */
 void hjb_batch_destroy(hjb_batch* b);
 
+/* ======================================================== learned warm start
+ * Not in the paper: a 6-layer 3x3 convolutional network (32 channels; input 5
+ * channels: speed, target mask, obstacle mask, sigma, lambda, padded to 16;
+ * output 33 channels: the coarse value over u_max and 32 control logits, padded
+ * to 48; ReLU between layers; BF16 weights and activations, FP32 accumulation)
+ * whose value channel replaces the coarse solve's initial value (Section 4.3
+ * "Initialization" uses a large constant).  Convolutions run as implicit GEMMs
+ * on the tcgen05 tensor cores (forward and input gradient); the weight gradient
+ * is an FP32 reduction.  Images are NHWC: pixel (b, y, x), channel c at
+ * ((b H + y) W + x) C + c.  Parameters (FP32): per layer l = 0..5 the weights
+ * w[cout][9][cin_store] (tap t = 3 (dy + 1) + (dx + 1) of the correlation
+ * y[p] = sum_t w[., t, .] x[p + (dy, dx)], zero outside the image; cin_store = 16
+ * for layer 0, 32 after) then the bias b[cout]; cout = 32, 33 for the last layer. */
+typedef struct hjb_net hjb_net;
+
+/* hjb_net_param_count -- number of FP32 parameters in the layout above. */
+long long hjb_net_param_count(void);
+
+/* hjb_net_create -- buffers for batches of up to max_batch H x W images on the
+ * given stream (NULL: the default stream).  Parameters start at zero: call
+ * hjb_net_set_params. */
+int hjb_net_create(int32_t max_batch, int32_t height, int32_t width, void* cuda_stream, hjb_net** out);
+
+/* hjb_net_set_params / hjb_net_get_params -- host FP32 parameter arrays
+ * (hjb_net_param_count() values); set also clears the optimizer state. */
+int hjb_net_set_params(hjb_net* net, const float* params);
+int hjb_net_get_params(const hjb_net* net, float* params);
+
+/* hjb_net_get_grads -- the parameter gradients of the last hjb_net_train_step
+ * (same layout). */
+int hjb_net_get_grads(const hjb_net* net, float* grads);
+
+/* hjb_net_forward -- x: DEVICE bf16 [batch][H][W][16]; out_host (nullable): host
+ * FP32 [batch][H][W][48] copy of the last layer. */
+int hjb_net_forward(hjb_net* net, int32_t batch, const void* x, float* out_host);
+
+/* hjb_net_train_step -- one Adam step (beta 0.9 / 0.999) on a batch: DEVICE
+ * inputs x (as above), tval (target value over u_max, FP32 per pixel), tctrl
+ * (target control index per pixel), freem (1 on pixels that count); the loss is
+ * w_value * mean (o0 - tval)^2 + w_ctrl * mean cross-entropy over the n_free
+ * counted pixels.  loss_out (nullable, 2 doubles): the two means. */
+int hjb_net_train_step(hjb_net* net, int32_t batch, const void* x, const float* tval, const uint8_t* tctrl,
+                       const uint8_t* freem, int64_t n_free, float lr, float w_value, float w_ctrl,
+                       double* loss_out);
+
+/* hjb_net_warm_values -- after hjb_net_forward: image `index`'s value channel x
+ * scale, clamped to [0, umax], as a coarse initial value u0 (DEVICE, H*W floats);
+ * target nodes 0, obstacle nodes uob (mask: DEVICE H*W codes). */
+int hjb_net_warm_values(hjb_net* net, int32_t index, const uint8_t* mask, float scale, float umax, float uob,
+                        float* u0);
+
+/* hjb_net_destroy -- NULL is ignored. */
+void hjb_net_destroy(hjb_net* net);
+
+/* Single 3x3 layers on host buffers (for checking against a reference):
+ * x / dy / mask are bf16 bit patterns, NHWC; w is [cout][9][cin] FP32; cin, cout <= 48.
+ *   hjb_conv3x3_forward: y = relu?(conv(x, w) + b)          (y: [B][H][W][cout] FP32)
+ *   hjb_conv3x3_dgrad:   dx = conv^T(dy, w) * (mask > 0)    (mask nullable; dx: [B][H][W][cin])
+ *   hjb_conv3x3_wgrad:   dw = sum_p dy (x) x-neighbourhood, db = sum_p dy (db nullable) */
+int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* x,
+                        const float* w, const float* b, int32_t relu, float* y);
+int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* dy,
+                      const float* w, const uint16_t* mask, float* dx);
+int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* x,
+                      const uint16_t* dy, float* dw, float* db);
+
 #ifdef __cplusplus
 }
 #endif

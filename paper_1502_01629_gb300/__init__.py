@@ -22,7 +22,7 @@ import numpy as np
 from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, BatchDesc, BatchInst, Desc, HJBError, RegimeInfo,
                    Stats, check, header_functions, lib)
 
-__all__ = ["Problem", "Batch", "HJBError", "regime", "kernel_launches", "lib", "header_functions",
+__all__ = ["Problem", "Batch", "Net", "HJBError", "regime", "kernel_launches", "lib", "header_functions",
            "HJB_ERR_NOT_CONVERGED"]
 
 
@@ -327,3 +327,97 @@ class Batch:
         out = np.empty(self.ns[index] ** 2, np.float32)
         check(lib().hjb_batch_get_uhat(self._h, index, _p(out)), "hjb_batch_get_uhat")
         return out
+
+
+# layer shapes of the warm-start network: (cin stored, cout)
+NET_LAYERS = [(16, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 33)]
+NET_IN_REAL = 5
+
+
+class Net:
+    """The learned warm start's network on the GPU (wraps an ``hjb_net*``).
+
+    Inputs and targets of ``train_step`` / ``forward`` are device tensors (any
+    object with ``data_ptr()``); parameters move through host arrays."""
+
+    def __init__(self, max_batch: int, height: int, width: int, stream=None):
+        self._h = None
+        self.max_batch, self.H, self.W = max_batch, height, width
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+        check(lib().hjb_net_create(max_batch, height, width, st, ctypes.byref(h)), "hjb_net_create")
+        self._h = h
+        self.n_params = int(lib().hjb_net_param_count())
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().hjb_net_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- parameters
+    @staticmethod
+    def unpack(params: np.ndarray) -> list:
+        """[(w (cout, 9, cin), b (cout,)), ...] views of a flat parameter array."""
+        out, o = [], 0
+        for cin, cout in NET_LAYERS:
+            nw = cout * 9 * cin
+            out.append((params[o:o + nw].reshape(cout, 9, cin), params[o + nw:o + nw + cout]))
+            o += nw + cout
+        return out
+
+    @staticmethod
+    def pack(layers) -> np.ndarray:
+        return np.concatenate([np.concatenate([np.asarray(w, np.float64).reshape(-1),
+                                               np.asarray(b, np.float64).reshape(-1)]) for w, b in layers])
+
+    def init_params(self, seed: int) -> np.ndarray:
+        """He-normal weights (std sqrt(2 / (9 cin)), cin the real inputs), zero
+        biases, zero weights on the padding input channels of layer 0."""
+        rng = np.random.default_rng(np.random.PCG64(seed))
+        layers = []
+        for li, (cin, cout) in enumerate(NET_LAYERS):
+            real = NET_IN_REAL if li == 0 else cin
+            w = np.zeros((cout, 9, cin))
+            w[:, :, :real] = rng.standard_normal((cout, 9, real)) * np.sqrt(2.0 / (9 * real))
+            layers.append((w, np.zeros(cout)))
+        return self.pack(layers)
+
+    def set_params(self, params: np.ndarray) -> None:
+        p = _c(params, np.float32)
+        check(lib().hjb_net_set_params(self._h, _p(p)), "hjb_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        check(lib().hjb_net_get_params(self._h, _p(out)), "hjb_net_get_params")
+        return out.astype(np.float64)
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        check(lib().hjb_net_get_grads(self._h, _p(out)), "hjb_net_get_grads")
+        return out.astype(np.float64)
+
+    # ------------------------------------------------------------- compute
+    def forward(self, x, batch: int, host_out: bool = False):
+        out = np.empty((batch, self.H, self.W, 48), np.float32) if host_out else None
+        check(lib().hjb_net_forward(self._h, batch, ctypes.c_void_p(x.data_ptr()), _p(out)), "hjb_net_forward")
+        return out
+
+    def train_step(self, x, tval, tctrl, free, n_free: int, lr: float = 1e-3, w_value: float = 1.0,
+                   w_ctrl: float = 0.1):
+        batch = int(x.shape[0])
+        loss = np.zeros(2)
+        check(lib().hjb_net_train_step(self._h, batch, ctypes.c_void_p(x.data_ptr()),
+                                       ctypes.c_void_p(tval.data_ptr()), ctypes.c_void_p(tctrl.data_ptr()),
+                                       ctypes.c_void_p(free.data_ptr()), int(n_free), lr, w_value, w_ctrl,
+                                       _p(loss)), "hjb_net_train_step")
+        return float(loss[0]), float(loss[1])
+
+    def warm_values(self, index: int, mask, scale: float, umax: float, uob: float, u0) -> None:
+        check(lib().hjb_net_warm_values(self._h, index, ctypes.c_void_p(mask.data_ptr()), scale, umax, uob,
+                                        ctypes.c_void_p(u0.data_ptr())), "hjb_net_warm_values")

@@ -117,6 +117,20 @@ _SIGNATURES = {
     "hjb_batch_get_labels": (ctypes.c_int, [_P, _I32, _PTR]),
     "hjb_batch_get_uhat": (ctypes.c_int, [_P, _I32, _PTR]),
     "hjb_batch_destroy": (None, [_P]),
+    "hjb_net_param_count": (ctypes.c_longlong, []),
+    "hjb_net_create": (ctypes.c_int, [_I32, _I32, _I32, _PTR, ctypes.POINTER(_P)]),
+    "hjb_net_set_params": (ctypes.c_int, [_P, _PTR]),
+    "hjb_net_get_params": (ctypes.c_int, [_P, _PTR]),
+    "hjb_net_get_grads": (ctypes.c_int, [_P, _PTR]),
+    "hjb_net_forward": (ctypes.c_int, [_P, _I32, _PTR, _PTR]),
+    "hjb_net_train_step": (ctypes.c_int, [_P, _I32, _PTR, _PTR, _PTR, _PTR, ctypes.c_int64, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, _PTR]),
+    "hjb_net_warm_values": (ctypes.c_int, [_P, _I32, _PTR, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                           _PTR]),
+    "hjb_net_destroy": (None, [_P]),
+    "hjb_conv3x3_forward": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _I32, _PTR]),
+    "hjb_conv3x3_dgrad": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _PTR]),
+    "hjb_conv3x3_wgrad": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _PTR]),
 }
 
 _LIB = None

@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhjb.so")
-SOURCES = ["api.cu", "sweep.cu", "precompute.cu", "waves.cu", "tiles.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "sweep.cu", "precompute.cu", "waves.cu", "tiles.cu", "batch.cu", "net.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
