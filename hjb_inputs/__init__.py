@@ -279,6 +279,39 @@ def large_instance(seed: int = 5000, n: int = 4097, coarse_n: int = 129,
                     name=f"large-seed{seed}-n{n}")
 
 
+def warmstart_instance(seed: int, n: int = 257, coarse_n: int = 129) -> Instance:
+    """One instance of the warm-start training / evaluation recipe: 257^2 fine grid
+    with a 129^2 coarse grid, random Fourier speed clipped to [0.2, 1.8], 1-3
+    target discs of radius 0.05-0.15, 0-4 seeded rectangular obstacles (sides
+    0.1-0.4, speed 0, clear of the discs), sigma ~ U[0, 0.1], lambda ~ U[0.5, 2],
+    32 controls, 4-16 patches."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    speed = speed_fourier(n, rng)
+    k = int(rng.integers(1, 4))
+    centres = [tuple(rng.uniform(-0.7, 0.7, 2)) for _ in range(k)]
+    radii = list(rng.uniform(0.05, 0.15, k))
+    mask = disc_target(n, centres, radii)
+    rects = []
+    n_obst = int(rng.integers(0, 5))
+    while len(rects) < n_obst:
+        w, hh = rng.uniform(0.1, 0.4, 2)
+        cx, cy = rng.uniform(-0.8, 0.8, 2)
+        r = (cx - w / 2, cy - hh / 2, cx + w / 2, cy + hh / 2)
+        clear = all(math.hypot(max(abs(cx - c[0]) - w / 2, 0.0), max(abs(cy - c[1]) - hh / 2, 0.0)) > rad + 0.05
+                    for c, rad in zip(centres, radii))
+        if clear:
+            rects.append(r)
+    mask = add_rect_obstacles(n, mask, rects)
+    speed = speed.copy()
+    speed[mask == MASK_OBSTACLE] = 0.0
+    n_p = int(rng.integers(4, 17))
+    sec = sectors_about_centres(n, mask, centres, n_p)
+    sigma = float(rng.uniform(0.0, 0.1))
+    lam = float(rng.uniform(0.5, 2.0))
+    return Instance(n=n, controls=control_set(32), speed=speed, mask=mask, sector=sec, lam=lam,
+                    sigma=sigma, coarse_n=coarse_n, n_patches=n_p, name=f"warmstart-seed{seed}-n{n}")
+
+
 def random_values(n: int, seed: int, lo: float = 0.0, hi: float = 1.0,
                   mask: Optional[np.ndarray] = None) -> np.ndarray:
     """A seeded random value field (float64, n*n) for operator-level tests; target

@@ -411,6 +411,46 @@ int hjb_batch_get_labels(const hjb_batch* b, int32_t index, int8_t* label_out);
 /* hjb_batch_get_uhat -- instance `index`'s interpolated coarse value u_hat. */
 int hjb_batch_get_uhat(const hjb_batch* b, int32_t index, float* uhat_out);
 
+/* hjb_batch_coarse_solve -- the coarse solves alone (Section 4.3 "Pre-computation",
+ * sigma = 0) until each instance's sup-increment is <= tol_c; sweeps_out /
+ * fallback_out (nullable, count entries): sweeps per instance, 1 where a warm
+ * start fell back to the plain start.  stats: node updates, ms_total. */
+int hjb_batch_coarse_solve(hjb_batch* b, double tol_c, int32_t max_sweeps, hjb_stats* stats,
+                           int32_t* sweeps_out, uint8_t* fallback_out);
+
+/* hjb_batch_precompute -- coarse solves, interpolation, synthesis, labels (no
+ * patch solve): u_hat, a* and the coarse values become readable. */
+int hjb_batch_precompute(hjb_batch* b, double tol_c, hjb_stats* stats);
+
+/* hjb_batch_get_coarse_value -- instance `index`'s coarse value (coarse_n^2 floats). */
+int hjb_batch_get_coarse_value(const hjb_batch* b, int32_t index, float* uc_out);
+
+/* hjb_batch_net_inputs -- the warm-start network's input for every instance (all
+ * instances must share one coarse size nc): DEVICE bf16 [count][nc][nc][16],
+ * channels speed / 2, target indicator, obstacle indicator, 10 sigma, lambda / 2,
+ * then zeros, from the coarse data. */
+int hjb_batch_net_inputs(const hjb_batch* b, void* x);
+
+/* hjb_batch_net_targets -- after hjb_batch_precompute: the warm-start network's
+ * training targets on every instance's coarse grid (DEVICE, [count][nc][nc]):
+ * tval = u_c / u_max, tctrl = a* of the fine node under each coarse node, freem = 1
+ * on free coarse nodes (0 elsewhere, where tctrl is 0). */
+int hjb_batch_net_targets(const hjb_batch* b, float* tval, uint8_t* tctrl, uint8_t* freem);
+
+/* hjb_batch_coarse_warm -- later coarse solves start the free nodes of instances
+ * [first, first + count) from the network output net_out (DEVICE FP32
+ * [count][nc][nc][48], image 0 = instance `first`, channel 0 = u / u_max):
+ * clamp(o0 * u_max, 0, u_max), u_max = l/lambda + h_c l (instances never given a
+ * prediction keep the plain start).  After k_sweeps sweeps from the prediction,
+ * if the last sweep changed no node by more than fallback_tol the refined
+ * prediction is accepted as the coarse value (the patch builder's u_hat);
+ * otherwise that instance restarts from the plain initial value u_max and runs
+ * to tol_c (fallback).  u_hat only seeds and orders the fine solve: the fine
+ * fixed point does not depend on it (the scheme is a contraction), only the
+ * iteration count.  net_out = NULL restores the plain start. */
+int hjb_batch_coarse_warm(hjb_batch* b, const float* net_out, int32_t first, int32_t count,
+                          int32_t k_sweeps, double fallback_tol);
+
 /* hjb_batch_destroy -- frees the batch; NULL is ignored. */
 void hjb_batch_destroy(hjb_batch* b);
 
@@ -418,14 +458,15 @@ void hjb_batch_destroy(hjb_batch* b);
  * Not in the paper: a 6-layer 3x3 convolutional network (32 channels; input 5
  * channels: speed, target mask, obstacle mask, sigma, lambda, padded to 16;
  * output 33 channels: the coarse value over u_max and 32 control logits, padded
- * to 48; ReLU between layers; BF16 weights and activations, FP32 accumulation)
+ * to 48; dilations 1, 2, 4, 8, 16, 32 so the receptive field spans a 129^2 grid;
+ * ReLU between layers; BF16 weights and activations, FP32 accumulation)
  * whose value channel replaces the coarse solve's initial value (Section 4.3
  * "Initialization" uses a large constant).  Convolutions run as implicit GEMMs
  * on the tcgen05 tensor cores (forward and input gradient); the weight gradient
  * is an FP32 reduction.  Images are NHWC: pixel (b, y, x), channel c at
  * ((b H + y) W + x) C + c.  Parameters (FP32): per layer l = 0..5 the weights
  * w[cout][9][cin_store] (tap t = 3 (dy + 1) + (dx + 1) of the correlation
- * y[p] = sum_t w[., t, .] x[p + (dy, dx)], zero outside the image; cin_store = 16
+ * y[p] = sum_t w[., t, .] x[p + dil (dy, dx)], zero outside the image; cin_store = 16
  * for layer 0, 32 after) then the bias b[cout]; cout = 32, 33 for the last layer. */
 typedef struct hjb_net hjb_net;
 
@@ -459,6 +500,10 @@ int hjb_net_train_step(hjb_net* net, int32_t batch, const void* x, const float* 
                        const uint8_t* freem, int64_t n_free, float lr, float w_value, float w_ctrl,
                        double* loss_out);
 
+/* hjb_net_output_device -- the DEVICE FP32 [batch][H][W][48] output of the last
+ * hjb_net_forward (owned by the network; valid until its next forward). */
+int hjb_net_output_device(const hjb_net* net, const float** out);
+
 /* hjb_net_warm_values -- after hjb_net_forward: image `index`'s value channel x
  * scale, clamped to [0, umax], as a coarse initial value u0 (DEVICE, H*W floats);
  * target nodes 0, obstacle nodes uob (mask: DEVICE H*W codes). */
@@ -468,17 +513,18 @@ int hjb_net_warm_values(hjb_net* net, int32_t index, const uint8_t* mask, float 
 /* hjb_net_destroy -- NULL is ignored. */
 void hjb_net_destroy(hjb_net* net);
 
-/* Single 3x3 layers on host buffers (for checking against a reference):
- * x / dy / mask are bf16 bit patterns, NHWC; w is [cout][9][cin] FP32; cin, cout <= 48.
+/* Single 3x3 layers (dilation dil >= 1) on host buffers, for checking against a
+ * reference: x / dy / mask are bf16 bit patterns, NHWC; w is [cout][9][cin] FP32;
+ * cin, cout <= 48.
  *   hjb_conv3x3_forward: y = relu?(conv(x, w) + b)          (y: [B][H][W][cout] FP32)
  *   hjb_conv3x3_dgrad:   dx = conv^T(dy, w) * (mask > 0)    (mask nullable; dx: [B][H][W][cin])
  *   hjb_conv3x3_wgrad:   dw = sum_p dy (x) x-neighbourhood, db = sum_p dy (db nullable) */
-int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* x,
-                        const float* w, const float* b, int32_t relu, float* y);
-int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* dy,
-                      const float* w, const uint16_t* mask, float* dx);
-int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* x,
-                      const uint16_t* dy, float* dw, float* db);
+int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dil,
+                        const uint16_t* x, const float* w, const float* b, int32_t relu, float* y);
+int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dil,
+                      const uint16_t* dy, const float* w, const uint16_t* mask, float* dx);
+int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dil,
+                      const uint16_t* x, const uint16_t* dy, float* dw, float* db);
 
 #ifdef __cplusplus
 }

@@ -6,8 +6,9 @@ coarse solve (Section 4.3, "Initialization").  Each function here is the
 textbook definition of its layer written out in float64 numpy, with no
 blocking or reordering:
 
-* ``conv3x3``: y[b, i, j, o] = sum_{t, c} w[o, t, c] x[b, i + dy_t, j + dx_t, c]
-  (+ bias, optional ReLU), taps t = 3 (dy + 1) + (dx + 1), zero outside the image;
+* ``conv3x3``: y[b, i, j, o] = sum_{t, c} w[o, t, c] x[b, i + d dy_t, j + d dx_t, c]
+  (+ bias, optional ReLU), taps t = 3 (dy + 1) + (dx + 1), dilation d, zero outside
+  the image;
 * ``conv3x3_dgrad``: the adjoint of conv3x3 in x (optionally times a ReLU mask);
 * ``conv3x3_wgrad``: the gradient of sum(dy * conv3x3(x, w)) in w and the bias;
 * ``loss_and_grad``: squared value error plus softmax cross-entropy of the
@@ -43,41 +44,42 @@ def _shifted(x: np.ndarray, dy: int, dx: int) -> np.ndarray:
     s = np.zeros_like(x)
     i0, i1 = max(0, -dy), min(H, H - dy)
     j0, j1 = max(0, -dx), min(W, W - dx)
-    s[:, i0:i1, j0:j1] = x[:, i0 + dy:i1 + dy, j0 + dx:j1 + dx]
+    if i1 > i0 and j1 > j0:          # a shift past the image reads only zeros
+        s[:, i0:i1, j0:j1] = x[:, i0 + dy:i1 + dy, j0 + dx:j1 + dx]
     return s
 
 
-def conv3x3(x, w, b=None, relu=False):
+def conv3x3(x, w, b=None, relu=False, dil=1):
     x = np.asarray(x, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     y = np.zeros(x.shape[:3] + (w.shape[0],))
     for t, (dy, dx) in enumerate(TAPS):
-        y += np.einsum("bijc,oc->bijo", _shifted(x, dy, dx), w[:, t, :])
+        y += np.einsum("bijc,oc->bijo", _shifted(x, dil * dy, dil * dx), w[:, t, :])
     if b is not None:
         y += np.asarray(b, dtype=np.float64)
     return np.maximum(y, 0.0) if relu else y
 
 
-def conv3x3_dgrad(dy, w, mask=None):
-    """dx[b, i, j, c] = sum_{t, o} w[o, t, c] dy[b, i - dy_t, j - dx_t, o]."""
+def conv3x3_dgrad(dy, w, mask=None, dil=1):
+    """dx[b, i, j, c] = sum_{t, o} w[o, t, c] dy[b, i - d dy_t, j - d dx_t, o]."""
     dy = np.asarray(dy, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     dx = np.zeros(dy.shape[:3] + (w.shape[2],))
     for t, (oy, ox) in enumerate(TAPS):
-        dx += np.einsum("bijo,oc->bijc", _shifted(dy, -oy, -ox), w[:, t, :])
+        dx += np.einsum("bijo,oc->bijc", _shifted(dy, -dil * oy, -dil * ox), w[:, t, :])
     if mask is not None:
         dx = dx * (np.asarray(mask) > 0)
     return dx
 
 
-def conv3x3_wgrad(x, dy):
-    """dw[o, t, c] = sum_{b, i, j} dy[b, i, j, o] x[b, i + dy_t, j + dx_t, c];
+def conv3x3_wgrad(x, dy, dil=1):
+    """dw[o, t, c] = sum_{b, i, j} dy[b, i, j, o] x[b, i + d dy_t, j + d dx_t, c];
     db[o] = sum dy[..., o]."""
     x = np.asarray(x, dtype=np.float64)
     dy = np.asarray(dy, dtype=np.float64)
     dw = np.zeros((dy.shape[3], 9, x.shape[3]))
     for t, (oy, ox) in enumerate(TAPS):
-        dw[:, t, :] = np.einsum("bijo,bijc->oc", dy, _shifted(x, oy, ox))
+        dw[:, t, :] = np.einsum("bijo,bijc->oc", dy, _shifted(x, dil * oy, dil * ox))
     return dw, dy.sum(axis=(0, 1, 2))
 
 

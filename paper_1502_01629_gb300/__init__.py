@@ -328,10 +328,53 @@ class Batch:
         check(lib().hjb_batch_get_uhat(self._h, index, _p(out)), "hjb_batch_get_uhat")
         return out
 
+    # --------------------------------------------------- coarse / warm start
+    def coarse_solve(self, tol_c: float = 1e-6, max_sweeps: int = 100000, check_conv: bool = True):
+        """The coarse solves alone; returns (stats, sweeps per instance, fallback flags)."""
+        st = Stats()
+        sw = np.zeros(self.count, np.int32)
+        fb = np.zeros(self.count, np.uint8)
+        rc = lib().hjb_batch_coarse_solve(self._h, tol_c, max_sweeps, ctypes.byref(st), _p(sw), _p(fb))
+        if not (rc == HJB_ERR_NOT_CONVERGED and not check_conv):
+            check(rc, "hjb_batch_coarse_solve")
+        return st.as_dict(), sw, fb
+
+    def precompute(self, tol_c: float = 1e-6) -> dict:
+        st = Stats()
+        check(lib().hjb_batch_precompute(self._h, tol_c, ctypes.byref(st)), "hjb_batch_precompute")
+        return st.as_dict()
+
+    def get_coarse_value(self, index: int, nc: int) -> np.ndarray:
+        out = np.empty(nc * nc, np.float32)
+        check(lib().hjb_batch_get_coarse_value(self._h, index, _p(out)), "hjb_batch_get_coarse_value")
+        return out
+
+    def net_inputs(self, x) -> None:
+        """Fill the device tensor x (bf16 bits [count][nc][nc][16]) with the network input."""
+        check(lib().hjb_batch_net_inputs(self._h, ctypes.c_void_p(x.data_ptr())), "hjb_batch_net_inputs")
+
+    def net_targets(self, tval, tctrl, freem) -> None:
+        check(lib().hjb_batch_net_targets(self._h, ctypes.c_void_p(tval.data_ptr()),
+                                          ctypes.c_void_p(tctrl.data_ptr()), ctypes.c_void_p(freem.data_ptr())),
+              "hjb_batch_net_targets")
+
+    def coarse_warm(self, net_out_ptr, first: int = 0, count: int = 0, k_sweeps: int = 4,
+                    fallback_tol: float = 1e-2) -> None:
+        """Start later coarse solves of instances [first, first + count) from a
+        network output (device pointer or tensor, FP32 [count][nc][nc][48]); None
+        restores the plain start for every instance."""
+        if net_out_ptr is None:
+            check(lib().hjb_batch_coarse_warm(self._h, None, 0, 0, 0, 0.0), "hjb_batch_coarse_warm")
+            return
+        ptr = net_out_ptr.data_ptr() if hasattr(net_out_ptr, "data_ptr") else int(net_out_ptr)
+        check(lib().hjb_batch_coarse_warm(self._h, ctypes.c_void_p(ptr), first, count or self.count, k_sweeps,
+                                          fallback_tol), "hjb_batch_coarse_warm")
+
 
 # layer shapes of the warm-start network: (cin stored, cout)
 NET_LAYERS = [(16, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 33)]
 NET_IN_REAL = 5
+NET_DIL = [1, 2, 4, 8, 16, 32]   # dilation of each layer
 
 
 class Net:
@@ -417,6 +460,12 @@ class Net:
                                        ctypes.c_void_p(free.data_ptr()), int(n_free), lr, w_value, w_ctrl,
                                        _p(loss)), "hjb_net_train_step")
         return float(loss[0]), float(loss[1])
+
+    def output_ptr(self) -> int:
+        """Device address of the last forward's output (FP32 [batch][H][W][48])."""
+        p = ctypes.c_void_p()
+        check(lib().hjb_net_output_device(self._h, ctypes.byref(p)), "hjb_net_output_device")
+        return int(p.value)
 
     def warm_values(self, index: int, mask, scale: float, umax: float, uob: float, u0) -> None:
         check(lib().hjb_net_warm_values(self._h, index, ctypes.c_void_p(mask.data_ptr()), scale, umax, uob,

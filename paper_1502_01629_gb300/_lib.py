@@ -117,6 +117,13 @@ _SIGNATURES = {
     "hjb_batch_get_labels": (ctypes.c_int, [_P, _I32, _PTR]),
     "hjb_batch_get_uhat": (ctypes.c_int, [_P, _I32, _PTR]),
     "hjb_batch_destroy": (None, [_P]),
+    "hjb_batch_coarse_solve": (ctypes.c_int, [_P, _D, _I32, ctypes.POINTER(Stats), _PTR, _PTR]),
+    "hjb_batch_precompute": (ctypes.c_int, [_P, _D, ctypes.POINTER(Stats)]),
+    "hjb_batch_get_coarse_value": (ctypes.c_int, [_P, _I32, _PTR]),
+    "hjb_batch_net_inputs": (ctypes.c_int, [_P, _PTR]),
+    "hjb_batch_net_targets": (ctypes.c_int, [_P, _PTR, _PTR, _PTR]),
+    "hjb_net_output_device": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "hjb_batch_coarse_warm": (ctypes.c_int, [_P, _PTR, _I32, _I32, _I32, _D]),
     "hjb_net_param_count": (ctypes.c_longlong, []),
     "hjb_net_create": (ctypes.c_int, [_I32, _I32, _I32, _PTR, ctypes.POINTER(_P)]),
     "hjb_net_set_params": (ctypes.c_int, [_P, _PTR]),
@@ -128,9 +135,9 @@ _SIGNATURES = {
     "hjb_net_warm_values": (ctypes.c_int, [_P, _I32, _PTR, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                            _PTR]),
     "hjb_net_destroy": (None, [_P]),
-    "hjb_conv3x3_forward": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _I32, _PTR]),
-    "hjb_conv3x3_dgrad": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _PTR]),
-    "hjb_conv3x3_wgrad": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _PTR]),
+    "hjb_conv3x3_forward": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _I32, _PTR]),
+    "hjb_conv3x3_dgrad": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _PTR]),
+    "hjb_conv3x3_wgrad": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _I32, _PTR, _PTR, _PTR, _PTR]),
 }
 
 _LIB = None

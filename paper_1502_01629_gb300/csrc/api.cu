@@ -1180,7 +1180,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
     if (tol64 > 0.0 && rc == HJB_OK) {
         Timer t2(p->st);
         t2.mark();
-        CU(launch_promote(p->N, p->u32, p->u64, p->st));
+        CU(launch_promote(p->N, p->u32, p->mask, p->uob, p->u64, p->st));
         p->value_f64 = true;
         int r2 = residual64(p, &res);
         if (r2) return r2;
@@ -1209,7 +1209,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
             w32.nodes += ww.nodes;
             last = ww.last_increment;
             tw.mark();
-            CU(launch_promote(p->N, p->u32, p->u64, p->st));
+            CU(launch_promote(p->N, p->u32, p->mask, p->uob, p->u64, p->st));
             r2 = residual64(p, &res);
             if (r2) return r2;
             ++n_res;
@@ -1287,7 +1287,7 @@ int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64, 
             CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, nullptr, p->u64, p->uob, p->st));
         } else {
             // FP64 sweeps only if the FP32 result misses the FP64 residual tolerance
-            CU(launch_promote(p->N, p->u32, p->u64, p->st));
+            CU(launch_promote(p->N, p->u32, p->mask, p->uob, p->u64, p->st));
             int r2 = residual64(p, &res);
             if (r2) return r2;
             p->value_f64 = true;
@@ -1368,7 +1368,7 @@ int hjb_residual(hjb_problem* p, double* residual) {
     g_last_error.clear();
     if (!p || !residual) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     if (!p->value_f64) {
-        CU(launch_promote(p->N, p->u32, p->u64, p->st));
+        CU(launch_promote(p->N, p->u32, p->mask, p->uob, p->u64, p->st));
     }
     return residual64(p, residual);
 }

@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "hjb_kernels.h"
 #include "precompute_device.cuh"
 #include "sweep_device.cuh"
@@ -47,7 +49,7 @@ struct BatchInst {
     float band_w;
     float uc0;           // coarse initial value on free nodes: l/lambda + h_c l
     float uob32;         // value held on obstacle nodes
-    int pad;
+    float sigma;
     double uob64;
 };
 
@@ -103,6 +105,59 @@ __global__ void k_b_synthesis(const BatchInst* __restrict__ I, const int2* __res
     if ((threadIdx.x & 31) == 0 && wm >= 0) atomicMax(max_key + bl.x, wm);
 }
 
+// network input of each instance's coarse grid (bf16 [count][nc][nc][16]):
+// speed / 2, target indicator, obstacle indicator, 10 sigma, lambda / 2, zeros
+__global__ void k_b_net_inputs(const BatchInst* __restrict__ I, const int2* __restrict__ blk, int nc,
+                               __nv_bfloat16* x) {
+    const int2 bl = blk[blockIdx.x];
+    const BatchInst& B = I[bl.x];
+    const int k = bl.y + threadIdx.x;
+    if (k >= B.nc * B.nc) return;
+    const int mk = B.mask_c[k];
+    float v[16] = {};
+    v[0] = 0.5f * B.speed_c[k];
+    v[1] = mk == kTarget ? 1.0f : 0.0f;
+    v[2] = mk == kObstacle ? 1.0f : 0.0f;
+    v[3] = 10.0f * B.sigma;
+    v[4] = 0.5f * B.lambda;
+    __nv_bfloat16* o = x + ((size_t)bl.x * nc * nc + k) * 16;
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(v[c]);
+}
+
+// training targets at each instance's coarse nodes: u_c / u_max, the feedback
+// control a* of the fine node (rI, rJ), and 1 on free coarse nodes
+__global__ void k_b_net_targets(const BatchInst* __restrict__ I, const int2* __restrict__ blk, int nc,
+                                float* tval, uint8_t* tctrl, uint8_t* freem) {
+    const int2 bl = blk[blockIdx.x];
+    const BatchInst& B = I[bl.x];
+    const int k = bl.y + threadIdx.x;
+    if (k >= B.nc * B.nc) return;
+    const int n = B.g.n;
+    const int r = (n - 1) / (B.nc - 1);
+    const int ci = k % B.nc, cj = k / B.nc;
+    const size_t o = (size_t)bl.x * nc * nc + k;
+    const bool fr = B.mask_c[k] == kFree;
+    const int a = B.a[(size_t)(r * cj) * n + r * ci];
+    tval[o] = B.uc[k] / B.uc0;
+    tctrl[o] = (fr && a < 255) ? (uint8_t)a : 0;
+    freem[o] = (fr && a < 255) ? 1 : 0;
+}
+
+// coarse initial values from the network output (FP32 [count][nc][nc][48], value
+// channel 0 = u / u_max): clamp(o0 * u_max, 0, u_max) on free nodes
+__global__ void k_b_warm_values(const BatchInst* __restrict__ I, const int2* __restrict__ blk, int nc,
+                                const float* __restrict__ out, int first, int count,
+                                const long long* __restrict__ coarse_off, float* init) {
+    const int2 bl = blk[blockIdx.x];
+    if (bl.x < first || bl.x >= first + count) return;
+    const BatchInst& B = I[bl.x];
+    const int k = bl.y + threadIdx.x;
+    if (k >= B.nc * B.nc) return;
+    const float um = B.uc0;
+    const float v = out[((size_t)(bl.x - first) * nc * nc + k) * 48] * um;
+    init[coarse_off[bl.x] + k] = fminf(fmaxf(v, 0.0f), um);
+}
+
 // successors as indices of the concatenated arrays
 __global__ void k_b_successors(const BatchInst* __restrict__ I, const int2* __restrict__ blk,
                                int32_t* succ) {
@@ -133,9 +188,16 @@ __global__ void k_b_labels(const BatchInst* __restrict__ I, const int2* __restri
 // memory; each sweep updates every free coarse node in place (one warp per
 // node, lanes over the controls, SLscheme3 with sigma = 0) and ends with a
 // block barrier; stops when a sweep's sup-increment is <= tol.
+// With a warm start (init != nullptr) free nodes start from init (the
+// instance's slice of the concatenated coarse arrays) and the solve stops after
+// k_warm sweeps when the last sweep changed no node by more than tol_fb (the
+// refined prediction is accepted as the coarse value); otherwise the free nodes
+// restart from the plain initial value, the solve runs to tol and fallback[b]
+// is set.
 __global__ void __launch_bounds__(kCoarseThreads)
 k_b_coarse_solve(const BatchInst* __restrict__ I, const int* __restrict__ order, float tol,
-                 int max_sweeps, int* sweeps_out, float* inc_out) {
+                 int max_sweeps, int* sweeps_out, float* inc_out, const float* __restrict__ init,
+                 const long long* __restrict__ coarse_off, int k_warm, float tol_fb, uint8_t* fallback) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int b = order[blockIdx.x];
     const BatchInst& B = I[b];
@@ -149,11 +211,13 @@ k_b_coarse_solve(const BatchInst* __restrict__ I, const int* __restrict__ order,
     __shared__ int s_done;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = g.ctrl32[m];
+    const float* ini = init ? init + coarse_off[b] : nullptr;
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
         const int mk = g.mask[k];
-        su[k] = mk == kFree ? B.uc0 : (mk == kTarget ? 0.0f : g.uob32);
+        su[k] = mk == kFree ? (ini ? ini[k] : B.uc0) : (mk == kTarget ? 0.0f : g.uob32);
     }
     __syncthreads();
+    bool fell_back = false;
     auto C = [&](int m) { return sctrl[m]; };
     // a tolerance below half an FP32 ulp of the largest value could stall
     tol = fmaxf(tol, 1.01f * ldexpf(fmaxf(1.0f, B.uc0), -23));
@@ -180,14 +244,23 @@ k_b_coarse_solve(const BatchInst* __restrict__ I, const int* __restrict__ order,
         if (threadIdx.x == 0) {
             last = bm;
             s_done = bm <= tol ? 1 : 0;
+            if (ini && !fell_back && sweep == k_warm && !s_done) s_done = bm <= tol_fb ? 1 : 2;
         }
         __syncthreads();
-        if (s_done) break;
+        if (s_done == 1) break;
+        if (s_done == 2) {
+            // the prediction is too far off: the plain initial value instead
+            fell_back = true;
+            for (int k = threadIdx.x; k < Nc; k += blockDim.x)
+                if (g.mask[k] == kFree) su[k] = B.uc0;
+            __syncthreads();
+        }
     }
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) B.uc[k] = su[k];
     if (threadIdx.x == 0) {
         sweeps_out[b] = sweep;
         inc_out[b] = last;
+        if (fallback) fallback[b] = fell_back ? 1 : 0;
     }
 }
 
@@ -332,7 +405,10 @@ __global__ void k_b_promote(const BatchInst* __restrict__ I, const int2* __restr
     const int k = bl.y + threadIdx.x;
     if (k >= B.g.n * B.g.n) return;
     const float* src = (sweeps && (sweeps[bl.x] & 1)) ? ub : ua;
-    u64[B.node_off + k] = (double)src[B.node_off + k];
+    const int mk = B.g.mask[k];
+    // exact FP64 held values on non-free nodes (their FP32 rounding would move
+    // the FP64 fixed point)
+    u64[B.node_off + k] = mk == kFree ? (double)src[B.node_off + k] : (mk == kTarget ? 0.0 : B.uob64);
 }
 
 // Jacobi start: u = 0 on free and target nodes, the obstacle value elsewhere.
@@ -450,6 +526,13 @@ struct hjb_batch {
     GridSync* sync = nullptr;
     WaveResult* wres = nullptr;
     WaveResult* h_wres = nullptr;        // pinned
+    // warm start of the coarse solves
+    float* coarse_init = nullptr;        // Nc
+    long long* d_coarse_off = nullptr;   // count + 1
+    uint8_t* c_fallback = nullptr;       // count
+    bool warm_on = false;
+    int warm_k = 0;
+    double warm_tol = 0.0;
     std::vector<long long> n_free;       // free fine nodes per instance
     std::vector<long long> n_free_c;     // free coarse nodes per instance
     bool built = false;
@@ -787,6 +870,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         B.band_w = (float)(b->band_width * h);
         B.uc0 = (float)uob_c;
         B.uob32 = (float)uob;
+        B.sigma = (float)x.sigma;
         B.uob64 = uob;
         TileInst& T = b->htile[i];
         T = TileInst{};
@@ -868,6 +952,11 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     BCUP(dalloc(b->j_sweeps, count));
     BCUP(dalloc(b->n_active, 1));
     BCUP(dalloc(b->rank_boff, count + 1));
+    BCUP(dalloc(b->d_coarse_off, count + 1));
+    BCUP(dalloc(b->c_fallback, count));
+    BCUP(cudaMemsetAsync(b->c_fallback, 0, count, b->st));
+    BCUP(cudaMemcpyAsync(b->d_coarse_off, b->coarse_off.data(), sizeof(long long) * (count + 1),
+                         cudaMemcpyHostToDevice, b->st));
     BCUP(dalloc(b->n_waves_dev, 1));
     BCUP(dalloc(b->sync, 1));
     BCUP(dalloc(b->wres, 1));
@@ -912,6 +1001,7 @@ void hjb_batch_destroy(hjb_batch* b) {
     dfree(b->queue); dfree(b->qcount); dfree(b->step_inc); dfree(b->sched_count); dfree(b->sched_off);
     dfree(b->max_key); dfree(b->c_sweeps); dfree(b->c_inc); dfree(b->res_bits); dfree(b->margin);
     dfree(b->active); dfree(b->inc_bits); dfree(b->j_sweeps); dfree(b->n_active); dfree(b->sync);
+    dfree(b->coarse_init); dfree(b->d_coarse_off); dfree(b->c_fallback);
     dfree(b->cb_wave); dfree(b->cb_key); dfree(b->cb_list); dfree(b->cb_off); dfree(b->cb_count);
     dfree(b->wres); dfree(b->rank_flags); dfree(b->rank_scan); dfree(b->rank_boff); dfree(b->n_waves_dev);
     if (b->h_wres) cudaFreeHost(b->h_wres);
@@ -934,7 +1024,8 @@ size_t coarse_smem(const hjb_batch* b) {
 int stage_coarse(hjb_batch* b, double tol_c, int max_sweeps, long long* nodes, bool* conv) {
     count_launches(1);
     k_b_coarse_solve<<<b->count, kCoarseThreads, coarse_smem(b), b->st>>>(
-        b->dinst, b->corder, (float)tol_c, max_sweeps, b->c_sweeps, b->c_inc);
+        b->dinst, b->corder, (float)tol_c, max_sweeps, b->c_sweeps, b->c_inc,
+        b->warm_on ? b->coarse_init : nullptr, b->d_coarse_off, b->warm_k, (float)b->warm_tol, b->c_fallback);
     BCU(cudaGetLastError());
     std::vector<int> sw(b->count);
     BCU(cudaMemcpyAsync(sw.data(), b->c_sweeps, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->st));
@@ -1445,6 +1536,134 @@ int hjb_batch_get_uhat(const hjb_batch* b, int32_t index, float* uhat_out) {
     if (index < 0 || index >= b->count) return bfail(HJB_ERR_INVALID_ARG, "index %d out of range", index);
     const long long o = b->node_off[index], n = b->node_off[index + 1] - o;
     BCU(cudaMemcpyAsync(uhat_out, b->uhat + o, sizeof(float) * n, cudaMemcpyDeviceToHost, b->st));
+    BCU(cudaStreamSynchronize(b->st));
+    return HJB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------ warm-start support
+namespace {
+int same_coarse_size(const hjb_batch* b) {
+    const int nc = b->desc[0].coarse_n;
+    for (const auto& x : b->desc)
+        if (x.coarse_n != nc) return 0;
+    return nc;
+}
+}  // namespace
+
+extern "C" {
+
+int hjb_batch_net_inputs(const hjb_batch* b, void* x) {
+    clear_last_error();
+    if (!b || !x) return bfail(HJB_ERR_INVALID_ARG, "NULL argument");
+    const int nc = same_coarse_size(b);
+    if (!nc) return bfail(HJB_ERR_INVALID_ARG, "instances have different coarse sizes");
+    count_launches(1);
+    k_b_net_inputs<<<b->ncblk, kBT, 0, b->st>>>(b->dinst, b->cblk, nc, reinterpret_cast<__nv_bfloat16*>(x));
+    BCU(cudaGetLastError());
+    BCU(cudaStreamSynchronize(b->st));
+    return HJB_OK;
+}
+
+int hjb_batch_coarse_warm(hjb_batch* b, const float* net_out, int32_t first, int32_t count,
+                          int32_t k_sweeps, double fallback_tol) {
+    clear_last_error();
+    if (!b) return bfail(HJB_ERR_INVALID_ARG, "batch is NULL");
+    if (!net_out) {
+        b->warm_on = false;
+        return HJB_OK;
+    }
+    if (k_sweeps < 1 || !(fallback_tol > 0.0)) return bfail(HJB_ERR_INVALID_ARG, "bad k_sweeps / fallback_tol");
+    if (first < 0 || count < 1 || first + count > b->count)
+        return bfail(HJB_ERR_INVALID_ARG, "instances [%d, %d) out of range", first, first + count);
+    const int nc = same_coarse_size(b);
+    if (!nc) return bfail(HJB_ERR_INVALID_ARG, "instances have different coarse sizes");
+    if (!b->coarse_init) {
+        BCU(dalloc(b->coarse_init, (size_t)b->Nc));
+        // instances without a prediction keep the plain start
+        std::vector<float> plain((size_t)b->Nc);
+        for (int i = 0; i < b->count; ++i)
+            for (long long k = b->coarse_off[i]; k < b->coarse_off[i + 1]; ++k) plain[k] = b->hinst[i].uc0;
+        BCU(cudaMemcpy(b->coarse_init, plain.data(), sizeof(float) * plain.size(), cudaMemcpyHostToDevice));
+    }
+    count_launches(1);
+    k_b_warm_values<<<b->ncblk, kBT, 0, b->st>>>(b->dinst, b->cblk, nc, net_out, first, count, b->d_coarse_off,
+                                                 b->coarse_init);
+    BCU(cudaGetLastError());
+    BCU(cudaStreamSynchronize(b->st));
+    b->warm_on = true;
+    b->warm_k = k_sweeps;
+    b->warm_tol = fallback_tol;
+    return HJB_OK;
+}
+
+int hjb_batch_coarse_solve(hjb_batch* b, double tol_c, int32_t max_sweeps, hjb_stats* stats,
+                           int32_t* sweeps_out, uint8_t* fallback_out) {
+    clear_last_error();
+    fill_stats(stats);
+    if (!b) return bfail(HJB_ERR_INVALID_ARG, "batch is NULL");
+    if (!(tol_c > 0.0) || max_sweeps < 1) return bfail(HJB_ERR_INVALID_ARG, "bad tol_c / max_sweeps");
+    BTimer t(b->st);
+    long long nodes = 0;
+    bool conv = true;
+    int rc = stage_coarse(b, tol_c, max_sweeps, &nodes, &conv);
+    if (rc) return rc;
+    const double ms = t.stop();
+    if (sweeps_out) BCU(cudaMemcpy(sweeps_out, b->c_sweeps, sizeof(int) * b->count, cudaMemcpyDeviceToHost));
+    if (fallback_out) BCU(cudaMemcpy(fallback_out, b->c_fallback, b->count, cudaMemcpyDeviceToHost));
+    rc = conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
+    if (stats) {
+        stats->node_updates = nodes;
+        stats->node_control_updates = nodes * b->na;
+        stats->ms_stage[3] = ms;
+        stats->ms_total = ms;
+        stats->status = rc;
+    }
+    return rc;
+}
+
+int hjb_batch_precompute(hjb_batch* b, double tol_c, hjb_stats* stats) {
+    clear_last_error();
+    fill_stats(stats);
+    if (!b) return bfail(HJB_ERR_INVALID_ARG, "batch is NULL");
+    if (!(tol_c > 0.0)) return bfail(HJB_ERR_INVALID_ARG, "bad tol_c");
+    BTimer t(b->st);
+    long long nodes = 0;
+    bool conv = true;
+    int rc = stage_coarse(b, tol_c, 100000, &nodes, &conv);
+    if (rc) return rc;
+    rc = stage_precompute(b);
+    if (rc) return rc;
+    BCU(cudaStreamSynchronize(b->st));
+    const double ms = t.stop();
+    if (stats) {
+        stats->node_updates = nodes;
+        stats->node_control_updates = nodes * b->na;
+        stats->ms_total = ms;
+        stats->status = conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
+    }
+    return conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
+}
+
+int hjb_batch_net_targets(const hjb_batch* b, float* tval, uint8_t* tctrl, uint8_t* freem) {
+    clear_last_error();
+    if (!b || !tval || !tctrl || !freem) return bfail(HJB_ERR_INVALID_ARG, "NULL argument");
+    const int nc = same_coarse_size(b);
+    if (!nc) return bfail(HJB_ERR_INVALID_ARG, "instances have different coarse sizes");
+    count_launches(1);
+    k_b_net_targets<<<b->ncblk, kBT, 0, b->st>>>(b->dinst, b->cblk, nc, tval, tctrl, freem);
+    BCU(cudaGetLastError());
+    BCU(cudaStreamSynchronize(b->st));
+    return HJB_OK;
+}
+
+int hjb_batch_get_coarse_value(const hjb_batch* b, int32_t index, float* uc_out) {
+    clear_last_error();
+    if (!b || !uc_out) return bfail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (index < 0 || index >= b->count) return bfail(HJB_ERR_INVALID_ARG, "index %d out of range", index);
+    const long long o = b->coarse_off[index], n = b->coarse_off[index + 1] - o;
+    BCU(cudaMemcpyAsync(uc_out, b->uc + o, sizeof(float) * n, cudaMemcpyDeviceToHost, b->st));
     BCU(cudaStreamSynchronize(b->st));
     return HJB_OK;
 }

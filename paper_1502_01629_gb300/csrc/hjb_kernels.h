@@ -86,7 +86,9 @@ cudaError_t launch_strided_gather(int nb, int stride, const int32_t* off, int32_
 cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const uint8_t* mask,
                          int n_patches, int n_bands, int32_t* bin_count, int32_t* bin_off,
                          int32_t* order, int32_t* band_off, cudaStream_t st);
-cudaError_t launch_promote(int N, const float* u32, double* u64, cudaStream_t st);
+// u64 = u32 on free nodes, the exact FP64 held values on the others
+cudaError_t launch_promote(int N, const float* u32, const uint8_t* mask, double uob64, double* u64,
+                           cudaStream_t st);
 cudaError_t launch_demote(int N, const double* u64, float* u32, cudaStream_t st);
 cudaError_t launch_init_values(int N, const uint8_t* mask, float free_val, float uob,
                                float* u32, double* u64, double uob64, cudaStream_t st);

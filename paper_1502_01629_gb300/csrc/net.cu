@@ -46,7 +46,7 @@ template <int CIN, int NPAD, bool OUT_F32>
 __global__ void __launch_bounds__(kConvThreads)
 k_conv3x3_tc(const bf16* __restrict__ x, const uint8_t* __restrict__ wpack,
              const float* __restrict__ bias, int nbias, int relu, const bf16* __restrict__ mask, int total,
-             int H, int W, void* __restrict__ out, int* err) {
+             int H, int W, int dil, void* __restrict__ out, int* err) {
     constexpr int K = 9 * CIN;
     constexpr int KC = K / 8;                      // 16-byte chunks per operand row
     constexpr int TMC = NPAD <= 32 ? 32 : 64;      // tensor-memory columns
@@ -73,7 +73,7 @@ k_conv3x3_tc(const bf16* __restrict__ x, const uint8_t* __restrict__ wpack,
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (p < total) {
             const int b = (int)(p / HW), r = (int)(p - (long long)b * HW);
-            const int yy = r / W + t / 3 - 1, xq = r % W + t % 3 - 1;
+            const int yy = r / W + (t / 3 - 1) * dil, xq = r % W + (t % 3 - 1) * dil;
             if (yy >= 0 && yy < H && xq >= 0 && xq < W)
                 v = *reinterpret_cast<const uint4*>(x + ((size_t)b * HW + (size_t)yy * W + xq) * CIN + cc * 8);
         }
@@ -142,7 +142,7 @@ k_conv3x3_tc(const bf16* __restrict__ x, const uint8_t* __restrict__ wpack,
 template <int CIN, int NPAD>
 __global__ void __launch_bounds__(256)
 k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int total, int H, int W,
-                int chunk, int cout, float* dw, float* db) {
+                int dil, int chunk, int cout, float* dw, float* db) {
     constexpr int K = 9 * CIN;
     constexpr int NOUT = NPAD * K;
     constexpr int PER = (NOUT + 255) / 256;
@@ -171,7 +171,7 @@ k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int tot
             float v = 0.0f;
             if (p < pend) {
                 const int b = (int)(p / HW), r = (int)(p - (long long)b * HW);
-                const int yy = r / W + t / 3 - 1, xq = r % W + t % 3 - 1;
+                const int yy = r / W + (t / 3 - 1) * dil, xq = r % W + (t % 3 - 1) * dil;
                 if (yy >= 0 && yy < H && xq >= 0 && xq < W)
                     v = __bfloat162float(x[((size_t)b * HW + (size_t)yy * W + xq) * CIN + ci]);
             }
@@ -303,31 +303,31 @@ __global__ void k_warm_values(const float* __restrict__ out, const uint8_t* __re
 // ----------------------------------------------------------- launch helpers
 template <int CIN, int NPAD, bool F32>
 cudaError_t conv_impl(const bf16* x, const uint8_t* wpack, const float* bias, int nbias, int relu,
-                      const bf16* mask, int total, int H, int W, void* out, int* err, cudaStream_t st) {
+                      const bf16* mask, int total, int H, int W, int dil, void* out, int* err, cudaStream_t st) {
     const size_t smem = (size_t)(128 + NPAD) * 9 * CIN * 2;
     auto kern = k_conv3x3_tc<CIN, NPAD, F32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    kern<<<(total + 127) / 128, kConvThreads, smem, st>>>(x, wpack, bias, nbias, relu, mask, total, H, W, out,
-                                                          err);
+    kern<<<(total + 127) / 128, kConvThreads, smem, st>>>(x, wpack, bias, nbias, relu, mask, total, H, W, dil,
+                                                          out, err);
     return cudaGetLastError();
 }
 
 cudaError_t conv_launch(int cinp, int npad, bool f32, const bf16* x, const uint8_t* wpack, const float* bias,
-                        int nbias, int relu, const bf16* mask, int total, int H, int W, void* out, int* err,
+                        int nbias, int relu, const bf16* mask, int total, int H, int W, int dil, void* out, int* err,
                         cudaStream_t st) {
-#define HJB_CONV(C, N)                                                                                         \
-    if (cinp == C && npad == N)                                                                                \
-        return f32 ? conv_impl<C, N, true>(x, wpack, bias, nbias, relu, mask, total, H, W, out, err, st)      \
-                   : conv_impl<C, N, false>(x, wpack, bias, nbias, relu, mask, total, H, W, out, err, st);
+#define HJB_CONV(C, N)                                                                                              \
+    if (cinp == C && npad == N)                                                                                     \
+        return f32 ? conv_impl<C, N, true>(x, wpack, bias, nbias, relu, mask, total, H, W, dil, out, err, st)      \
+                   : conv_impl<C, N, false>(x, wpack, bias, nbias, relu, mask, total, H, W, dil, out, err, st);
     HJB_CONV(16, 32) HJB_CONV(16, 48) HJB_CONV(32, 32) HJB_CONV(32, 48) HJB_CONV(48, 32) HJB_CONV(48, 48)
 #undef HJB_CONV
     return cudaErrorInvalidValue;
 }
 
 template <int CIN, int NPAD>
-cudaError_t wgrad_impl(const bf16* x, const bf16* dy, int total, int H, int W, int cout, float* dw,
+cudaError_t wgrad_impl(const bf16* x, const bf16* dy, int total, int H, int W, int dil, int cout, float* dw,
                        float* db, cudaStream_t st) {
     const size_t smem = (size_t)32 * (NPAD + 9 * CIN) * sizeof(float);
     auto kern = k_conv3x3_wgrad<CIN, NPAD>;
@@ -335,14 +335,14 @@ cudaError_t wgrad_impl(const bf16* x, const bf16* dy, int total, int H, int W, i
     if (e != cudaSuccess) return e;
     const int chunk = 2048;
     count_launches(1);
-    kern<<<(total + chunk - 1) / chunk, 256, smem, st>>>(x, dy, total, H, W, chunk, cout, dw, db);
+    kern<<<(total + chunk - 1) / chunk, 256, smem, st>>>(x, dy, total, H, W, dil, chunk, cout, dw, db);
     return cudaGetLastError();
 }
 
-cudaError_t wgrad_launch(int cinp, int npad, const bf16* x, const bf16* dy, int total, int H, int W,
+cudaError_t wgrad_launch(int cinp, int npad, const bf16* x, const bf16* dy, int total, int H, int W, int dil,
                          int cout, float* dw, float* db, cudaStream_t st) {
 #define HJB_WG(C, N) \
-    if (cinp == C && npad == N) return wgrad_impl<C, N>(x, dy, total, H, W, cout, dw, db, st);
+    if (cinp == C && npad == N) return wgrad_impl<C, N>(x, dy, total, H, W, dil, cout, dw, db, st);
     HJB_WG(16, 32) HJB_WG(16, 48) HJB_WG(32, 32) HJB_WG(32, 48) HJB_WG(48, 32) HJB_WG(48, 48)
 #undef HJB_WG
     return cudaErrorInvalidValue;
@@ -369,10 +369,13 @@ constexpr int kOutCh = 33;       // value + 32 control logits
 constexpr int kOutPad = 48;
 
 struct LayerShape {
-    int cin, cinp, cout, npad;
+    int cin, cinp, cout, npad, dil;
 };
-constexpr LayerShape kShape[kLayers] = {{kInCh, kInPad, kCh, 32}, {kCh, kCh, kCh, 32}, {kCh, kCh, kCh, 32},
-                                        {kCh, kCh, kCh, 32},      {kCh, kCh, kCh, 32}, {kCh, kCh, kOutCh, kOutPad}};
+// dilations 1, 2, ..., 32: the receptive field (127 cells) spans the 129^2 coarse
+// grid, so every pixel sees the targets its travel time depends on
+constexpr LayerShape kShape[kLayers] = {{kInCh, kInPad, kCh, 32, 1}, {kCh, kCh, kCh, 32, 2},
+                                        {kCh, kCh, kCh, 32, 4},      {kCh, kCh, kCh, 32, 8},
+                                        {kCh, kCh, kCh, 32, 16},     {kCh, kCh, kOutCh, kOutPad, 32}};
 
 int nfail(int code, const char* fmt, ...) {
     char buf[512];
@@ -463,11 +466,11 @@ int forward(hjb_net* nt, int batch, const bf16* x) {
         const float* b = nt->params + param_offset_b(l);
         if (l + 1 < kLayers) {
             NCU(conv_launch(L.cinp, L.npad, false, in, nt->wfwd[l], b, L.cout, 1, nullptr, total, nt->H, nt->W,
-                            nt->act[l + 1], nt->err, nt->st));
+                            L.dil, nt->act[l + 1], nt->err, nt->st));
             in = nt->act[l + 1];
         } else {
             NCU(conv_launch(L.cinp, L.npad, true, in, nt->wfwd[l], b, L.cout, 0, nullptr, total, nt->H, nt->W,
-                            nt->out, nt->err, nt->st));
+                            L.dil, nt->out, nt->err, nt->st));
         }
     }
     return HJB_OK;
@@ -551,6 +554,13 @@ int hjb_net_get_params(const hjb_net* nt, float* params) {
     return HJB_OK;
 }
 
+int hjb_net_output_device(const hjb_net* nt, const float** out) {
+    clear_last_error();
+    if (!nt || !out) return nfail(HJB_ERR_INVALID_ARG, "NULL argument");
+    *out = nt->out;
+    return HJB_OK;
+}
+
 int hjb_net_get_grads(const hjb_net* nt, float* grads) {
     clear_last_error();
     if (!nt || !grads) return nfail(HJB_ERR_INVALID_ARG, "NULL argument");
@@ -593,12 +603,12 @@ int hjb_net_train_step(hjb_net* nt, int32_t batch, const void* x, const float* t
     for (int l = kLayers - 1; l >= 0; --l) {
         const LayerShape& L = kShape[l];
         const bf16* xin = l == 0 ? x0 : nt->act[l];
-        NCU(wgrad_launch(L.cinp, L.npad, xin, dzl, total, nt->H, nt->W, L.cout,
+        NCU(wgrad_launch(L.cinp, L.npad, xin, dzl, total, nt->H, nt->W, L.dil, L.cout,
                          nt->grads + param_offset_w(l), nt->grads + param_offset_b(l), nt->st));
         if (l > 0) {
             bf16* dnext = nt->dz[l & 1];
             NCU(conv_launch(L.npad, 32, false, dzl, nt->wdgr[l], nullptr, 0, 0, nt->act[l], total, nt->H,
-                            nt->W, dnext, nt->err, nt->st));
+                            nt->W, L.dil, dnext, nt->err, nt->st));
             dzl = dnext;
         }
     }
@@ -683,13 +693,18 @@ int check_layer_args(int batch, int H, int W, int cin, int cout) {
     if (cin < 1 || cin > 48 || cout < 1 || cout > 48) return nfail(HJB_ERR_INVALID_ARG, "cin, cout must be 1..48");
     return HJB_OK;
 }
+int check_dil(int dil) {
+    if (dil < 1 || dil > 1024) return nfail(HJB_ERR_INVALID_ARG, "dilation must be 1..1024");
+    return HJB_OK;
+}
 }  // namespace
 
-int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* x,
-                        const float* w, const float* b, int32_t relu, float* y) {
+int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dil,
+                        const uint16_t* x, const float* w, const float* b, int32_t relu, float* y) {
     clear_last_error();
     if (!x || !w || !y) return nfail(HJB_ERR_INVALID_ARG, "NULL argument");
     int rc = check_layer_args(batch, H, W, cin, cout);
+    if (!rc) rc = check_dil(dil);
     if (rc) return rc;
     const long long P = (long long)batch * H * W;
     const int cinp = pad_channels(cin), npad = pad_outputs(cout);
@@ -709,7 +724,8 @@ int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_
     count_launches(1);
     k_pack_fwd<<<(npad * 9 * cinp + 255) / 256, 256>>>(B.w, cout, cin, cinp, npad, B.wp);
     NCU(cudaGetLastError());
-    NCU(conv_launch(cinp, npad, true, B.x, B.wp, B.b, cout, relu, nullptr, (int)P, H, W, B.out, B.err, nullptr));
+    NCU(conv_launch(cinp, npad, true, B.x, B.wp, B.b, cout, relu, nullptr, (int)P, H, W, dil, B.out, B.err,
+                    nullptr));
     std::vector<float> h((size_t)P * npad);
     NCU(cudaMemcpy(h.data(), B.out, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
     int e = 0;
@@ -720,11 +736,12 @@ int hjb_conv3x3_forward(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_
     return HJB_OK;
 }
 
-int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* dy,
-                      const float* w, const uint16_t* mask, float* dx) {
+int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dil,
+                      const uint16_t* dy, const float* w, const uint16_t* mask, float* dx) {
     clear_last_error();
     if (!dy || !w || !dx) return nfail(HJB_ERR_INVALID_ARG, "NULL argument");
     int rc = check_layer_args(batch, H, W, cin, cout);
+    if (!rc) rc = check_dil(dil);
     if (rc) return rc;
     const long long P = (long long)batch * H * W;
     const int coutp = pad_channels(cout), npad = pad_outputs(cin);
@@ -744,7 +761,8 @@ int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t 
     count_launches(1);
     k_pack_dgrad<<<(npad * 9 * coutp + 255) / 256, 256>>>(B.w, cout, cin, coutp, npad, B.wp);
     NCU(cudaGetLastError());
-    NCU(conv_launch(coutp, npad, true, B.x, B.wp, nullptr, 0, 0, B.mask, (int)P, H, W, B.out, B.err, nullptr));
+    NCU(conv_launch(coutp, npad, true, B.x, B.wp, nullptr, 0, 0, B.mask, (int)P, H, W, dil, B.out, B.err,
+                    nullptr));
     std::vector<float> h((size_t)P * npad);
     NCU(cudaMemcpy(h.data(), B.out, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
     int e = 0;
@@ -755,11 +773,12 @@ int hjb_conv3x3_dgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t 
     return HJB_OK;
 }
 
-int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, const uint16_t* x,
-                      const uint16_t* dy, float* dw, float* db) {
+int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dil,
+                      const uint16_t* x, const uint16_t* dy, float* dw, float* db) {
     clear_last_error();
     if (!x || !dy || !dw) return nfail(HJB_ERR_INVALID_ARG, "NULL argument");
     int rc = check_layer_args(batch, H, W, cin, cout);
+    if (!rc) rc = check_dil(dil);
     if (rc) return rc;
     const long long P = (long long)batch * H * W;
     const int cinp = pad_channels(cin), npad = pad_outputs(cout);
@@ -772,7 +791,7 @@ int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t 
     NCU(cudaMalloc(&B.b, sizeof(float) * cout));
     NCU(cudaMemset(B.w, 0, sizeof(float) * cout * 9 * cinp));
     NCU(cudaMemset(B.b, 0, sizeof(float) * cout));
-    NCU(wgrad_launch(cinp, npad, B.x, B.y, (int)P, H, W, cout, B.w, B.b, nullptr));
+    NCU(wgrad_launch(cinp, npad, B.x, B.y, (int)P, H, W, dil, cout, B.w, B.b, nullptr));
     std::vector<float> h((size_t)cout * 9 * cinp);
     NCU(cudaMemcpy(h.data(), B.w, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
     for (int n = 0; n < cout; ++n)

@@ -174,9 +174,15 @@ __global__ void k_band_off(int n_bands, int stride, const int32_t* __restrict__ 
     if (b <= n_bands) band_off[b] = bin_off[b * stride];
 }
 
-__global__ void k_promote(int N, const float* __restrict__ a, double* b) {
+// u64 = u32 on free nodes; the exact FP64 held values elsewhere (0 on targets,
+// the obstacle value on obstacles -- promoting its FP32 rounding would move the
+// FP64 fixed point)
+__global__ void k_promote(int N, const float* __restrict__ a, const uint8_t* __restrict__ mask, double uob64,
+                          double* b) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) b[k] = (double)a[k];
+    if (k >= N) return;
+    const int mk = mask[k];
+    b[k] = mk == kFree ? (double)a[k] : (mk == kTarget ? 0.0 : uob64);
 }
 
 __global__ void k_demote(int N, const double* __restrict__ a, float* b) {
@@ -325,9 +331,10 @@ cudaError_t launch_strided_gather(int nb, int stride, const int32_t* off, int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_promote(int N, const float* u32, double* u64, cudaStream_t st) {
+cudaError_t launch_promote(int N, const float* u32, const uint8_t* mask, double uob64, double* u64,
+                           cudaStream_t st) {
     count_launches(1);
-    k_promote<<<blocks_for(N), kThreads, 0, st>>>(N, u32, u64);
+    k_promote<<<blocks_for(N), kThreads, 0, st>>>(N, u32, mask, uob64, u64);
     return cudaGetLastError();
 }
 

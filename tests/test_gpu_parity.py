@@ -381,3 +381,20 @@ def test_large_workload_full_size_sampled():
     # obstacle nodes hold l/lambda + h l (R16); the two sides round the formula
     # differently in the last place
     np.testing.assert_allclose(u[inst.mask == hi.MASK_OBSTACLE], O.u_max, rtol=0, atol=1e-12)
+
+
+def test_obstacle_values_stay_exact_in_fp64():
+    """Obstacle nodes hold l/lambda + h l; with a lambda whose held value is not
+    an FP32 number, promoting the FP32 field must not carry the rounded value
+    into the FP64 polish (it would move the FP64 fixed point near obstacles)."""
+    inst = hi.warmstart_instance(7001, n=65, coarse_n=33)
+    assert (inst.mask == hi.MASK_OBSTACLE).any()
+    O = oracle.Problem.from_instance(inst)
+    assert float(np.float32(O.u_max)) != O.u_max
+    u_ref, _, _ = O.solve(scheme=3, tol=1e-14)
+    with P_gpu(inst) as G:
+        G.coarse_solve(tol_c=1e-6)
+        G.build_patches()
+        st = G.solve_patches(tol32=3e-7, tol64=1e-12)
+        assert st["residual"] <= 1e-12
+        np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)

@@ -51,24 +51,50 @@ def test_conv3x3_matches_scipy_correlation():
     np.testing.assert_array_equal(cn.conv3x3(x, wid), x)
 
 
-def test_dgrad_is_the_adjoint_of_conv3x3():
+def test_taps_past_the_image_read_zero():
+    rng = _rng(13)
+    x = rng.standard_normal((1, 4, 5, 2))
+    w = rng.standard_normal((3, 9, 2))
+    # dilation 8 > image: only the centre tap sees the image
+    np.testing.assert_allclose(cn.conv3x3(x, w, dil=8), np.einsum("bijc,oc->bijo", x, w[:, 4, :]),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_dilated_conv3x3_is_a_zero_interleaved_5x5_correlation():
+    from scipy.signal import correlate2d
+    rng = _rng(12)
+    x = rng.standard_normal((1, 10, 9, 2))
+    w = rng.standard_normal((3, 9, 2))
+    y = cn.conv3x3(x, w, dil=2)
+    for o in range(3):
+        ref = np.zeros((10, 9))
+        for c in range(2):
+            k5 = np.zeros((5, 5))
+            k5[::2, ::2] = w[o, :, c].reshape(3, 3)
+            ref += correlate2d(x[0, :, :, c], k5, mode="same", boundary="fill", fillvalue=0.0)
+        np.testing.assert_allclose(y[0, :, :, o], ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dil", [1, 3])
+def test_dgrad_is_the_adjoint_of_conv3x3(dil):
     rng = _rng(2)
     x = rng.standard_normal((2, 7, 5, 6))
     dy = rng.standard_normal((2, 7, 5, 4))
     w = rng.standard_normal((4, 9, 6))
-    lhs = (cn.conv3x3(x, w) * dy).sum()
-    rhs = (x * cn.conv3x3_dgrad(dy, w)).sum()
+    lhs = (cn.conv3x3(x, w, dil=dil) * dy).sum()
+    rhs = (x * cn.conv3x3_dgrad(dy, w, dil=dil)).sum()
     assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
 
 
-def test_wgrad_is_the_gradient_of_the_pairing():
+@pytest.mark.parametrize("dil", [1, 2])
+def test_wgrad_is_the_gradient_of_the_pairing(dil):
     rng = _rng(3)
     x = rng.standard_normal((2, 6, 8, 3))
     dy = rng.standard_normal((2, 6, 8, 5))
     w = rng.standard_normal((5, 9, 3))
     b = rng.standard_normal(5)
-    dw, db = cn.conv3x3_wgrad(x, dy)
-    f = lambda ww, bb: (cn.conv3x3(x, ww, bb) * dy).sum()
+    dw, db = cn.conv3x3_wgrad(x, dy, dil=dil)
+    f = lambda ww, bb: (cn.conv3x3(x, ww, bb, dil=dil) * dy).sum()
     base = f(w, b)
     for (o, t, c) in [(0, 0, 0), (4, 8, 2), (2, 4, 1), (1, 3, 0)]:
         e = np.zeros_like(w)
@@ -115,13 +141,13 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-SHAPES = [(2, 17, 23, 5, 32), (1, 33, 33, 32, 32), (3, 9, 14, 32, 33), (1, 12, 40, 48, 32),
-          (2, 11, 13, 16, 48), (1, 5, 7, 3, 7)]
+SHAPES = [(2, 17, 23, 5, 32, 1), (1, 33, 33, 32, 32, 4), (3, 9, 14, 32, 33, 1), (1, 12, 40, 48, 32, 16),
+          (2, 11, 13, 16, 48, 3), (1, 5, 7, 3, 7, 2)]
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("B,H,W,cin,cout", SHAPES, ids=[str(s) for s in SHAPES])
-def test_conv3x3_forward_on_tensor_cores(L, B, H, W, cin, cout):
+@pytest.mark.parametrize("B,H,W,cin,cout,dil", SHAPES, ids=[str(s) for s in SHAPES])
+def test_conv3x3_forward_on_tensor_cores(L, B, H, W, cin, cout, dil):
     rng = _rng(10 + cin + cout)
     x = cn.bf16_round(rng.uniform(-1, 1, (B, H, W, cin)))
     w = rng.standard_normal((cout, 9, cin)) * 0.2
@@ -131,40 +157,40 @@ def test_conv3x3_forward_on_tensor_cores(L, B, H, W, cin, cout):
         xb = np.ascontiguousarray(cn.bf16_bits(x))
         wf = np.ascontiguousarray(w, np.float32)
         bf = np.ascontiguousarray(b, np.float32)
-        rc = L.lib().hjb_conv3x3_forward(B, H, W, cin, cout, _p(xb), _p(wf), _p(bf), relu, _p(y))
+        rc = L.lib().hjb_conv3x3_forward(B, H, W, cin, cout, dil, _p(xb), _p(wf), _p(bf), relu, _p(y))
         assert rc == 0, L.lib().hjb_last_error()
-        ref = cn.conv3x3(x, cn.bf16_round(wf), bf.astype(np.float64), relu=bool(relu))
+        ref = cn.conv3x3(x, cn.bf16_round(wf), bf.astype(np.float64), relu=bool(relu), dil=dil)
         np.testing.assert_allclose(y, ref, rtol=0, atol=1e-4 * max(1.0, np.abs(ref).max()))
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("B,H,W,cin,cout", SHAPES, ids=[str(s) for s in SHAPES])
-def test_conv3x3_dgrad_on_tensor_cores(L, B, H, W, cin, cout):
+@pytest.mark.parametrize("B,H,W,cin,cout,dil", SHAPES, ids=[str(s) for s in SHAPES])
+def test_conv3x3_dgrad_on_tensor_cores(L, B, H, W, cin, cout, dil):
     rng = _rng(20 + cin + cout)
     dy = cn.bf16_round(rng.standard_normal((B, H, W, cout)))
     w = rng.standard_normal((cout, 9, cin)) * 0.2
     mask = cn.bf16_round(np.maximum(rng.standard_normal((B, H, W, cin)), 0.0))
     dx = np.empty((B, H, W, cin), np.float32)
     wf = np.ascontiguousarray(w, np.float32)
-    rc = L.lib().hjb_conv3x3_dgrad(B, H, W, cin, cout, _p(np.ascontiguousarray(cn.bf16_bits(dy))), _p(wf),
-                                   _p(np.ascontiguousarray(cn.bf16_bits(mask))), _p(dx))
+    rc = L.lib().hjb_conv3x3_dgrad(B, H, W, cin, cout, dil, _p(np.ascontiguousarray(cn.bf16_bits(dy))),
+                                   _p(wf), _p(np.ascontiguousarray(cn.bf16_bits(mask))), _p(dx))
     assert rc == 0, L.lib().hjb_last_error()
-    ref = cn.conv3x3_dgrad(dy, cn.bf16_round(wf), mask)
+    ref = cn.conv3x3_dgrad(dy, cn.bf16_round(wf), mask, dil=dil)
     np.testing.assert_allclose(dx, ref, rtol=0, atol=1e-4 * max(1.0, np.abs(ref).max()))
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("B,H,W,cin,cout", SHAPES[:4], ids=[str(s) for s in SHAPES[:4]])
-def test_conv3x3_wgrad(L, B, H, W, cin, cout):
+@pytest.mark.parametrize("B,H,W,cin,cout,dil", SHAPES[:4], ids=[str(s) for s in SHAPES[:4]])
+def test_conv3x3_wgrad(L, B, H, W, cin, cout, dil):
     rng = _rng(30 + cin + cout)
     x = cn.bf16_round(rng.uniform(-1, 1, (B, H, W, cin)))
     dy = cn.bf16_round(rng.standard_normal((B, H, W, cout)) * 0.1)
     dw = np.empty((cout, 9, cin), np.float32)
     db = np.empty(cout, np.float32)
-    rc = L.lib().hjb_conv3x3_wgrad(B, H, W, cin, cout, _p(np.ascontiguousarray(cn.bf16_bits(x))),
+    rc = L.lib().hjb_conv3x3_wgrad(B, H, W, cin, cout, dil, _p(np.ascontiguousarray(cn.bf16_bits(x))),
                                    _p(np.ascontiguousarray(cn.bf16_bits(dy))), _p(dw), _p(db))
     assert rc == 0, L.lib().hjb_last_error()
-    rdw, rdb = cn.conv3x3_wgrad(x, dy)
+    rdw, rdb = cn.conv3x3_wgrad(x, dy, dil=dil)
     np.testing.assert_allclose(dw, rdw, rtol=0, atol=1e-4 * max(1.0, np.abs(rdw).max()))
     np.testing.assert_allclose(db, rdb, rtol=0, atol=1e-4 * max(1.0, np.abs(rdb).max()))
 
@@ -175,7 +201,7 @@ def test_network_training_step_matches_reference_gradients(L):
     reference Adam step on the gradients the FP64 reference computes through the
     whole network (forward of all six layers, loss, backward)."""
     import torch
-    from paper_1502_01629_gb300 import Net
+    from paper_1502_01629_gb300 import Net, NET_DIL
     rng = _rng(40)
     B, H, W = 2, 13, 17
     net = Net(max_batch=B, height=H, width=W)
@@ -197,10 +223,10 @@ def test_network_training_step_matches_reference_gradients(L):
     for li, (w, b) in enumerate(layers):
         wq = cn.bf16_round(w)
         if li < 5:
-            h = cn.bf16_round(cn.conv3x3(h, wq, b, relu=True))
+            h = cn.bf16_round(cn.conv3x3(h, wq, b, relu=True, dil=NET_DIL[li]))
             acts.append(h)
         else:
-            out = cn.conv3x3(h, wq, b)
+            out = cn.conv3x3(h, wq, b, dil=NET_DIL[li])
     lv, lc, g = cn.loss_and_grad(np.concatenate([out, np.zeros(out.shape[:3] + (15,))], -1), tval, tctrl,
                                  free, 1.0, 0.1)
     assert abs(loss[0] - lv) <= 1e-3 * max(1.0, lv) and abs(loss[1] - lc) <= 1e-3 * max(1.0, lc)
@@ -208,9 +234,9 @@ def test_network_training_step_matches_reference_gradients(L):
     grads = [None] * 6
     for li in range(5, -1, -1):
         w, b = layers[li]
-        grads[li] = cn.conv3x3_wgrad(acts[li], dz)
+        grads[li] = cn.conv3x3_wgrad(acts[li], dz, dil=NET_DIL[li])
         if li > 0:
-            dz = cn.bf16_round(cn.conv3x3_dgrad(dz, cn.bf16_round(w), acts[li]))
+            dz = cn.bf16_round(cn.conv3x3_dgrad(dz, cn.bf16_round(w), acts[li], dil=NET_DIL[li]))
     ref_grad = net.pack([(gw, gb) for gw, gb in grads])
     got = net.get_grads()
     # per layer: the gradients agree up to the bf16 rounding of the activations

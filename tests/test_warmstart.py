@@ -1,0 +1,117 @@
+"""Warm start of the coarse solve (the network's role in the pipeline), checked
+with predictions whose quality is known: the oracle's coarse fixed point must be
+accepted after K refinement sweeps, a bad prediction must fall back to the
+plain coarse solve, and the fine fixed point must not depend on the start."""
+import numpy as np
+import pytest
+
+import hjb_inputs as hi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the -m gpu tests")
+    from paper_1502_01629_gb300 import build
+    build.build()
+    import paper_1502_01629_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def cases():
+    insts = [hi.warmstart_instance(7000 + k, n=65, coarse_n=33) for k in range(3)]
+    pre = [oracle.patchy_precompute(i, tol_c=1e-12) for i in insts]
+    return insts, pre
+
+
+def _fake_output(pre, scale=1.0, const=None):
+    """A network output tensor [count][33][33][48] whose value channel holds the
+    given coarse values over u_max (the oracle's, scaled, or a constant)."""
+    import torch
+    out = np.zeros((len(pre), 33, 33, 48), np.float32)
+    for b, r in enumerate(pre):
+        v = r["uc"] / r["coarse"].u_max * scale if const is None else np.full(33 * 33, const)
+        out[b, :, :, 0] = v.reshape(33, 33)
+    return torch.from_numpy(out).cuda()
+
+
+def test_exact_prediction_is_accepted_after_k_sweeps(pkg, cases):
+    insts, pre = cases
+    with pkg.Batch.from_instances(insts) as B:
+        out = _fake_output(pre)
+        B.coarse_warm(out, k_sweeps=2, fallback_tol=1e-4)
+        st, sw, fb = B.coarse_solve(tol_c=1e-6)
+        assert (sw <= 2).all() and (fb == 0).all(), (sw, fb)
+        for b, r in enumerate(pre):
+            uc = B.get_coarse_value(b, 33)
+            assert np.abs(uc - r["uc"]).max() <= 1e-5 * max(1.0, np.abs(r["uc"]).max())
+
+
+def test_bad_prediction_falls_back_to_the_plain_coarse_solve(pkg, cases):
+    insts, pre = cases
+    with pkg.Batch.from_instances(insts) as B:
+        st, sw_plain, _ = B.coarse_solve(tol_c=1e-6)
+        plain = [B.get_coarse_value(b, 33) for b in range(len(insts))]
+        B.coarse_warm(_fake_output(pre, const=0.0), k_sweeps=2, fallback_tol=1e-4)
+        st, sw, fb = B.coarse_solve(tol_c=1e-6)
+        assert (fb == 1).all(), fb
+        assert (sw > sw_plain).all()          # the two wasted sweeps, then the plain solve
+        for b in range(len(insts)):
+            uc = B.get_coarse_value(b, 33)
+            assert np.abs(uc - plain[b]).max() <= 1e-5 * max(1.0, np.abs(plain[b]).max())
+
+
+def test_fine_fixed_point_does_not_depend_on_the_start(pkg, cases):
+    """A perturbed (5% high) prediction, accepted with a loose threshold, seeds
+    u_hat differently; the patchy solve still reaches the oracle's fine fixed
+    point within the FP64 gate."""
+    insts, pre = cases
+    refs = [oracle.Problem.from_instance(i).solve(scheme=3, tol=1e-14)[0] for i in insts]
+    with pkg.Batch.from_instances(insts) as B:
+        B.coarse_warm(_fake_output(pre, scale=1.05), k_sweeps=1, fallback_tol=1.0)
+        st, res = B.solve(tol_c=1e-6, tol32=3e-7, tol64=1e-12)
+        for b, u_ref in enumerate(refs):
+            np.testing.assert_allclose(B.get_value(b), u_ref, rtol=0, atol=1e-10)
+
+
+def test_trained_network_replaces_coarse_sweeps(pkg):
+    """Train the network briefly on solver data (the library's tensor-core
+    kernels), then solve held-out instances: accepted predictions replace the
+    coarse solve by a few refinement sweeps, and the patchy solutions stay those
+    of the plain start (same fixed point, FP64 residual <= 1e-6).  The gain is
+    in coarse iterations; the effect on the whole solve time is measured by
+    the warm-start evaluation, not asserted here."""
+    import torch
+    from paper_1502_01629_gb300 import warmstart as ws
+    dev = torch.device("cuda")
+    ds = ws.build_dataset(range(ws.TRAIN_SEED0, ws.TRAIN_SEED0 + 1024), dev, chunk=512)
+    net = pkg.Net(max_batch=32, height=ws.NC, width=ws.NC)
+    net.set_params(net.init_params(seed=1))
+    hist = ws.train(net, ds, epochs=6, batch=32, lr=2e-3)
+    assert hist[-1][0] < 0.5 * hist[0][0]
+    insts = ws.generate(range(ws.EVAL_SEED0, ws.EVAL_SEED0 + 16), procs=1)
+    with pkg.Batch.from_instances(insts) as B:
+        _, sw_plain, _ = B.coarse_solve(tol_c=1e-6)
+        st, res_plain = B.solve(tol_c=1e-6, tol32=2.5e-7, tol64=1e-6)
+        u_plain = [B.get_value(i) for i in range(len(insts))]
+        x = torch.empty((len(insts), ws.NC, ws.NC, 16), dtype=torch.int16, device=dev)
+        B.net_inputs(x)
+        for b0 in range(0, len(insts), 16):
+            net.forward(x[b0:b0 + 16], min(16, len(insts) - b0))
+            B.coarse_warm(net.output_ptr(), first=b0, count=min(16, len(insts) - b0), k_sweeps=4,
+                          fallback_tol=0.2)
+        _, sw_warm, fb = B.coarse_solve(tol_c=1e-6)
+        # a briefly trained network: a quarter of its predictions or more are
+        # accepted, each replacing ~80 coarse sweeps by 4
+        assert (fb == 0).sum() >= 4 and sw_warm.sum() <= 0.8 * sw_plain.sum(), (sw_warm, sw_plain, fb)
+        st, res = B.solve(tol_c=1e-6, tol32=2.5e-7, tol64=1e-6)
+        assert (res <= 1e-6).all()
+        for i in range(len(insts)):
+            scale = max(1.0, np.abs(u_plain[i]).max())
+            assert np.abs(B.get_value(i) - u_plain[i]).max() <= 1e-5 * scale
+    net.close()
