@@ -18,6 +18,13 @@ Conventions (shared by every consumer):
   * sector: int8 (n*n): the boundary subset Gamma_p a target node belongs
     to (0..N_P-1), -1 for every other node.
   * controls: float64 (N_A, 2): the points discretising the control set A.
+  * general terms (Section 5.3), all optional: sigma_field float32 (n*n), the
+    diffusion sigma(x) per node (replacing the constant sigma); diffusion 0 for
+    sigma(x) I_2, 1 for sigma(x) a (a one-dimensional Wiener process along the
+    control); cost_field float32 (n*n), l(x) per node (replacing the constant
+    cost); control_cost float64 (N_A), m(a_m): the running cost is l(x) + m(a).
+    sigma is in the units of the points x + h f +- sqrt(2h) sigma e_k, so the
+    paper's sqrt(2 eps) I_2 is sigma = sqrt(eps).
 """
 from __future__ import annotations
 
@@ -180,6 +187,10 @@ class Instance:
     cost: float = 1.0               # running cost l
     drift: Optional[np.ndarray] = None   # float32 (n*n*2) or None
     name: str = ""
+    sigma_field: Optional[np.ndarray] = None    # float32 (n*n): sigma(x), or None
+    diffusion: int = 0                          # 0: sigma(x) I_2, 1: sigma(x) a
+    cost_field: Optional[np.ndarray] = None     # float32 (n*n): l(x), or None
+    control_cost: Optional[np.ndarray] = None   # float64 (N_A): m(a_m), or None
 
     @property
     def dx(self) -> float:
@@ -321,3 +332,132 @@ def random_values(n: int, seed: int, lo: float = 0.0, hi: float = 1.0,
     if mask is not None:
         u[mask == MASK_TARGET] = 0.0
     return u
+
+
+# ------------------------------------------------ the problems of Section 5
+
+def h_upper_bound(n: int, f_max: float, eps: float, theta: float = 0.9) -> float:
+    """The time step with h f_max + sqrt(2 eps h) = theta dx (the bound of
+    Section 4.1 that keeps every point in the first neighbouring cells)."""
+    dx = 2.0 / (n - 1)
+    if f_max <= 0.0:
+        return (theta * dx) ** 2 / (2.0 * eps)
+    b = math.sqrt(2.0 * eps)
+    q = (-b + math.sqrt(b * b + 4.0 * f_max * theta * dx)) / (2.0 * f_max)
+    return q * q
+
+
+def boundary_instance(n: int, speed: np.ndarray, *, n_controls: int = 16, h: float = 0.0,
+                      lam: float = 0.0, sigma: float = 0.0, drift: Optional[np.ndarray] = None,
+                      coarse_n: int = 0, name: str = "", **general) -> Instance:
+    """Exit-time problem of Section 5: target = the boundary of the square (u = g = 0
+    there), the four sides as the boundary subsets Gamma_p, N_A unit directions,
+    undiscounted unless lam > 0."""
+    mask = square_boundary_target(n)
+    return Instance(n=n, controls=control_set(n_controls), speed=speed, mask=mask,
+                    sector=sectors_square_sides(n, mask), h=h, lam=lam, sigma=sigma,
+                    coarse_n=coarse_n, n_patches=4, drift=drift, name=name, **general)
+
+
+def speed_general(n: int) -> np.ndarray:
+    """c(x) = 1 + max{x2, max{x1, 0}} (eq. nonomog)."""
+    X1, X2 = mesh(n)
+    return (1.0 + np.maximum(X2, np.maximum(X1, 0.0))).astype(np.float32).reshape(-1)
+
+
+def upper_half(n: int) -> np.ndarray:
+    """chi_{x2 >= 0} per node (float64)."""
+    _, X2 = mesh(n)
+    return (X2 >= 0.0).astype(np.float64).reshape(-1)
+
+
+def general_instance(n: int, sigma_kind: int, cost_kind: int, *, eps: float = 0.1,
+                     n_controls: int = 16, coarse_n: int = 0, h: float = 0.0) -> Instance:
+    """The general nonlinear problems of Section 5.3: f = c(x) a with c of eq.
+    nonomog, d_eps(x) = sqrt(2 eps) chi_{x2 >= 0}, diffusion sigma_1 = 0,
+    sigma_2 = d_eps I_2 or sigma_3 = d_eps a (eq. s123), running cost l_1 = 1,
+    l_2 = 1 + |x1 x2| or l_3 = l_2 + |a1 / (2 + a2)| (eq. l123); boundary target,
+    no discount.  h defaults to the Section 4.1 bound with f_max = 2."""
+    if sigma_kind not in (1, 2, 3) or cost_kind not in (1, 2, 3):
+        raise ValueError("sigma_kind and cost_kind are 1, 2 or 3")
+    if h <= 0.0:
+        h = h_upper_bound(n, 2.0, eps)
+    X1, X2 = mesh(n)
+    gen = {}
+    if sigma_kind > 1:
+        gen["sigma_field"] = (math.sqrt(eps) * upper_half(n)).astype(np.float32)
+        gen["diffusion"] = 0 if sigma_kind == 2 else 1
+    if cost_kind > 1:
+        gen["cost_field"] = (1.0 + np.abs(X1 * X2)).astype(np.float32).reshape(-1)
+    if cost_kind == 3:
+        a = control_set(n_controls)
+        gen["control_cost"] = np.abs(a[:, 0] / (2.0 + a[:, 1]))
+    return boundary_instance(n, speed_general(n), n_controls=n_controls, h=h, coarse_n=coarse_n,
+                             name=f"general-l{cost_kind}-sigma{sigma_kind}-n{n}", **gen)
+
+
+def degenerate_instance(n: int, *, eps: float = 0.1, n_controls: int = 16, coarse_n: int = 0,
+                        h: float = 0.0) -> Instance:
+    """Degenerate diffusion of Section 5.2: eps(x) = 0.1 chi_{x2 >= 0} (sigma(x) =
+    sqrt(eps(x)) I_2 in the units above), speed c = 1 + chi_{x1 >= 0}, l = 1,
+    boundary target, no discount."""
+    if h <= 0.0:
+        h = h_upper_bound(n, 2.0, eps)
+    return boundary_instance(n, speed_halfplane(n, 1.0, 2.0), n_controls=n_controls, h=h,
+                             coarse_n=coarse_n, name=f"degenerate-n{n}",
+                             sigma_field=(math.sqrt(eps) * upper_half(n)).astype(np.float32))
+
+
+def zermelo_fields(n: int, eta: float, theta: float) -> Tuple[np.ndarray, np.ndarray]:
+    """f(x, a) = (R_theta x/|x| + (eta/2) a) / (1 + |x|^2) (dynamics C) as the drift
+    b(x) = R_theta x/|x| / (1 + |x|^2) (0 at the origin) and the speed
+    c(x) = (eta/2) / (1 + |x|^2)."""
+    X1, X2 = mesh(n)
+    r = np.hypot(X1, X2)
+    q = 1.0 / (1.0 + r * r)
+    inv = np.where(r > 0.0, 1.0 / np.where(r > 0.0, r, 1.0), 0.0)
+    ct, st = math.cos(theta), math.sin(theta)
+    bx = (ct * X1 - st * X2) * inv * q
+    by = (st * X1 + ct * X2) * inv * q
+    drift = np.stack([bx.reshape(-1), by.reshape(-1)], axis=1).astype(np.float32).reshape(-1)
+    speed = (0.5 * eta * q).astype(np.float32).reshape(-1)
+    return speed, drift
+
+
+def zermelo_instance(n: int, *, eta: float = 1.0, eps: float = 0.1, theta: float = math.pi / 4,
+                     n_controls: int = 16, coarse_n: int = 0, h: float = 0.0) -> Instance:
+    """The Zermelo navigation problem of Section 5.2 (dynamics C) with uniform
+    diffusion eps (sigma = sqrt(eps)), l = 1, boundary target, no discount.
+    |f| <= 1 + eta/2; h defaults to the Section 4.1 bound."""
+    speed, drift = zermelo_fields(n, eta, theta)
+    if h <= 0.0:
+        h = h_upper_bound(n, 1.0 + 0.5 * eta, max(eps, 1e-300)) if eps > 0 else 0.9 * (2.0 / (n - 1)) / (1.0 + 0.5 * eta)
+    return boundary_instance(n, speed, n_controls=n_controls, h=h, sigma=math.sqrt(eps), drift=drift,
+                             coarse_n=coarse_n, name=f"zermelo-eta{eta:g}-eps{eps:g}-n{n}")
+
+
+TABLE0_ROWS = [("A", 0.0), ("A", 1e-2), ("B1", 0.0), ("B1", 1e-2), ("Bchi", 0.0), ("Bchi", 1e-2),
+               ("C", 0.0), ("C", 1e-2)]
+
+
+def table0_instance(dynamics: str, eps: float, n: int = 50, n_controls: int = 16,
+                    theta: float = math.pi / 4) -> Instance:
+    """One row of Table 0 on the n x n grid: dynamics A (b = (1, 0)), B1 (c = 1),
+    Bchi (c = 1 + chi_{x1 >= 0}) or C (Zermelo, eta = 1), diffusion eps,
+    boundary target, no discount, h = dx / 2."""
+    h = 0.5 * 2.0 / (n - 1)
+    drift = None
+    if dynamics == "A":
+        speed = speed_constant(n, 0.0)
+        drift = np.tile(np.array([1.0, 0.0], np.float32), n * n)
+    elif dynamics == "B1":
+        speed = speed_constant(n, 1.0)
+    elif dynamics == "Bchi":
+        speed = speed_halfplane(n, 1.0, 2.0)
+    elif dynamics == "C":
+        speed, drift = zermelo_fields(n, 1.0, theta)
+    else:
+        raise ValueError(dynamics)
+    return boundary_instance(n, speed, n_controls=n_controls, h=h, sigma=math.sqrt(eps), drift=drift,
+                             name=f"table0-{dynamics}-eps{eps:g}-n{n}")
+

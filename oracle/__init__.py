@@ -80,7 +80,11 @@ class _Problem(ctypes.Structure):
                 ("speed", ctypes.POINTER(ctypes.c_float)),
                 ("drift", ctypes.POINTER(ctypes.c_float)),
                 ("mask", ctypes.POINTER(ctypes.c_uint8)),
-                ("controls", ctypes.POINTER(ctypes.c_double))]
+                ("controls", ctypes.POINTER(ctypes.c_double)),
+                ("sigma_field", ctypes.POINTER(ctypes.c_float)),
+                ("diffusion", ctypes.c_int32),
+                ("cost_field", ctypes.POINTER(ctypes.c_float)),
+                ("control_cost", ctypes.POINTER(ctypes.c_double))]
 
 
 def _ptr(a: np.ndarray, ct):
@@ -89,11 +93,20 @@ def _ptr(a: np.ndarray, ct):
 
 class Problem:
     """Discrete problem on G: the data of Section 3 (f = b + c a, l, sigma, g = 0 on
-    the target) plus the time step h and the discount lambda (beta = 1/(1+lambda h))."""
+    the target) plus the time step h and the discount lambda (beta = 1/(1+lambda h)).
+
+    General terms of Section 5.3: ``sigma_field`` (sigma(x) per node, replacing
+    the constant sigma), ``diffusion`` (0: sigma(x) I_2; 1: sigma(x) a, a
+    one-dimensional Wiener process along the control), ``cost_field`` (l(x) per
+    node, replacing the constant cost) and ``control_cost`` (m(a_m) per control);
+    the running cost is l(x) + m(a)."""
 
     def __init__(self, n: int, controls: np.ndarray, speed: np.ndarray, mask: np.ndarray,
                  h: float = 0.0, lam: float = 1.0, sigma: float = 0.0, cost: float = 1.0,
-                 drift: Optional[np.ndarray] = None, u_obstacle: Optional[float] = None):
+                 drift: Optional[np.ndarray] = None, u_obstacle: Optional[float] = None,
+                 sigma_field: Optional[np.ndarray] = None, diffusion: int = 0,
+                 cost_field: Optional[np.ndarray] = None,
+                 control_cost: Optional[np.ndarray] = None):
         self.n = int(n)
         self.dx = 2.0 / (n - 1)
         self.h = float(h) if h > 0 else self.dx
@@ -105,19 +118,40 @@ class Problem:
         self.speed = np.ascontiguousarray(speed, dtype=np.float32).reshape(-1)
         self.mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
         self.drift = None if drift is None else np.ascontiguousarray(drift, dtype=np.float32).reshape(-1)
+        self.sigma_field = (None if sigma_field is None
+                            else np.ascontiguousarray(sigma_field, dtype=np.float32).reshape(-1))
+        self.diffusion = int(diffusion)
+        self.cost_field = (None if cost_field is None
+                           else np.ascontiguousarray(cost_field, dtype=np.float32).reshape(-1))
+        self.control_cost = (None if control_cost is None
+                             else np.ascontiguousarray(control_cost, dtype=np.float64).reshape(-1))
         if u_obstacle is None:
             u_obstacle = self.u_max if self.lam > 0 else 1e6
         self.u_obstacle = float(u_obstacle)
         assert self.speed.size == n * n and self.mask.size == n * n
+        assert self.diffusion in (0, 1)
+        assert self.sigma_field is None or self.sigma_field.size == n * n
+        assert self.cost_field is None or self.cost_field.size == n * n
+        assert self.control_cost is None or self.control_cost.size == self.controls.shape[0]
+        fp = ctypes.POINTER(ctypes.c_float)
         self._s = _Problem(self.n, self.controls.shape[0], self.h, self.lam, self.sigma,
                            self.cost, self.u_obstacle, _ptr(self.speed, ctypes.c_float),
-                           _ptr(self.drift, ctypes.c_float) if self.drift is not None
-                           else ctypes.POINTER(ctypes.c_float)(),
-                           _ptr(self.mask, ctypes.c_uint8), _ptr(self.controls, ctypes.c_double))
+                           _ptr(self.drift, ctypes.c_float) if self.drift is not None else fp(),
+                           _ptr(self.mask, ctypes.c_uint8), _ptr(self.controls, ctypes.c_double),
+                           _ptr(self.sigma_field, ctypes.c_float) if self.sigma_field is not None
+                           else fp(), self.diffusion,
+                           _ptr(self.cost_field, ctypes.c_float) if self.cost_field is not None
+                           else fp(),
+                           _ptr(self.control_cost, ctypes.c_double) if self.control_cost is not None
+                           else ctypes.POINTER(ctypes.c_double)())
 
     @classmethod
     def from_instance(cls, inst, **kw) -> "Problem":
-        args = dict(h=inst.h, lam=inst.lam, sigma=inst.sigma, cost=inst.cost, drift=inst.drift)
+        args = dict(h=inst.h, lam=inst.lam, sigma=inst.sigma, cost=inst.cost, drift=inst.drift,
+                    sigma_field=getattr(inst, "sigma_field", None),
+                    diffusion=getattr(inst, "diffusion", 0),
+                    cost_field=getattr(inst, "cost_field", None),
+                    control_cost=getattr(inst, "control_cost", None))
         args.update(kw)
         return cls(inst.n, inst.controls, inst.speed, inst.mask, **args)
 
@@ -126,9 +160,17 @@ class Problem:
         return self.n * self.n
 
     @property
+    def l_max(self) -> float:
+        """The largest running cost max_x l(x) + max_a m(a)."""
+        lx = float(self.cost_field.max()) if self.cost_field is not None else self.cost
+        la = float(self.control_cost.max()) if self.control_cost is not None else 0.0
+        return lx + la
+
+    @property
     def u_max(self) -> float:
-        """h l / (1 - beta) = l (1/lambda + h): the value of never reaching the target."""
-        return self.h * self.cost / (1.0 - self.beta)
+        """h l / (1 - beta) = l (1/lambda + h) with the largest l: a bound on the
+        value of never reaching the target."""
+        return self.h * self.l_max / (1.0 - self.beta)
 
     # ------------------------------------------------------------- scheme
     def node_update(self, u: np.ndarray, k: int, scheme: int = 3) -> Tuple[float, int]:
@@ -276,8 +318,17 @@ def patchy_precompute(inst, tol_c: float = 1e-10, band_factor: float = 1.0,
     fine = Problem.from_instance(inst)
     sc, mc = coarse_data(n, nc, inst.speed, inst.mask)
     hc = 2.0 / (nc - 1) if inst.h <= 0 else inst.h * (n - 1) / (nc - 1)
+    # the other per-node data on G_c are the fine data at the nested nodes
+    r = (n - 1) // (nc - 1)
+
+    def nested(a, comps=1):
+        return None if a is None else np.ascontiguousarray(
+            np.asarray(a).reshape(n, n, comps)[::r, ::r]).reshape(-1)
+
     coarse = Problem(nc, inst.controls, sc, mc, h=hc, lam=inst.lam, sigma=0.0,
-                     cost=inst.cost, u_obstacle=fine.u_obstacle)
+                     cost=inst.cost, u_obstacle=fine.u_obstacle, drift=nested(inst.drift, 2),
+                     cost_field=nested(getattr(inst, "cost_field", None)),
+                     control_cost=getattr(inst, "control_cost", None))
     u0 = np.full(nc * nc, coarse.u_max if inst.lam > 0 else 1e6)
     uc, sweeps, _ = coarse.solve(u0, scheme=3, method="gs", tol=tol_c)
     uhat = interp_coarse(nc, uc, n, inst.mask, fine.u_obstacle)

@@ -27,7 +27,13 @@
  *     a point on the right/top edge uses the last cell with fraction 1;
  *   - the self weight lambda_{i0} is the Q1 weight of x_i when x_i is a vertex
  *     of the point's cell, and 0 otherwise (the stencil may reach further than
- *     the first neighbouring cells when h = dx).
+ *     the first neighbouring cells when h = dx);
+ *   - general terms (Section 5.3): sigma(x) may vary per node; the diffusion is
+ *     either sigma(x) I_2 (two Wiener components, 2d = 4 points along e_1, e_2)
+ *     or sigma(x) a, a one-dimensional Wiener process along the control (2d = 2
+ *     points x + h f +- sqrt(2h) sigma(x) a, weight 1/2 each: the k of eq.
+ *     SLscheme2 runs over the columns of sigma); the running cost is
+ *     l(x, a) = l(x) + m(a), which holds the paper's l_1, l_2 and l_3.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,6 +56,10 @@ typedef struct {
     const float *drift;      /* b(x), n*n*2 interleaved, or NULL */
     const uint8_t *mask;     /* 0 free, 1 target, 2 obstacle */
     const double *controls;  /* a_m = (controls[2m], controls[2m+1]) */
+    const float *sigma_field;   /* sigma(x) per node, or NULL: sigma everywhere */
+    int32_t diffusion;          /* 0: sigma(x) I_2; 1: sigma(x) a (along the control) */
+    const float *cost_field;    /* l(x) per node, or NULL: cost everywhere */
+    const double *control_cost; /* m(a_m) per control, or NULL: m = 0 */
 } orc_problem;
 
 static double orc_dx(const orc_problem *P) { return 2.0 / (P->n - 1); }
@@ -118,6 +128,42 @@ static void foot(const orc_problem *P, int64_t k, int m, double *xi, double *eta
     *eta = (double)j + P->h * fy / dx;
 }
 
+/* The 2d points x_{i,k}^{a,s} of eq. SLscheme2 for control m at node k, in
+ * grid units, and their common weight 1/(2d).  The Wiener part is
+ * sqrt(h) sigma_k with sigma = sqrt(2) sigma(x) I_2 (d = 2, points along the
+ * axes) or sigma = sqrt(2) sigma(x) a_m (d = 1, points along the control).
+ * With sigma(x) = 0 the points coincide with the foot.  Returns 2d. */
+static int scheme_points(const orc_problem *P, int64_t k, int m, double px[4], double py[4],
+                         double *weight)
+{
+    const double dx = orc_dx(P);
+    const double sig = P->sigma_field ? (double)P->sigma_field[k] : P->sigma;
+    const double r = sqrt(2.0 * P->h) * sig / dx;   /* sqrt(h) |sigma_k| in grid units */
+    double xi, eta;
+    foot(P, k, m, &xi, &eta);
+    if (P->diffusion == 1) {
+        const double ax = P->controls[2 * m], ay = P->controls[2 * m + 1];
+        px[0] = xi + r * ax;  py[0] = eta + r * ay;
+        px[1] = xi - r * ax;  py[1] = eta - r * ay;
+        *weight = 0.5;
+        return 2;
+    }
+    px[0] = xi + r;  py[0] = eta;
+    px[1] = xi - r;  py[1] = eta;
+    px[2] = xi;      py[2] = eta + r;
+    px[3] = xi;      py[3] = eta - r;
+    *weight = 0.25;
+    return 4;
+}
+
+/* h l(x_k, a_m) with l(x, a) = l(x) + m(a). */
+static double running_cost(const orc_problem *P, int64_t k, int m)
+{
+    const double lx = P->cost_field ? (double)P->cost_field[k] : P->cost;
+    const double la = P->control_cost ? P->control_cost[m] : 0.0;
+    return P->h * (lx + la);
+}
+
 /* ------------------------------------------------------------------------
  * One node update (free node k).
  *   scheme 2: original scheme (Section 3, eq. SLscheme2):
@@ -133,29 +179,26 @@ static void foot(const orc_problem *P, int64_t k, int m, double *xi, double *eta
 double orc_node_update(const orc_problem *P, const double *u, int64_t k, int scheme,
                        int32_t *argmin)
 {
-    static const double dirs[4][2] = {{1.0, 0.0}, {-1.0, 0.0}, {0.0, 1.0}, {0.0, -1.0}};
-    const int n = P->n;
-    const double dx = orc_dx(P);
     const double beta = orc_beta(P);
-    const double d = sqrt(2.0 * P->h) * P->sigma / dx;   /* sqrt(h)*|sigma_k| in grid units */
     double best = INFINITY;
     int32_t best_m = -1;
     for (int m = 0; m < P->n_controls; m++) {
-        double xi, eta;
-        foot(P, k, m, &xi, &eta);
+        double px[4], py[4], w;
+        const int np = scheme_points(P, k, m, px, py, &w);
         double lam1 = 0.0, lam0 = 0.0;
-        for (int p = 0; p < 4; p++) {            /* 2d = 4 points, weight 1/(2d) */
+        for (int p = 0; p < np; p++) {           /* 2d points, weight 1/(2d) */
             double e, s;
-            q1_split(u, n, xi + d * dirs[p][0], eta + d * dirs[p][1], k, &e, &s);
-            lam1 += 0.25 * e;
-            lam0 += 0.25 * s;
+            q1_split(u, P->n, px[p], py[p], k, &e, &s);
+            lam1 += w * e;
+            lam0 += w * s;
         }
+        const double hl = running_cost(P, k, m);
         double v;
         if (scheme == 3) {
             double den = 1.0 - beta * lam0;
-            v = den > 0.0 ? (beta * lam1 + P->h * P->cost) / den : INFINITY;
+            v = den > 0.0 ? (beta * lam1 + hl) / den : INFINITY;
         } else {
-            v = beta * (lam1 + lam0 * u[k]) + P->h * P->cost;
+            v = beta * (lam1 + lam0 * u[k]) + hl;
         }
         if (v < best) {
             best = v;
@@ -172,25 +215,23 @@ double orc_node_update(const orc_problem *P, const double *u, int64_t k, int sch
 void orc_node_candidates(const orc_problem *P, const double *u, int64_t k, int scheme,
                          double *vals)
 {
-    static const double dirs[4][2] = {{1.0, 0.0}, {-1.0, 0.0}, {0.0, 1.0}, {0.0, -1.0}};
-    const double dx = orc_dx(P);
     const double beta = orc_beta(P);
-    const double d = sqrt(2.0 * P->h) * P->sigma / dx;
     for (int m = 0; m < P->n_controls; m++) {
-        double xi, eta;
-        foot(P, k, m, &xi, &eta);
+        double px[4], py[4], w;
+        const int np = scheme_points(P, k, m, px, py, &w);
         double lam1 = 0.0, lam0 = 0.0;
-        for (int p = 0; p < 4; p++) {
+        for (int p = 0; p < np; p++) {
             double e, s;
-            q1_split(u, P->n, xi + d * dirs[p][0], eta + d * dirs[p][1], k, &e, &s);
-            lam1 += 0.25 * e;
-            lam0 += 0.25 * s;
+            q1_split(u, P->n, px[p], py[p], k, &e, &s);
+            lam1 += w * e;
+            lam0 += w * s;
         }
+        const double hl = running_cost(P, k, m);
         if (scheme == 3) {
             double den = 1.0 - beta * lam0;
-            vals[m] = den > 0.0 ? (beta * lam1 + P->h * P->cost) / den : INFINITY;
+            vals[m] = den > 0.0 ? (beta * lam1 + hl) / den : INFINITY;
         } else {
-            vals[m] = beta * (lam1 + lam0 * u[k]) + P->h * P->cost;
+            vals[m] = beta * (lam1 + lam0 * u[k]) + hl;
         }
     }
 }
@@ -352,8 +393,8 @@ void orc_interp_coarse(int32_t nc, const double *uc, int32_t n, const uint8_t *m
 }
 
 /* Discrete feedback synthesis (Section 4.3, eq. discrete-synthesis) with the
- * discount: a*(x_i) = argmin_a { beta u_hat(x_i + h f(x_i,a)) + h l }, sigma = 0,
- * ties to the lowest control index.  a_out = 255 on non-free nodes. */
+ * discount: a*(x_i) = argmin_a { beta u_hat(x_i + h f(x_i,a)) + h l(x_i, a) },
+ * sigma = 0, ties to the lowest control index.  a_out = 255 on non-free nodes. */
 void orc_synthesis(const orc_problem *P, const double *uhat, uint8_t *a_out)
 {
     const int64_t N = (int64_t)P->n * P->n;
@@ -365,14 +406,14 @@ void orc_synthesis(const orc_problem *P, const double *uhat, uint8_t *a_out)
         for (int m = 0; m < P->n_controls; m++) {
             double xi, eta;
             foot(P, k, m, &xi, &eta);
-            double v = beta * q1_full(uhat, P->n, xi, eta) + P->h * P->cost;
+            double v = beta * q1_full(uhat, P->n, xi, eta) + running_cost(P, k, m);
             if (v < best) { best = v; best_m = m; }
         }
         a_out[k] = (uint8_t)best_m;
     }
 }
 
-/* The synthesis objective beta u_hat(foot) + h l for every control at the
+/* The synthesis objective beta u_hat(foot) + h l(x, a) for every control at the
  * listed nodes: vals[t*N_A + m].  Used to judge near-ties. */
 void orc_synthesis_values(const orc_problem *P, const double *uhat, const int64_t *nodes,
                           int64_t n_nodes, double *vals)
@@ -382,7 +423,8 @@ void orc_synthesis_values(const orc_problem *P, const double *uhat, const int64_
         for (int m = 0; m < P->n_controls; m++) {
             double xi, eta;
             foot(P, nodes[t], m, &xi, &eta);
-            vals[t * P->n_controls + m] = beta * q1_full(uhat, P->n, xi, eta) + P->h * P->cost;
+            vals[t * P->n_controls + m] = beta * q1_full(uhat, P->n, xi, eta) +
+                                          running_cost(P, nodes[t], m);
         }
     }
 }

@@ -1,0 +1,236 @@
+"""Pins of the oracle's general terms (Section 5): a diffusion sigma(x) that varies
+per node, the one-dimensional diffusion sigma(x) a along the control, the running
+cost l(x) + m(a), the Zermelo dynamics and the Table 0 behaviour of the two
+schemes.  Each check rests on a closed form, a special case that reduces to the
+already pinned constant-coefficient scheme, or an exact count the paper argues
+for -- never on the oracle's own formula retyped."""
+import math
+
+import numpy as np
+import pytest
+
+import hjb_inputs as hi
+import oracle
+
+
+def _problem(inst, **kw):
+    return oracle.Problem.from_instance(inst, **kw)
+
+
+def _interior_nodes(n, margin):
+    i = np.arange(margin, n - margin)
+    J, I = np.meshgrid(i, i, indexing="ij")
+    return (J * n + I).reshape(-1)
+
+
+# ------------------------------------------------------------ sigma(x)
+
+def test_constant_sigma_field_is_the_uniform_scheme():
+    """sigma(x) = s everywhere gives the constant-sigma scheme bit for bit."""
+    n = 41
+    inst = hi.disc_instance(n, 0.0625, n_controls=12, speed=hi.speed_sine(n))
+    u = hi.random_values(n, 3, mask=inst.mask)
+    uni = _problem(inst)
+    fld = _problem(inst, sigma=0.0, sigma_field=np.full(n * n, 0.0625, np.float32))
+    for k in _interior_nodes(n, 0)[::7]:
+        if inst.mask[k] != hi.MASK_FREE:
+            continue
+        for sch in (2, 3):
+            assert uni.node_update(u, k, sch) == fld.node_update(u, k, sch)
+
+
+def test_degenerate_diffusion_recovers_both_schemes():
+    """eps(x) = 0.1 chi_{x2 >= 0} (Section 5.2): below the x1 axis every node update
+    is the first-order scheme (sigma = 0), above it the uniform-diffusion one."""
+    n = 41
+    inst = hi.degenerate_instance(n)
+    u = hi.random_values(n, 5, mask=inst.mask)
+    gen = _problem(inst)
+    first = _problem(inst, sigma_field=None, sigma=0.0)
+    s_up = float(np.float32(math.sqrt(0.1)))
+    diff = _problem(inst, sigma_field=None, sigma=s_up)
+    up = hi.upper_half(n) > 0
+    checked = [0, 0]
+    for k in range(n * n):
+        if inst.mask[k] != hi.MASK_FREE or k % 3:
+            continue
+        ref = diff if up[k] else first
+        for sch in (2, 3):
+            assert gen.node_update(u, k, sch) == ref.node_update(u, k, sch)
+        checked[int(up[k])] += 1
+    assert min(checked) > 50
+
+
+# ------------------------------------------------- diffusion along the control
+
+def _bilinear(n, kappa, alpha, gamma, c0):
+    X1, X2 = hi.mesh(n)
+    return (c0 + alpha * X1 + gamma * X2 + kappa * X1 * X2).reshape(-1)
+
+
+@pytest.mark.parametrize("t", [0.3, 1.1, 2.5, 4.0])
+def test_control_diffusion_on_a_bilinear_function(t):
+    """Q1 interpolation reproduces u = c0 + alpha x1 + gamma x2 + kappa x1 x2, so
+    with one control a and the points y +- delta, delta = sqrt(2h) sigma a,
+    y = x + h c a, the original scheme gives exactly
+        beta (u(y) + kappa delta_1 delta_2) + h (l(x) + m(a))   (sigma(x) a),
+        beta u(y) + h (l(x) + m(a))                              (sigma(x) I_2:
+    the axis offsets have delta_1 delta_2 = 0)."""
+    n = 41
+    a = np.array([[math.cos(t), math.sin(t)]])
+    speed = np.full(n * n, 0.75, np.float32)
+    mask = np.zeros(n * n, np.uint8)
+    h, lam, sig, kappa = 0.03, 0.8, 0.5, 1.7
+    cost_field = (1.0 + 0.25 * np.arange(n * n) % 7).astype(np.float32)
+    m = np.array([0.3])
+    u = _bilinear(n, kappa, -0.4, 0.9, 2.0)
+    X1, X2 = hi.mesh(n)
+    X1, X2 = X1.reshape(-1), X2.reshape(-1)
+    beta = 1.0 / (1.0 + lam * h)
+    for diffusion in (1, 0):
+        P = oracle.Problem(n, a, speed, mask, h=h, lam=lam, sigma=0.0, diffusion=diffusion,
+                           sigma_field=np.full(n * n, sig, np.float32), cost_field=cost_field,
+                           control_cost=m)
+        for k in _interior_nodes(n, 8)[::11]:
+            y1 = X1[k] + h * 0.75 * a[0, 0]
+            y2 = X2[k] + h * 0.75 * a[0, 1]
+            uy = 2.0 + (-0.4) * y1 + 0.9 * y2 + kappa * y1 * y2
+            d1, d2 = math.sqrt(2 * h) * sig * a[0]
+            extra = kappa * d1 * d2 if diffusion == 1 else 0.0
+            want = beta * (uy + extra) + h * (float(cost_field[k]) + m[0])
+            got, am = P.node_update(u, k, 2)
+            assert am == 0
+            assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (diffusion, k, got, want)
+
+
+def test_control_diffusion_reaches_along_the_control_only():
+    """With sigma(x) a the two points lie on the line through the foot along a:
+    for a = e_1 and u depending on x2 only (u = x2^2, not Q1-exact) the
+    diffusion changes nothing, while the isotropic form smooths along x2."""
+    n = 41
+    a = np.array([[1.0, 0.0]])
+    speed = np.zeros(n * n, np.float32)
+    mask = np.zeros(n * n, np.uint8)
+    _, X2 = hi.mesh(n)
+    u = (X2 ** 2).reshape(-1)
+    h, sig = 0.05, 0.4
+    common = dict(h=h, lam=0.0, sigma_field=np.full(n * n, sig, np.float32))
+    along = oracle.Problem(n, a, speed, mask, diffusion=1, **common)
+    iso = oracle.Problem(n, a, speed, mask, diffusion=0, **common)
+    k = 20 * n + 20
+    v_along, _ = along.node_update(u, k, 2)
+    v_iso, _ = iso.node_update(u, k, 2)
+    assert abs(v_along - (u[k] + h)) <= 1e-15
+    assert v_iso > v_along + 1e-4
+
+
+# ------------------------------------------------------- running cost l(x) + m(a)
+
+def test_running_cost_terms_on_a_constant_field():
+    """u = C everywhere: every point interpolates to C, so the original scheme is
+    beta C + h (l(x) + min_a m(a)) and its argmin is the cheapest control."""
+    n = 33
+    inst = hi.general_instance(n, 1, 3)
+    P = _problem(inst)
+    C = 0.625
+    u = np.full(n * n, C)
+    mvals = np.abs(inst.controls[:, 0] / (2.0 + inst.controls[:, 1]))
+    X1, X2 = hi.mesh(n)
+    lx = (1.0 + np.abs(X1 * X2)).astype(np.float32).reshape(-1)
+    for k in _interior_nodes(n, 1)[::13]:
+        got, am = P.node_update(u, k, 2)
+        want = C + P.h * (float(lx[k]) + mvals.min())       # beta = 1 (no discount)
+        assert abs(got - want) <= 1e-15 * 4
+        assert am == int(np.argmin(mvals))
+
+
+def test_costs_order_the_solutions():
+    """Comparison principle of the monotone scheme: l_1 <= l_2 <= l_3 pointwise
+    gives u_1 <= u_2 <= u_3 on every node, for each diffusion."""
+    n = 33
+    for sk in (1, 2, 3):
+        us = []
+        for ck in (1, 2, 3):
+            P = _problem(hi.general_instance(n, sk, ck))
+            u, s, _ = P.solve(np.full(P.N, 1e6), scheme=3, tol=1e-12)
+            assert s > 0
+            us.append(u)
+        free = hi.general_instance(n, 1, 1).mask == 0
+        assert np.all(us[0][free] <= us[1][free] + 1e-12)
+        assert np.all(us[1][free] <= us[2][free] + 1e-12)
+        assert (us[2] - us[0])[free].max() > 1e-3
+
+
+# ------------------------------------------------------------------ Zermelo
+
+def test_zermelo_radial_drift_gives_the_ray_exit_time():
+    """Dynamics C with theta = 0, eta = 0, eps = 0: the state moves along rays
+    with speed 1 / (1 + r^2), so the exit time from radius r along a ray that
+    leaves the square at radius R is (R - r) + (R^3 - r^3) / 3.  Away from the
+    diagonals (where R has a kink) the first-order scheme converges to it."""
+    errs = []
+    for n in (51, 101):
+        inst = hi.zermelo_instance(n, eta=0.0, eps=0.0, theta=0.0)
+        P = _problem(inst)
+        u, s, _ = P.solve(np.full(P.N, 1e6), scheme=3, tol=1e-10)
+        X1, X2 = hi.mesh(n)
+        X1, X2 = X1.reshape(-1), X2.reshape(-1)
+        r = np.hypot(X1, X2)
+        R = r / np.maximum(np.abs(X1), np.abs(X2)).clip(1e-300)
+        T = (R - r) + (R ** 3 - r ** 3) / 3.0
+        sel = (r >= 0.2) & (inst.mask == 0) & (np.abs(np.abs(X1) - np.abs(X2)) > 0.1)
+        errs.append(np.abs(u - T)[sel].max())
+    assert errs[1] < 0.03 and errs[1] < 0.75 * errs[0], errs
+
+
+def test_zermelo_rotation_is_counter_clockwise():
+    """R_theta rotates x/|x| counter-clockwise: at (x, 0), x > 0, the drift points
+    up-right for 0 < theta < pi/2."""
+    n = 21
+    speed, drift = hi.zermelo_fields(n, 1.0, math.pi / 4)
+    d = drift.reshape(n, n, 2)
+    bx, by = d[n // 2, n - 3]
+    x = hi.node_coords(n)[0][n - 3]
+    q = 1.0 / (1.0 + x * x)
+    assert abs(bx - q * math.cos(math.pi / 4)) < 1e-6 and abs(by - q * math.sin(math.pi / 4)) < 1e-6
+    assert abs(speed.reshape(n, n)[n // 2, n - 3] - 0.5 * q) < 1e-6
+
+
+# ------------------------------------------------------------------ Table 0
+
+def test_table0_advection_in_causal_order_converges_in_one_sweep():
+    """Dynamics A, b = (1, 0), eps = 0: each node depends only on the node to its
+    right.  Gauss-Seidel from right to left makes the modified scheme exact in
+    one sweep (plus the checking sweep), whereas the original scheme keeps the
+    self-dependency and needs many more (Section 5.1)."""
+    P = _problem(hi.table0_instance("A", 0.0))
+    order = np.arange(P.N - 1, -1, -1)
+    _, s3, _ = P.solve(np.full(P.N, 1e6), scheme=3, tol=1e-6, order=order)
+    _, s2, _ = P.solve(np.full(P.N, 1e6), scheme=2, tol=1e-6, order=order)
+    assert s3 == 2
+    assert s2 > 50
+
+
+def test_table0_eikonal_sweeps_grow_with_half_the_grid():
+    """Dynamics B, c = 1, eps = 0: characteristics are straight lines from the
+    boundary to the diagonals, so row-major Gauss-Seidel needs about n/2 sweeps
+    to carry the information to the middle (Section 5.1)."""
+    counts = []
+    for n in (50, 100):
+        P = _problem(hi.table0_instance("B1", 0.0, n=n))
+        _, s, _ = P.solve(np.full(P.N, 1e6), scheme=3, tol=1e-6)
+        counts.append(s)
+    assert abs(counts[0] - 25) <= 2 and abs(counts[1] - 50) <= 2, counts
+
+
+def test_table0_modified_scheme_needs_fewer_sweeps_on_every_row():
+    """Every row of Table 0: the modified scheme (eq. SLscheme3) converges in fewer
+    sweeps than the original one (eq. SLscheme2), and diffusion costs sweeps."""
+    res = {}
+    for dyn, eps in hi.TABLE0_ROWS:
+        P = _problem(hi.table0_instance(dyn, eps))
+        s = [P.solve(np.full(P.N, 1e6), scheme=sch, tol=1e-6)[1] for sch in (2, 3)]
+        assert 0 < s[1] < s[0], (dyn, eps, s)
+        res[(dyn, eps)] = s
+    for dyn in ("A", "B1", "C"):
+        assert res[(dyn, 1e-2)][1] > res[(dyn, 0.0)][1]
