@@ -152,6 +152,39 @@ int hjb_create_problem(const hjb_desc* desc, const float* speed, const uint8_t* 
                        const int8_t* sector, const double* controls, const float* drift,
                        void* cuda_stream, hjb_problem** out);
 
+/* General terms of Section 5.3 (eqs. s123, l123 and the degenerate diffusion of
+ * Section 5.2), all optional:
+ *     sigma(x, a) = sqrt(2) sigma(x) I_2  (HJB_DIFFUSION_ISOTROPIC: the four points
+ *                   x + h f +- sqrt(2h) sigma(x) e_k, weight 1/4 each), or
+ *     sigma(x, a) = sqrt(2) sigma(x) a    (HJB_DIFFUSION_CONTROL: a one-dimensional
+ *                   Wiener process along the control, the two points
+ *                   x + h f +- sqrt(2h) sigma(x) a, weight 1/2 each),
+ *     l(x, a)     = l(x) + m(a).
+ * The paper's d_eps(x) = sqrt(2 eps) chi_{x2 >= 0} is sigma(x) = sqrt(eps) chi. */
+#define HJB_DIFFUSION_ISOTROPIC 0
+#define HJB_DIFFUSION_CONTROL 1
+typedef struct {
+    const float*  sigma_field;   /* host float[n*n], sigma(x) >= 0 (finite), or NULL: desc->sigma
+                                    everywhere; when given, desc->sigma is ignored              */
+    int32_t       diffusion;     /* HJB_DIFFUSION_ISOTROPIC or HJB_DIFFUSION_CONTROL            */
+    int32_t       reserved;      /* must be 0                                                   */
+    const float*  cost_field;    /* host float[n*n], l(x) > 0 (finite), or NULL: desc->cost     */
+    const double* control_cost;  /* host double[n_controls], m(a_m) >= 0 (finite), or NULL: 0   */
+} hjb_terms;
+
+/* hjb_create_problem_general -- hjb_create_problem with the general terms above
+ * (terms may be NULL: the constant-coefficient problem).  The arrays are copied;
+ * the coarse grid takes l(x) at its nested nodes (and no diffusion, as always).
+ * The obstacle value and the initial coarse value use the largest running cost
+ * max l(x) + max m(a).  Every entry point accepts the problem; the kernels
+ * evaluate the general terms on the per-node path (the FP32 software-pipelined
+ * tile path serves constant coefficients only).  Errors: as hjb_create_problem,
+ * plus HJB_ERR_INVALID_ARG for a negative / non-finite sigma(x) or m(a), a
+ * non-positive / non-finite l(x), an unknown diffusion or reserved != 0. */
+int hjb_create_problem_general(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                               const int8_t* sector, const double* controls, const float* drift,
+                               const hjb_terms* terms, void* cuda_stream, hjb_problem** out);
+
 /* hjb_create_problem_device -- as hjb_create_problem, but speed, mask, sector and
  * drift are DEVICE pointers (e.g. torch CUDA tensors' data_ptr) on the current
  * device; they are copied device-to-device on cuda_stream.  controls stays a host

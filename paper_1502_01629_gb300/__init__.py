@@ -19,7 +19,7 @@ from typing import Optional
 
 import numpy as np
 
-from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, BatchDesc, BatchInst, Desc, HJBError, RegimeInfo,
+from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, BatchDesc, BatchInst, Desc, HJBError, RegimeInfo, Terms,
                    Stats, check, header_functions, lib)
 
 __all__ = ["Problem", "Batch", "Net", "HJBError", "regime", "kernel_launches", "lib", "header_functions",
@@ -57,7 +57,10 @@ class Problem:
                  band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
                  schedule: int = 0, tile_waves: int = 0, tile_period: int = 2,
                  local_sweeps: int = 1, tile_shape: int = -1,
-                 drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False):
+                 drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False,
+                 sigma_field: Optional[np.ndarray] = None, diffusion: int = 0,
+                 cost_field: Optional[np.ndarray] = None,
+                 control_cost: Optional[np.ndarray] = None):
         self._h = None
         self.n = int(n)
         self.N = self.n * self.n
@@ -79,6 +82,10 @@ class Problem:
         if stream is not None:
             st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         handle = ctypes.c_void_p()
+        general = (sigma_field is not None or cost_field is not None or control_cost is not None
+                   or int(diffusion) != 0)
+        if general and device_inputs:
+            raise ValueError("the general terms take host arrays")
         if device_inputs:
             # torch CUDA tensors (or raw device pointers as ints)
             ptr = lambda t: None if t is None else ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr())
@@ -92,16 +99,33 @@ class Problem:
             self._drift = None if drift is None else _c(drift, np.float32).reshape(-1)
             if self._speed.size != self.N or self._mask.size != self.N:
                 raise ValueError("speed and mask must have n*n entries")
-            rc = lib().hjb_create_problem(ctypes.byref(d), _p(self._speed), _p(self._mask),
-                                          _p(self._sector), _p(self.controls), _p(self._drift), st,
-                                          ctypes.byref(handle))
+            if general:
+                # sigma(x), the diffusion form and l(x) + m(a) of Section 5.3
+                self._sigf = None if sigma_field is None else _c(sigma_field, np.float32).reshape(-1)
+                self._costf = None if cost_field is None else _c(cost_field, np.float32).reshape(-1)
+                self._cctl = None if control_cost is None else _c(control_cost, np.float64).reshape(-1)
+                t = Terms()
+                t.sigma_field, t.diffusion = _p(self._sigf), int(diffusion)
+                t.cost_field, t.control_cost = _p(self._costf), _p(self._cctl)
+                rc = lib().hjb_create_problem_general(ctypes.byref(d), _p(self._speed), _p(self._mask),
+                                                      _p(self._sector), _p(self.controls),
+                                                      _p(self._drift), ctypes.byref(t), st,
+                                                      ctypes.byref(handle))
+            else:
+                rc = lib().hjb_create_problem(ctypes.byref(d), _p(self._speed), _p(self._mask),
+                                              _p(self._sector), _p(self.controls), _p(self._drift),
+                                              st, ctypes.byref(handle))
         check(rc, "hjb_create_problem")
         self._h = handle
 
     @classmethod
     def from_instance(cls, inst, **kw) -> "Problem":
         args = dict(h=inst.h, lam=inst.lam, sigma=inst.sigma, cost=inst.cost,
-                    coarse_n=inst.coarse_n, n_patches=inst.n_patches, drift=inst.drift)
+                    coarse_n=inst.coarse_n, n_patches=inst.n_patches, drift=inst.drift,
+                    sigma_field=getattr(inst, "sigma_field", None),
+                    diffusion=getattr(inst, "diffusion", 0),
+                    cost_field=getattr(inst, "cost_field", None),
+                    control_cost=getattr(inst, "control_cost", None))
         args.update(kw)
         return cls(inst.n, inst.controls, inst.speed, inst.mask, inst.sector, **args)
 

@@ -60,6 +60,12 @@ class RegimeInfo(ctypes.Structure):
                 ("lower_ok", ctypes.c_int32), ("reach_cells", ctypes.c_int32)]
 
 
+class Terms(ctypes.Structure):
+    _fields_ = [("sigma_field", ctypes.c_void_p), ("diffusion", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("cost_field", ctypes.c_void_p),
+                ("control_cost", ctypes.c_void_p)]
+
+
 class BatchInst(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("coarse_n", ctypes.c_int32), ("n_patches", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("h", ctypes.c_double), ("lam", ctypes.c_double),
@@ -84,6 +90,8 @@ _SIGNATURES = {
                                           ctypes.POINTER(_P)]),
     "hjb_create_problem_device": (ctypes.c_int, [ctypes.POINTER(Desc), _PTR, _PTR, _PTR, _PTR, _PTR,
                                                  _PTR, ctypes.POINTER(_P)]),
+    "hjb_create_problem_general": (ctypes.c_int, [ctypes.POINTER(Desc), _PTR, _PTR, _PTR, _PTR, _PTR,
+                                                  ctypes.POINTER(Terms), _PTR, ctypes.POINTER(_P)]),
     "hjb_coarse_solve": (ctypes.c_int, [_P, _D, _I32, ctypes.POINTER(Stats)]),
     "hjb_build_patches": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "hjb_set_feedback": (ctypes.c_int, [_P, _PTR]),

@@ -116,6 +116,23 @@ struct hjb_problem {
     bool own_stream = false;
     int device = 0, num_sms = 0;
     bool has_drift = false;
+    // general terms (Section 5.3)
+    bool gen = false, along = false;
+    float* sigf = nullptr;         // sigma(x), n*n
+    float* costf = nullptr;        // l(x), n*n
+    float* costf_c = nullptr;      // l(x) at the coarse nodes
+    float* hm32 = nullptr;         // h m(a_m)
+    double* hm64 = nullptr;
+    float* hmc32 = nullptr;        // h_c m(a_m) for the coarse grid
+    double* hmc64 = nullptr;
+    double lmax = 0;               // max l(x) + max m(a)
+    double amp32 = 1.0;            // FP32 noise amplification 1/D of SLscheme3 (>= 1)
+    double uc_max = 0;             // largest coarse value (set by hjb_coarse_solve)
+
+    // FP32 tolerance floor: half an ulp of the largest value (R17), times the
+    // amplification 1/(1 - beta Lambda0) of eq. SLscheme3, which divides the
+    // rounding of the numerator by the foot's distance from the node in cells
+    double floor32(double U) const { return fp32_tol_floor(U) * amp32; }
 
     // fine data
     float* speed = nullptr;
@@ -195,6 +212,29 @@ struct hjb_problem {
     int hist_cap = 0;
     int wave_blocks32 = 0, wave_blocks64 = 0;
 
+    // A bound on the values the solve meets: the obstacle value l/lambda + h l
+    // with a discount; without one, four times the largest coarse value once the
+    // coarse solve has run (the value is a minimum time of the same order),
+    // else the placeholder obstacle value.
+    double value_bound() const {
+        if (lambda > 0.0 || !coarse_done) return uob;
+        return std::max(1.0, 4.0 * uc_max);
+    }
+
+    void set_general(GridView& g, double hh, double dxx, bool coarse) const {
+        g.gen = (sigf && !coarse) || costf || hm32 ? 1 : 0;
+        g.along = along && !coarse ? 1 : 0;
+        g.sigf = coarse ? nullptr : sigf;
+        g.costf = coarse ? costf_c : costf;
+        g.hm32 = coarse ? hmc32 : hm32;
+        g.hm64 = coarse ? hmc64 : hm64;
+        const double du = coarse ? 0.0 : std::sqrt(2.0 * hh) / dxx;
+        g.du32 = (float)du;
+        g.du64 = du;
+        g.h32 = (float)hh;
+        g.h64 = hh;
+    }
+
     GridView fine_view() const {
         GridView g{};
         g.n = n;
@@ -216,6 +256,7 @@ struct hjb_problem {
         g.hl64 = hl;
         g.uob32 = (float)uob;
         g.uob64 = uob;
+        set_general(g, h, dx, false);
         return g;
     }
     GridView coarse_view() const {
@@ -239,6 +280,7 @@ struct hjb_problem {
         g.hl64 = hl_c;
         g.uob32 = (float)uob;     // obstacles hold the fine scheme's value on both grids
         g.uob64 = uob;
+        set_general(g, hc, dxc, true);
         return g;
     }
 };
@@ -247,6 +289,7 @@ namespace {
 
 struct Scalars {
     unsigned int relax_inc[3];
+    unsigned int relax_umax[3];
     unsigned int inc32;
     int max_key;
     int n_waves;
@@ -287,7 +330,8 @@ int validate_desc(const hjb_desc* d) {
 
 int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                   const int8_t* sector, const double* controls, const float* drift,
-                  void* cuda_stream, hjb_problem** out, bool device_inputs) {
+                  void* cuda_stream, hjb_problem** out, bool device_inputs,
+                  const hjb_terms* terms = nullptr) {
     g_last_error.clear();
     if (!out) return fail(HJB_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -333,6 +377,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         }
     }
     double cmax = 0.0, bmax = 0.0;
+    double fsum = 0.0;             // sum of c |a|_max + |b| over free nodes (for the FP32 floor)
     long long n_free_total = 0;
     bool any_obstacle = false, any_target = false;
     for (size_t k = 0; k < N; ++k) {
@@ -342,6 +387,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         any_target |= (m_h[k] == HJB_MASK_TARGET);
         if (m_h[k] == HJB_MASK_FREE) {
             cmax = std::fmax(cmax, (double)s_h[k]);
+            fsum += (double)s_h[k] * amax;
             ++n_free_total;
         }
         if (sec_h && m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
@@ -349,11 +395,45 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         if (d_h) {
             if (!std::isfinite(d_h[2 * k]) || !std::isfinite(d_h[2 * k + 1]))
                 return fail(HJB_ERR_INVALID_ARG, "drift[%zu] not finite", k);
-            if (m_h[k] == HJB_MASK_FREE)
-                bmax = std::fmax(bmax, std::hypot((double)d_h[2 * k], (double)d_h[2 * k + 1]));
+            if (m_h[k] == HJB_MASK_FREE) {
+                const double bk = std::hypot((double)d_h[2 * k], (double)d_h[2 * k + 1]);
+                bmax = std::fmax(bmax, bk);
+                fsum += bk;
+            }
         }
     }
     (void)any_target;
+    // general terms (host arrays)
+    double sig_max = desc->sigma, lx_max = desc->cost, ma_max = 0.0;
+    if (terms) {
+        if (terms->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "terms->reserved must be 0");
+        if (terms->diffusion != HJB_DIFFUSION_ISOTROPIC && terms->diffusion != HJB_DIFFUSION_CONTROL)
+            return fail(HJB_ERR_INVALID_ARG, "terms->diffusion=%d unknown", terms->diffusion);
+        if (terms->sigma_field) {
+            sig_max = 0.0;
+            for (size_t k = 0; k < N; ++k) {
+                const float v = terms->sigma_field[k];
+                if (!std::isfinite(v) || v < 0.0f) return fail(HJB_ERR_INVALID_ARG, "sigma_field[%zu] invalid", k);
+                if (m_h[k] == HJB_MASK_FREE) sig_max = std::fmax(sig_max, (double)v);
+            }
+        }
+        if (terms->cost_field) {
+            lx_max = 0.0;
+            for (size_t k = 0; k < N; ++k) {
+                const float v = terms->cost_field[k];
+                if (!std::isfinite(v) || !(v > 0.0f)) return fail(HJB_ERR_INVALID_ARG, "cost_field[%zu] invalid", k);
+                lx_max = std::fmax(lx_max, (double)v);
+            }
+        }
+        if (terms->control_cost) {
+            for (int m = 0; m < na; ++m) {
+                const double v = terms->control_cost[m];
+                if (!std::isfinite(v) || v < 0.0) return fail(HJB_ERR_INVALID_ARG, "control_cost[%d] invalid", m);
+                ma_max = std::fmax(ma_max, v);
+            }
+        }
+    }
+    const bool along = terms && terms->diffusion == HJB_DIFFUSION_CONTROL;
     if (any_obstacle && desc->lambda <= 0.0)
         return fail(HJB_ERR_INVALID_ARG, "obstacles need lambda > 0 (their value is l/lambda + h l)");
 
@@ -372,13 +452,26 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     p->dx = 2.0 / (n - 1);
     p->h = desc->h > 0.0 ? desc->h : p->dx;
     p->lambda = desc->lambda;
-    p->sigma = desc->sigma;
+    p->sigma = sig_max;           // the largest sigma(x): selects the diffusion kernels and the reach
     p->beta = 1.0 / (1.0 + p->lambda * p->h);
     p->hl = p->h * desc->cost;
-    p->uob = p->lambda > 0.0 ? p->hl / (1.0 - p->beta) : 1e6;
+    p->lmax = lx_max + ma_max;
+    p->uob = p->lambda > 0.0 ? p->h * p->lmax / (1.0 - p->beta) : 1e6;
     p->has_drift = drift != nullptr;
     p->n_free_total = n_free_total;
-    p->reach = (p->h * (cmax * amax + bmax) + std::sqrt(2.0 * p->h) * p->sigma) / p->dx;
+    p->along = along;
+    {
+        // the foot moves about h |f| / dx cells, so 1 - beta Lambda0 ~ that distance and
+        // FP32 rounding of the numerator of eq. SLscheme3 grows by its inverse; the
+        // mean |f| over free nodes stands for the minimising controls' speed
+        const double fmean = n_free_total > 0 ? fsum / (double)n_free_total : 1.0;
+        const double cells = p->h * fmean / p->dx;
+        p->amp32 = cells > 0.0 ? std::min(64.0, std::max(1.0, 1.0 / cells)) : 64.0;
+    }
+    // offsets: |h f| <= h (c |a| + |b|); the diffusion adds sqrt(2h) sigma (axes)
+    // or sqrt(2h) sigma |a| (along the control)
+    p->reach = (p->h * (cmax * amax + bmax) + std::sqrt(2.0 * p->h) * p->sigma * (along ? amax : 1.0)) /
+               p->dx;
     p->halo = sweep_halo(p->reach);
     if (p->halo > 64) {
         delete p;
@@ -441,6 +534,27 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMalloc(&p->drift, N * sizeof(float2)));
         CUP(cudaMemcpyAsync(p->drift, drift, N * sizeof(float2), kind, p->st));
     }
+    if (terms && terms->sigma_field) {
+        CUP(cudaMalloc(&p->sigf, N * sizeof(float)));
+        CUP(cudaMemcpy(p->sigf, terms->sigma_field, N * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (terms && terms->cost_field) {
+        CUP(cudaMalloc(&p->costf, N * sizeof(float)));
+        CUP(cudaMemcpy(p->costf, terms->cost_field, N * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (terms && terms->control_cost) {
+        std::vector<float> h32(na);
+        std::vector<double> h64(na);
+        for (int m = 0; m < na; ++m) {
+            h64[m] = p->h * terms->control_cost[m];
+            h32[m] = (float)h64[m];
+        }
+        CUP(cudaMalloc(&p->hm32, na * sizeof(float)));
+        CUP(cudaMalloc(&p->hm64, na * sizeof(double)));
+        CUP(cudaMemcpy(p->hm32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice));
+        CUP(cudaMemcpy(p->hm64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    p->gen = p->sigf || p->costf || p->hm32;
     {
         std::vector<float2> c32(na);
         std::vector<double2> c64(na);
@@ -469,8 +583,29 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         p->hc = p->h * p->r;
         p->beta_c = 1.0 / (1.0 + p->lambda * p->hc);
         p->hl_c = p->hc * desc->cost;
-        p->uob_c = p->lambda > 0.0 ? p->hl_c / (1.0 - p->beta_c) : 1e6;
+        p->uob_c = p->lambda > 0.0 ? p->hc * p->lmax / (1.0 - p->beta_c) : 1e6;
         const size_t Nc = (size_t)nc * nc;
+        if (terms && terms->cost_field) {
+            // l(x) of the coarse grid: the fine value at the nested node (rI, rJ)
+            std::vector<float> lc(Nc);
+            for (int J = 0; J < nc; ++J)
+                for (int I = 0; I < nc; ++I)
+                    lc[(size_t)J * nc + I] = terms->cost_field[(size_t)(p->r * J) * n + (size_t)(p->r * I)];
+            CUP(cudaMalloc(&p->costf_c, Nc * sizeof(float)));
+            CUP(cudaMemcpy(p->costf_c, lc.data(), Nc * sizeof(float), cudaMemcpyHostToDevice));
+        }
+        if (terms && terms->control_cost) {
+            std::vector<float> h32(na);
+            std::vector<double> h64(na);
+            for (int m = 0; m < na; ++m) {
+                h64[m] = p->hc * terms->control_cost[m];
+                h32[m] = (float)h64[m];
+            }
+            CUP(cudaMalloc(&p->hmc32, na * sizeof(float)));
+            CUP(cudaMalloc(&p->hmc64, na * sizeof(double)));
+            CUP(cudaMemcpy(p->hmc32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice));
+            CUP(cudaMemcpy(p->hmc64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+        }
         if (grid_relax_smem(nc, na) > 200 * 1024)
             return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d too large for the coarse solve "
                                                   "(its field must fit in shared memory)", nc));
@@ -648,7 +783,7 @@ int jacobi64(hjb_problem* p, double* buf0, double* buf1, double tol, int max_swe
 // offset, times the largest value difference across a cell), which is below
 // 1e-5 U for a reach under 26 cells; the margin 2e-5 max(1, U) exceeds 2E.
 float screening_margin(const hjb_problem* p) {
-    const double U = std::max(1.0, p->uob);
+    const double U = std::max(1.0, p->value_bound());
     return (float)(2e-5 * U);
 }
 
@@ -973,6 +1108,12 @@ int hjb_create_problem(const hjb_desc* desc, const float* speed, const uint8_t* 
     return create_common(desc, speed, mask, sector, controls, drift, cuda_stream, out, false);
 }
 
+int hjb_create_problem_general(const hjb_desc* desc, const float* speed, const uint8_t* mask,
+                               const int8_t* sector, const double* controls, const float* drift,
+                               const hjb_terms* terms, void* cuda_stream, hjb_problem** out) {
+    return create_common(desc, speed, mask, sector, controls, drift, cuda_stream, out, false, terms);
+}
+
 int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                               const int8_t* sector, const double* controls, const float* drift,
                               void* cuda_stream, hjb_problem** out) {
@@ -986,6 +1127,8 @@ void hjb_destroy(hjb_problem* p) {
     dfree(p->ctrl32); dfree(p->ctrl64);
     dfree(p->u32); dfree(p->u32b); dfree(p->u64); dfree(p->u64b);
     dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc);
+    dfree(p->sigf); dfree(p->costf); dfree(p->costf_c); dfree(p->hm32); dfree(p->hm64);
+    dfree(p->hmc32); dfree(p->hmc64);
     dfree(p->uhat); dfree(p->a); dfree(p->succ); dfree(p->jump_a); dfree(p->jump_b);
     dfree(p->label); dfree(p->key); dfree(p->order); dfree(p->bin_count); dfree(p->bin_off);
     dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
@@ -1018,11 +1161,16 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     CU(cudaMemsetAsync(&ds->wave, 0, sizeof(WaveResult), p->st));
     CU(cudaMemsetAsync(&ds->sync, 0, sizeof(GridSync), p->st));
     CU(cudaMemsetAsync(ds->relax_inc, 0, sizeof(ds->relax_inc), p->st));
+    CU(cudaMemsetAsync(ds->relax_umax, 0, sizeof(ds->relax_umax), p->st));
     RelaxArgs ra{};
     ra.g = gc;
-    ra.tol = (float)std::max(tol_c, fp32_tol_floor(p->uob_c));
+    // FP32 floor: from the obstacle value with a discount; without one the
+    // kernel takes it from the largest value of each sweep
+    ra.tol = (float)(p->lambda > 0.0 ? std::max(tol_c, p->floor32(p->uob_c)) : tol_c);
+    ra.floor_amp = (float)p->amp32;
     ra.max_sweeps = max_sweeps;
     ra.sweep_inc = ds->relax_inc;
+    ra.sweep_umax = ds->relax_umax;
     ra.sync = &ds->sync;
     ra.res = &ds->wave;
     ra.timeout_ns = kTimeoutNs;
@@ -1044,6 +1192,17 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     CoarseResult cr;
     cr.sweeps = conv ? sweeps : -sweeps;
     cr.increment = (float)last;
+    if (p->lambda <= 0.0) {
+        // largest coarse value over free nodes (the value bound without a discount)
+        std::vector<float> hu((size_t)Nc);
+        std::vector<uint8_t> hmk((size_t)Nc);
+        CU(cudaMemcpy(hu.data(), p->uc, (size_t)Nc * sizeof(float), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hmk.data(), p->mask_c, (size_t)Nc, cudaMemcpyDeviceToHost));
+        double mx = 0.0;
+        for (int k = 0; k < Nc; ++k)
+            if (hmk[k] == HJB_MASK_FREE && std::isfinite(hu[k])) mx = std::max(mx, (double)hu[k]);
+        p->uc_max = mx;
+    }
     p->coarse_done = true;
     p->built = false;
     int rc = cr.sweeps > 0 ? HJB_OK : HJB_ERR_NOT_CONVERGED;
@@ -1134,7 +1293,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
     if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
     if (!(tol32 > 0.0) || max_passes < 1 || !(tol64 >= 0.0))
         return fail(HJB_ERR_INVALID_ARG, "bad tolerances / max_passes");
-    tol32 = std::max(tol32, fp32_tol_floor(p->uob));
+    tol32 = std::max(tol32, p->floor32(p->value_bound()));
     Timer tm(p->st);
     tm.mark();
     WaveResult w32{}, w64{};
@@ -1194,7 +1353,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         // value (warm: every tile in the first two steps) before any FP64 pass.
         // The tightened tolerance stays at 8 ulp or more: nearer the rounding
         // noise of a converged FP32 field every tile would keep re-queueing.
-        const double floor32 = std::ldexp(std::max(1.0, p->uob), -22);
+        const double floor32 = std::ldexp(std::max(1.0, p->value_bound()), -22) * p->amp32;
         double tol_w = tol32;
         for (int tries = 0; tries < 2 && res > tol64 && tol64 >= floor32 &&
                             0.25 * tol_w >= 2.0 * floor32 && p->desc.schedule == 0 &&
@@ -1274,7 +1433,7 @@ int hjb_solve_full(hjb_problem* p, int32_t precision, double tol, double tol64, 
     if (precision == 32) {
         CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, nullptr, p->uob, p->st));
         CU(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32b, nullptr, p->uob, p->st));
-        rc = jacobi32(p, p->fine_view(), p->halo, p->u32, p->u32b, std::max(tol, fp32_tol_floor(p->uob)),
+        rc = jacobi32(p, p->fine_view(), p->halo, p->u32, p->u32b, std::max(tol, p->floor32(p->value_bound())),
                       max_sweeps, &s32, &last, &conv);
         if (rc) return rc;
         p->value_f64 = false;

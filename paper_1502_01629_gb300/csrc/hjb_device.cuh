@@ -30,6 +30,15 @@ struct GridView {
     float beta32; double beta64; // 1 / (1 + lambda h)
     float hl32;  double hl64;    // h * l
     float uob32; double uob64;   // value held on obstacle nodes
+    // General terms (Section 5.3); zero / null for a constant sigma and cost.
+    int gen;                     // 1 when any of the fields below is in use
+    int along;                   // diffusion sigma(x) a: two points along the control
+    const float* sigf;           // sigma(x) per node, or nullptr (d32 / d64 everywhere)
+    const float* costf;          // l(x) per node, or nullptr (hl32 / hl64 everywhere)
+    const float* hm32;           // h m(a_m) per control, or nullptr (m = 0)
+    const double* hm64;
+    float du32;  double du64;    // sqrt(2h) / dx: offset in cells per unit of sigma
+    float h32;   double h64;     // h
 };
 
 template <typename T> struct RealOf;
@@ -45,6 +54,9 @@ template <> struct RealOf<float> {
     __device__ static float hl(const GridView& g) { return g.hl32; }
     __device__ static float uob(const GridView& g) { return g.uob32; }
     __device__ static float2 ctrl(const GridView& g, int m) { return g.ctrl32[m]; }
+    __device__ static float du(const GridView& g) { return g.du32; }
+    __device__ static float h(const GridView& g) { return g.h32; }
+    __device__ static float hm(const GridView& g, int m) { return g.hm32[m]; }
 };
 template <> struct RealOf<double> {
     using V2 = double2;
@@ -54,6 +66,9 @@ template <> struct RealOf<double> {
     __device__ static double hl(const GridView& g) { return g.hl64; }
     __device__ static double uob(const GridView& g) { return g.uob64; }
     __device__ static double2 ctrl(const GridView& g, int m) { return g.ctrl64[m]; }
+    __device__ static double du(const GridView& g) { return g.du64; }
+    __device__ static double h(const GridView& g) { return g.h64; }
+    __device__ static double hm(const GridView& g, int m) { return g.hm64[m]; }
 };
 
 // One axis of a point's Q1 cell, relative to the node: the point sits at offset
@@ -155,10 +170,9 @@ __device__ __forceinline__ T bilinear_rel(const Axis<T>& ax, const Axis<T>& ay, 
 // the four points coincide with the foot (Sd4, L4 are then the single point's
 // terms, already "averaged").
 template <typename T, bool SIG, bool CLAMP, typename Acc>
-__device__ __forceinline__ void control_terms4(const GridView& g, const NodeBox<T>& bx, T fx, T fy,
-                                               T uk, const Acc& U, T& Sd, T& L) {
+__device__ __forceinline__ void control_terms4d(const NodeBox<T>& bx, T fx, T fy, T d, T uk,
+                                                const Acc& U, T& Sd, T& L) {
     if (SIG) {
-        const T d = RealOf<T>::d(g);
         const Axis<T> xm = axis_cell<T, CLAMP>(fx - d, bx.lox, bx.hix, bx.capx);
         const Axis<T> x0 = axis_cell<T, CLAMP>(fx, bx.lox, bx.hix, bx.capx);
         const Axis<T> xp = axis_cell<T, CLAMP>(fx + d, bx.lox, bx.hix, bx.capx);
@@ -174,6 +188,12 @@ __device__ __forceinline__ void control_terms4(const GridView& g, const NodeBox<
         Sd = bilinear_rel<T>(x0, y0, uk, U);
         L = x0.sw * y0.sw;
     }
+}
+
+template <typename T, bool SIG, bool CLAMP, typename Acc>
+__device__ __forceinline__ void control_terms4(const GridView& g, const NodeBox<T>& bx, T fx, T fy,
+                                               T uk, const Acc& U, T& Sd, T& L) {
+    control_terms4d<T, SIG, CLAMP>(bx, fx, fy, SIG ? RealOf<T>::d(g) : T(0), uk, U, Sd, L);
 }
 
 // Sd and L with the 1/2d = 1/4 applied (for callers that need the terms).
@@ -222,14 +242,78 @@ __device__ __forceinline__ void candidate(const GridView& g, int scheme, const N
     }
 }
 
+// best_over_controls with the general terms of Section 5.3: the offset
+// d = sqrt(2h) sigma(x) / dx of the node (or the constant one), the two points
+// foot +- d a of the diffusion sigma(x) a along the control (weight 1/2: their
+// pair sums are doubled so that the common beta/4 of the four-point form
+// applies), and the running cost h l(x) + h m(a).  Same candidates, fractions
+// and tie rule as the constant-coefficient form.
+template <typename T, bool SIG, bool CLAMP, typename CtrlFn, typename Acc>
+__device__ __forceinline__ void best_over_controls_gen(const GridView& g, int scheme, int i, int j,
+                                                       T uk, T c, T bx, T by, int m0, int stride,
+                                                       const CtrlFn& ctrl, const Acc& U,
+                                                       T& bestN, T& bestD, int& bestM) {
+    const size_t k = (size_t)j * g.n + i;
+    const T s = RealOf<T>::s(g);
+    const T beta = RealOf<T>::beta(g);
+    const T bq = SIG ? beta * T(0.25) : beta;
+    const T hl = g.costf ? RealOf<T>::h(g) * (T)g.costf[k] : RealOf<T>::hl(g);
+    const T c0 = fma(-(T(1) - beta), uk, hl);
+    T d = T(0);
+    if (SIG) d = g.sigf ? RealOf<T>::du(g) * (T)g.sigf[k] : RealOf<T>::d(g);
+    const NodeBox<T> box = node_box<T>(i, j, g.n);
+    bestN = T(INFINITY);
+    bestD = T(1);
+    bestM = 0x7fffffff;
+    for (int m = m0; m < g.na; m += stride) {
+        const V2Of<T> a = ctrl(m);
+        const T fx = s * fma(c, (T)a.x, bx);
+        const T fy = s * fma(c, (T)a.y, by);
+        T Sd, L;
+        if (SIG && g.along) {
+            const T ex = d * (T)a.x, ey = d * (T)a.y;
+            const Axis<T> xp = axis_cell<T, CLAMP>(fx + ex, box.lox, box.hix, box.capx);
+            const Axis<T> yp = axis_cell<T, CLAMP>(fy + ey, box.loy, box.hiy, box.capy);
+            const Axis<T> xm = axis_cell<T, CLAMP>(fx - ex, box.lox, box.hix, box.capx);
+            const Axis<T> ym = axis_cell<T, CLAMP>(fy - ey, box.loy, box.hiy, box.capy);
+            Sd = T(2) * (bilinear_rel<T>(xp, yp, uk, U) + bilinear_rel<T>(xm, ym, uk, U));
+            L = T(2) * (xp.sw * yp.sw + xm.sw * ym.sw);
+        } else {
+            control_terms4d<T, SIG, CLAMP>(box, fx, fy, d, uk, U, Sd, L);
+        }
+        const T cm = g.hm32 ? c0 + RealOf<T>::hm(g, m) : c0;
+        T N = fma(bq, Sd, cm);
+        T D = T(1);
+        if (scheme == 3) {
+            D = fma(-bq, L, T(1));
+            if (!(D > T(0))) {
+                N = T(INFINITY);
+                D = T(1);
+            }
+        }
+        if (N * bestD < bestN * D) {
+            bestN = N;
+            bestD = D;
+            bestM = m;
+        }
+    }
+}
+
 // Evaluate every control handled by this thread (m = m0, m0+stride, ...) for
 // node (i, j) with value uk, speed c, drift (bx, by); returns the best
 // increment as a fraction N/D and its control index (ties: lowest index).
-template <typename T, bool SIG, bool CLAMP = true, typename CtrlFn, typename Acc>
+// GEN = false compiles the constant-coefficient form only (for kernels whose
+// launcher sends general problems to their GEN = true instantiation).
+template <typename T, bool SIG, bool CLAMP = true, bool GEN = true, typename CtrlFn, typename Acc>
 __device__ __forceinline__ void best_over_controls(const GridView& g, int scheme, int i, int j,
                                                    T uk, T c, T bx, T by, int m0, int stride,
                                                    const CtrlFn& ctrl, const Acc& U,
                                                    T& bestN, T& bestD, int& bestM) {
+    if (GEN && g.gen) {
+        best_over_controls_gen<T, SIG, CLAMP>(g, scheme, i, j, uk, c, bx, by, m0, stride, ctrl, U,
+                                              bestN, bestD, bestM);
+        return;
+    }
     const T s = RealOf<T>::s(g);
     const T beta = RealOf<T>::beta(g);
     const T bq = SIG ? beta * T(0.25) : beta;

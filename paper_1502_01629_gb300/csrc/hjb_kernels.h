@@ -127,6 +127,8 @@ struct RelaxArgs {
     float tol;
     int max_sweeps;
     unsigned int* sweep_inc;  // ring of 3 per-sweep maxima (float bits), zeroed by the host
+    unsigned int* sweep_umax; // ring of 3 per-sweep largest free values (float bits), zeroed
+    float floor_amp;          // FP32 floor factor (1 / distance of the foot in cells, >= 1)
     GridSync* sync;
     WaveResult* res;
     unsigned long long timeout_ns;

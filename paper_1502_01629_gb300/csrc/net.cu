@@ -184,6 +184,9 @@ k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int tot
             if (o < NOUT) {
                 const int n = o / K, k = o - (o / K) * K;
                 float a = acc[j];
+                // two shared loads per FMA: a short unroll keeps the code (and
+                // the build) small at no cost
+#pragma unroll 4
                 for (int q = 0; q < SUB; ++q) a = fmaf(sdy[q * NPAD + n], sx[q * K + k], a);
                 acc[j] = a;
             }

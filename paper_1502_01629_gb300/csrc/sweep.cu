@@ -21,7 +21,7 @@ template <typename T> struct IncBits;
 template <> struct IncBits<float> { using type = unsigned int; };
 template <> struct IncBits<double> { using type = unsigned long long; };
 
-template <typename T, bool SIG>
+template <typename T, bool SIG, bool GEN>
 __global__ void __launch_bounds__(kTileX * kBlockY)
 k_sweep_tile(GridView g, int scheme, int R, const T* __restrict__ uin, T* __restrict__ uout,
              int32_t* __restrict__ argmin, typename IncBits<T>::type* incmax) {
@@ -71,8 +71,8 @@ k_sweep_tile(GridView g, int scheme, int R, const T* __restrict__ uin, T* __rest
             const T* base = tile + ly * W + lx;
             auto C = [&](int m) { return sctrl[m]; };
             int M;
-            const T du = interior ? node_increment<T, SIG, false>(g, scheme, i, j, k, base, W, C, M)
-                                  : node_increment<T, SIG, true>(g, scheme, i, j, k, base, W, C, M);
+            const T du = interior ? node_increment<T, SIG, false, GEN>(g, scheme, i, j, k, base, W, C, M)
+                                  : node_increment<T, SIG, true, GEN>(g, scheme, i, j, k, base, W, C, M);
             out = uk + du;
             am = M;
             lmax = fmax(lmax, fabs(du));
@@ -90,7 +90,8 @@ cudaError_t launch_sweep_impl(const GridView& g, int scheme, int R, const T* uin
     using V2 = typename RealOf<T>::V2;
     const size_t ctrl_bytes = ((size_t)g.na * sizeof(V2) + 15) & ~(size_t)15;
     const size_t smem = ctrl_bytes + (size_t)(kTileX + 2 * R) * (kTileY + 2 * R) * sizeof(T);
-    auto kern = k_sweep_tile<T, SIG>;
+    // problems with general terms (Section 5.3) take their own instantiation
+    auto kern = g.gen ? k_sweep_tile<T, SIG, true> : k_sweep_tile<T, SIG, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -11,7 +11,7 @@ namespace hjb {
 // One application of the scheme at free node k = (i, j) whose value sits at
 // base[0] in the staged tile: returns the increment N/D of the best control and
 // its index.  CLAMP = false when the staged window lies inside the grid.
-template <typename T, bool SIG, bool CLAMP, typename CtrlFn>
+template <typename T, bool SIG, bool CLAMP, bool GEN = true, typename CtrlFn>
 __device__ __forceinline__ T node_increment(const GridView& g, int scheme, int i, int j, size_t k,
                                             const T* base, int W, const CtrlFn& C, int& M) {
     const T uk = base[0];
@@ -24,7 +24,7 @@ __device__ __forceinline__ T node_increment(const GridView& g, int scheme, int i
     }
     auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
     T N, D;
-    best_over_controls<T, SIG, CLAMP>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
+    best_over_controls<T, SIG, CLAMP, GEN>(g, scheme, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
     return N / D;
 }
 
@@ -53,6 +53,15 @@ __device__ __forceinline__ double residual_node(const GridView& g, int i, int j,
     }
     const float uk32 = b32[0];
     const double uk64 = b64[0];
+    if (g.gen) {
+        // general terms (Section 5.3): every control in FP64, no screening
+        auto C64 = [&](int m) { return c64[m]; };
+        double N, D;
+        int M;
+        best_over_controls<double, SIG>(g, 2, i, j, uk64, (double)ck32, (double)bx32, (double)by32,
+                                        0, 1, C64, U64, N, D, M);
+        return fabs(N / D);
+    }
     // FP32 screening pass
     const float s32 = g.s32, beta32 = g.beta32;
     const float c0_32 = fmaf(-(1.0f - beta32), uk32, g.hl32);

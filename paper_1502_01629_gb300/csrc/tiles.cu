@@ -457,7 +457,7 @@ k_wtiles(TileArgs a) {
             };
             bool piped = false;
             if constexpr (sizeof(T) == 4) {
-                if (g.drift == nullptr && na <= 32) {
+                if (g.drift == nullptr && na <= 32 && !g.gen) {
                     piped = true;
                     if (interior)
                         visit32(std::false_type{});

@@ -178,10 +178,13 @@ k_grid_relax(RelaxArgs a, float* u) {
     int converged = 0;
     float last = 0.0f;
     for (s = 0; s < a.max_sweeps; ++s) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.sweep_inc[(s + 1) % 3] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.sweep_inc[(s + 1) % 3] = 0u;
+            a.sweep_umax[(s + 1) % 3] = 0u;
+        }
         for (int k = threadIdx.x; k < N; k += blockDim.x) su[k] = __ldcg(u + k);
         __syncthreads();
-        float lmax = 0.0f;
+        float lmax = 0.0f, umax = 0.0f;
         for (int t = gw; t < N; t += nw) {
             const int k = (s & 1) ? (N - 1 - t) : t;
             if (g.mask[k] != kFree) continue;
@@ -202,13 +205,20 @@ k_grid_relax(RelaxArgs a, float* u) {
             const float du = warp_min_increment(Nn, D, M);
             if (lane == 0) __stcg(u + k, uk + du);
             lmax = fmaxf(lmax, fabsf(du));
+            umax = fmaxf(umax, fabsf(uk + du));
         }
         const float bm = block_max<float>(lmax, red);
         if (threadIdx.x == 0 && bm > 0.0f) atomicMax(a.sweep_inc + s % 3, __float_as_uint(bm));
+        const float bu = block_max<float>(umax, red);
+        if (threadIdx.x == 0 && bu > 0.0f) atomicMax(a.sweep_umax + s % 3, __float_as_uint(bu));
         if (!grid_sync(a.sync, gridDim.x, a.timeout_ns)) break;
         if (threadIdx.x == 0) {
             last = __uint_as_float(__ldcg(a.sweep_inc + s % 3));
-            s_flag = last <= a.tol ? 1 : 0;
+            // FP32 floor of the largest free value: 1.01 ulp(max(1, U)) / 2 times
+            // the amplification of the scheme's division
+            const float U = __uint_as_float(__ldcg(a.sweep_umax + s % 3));
+            const float tol = fmaxf(a.tol, 1.01f * 1.1920929e-7f * fmaxf(1.0f, U) * a.floor_amp);
+            s_flag = last <= tol ? 1 : 0;
         }
         __syncthreads();
         if (s_flag) {
