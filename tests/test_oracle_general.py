@@ -234,3 +234,60 @@ def test_table0_modified_scheme_needs_fewer_sweeps_on_every_row():
         res[(dyn, eps)] = s
     for dyn in ("A", "B1", "C"):
         assert res[(dyn, 1e-2)][1] > res[(dyn, 0.0)][1]
+
+
+# --------------------------------------------------------- Tables 1 and 2
+
+def _pdd_dd_sweeps(inst):
+    """Sweeps of the patchy method (Gauss-Seidel in the order of increasing u_hat,
+    the coarse solution on the 51^2 grid interpolated, Section 4.3) and of the
+    static method (row-major Gauss-Seidel on the whole grid), both from a large
+    initial value to a sup-increment of 1e-6."""
+    O = oracle.Problem.from_instance(inst)
+    ref = oracle.patchy_precompute(inst, tol_c=1e-10)
+    order = np.argsort(ref["uhat"], kind="stable")
+    u0 = np.full(O.N, 1e6)
+    _, s_pdd, _ = O.solve(u0, scheme=3, order=order, tol=1e-6)
+    _, s_dd, _ = O.solve(u0, scheme=3, tol=1e-6)
+    return s_pdd, s_dd
+
+
+def _table1_instance(n, eps):
+    dx = 2.0 / (n - 1)      # Upsilon = 1: alpha = 1/2, h = alpha dx / f_min = dx / 2
+    return hi.boundary_instance(n, hi.speed_constant(n, 1.0), h=0.5 * dx, sigma=math.sqrt(eps),
+                                coarse_n=51)
+
+
+def test_table1_eikonal_diffusion_trends():
+    """Table 1 (Section 5.4), eikonal-diffusion with c = 1: in the regime of the
+    upwind diffusion ball condition the patchy method needs a handful of sweeps
+    at every grid size, while the static method needs about n/2 (the paper
+    prints 6 vs 52 at 100^2 and 6 vs 102 at 200^2 for eps = 1e-9); more
+    diffusion costs the patchy method sweeps, and it stays ahead."""
+    p101, d101 = _pdd_dd_sweeps(_table1_instance(101, 1e-9))
+    p201, d201 = _pdd_dd_sweeps(_table1_instance(201, 1e-9))
+    assert abs(d101 - 52) <= 2 and abs(d201 - 102) <= 2, (d101, d201)
+    assert p101 <= 8 and p201 <= 8, (p101, p201)
+    counts = [_pdd_dd_sweeps(_table1_instance(101, eps)) for eps in (1e-6, 1e-4, 5e-3, 1e-2)]
+    pdd = [p101] + [c[0] for c in counts]
+    assert all(a <= b for a, b in zip(pdd, pdd[1:])), pdd
+    assert pdd[-1] >= 4 * pdd[0]
+    assert all(p < d for p, d in counts)
+
+
+def test_table2_zermelo_trends():
+    """Table 2 (Section 5.4), Zermelo with eta = 1 (f_min = 1/6, f_max = 3/2,
+    Upsilon = 9, h = alpha dx / f_min = 0.6 dx): the patchy sweep count does not
+    move over several orders of magnitude of eps, rises moderately above the
+    threshold dx/120, stays below the static count, and the two approach each
+    other as the diffusion grows."""
+    n = 101
+    dx = 2.0 / (n - 1)
+    res = []
+    for eps in (1e-9, 1e-5, 1e-3, 5e-3):
+        res.append(_pdd_dd_sweeps(hi.zermelo_instance(n, eta=1.0, eps=eps, coarse_n=51, h=0.6 * dx)))
+    pdd = [r[0] for r in res]
+    assert abs(pdd[1] - pdd[0]) <= 2, pdd
+    assert pdd[0] < pdd[2] < pdd[3], pdd
+    assert all(p < d for p, d in res), res
+    assert res[-1][0] / res[-1][1] > res[0][0] / res[0][1], res
