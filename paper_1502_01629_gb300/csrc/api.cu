@@ -112,6 +112,9 @@ struct hjb_problem {
     double dx = 0, h = 0, beta = 0, hl = 0, uob = 0, sigma = 0, lambda = 0;
     double reach = 0;     // max |h f| / dx + d, cells
     int halo = 1;
+    int halo_c = 1;       // coarse grid: reach without the diffusion (R7), same h/dx
+    RelaxArgs relax_plan{};   // coarse relaxation tiles (tw, th, ntx, halo)
+    int relax_blocks = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
     int device = 0, num_sms = 0;
@@ -473,6 +476,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     p->reach = (p->h * (cmax * amax + bmax) + std::sqrt(2.0 * p->h) * p->sigma * (along ? amax : 1.0)) /
                p->dx;
     p->halo = sweep_halo(p->reach);
+    p->halo_c = sweep_halo(p->h * (cmax * amax + bmax) / p->dx);
     if (p->halo > 64) {
         delete p;
         return fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach);
@@ -606,9 +610,10 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             CUP(cudaMemcpy(p->hmc32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice));
             CUP(cudaMemcpy(p->hmc64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice));
         }
-        if (grid_relax_smem(nc, na) > 200 * 1024)
-            return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d too large for the coarse solve "
-                                                  "(its field must fit in shared memory)", nc));
+        p->relax_blocks = grid_relax_plan(nc, na, p->halo_c, p->num_sms, false, &p->relax_plan);
+        if (p->relax_blocks <= 0)
+            return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d: no co-resident tiling for the coarse "
+                                                  "solve", nc));
         CUP(cudaMalloc(&p->speed_c, Nc * sizeof(float)));
         CUP(cudaMalloc(&p->mask_c, Nc));
         CUP(cudaMalloc(&p->uc, Nc * sizeof(float)));
@@ -1174,12 +1179,13 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     ra.sync = &ds->sync;
     ra.res = &ds->wave;
     ra.timeout_ns = kTimeoutNs;
-    {
-        // one block per SM, but not more warps than coarse nodes
-        const int warps = grid_relax_threads() / 32;
-        const int blocks = std::max(1, std::min(p->num_sms, (Nc + warps - 1) / warps));
-        CU(launch_grid_relax(ra, p->uc, false, blocks, p->st));
-    }
+    ra.tw = p->relax_plan.tw;
+    ra.th = p->relax_plan.th;
+    ra.ntx = p->relax_plan.ntx;
+    ra.halo = p->relax_plan.halo;
+    ra.local_sweeps = kCoarseLocalSweeps;
+    ra.pre = p->relax_plan.pre;
+    CU(launch_grid_relax(ra, p->uc, false, p->relax_blocks, p->st));
     tm.mark();
     CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
     CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));
@@ -1211,7 +1217,7 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
         stats->increment = cr.increment;
         stats->ms_total = tm.ms(0, 1);
         stats->ms_stage[0] = stats->ms_total;
-        stats->node_updates = (long long)stats->sweeps * (long long)p->nc * p->nc;
+        stats->node_updates = (long long)stats->sweeps * kCoarseLocalSweeps * (long long)p->nc * p->nc;
         stats->node_control_updates = stats->node_updates * p->na;
         stats->status = rc;
     }

@@ -129,13 +129,19 @@ struct RelaxArgs {
     unsigned int* sweep_inc;  // ring of 3 per-sweep maxima (float bits), zeroed by the host
     unsigned int* sweep_umax; // ring of 3 per-sweep largest free values (float bits), zeroed
     float floor_amp;          // FP32 floor factor (1 / distance of the foot in cells, >= 1)
+    int tw, th, ntx;          // block tiles of the grid (set by grid_relax_plan)
+    int halo;                 // R: cells staged around a tile (>= the interpolation reach)
+    int local_sweeps;         // in-place relaxations of a tile per global sweep
+    int pre;                  // 1: the per-(node, control) geometry is kept in shared memory
     GridSync* sync;
     WaveResult* res;
     unsigned long long timeout_ns;
 };
-// One block per SM; the n x n field must fit in shared memory (grid_relax_smem).
+// Plans the block tiles of an n x n grid (sets tw, th, ntx, halo) so that every
+// tile has a co-resident block; returns the number of blocks, 0 if impossible.
+constexpr int kCoarseLocalSweeps = 4;   // local relaxations of a coarse tile per global sweep
+int grid_relax_plan(int n, int na, int halo, int num_sms, bool sig, RelaxArgs* a);
 cudaError_t launch_grid_relax(const RelaxArgs& a, float* u, bool sig, int blocks, cudaStream_t st);
-size_t grid_relax_smem(int n, int na);
 int grid_relax_threads();
 
 // Persistent cooperative kernel: max_passes passes of band-ordered waves over

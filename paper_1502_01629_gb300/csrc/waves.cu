@@ -148,15 +148,35 @@ k_waves(WaveArgs a, T* u) {
     }
 }
 
-// Whole-grid relaxation in one cooperative launch (used for the coarse solve,
-// Section 4.3): at the start of every sweep each block copies the whole value
-// field into its shared memory (the coarse grid is small), then updates its
-// share of the free nodes from that copy -- a warp per node, lanes over the
-// controls -- and writes them back; the node order alternates between
-// row-major and reverse; a grid barrier closes each sweep and the loop stops
-// once a sweep's sup-increment is <= tol.  One block of kRelaxThreads per SM.
-constexpr int kRelaxThreads = 1024;
+// Coarse-grid relaxation in one cooperative launch (the coarse solve of
+// Section 4.3, eq. SLscheme3 with sigma = 0): block b owns a fixed TW x TH tile
+// of G_c and keeps the tile's speed, drift and mask in shared memory for the
+// whole solve.  A global sweep stages the tile and a halo of R cells from u,
+// runs `local_sweeps` in-place relaxations of the tile (alternating direction;
+// a warp per node, lanes over the controls), writes the tile back and meets the
+// other blocks at the grid barrier.  Information thus crosses a whole tile per
+// global sweep.  The solve stops once the first local sweep after a staging --
+// the increment of the operator on the staged field -- is <= tol everywhere.
+// Without diffusion (the coarse problem) the geometry of every (node, control)
+// pair -- the foot's cell in the window, its fractions and 1/(1 - beta L) --
+// does not change across sweeps; when it fits (a.pre) it is formed once into
+// shared memory and a candidate costs four loads and three FMAs.
+constexpr int kRelaxThreads = 512;
 constexpr int kRelaxWarps = kRelaxThreads / 32;
+
+struct RelaxGeo {
+    float fx, fy;   // fractions of the foot in its cell
+    float rd;       // 1 / (1 - beta L), 0 when the candidate is excluded (D <= 0)
+    int off;        // window offset of the cell's lower-left vertex from the node
+};
+
+__host__ __device__ inline size_t relax_tile_bytes(int tw, int th, int R, int na, bool pre) {
+    const size_t ctrl = ((size_t)na * sizeof(float2) + 15) & ~(size_t)15;
+    const size_t win = (((size_t)(tw + 2 * R) * (th + 2 * R) * sizeof(float)) + 15) & ~(size_t)15;
+    const size_t per = (size_t)tw * th;
+    const size_t geo = pre ? per * na * sizeof(RelaxGeo) + per * sizeof(float) : 0;
+    return ctrl + geo + win + per * (sizeof(float2) + sizeof(float)) + ((per + 15) & ~(size_t)15);
+}
 
 template <bool SIG>
 __global__ void __launch_bounds__(kRelaxThreads)
@@ -164,16 +184,65 @@ k_grid_relax(RelaxArgs a, float* u) {
     extern __shared__ __align__(16) unsigned char smem[];
     const GridView& g = a.g;
     const int n = g.n;
-    const int N = n * n;
+    const int TW = a.tw, TH = a.th, R = a.halo;
+    const int W = TW + 2 * R, H = TH + 2 * R;
+    const int P = TW * TH;
     float2* sctrl = reinterpret_cast<float2*>(smem);
-    float* su = reinterpret_cast<float*>(smem + (((size_t)g.na * sizeof(float2) + 15) & ~(size_t)15));
+    const bool pre = !SIG && a.pre;
+    RelaxGeo* sgeo = reinterpret_cast<RelaxGeo*>(smem + (((size_t)g.na * sizeof(float2) + 15) & ~(size_t)15));
+    float* shl = reinterpret_cast<float*>(sgeo + (pre ? (size_t)P * g.na : 0));   // h l(x) per node
+    unsigned char* p0 = reinterpret_cast<unsigned char*>(shl + (pre ? P : 0));
+    float* su = reinterpret_cast<float*>(p0);
+    unsigned char* p1 = p0 + ((((size_t)W * H * sizeof(float)) + 15) & ~(size_t)15);
+    float2* sdrift = reinterpret_cast<float2*>(p1);
+    float* sspeed = reinterpret_cast<float*>(p1 + (size_t)P * sizeof(float2));
+    uint8_t* smask = reinterpret_cast<uint8_t*>(p1 + (size_t)P * (sizeof(float2) + sizeof(float)));
     __shared__ float red[32];
     __shared__ int s_flag;
     const int lane = threadIdx.x & 31;
-    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const int nw = gridDim.x * kRelaxWarps;
+    const int warp = threadIdx.x >> 5;
+    const int bi = (blockIdx.x % a.ntx) * TW, bj = (blockIdx.x / a.ntx) * TH;
+    const int gx0 = bi - R, gy0 = bj - R;
     for (int m = threadIdx.x; m < g.na; m += blockDim.x) sctrl[m] = g.ctrl32[m];
+    for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        const int i = bi + e % TW, j = bj + e / TW;
+        const bool in = i < n && j < n;
+        const size_t k = in ? (size_t)j * n + i : 0;
+        smask[e] = in ? g.mask[k] : (uint8_t)kTarget;    // outside the grid: never updated
+        sspeed[e] = in ? g.speed[k] : 0.0f;
+        sdrift[e] = (in && g.drift) ? g.drift[k] : make_float2(0.0f, 0.0f);
+    }
     auto C = [&](int m) { return sctrl[m]; };
+    const float beta = g.beta32;
+    __syncthreads();
+    if (pre) {
+        // the geometry of eq. SLscheme3 with sigma = 0 per (node, control), as
+        // control_terms4 / candidate form it
+        for (int q = threadIdx.x; q < P * g.na; q += blockDim.x) {
+            const int e = q / g.na, m = q - e * g.na;
+            RelaxGeo r{0.0f, 0.0f, 0.0f, 0};
+            if (smask[e] == kFree) {
+                const int i = bi + e % TW, j = bj + e / TW;
+                const NodeBox<float> box = node_box<float>(i, j, n);
+                const float2 ac = sctrl[m];
+                const float2 b = sdrift[e];
+                const float fx = g.s32 * fmaf(sspeed[e], ac.x, b.x);
+                const float fy = g.s32 * fmaf(sspeed[e], ac.y, b.y);
+                const Axis<float> x0 = axis_cell<float, true>(fx, box.lox, box.hix, box.capx);
+                const Axis<float> y0 = axis_cell<float, true>(fy, box.loy, box.hiy, box.capy);
+                const float D = fmaf(-beta, x0.sw * y0.sw, 1.0f);
+                r.fx = x0.fr;
+                r.fy = y0.fr;
+                r.rd = D > 0.0f ? 1.0f / D : 0.0f;
+                r.off = y0.off * W + x0.off;
+            }
+            sgeo[q] = r;
+        }
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            const int i = bi + e % TW, j = bj + e / TW;
+            shl[e] = (g.costf && smask[e] == kFree) ? g.h32 * g.costf[(size_t)j * n + i] : g.hl32;
+        }
+    }
     int s = 0;
     int converged = 0;
     float last = 0.0f;
@@ -182,30 +251,56 @@ k_grid_relax(RelaxArgs a, float* u) {
             a.sweep_inc[(s + 1) % 3] = 0u;
             a.sweep_umax[(s + 1) % 3] = 0u;
         }
-        for (int k = threadIdx.x; k < N; k += blockDim.x) su[k] = __ldcg(u + k);
+        for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+            const int gx = min(max(gx0 + e % W, 0), n - 1);
+            const int gy = min(max(gy0 + e / W, 0), n - 1);
+            su[e] = __ldcg(u + (size_t)gy * n + gx);
+        }
         __syncthreads();
         float lmax = 0.0f, umax = 0.0f;
-        for (int t = gw; t < N; t += nw) {
-            const int k = (s & 1) ? (N - 1 - t) : t;
-            if (g.mask[k] != kFree) continue;
-            const int i = k % n, j = k / n;
-            const float uk = su[k];
-            const float c = g.speed[k];
-            float bx = 0.0f, by = 0.0f;
-            if (g.drift) {
-                const float2 bb = g.drift[k];
-                bx = bb.x;
-                by = bb.y;
+        for (int ls = 0; ls < a.local_sweeps; ++ls) {
+            for (int t = warp; t < P; t += kRelaxWarps) {
+                const int e = ((s + ls) & 1) ? (P - 1 - t) : t;
+                if (smask[e] != kFree) continue;
+                const int ex = e % TW, ey = e / TW;
+                float* base = su + (R + ey) * W + (R + ex);
+                const float uk = base[0];
+                float du;
+                if (pre) {
+                    // (beta Sd + h l - (1 - beta) uk + h m) / D, lanes over the controls
+                    const float c0 = fmaf(-(1.0f - beta), uk, shl[e]);
+                    float v = INFINITY;
+                    for (int m = lane; m < g.na; m += 32) {
+                        const RelaxGeo r = sgeo[e * g.na + m];
+                        const float* q = base + r.off;
+                        const float a0 = fmaf(r.fx, q[1] - q[0], q[0] - uk);
+                        const float a1 = fmaf(r.fx, q[W + 1] - q[W], q[W] - uk);
+                        const float Sd = fmaf(r.fy, a1 - a0, a0);
+                        const float cm = g.hm32 ? c0 + g.hm32[m] : c0;
+                        const float N = fmaf(beta, Sd, cm);
+                        if (r.rd > 0.0f) v = fminf(v, N * r.rd);
+                    }
+                    du = order_val(__reduce_min_sync(0xffffffffu, order_key(v)));
+                } else {
+                    const float2 b = sdrift[e];
+                    auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
+                    float Nn, D;
+                    int M;
+                    best_over_controls<float, SIG>(g, 3, bi + ex, bj + ey, uk, sspeed[e], b.x, b.y, lane, 32,
+                                                   C, U, Nn, D, M);
+                    du = warp_min_increment(Nn, D, M);
+                }
+                __syncwarp();
+                if (lane == 0) base[0] = uk + du;
+                if (ls == 0) lmax = fmaxf(lmax, fabsf(du));
+                if (ls == a.local_sweeps - 1) umax = fmaxf(umax, fabsf(uk + du));
             }
-            const float* base = su + k;
-            auto U = [&](int dx, int dy) { return base[dy * n + dx]; };
-            float Nn, D;
-            int M;
-            best_over_controls<float, SIG>(g, 3, i, j, uk, c, bx, by, lane, 32, C, U, Nn, D, M);
-            const float du = warp_min_increment(Nn, D, M);
-            if (lane == 0) __stcg(u + k, uk + du);
-            lmax = fmaxf(lmax, fabsf(du));
-            umax = fmaxf(umax, fabsf(uk + du));
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            if (smask[e] != kFree) continue;
+            const int ex = e % TW, ey = e / TW;
+            __stcg(u + (size_t)(bj + ey) * n + bi + ex, su[(R + ey) * W + (R + ex)]);
         }
         const float bm = block_max<float>(lmax, red);
         if (threadIdx.x == 0 && bm > 0.0f) atomicMax(a.sweep_inc + s % 3, __float_as_uint(bm));
@@ -216,8 +311,8 @@ k_grid_relax(RelaxArgs a, float* u) {
             last = __uint_as_float(__ldcg(a.sweep_inc + s % 3));
             // FP32 floor of the largest free value: 1.01 ulp(max(1, U)) / 2 times
             // the amplification of the scheme's division
-            const float U = __uint_as_float(__ldcg(a.sweep_umax + s % 3));
-            const float tol = fmaxf(a.tol, 1.01f * 1.1920929e-7f * fmaxf(1.0f, U) * a.floor_amp);
+            const float Uv = __uint_as_float(__ldcg(a.sweep_umax + s % 3));
+            const float tol = fmaxf(a.tol, 1.01f * 1.1920929e-7f * fmaxf(1.0f, Uv) * a.floor_amp);
             s_flag = last <= tol ? 1 : 0;
         }
         __syncthreads();
@@ -257,12 +352,37 @@ int blocks_per_sm_impl(int na) {
 
 int wave_threads() { return kWaveThreads; }
 
-size_t grid_relax_smem(int n, int na) {
-    return (((size_t)na * sizeof(float2) + 15) & ~(size_t)15) + (size_t)n * n * sizeof(float);
+int grid_relax_plan(int n, int na, int halo, int num_sms, bool sig, RelaxArgs* a) {
+    // 16-wide tiles, as many rows per tile as it takes to give every block of
+    // one co-resident wave a tile; the per-(node, control) geometry is kept in
+    // shared memory when a plan with it exists
+    const void* kern = sig ? (const void*)k_grid_relax<true> : (const void*)k_grid_relax<false>;
+    const int tw = 16;
+    const int ntx = (n + tw - 1) / tw;
+    for (int pre = sig ? 0 : 1; pre >= 0; --pre) {
+        for (int th = 8; th <= 4 * n; th = th < 16 ? th + 1 : 2 * th) {
+            const size_t smem = relax_tile_bytes(tw, th, halo, na, pre != 0);
+            if (smem > 200 * 1024) break;
+            int per_sm = 0;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRelaxThreads, smem) != cudaSuccess)
+                return 0;
+            const int nty = (n + th - 1) / th;
+            if (per_sm > 0 && ntx * nty <= per_sm * num_sms) {
+                a->tw = tw;
+                a->th = th;
+                a->ntx = ntx;
+                a->halo = halo;
+                a->pre = pre;
+                return ntx * nty;
+            }
+        }
+    }
+    return 0;
 }
 
 cudaError_t launch_grid_relax(const RelaxArgs& a, float* u, bool sig, int blocks, cudaStream_t st) {
-    const size_t smem = grid_relax_smem(a.g.n, a.g.na);
+    const size_t smem = relax_tile_bytes(a.tw, a.th, a.halo, a.g.na, a.pre != 0);
     const void* kern = sig ? (const void*)k_grid_relax<true> : (const void*)k_grid_relax<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
