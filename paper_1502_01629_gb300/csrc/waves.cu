@@ -15,6 +15,7 @@
 //
 // Values written by other SMs during the kernel are read through L2
 // (ld.global.cg), never from a possibly stale L1 line.
+#include <algorithm>
 #include "hjb_kernels.h"
 
 namespace hjb {
@@ -163,6 +164,7 @@ k_waves(WaveArgs a, T* u) {
 // shared memory and a candidate costs four loads and three FMAs.
 constexpr int kRelaxThreads = 512;
 constexpr int kRelaxWarps = kRelaxThreads / 32;
+constexpr int kRelaxTW = 16;    // tile width (a power of two: node coordinates by shifts)
 
 struct RelaxGeo {
     float fx, fy;   // fractions of the foot in its cell
@@ -184,7 +186,8 @@ k_grid_relax(RelaxArgs a, float* u) {
     extern __shared__ __align__(16) unsigned char smem[];
     const GridView& g = a.g;
     const int n = g.n;
-    const int TW = a.tw, TH = a.th, R = a.halo;
+    constexpr int TW = kRelaxTW;
+    const int TH = a.th, R = a.halo;
     const int W = TW + 2 * R, H = TH + 2 * R;
     const int P = TW * TH;
     float2* sctrl = reinterpret_cast<float2*>(smem);
@@ -357,8 +360,11 @@ int grid_relax_plan(int n, int na, int halo, int num_sms, bool sig, RelaxArgs* a
     // one co-resident wave a tile; the per-(node, control) geometry is kept in
     // shared memory when a plan with it exists
     const void* kern = sig ? (const void*)k_grid_relax<true> : (const void*)k_grid_relax<false>;
-    const int tw = 16;
+    // one block per SM where the tiles allow it: a second block on one SM would
+    // make every other block wait for it at each barrier
+    const int tw = kRelaxTW;
     const int ntx = (n + tw - 1) / tw;
+    for (int pass = 0; pass < 2; ++pass)
     for (int pre = sig ? 0 : 1; pre >= 0; --pre) {
         for (int th = 8; th <= 4 * n; th = th < 16 ? th + 1 : 2 * th) {
             const size_t smem = relax_tile_bytes(tw, th, halo, na, pre != 0);
@@ -368,7 +374,8 @@ int grid_relax_plan(int n, int na, int halo, int num_sms, bool sig, RelaxArgs* a
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRelaxThreads, smem) != cudaSuccess)
                 return 0;
             const int nty = (n + th - 1) / th;
-            if (per_sm > 0 && ntx * nty <= per_sm * num_sms) {
+            const int cap = pass == 0 ? std::min(per_sm, 1) * num_sms : per_sm * num_sms;
+            if (per_sm > 0 && ntx * nty <= cap && (pass == 1 || th <= 32)) {
                 a->tw = tw;
                 a->th = th;
                 a->ntx = ntx;
