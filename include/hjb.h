@@ -185,6 +185,12 @@ int hjb_create_problem_general(const hjb_desc* desc, const float* speed, const u
                                const int8_t* sector, const double* controls, const float* drift,
                                const hjb_terms* terms, void* cuda_stream, hjb_problem** out);
 
+/* hjb_trim_memory -- the problems' device memory comes from a stream-ordered pool
+ * per device that keeps the blocks of destroyed problems for the next ones (no
+ * device-wide synchronisation on create / destroy).  This releases every cached
+ * block that no live problem holds.  Returns HJB_OK or HJB_ERR_CUDA. */
+int hjb_trim_memory(void);
+
 /* hjb_create_problem_device -- as hjb_create_problem, but speed, mask, sector and
  * drift are DEVICE pointers (e.g. torch CUDA tensors' data_ptr) on the current
  * device; they are copied device-to-device on cuda_stream.  controls stays a host

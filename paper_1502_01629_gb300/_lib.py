@@ -90,6 +90,7 @@ _SIGNATURES = {
                                           ctypes.POINTER(_P)]),
     "hjb_create_problem_device": (ctypes.c_int, [ctypes.POINTER(Desc), _PTR, _PTR, _PTR, _PTR, _PTR,
                                                  _PTR, ctypes.POINTER(_P)]),
+    "hjb_trim_memory": (ctypes.c_int, []),
     "hjb_create_problem_general": (ctypes.c_int, [ctypes.POINTER(Desc), _PTR, _PTR, _PTR, _PTR, _PTR,
                                                   ctypes.POINTER(Terms), _PTR, ctypes.POINTER(_P)]),
     "hjb_coarse_solve": (ctypes.c_int, [_P, _D, _I32, ctypes.POINTER(Stats)]),

@@ -4,12 +4,14 @@
 // full-grid comparator, the regime helper of Section 4.1 and the getters.
 #include <algorithm>
 #include <atomic>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "hjb.h"
@@ -64,6 +66,93 @@ template <typename T>
 void dfree(T*& p) {
     if (p) cudaFree((void*)p);
     p = nullptr;
+}
+
+// Device memory of the problems comes from one stream-ordered pool per device
+// that keeps freed blocks (release threshold: unlimited): creating and
+// destroying a problem then costs no device-wide synchronisation and almost no
+// driver time.  hjb_trim_memory hands the cached blocks back.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaError_t problem_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&g_pools[dev], &props);
+        if (e != cudaSuccess) {
+            g_pools[dev] = nullptr;
+            return e;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t palloc(T** ptr, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool;
+    cudaError_t e = problem_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, pool, st);
+}
+
+template <typename T>
+void pfree(T*& ptr, cudaStream_t st) {
+    if (ptr) cudaFreeAsync((void*)ptr, st);
+    ptr = nullptr;
+}
+
+// Pinned host words for the small results the host reads back: one slab of
+// slots shared by the problems (cudaMallocHost / cudaFreeHost per problem cost
+// a page pinning each); past the slab, a plain pinned allocation.
+constexpr int kPinnedSlots = 128;
+constexpr size_t kPinnedSlot = 1024;
+std::mutex g_pin_mu;
+unsigned char* g_pin_slab = nullptr;
+bool g_pin_used[kPinnedSlots] = {};
+
+cudaError_t pinned_alloc(void** out, size_t bytes) {
+    if (bytes <= kPinnedSlot) {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_slab) {
+            void* slab = nullptr;
+            if (cudaMallocHost(&slab, kPinnedSlots * kPinnedSlot) == cudaSuccess)
+                g_pin_slab = static_cast<unsigned char*>(slab);
+        }
+        if (g_pin_slab) {
+            for (int i = 0; i < kPinnedSlots; ++i) {
+                if (!g_pin_used[i]) {
+                    g_pin_used[i] = true;
+                    *out = g_pin_slab + (size_t)i * kPinnedSlot;
+                    return cudaSuccess;
+                }
+            }
+        }
+    }
+    return cudaMallocHost(out, bytes);
+}
+
+void pinned_free(void* ptr) {
+    if (!ptr) return;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        unsigned char* q = static_cast<unsigned char*>(ptr);
+        if (g_pin_slab && q >= g_pin_slab && q < g_pin_slab + kPinnedSlots * kPinnedSlot) {
+            g_pin_used[(q - g_pin_slab) / kPinnedSlot] = false;
+            return;
+        }
+    }
+    cudaFreeHost(ptr);
 }
 
 // Device allocation released at scope exit (test-path temporaries only).
@@ -383,19 +472,67 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     double fsum = 0.0;             // sum of c |a|_max + |b| over free nodes (for the FP32 floor)
     long long n_free_total = 0;
     bool any_obstacle = false, any_target = false;
-    for (size_t k = 0; k < N; ++k) {
-        if (!std::isfinite(s_h[k]) || s_h[k] < 0.0f) return fail(HJB_ERR_INVALID_ARG, "speed[%zu] invalid", k);
-        if (m_h[k] > HJB_MASK_OBSTACLE) return fail(HJB_ERR_INVALID_ARG, "mask[%zu]=%d invalid", k, m_h[k]);
-        any_obstacle |= (m_h[k] == HJB_MASK_OBSTACLE);
-        any_target |= (m_h[k] == HJB_MASK_TARGET);
-        if (m_h[k] == HJB_MASK_FREE) {
-            cmax = std::fmax(cmax, (double)s_h[k]);
-            fsum += (double)s_h[k] * amax;
-            ++n_free_total;
+    {
+        // one pass, row by row, eight independent partial results per row (the
+        // compiler vectorises it); the index of a bad entry is looked up only
+        // when one is found
+        unsigned bad = 0, obst = 0;
+        float cm = 0.0f;
+        for (size_t r = 0; r < N; r += (size_t)n) {
+            float rs[8] = {}, c8[8] = {};
+            unsigned b8 = 0, o8 = 0, n8 = 0;
+            size_t k = r;
+            const size_t end = r + (size_t)n;
+            for (; k + 8 <= end; k += 8) {
+                for (int q = 0; q < 8; ++q) {
+                    const float sv = s_h[k + q];
+                    const unsigned mk = m_h[k + q];
+                    b8 |= (unsigned)!(sv >= 0.0f && sv <= FLT_MAX) | (unsigned)(mk > (unsigned)HJB_MASK_OBSTACLE);
+                    const unsigned fr = mk == (unsigned)HJB_MASK_FREE;
+                    o8 |= (unsigned)(mk == (unsigned)HJB_MASK_OBSTACLE);
+                    const float sf = fr ? sv : 0.0f;
+                    c8[q] = c8[q] > sf ? c8[q] : sf;
+                    rs[q] += sf;
+                    n8 += fr;
+                }
+            }
+            for (; k < end; ++k) {
+                const float sv = s_h[k];
+                const unsigned mk = m_h[k];
+                b8 |= (unsigned)!(sv >= 0.0f && sv <= FLT_MAX) | (unsigned)(mk > (unsigned)HJB_MASK_OBSTACLE);
+                const unsigned fr = mk == (unsigned)HJB_MASK_FREE;
+                o8 |= (unsigned)(mk == (unsigned)HJB_MASK_OBSTACLE);
+                const float sf = fr ? sv : 0.0f;
+                c8[0] = c8[0] > sf ? c8[0] : sf;
+                rs[0] += sf;
+                n8 += fr;
+            }
+            double row = 0.0;
+            for (int q = 0; q < 8; ++q) {
+                cm = cm > c8[q] ? cm : c8[q];
+                row += (double)rs[q];
+            }
+            fsum += row * amax;
+            bad |= b8;
+            obst |= o8;
+            n_free_total += n8;
         }
-        if (sec_h && m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
-            return fail(HJB_ERR_INVALID_ARG, "sector[%zu]=%d >= n_patches", k, sec_h[k]);
-        if (d_h) {
+        if (bad) {
+            for (size_t k = 0; k < N; ++k) {
+                if (!std::isfinite(s_h[k]) || s_h[k] < 0.0f) return fail(HJB_ERR_INVALID_ARG, "speed[%zu] invalid", k);
+                if (m_h[k] > HJB_MASK_OBSTACLE) return fail(HJB_ERR_INVALID_ARG, "mask[%zu]=%d invalid", k, m_h[k]);
+            }
+        }
+        cmax = (double)cm;
+        any_obstacle = obst != 0;
+    }
+    if (sec_h) {
+        for (size_t k = 0; k < N; ++k)
+            if (m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
+                return fail(HJB_ERR_INVALID_ARG, "sector[%zu]=%d >= n_patches", k, sec_h[k]);
+    }
+    if (d_h) {
+        for (size_t k = 0; k < N; ++k) {
             if (!std::isfinite(d_h[2 * k]) || !std::isfinite(d_h[2 * k + 1]))
                 return fail(HJB_ERR_INVALID_ARG, "drift[%zu] not finite", k);
             if (m_h[k] == HJB_MASK_FREE) {
@@ -524,9 +661,9 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         p->own_stream = true;
     }
     const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CUP(cudaMalloc(&p->speed, N * sizeof(float)));
-    CUP(cudaMalloc(&p->mask, N));
-    CUP(cudaMalloc(&p->sector, N));
+    CUP(palloc(&p->speed, N * sizeof(float), p->st));
+    CUP(palloc(&p->mask, N, p->st));
+    CUP(palloc(&p->sector, N, p->st));
     CUP(cudaMemcpyAsync(p->speed, speed, N * sizeof(float), kind, p->st));
     CUP(cudaMemcpyAsync(p->mask, mask, N, kind, p->st));
     if (sector) {
@@ -535,16 +672,16 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         CUP(cudaMemsetAsync(p->sector, 0xff, N, p->st));
     }
     if (drift) {
-        CUP(cudaMalloc(&p->drift, N * sizeof(float2)));
+        CUP(palloc(&p->drift, N * sizeof(float2), p->st));
         CUP(cudaMemcpyAsync(p->drift, drift, N * sizeof(float2), kind, p->st));
     }
     if (terms && terms->sigma_field) {
-        CUP(cudaMalloc(&p->sigf, N * sizeof(float)));
-        CUP(cudaMemcpy(p->sigf, terms->sigma_field, N * sizeof(float), cudaMemcpyHostToDevice));
+        CUP(palloc(&p->sigf, N * sizeof(float), p->st));
+        CUP(cudaMemcpyAsync(p->sigf, terms->sigma_field, N * sizeof(float), cudaMemcpyHostToDevice, p->st));
     }
     if (terms && terms->cost_field) {
-        CUP(cudaMalloc(&p->costf, N * sizeof(float)));
-        CUP(cudaMemcpy(p->costf, terms->cost_field, N * sizeof(float), cudaMemcpyHostToDevice));
+        CUP(palloc(&p->costf, N * sizeof(float), p->st));
+        CUP(cudaMemcpyAsync(p->costf, terms->cost_field, N * sizeof(float), cudaMemcpyHostToDevice, p->st));
     }
     if (terms && terms->control_cost) {
         std::vector<float> h32(na);
@@ -553,10 +690,10 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             h64[m] = p->h * terms->control_cost[m];
             h32[m] = (float)h64[m];
         }
-        CUP(cudaMalloc(&p->hm32, na * sizeof(float)));
-        CUP(cudaMalloc(&p->hm64, na * sizeof(double)));
-        CUP(cudaMemcpy(p->hm32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice));
-        CUP(cudaMemcpy(p->hm64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+        CUP(palloc(&p->hm32, na * sizeof(float), p->st));
+        CUP(palloc(&p->hm64, na * sizeof(double), p->st));
+        CUP(cudaMemcpyAsync(p->hm32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice, p->st));
+        CUP(cudaMemcpyAsync(p->hm64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice, p->st));
     }
     p->gen = p->sigf || p->costf || p->hm32;
     {
@@ -566,18 +703,18 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             c32[m] = make_float2((float)controls[2 * m], (float)controls[2 * m + 1]);
             c64[m] = make_double2(controls[2 * m], controls[2 * m + 1]);
         }
-        CUP(cudaMalloc(&p->ctrl32, na * sizeof(float2)));
-        CUP(cudaMalloc(&p->ctrl64, na * sizeof(double2)));
-        CUP(cudaMemcpy(p->ctrl32, c32.data(), na * sizeof(float2), cudaMemcpyHostToDevice));
-        CUP(cudaMemcpy(p->ctrl64, c64.data(), na * sizeof(double2), cudaMemcpyHostToDevice));
+        CUP(palloc(&p->ctrl32, na * sizeof(float2), p->st));
+        CUP(palloc(&p->ctrl64, na * sizeof(double2), p->st));
+        CUP(cudaMemcpyAsync(p->ctrl32, c32.data(), na * sizeof(float2), cudaMemcpyHostToDevice, p->st));
+        CUP(cudaMemcpyAsync(p->ctrl64, c64.data(), na * sizeof(double2), cudaMemcpyHostToDevice, p->st));
     }
-    CUP(cudaMalloc(&p->u32, N * sizeof(float)));
-    CUP(cudaMalloc(&p->u32b, N * sizeof(float)));
-    CUP(cudaMalloc(&p->u64, N * sizeof(double)));
-    CUP(cudaMalloc(&p->u64b, N * sizeof(double)));
-    CUP(cudaMalloc(&p->scratch, sizeof(Scalars)));
+    CUP(palloc(&p->u32, N * sizeof(float), p->st));
+    CUP(palloc(&p->u32b, N * sizeof(float), p->st));
+    CUP(palloc(&p->u64, N * sizeof(double), p->st));
+    CUP(palloc(&p->u64b, N * sizeof(double), p->st));
+    CUP(palloc(&p->scratch, sizeof(Scalars), p->st));
     CUP(cudaMemsetAsync(p->scratch, 0, sizeof(Scalars), p->st));
-    CUP(cudaMallocHost(&p->host_pinned, sizeof(Scalars)));
+    CUP(pinned_alloc(&p->host_pinned, sizeof(Scalars)));
     CUP(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, p->u64, p->uob, p->st));
 
     if (desc->coarse_n > 0) {
@@ -595,8 +732,8 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             for (int J = 0; J < nc; ++J)
                 for (int I = 0; I < nc; ++I)
                     lc[(size_t)J * nc + I] = terms->cost_field[(size_t)(p->r * J) * n + (size_t)(p->r * I)];
-            CUP(cudaMalloc(&p->costf_c, Nc * sizeof(float)));
-            CUP(cudaMemcpy(p->costf_c, lc.data(), Nc * sizeof(float), cudaMemcpyHostToDevice));
+            CUP(palloc(&p->costf_c, Nc * sizeof(float), p->st));
+            CUP(cudaMemcpyAsync(p->costf_c, lc.data(), Nc * sizeof(float), cudaMemcpyHostToDevice, p->st));
         }
         if (terms && terms->control_cost) {
             std::vector<float> h32(na);
@@ -605,29 +742,29 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                 h64[m] = p->hc * terms->control_cost[m];
                 h32[m] = (float)h64[m];
             }
-            CUP(cudaMalloc(&p->hmc32, na * sizeof(float)));
-            CUP(cudaMalloc(&p->hmc64, na * sizeof(double)));
-            CUP(cudaMemcpy(p->hmc32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice));
-            CUP(cudaMemcpy(p->hmc64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+            CUP(palloc(&p->hmc32, na * sizeof(float), p->st));
+            CUP(palloc(&p->hmc64, na * sizeof(double), p->st));
+            CUP(cudaMemcpyAsync(p->hmc32, h32.data(), na * sizeof(float), cudaMemcpyHostToDevice, p->st));
+            CUP(cudaMemcpyAsync(p->hmc64, h64.data(), na * sizeof(double), cudaMemcpyHostToDevice, p->st));
         }
         p->relax_blocks = grid_relax_plan(nc, na, p->halo_c, p->num_sms, false, &p->relax_plan);
         if (p->relax_blocks <= 0)
             return bail(fail(HJB_ERR_INVALID_ARG, "coarse_n=%d: no co-resident tiling for the coarse "
                                                   "solve", nc));
-        CUP(cudaMalloc(&p->speed_c, Nc * sizeof(float)));
-        CUP(cudaMalloc(&p->mask_c, Nc));
-        CUP(cudaMalloc(&p->uc, Nc * sizeof(float)));
-        if (drift) CUP(cudaMalloc(&p->drift_c, Nc * sizeof(float2)));
+        CUP(palloc(&p->speed_c, Nc * sizeof(float), p->st));
+        CUP(palloc(&p->mask_c, Nc, p->st));
+        CUP(palloc(&p->uc, Nc * sizeof(float), p->st));
+        if (drift) CUP(palloc(&p->drift_c, Nc * sizeof(float2), p->st));
         CUP(launch_coarse_data(n, nc, p->speed, p->drift, p->mask, p->speed_c, p->drift_c,
                                p->mask_c, p->st));
-        CUP(cudaMalloc(&p->uhat, N * sizeof(float)));
-        CUP(cudaMalloc(&p->a, N));
-        CUP(cudaMalloc(&p->succ, N * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->jump_a, N * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->jump_b, N * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->label, N));
-        CUP(cudaMalloc(&p->key, N * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->order, N * sizeof(int32_t)));
+        CUP(palloc(&p->uhat, N * sizeof(float), p->st));
+        CUP(palloc(&p->a, N, p->st));
+        CUP(palloc(&p->succ, N * sizeof(int32_t), p->st));
+        CUP(palloc(&p->jump_a, N * sizeof(int32_t), p->st));
+        CUP(palloc(&p->jump_b, N * sizeof(int32_t), p->st));
+        CUP(palloc(&p->label, N, p->st));
+        CUP(palloc(&p->key, N * sizeof(int32_t), p->st));
+        CUP(palloc(&p->order, N * sizeof(int32_t), p->st));
         const bool warp_tiles = p->desc.schedule == 0;
         int tw = kTileSize, th = kTileSize;
         if (warp_tiles) wtile_dims(p->shape, &tw, &th);
@@ -636,33 +773,33 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         p->nt = p->ntx * p->nty;
         p->act_radius = std::max(1, (p->halo + std::min(tw, th) - 1) / std::min(tw, th));
         const size_t nt = p->nt;
-        CUP(cudaMalloc(&p->tile_min, nt * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_wave, nt * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_key, nt * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_list, nt * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->tile_inc, nt * sizeof(unsigned int)));
+        CUP(palloc(&p->tile_min, nt * sizeof(int32_t), p->st));
+        CUP(palloc(&p->tile_wave, nt * sizeof(int32_t), p->st));
+        CUP(palloc(&p->tile_key, nt * sizeof(int32_t), p->st));
+        CUP(palloc(&p->tile_list, nt * sizeof(int32_t), p->st));
+        CUP(palloc(&p->tile_inc, nt * sizeof(unsigned int), p->st));
         if (warp_tiles) {
-            CUP(cudaMalloc(&p->wt_nodes, nt * kWarpTileNodes * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->wt_speed, nt * kWarpTileNodes * sizeof(float)));
-            CUP(cudaMalloc(&p->wt_count, nt * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->wt_stamp, nt * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->wt_queue, (p->desc.tile_period + 2) * nt * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->wt_qcount, (p->desc.tile_period + 2) * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->cb_wave, nt * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->cb_key, nt * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->cb_list, nt * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->cb_off, 3 * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->cb_count, 2 * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->tinst, sizeof(TileInst)));
-            CUP(cudaMalloc(&p->rank_boff, 2 * sizeof(int32_t)));
+            CUP(palloc(&p->wt_nodes, nt * kWarpTileNodes * sizeof(int32_t), p->st));
+            CUP(palloc(&p->wt_speed, nt * kWarpTileNodes * sizeof(float), p->st));
+            CUP(palloc(&p->wt_count, nt * sizeof(int32_t), p->st));
+            CUP(palloc(&p->wt_stamp, nt * sizeof(int32_t), p->st));
+            CUP(palloc(&p->wt_queue, (p->desc.tile_period + 2) * nt * sizeof(int32_t), p->st));
+            CUP(palloc(&p->wt_qcount, (p->desc.tile_period + 2) * sizeof(int32_t), p->st));
+            CUP(palloc(&p->cb_wave, nt * sizeof(int32_t), p->st));
+            CUP(palloc(&p->cb_key, nt * sizeof(int32_t), p->st));
+            CUP(palloc(&p->cb_list, nt * sizeof(int32_t), p->st));
+            CUP(palloc(&p->cb_off, 3 * sizeof(int32_t), p->st));
+            CUP(palloc(&p->cb_count, 2 * sizeof(int32_t), p->st));
+            CUP(palloc(&p->tinst, sizeof(TileInst), p->st));
+            CUP(palloc(&p->rank_boff, 2 * sizeof(int32_t), p->st));
         } else {
-            CUP(cudaMalloc(&p->tile_key2, N * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->tile_nodes, N * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->tile_bin_count, nt * kLocalBands * sizeof(int32_t)));
-            CUP(cudaMalloc(&p->tile_bin_off, (nt * kLocalBands + 1) * sizeof(int32_t)));
+            CUP(palloc(&p->tile_key2, N * sizeof(int32_t), p->st));
+            CUP(palloc(&p->tile_nodes, N * sizeof(int32_t), p->st));
+            CUP(palloc(&p->tile_bin_count, nt * kLocalBands * sizeof(int32_t), p->st));
+            CUP(palloc(&p->tile_bin_off, (nt * kLocalBands + 1) * sizeof(int32_t), p->st));
         }
-        CUP(cudaMalloc(&p->res_off, (p->desc.tile_period + 1) * sizeof(int32_t)));
-        CUP(cudaMalloc(&p->step_inc, 2 * p->desc.tile_period * sizeof(unsigned int)));
+        CUP(palloc(&p->res_off, (p->desc.tile_period + 1) * sizeof(int32_t), p->st));
+        CUP(palloc(&p->step_inc, 2 * p->desc.tile_period * sizeof(unsigned int), p->st));
     }
     const bool sig = p->sigma > 0.0;
     {
@@ -698,10 +835,10 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
 
 int ensure_hist(hjb_problem* p, int cap) {
     if (p->hist_cap >= cap) return HJB_OK;
-    dfree(p->inc_hist32);
-    dfree(p->inc_hist64);
-    CU(cudaMalloc(&p->inc_hist32, sizeof(unsigned int) * (size_t)cap));
-    CU(cudaMalloc(&p->inc_hist64, sizeof(unsigned long long) * (size_t)cap));
+    pfree(p->inc_hist32, p->st);
+    pfree(p->inc_hist64, p->st);
+    CU(palloc(&p->inc_hist32, sizeof(unsigned int) * (size_t)cap, p->st));
+    CU(palloc(&p->inc_hist64, sizeof(unsigned long long) * (size_t)cap, p->st));
     p->hist_cap = cap;
     return HJB_OK;
 }
@@ -853,17 +990,17 @@ int rebuild_order(hjb_problem* p) {
     CU(launch_labels(p->N, p->succ, p->mask, p->sector, p->np, p->jump_a, p->jump_b, p->label, p->st));
     const int bins = p->n_bands * (p->np + 1);
     if (bins > p->bins_cap) {
-        dfree(p->bin_count);
-        dfree(p->bin_off);
-        CU(cudaMalloc(&p->bin_count, sizeof(int32_t) * (size_t)bins));
-        CU(cudaMalloc(&p->bin_off, sizeof(int32_t) * (size_t)(bins + 1)));
+        pfree(p->bin_count, p->st);
+        pfree(p->bin_off, p->st);
+        CU(palloc(&p->bin_count, sizeof(int32_t) * (size_t)bins, p->st));
+        CU(palloc(&p->bin_off, sizeof(int32_t) * (size_t)(bins + 1), p->st));
         p->bins_cap = bins;
     }
     if (p->n_bands > p->bands_cap) {
-        dfree(p->band_off);
-        dfree(p->inc_bits);
-        CU(cudaMalloc(&p->band_off, sizeof(int32_t) * (size_t)(p->n_bands + 1)));
-        CU(cudaMalloc(&p->inc_bits, sizeof(unsigned int) * 2 * (size_t)p->n_bands));
+        pfree(p->band_off, p->st);
+        pfree(p->inc_bits, p->st);
+        CU(palloc(&p->band_off, sizeof(int32_t) * (size_t)(p->n_bands + 1), p->st));
+        CU(palloc(&p->inc_bits, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
         p->bands_cap = p->n_bands;
     }
     CU(cudaMemsetAsync(p->inc_bits, 0, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
@@ -895,10 +1032,10 @@ int build_tiles(hjb_problem* p, const float* key_val) {
         // dense waves: rank of each tile's lowest band among the distinct ones
         const int S = std::max(p->n_bands, 1);
         if (S + 1 > p->rank_cap) {
-            dfree(p->rank_flags);
-            dfree(p->rank_scan);
-            CU(cudaMalloc(&p->rank_flags, sizeof(int32_t) * (size_t)(S + 1)));
-            CU(cudaMalloc(&p->rank_scan, sizeof(int32_t) * (size_t)(S + 1)));
+            pfree(p->rank_flags, p->st);
+            pfree(p->rank_scan, p->st);
+            CU(palloc(&p->rank_flags, sizeof(int32_t) * (size_t)(S + 1), p->st));
+            CU(palloc(&p->rank_scan, sizeof(int32_t) * (size_t)(S + 1), p->st));
             p->rank_cap = S + 1;
         }
         const int32_t boff[2] = {0, S};
@@ -915,10 +1052,10 @@ int build_tiles(hjb_problem* p, const float* key_val) {
     const int Dk = p->desc.schedule == 0 ? 1 : D;
     const int bins = Dk * p->n_waves;
     if (bins > p->sched_cap) {
-        dfree(p->sched_count);
-        dfree(p->sched_off);
-        CU(cudaMalloc(&p->sched_count, sizeof(int32_t) * (size_t)bins));
-        CU(cudaMalloc(&p->sched_off, sizeof(int32_t) * (size_t)(bins + 1)));
+        pfree(p->sched_count, p->st);
+        pfree(p->sched_off, p->st);
+        CU(palloc(&p->sched_count, sizeof(int32_t) * (size_t)bins, p->st));
+        CU(palloc(&p->sched_off, sizeof(int32_t) * (size_t)(bins + 1), p->st));
         p->sched_cap = bins;
     }
     if (p->desc.schedule != 0)
@@ -1037,17 +1174,17 @@ int resort_by_value(hjb_problem* p) {
     p->n_bands = hscal(p)->max_key + 1;
     const int bins = p->n_bands * (p->np + 1);
     if (bins > p->bins_cap) {
-        dfree(p->bin_count);
-        dfree(p->bin_off);
-        CU(cudaMalloc(&p->bin_count, sizeof(int32_t) * (size_t)bins));
-        CU(cudaMalloc(&p->bin_off, sizeof(int32_t) * (size_t)(bins + 1)));
+        pfree(p->bin_count, p->st);
+        pfree(p->bin_off, p->st);
+        CU(palloc(&p->bin_count, sizeof(int32_t) * (size_t)bins, p->st));
+        CU(palloc(&p->bin_off, sizeof(int32_t) * (size_t)(bins + 1), p->st));
         p->bins_cap = bins;
     }
     if (p->n_bands > p->bands_cap) {
-        dfree(p->band_off);
-        dfree(p->inc_bits);
-        CU(cudaMalloc(&p->band_off, sizeof(int32_t) * (size_t)(p->n_bands + 1)));
-        CU(cudaMalloc(&p->inc_bits, sizeof(unsigned int) * 2 * (size_t)p->n_bands));
+        pfree(p->band_off, p->st);
+        pfree(p->inc_bits, p->st);
+        CU(palloc(&p->band_off, sizeof(int32_t) * (size_t)(p->n_bands + 1), p->st));
+        CU(palloc(&p->inc_bits, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
         p->bands_cap = p->n_bands;
     }
     CU(cudaMemsetAsync(p->inc_bits, 0, sizeof(unsigned int) * 2 * (size_t)p->n_bands, p->st));
@@ -1113,6 +1250,16 @@ int hjb_create_problem(const hjb_desc* desc, const float* speed, const uint8_t* 
     return create_common(desc, speed, mask, sector, controls, drift, cuda_stream, out, false);
 }
 
+int hjb_trim_memory(void) {
+    g_last_error.clear();
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& pool : g_pools) {
+        if (!pool) continue;
+        CU(cudaMemPoolTrimTo(pool, 0));
+    }
+    return HJB_OK;
+}
+
 int hjb_create_problem_general(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                                const int8_t* sector, const double* controls, const float* drift,
                                const hjb_terms* terms, void* cuda_stream, hjb_problem** out) {
@@ -1128,24 +1275,25 @@ int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const ui
 void hjb_destroy(hjb_problem* p) {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st);
-    dfree(p->speed); dfree(p->drift); dfree(p->mask); dfree(p->sector);
-    dfree(p->ctrl32); dfree(p->ctrl64);
-    dfree(p->u32); dfree(p->u32b); dfree(p->u64); dfree(p->u64b);
-    dfree(p->speed_c); dfree(p->drift_c); dfree(p->mask_c); dfree(p->uc);
-    dfree(p->sigf); dfree(p->costf); dfree(p->costf_c); dfree(p->hm32); dfree(p->hm64);
-    dfree(p->hmc32); dfree(p->hmc64);
-    dfree(p->uhat); dfree(p->a); dfree(p->succ); dfree(p->jump_a); dfree(p->jump_b);
-    dfree(p->label); dfree(p->key); dfree(p->order); dfree(p->bin_count); dfree(p->bin_off);
-    dfree(p->band_off); dfree(p->inc_bits); dfree(p->inc_hist32); dfree(p->inc_hist64);
-    dfree(p->tile_min); dfree(p->tile_wave); dfree(p->tile_key); dfree(p->tile_list);
-    dfree(p->tile_inc); dfree(p->tile_key2); dfree(p->tile_nodes); dfree(p->tile_bin_count);
-    dfree(p->tile_bin_off); dfree(p->wt_nodes); dfree(p->wt_count); dfree(p->wt_speed);
-    dfree(p->wt_stamp); dfree(p->wt_queue); dfree(p->wt_qcount);
-    dfree(p->cb_wave); dfree(p->cb_key); dfree(p->cb_list); dfree(p->cb_off); dfree(p->cb_count);
-    dfree(p->tinst); dfree(p->rank_flags); dfree(p->rank_scan); dfree(p->rank_boff); dfree(p->sched_count); dfree(p->sched_off); dfree(p->res_off);
-    dfree(p->step_inc);
-    if (p->scratch) cudaFree(p->scratch);
-    if (p->host_pinned) cudaFreeHost(p->host_pinned);
+    pfree(p->speed, p->st); pfree(p->drift, p->st); pfree(p->mask, p->st); pfree(p->sector, p->st);
+    pfree(p->ctrl32, p->st); pfree(p->ctrl64, p->st);
+    pfree(p->u32, p->st); pfree(p->u32b, p->st); pfree(p->u64, p->st); pfree(p->u64b, p->st);
+    pfree(p->speed_c, p->st); pfree(p->drift_c, p->st); pfree(p->mask_c, p->st); pfree(p->uc, p->st);
+    pfree(p->sigf, p->st); pfree(p->costf, p->st); pfree(p->costf_c, p->st); pfree(p->hm32, p->st); pfree(p->hm64, p->st);
+    pfree(p->hmc32, p->st); pfree(p->hmc64, p->st);
+    pfree(p->uhat, p->st); pfree(p->a, p->st); pfree(p->succ, p->st); pfree(p->jump_a, p->st); pfree(p->jump_b, p->st);
+    pfree(p->label, p->st); pfree(p->key, p->st); pfree(p->order, p->st); pfree(p->bin_count, p->st); pfree(p->bin_off, p->st);
+    pfree(p->band_off, p->st); pfree(p->inc_bits, p->st); pfree(p->inc_hist32, p->st); pfree(p->inc_hist64, p->st);
+    pfree(p->tile_min, p->st); pfree(p->tile_wave, p->st); pfree(p->tile_key, p->st); pfree(p->tile_list, p->st);
+    pfree(p->tile_inc, p->st); pfree(p->tile_key2, p->st); pfree(p->tile_nodes, p->st); pfree(p->tile_bin_count, p->st);
+    pfree(p->tile_bin_off, p->st); pfree(p->wt_nodes, p->st); pfree(p->wt_count, p->st); pfree(p->wt_speed, p->st);
+    pfree(p->wt_stamp, p->st); pfree(p->wt_queue, p->st); pfree(p->wt_qcount, p->st);
+    pfree(p->cb_wave, p->st); pfree(p->cb_key, p->st); pfree(p->cb_list, p->st); pfree(p->cb_off, p->st); pfree(p->cb_count, p->st);
+    pfree(p->tinst, p->st); pfree(p->rank_flags, p->st); pfree(p->rank_scan, p->st); pfree(p->rank_boff, p->st); pfree(p->sched_count, p->st); pfree(p->sched_off, p->st); pfree(p->res_off, p->st);
+    pfree(p->step_inc, p->st);
+    pfree(p->scratch, p->st);
+    pinned_free(p->host_pinned);
+    p->host_pinned = nullptr;
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
     delete p;
 }
@@ -1202,8 +1350,9 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
         // largest coarse value over free nodes (the value bound without a discount)
         std::vector<float> hu((size_t)Nc);
         std::vector<uint8_t> hmk((size_t)Nc);
-        CU(cudaMemcpy(hu.data(), p->uc, (size_t)Nc * sizeof(float), cudaMemcpyDeviceToHost));
-        CU(cudaMemcpy(hmk.data(), p->mask_c, (size_t)Nc, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpyAsync(hu.data(), p->uc, (size_t)Nc * sizeof(float), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaMemcpyAsync(hmk.data(), p->mask_c, (size_t)Nc, cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
         double mx = 0.0;
         for (int k = 0; k < Nc; ++k)
             if (hmk[k] == HJB_MASK_FREE && std::isfinite(hu[k])) mx = std::max(mx, (double)hu[k]);
@@ -1275,7 +1424,8 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a) {
     if (!p || !a) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
     std::vector<uint8_t> m(p->N);
-    CU(cudaMemcpy(m.data(), p->mask, p->N, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpyAsync(m.data(), p->mask, p->N, cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
     std::vector<uint8_t> clean(a, a + p->N);
     for (int k = 0; k < p->N; ++k) {
         if (m[k] == HJB_MASK_FREE) {
