@@ -204,6 +204,7 @@ struct hjb_problem {
     int halo_c = 1;       // coarse grid: reach without the diffusion (R7), same h/dx
     RelaxArgs relax_plan{};   // coarse relaxation tiles (tw, th, ntx, halo)
     int relax_blocks = 0;
+    GraphCache labels_graph;  // successors + label rounds (fixed buffers)
     cudaStream_t st = nullptr;
     bool own_stream = false;
     int device = 0, num_sms = 0;
@@ -986,8 +987,13 @@ int run_waves(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
 int rebuild_order(hjb_problem* p) {
     // successors -> labels -> (band, patch) ordering, from p->a and p->key
     const GridView g = p->fine_view();
-    CU(launch_successors(g, p->a, p->succ, p->st));
-    CU(launch_labels(p->N, p->succ, p->mask, p->sector, p->np, p->jump_a, p->jump_b, p->label, p->st));
+    // successors and the pointer-jumping rounds of the labels: a short-kernel
+    // sequence over fixed buffers, replayed from a CUDA graph
+    CU(p->labels_graph.run(p->st, [&](cudaStream_t st) {
+        cudaError_t e = launch_successors(g, p->a, p->succ, st);
+        if (e != cudaSuccess) return e;
+        return launch_labels(p->N, p->succ, p->mask, p->sector, p->np, p->jump_a, p->jump_b, p->label, st);
+    }));
     const int bins = p->n_bands * (p->np + 1);
     if (bins > p->bins_cap) {
         pfree(p->bin_count, p->st);
@@ -1291,6 +1297,7 @@ void hjb_destroy(hjb_problem* p) {
     pfree(p->cb_wave, p->st); pfree(p->cb_key, p->st); pfree(p->cb_list, p->st); pfree(p->cb_off, p->st); pfree(p->cb_count, p->st);
     pfree(p->tinst, p->st); pfree(p->rank_flags, p->st); pfree(p->rank_scan, p->st); pfree(p->rank_boff, p->st); pfree(p->sched_count, p->st); pfree(p->sched_off, p->st); pfree(p->res_off, p->st);
     pfree(p->step_inc, p->st);
+    p->labels_graph.reset();
     pfree(p->scratch, p->st);
     pinned_free(p->host_pinned);
     p->host_pinned = nullptr;

@@ -432,6 +432,7 @@ __global__ void k_b_init_zero(const BatchInst* __restrict__ I, const int2* __res
 using namespace hjb;
 
 struct hjb_batch {
+    GraphCache pre_graph;        // the pre-computation sequence (fixed buffers)
     int count = 0;
     int na = 0;
     int scheme = 3;
@@ -990,6 +991,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
 
 void hjb_batch_destroy(hjb_batch* b) {
     if (!b) return;
+    b->pre_graph.reset();
     if (b->st) cudaStreamSynchronize(b->st);
     dfree(b->dinst); dfree(b->dtile);
     dfree(b->speed); dfree(b->mask); dfree(b->sector); dfree(b->u32); dfree(b->u32b); dfree(b->u64);
@@ -1041,27 +1043,35 @@ int stage_coarse(hjb_batch* b, double tol_c, int max_sweeps, long long* nodes, b
     return HJB_OK;
 }
 
-// interpolation, synthesis, bands, successors, labels; u32 = u_hat
+// interpolation, synthesis, bands, successors, labels; u32 = u_hat.  A fixed
+// sequence of about 25 short kernels over the batch's buffers, replayed from a
+// CUDA graph after the first call.
 int stage_precompute(hjb_batch* b) {
-    count_launches(1);
-    k_b_interp<<<b->nfblk, kBT, 0, b->st>>>(b->dinst, b->fblk);
-    BCU(cudaMemsetAsync(b->max_key, 0, sizeof(int) * b->count, b->st));
-    count_launches(1);
-    k_b_synthesis<<<b->nfblk, kBT, (size_t)b->na * sizeof(float2), b->st>>>(b->dinst, b->fblk, kBandCap,
-                                                                             b->max_key);
-    count_launches(1);
-    k_b_successors<<<b->nfblk, kBT, 0, b->st>>>(b->dinst, b->fblk, b->succ);
-    BCU(cudaGetLastError());
     long long nmax = 0;
     for (const auto& x : b->desc) nmax = std::max(nmax, (long long)x.n * x.n);
     int rounds = 1;
     while ((1LL << rounds) < nmax) ++rounds;
-    const int32_t* end = nullptr;
-    BCU(launch_pointer_jumps(b->N, b->succ, rounds, b->jump_a, b->jump_b, &end, b->st));
-    count_launches(1);
-    k_b_labels<<<b->nfblk, kBT, 0, b->st>>>(b->dinst, b->fblk, end, b->mask, b->sector);
-    BCU(cudaGetLastError());
-    BCU(cudaMemcpyAsync(b->u32, b->uhat, sizeof(float) * (size_t)b->N, cudaMemcpyDeviceToDevice, b->st));
+    BCU(b->pre_graph.run(b->st, [&](cudaStream_t st) {
+        count_launches(1);
+        k_b_interp<<<b->nfblk, kBT, 0, st>>>(b->dinst, b->fblk);
+        cudaError_t e = cudaMemsetAsync(b->max_key, 0, sizeof(int) * b->count, st);
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        k_b_synthesis<<<b->nfblk, kBT, (size_t)b->na * sizeof(float2), st>>>(b->dinst, b->fblk, kBandCap,
+                                                                          b->max_key);
+        count_launches(1);
+        k_b_successors<<<b->nfblk, kBT, 0, st>>>(b->dinst, b->fblk, b->succ);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int32_t* end = nullptr;
+        e = launch_pointer_jumps(b->N, b->succ, rounds, b->jump_a, b->jump_b, &end, st);
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        k_b_labels<<<b->nfblk, kBT, 0, st>>>(b->dinst, b->fblk, end, b->mask, b->sector);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(b->u32, b->uhat, sizeof(float) * (size_t)b->N, cudaMemcpyDeviceToDevice, st);
+    }));
     b->value_f64 = false;
     return HJB_OK;
 }

@@ -25,6 +25,54 @@ void clear_last_error();
 // change it), so a tolerance below this could stall short of it.
 inline double fp32_tol_floor(double umax) { return 1.01 * std::ldexp(umax > 1.0 ? umax : 1.0, -23); }
 
+// A launch sequence recorded once as a CUDA graph and replayed: for stages made
+// of many short kernels (the pointer-jumping rounds of the labels) the launch
+// latency is paid once per replay instead of once per kernel.  body(st) issues
+// the sequence on st and may depend only on values fixed for the graph's
+// owner (buffers, sizes); if recording or instantiation fails, the body runs
+// directly from then on.  The launch counter counts each replay's kernels.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    bool failed = false;
+
+    template <typename F>
+    cudaError_t run(cudaStream_t st, F&& body) {
+        if (exec) {
+            count_launches(kernels);
+            return cudaGraphLaunch(exec, st);
+        }
+        if (!failed && st != nullptr) {
+            const long long k0 = launches();
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const cudaError_t eb = body(st);
+                const cudaError_t ee = cudaStreamEndCapture(st, &g);
+                const long long k = launches() - k0;
+                count_launches(-k);                    // recorded, not run
+                if (eb == cudaSuccess && ee == cudaSuccess && g != nullptr &&
+                    cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+                    cudaGraphDestroy(g);
+                    kernels = k;
+                    count_launches(kernels);
+                    return cudaGraphLaunch(exec, st);
+                }
+                if (g) cudaGraphDestroy(g);
+                exec = nullptr;
+            }
+            cudaGetLastError();
+            failed = true;
+        }
+        return body(st);
+    }
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        kernels = 0;
+        failed = false;
+    }
+};
+
 constexpr int kBandCap = 1 << 20;                          // causal bands per problem
 constexpr unsigned long long kTimeoutNs = 4000000000ull;   // grid-wide wait limit: 4 s
 
