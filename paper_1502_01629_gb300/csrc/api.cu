@@ -479,6 +479,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         // when one is found
         unsigned bad = 0, obst = 0;
         float cm = 0.0f;
+        const int np_in = desc->n_patches;
         for (size_t r = 0; r < N; r += (size_t)n) {
             float rs[8] = {}, c8[8] = {};
             unsigned b8 = 0, o8 = 0, n8 = 0;
@@ -489,6 +490,8 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                     const float sv = s_h[k + q];
                     const unsigned mk = m_h[k + q];
                     b8 |= (unsigned)!(sv >= 0.0f && sv <= FLT_MAX) | (unsigned)(mk > (unsigned)HJB_MASK_OBSTACLE);
+                    if (sec_h)
+                        b8 |= (unsigned)(mk == (unsigned)HJB_MASK_TARGET) & (unsigned)(sec_h[k + q] >= np_in);
                     const unsigned fr = mk == (unsigned)HJB_MASK_FREE;
                     o8 |= (unsigned)(mk == (unsigned)HJB_MASK_OBSTACLE);
                     const float sf = fr ? sv : 0.0f;
@@ -501,6 +504,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                 const float sv = s_h[k];
                 const unsigned mk = m_h[k];
                 b8 |= (unsigned)!(sv >= 0.0f && sv <= FLT_MAX) | (unsigned)(mk > (unsigned)HJB_MASK_OBSTACLE);
+                if (sec_h) b8 |= (unsigned)(mk == (unsigned)HJB_MASK_TARGET) & (unsigned)(sec_h[k] >= np_in);
                 const unsigned fr = mk == (unsigned)HJB_MASK_FREE;
                 o8 |= (unsigned)(mk == (unsigned)HJB_MASK_OBSTACLE);
                 const float sf = fr ? sv : 0.0f;
@@ -522,15 +526,12 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             for (size_t k = 0; k < N; ++k) {
                 if (!std::isfinite(s_h[k]) || s_h[k] < 0.0f) return fail(HJB_ERR_INVALID_ARG, "speed[%zu] invalid", k);
                 if (m_h[k] > HJB_MASK_OBSTACLE) return fail(HJB_ERR_INVALID_ARG, "mask[%zu]=%d invalid", k, m_h[k]);
+                if (sec_h && m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
+                    return fail(HJB_ERR_INVALID_ARG, "sector[%zu]=%d >= n_patches", k, sec_h[k]);
             }
         }
         cmax = (double)cm;
         any_obstacle = obst != 0;
-    }
-    if (sec_h) {
-        for (size_t k = 0; k < N; ++k)
-            if (m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
-                return fail(HJB_ERR_INVALID_ARG, "sector[%zu]=%d >= n_patches", k, sec_h[k]);
     }
     if (d_h) {
         for (size_t k = 0; k < N; ++k) {

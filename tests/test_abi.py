@@ -81,6 +81,8 @@ def test_invalid_arrays_are_rejected_on_host(L):
     assert _create(L, d, bad_sp, mk, ctr) == L.HJB_ERR_INVALID_ARG
     neg = sp.copy(); neg[3] = -1
     assert _create(L, d, neg, mk, ctr) == L.HJB_ERR_INVALID_ARG
+    inf = sp.copy(); inf[n * n - 1] = np.inf          # the last element (tail of a row pass)
+    assert _create(L, d, inf, mk, ctr) == L.HJB_ERR_INVALID_ARG
     bad_mk = mk.copy(); bad_mk[7] = 3
     assert _create(L, d, sp, bad_mk, ctr) == L.HJB_ERR_INVALID_ARG
     obst = mk.copy(); obst[7] = 2
