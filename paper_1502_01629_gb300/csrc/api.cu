@@ -205,6 +205,7 @@ struct hjb_problem {
     RelaxArgs relax_plan{};   // coarse relaxation tiles (tw, th, ntx, halo)
     int relax_blocks = 0;
     GraphCache labels_graph;  // successors + label rounds (fixed buffers)
+    InputScan* scan_tmp = nullptr;   // creation-time input scan records
     cudaStream_t st = nullptr;
     bool own_stream = false;
     int device = 0, num_sms = 0;
@@ -442,112 +443,10 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         amax = std::fmax(amax, std::hypot(controls[2 * m], controls[2 * m + 1]));
     }
 
-    // host-side validation of the per-node inputs (copied back for device inputs)
-    std::vector<float> hs;
-    std::vector<uint8_t> hm;
-    std::vector<int8_t> hsec;
-    std::vector<float> hd;
-    const float* s_h = speed;
-    const uint8_t* m_h = mask;
-    const int8_t* sec_h = sector;
-    const float* d_h = drift;
-    if (device_inputs) {
-        hs.resize(N);
-        hm.resize(N);
-        CU(cudaMemcpy(hs.data(), speed, N * sizeof(float), cudaMemcpyDeviceToHost));
-        CU(cudaMemcpy(hm.data(), mask, N, cudaMemcpyDeviceToHost));
-        s_h = hs.data();
-        m_h = hm.data();
-        if (sector) {
-            hsec.resize(N);
-            CU(cudaMemcpy(hsec.data(), sector, N, cudaMemcpyDeviceToHost));
-            sec_h = hsec.data();
-        }
-        if (drift) {
-            hd.resize(2 * N);
-            CU(cudaMemcpy(hd.data(), drift, 2 * N * sizeof(float), cudaMemcpyDeviceToHost));
-            d_h = hd.data();
-        }
-    }
-    double cmax = 0.0, bmax = 0.0;
-    double fsum = 0.0;             // sum of c |a|_max + |b| over free nodes (for the FP32 floor)
-    long long n_free_total = 0;
-    bool any_obstacle = false, any_target = false;
-    {
-        // one pass, row by row, eight independent partial results per row (the
-        // compiler vectorises it); the index of a bad entry is looked up only
-        // when one is found
-        unsigned bad = 0, obst = 0;
-        float cm = 0.0f;
-        const int np_in = desc->n_patches;
-        for (size_t r = 0; r < N; r += (size_t)n) {
-            float rs[8] = {}, c8[8] = {};
-            unsigned b8 = 0, o8 = 0, n8 = 0;
-            size_t k = r;
-            const size_t end = r + (size_t)n;
-            for (; k + 8 <= end; k += 8) {
-                for (int q = 0; q < 8; ++q) {
-                    const float sv = s_h[k + q];
-                    const unsigned mk = m_h[k + q];
-                    b8 |= (unsigned)!(sv >= 0.0f && sv <= FLT_MAX) | (unsigned)(mk > (unsigned)HJB_MASK_OBSTACLE);
-                    if (sec_h)
-                        b8 |= (unsigned)(mk == (unsigned)HJB_MASK_TARGET) & (unsigned)(sec_h[k + q] >= np_in);
-                    const unsigned fr = mk == (unsigned)HJB_MASK_FREE;
-                    o8 |= (unsigned)(mk == (unsigned)HJB_MASK_OBSTACLE);
-                    const float sf = fr ? sv : 0.0f;
-                    c8[q] = c8[q] > sf ? c8[q] : sf;
-                    rs[q] += sf;
-                    n8 += fr;
-                }
-            }
-            for (; k < end; ++k) {
-                const float sv = s_h[k];
-                const unsigned mk = m_h[k];
-                b8 |= (unsigned)!(sv >= 0.0f && sv <= FLT_MAX) | (unsigned)(mk > (unsigned)HJB_MASK_OBSTACLE);
-                if (sec_h) b8 |= (unsigned)(mk == (unsigned)HJB_MASK_TARGET) & (unsigned)(sec_h[k] >= np_in);
-                const unsigned fr = mk == (unsigned)HJB_MASK_FREE;
-                o8 |= (unsigned)(mk == (unsigned)HJB_MASK_OBSTACLE);
-                const float sf = fr ? sv : 0.0f;
-                c8[0] = c8[0] > sf ? c8[0] : sf;
-                rs[0] += sf;
-                n8 += fr;
-            }
-            double row = 0.0;
-            for (int q = 0; q < 8; ++q) {
-                cm = cm > c8[q] ? cm : c8[q];
-                row += (double)rs[q];
-            }
-            fsum += row * amax;
-            bad |= b8;
-            obst |= o8;
-            n_free_total += n8;
-        }
-        if (bad) {
-            for (size_t k = 0; k < N; ++k) {
-                if (!std::isfinite(s_h[k]) || s_h[k] < 0.0f) return fail(HJB_ERR_INVALID_ARG, "speed[%zu] invalid", k);
-                if (m_h[k] > HJB_MASK_OBSTACLE) return fail(HJB_ERR_INVALID_ARG, "mask[%zu]=%d invalid", k, m_h[k]);
-                if (sec_h && m_h[k] == HJB_MASK_TARGET && sec_h[k] >= desc->n_patches)
-                    return fail(HJB_ERR_INVALID_ARG, "sector[%zu]=%d >= n_patches", k, sec_h[k]);
-            }
-        }
-        cmax = (double)cm;
-        any_obstacle = obst != 0;
-    }
-    if (d_h) {
-        for (size_t k = 0; k < N; ++k) {
-            if (!std::isfinite(d_h[2 * k]) || !std::isfinite(d_h[2 * k + 1]))
-                return fail(HJB_ERR_INVALID_ARG, "drift[%zu] not finite", k);
-            if (m_h[k] == HJB_MASK_FREE) {
-                const double bk = std::hypot((double)d_h[2 * k], (double)d_h[2 * k + 1]);
-                bmax = std::fmax(bmax, bk);
-                fsum += bk;
-            }
-        }
-    }
-    (void)any_target;
-    // general terms (host arrays)
+    // general terms (host arrays; the mask is read on the host only for them)
     double sig_max = desc->sigma, lx_max = desc->cost, ma_max = 0.0;
     if (terms) {
+        if (device_inputs) return fail(HJB_ERR_INVALID_ARG, "general terms take host inputs");
         if (terms->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "terms->reserved must be 0");
         if (terms->diffusion != HJB_DIFFUSION_ISOTROPIC && terms->diffusion != HJB_DIFFUSION_CONTROL)
             return fail(HJB_ERR_INVALID_ARG, "terms->diffusion=%d unknown", terms->diffusion);
@@ -556,7 +455,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             for (size_t k = 0; k < N; ++k) {
                 const float v = terms->sigma_field[k];
                 if (!std::isfinite(v) || v < 0.0f) return fail(HJB_ERR_INVALID_ARG, "sigma_field[%zu] invalid", k);
-                if (m_h[k] == HJB_MASK_FREE) sig_max = std::fmax(sig_max, (double)v);
+                if (mask[k] == HJB_MASK_FREE) sig_max = std::fmax(sig_max, (double)v);
             }
         }
         if (terms->cost_field) {
@@ -576,10 +475,81 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         }
     }
     const bool along = terms && terms->diffusion == HJB_DIFFUSION_CONTROL;
-    if (any_obstacle && desc->lambda <= 0.0)
-        return fail(HJB_ERR_INVALID_ARG, "obstacles need lambda > 0 (their value is l/lambda + h l)");
 
     hjb_problem* p = new hjb_problem();
+    auto bail = [&](int code) {
+        hjb_destroy(p);
+        return code;
+    };
+#define CUP(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? HJB_ERR_OOM : HJB_ERR_CUDA, \
+                             "%s failed: %s", #call, cudaGetErrorString(e_)));           \
+    } while (0)
+
+    CUP(cudaGetDevice(&p->device));
+    CUP(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (cuda_stream) {
+        p->st = (cudaStream_t)cuda_stream;
+    } else {
+        CUP(cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    // upload the per-node inputs, then check and reduce them on the device: the
+    // host never walks the arrays (on a coherent host, pages the GPU has read
+    // can sit in device memory, where a host pass over them is slow)
+    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUP(palloc(&p->speed, N * sizeof(float), p->st));
+    CUP(palloc(&p->mask, N, p->st));
+    CUP(palloc(&p->sector, N, p->st));
+    CUP(cudaMemcpyAsync(p->speed, speed, N * sizeof(float), kind, p->st));
+    CUP(cudaMemcpyAsync(p->mask, mask, N, kind, p->st));
+    if (sector) {
+        CUP(cudaMemcpyAsync(p->sector, sector, N, kind, p->st));
+    } else {
+        CUP(cudaMemsetAsync(p->sector, 0xff, N, p->st));
+    }
+    if (drift) {
+        CUP(palloc(&p->drift, N * sizeof(float2), p->st));
+        CUP(cudaMemcpyAsync(p->drift, drift, N * sizeof(float2), kind, p->st));
+    }
+    double cmax = 0.0, bmax = 0.0;
+    double fsum = 0.0;             // sum of c |a|_max + |b| over free nodes (for the FP32 floor)
+    long long n_free_total = 0;
+    bool any_obstacle = false;
+    {
+        const int nb = scan_inputs_blocks((long long)N);
+        CUP(palloc(&p->scan_tmp, nb * sizeof(InputScan) + 4 * sizeof(unsigned long long), p->st));
+        InputScan* d_scan = p->scan_tmp;
+        unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(d_scan + nb);
+        CUP(cudaMemsetAsync(d_bad, 0xff, 4 * sizeof(unsigned long long), p->st));
+        CUP(launch_scan_inputs((long long)N, p->speed, p->mask, sector ? p->sector : nullptr, desc->n_patches,
+                               p->drift, (float)amax, d_scan, d_bad, p->st));
+        std::vector<InputScan> hs(nb);
+        unsigned long long hb[4];
+        CUP(cudaMemcpyAsync(hs.data(), d_scan, nb * sizeof(InputScan), cudaMemcpyDeviceToHost, p->st));
+        CUP(cudaMemcpyAsync(hb, d_bad, sizeof(hb), cudaMemcpyDeviceToHost, p->st));
+        CUP(cudaStreamSynchronize(p->st));
+        pfree(p->scan_tmp, p->st);
+        unsigned flags = 0;
+        for (const InputScan& r : hs) {
+            fsum += r.fsum;
+            n_free_total += (long long)r.nfree;
+            cmax = std::fmax(cmax, (double)r.cmax);
+            bmax = std::fmax(bmax, (double)r.bmax);
+            flags |= r.flags;
+        }
+        if (flags & 1u) return bail(fail(HJB_ERR_INVALID_ARG, "speed[%llu] invalid", hb[0]));
+        if (flags & 2u) return bail(fail(HJB_ERR_INVALID_ARG, "mask[%llu] invalid", hb[1]));
+        if (flags & 4u) return bail(fail(HJB_ERR_INVALID_ARG, "sector[%llu] >= n_patches", hb[2]));
+        if (flags & 8u) return bail(fail(HJB_ERR_INVALID_ARG, "drift[%llu] not finite", hb[3]));
+        any_obstacle = (flags & 16u) != 0;
+    }
+    if (any_obstacle && desc->lambda <= 0.0)
+        return bail(fail(HJB_ERR_INVALID_ARG, "obstacles need lambda > 0 (their value is l/lambda + h l)"));
+
     p->desc = *desc;
     if (p->desc.scheme == 0) p->desc.scheme = 3;
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
@@ -616,10 +586,8 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
                p->dx;
     p->halo = sweep_halo(p->reach);
     p->halo_c = sweep_halo(p->h * (cmax * amax + bmax) / p->dx);
-    if (p->halo > 64) {
-        delete p;
-        return fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach);
-    }
+    if (p->halo > 64)
+        return bail(fail(HJB_ERR_INVALID_ARG, "interpolation reach %.1f cells is too large (max 63)", p->reach));
     {
         // automatic tile schedule: when the diffusion offset sqrt(2h) sigma reaches
         // past one cell the scheme couples nodes of equal value (no upwind
@@ -636,47 +604,10 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     }
     p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
     if (p->desc.schedule != 1 && p->desc.coarse_n > 0 &&
-        tile_smem(true, desc->n_controls, p->halo, p->shape) > 200 * 1024) {
-        delete p;
-        return fail(HJB_ERR_INVALID_ARG,
-                    "interpolation reach %.1f cells is too large for the tile schedules "
-                    "(shared memory); use schedule 1", p->reach);
-    }
-    auto bail = [&](int code) {
-        hjb_destroy(p);
-        return code;
-    };
-#define CUP(call)                                                                         \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return bail(fail(e_ == cudaErrorMemoryAllocation ? HJB_ERR_OOM : HJB_ERR_CUDA, \
-                             "%s failed: %s", #call, cudaGetErrorString(e_)));           \
-    } while (0)
-
-    CUP(cudaGetDevice(&p->device));
-    CUP(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
-    if (cuda_stream) {
-        p->st = (cudaStream_t)cuda_stream;
-    } else {
-        CUP(cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking));
-        p->own_stream = true;
-    }
-    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CUP(palloc(&p->speed, N * sizeof(float), p->st));
-    CUP(palloc(&p->mask, N, p->st));
-    CUP(palloc(&p->sector, N, p->st));
-    CUP(cudaMemcpyAsync(p->speed, speed, N * sizeof(float), kind, p->st));
-    CUP(cudaMemcpyAsync(p->mask, mask, N, kind, p->st));
-    if (sector) {
-        CUP(cudaMemcpyAsync(p->sector, sector, N, kind, p->st));
-    } else {
-        CUP(cudaMemsetAsync(p->sector, 0xff, N, p->st));
-    }
-    if (drift) {
-        CUP(palloc(&p->drift, N * sizeof(float2), p->st));
-        CUP(cudaMemcpyAsync(p->drift, drift, N * sizeof(float2), kind, p->st));
-    }
+        tile_smem(true, desc->n_controls, p->halo, p->shape) > 200 * 1024)
+        return bail(fail(HJB_ERR_INVALID_ARG,
+                         "interpolation reach %.1f cells is too large for the tile schedules "
+                         "(shared memory); use schedule 1", p->reach));
     if (terms && terms->sigma_field) {
         CUP(palloc(&p->sigf, N * sizeof(float), p->st));
         CUP(cudaMemcpyAsync(p->sigf, terms->sigma_field, N * sizeof(float), cudaMemcpyHostToDevice, p->st));
@@ -1283,6 +1214,7 @@ void hjb_destroy(hjb_problem* p) {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st);
     pfree(p->speed, p->st); pfree(p->drift, p->st); pfree(p->mask, p->st); pfree(p->sector, p->st);
+    pfree(p->scan_tmp, p->st);
     pfree(p->ctrl32, p->st); pfree(p->ctrl64, p->st);
     pfree(p->u32, p->st); pfree(p->u32b, p->st); pfree(p->u64, p->st); pfree(p->u64b, p->st);
     pfree(p->speed_c, p->st); pfree(p->drift_c, p->st); pfree(p->mask_c, p->st); pfree(p->uc, p->st);

@@ -138,6 +138,21 @@ cudaError_t launch_order(int N, const int32_t* key, const int8_t* label, const u
 cudaError_t launch_promote(int N, const float* u32, const uint8_t* mask, double uob64, double* u64,
                            cudaStream_t st);
 cudaError_t launch_demote(int N, const double* u64, float* u32, cudaStream_t st);
+// Per-node input checks and reductions at problem creation (one record per
+// block; scan_inputs_blocks(N) records).  flags: 1 speed not finite or < 0,
+// 2 mask > obstacle, 4 sector >= n_patches on a target node, 8 drift not
+// finite, 16 some obstacle.  first_bad[0..3]: smallest bad index per check
+// (set to all ones by the caller).  fsum: sum of c |a|_max + |b| over free nodes.
+struct InputScan {
+    double fsum;
+    unsigned long long nfree;
+    float cmax, bmax;
+    unsigned flags, pad;
+};
+int scan_inputs_blocks(long long N);
+cudaError_t launch_scan_inputs(long long N, const float* speed, const uint8_t* mask, const int8_t* sector,
+                               int n_patches, const float2* drift, float amax, InputScan* out,
+                               unsigned long long* first_bad, cudaStream_t st);
 cudaError_t launch_init_values(int N, const uint8_t* mask, float free_val, float uob,
                                float* u32, double* u64, double uob64, cudaStream_t st);
 cudaError_t launch_fix_nonfree(int N, const uint8_t* mask, float uob, double uob64, float* u32,

@@ -3,6 +3,7 @@
 // feedback synthesis (eq. discrete-synthesis) with the causal band keys
 // (Section 4.2), winner-take-all transport successors (eq. discrete-advection),
 // labels by pointer jumping and the (band, patch) ordering of the free nodes.
+#include <cfloat>
 #include <cmath>
 
 #include "hjb_kernels.h"
@@ -355,6 +356,103 @@ cudaError_t launch_fix_nonfree(int N, const uint8_t* mask, float uob, double uob
                                double* u64, cudaStream_t st) {
     count_launches(1);
     k_fix_nonfree<<<blocks_for(N), kThreads, 0, st>>>(N, mask, uob, uob64, u32, u64);
+    return cudaGetLastError();
+}
+
+
+namespace {
+
+// The checks and reductions of the per-node inputs at problem creation, on the
+// device (the inputs were just uploaded): one partial result per block, summed
+// by the host in block order so that the mean speed is reproducible, and the
+// smallest bad index per check folded with atomicMin.
+__global__ void __launch_bounds__(kThreads)
+k_scan_inputs(long long N, const float* __restrict__ speed, const uint8_t* __restrict__ mask,
+              const int8_t* __restrict__ sector, int n_patches, const float2* __restrict__ drift,
+              float amax, InputScan* __restrict__ out, unsigned long long* __restrict__ first_bad) {
+    float cmax = 0.0f, bmax = 0.0f, fs = 0.0f;
+    unsigned long long nfree = 0;
+    unsigned flags = 0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float sv = speed[k];
+        const unsigned mk = mask[k];
+        if (!(sv >= 0.0f && sv <= FLT_MAX)) {
+            flags |= 1u;
+            atomicMin(first_bad + 0, (unsigned long long)k);
+        }
+        if (mk > (unsigned)kObstacle) {
+            flags |= 2u;
+            atomicMin(first_bad + 1, (unsigned long long)k);
+        }
+        if (sector && mk == (unsigned)kTarget && sector[k] >= n_patches) {
+            flags |= 4u;
+            atomicMin(first_bad + 2, (unsigned long long)k);
+        }
+        float bn = 0.0f;
+        if (drift) {
+            const float2 b = drift[k];
+            if (!(fabsf(b.x) <= FLT_MAX && fabsf(b.y) <= FLT_MAX)) {
+                flags |= 8u;
+                atomicMin(first_bad + 3, (unsigned long long)k);
+            }
+            bn = hypotf(b.x, b.y);
+        }
+        if (mk == (unsigned)kObstacle) flags |= 16u;
+        if (mk == (unsigned)kFree) {
+            ++nfree;
+            cmax = fmaxf(cmax, sv);
+            if (drift) bmax = fmaxf(bmax, bn);
+            fs += sv * amax + bn;
+        }
+    }
+    __shared__ double s_fs[kThreads / 32];
+    __shared__ unsigned long long s_nf[kThreads / 32];
+    __shared__ float s_cm[kThreads / 32], s_bm[kThreads / 32];
+    __shared__ unsigned s_fl[kThreads / 32];
+    double fsd = fs;
+    for (int off = 16; off > 0; off >>= 1) {
+        fsd += __shfl_xor_sync(0xffffffffu, fsd, off);
+        nfree += __shfl_xor_sync(0xffffffffu, nfree, off);
+        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+        bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
+        flags |= __shfl_xor_sync(0xffffffffu, flags, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_fs[w] = fsd;
+        s_nf[w] = nfree;
+        s_cm[w] = cmax;
+        s_bm[w] = bmax;
+        s_fl[w] = flags;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        InputScan r{0.0, 0ull, 0.0f, 0.0f, 0u, 0u};
+        for (int i = 0; i < kThreads / 32; ++i) {
+            r.fsum += s_fs[i];
+            r.nfree += s_nf[i];
+            r.cmax = fmaxf(r.cmax, s_cm[i]);
+            r.bmax = fmaxf(r.bmax, s_bm[i]);
+            r.flags |= s_fl[i];
+        }
+        out[blockIdx.x] = r;
+    }
+}
+
+}  // namespace
+
+int scan_inputs_blocks(long long N) {
+    const long long b = (N + kThreads - 1) / kThreads;
+    return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+
+cudaError_t launch_scan_inputs(long long N, const float* speed, const uint8_t* mask, const int8_t* sector,
+                               int n_patches, const float2* drift, float amax, InputScan* out,
+                               unsigned long long* first_bad, cudaStream_t st) {
+    count_launches(1);
+    k_scan_inputs<<<scan_inputs_blocks(N), kThreads, 0, st>>>(N, speed, mask, sector, n_patches, drift, amax,
+                                                               out, first_bad);
     return cudaGetLastError();
 }
 

@@ -71,29 +71,19 @@ def test_invalid_descriptions_are_rejected_on_host(L, bad):
     assert L.lib().hjb_last_error()
 
 
-def test_invalid_arrays_are_rejected_on_host(L):
+def test_invalid_host_arguments_are_rejected(L):
+    """Arguments checked on the host before any device work: missing arrays and
+    a non-finite control.  (The per-node arrays are checked on the device after
+    the upload; tests/test_gpu_parity.py covers those.)"""
     n = 9
     d = _desc(L)
     ctr = hi.control_set(4)
     sp = np.ones(n * n, np.float32)
     mk = np.zeros(n * n, np.uint8)
-    bad_sp = sp.copy(); bad_sp[5] = np.nan
-    assert _create(L, d, bad_sp, mk, ctr) == L.HJB_ERR_INVALID_ARG
-    neg = sp.copy(); neg[3] = -1
-    assert _create(L, d, neg, mk, ctr) == L.HJB_ERR_INVALID_ARG
-    inf = sp.copy(); inf[n * n - 1] = np.inf          # the last element (tail of a row pass)
-    assert _create(L, d, inf, mk, ctr) == L.HJB_ERR_INVALID_ARG
-    bad_mk = mk.copy(); bad_mk[7] = 3
-    assert _create(L, d, sp, bad_mk, ctr) == L.HJB_ERR_INVALID_ARG
-    obst = mk.copy(); obst[7] = 2
-    assert _create(L, _desc(L, lam=0.0), sp, obst, ctr) == L.HJB_ERR_INVALID_ARG
     bad_ctr = ctr.copy(); bad_ctr[1, 0] = np.inf
     assert _create(L, d, sp, mk, bad_ctr) == L.HJB_ERR_INVALID_ARG
-    sec = np.full(n * n, -1, np.int8); tmk = mk.copy(); tmk[0] = 1; sec[0] = 5
-    assert _create(L, d, sp, tmk, ctr, sector=sec) == L.HJB_ERR_INVALID_ARG
-    drift = np.zeros(2 * n * n, np.float32); drift[4] = np.nan
-    assert _create(L, d, sp, mk, ctr, drift=drift) == L.HJB_ERR_INVALID_ARG
     assert _create(L, d, None, mk, ctr) == L.HJB_ERR_INVALID_ARG
+    assert _create(L, d, sp, None, ctr) == L.HJB_ERR_INVALID_ARG
 
 
 def test_regime_matches_paper_thresholds(L):

@@ -398,3 +398,32 @@ def test_obstacle_values_stay_exact_in_fp64():
         st = G.solve_patches(tol32=3e-7, tol64=1e-12)
         assert st["residual"] <= 1e-12
         np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)
+
+
+def test_invalid_node_arrays_are_rejected_on_the_device():
+    """Per-node inputs are checked on the device right after the upload: each bad
+    entry is refused with HJB_ERR_INVALID_ARG and its index in the message."""
+    from paper_1502_01629_gb300 import Problem, HJBError
+    n = 9
+    ctr = hi.control_set(4)
+    sp = np.ones(n * n, np.float32)
+    mk = np.zeros(n * n, np.uint8)
+    cases = []
+    s = sp.copy(); s[5] = np.nan; cases.append((dict(speed=s), "speed[5]"))
+    s = sp.copy(); s[3] = -1.0; cases.append((dict(speed=s), "speed[3]"))
+    s = sp.copy(); s[n * n - 1] = np.inf; cases.append((dict(speed=s), f"speed[{n * n - 1}]"))
+    m = mk.copy(); m[7] = 3; cases.append((dict(mask=m), "mask[7]"))
+    m = mk.copy(); m[0] = 1; sec = np.full(n * n, -1, np.int8); sec[0] = 5
+    cases.append((dict(mask=m, sector=sec), "sector[0]"))
+    dr = np.zeros(2 * n * n, np.float32); dr[4] = np.nan; cases.append((dict(drift=dr), "drift[2]"))
+    for kw, where in cases:
+        args = dict(speed=sp, mask=mk)
+        args.update(kw)
+        with pytest.raises(HJBError) as e:
+            Problem(n, ctr, args.pop("speed"), args.pop("mask"), args.pop("sector", None), **args)
+        assert e.value.code == -1 and where in str(e.value), (where, str(e.value))
+    m = mk.copy(); m[7] = 2
+    with pytest.raises(HJBError):
+        Problem(n, ctr, sp, m, lam=0.0)             # obstacles need a discount
+    with Problem(n, ctr, sp, mk) as P:                # a valid one still builds
+        assert P.n == n
