@@ -526,7 +526,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(d_scan + nb);
         CUP(cudaMemsetAsync(d_bad, 0xff, 4 * sizeof(unsigned long long), p->st));
         CUP(launch_scan_inputs((long long)N, p->speed, p->mask, sector ? p->sector : nullptr, desc->n_patches,
-                               p->drift, (float)amax, d_scan, d_bad, p->st));
+                               p->drift, (float)amax, d_scan, d_bad, nb, p->st));
         std::vector<InputScan> hs(nb);
         unsigned long long hb[4];
         CUP(cudaMemcpyAsync(hs.data(), d_scan, nb * sizeof(InputScan), cudaMemcpyDeviceToHost, p->st));
@@ -543,7 +543,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         }
         if (flags & 1u) return bail(fail(HJB_ERR_INVALID_ARG, "speed[%llu] invalid", hb[0]));
         if (flags & 2u) return bail(fail(HJB_ERR_INVALID_ARG, "mask[%llu] invalid", hb[1]));
-        if (flags & 4u) return bail(fail(HJB_ERR_INVALID_ARG, "sector[%llu] >= n_patches", hb[2]));
+        if (flags & 4u) return bail(fail(HJB_ERR_INVALID_ARG, "sector[%llu] out of range", hb[2]));
         if (flags & 8u) return bail(fail(HJB_ERR_INVALID_ARG, "drift[%llu] not finite", hb[3]));
         any_obstacle = (flags & 16u) != 0;
     }

@@ -433,6 +433,7 @@ using namespace hjb;
 
 struct hjb_batch {
     GraphCache pre_graph;        // the pre-computation sequence (fixed buffers)
+    InputScan* scan_tmp = nullptr;   // creation-time input scan records
     int count = 0;
     int na = 0;
     int scheme = 3;
@@ -717,23 +718,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     }
     b->N = b->node_off[count];
     b->Nc = b->coarse_off[count];
-    // host-side input checks (finite non-negative speed, mask codes, sectors)
     std::vector<float> cmax(count, 0.0f);
-    for (int i = 0; i < count; ++i) {
-        const long long o = b->node_off[i], e = b->node_off[i + 1];
-        for (long long k = o; k < e; ++k) {
-            if (!(speed[k] >= 0.0f) || !std::isfinite(speed[k]))
-                return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: speed[%lld] is negative or not finite",
-                                  i, k - o));
-            if (mask[k] > 2)
-                return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: mask[%lld]=%d", i, k - o, mask[k]));
-            if (sector && mask[k] == HJB_MASK_TARGET &&
-                (sector[k] < -1 || sector[k] >= insts[i].n_patches))
-                return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: sector[%lld]=%d out of range", i,
-                                  k - o, sector[k]));
-            cmax[i] = std::max(cmax[i], speed[k]);
-        }
-    }
     if (cuda_stream) {
         b->st = (cudaStream_t)cuda_stream;
     } else {
@@ -779,6 +764,46 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         for (size_t k = 0; k < N; ++k) sec[k] = mask[k] == HJB_MASK_TARGET ? 0 : -1;
         BCUP(cudaMemcpyAsync(b->sector, sec.data(), N, cudaMemcpyHostToDevice, b->st));
         BCUP(cudaStreamSynchronize(b->st));
+    }
+    {
+        // per-instance checks and speed maxima on the device, after the upload
+        // (the host never walks the concatenated arrays)
+        constexpr int kScanBlocks = 64;
+        BCUP(dalloc(b->scan_tmp, (size_t)count * kScanBlocks + (size_t)count));
+        InputScan* rec = b->scan_tmp;
+        unsigned long long* bad = reinterpret_cast<unsigned long long*>(rec + (size_t)count * kScanBlocks);
+        BCUP(cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long) * 4 * (size_t)count, b->st));
+        std::vector<int> nbk(count);
+        for (int i = 0; i < count; ++i) {
+            const long long o = b->node_off[i], Ni = b->node_off[i + 1] - o;
+            nbk[i] = std::min(kScanBlocks, scan_inputs_blocks(Ni));
+            BCUP(launch_scan_inputs(Ni, b->speed + o, b->mask + o, sector ? b->sector + o : nullptr,
+                                    insts[i].n_patches, nullptr, 1.0f, rec + (size_t)i * kScanBlocks,
+                                    bad + 4 * (size_t)i, nbk[i], b->st));
+        }
+        std::vector<InputScan> hr((size_t)count * kScanBlocks);
+        std::vector<unsigned long long> hb(4 * (size_t)count);
+        BCUP(cudaMemcpyAsync(hr.data(), rec, sizeof(InputScan) * hr.size(), cudaMemcpyDeviceToHost, b->st));
+        BCUP(cudaMemcpyAsync(hb.data(), bad, sizeof(unsigned long long) * hb.size(), cudaMemcpyDeviceToHost,
+                             b->st));
+        BCUP(cudaStreamSynchronize(b->st));
+        dfree(b->scan_tmp);
+        for (int i = 0; i < count; ++i) {
+            unsigned flags = 0;
+            for (int q = 0; q < nbk[i]; ++q) {
+                const InputScan& r = hr[(size_t)i * kScanBlocks + q];
+                flags |= r.flags;
+                cmax[i] = std::max(cmax[i], r.cmax);
+            }
+            if (flags & 1u)
+                return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: speed[%llu] is negative or not finite", i,
+                                  hb[4 * (size_t)i]));
+            if (flags & 2u)
+                return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: mask[%llu] invalid", i, hb[4 * (size_t)i + 1]));
+            if (flags & 4u)
+                return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: sector[%llu] out of range", i,
+                                  hb[4 * (size_t)i + 2]));
+        }
     }
     {
         std::vector<float2> c32(na);
@@ -992,6 +1017,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
 void hjb_batch_destroy(hjb_batch* b) {
     if (!b) return;
     b->pre_graph.reset();
+    dfree(b->scan_tmp);
     if (b->st) cudaStreamSynchronize(b->st);
     dfree(b->dinst); dfree(b->dtile);
     dfree(b->speed); dfree(b->mask); dfree(b->sector); dfree(b->u32); dfree(b->u32b); dfree(b->u64);

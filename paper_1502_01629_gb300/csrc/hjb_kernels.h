@@ -139,8 +139,8 @@ cudaError_t launch_promote(int N, const float* u32, const uint8_t* mask, double 
                            cudaStream_t st);
 cudaError_t launch_demote(int N, const double* u64, float* u32, cudaStream_t st);
 // Per-node input checks and reductions at problem creation (one record per
-// block; scan_inputs_blocks(N) records).  flags: 1 speed not finite or < 0,
-// 2 mask > obstacle, 4 sector >= n_patches on a target node, 8 drift not
+// block, `blocks` <= scan_inputs_blocks(N) of them).  flags: 1 speed not finite
+// or < 0, 2 mask > obstacle, 4 sector outside -1..n_patches-1 on a target node, 8 drift not
 // finite, 16 some obstacle.  first_bad[0..3]: smallest bad index per check
 // (set to all ones by the caller).  fsum: sum of c |a|_max + |b| over free nodes.
 struct InputScan {
@@ -152,7 +152,7 @@ struct InputScan {
 int scan_inputs_blocks(long long N);
 cudaError_t launch_scan_inputs(long long N, const float* speed, const uint8_t* mask, const int8_t* sector,
                                int n_patches, const float2* drift, float amax, InputScan* out,
-                               unsigned long long* first_bad, cudaStream_t st);
+                               unsigned long long* first_bad, int blocks, cudaStream_t st);
 cudaError_t launch_init_values(int N, const uint8_t* mask, float free_val, float uob,
                                float* u32, double* u64, double uob64, cudaStream_t st);
 cudaError_t launch_fix_nonfree(int N, const uint8_t* mask, float uob, double uob64, float* u32,

@@ -385,7 +385,7 @@ k_scan_inputs(long long N, const float* __restrict__ speed, const uint8_t* __res
             flags |= 2u;
             atomicMin(first_bad + 1, (unsigned long long)k);
         }
-        if (sector && mk == (unsigned)kTarget && sector[k] >= n_patches) {
+        if (sector && mk == (unsigned)kTarget && (sector[k] < -1 || sector[k] >= n_patches)) {
             flags |= 4u;
             atomicMin(first_bad + 2, (unsigned long long)k);
         }
@@ -449,10 +449,9 @@ int scan_inputs_blocks(long long N) {
 
 cudaError_t launch_scan_inputs(long long N, const float* speed, const uint8_t* mask, const int8_t* sector,
                                int n_patches, const float2* drift, float amax, InputScan* out,
-                               unsigned long long* first_bad, cudaStream_t st) {
+                               unsigned long long* first_bad, int blocks, cudaStream_t st) {
     count_launches(1);
-    k_scan_inputs<<<scan_inputs_blocks(N), kThreads, 0, st>>>(N, speed, mask, sector, n_patches, drift, amax,
-                                                               out, first_bad);
+    k_scan_inputs<<<blocks, kThreads, 0, st>>>(N, speed, mask, sector, n_patches, drift, amax, out, first_bad);
     return cudaGetLastError();
 }
 

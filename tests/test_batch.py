@@ -51,7 +51,6 @@ def _create(L, insts, **kw):
     dict(desc=dict(tile_shape=4)), dict(desc=dict(reserved=2)), dict(desc=dict(cost=0.0)),
     dict(inst=dict(n=5)), dict(inst=dict(coarse_n=7), at=1), dict(inst=dict(lam=0.0), at=2),
     dict(inst=dict(sigma=-1.0)), dict(inst=dict(n_patches=0), at=3), dict(inst=dict(reserved=1)),
-    dict(speed_at=100), dict(mask_at=5000),
 ])
 def test_invalid_batches_are_rejected_on_host(bad):
     from paper_1502_01629_gb300 import build
@@ -63,6 +62,22 @@ def test_invalid_batches_are_rejected_on_host(bad):
 
 
 # ----------------------------------------------------------------------- GPU
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bad", [dict(speed_at=100), dict(mask_at=5000)])
+def test_invalid_node_arrays_are_rejected_on_the_device(bad):
+    """The concatenated per-node arrays are checked on the device after the
+    upload; a bad entry is refused with HJB_ERR_INVALID_ARG."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the -m gpu tests")
+    from paper_1502_01629_gb300 import build
+    build.build()
+    from paper_1502_01629_gb300 import _lib as L
+    rc = _create(L, _small_batch(), **bad)
+    assert rc == L.HJB_ERR_INVALID_ARG
+    assert b"instance" in L.lib().hjb_last_error()
+
 
 @pytest.fixture(scope="module")
 def gpu():
