@@ -8,6 +8,8 @@
  * Problem (Section 3, eqs. HJB2 and SDE, with a discount):
  *     dX = f(X, a) dt + sigma dW,   f(x, a) = b(x) + c(x) a,   l = const,
  *     u = 0 on the target, value = E[ int_0^tau e^{-lambda t} l dt ].
+ *   hjb_create_problem_general adds the general terms of Section 5.3: sigma(x)
+ *   per node, the diffusion sigma(x) a along the control, l(x, a) = l(x) + m(a).
  * Scheme (Section 3, eq. SLscheme3; 2-D isotropic form of Section 4.1):
  *     for every free node x_i and control a in the discrete set A,
  *       x_{i,k}^{a,s} = x_i + h f(x_i, a) + s sqrt(2h) sigma e_k   (k = 1,2, s = +-1),
@@ -35,6 +37,11 @@
  *     a stream the library creates).  Entry points that return host data
  *     synchronise that stream.
  *   - A problem object may be used by one host thread at a time.
+ *   - Device memory comes from a stream-ordered pool per device that keeps the
+ *     blocks of destroyed problems for the next ones (hjb_trim_memory releases
+ *     them).  The per-node input arrays are checked on the device right after
+ *     they are uploaded; a bad entry fails the creation with HJB_ERR_INVALID_ARG
+ *     and its index in hjb_last_error().
  */
 #ifndef HJB_H
 #define HJB_H
