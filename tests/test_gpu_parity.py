@@ -427,3 +427,43 @@ def test_invalid_node_arrays_are_rejected_on_the_device():
         Problem(n, ctr, sp, m, lam=0.0)             # obstacles need a discount
     with Problem(n, ctr, sp, mk) as P:                # a valid one still builds
         assert P.n == n
+
+
+@pytest.mark.parametrize("sigma", [0.0, 0.02, 0.1])
+def test_patchy_1025_full_size_sampled(sigma):
+    """The 1025^2 workload exactly as bench.py runs it (its solver settings and
+    tolerances): too large for a full oracle solve at test time, so the FP64
+    oracle evaluates eq. SLscheme2 at 3000 sampled free nodes (random ones plus
+    nodes next to the target and the domain edge) from the returned values of
+    both the patchy solve and the plain Jacobi comparator: every sampled
+    |T u - u| lies within the residual each reports, both respect
+    0 <= u <= u_max, and the two solutions agree within the distance the two
+    residuals allow, (r1 + r2) / (1 - beta)."""
+    import bench
+    inst = hi.patchy_1025(sigma)
+    n = inst.n
+    O = oracle.Problem.from_instance(inst)
+    with P_gpu(inst, **bench.SOLVER_KW) as G:
+        G.coarse_solve(tol_c=bench.TOL_C)
+        G.build_patches()
+        st = G.solve_patches(tol32=bench.TOL32, tol64=bench.TOL64)
+        u = G.get_value()
+        sf = G.solve_full(precision=32, tol=bench.TOL32, tol64=bench.TOL64)
+        v = G.get_value()
+    assert st["residual"] <= bench.TOL64 and sf["residual"] <= bench.TOL64
+    m = inst.mask.reshape(n, n)
+    free = m == hi.MASK_FREE
+    near = np.zeros_like(free)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            near |= np.roll(np.roll(m != hi.MASK_FREE, dy, 0), dx, 1)
+    near[0, :] = near[-1, :] = near[:, 0] = near[:, -1] = True
+    rng = np.random.default_rng(13)
+    special = np.flatnonzero((near & free).reshape(-1))
+    pick = np.concatenate([rng.choice(np.flatnonzero(free.reshape(-1)), 2000, replace=False),
+                           rng.choice(special, 1000, replace=False)])
+    for w, res in ((u, st["residual"]), (v, sf["residual"])):
+        worst = max(abs(O.node_update(w, int(k), scheme=2)[0] - w[k]) for k in pick)
+        assert worst <= res * (1 + 1e-9) + 1e-15, (worst, res)
+        assert w.min() >= 0.0 and w.max() <= O.u_max * (1 + 1e-12)
+    assert np.abs(u - v).max() <= (st["residual"] + sf["residual"]) / (1.0 - O.beta) + 1e-12
