@@ -467,3 +467,30 @@ def test_patchy_1025_full_size_sampled(sigma):
         assert worst <= res * (1 + 1e-9) + 1e-15, (worst, res)
         assert w.min() >= 0.0 and w.max() <= O.u_max * (1 + 1e-12)
     assert np.abs(u - v).max() <= (st["residual"] + sf["residual"]) / (1.0 - O.beta) + 1e-12
+
+
+def test_device_pointer_inputs_match_host_inputs():
+    """hjb_create_problem_device takes the per-node arrays as device pointers
+    (torch CUDA tensors here): same checks, same problem -- the operator and the
+    patchy solve give the host-created problem's results bit for bit, and a bad
+    entry is refused the same way."""
+    from paper_1502_01629_gb300 import Problem, HJBError
+    inst = hi.patchy_1025(0.02, n=129, coarse_n=17)
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sp, mk, sec = t(inst.speed), t(inst.mask), t(inst.sector)
+    kw = dict(sigma=inst.sigma, lam=inst.lam, coarse_n=inst.coarse_n, n_patches=inst.n_patches)
+    u = oracle.Problem.from_instance(inst).fix_nonfree(hi.random_values(inst.n, 5, 0.0, 1.0, inst.mask))
+    with Problem(inst.n, inst.controls, inst.speed, inst.mask, inst.sector, **kw) as H, \
+            Problem(inst.n, inst.controls, sp, mk, sec, device_inputs=True, **kw) as D:
+        for P in (H, D):
+            P.coarse_solve(tol_c=1e-6)
+            P.build_patches()
+            P.solve_patches(tol32=3e-7, tol64=1e-10)
+        np.testing.assert_array_equal(D.get_value(), H.get_value())
+        np.testing.assert_array_equal(D.apply_operator(u)[0], H.apply_operator(u)[0])
+    bad = sp.clone()
+    bad[17] = float("nan")
+    with pytest.raises(HJBError) as e:
+        Problem(inst.n, inst.controls, bad, mk, sec, device_inputs=True, **kw)
+    assert "speed[17]" in str(e.value)
