@@ -471,8 +471,10 @@ def test_patchy_1025_full_size_sampled(sigma):
 
 def test_device_pointer_inputs_match_host_inputs():
     """hjb_create_problem_device takes the per-node arrays as device pointers
-    (torch CUDA tensors here): same checks, same problem -- the operator and the
-    patchy solve give the host-created problem's results bit for bit, and a bad
+    (torch CUDA tensors here): same checks, same problem -- the operator gives
+    the host-created problem's results bit for bit, the two patchy solves agree
+    within what their FP64 residuals allow (the relaxations read neighbours'
+    values as they are being updated, so the last bits may differ), and a bad
     entry is refused the same way."""
     from paper_1502_01629_gb300 import Problem, HJBError
     inst = hi.patchy_1025(0.02, n=129, coarse_n=17)
@@ -483,11 +485,13 @@ def test_device_pointer_inputs_match_host_inputs():
     u = oracle.Problem.from_instance(inst).fix_nonfree(hi.random_values(inst.n, 5, 0.0, 1.0, inst.mask))
     with Problem(inst.n, inst.controls, inst.speed, inst.mask, inst.sector, **kw) as H, \
             Problem(inst.n, inst.controls, sp, mk, sec, device_inputs=True, **kw) as D:
+        res = []
         for P in (H, D):
             P.coarse_solve(tol_c=1e-6)
             P.build_patches()
-            P.solve_patches(tol32=3e-7, tol64=1e-10)
-        np.testing.assert_array_equal(D.get_value(), H.get_value())
+            res.append(P.solve_patches(tol32=3e-7, tol64=1e-10)["residual"])
+        beta = 1.0 / (1.0 + inst.lam * 2.0 / (inst.n - 1))
+        assert np.abs(D.get_value() - H.get_value()).max() <= sum(res) / (1.0 - beta) + 1e-12
         np.testing.assert_array_equal(D.apply_operator(u)[0], H.apply_operator(u)[0])
     bad = sp.clone()
     bad[17] = float("nan")
