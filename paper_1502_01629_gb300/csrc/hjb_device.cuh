@@ -432,7 +432,8 @@ __device__ __forceinline__ T block_max(T v, T* scratch32) {
 
 // State of the grid-wide barrier of a cooperative (co-resident) launch.  Blocks
 // arrive on one of kSyncGroups group counters (each on its own 128-byte line);
-// the last arriver of a group arrives on the top counter.
+// the last arriver of a group arrives on the top counter `count`.  `gen` is
+// unused (kept for the layout).
 constexpr int kSyncGroups = 16;
 struct GridSync {
     unsigned int count;
@@ -460,10 +461,18 @@ __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
     return v;
 }
 
-// Two-level generation barrier.  Every wait is bounded by `timeout_ns` of global
-// time; on expiry the block records HJB_ERR_TIMEOUT and every block leaves at
-// its next barrier.  Returns false when the grid must stop.  Requires all
-// blocks to be co-resident (cudaLaunchCooperativeKernel).
+// Two-level counting barrier.  The counters only grow: a block arriving at the
+// e-th barrier of the launch (e = 0, 1, ...) finds its group counter at
+// e * members + k (k earlier arrivals of its group), so the epoch e is known from
+// the arrival itself; the last arriver of a group adds one to the top counter,
+// and the barrier is complete once the top counter reaches (e + 1) * G.  No
+// counter is reset and no generation word is written, so the last block's path
+// through the barrier is two atomics and the waiters' next poll.  Every wait is
+// bounded by `timeout_ns` of global time; on expiry the block records
+// HJB_ERR_TIMEOUT and every block leaves at its next barrier.  Returns false
+// when the grid must stop.  Requires all blocks to be co-resident
+// (cudaLaunchCooperativeKernel) and the GridSync zeroed before the launch; the
+// counters allow 2^32 / (blocks per group) barriers per launch.
 __device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int nblocks,
                                           unsigned long long timeout_ns) {
     __syncthreads();
@@ -471,29 +480,22 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned int nblocks,
         const unsigned int G = nblocks < (unsigned int)kSyncGroups ? nblocks : (unsigned int)kSyncGroups;
         const unsigned int my = blockIdx.x % G;
         const unsigned int members = nblocks / G + (my < nblocks % G ? 1u : 0u);
-        const unsigned int g = ld_acquire_u32(&gs->gen);
         __threadfence();
-        bool release = false;
-        if (atomicAdd(&gs->group[my * 32], 1u) == members - 1) {
-            atomicExch(&gs->group[my * 32], 0u);
+        const unsigned int old = atomicAdd(&gs->group[my * 32], 1u);
+        const unsigned int epoch = old / members;
+        const unsigned int target = (epoch + 1u) * G;
+        if (old == (epoch + 1u) * members - 1u) {
             __threadfence();
-            if (atomicAdd(&gs->count, 1u) == G - 1) {
-                atomicExch(&gs->count, 0u);
-                __threadfence();
-                atomicAdd(&gs->gen, 1u);
-                release = true;
-            }
+            atomicAdd(&gs->count, 1u);
         }
-        if (!release) {
-            const unsigned long long t0 = global_ns();
-            while (ld_acquire_u32(&gs->gen) == g) {
-                if (ld_relaxed_s32(&gs->err) != 0) break;
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicCAS(&gs->err, 0, HJB_ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire_u32(&gs->count) < target) {
+            if (ld_relaxed_s32(&gs->err) != 0) break;
+            if (global_ns() - t0 > timeout_ns) {
+                atomicCAS(&gs->err, 0, HJB_ERR_TIMEOUT);
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
     }
