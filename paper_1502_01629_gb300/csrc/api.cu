@@ -116,7 +116,7 @@ void pfree(T*& ptr, cudaStream_t st) {
 // slots shared by the problems (cudaMallocHost / cudaFreeHost per problem cost
 // a page pinning each); past the slab, a plain pinned allocation.
 constexpr int kPinnedSlots = 128;
-constexpr size_t kPinnedSlot = 1024;
+constexpr size_t kPinnedSlot = 4096;
 std::mutex g_pin_mu;
 unsigned char* g_pin_slab = nullptr;
 bool g_pin_used[kPinnedSlots] = {};
@@ -392,6 +392,8 @@ struct Scalars {
     WaveResult wave;
     GridSync sync;
 };
+
+static_assert(sizeof(Scalars) <= kPinnedSlot, "a problem's pinned scalars must fit one pinned slot");
 
 Scalars* dscal(hjb_problem* p) { return reinterpret_cast<Scalars*>(p->scratch); }
 Scalars* hscal(hjb_problem* p) { return reinterpret_cast<Scalars*>(p->host_pinned); }
