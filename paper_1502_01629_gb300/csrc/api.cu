@@ -98,17 +98,30 @@ cudaError_t problem_pool(cudaMemPool_t* out) {
     return cudaSuccess;
 }
 
-template <typename T>
-cudaError_t palloc(T** ptr, size_t bytes, cudaStream_t st) {
+}  // namespace
+
+namespace hjb {
+cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t st) {
     cudaMemPool_t pool;
     cudaError_t e = problem_pool(&pool);
     if (e != cudaSuccess) return e;
-    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, pool, st);
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+void pool_free(void* ptr, cudaStream_t st) {
+    if (ptr) cudaFreeAsync(ptr, st);
+}
+}  // namespace hjb
+
+namespace {
+
+template <typename T>
+cudaError_t palloc(T** ptr, size_t bytes, cudaStream_t st) {
+    return hjb::pool_alloc(reinterpret_cast<void**>(ptr), bytes, st);
 }
 
 template <typename T>
 void pfree(T*& ptr, cudaStream_t st) {
-    if (ptr) cudaFreeAsync((void*)ptr, st);
+    hjb::pool_free((void*)ptr, st);
     ptr = nullptr;
 }
 

@@ -562,12 +562,12 @@ int bfail(int code, const char* fmt, ...) {
     } while (0)
 
 template <typename T>
-cudaError_t dalloc(T*& p, size_t count) {
-    return cudaMalloc((void**)&p, std::max<size_t>(count, 1) * sizeof(T));
+cudaError_t dalloc(T*& p, size_t count, cudaStream_t st) {
+    return pool_alloc((void**)&p, std::max<size_t>(count, 1) * sizeof(T), st);
 }
 template <typename T>
-void dfree(T*& p) {
-    if (p) cudaFree((void*)p);
+void dfree(T*& p, cudaStream_t st) {
+    pool_free((void*)p, st);
     p = nullptr;
 }
 
@@ -737,24 +737,24 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     BCUP(cudaGetDevice(&dev));
     BCUP(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t N = (size_t)b->N, Nc = (size_t)b->Nc;
-    BCUP(dalloc(b->speed, N));
-    BCUP(dalloc(b->mask, N));
-    BCUP(dalloc(b->sector, N));
-    BCUP(dalloc(b->u32, N));
-    BCUP(dalloc(b->u32b, N));
-    BCUP(dalloc(b->u64, N));
-    BCUP(dalloc(b->uhat, N));
-    BCUP(dalloc(b->a, N));
-    BCUP(dalloc(b->key, N));
-    BCUP(dalloc(b->succ, N));
-    BCUP(dalloc(b->jump_a, N));
-    BCUP(dalloc(b->jump_b, N));
-    BCUP(dalloc(b->label, N));
-    BCUP(dalloc(b->speed_c, Nc));
-    BCUP(dalloc(b->mask_c, Nc));
-    BCUP(dalloc(b->uc, Nc));
-    BCUP(dalloc(b->ctrl32, na));
-    BCUP(dalloc(b->ctrl64, na));
+    BCUP(dalloc(b->speed, N, b->st));
+    BCUP(dalloc(b->mask, N, b->st));
+    BCUP(dalloc(b->sector, N, b->st));
+    BCUP(dalloc(b->u32, N, b->st));
+    BCUP(dalloc(b->u32b, N, b->st));
+    BCUP(dalloc(b->u64, N, b->st));
+    BCUP(dalloc(b->uhat, N, b->st));
+    BCUP(dalloc(b->a, N, b->st));
+    BCUP(dalloc(b->key, N, b->st));
+    BCUP(dalloc(b->succ, N, b->st));
+    BCUP(dalloc(b->jump_a, N, b->st));
+    BCUP(dalloc(b->jump_b, N, b->st));
+    BCUP(dalloc(b->label, N, b->st));
+    BCUP(dalloc(b->speed_c, Nc, b->st));
+    BCUP(dalloc(b->mask_c, Nc, b->st));
+    BCUP(dalloc(b->uc, Nc, b->st));
+    BCUP(dalloc(b->ctrl32, na, b->st));
+    BCUP(dalloc(b->ctrl64, na, b->st));
     BCUP(cudaMemcpyAsync(b->speed, speed, N * sizeof(float), cudaMemcpyHostToDevice, b->st));
     BCUP(cudaMemcpyAsync(b->mask, mask, N, cudaMemcpyHostToDevice, b->st));
     if (sector) {
@@ -769,7 +769,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         // per-instance checks and speed maxima on the device, after the upload
         // (the host never walks the concatenated arrays)
         constexpr int kScanBlocks = 64;
-        BCUP(dalloc(b->scan_tmp, (size_t)count * kScanBlocks + (size_t)count));
+        BCUP(dalloc(b->scan_tmp, (size_t)count * kScanBlocks + (size_t)count, b->st));
         InputScan* rec = b->scan_tmp;
         unsigned long long* bad = reinterpret_cast<unsigned long long*>(rec + (size_t)count * kScanBlocks);
         BCUP(cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long) * 4 * (size_t)count, b->st));
@@ -787,7 +787,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         BCUP(cudaMemcpyAsync(hb.data(), bad, sizeof(unsigned long long) * hb.size(), cudaMemcpyDeviceToHost,
                              b->st));
         BCUP(cudaStreamSynchronize(b->st));
-        dfree(b->scan_tmp);
+        dfree(b->scan_tmp, b->st);
         for (int i = 0; i < count; ++i) {
             unsigned flags = 0;
             for (int q = 0; q < nbk[i]; ++q) {
@@ -916,8 +916,8 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         nc_max = std::max(nc_max, nc);
     }
     b->nt_cap = nt_cap;
-    BCUP(dalloc(b->dinst, count));
-    BCUP(dalloc(b->dtile, count));
+    BCUP(dalloc(b->dinst, count, b->st));
+    BCUP(dalloc(b->dtile, count, b->st));
     BCUP(cudaMemcpyAsync(b->dinst, b->hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice,
                          b->st));
     // block tables
@@ -937,10 +937,10 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         b->nfblk = (int)fb.size();
         b->ncblk = (int)cbk.size();
         b->nrblk = (int)rb.size();
-        BCUP(dalloc(b->fblk, fb.size()));
-        BCUP(dalloc(b->cblk, cbk.size()));
-        BCUP(dalloc(b->rblk, rb.size()));
-        BCUP(dalloc(b->corder, count));
+        BCUP(dalloc(b->fblk, fb.size(), b->st));
+        BCUP(dalloc(b->cblk, cbk.size(), b->st));
+        BCUP(dalloc(b->rblk, rb.size(), b->st));
+        BCUP(dalloc(b->corder, count, b->st));
         BCUP(cudaMemcpyAsync(b->fblk, fb.data(), sizeof(int2) * fb.size(), cudaMemcpyHostToDevice, b->st));
         BCUP(cudaMemcpyAsync(b->cblk, cbk.data(), sizeof(int2) * cbk.size(), cudaMemcpyHostToDevice, b->st));
         BCUP(cudaMemcpyAsync(b->rblk, rb.data(), sizeof(int4) * rb.size(), cudaMemcpyHostToDevice, b->st));
@@ -949,43 +949,43 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     }
     // tiles, sized for the finest shape (4x4)
     const size_t ntc = (size_t)nt_cap;
-    BCUP(dalloc(b->tile_inst, ntc));
-    BCUP(dalloc(b->wt_nodes, ntc * kWarpTileNodes));
-    BCUP(dalloc(b->wt_speed, ntc * kWarpTileNodes));
-    BCUP(dalloc(b->wt_count, ntc));
-    BCUP(dalloc(b->tile_min, ntc));
-    BCUP(dalloc(b->tile_wave, ntc));
-    BCUP(dalloc(b->tile_key, ntc));
-    BCUP(dalloc(b->tile_list, ntc));
-    BCUP(dalloc(b->tile_inc, ntc));
-    BCUP(dalloc(b->stamp, ntc));
-    BCUP(dalloc(b->queue, ntc * (size_t)(b->D + 2)));
-    BCUP(dalloc(b->cb_wave, ntc));
-    BCUP(dalloc(b->cb_key, ntc));
-    BCUP(dalloc(b->cb_list, ntc));
-    BCUP(dalloc(b->cb_off, 3));
-    BCUP(dalloc(b->cb_count, 2));
-    BCUP(dalloc(b->qcount, b->D + 2));
-    BCUP(dalloc(b->step_inc, 2 * b->D));
+    BCUP(dalloc(b->tile_inst, ntc, b->st));
+    BCUP(dalloc(b->wt_nodes, ntc * kWarpTileNodes, b->st));
+    BCUP(dalloc(b->wt_speed, ntc * kWarpTileNodes, b->st));
+    BCUP(dalloc(b->wt_count, ntc, b->st));
+    BCUP(dalloc(b->tile_min, ntc, b->st));
+    BCUP(dalloc(b->tile_wave, ntc, b->st));
+    BCUP(dalloc(b->tile_key, ntc, b->st));
+    BCUP(dalloc(b->tile_list, ntc, b->st));
+    BCUP(dalloc(b->tile_inc, ntc, b->st));
+    BCUP(dalloc(b->stamp, ntc, b->st));
+    BCUP(dalloc(b->queue, ntc * (size_t)(b->D + 2), b->st));
+    BCUP(dalloc(b->cb_wave, ntc, b->st));
+    BCUP(dalloc(b->cb_key, ntc, b->st));
+    BCUP(dalloc(b->cb_list, ntc, b->st));
+    BCUP(dalloc(b->cb_off, 3, b->st));
+    BCUP(dalloc(b->cb_count, 2, b->st));
+    BCUP(dalloc(b->qcount, b->D + 2, b->st));
+    BCUP(dalloc(b->step_inc, 2 * b->D, b->st));
     // per-instance scalars
-    BCUP(dalloc(b->max_key, count));
-    BCUP(dalloc(b->c_sweeps, count));
-    BCUP(dalloc(b->c_inc, count));
-    BCUP(dalloc(b->res_bits, count));
-    BCUP(dalloc(b->margin, count));
-    BCUP(dalloc(b->active, count));
-    BCUP(dalloc(b->inc_bits, count));
-    BCUP(dalloc(b->j_sweeps, count));
-    BCUP(dalloc(b->n_active, 1));
-    BCUP(dalloc(b->rank_boff, count + 1));
-    BCUP(dalloc(b->d_coarse_off, count + 1));
-    BCUP(dalloc(b->c_fallback, count));
+    BCUP(dalloc(b->max_key, count, b->st));
+    BCUP(dalloc(b->c_sweeps, count, b->st));
+    BCUP(dalloc(b->c_inc, count, b->st));
+    BCUP(dalloc(b->res_bits, count, b->st));
+    BCUP(dalloc(b->margin, count, b->st));
+    BCUP(dalloc(b->active, count, b->st));
+    BCUP(dalloc(b->inc_bits, count, b->st));
+    BCUP(dalloc(b->j_sweeps, count, b->st));
+    BCUP(dalloc(b->n_active, 1, b->st));
+    BCUP(dalloc(b->rank_boff, count + 1, b->st));
+    BCUP(dalloc(b->d_coarse_off, count + 1, b->st));
+    BCUP(dalloc(b->c_fallback, count, b->st));
     BCUP(cudaMemsetAsync(b->c_fallback, 0, count, b->st));
     BCUP(cudaMemcpyAsync(b->d_coarse_off, b->coarse_off.data(), sizeof(long long) * (count + 1),
                          cudaMemcpyHostToDevice, b->st));
-    BCUP(dalloc(b->n_waves_dev, 1));
-    BCUP(dalloc(b->sync, 1));
-    BCUP(dalloc(b->wres, 1));
+    BCUP(dalloc(b->n_waves_dev, 1, b->st));
+    BCUP(dalloc(b->sync, 1, b->st));
+    BCUP(dalloc(b->wres, 1, b->st));
     BCUP(cudaMallocHost((void**)&b->h_wres, sizeof(WaveResult)));
     BCUP(cudaMemcpyAsync(b->margin, hmargin.data(), sizeof(float) * count, cudaMemcpyHostToDevice, b->st));
     // coarse data (inputs are fixed)
@@ -1003,7 +1003,8 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         b->n_free.assign(count, 0);
         b->n_free_c.assign(count, 0);
         std::vector<uint8_t> mc((size_t)b->Nc);
-        BCUP(cudaMemcpy(mc.data(), b->mask_c, (size_t)b->Nc, cudaMemcpyDeviceToHost));
+        BCUP(cudaMemcpyAsync(mc.data(), b->mask_c, (size_t)b->Nc, cudaMemcpyDeviceToHost, b->st));
+        BCUP(cudaStreamSynchronize(b->st));
         for (int i = 0; i < count; ++i) {
             for (long long k = b->node_off[i]; k < b->node_off[i + 1]; ++k) b->n_free[i] += mask[k] == 0;
             for (long long k = b->coarse_off[i]; k < b->coarse_off[i + 1]; ++k) b->n_free_c[i] += mc[k] == 0;
@@ -1017,21 +1018,21 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
 void hjb_batch_destroy(hjb_batch* b) {
     if (!b) return;
     b->pre_graph.reset();
-    dfree(b->scan_tmp);
+    dfree(b->scan_tmp, b->st);
     if (b->st) cudaStreamSynchronize(b->st);
-    dfree(b->dinst); dfree(b->dtile);
-    dfree(b->speed); dfree(b->mask); dfree(b->sector); dfree(b->u32); dfree(b->u32b); dfree(b->u64);
-    dfree(b->uhat); dfree(b->a); dfree(b->key); dfree(b->succ); dfree(b->jump_a); dfree(b->jump_b);
-    dfree(b->label); dfree(b->speed_c); dfree(b->mask_c); dfree(b->uc); dfree(b->ctrl32); dfree(b->ctrl64);
-    dfree(b->fblk); dfree(b->cblk); dfree(b->rblk); dfree(b->corder);
-    dfree(b->tile_inst); dfree(b->wt_nodes); dfree(b->wt_speed); dfree(b->wt_count); dfree(b->tile_min);
-    dfree(b->tile_wave); dfree(b->tile_key); dfree(b->tile_list); dfree(b->tile_inc); dfree(b->stamp);
-    dfree(b->queue); dfree(b->qcount); dfree(b->step_inc); dfree(b->sched_count); dfree(b->sched_off);
-    dfree(b->max_key); dfree(b->c_sweeps); dfree(b->c_inc); dfree(b->res_bits); dfree(b->margin);
-    dfree(b->active); dfree(b->inc_bits); dfree(b->j_sweeps); dfree(b->n_active); dfree(b->sync);
-    dfree(b->coarse_init); dfree(b->d_coarse_off); dfree(b->c_fallback);
-    dfree(b->cb_wave); dfree(b->cb_key); dfree(b->cb_list); dfree(b->cb_off); dfree(b->cb_count);
-    dfree(b->wres); dfree(b->rank_flags); dfree(b->rank_scan); dfree(b->rank_boff); dfree(b->n_waves_dev);
+    dfree(b->dinst, b->st); dfree(b->dtile, b->st);
+    dfree(b->speed, b->st); dfree(b->mask, b->st); dfree(b->sector, b->st); dfree(b->u32, b->st); dfree(b->u32b, b->st); dfree(b->u64, b->st);
+    dfree(b->uhat, b->st); dfree(b->a, b->st); dfree(b->key, b->st); dfree(b->succ, b->st); dfree(b->jump_a, b->st); dfree(b->jump_b, b->st);
+    dfree(b->label, b->st); dfree(b->speed_c, b->st); dfree(b->mask_c, b->st); dfree(b->uc, b->st); dfree(b->ctrl32, b->st); dfree(b->ctrl64, b->st);
+    dfree(b->fblk, b->st); dfree(b->cblk, b->st); dfree(b->rblk, b->st); dfree(b->corder, b->st);
+    dfree(b->tile_inst, b->st); dfree(b->wt_nodes, b->st); dfree(b->wt_speed, b->st); dfree(b->wt_count, b->st); dfree(b->tile_min, b->st);
+    dfree(b->tile_wave, b->st); dfree(b->tile_key, b->st); dfree(b->tile_list, b->st); dfree(b->tile_inc, b->st); dfree(b->stamp, b->st);
+    dfree(b->queue, b->st); dfree(b->qcount, b->st); dfree(b->step_inc, b->st); dfree(b->sched_count, b->st); dfree(b->sched_off, b->st);
+    dfree(b->max_key, b->st); dfree(b->c_sweeps, b->st); dfree(b->c_inc, b->st); dfree(b->res_bits, b->st); dfree(b->margin, b->st);
+    dfree(b->active, b->st); dfree(b->inc_bits, b->st); dfree(b->j_sweeps, b->st); dfree(b->n_active, b->st); dfree(b->sync, b->st);
+    dfree(b->coarse_init, b->st); dfree(b->d_coarse_off, b->st); dfree(b->c_fallback, b->st);
+    dfree(b->cb_wave, b->st); dfree(b->cb_key, b->st); dfree(b->cb_list, b->st); dfree(b->cb_off, b->st); dfree(b->cb_count, b->st);
+    dfree(b->wres, b->st); dfree(b->rank_flags, b->st); dfree(b->rank_scan, b->st); dfree(b->rank_boff, b->st); dfree(b->n_waves_dev, b->st);
     if (b->h_wres) cudaFreeHost(b->h_wres);
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     delete b;
@@ -1117,10 +1118,10 @@ int stage_tiles(hjb_batch* b) {
     for (int i = 0; i < b->count; ++i) boff[i + 1] = boff[i] + std::max(mk[i], 0) + 1;
     const int S = boff[b->count];
     if (S + 1 > b->rank_cap) {
-        dfree(b->rank_flags);
-        dfree(b->rank_scan);
-        BCU(dalloc(b->rank_flags, (size_t)S + 1));
-        BCU(dalloc(b->rank_scan, (size_t)S + 1));
+        dfree(b->rank_flags, b->st);
+        dfree(b->rank_scan, b->st);
+        BCU(dalloc(b->rank_flags, (size_t)S + 1, b->st));
+        BCU(dalloc(b->rank_scan, (size_t)S + 1, b->st));
         b->rank_cap = S + 1;
     }
     BCU(cudaMemcpyAsync(b->rank_boff, boff.data(), sizeof(int32_t) * (b->count + 1), cudaMemcpyHostToDevice,
@@ -1132,10 +1133,10 @@ int stage_tiles(hjb_batch* b) {
     BCU(cudaStreamSynchronize(b->st));
     b->n_waves = std::max(1, nw);
     if (b->n_waves > b->sched_cap) {
-        dfree(b->sched_count);
-        dfree(b->sched_off);
-        BCU(dalloc(b->sched_count, b->n_waves));
-        BCU(dalloc(b->sched_off, b->n_waves + 1));
+        dfree(b->sched_count, b->st);
+        dfree(b->sched_off, b->st);
+        BCU(dalloc(b->sched_count, b->n_waves, b->st));
+        BCU(dalloc(b->sched_off, b->n_waves + 1, b->st));
         b->sched_cap = b->n_waves;
     }
     BCU(launch_counting_sort(b->NT, b->tile_key, b->n_waves, b->sched_count, b->sched_off, b->tile_list,
@@ -1616,12 +1617,13 @@ int hjb_batch_coarse_warm(hjb_batch* b, const float* net_out, int32_t first, int
     const int nc = same_coarse_size(b);
     if (!nc) return bfail(HJB_ERR_INVALID_ARG, "instances have different coarse sizes");
     if (!b->coarse_init) {
-        BCU(dalloc(b->coarse_init, (size_t)b->Nc));
+        BCU(dalloc(b->coarse_init, (size_t)b->Nc, b->st));
         // instances without a prediction keep the plain start
         std::vector<float> plain((size_t)b->Nc);
         for (int i = 0; i < b->count; ++i)
             for (long long k = b->coarse_off[i]; k < b->coarse_off[i + 1]; ++k) plain[k] = b->hinst[i].uc0;
-        BCU(cudaMemcpy(b->coarse_init, plain.data(), sizeof(float) * plain.size(), cudaMemcpyHostToDevice));
+        BCU(cudaMemcpyAsync(b->coarse_init, plain.data(), sizeof(float) * plain.size(), cudaMemcpyHostToDevice,
+                            b->st));
     }
     count_launches(1);
     k_b_warm_values<<<b->ncblk, kBT, 0, b->st>>>(b->dinst, b->cblk, nc, net_out, first, count, b->d_coarse_off,
@@ -1646,8 +1648,10 @@ int hjb_batch_coarse_solve(hjb_batch* b, double tol_c, int32_t max_sweeps, hjb_s
     int rc = stage_coarse(b, tol_c, max_sweeps, &nodes, &conv);
     if (rc) return rc;
     const double ms = t.stop();
-    if (sweeps_out) BCU(cudaMemcpy(sweeps_out, b->c_sweeps, sizeof(int) * b->count, cudaMemcpyDeviceToHost));
-    if (fallback_out) BCU(cudaMemcpy(fallback_out, b->c_fallback, b->count, cudaMemcpyDeviceToHost));
+    if (sweeps_out)
+        BCU(cudaMemcpyAsync(sweeps_out, b->c_sweeps, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->st));
+    if (fallback_out) BCU(cudaMemcpyAsync(fallback_out, b->c_fallback, b->count, cudaMemcpyDeviceToHost, b->st));
+    BCU(cudaStreamSynchronize(b->st));
     rc = conv ? HJB_OK : HJB_ERR_NOT_CONVERGED;
     if (stats) {
         stats->node_updates = nodes;

@@ -11,6 +11,11 @@
 
 namespace hjb {
 
+// Stream-ordered device memory from the library's pool (one per device; freed
+// blocks stay cached for later allocations, hjb_trim_memory releases them).
+cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t st);
+void pool_free(void* ptr, cudaStream_t st);
+
 // Number of kernels this library has launched (all threads), for reporting.
 void count_launches(long long k);
 long long launches();
