@@ -1,7 +1,7 @@
 """FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
 
 A plain, slow, single-threaded restatement of the paper's scheme and
-pre-computation (Cacace & Falcone, Sections 3-4), used to judge the CUDA
+pre-computation (Cacace & Falcone, Sections 3-4), used to check the CUDA
 solver.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import it; the solver package never does, and the two
 share no code (inputs come from ``hjb_inputs``).

@@ -210,7 +210,7 @@ double orc_node_update(const orc_problem *P, const double *u, int64_t k, int sch
 }
 
 /* Every control's candidate value at free node k (the quantities the min of
- * eq. SLscheme2 / SLscheme3 compares), vals[m] for m < N_A.  Used to judge
+ * eq. SLscheme2 / SLscheme3 compares), vals[m] for m < N_A.  Used to decide
  * whether a minimiser chosen elsewhere is a valid one at a near-tie. */
 void orc_node_candidates(const orc_problem *P, const double *u, int64_t k, int scheme,
                          double *vals)
@@ -414,7 +414,7 @@ void orc_synthesis(const orc_problem *P, const double *uhat, uint8_t *a_out)
 }
 
 /* The synthesis objective beta u_hat(foot) + h l(x, a) for every control at the
- * listed nodes: vals[t*N_A + m].  Used to judge near-ties. */
+ * listed nodes: vals[t*N_A + m].  Used to decide near-ties. */
 void orc_synthesis_values(const orc_problem *P, const double *uhat, const int64_t *nodes,
                           int64_t n_nodes, double *vals)
 {

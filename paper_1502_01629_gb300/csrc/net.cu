@@ -2,7 +2,7 @@
 // (32 channels, BF16 weights and activations, FP32 accumulation) that maps a
 // coarse instance (speed, target mask, obstacle mask, sigma, lambda) to the
 // coarse value and the feedback control index.  The coarse solve of Section 4.3
-// stays the judge: the prediction only replaces its initial value, and a plain
+// has the last word: the prediction only replaces its initial value, and a plain
 // start is restored when the value after K sweeps still moves by more than a
 // threshold, so the fixed point is unchanged and only the sweep count moves.
 //

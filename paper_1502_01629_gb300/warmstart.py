@@ -5,7 +5,7 @@ start.
 The network (``Net``) maps an instance's coarse grid (speed, target, obstacles,
 sigma, lambda) to its coarse value and feedback control; its value channel
 replaces the large constant the coarse solve of Section 4.3 starts from.  The
-coarse solve stays the judge: it runs to the same tolerance from the predicted
+coarse solve has the last word: it runs to the same tolerance from the predicted
 start (falling back to the plain start when the prediction is far off), so the
 fixed point is the same and only the sweep count changes.
 
