@@ -498,3 +498,24 @@ def test_device_pointer_inputs_match_host_inputs():
     with pytest.raises(HJBError) as e:
         Problem(inst.n, inst.controls, bad, mk, sec, device_inputs=True, **kw)
     assert "speed[17]" in str(e.value)
+
+
+def test_pool_memory_is_reused_and_trimmed():
+    """Problems draw device memory from the library's stream-ordered pool: many
+    create / destroy cycles do not grow the device's used memory beyond one
+    problem's share, and hjb_trim_memory returns the cached blocks."""
+    from paper_1502_01629_gb300 import Problem, lib
+    inst = hi.patchy_1025(0.0, n=257, coarse_n=33)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(6):
+        with Problem.from_instance(inst) as P:
+            P.coarse_solve(tol_c=1e-6)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    one = 200 * inst.n * inst.n                      # well above a problem's ~70 B/node
+    assert free0 - free1 <= one + (64 << 20), (free0 - free1)
+    assert lib().hjb_trim_memory() == 0
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 >= free1
