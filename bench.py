@@ -58,7 +58,7 @@ BATCH_COUNT = 512
 # workload, mean of the three launches of a step, from one ncu capture of this
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum); None for the other
 # workloads (not captured)
-WTILES_DRAM_BYTES_1025 = 14.32e6
+WTILES_DRAM_BYTES_1025 = 14.22e6
 
 
 def flops_per_node_control(sigma: float) -> int:
