@@ -62,12 +62,6 @@ namespace {
     } while (0)
 
 
-template <typename T>
-void dfree(T*& p) {
-    if (p) cudaFree((void*)p);
-    p = nullptr;
-}
-
 // Device memory of the problems comes from one stream-ordered pool per device
 // that keeps freed blocks (release threshold: unlimited): creating and
 // destroying a problem then costs no device-wide synchronisation and almost no
