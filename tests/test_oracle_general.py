@@ -291,3 +291,21 @@ def test_table2_zermelo_trends():
     assert pdd[0] < pdd[2] < pdd[3], pdd
     assert all(p < d for p, d in res), res
     assert res[-1][0] / res[-1][1] > res[0][0] / res[0][1], res
+
+
+def test_synthesis_takes_the_cheapest_control_on_a_flat_field():
+    """Eq. discrete-synthesis with l(x, a) = l(x) + m(a): when u_hat is constant every
+    foot interpolates the same value, so the feedback is the control of least
+    m(a) (ties to the lowest index) on every free node, whatever l(x)."""
+    n = 33
+    inst = hi.general_instance(n, 1, 3)
+    P = _problem(inst)
+    uhat = np.full(n * n, 0.4)
+    a = P.synthesis(uhat)
+    mvals = np.abs(inst.controls[:, 0] / (2.0 + inst.controls[:, 1]))
+    free = inst.mask == hi.MASK_FREE
+    assert (a[free] == int(np.argmin(mvals))).all()
+    assert (a[~free] == 255).all()
+    # without the control cost every control ties and the lowest index wins
+    b = _problem(inst, control_cost=None).synthesis(uhat)
+    assert (b[free] == 0).all()
