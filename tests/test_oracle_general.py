@@ -294,13 +294,15 @@ def test_table2_zermelo_trends():
 
 
 def test_synthesis_takes_the_cheapest_control_on_a_flat_field():
-    """Eq. discrete-synthesis with l(x, a) = l(x) + m(a): when u_hat is constant every
-    foot interpolates the same value, so the feedback is the control of least
-    m(a) (ties to the lowest index) on every free node, whatever l(x)."""
+    """Eq. discrete-synthesis with l(x, a) = l(x) + m(a): when u_hat vanishes every
+    foot interpolates exactly 0, so the feedback is the control of least m(a)
+    (ties to the lowest index) on every free node, whatever l(x).  (A nonzero
+    constant would be interpolated with rounding noise of the weights, which
+    would decide ties between equal costs.)"""
     n = 33
     inst = hi.general_instance(n, 1, 3)
     P = _problem(inst)
-    uhat = np.full(n * n, 0.4)
+    uhat = np.zeros(n * n)
     a = P.synthesis(uhat)
     mvals = np.abs(inst.controls[:, 0] / (2.0 + inst.controls[:, 1]))
     free = inst.mask == hi.MASK_FREE
