@@ -183,6 +183,34 @@ WORKLOAD_DESC = {
 }
 
 
+def workload_config(insts, ws):
+    """The `config` of a patchy1025 / large4097 line (both arms)."""
+    return {
+        "workload": WORKLOAD_DESC[WORKLOAD],
+        "n": N_FINE, "coarse_n": N_COARSE, "n_patches": insts[0].n_patches,
+        "n_controls": insts[0].n_controls,
+        "sigmas": [i.sigma for i in insts], "tol32": TOL32, "tol64_residual": TOL64,
+        "solver": SOLVER_KW,
+        "l2": ("flushed between timed steps (256 MiB write); working set < L2"
+               if WORKLOAD == "patchy1025" else
+               "flushed between timed steps (256 MiB write); working set > L2"),
+        "parallelism": f"replicas x{ws}",
+    }
+
+
+def batched_config(insts, n_free, ws):
+    """The `config` of a batched512 line (both arms; the GPU arm adds its autotune)."""
+    return {
+        "workload": f"batched {BATCH_COUNT} instances, n=8k+1 in 65..513, random Fourier speed "
+                    "in [0.2,1.8], 1-3 discs r 0.05-0.15, sigma~U[0,0.1], lambda~U[0.5,2], "
+                    "32 controls, 4-16 patches, coarse (n-1)/4+1, FP32 passes + FP64 residual <= 1e-6",
+        "instances": BATCH_COUNT, "nodes": sum(i.n * i.n for i in insts), "free_nodes": n_free,
+        "tol32": TOL32, "tol64_residual": TOL64,
+        "l2": "flushed between timed steps (256 MiB write); working set > L2",
+        "parallelism": f"replicas x{ws}",
+    }
+
+
 def make_instances():
     """(label, instance) pairs of one step."""
     if WORKLOAD == "large4097":
@@ -344,17 +372,7 @@ def ours(args, ws, rank, local):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {
-            "workload": WORKLOAD_DESC[WORKLOAD],
-            "n": N_FINE, "coarse_n": N_COARSE, "n_patches": insts[0].n_patches,
-            "n_controls": insts[0].n_controls,
-            "sigmas": [i.sigma for i in insts], "tol32": TOL32, "tol64_residual": TOL64,
-            "solver": SOLVER_KW,
-            "l2": ("flushed between timed steps (256 MiB write); working set < L2"
-                   if WORKLOAD == "patchy1025" else
-                   "flushed between timed steps (256 MiB write); working set > L2"),
-            "parallelism": f"replicas x{ws}",
-        },
+        "config": workload_config(insts, ws),
         "time_to_1e-6_ms": {
             "patchy": {str(s): patchy_ms[s] for s in labels},
             "plain_jacobi_fp32": {str(s): plain[s]["ms"] for s in labels},
@@ -501,15 +519,7 @@ def ours_batched(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {
-            "workload": f"batched {BATCH_COUNT} instances, n=8k+1 in 65..513, random Fourier speed "
-                        "in [0.2,1.8], 1-3 discs r 0.05-0.15, sigma~U[0,0.1], lambda~U[0.5,2], "
-                        "32 controls, 4-16 patches, coarse (n-1)/4+1, FP32 passes + FP64 residual <= 1e-6",
-            "instances": BATCH_COUNT, "nodes": sum(i.n * i.n for i in insts), "free_nodes": n_free,
-            "tol32": TOL32, "tol64_residual": TOL64, "autotune": tune,
-            "l2": "flushed between timed steps (256 MiB write); working set > L2",
-            "parallelism": f"replicas x{ws}",
-        },
+        "config": dict(batched_config(insts, n_free, ws), autotune=tune),
         "time_to_1e-6_ms": {"patchy_batch": patchy, "plain_jacobi_fp32_batch": plain,
                             "speedup_vs_plain": plain / patchy},
         "solver_stats": {"steps": st["fp32_passes"], "node_updates": st["node_updates"],
@@ -561,31 +571,48 @@ def cpu_baseline(seconds: float, inst=None) -> dict:
 
 
 def reference(args, ws, rank, local):
-    """Reference arm: the FP64 oracle on the host cores, one bounded sample per step."""
+    """Reference arm: the FP64 oracle on the host cores, one bounded sample of the
+    selected workload per step (Gauss-Seidel updates of a block of nodes)."""
     if rank != 0:
         return None
     import oracle
-    inst = hi.patchy_1025(0.02, n=N_FINE, coarse_n=N_COARSE, n_patches=N_PATCH)
-    O = oracle.Problem.from_instance(inst)
-    u = O.fix_nonfree(np.zeros(O.N))
-    nfree = int((inst.mask == 0).sum())
-    # each step: a bounded block of rows of one Gauss-Seidel sweep (1/8 of the grid)
-    rows = np.arange(0, O.N // 8, dtype=np.int64)
-    for _ in range(args.warmup):
+    if WORKLOAD == "batched512":
+        insts = [hi.batched_instance(1000 + k) for k in range(BATCH_COUNT)]
+        n_free = sum(int((i.mask == 0).sum()) for i in insts)
+        config = batched_config(insts, n_free, ws)
+        # step k: one full sweep of instance k (about 0.1-0.7 s each)
+        plan = [(insts[k % BATCH_COUNT], None) for k in range(args.warmup + args.steps)]
+        what = "a full Gauss-Seidel sweep of one instance per step (instances 0, 1, ...)"
+    else:
+        insts = [inst for _, inst in make_instances()]
+        config = workload_config(insts, ws)
+        frac = 8 if WORKLOAD == "patchy1025" else 64
+        # step k: the first 1/frac of the nodes of instance k mod (number of instances)
+        plan = [(insts[k % len(insts)], frac) for k in range(args.warmup + args.steps)]
+        what = (f"each step: Gauss-Seidel update of the first 1/{frac} of the nodes of one "
+                f"instance (sigma cycling through {[i.sigma for i in insts]})")
+    problems, values = {}, {}
+    nodes = 0
+    dt = 0.0
+    for k, (inst, frac) in enumerate(plan):
+        key = id(inst)
+        if key not in problems:
+            O = oracle.Problem.from_instance(inst)
+            problems[key] = O
+            values[key] = O.fix_nonfree(np.zeros(O.N))
+        O, u = problems[key], values[key]
+        rows = np.arange(0, O.N // frac if frac else O.N, dtype=np.int64)
+        t0 = time.perf_counter()
         O.sweep_gs(u, 3, rows)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.sweep_gs(u, 3, rows)
-    dt = time.perf_counter() - t0
-    nodes = int((inst.mask[rows] == 0).sum())
-    val = nodes * inst.n_controls * args.steps / dt
-    sample = (f"each step: Gauss-Seidel update of the first {rows.size} nodes (1/8 of the grid) "
-              f"of the 1025^2 sigma=0.02 instance, FP64 oracle, 1 core")
+        if k >= args.warmup:
+            dt += time.perf_counter() - t0
+            nodes += int((inst.mask[rows] == 0).sum()) * inst.n_controls
+    val = nodes / dt if dt > 0 else 0.0
+    sample = f"{what}, FP64 oracle, 1 core"
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "patchy 1025x1025 sigma=0.02 (oracle sample)", "n": N_FINE},
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
