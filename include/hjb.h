@@ -208,10 +208,13 @@ int hjb_create_problem_device(const hjb_desc* desc, const float* speed, const ui
 
 /* hjb_coarse_solve -- Section 4.3 "Pre-computation", first item: starting from
  * u_c^0 = l(1/lambda + h) off the target (the paper's "very big value"), iterate
- * SLscheme3 with sigma = 0 on G_c (whole-grid in-place sweeps in one cooperative
- * launch, a warp per node -- the paper's "standard (static) domain decomposition"
- * of the coarse solve taken to one node per warp) until the sup-increment of a
- * sweep is <= tol_c.  G_c is
+ * SLscheme3 with sigma = 0 on G_c (one cooperative launch: each block keeps a
+ * tile of G_c resident and relaxes it in place, a warp per node, between grid
+ * barriers -- the paper's "standard (static) domain decomposition" of the coarse
+ * solve with one tile per SM) until the sup-increment of the first relaxation
+ * after each exchange is <= tol_c (raised to the FP32 floor of the values; without
+ * a discount the floor follows the largest value).  stats->sweeps counts global
+ * sweeps (each with 4 local relaxations).  G_c is
  * nested in G: coarse node (I,J) is fine node (rI, rJ), r = (n-1)/(coarse_n-1);
  * its speed is the fine speed there; it is a target when a fine target node lies
  * within r/2 fine cells in both axes, else an obstacle when its fine node is one.
