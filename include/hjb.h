@@ -259,10 +259,14 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
  * (band waves): band_group bands per grid-wide wave, nodes taken in sorted order
  * by the wave_warps warps in flight; passes after the first skip groups whose
  * neighbourhood did not change.  FP32 until a
- * pass's sup-increment is <= tol32; then, if tol64 > 0, the FP64 sup-residual
+ * pass's sup-increment is <= tol32 (raised to the FP32 floor
+ * 1.01 * 2^-23 * max(1, U) * A, where U bounds the values -- l/lambda + h l, or
+ * without a discount four times the largest coarse value -- and A >= 1 is the
+ * 1 / (1 - beta Lambda0) amplification of the scheme, about dx / (h mean|f|));
+ * then, if tol64 > 0, the FP64 sup-residual
  * ||T2 u - u|| is evaluated; if it exceeds tol64 while tol64 is at least 2^-22
- * max(1, u_max), at most two more FP32 phases run from the current value with
- * the tolerance divided by 4 each time while it stays >= 2^-21 max(1, u_max)
+ * max(1, U) A, at most two more FP32 phases run from the current value with
+ * the tolerance divided by 4 each time while it stays >= 2^-21 max(1, U) A
  * (schedule 0, every tile visited in the first two steps in checkerboard
  * order); then FP64 passes until the FP64
  * sup-residual is <= tol64.  max_passes caps each phase.
