@@ -22,7 +22,7 @@ import numpy as np
 from ._lib import (HJB_ERR_NOT_CONVERGED, HJB_OK, BatchDesc, BatchInst, Desc, HJBError, RegimeInfo, Terms,
                    Stats, check, header_functions, lib)
 
-__all__ = ["Problem", "Batch", "Net", "HJBError", "regime", "kernel_launches", "lib", "header_functions",
+__all__ = ["Problem", "Batch", "Net", "HJBError", "regime", "kernel_launches", "lib", "header_functions", "trim_memory",
            "HJB_ERR_NOT_CONVERGED"]
 
 
@@ -47,8 +47,22 @@ def regime(dx: float, f_min: float, f_max: float, eps: float) -> dict:
     return {f: getattr(out, f) for f, _ in out._fields_}
 
 
+def trim_memory() -> None:
+    """Return the device memory the library's pool keeps cached from destroyed
+    problems and batches (``hjb_trim_memory``)."""
+    check(lib().hjb_trim_memory(), "hjb_trim_memory")
+
+
 class Problem:
-    """One problem instance on the GPU (wraps an ``hjb_problem*``)."""
+    """One problem instance on the GPU (wraps an ``hjb_problem*``).
+
+    The data follow ``hjb_inputs.Instance``: n nodes per side on [-1, 1]^2, the
+    control set, speed c(x), mask (0 free, 1 target, 2 obstacle), the boundary
+    sectors, and the discretisation knobs (h, lam, sigma, cost, coarse grid, patch
+    schedule).  ``sigma_field``, ``diffusion``, ``cost_field`` and ``control_cost``
+    select the general terms of Section 5.3 (``hjb_create_problem_general``);
+    ``device_inputs=True`` takes torch CUDA tensors (or raw device pointers) for
+    the per-node arrays (``hjb_create_problem_device``)."""
 
     def __init__(self, n: int, controls: np.ndarray, speed: np.ndarray, mask: np.ndarray,
                  sector: Optional[np.ndarray] = None, *, h: float = 0.0, lam: float = 1.0,
