@@ -341,13 +341,20 @@ int hjb_device_info(hjb_problem* p, int32_t* num_sms, int32_t* wave_blocks32,
  * memory is wholly owned by another allocator (a caching pool, a fixed budget).
  *   desc     : host; uses n, n_controls, h, lambda, sigma, cost (no coarse grid).
  *   speed, mask, drift (nullable), u : DEVICE arrays with the layouts of
- *              hjb_create_problem (u: double[n*n]); controls: DEVICE double[2*n_controls]
- *              (16-byte aligned); residual_out: DEVICE double[1] (written by the call).
+ *              hjb_create_problem (u: double[n*n], 8-byte aligned; drift 8-byte
+ *              aligned); controls: DEVICE double[2*n_controls] (16-byte aligned);
+ *              residual_out: DEVICE double[1] (written by the call).
+ *              u is read at free nodes only: target nodes count as 0 and obstacle
+ *              nodes as h l/(1 - beta) (1e6 when lambda = 0), the values the
+ *              solver holds there, whatever u contains at those nodes.
+ *              A non-finite increment at any free node (NaN or Inf in u, or in
+ *              the inputs it meets) makes *residual_out = +Inf.
  *   cuda_stream: the stream the work is queued on (NULL: the legacy default stream);
  *              the call returns before the result is ready.
  * Scratch: one partial maximum per 32x16-node tile, held in a fixed device array of
  * 65536 doubles (512 KiB) that every GPU loading the library keeps until exit; grids
- * with more tiles (n above 5760 in general) are rejected with HJB_ERR_INVALID_ARG.
+ * with more tiles, ceil(n/32) * ceil(n/16) > 65536 (n >= 5793), are rejected with
+ * HJB_ERR_INVALID_ARG before any device work.
  * Every call overwrites the partials it reads, so nothing needs clearing, but all
  * calls share the one array: calls whose work overlaps on the GPU race.  The first
  * call on a device resolves the array's device address (cudaGetSymbolAddress) with
@@ -455,6 +462,12 @@ int hjb_batch_autotune(hjb_batch* b, double tol_c, double tol32, int32_t* shape_
 
 /* hjb_batch_get_value -- instance `index`'s current value (n*n doubles). */
 int hjb_batch_get_value(const hjb_batch* b, int32_t index, double* u_out);
+
+/* hjb_batch_get_values -- every instance's current value in one read-back:
+ * u_out (host, caller-owned) holds sum_i n_i^2 doubles, instance i's n_i x n_i
+ * field (the layout of hjb_create_problem) starting after those of instances
+ * 0 .. i-1.  One device-to-host copy and one stream synchronisation. */
+int hjb_batch_get_values(const hjb_batch* b, double* u_out);
 
 /* hjb_batch_get_feedback / hjb_batch_get_labels -- instance `index`'s a*
  * (255 on non-free nodes) and patch labels after a solve. */

@@ -208,7 +208,7 @@ struct hjb_problem {
     double dx = 0, h = 0, beta = 0, hl = 0, uob = 0, sigma = 0, lambda = 0;
     double reach = 0;     // max |h f| / dx + d, cells
     int halo = 1;
-    int halo_c = 1;       // coarse grid: reach without the diffusion (R7), same h/dx
+    int halo_c = 1;       // coarse grid: reach without the diffusion (Section 4: the coarse solve is first order), same h/dx
     RelaxArgs relax_plan{};   // coarse relaxation tiles (tw, th, ntx, halo)
     int relax_blocks = 0;
     GraphCache labels_graph;  // successors + label rounds (fixed buffers)
@@ -230,7 +230,7 @@ struct hjb_problem {
     double amp32 = 1.0;            // FP32 noise amplification 1/D of SLscheme3 (>= 1)
     double uc_max = 0;             // largest coarse value (set by hjb_coarse_solve)
 
-    // FP32 tolerance floor: half an ulp of the largest value (R17), times the
+    // FP32 tolerance floor: half an ulp of the largest value (an FP32 iteration cannot settle finer), times the
     // amplification 1/(1 - beta Lambda0) of eq. SLscheme3, which divides the
     // rounding of the numerator by the foot's distance from the node in cells
     double floor32(double U) const { return fp32_tol_floor(U) * amp32; }

@@ -54,13 +54,23 @@ k_residual_partials(GridView g, const double* __restrict__ u, double* partials) 
             bx = (double)b.x;
             by = (double)b.y;
         }
+        // non-free vertices take the scheme's fixed values (0 on the target, the
+        // obstacle value on obstacles) whatever the caller's array holds there
         const double* base = u + k;
-        auto U = [&](int dx, int dy) { return __ldg(base + (ptrdiff_t)dy * n + dx); };
+        const uint8_t* mbase = g.mask + k;
+        auto U = [&](int dx, int dy) {
+            const ptrdiff_t o = (ptrdiff_t)dy * n + dx;
+            const uint8_t m = __ldg(mbase + o);
+            return m == kFree ? __ldg(base + o) : (m == kTarget ? 0.0 : g.uob64);
+        };
         auto C = [&](int m) { return g.ctrl64[m]; };
         double N, D;
         int M;
         best_over_controls<double, SIG>(g, 2, i, j, uk, c, bx, by, 0, 1, C, U, N, D, M);
-        lmax = fmax(lmax, fabs(N / D));
+        // a NaN increment (non-finite values in u or in the inputs) makes the
+        // residual +infinity: fmax alone would drop it
+        const double inc = fabs(N / D);
+        lmax = inc == inc ? fmax(lmax, inc) : INFINITY;
     }
     const double bm = block_max<double>(lmax, red);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = bm;
@@ -70,7 +80,10 @@ __global__ void __launch_bounds__(1024) k_max_partials(const double* partials, i
                                                        double* out) {
     __shared__ double red[32];
     double m = 0.0;
-    for (int t = threadIdx.x; t < count; t += blockDim.x) m = fmax(m, partials[t]);
+    for (int t = threadIdx.x; t < count; t += blockDim.x) {
+        const double p = partials[t];
+        m = p == p ? fmax(m, p) : INFINITY;
+    }
     const double bm = block_max<double>(m, red);
     if (threadIdx.x == 0) *out = bm;
 }

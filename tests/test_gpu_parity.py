@@ -320,7 +320,7 @@ def test_large_recipe_matches_oracle():
         np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)
         u = G.get_value()
     assert np.all(u[inst.mask == hi.MASK_TARGET] == 0.0)
-    # obstacle nodes hold l/lambda + h l (R16); the two sides round the formula
+    # obstacle nodes hold l/lambda + h l (obstacles as a penalty: never updated, the largest value); the two sides round the formula
     # differently in the last place
     np.testing.assert_allclose(u[inst.mask == hi.MASK_OBSTACLE], O.u_max, rtol=0, atol=1e-12)
 
@@ -378,7 +378,7 @@ def test_large_workload_full_size_sampled():
         worst = max(worst, abs(v - u[k]))
     assert worst <= st["residual"] * (1 + 1e-9) + 1e-15, (worst, st["residual"])
     assert u.min() >= 0.0 and u.max() <= O.u_max * (1 + 1e-12)
-    # obstacle nodes hold l/lambda + h l (R16); the two sides round the formula
+    # obstacle nodes hold l/lambda + h l (obstacles as a penalty: never updated, the largest value); the two sides round the formula
     # differently in the last place
     np.testing.assert_allclose(u[inst.mask == hi.MASK_OBSTACLE], O.u_max, rtol=0, atol=1e-12)
 
