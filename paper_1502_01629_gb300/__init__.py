@@ -351,6 +351,14 @@ class Batch:
         check(lib().hjb_batch_get_value(self._h, index, _p(out)), "hjb_batch_get_value")
         return out
 
+    def get_values(self) -> list:
+        """Every instance's value from one read-back (``hjb_batch_get_values``): a
+        list of n_i^2 arrays, views of one buffer."""
+        sizes = [n * n for n in self.ns]
+        out = np.empty(sum(sizes))
+        check(lib().hjb_batch_get_values(self._h, _p(out)), "hjb_batch_get_values")
+        return np.split(out, np.cumsum(sizes)[:-1])
+
     def get_feedback(self, index: int) -> np.ndarray:
         out = np.empty(self.ns[index] ** 2, np.uint8)
         check(lib().hjb_batch_get_feedback(self._h, index, _p(out)), "hjb_batch_get_feedback")

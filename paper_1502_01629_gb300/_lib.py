@@ -122,6 +122,7 @@ _SIGNATURES = {
     "hjb_batch_solve_full": (ctypes.c_int, [_P, _D, _D, _I32, ctypes.POINTER(Stats), _PTR]),
     "hjb_batch_autotune": (ctypes.c_int, [_P, _D, _D, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _PTR]),
     "hjb_batch_get_value": (ctypes.c_int, [_P, _I32, _PTR]),
+    "hjb_batch_get_values": (ctypes.c_int, [_P, _PTR]),
     "hjb_batch_get_feedback": (ctypes.c_int, [_P, _I32, _PTR]),
     "hjb_batch_get_labels": (ctypes.c_int, [_P, _I32, _PTR]),
     "hjb_batch_get_uhat": (ctypes.c_int, [_P, _I32, _PTR]),

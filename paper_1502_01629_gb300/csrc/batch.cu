@@ -1547,6 +1547,22 @@ int hjb_batch_get_value(const hjb_batch* b, int32_t index, double* u_out) {
     return HJB_OK;
 }
 
+int hjb_batch_get_values(const hjb_batch* b, double* u_out) {
+    clear_last_error();
+    if (!b || !u_out) return bfail(HJB_ERR_INVALID_ARG, "NULL argument");
+    const long long n = b->node_off[b->count];
+    if (b->value_f64) {
+        BCU(cudaMemcpyAsync(u_out, b->u64, sizeof(double) * n, cudaMemcpyDeviceToHost, b->st));
+        BCU(cudaStreamSynchronize(b->st));
+    } else {
+        std::vector<float> h(n);
+        BCU(cudaMemcpyAsync(h.data(), b->u32, sizeof(float) * n, cudaMemcpyDeviceToHost, b->st));
+        BCU(cudaStreamSynchronize(b->st));
+        for (long long k = 0; k < n; ++k) u_out[k] = h[k];
+    }
+    return HJB_OK;
+}
+
 int hjb_batch_get_feedback(const hjb_batch* b, int32_t index, uint8_t* a_out) {
     clear_last_error();
     if (!b || !a_out) return bfail(HJB_ERR_INVALID_ARG, "NULL argument");
