@@ -533,26 +533,44 @@ int32_t orc_labels(int32_t n, const int32_t *succ, const uint8_t *mask, const in
 }
 
 /* Causal band of each free node (Section 4.2: nodes are processed by
- * increasing u_hat).  The value is mapped to the travel-time scale
+ * increasing u_hat).  Bands are intervals of the travel-time scale
  * T(u) = -log(1 - lambda u)/lambda (T = u when lambda = 0), on which one
- * characteristic step costs about h, and the band is floor(T / width), capped
- * at n_bands-1; lambda*u is clipped to [0, 1 - 1e-6].  keys = -1 on non-free nodes. */
+ * characteristic step costs about h: band k holds T in [k w, (k+1) w).  With
+ * lambda > 0 the band edges are taken on the value scale,
+ * e_k = T^{-1}(k w) = (1 - exp(-(lambda (k w)))) / lambda for k = 1 .. L-1 with
+ * L = min(n_bands, floor(log(1e6) / (lambda w)) + 2) (travel times beyond
+ * log(1e6)/lambda, i.e. lambda u > 1 - 1e-6, share the last band), and the key of
+ * u is the number of edges <= u, an exact comparison of u with FP64 edges; with
+ * lambda = 0 the key is floor(u / w), capped at n_bands - 1.  u < 0 counts as 0.
+ * keys = -1 on non-free nodes. */
 void orc_band_keys(int64_t N, const double *uhat, const uint8_t *mask, double lambda,
                    double width, int32_t n_bands, int32_t *keys)
 {
+    int64_t L = 0;
+    double *edge = NULL;
+    if (lambda > 0.0) {
+        const double span = floor(log(1e6) / (lambda * width));
+        L = span + 2.0 < (double)n_bands ? (int64_t)span + 2 : n_bands;
+        edge = (double *)malloc((size_t)L * sizeof(double));
+        edge[0] = 0.0;
+        for (int64_t k = 1; k < L; k++)
+            edge[k] = (1.0 - exp(-(lambda * ((double)k * width)))) / lambda;
+    }
     for (int64_t k = 0; k < N; k++) {
         if (mask[k] != MASK_FREE) { keys[k] = -1; continue; }
-        double u = uhat[k] < 0.0 ? 0.0 : uhat[k];
-        double T;
+        const double u = uhat[k] < 0.0 ? 0.0 : uhat[k];
         if (lambda > 0.0) {
-            double lu = lambda * u;
-            if (lu > 1.0 - 1e-6) lu = 1.0 - 1e-6;
-            T = -log(1.0 - lu) / lambda;
+            /* number of edges e_1 .. e_{L-1} that are <= u (binary search) */
+            int64_t lo = 0, hi = L - 1;       /* answer in [lo, hi] */
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo + 1) / 2;
+                if (edge[mid] <= u) lo = mid; else hi = mid - 1;
+            }
+            keys[k] = (int32_t)lo;
         } else {
-            T = u;
+            const double b = floor(u / width);
+            keys[k] = b >= (double)(n_bands - 1) ? n_bands - 1 : (int32_t)b;
         }
-        double b = floor(T / width);
-        if (b > n_bands - 1) b = n_bands - 1;
-        keys[k] = (int32_t)b;
     }
+    free(edge);
 }

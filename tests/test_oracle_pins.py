@@ -496,6 +496,31 @@ def test_band_keys_follow_travel_time():
     np.testing.assert_array_equal(keys0, np.minimum(b, 49))
 
 
+def test_band_keys_exact_at_the_edges():
+    """The band edges are the values whose travel time is a multiple of the width,
+    e_k = T^{-1}(k w) = (1 - exp(-lambda k w))/lambda (here from Python's math
+    module): a value equal to an edge opens band k, the float just below it is in
+    band k-1, values past log(1e6)/lambda of travel time share the last band, and
+    away from the edges the key is floor(T(u)/w) with T from log1p."""
+    import math
+    lam, w = 0.8, 2.0 / 1024
+    mask = np.zeros(1, np.uint8)
+    key = lambda u: int(oracle.band_keys(np.array([u]), mask, lam, w, 1 << 20)[0])
+    for k in (1, 2, 7, 100, 1234, 5000):
+        e = (1.0 - math.exp(-(lam * (float(k) * w)))) / lam
+        assert key(e) == k
+        assert key(np.nextafter(e, 0.0)) == k - 1
+        mid = (1.0 - math.exp(-(lam * ((k + 0.5) * w)))) / lam
+        assert key(mid) == k == math.floor(-math.log1p(-lam * mid) / lam / w)
+    L = math.floor(math.log(1e6) / (lam * w)) + 2
+    assert key(1.0 / lam) == L - 1
+    assert key(10.0) == L - 1
+    assert key(-0.5) == 0
+    # no discount: floor(u / w), capped
+    k0 = oracle.band_keys(np.array([0.0, 2.5 * w, 99.99 * w, 1e9]), np.zeros(4, np.uint8), 0.0, w, 100)
+    np.testing.assert_array_equal(k0, [0, 2, 99, 99])
+
+
 def test_argmin_ties_go_to_lowest_control():
     """Duplicated controls give exactly tied candidates in the min of eq. SLscheme3 and
     of eq. discrete-synthesis; the tie goes to the lowest index (a reading: the paper
