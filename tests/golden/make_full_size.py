@@ -1,0 +1,108 @@
+#!/usr/bin/env python3
+"""Write the full-size oracle solutions the value-gate tests compare against.
+
+Calls only ``oracle/`` (the FP64 CPU oracle) and the seeded input generators of
+``hjb_inputs``; nothing here touches the CUDA solver.
+
+    python tests/golden/make_full_size.py patchy1025    # three files, one per sigma
+    python tests/golden/make_full_size.py large4097     # sampled nodes only
+
+What is solved: the fixed point u* of eq. SLscheme3 (Section 3; the same fixed
+point as eq. SLscheme2 by the Section 3 proof) on the workload's grid, by the
+oracle's Gauss-Seidel value iteration in increasing u_hat (Section 4.3: the
+nodes ordered by the interpolated coarse solution; the order changes the speed
+only), started from u_hat and stopped at a sup-increment <= 1e-13.  For
+Gauss-Seidel of a beta-contraction the error after a sweep whose increment is
+d is at most d beta / (1 - beta): 5e-11 at 1025^2, 2e-10 at 4097^2.
+
+Stored per workload and sigma (``tests/golden/<name>.npz``):
+  u32        -- u* rounded to float32, every node (1025^2 only): enough for the
+                FP32 gate 1e-5 max(1, |u|) (rounding 6e-8 |u|);
+  idx, u64   -- a seeded sample of free nodes and u* there in float64, for the
+                1e-10 gate after the FP64 polish;
+  sum64      -- sum of u* over all nodes in float64 (a checksum of the file);
+  sweeps, last_increment, residual -- the oracle's own convergence record
+                (residual = ||T2 u - u|| over the free nodes, eq. SLscheme2).
+"""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+TOL = 1e-13
+SIGMAS_1025 = (0.0, 0.02, 0.1)
+N_SAMPLES = {"patchy1025": 8192, "large4097": 65536}
+
+
+def golden_path(name: str) -> str:
+    return os.path.join(HERE, name + ".npz")
+
+
+def patchy1025_name(sigma: float) -> str:
+    return f"patchy1025_sigma{sigma:g}"
+
+
+def large4097_name() -> str:
+    return "large4097_sigma0.01"
+
+
+def sample_nodes(mask: np.ndarray, count: int, seed: int = 20260) -> np.ndarray:
+    """A seeded sorted sample of free nodes (mask 0)."""
+    free = np.flatnonzero(mask == 0)
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    return np.sort(rng.choice(free, size=min(count, free.size), replace=False)).astype(np.int64)
+
+
+def solve_one(job):
+    workload, sigma = job
+    import hjb_inputs as hi
+    import oracle
+    if workload == "patchy1025":
+        inst = hi.patchy_1025(sigma)
+        name = patchy1025_name(sigma)
+    else:
+        inst = hi.large_instance()
+        name = large4097_name()
+    t0 = time.time()
+    pre = oracle.patchy_precompute(inst, tol_c=1e-10)
+    O = pre["fine"]
+    order = np.argsort(pre["uhat"], kind="stable")
+    u, sweeps, last = O.solve(u0=O.fix_nonfree(pre["uhat"]), scheme=3, method="gs",
+                              order=order, tol=TOL, max_sweeps=200000)
+    if sweeps < 0:
+        raise RuntimeError(f"{name}: the oracle did not reach {TOL}")
+    res = O.residual(u)
+    idx = sample_nodes(inst.mask, N_SAMPLES[workload])
+    out = dict(idx=idx, u64=u[idx], sum64=np.float64(u.sum()), sweeps=np.int64(sweeps),
+               last_increment=np.float64(last), residual=np.float64(res),
+               n=np.int64(inst.n), sigma=np.float64(inst.sigma))
+    if workload == "patchy1025":
+        out["u32"] = u.astype(np.float32)
+    np.savez_compressed(golden_path(name), **out)
+    return f"{name}: {sweeps} sweeps, last increment {last:.2e}, residual {res:.2e}, {time.time() - t0:.0f} s"
+
+
+def main(argv):
+    which = argv[1] if len(argv) > 1 else "patchy1025"
+    if which == "patchy1025":
+        jobs = [("patchy1025", s) for s in SIGMAS_1025]
+    elif which == "large4097":
+        jobs = [("large4097", 0.01)]
+    else:
+        raise SystemExit("usage: make_full_size.py patchy1025|large4097")
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        for line in pool.imap_unordered(solve_one, jobs):
+            print(line, flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv)
