@@ -98,7 +98,11 @@ typedef struct {
     int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (8x8 when the
                              diffusion offset exceeds one cell, n > 2049 or more than 32
                              controls, else 8x4)                                              */
-    int32_t reserved;     /* must be 0                                                        */
+    int32_t visit;        /* warp tiles, FP32: how a warp updates a tile's nodes: 1 one node
+                             at a time (a control per lane, warp minimum, Gauss-Seidel through
+                             the tile), 2 32 nodes at a time (a node per lane, every control
+                             in the lane), 0 automatic (2 when the diffusion offset
+                             sqrt(2h) sigma exceeds one cell, else 1)                         */
 } hjb_desc;
 
 /* Per-call statistics; every field is written by the call that receives it. */
@@ -237,6 +241,18 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
  * ms_stage: [0] interpolation, [1] synthesis + band keys, [2] successors + labels,
  * [3] ordering.  Errors: HJB_ERR_STATE (coarse_solve not run). */
 int hjb_build_patches(hjb_problem* p, hjb_stats* stats);
+
+/* hjb_set_uhat -- replace u_hat by the caller's host float[n*n] (finite values on
+ * free nodes; the fixed values are taken elsewhere) and redo what follows it in
+ * Section 4.3 "Pre-computation": the synthesis a* (eq. discrete-synthesis) with
+ * the causal band keys of Section 4.2, successors, labels, ordering, tiles, and
+ * the start value u = u_hat.  Lets a caller (a test) run the pre-computation on a
+ * u_hat computed elsewhere.  Band key of a value u (exact, FP64): with lambda > 0
+ * the number of edges e_k = (1 - exp(-(lambda (k w)))) / lambda, k = 1 .. L-1,
+ * that are <= u, with w = band_width h and L = min(2^20, floor(log(1e6)/(lambda w))
+ * + 2); with lambda = 0, floor(u / w).  Requires build_patches.
+ * Errors: HJB_ERR_INVALID_ARG (NULL, non-finite value), HJB_ERR_STATE. */
+int hjb_set_uhat(hjb_problem* p, const float* uhat);
 
 /* hjb_set_feedback -- replace a* by the caller's host uint8[n*n] (values < N_A on
  * free nodes, ignored elsewhere) and recompute successors, labels and ordering

@@ -70,7 +70,7 @@ class Problem:
                  scheme: int = 3, band_width: float = 1.0, band_window: int = 8,
                  band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
                  schedule: int = 0, tile_waves: int = 0, tile_period: int = 2,
-                 local_sweeps: int = 1, tile_shape: int = -1,
+                 local_sweeps: int = 1, tile_shape: int = -1, visit: int = 0,
                  drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False,
                  sigma_field: Optional[np.ndarray] = None, diffusion: int = 0,
                  cost_field: Optional[np.ndarray] = None,
@@ -91,6 +91,7 @@ class Problem:
         d.schedule, d.tile_waves, d.tile_period = int(schedule), int(tile_waves), int(tile_period)
         d.local_sweeps = int(local_sweeps)
         d.tile_shape = int(tile_shape)
+        d.visit = int(visit)
         self.desc = d
         st = None
         if stream is not None:
@@ -179,6 +180,11 @@ class Problem:
         st = Stats()
         check(lib().hjb_build_patches(self._h, ctypes.byref(st)), "hjb_build_patches")
         return st.as_dict()
+
+    def set_uhat(self, uhat: np.ndarray) -> None:
+        """Replace u_hat (``hjb_set_uhat``) and redo the pre-computation after it."""
+        uhat = _c(uhat, np.float32).reshape(-1)
+        check(lib().hjb_set_uhat(self._h, _p(uhat)), "hjb_set_uhat")
 
     def set_feedback(self, a: np.ndarray) -> None:
         a = _c(a, np.uint8).reshape(-1)

@@ -33,7 +33,7 @@ class Desc(ctypes.Structure):
                 ("resort_passes", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("tile_waves", ctypes.c_int32), ("tile_period", ctypes.c_int32),
                 ("local_sweeps", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("visit", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -96,6 +96,7 @@ _SIGNATURES = {
     "hjb_coarse_solve": (ctypes.c_int, [_P, _D, _I32, ctypes.POINTER(Stats)]),
     "hjb_build_patches": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "hjb_set_feedback": (ctypes.c_int, [_P, _PTR]),
+    "hjb_set_uhat": (ctypes.c_int, [_P, _PTR]),
     "hjb_solve_patches": (ctypes.c_int, [_P, _D, _D, _I32, ctypes.POINTER(Stats)]),
     "hjb_solve_full": (ctypes.c_int, [_P, _I32, _D, _D, _I32, ctypes.POINTER(Stats)]),
     "hjb_apply_operator": (ctypes.c_int, [_P, _I32, _I32, _PTR, _PTR, _PTR]),

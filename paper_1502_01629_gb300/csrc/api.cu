@@ -266,6 +266,8 @@ struct hjb_problem {
     int32_t* bin_count = nullptr;
     int32_t* bin_off = nullptr;
     int32_t* band_off = nullptr;
+    double* band_e = nullptr;     // band edges (FP64), band_L entries
+    int band_L = 0;
     unsigned int* inc_bits = nullptr;
     int n_bands = 0, n_free = 0, bins_cap = 0, bands_cap = 0;
     // tile schedule
@@ -334,6 +336,17 @@ struct hjb_problem {
         g.du64 = du;
         g.h32 = (float)hh;
         g.h64 = hh;
+    }
+
+    BandMap band_map() const {
+        BandMap b{};
+        b.lambda = (float)lambda;
+        b.w64 = desc.band_width * h;
+        b.w32 = (float)b.w64;
+        b.edges = band_e;
+        b.n_edges = band_L;
+        b.cap = kBandCap;
+        return b;
     }
 
     GridView fine_view() const {
@@ -427,7 +440,8 @@ int validate_desc(const hjb_desc* d) {
     if (d->schedule < 0 || d->schedule > 2) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0, 1 or 2");
     if (d->tile_shape < -1 || d->tile_shape > 2)
         return fail(HJB_ERR_INVALID_ARG, "tile_shape must be -1 (auto), 0 (8x8), 1 (8x4) or 2 (4x4)");
-    if (d->reserved != 0) return fail(HJB_ERR_INVALID_ARG, "reserved field must be 0");
+    if (d->visit < 0 || d->visit > 2)
+        return fail(HJB_ERR_INVALID_ARG, "visit must be 0 (auto), 1 (a node at a time) or 2 (32 nodes at a time)");
     return HJB_OK;
 }
 
@@ -610,6 +624,9 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         const bool big = desc->n > 2049 || desc->n_controls > 32;
         if (p->desc.tile_shape < 0) p->desc.tile_shape = (wide || big) ? 0 : 1;
         if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
+        // a wide diffusion reaches past the tile's own nodes, so ordering them
+        // within a visit gains little: update 32 of them at a time
+        if (p->desc.visit == 0) p->desc.visit = wide ? 2 : 1;
     }
     p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
     if (p->desc.schedule != 1 && p->desc.coarse_n > 0 &&
@@ -658,6 +675,17 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     CUP(cudaMemsetAsync(p->scratch, 0, sizeof(Scalars), p->st));
     CUP(pinned_alloc(&p->host_pinned, sizeof(Scalars)));
     CUP(launch_init_values(p->N, p->mask, 0.0f, (float)p->uob, p->u32, p->u64, p->uob, p->st));
+    {
+        // band edges of the causal ordering (exact keys, see band_key)
+        std::vector<double> e;
+        band_edges(p->lambda, p->desc.band_width * p->h, kBandCap, e);
+        p->band_L = (int)e.size();
+        if (p->band_L > 0) {
+            CUP(palloc(&p->band_e, e.size() * sizeof(double), p->st));
+            CUP(cudaMemcpyAsync(p->band_e, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                p->st));
+        }
+    }
 
     if (desc->coarse_n > 0) {
         const int nc = desc->coarse_n;
@@ -1068,6 +1096,16 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.n_waves = n_waves;
     a.period = D;
     a.local_sweeps = p->desc.local_sweeps;
+    a.node_lanes = p->desc.visit == 2 ? 1 : 0;
+    {
+        // the self weight of eq. self-dependency is zero for every candidate when
+        // each diffusion point lies more than a cell from the node: offset d
+        // beyond 1 + the drift's reach (interior tiles; the projection can pull
+        // points back next to nodes at the edge).  Scheme 2 keeps it in the sum.
+        const double dcell = std::sqrt(2.0 * p->h) * p->sigma / p->dx;
+        const double drift_cells = p->reach - dcell;
+        a.no_self = p->desc.scheme == 2 ? 2 : (p->sigma > 0.0 && dcell >= 1.0 + drift_cells + 1e-3 ? 1 : 0);
+    }
     a.max_steps = n_waves + max_passes * D;
     a.tol = (float)tol;
     a.sync = &ds->sync;
@@ -1113,9 +1151,7 @@ int run_phase(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
 int resort_by_value(hjb_problem* p) {
     Scalars* ds = dscal(p);
     CU(cudaMemsetAsync(&ds->max_key, 0, sizeof(int), p->st));
-    CU(launch_keys_from_values(p->N, p->mask, p->u32, (float)p->lambda,
-                               (float)(p->desc.band_width * p->h), kBandCap, p->key, &ds->max_key,
-                               p->st));
+    CU(launch_keys_from_values(p->N, p->mask, p->u32, p->band_map(), p->key, &ds->max_key, p->st));
     CU(cudaMemcpyAsync(&hscal(p)->max_key, &ds->max_key, sizeof(int), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
     p->n_bands = hscal(p)->max_key + 1;
@@ -1231,7 +1267,7 @@ void hjb_destroy(hjb_problem* p) {
     pfree(p->hmc32, p->st); pfree(p->hmc64, p->st);
     pfree(p->uhat, p->st); pfree(p->a, p->st); pfree(p->succ, p->st); pfree(p->jump_a, p->st); pfree(p->jump_b, p->st);
     pfree(p->label, p->st); pfree(p->key, p->st); pfree(p->order, p->st); pfree(p->bin_count, p->st); pfree(p->bin_off, p->st);
-    pfree(p->band_off, p->st); pfree(p->inc_bits, p->st); pfree(p->inc_hist32, p->st); pfree(p->inc_hist64, p->st);
+    pfree(p->band_off, p->st); pfree(p->band_e, p->st); pfree(p->inc_bits, p->st); pfree(p->inc_hist32, p->st); pfree(p->inc_hist64, p->st);
     pfree(p->tile_min, p->st); pfree(p->tile_wave, p->st); pfree(p->tile_key, p->st); pfree(p->tile_list, p->st);
     pfree(p->tile_inc, p->st); pfree(p->tile_key2, p->st); pfree(p->tile_nodes, p->st); pfree(p->tile_bin_count, p->st);
     pfree(p->tile_bin_off, p->st); pfree(p->wt_nodes, p->st); pfree(p->wt_count, p->st); pfree(p->wt_speed, p->st);
@@ -1323,21 +1359,15 @@ int hjb_coarse_solve(hjb_problem* p, double tol_c, int32_t max_sweeps, hjb_stats
     return rc;
 }
 
-int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
-    g_last_error.clear();
-    clear_stats(stats);
-    if (!p) return fail(HJB_ERR_INVALID_ARG, "problem is NULL");
-    if (!p->coarse_done) return fail(HJB_ERR_STATE, "hjb_coarse_solve has not run");
-    Timer tm(p->st);
+namespace {
+
+// The pre-computation that follows u_hat (Section 4.3): synthesis a* with the
+// band keys, successors, labels, ordering, tiles, and the start value u = u_hat.
+int precompute_from_uhat(hjb_problem* p, Timer& tm) {
     Scalars* ds = dscal(p);
     const GridView g = p->fine_view();
-    tm.mark();
-    CU(launch_interp(p->nc, p->uc, p->n, p->mask, (float)p->uob, p->uhat, p->st));
-    tm.mark();
     CU(cudaMemsetAsync(&ds->max_key, 0, sizeof(int), p->st));
-    const double band_w = p->desc.band_width * p->h;
-    CU(launch_synthesis(g, p->uhat, (float)p->lambda, (float)band_w, kBandCap, p->a, p->key,
-                        &ds->max_key, p->st));
+    CU(launch_synthesis(g, p->uhat, p->band_map(), p->a, p->key, &ds->max_key, p->st));
     CU(cudaMemcpyAsync(&hscal(p)->max_key, &ds->max_key, sizeof(int), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
     tm.mark();
@@ -1357,6 +1387,22 @@ int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
     CU(cudaStreamSynchronize(p->st));
     p->n_free = nfree;
     p->built = true;
+    return HJB_OK;
+}
+
+}  // namespace
+
+int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
+    g_last_error.clear();
+    clear_stats(stats);
+    if (!p) return fail(HJB_ERR_INVALID_ARG, "problem is NULL");
+    if (!p->coarse_done) return fail(HJB_ERR_STATE, "hjb_coarse_solve has not run");
+    Timer tm(p->st);
+    tm.mark();
+    CU(launch_interp(p->nc, p->uc, p->n, p->mask, (float)p->uob, p->uhat, p->st));
+    tm.mark();
+    const int rc = precompute_from_uhat(p, tm);
+    if (rc) return rc;
     if (stats) {
         stats->ms_stage[0] = tm.ms(0, 1);
         stats->ms_stage[1] = tm.ms(1, 2);
@@ -1366,6 +1412,27 @@ int hjb_build_patches(hjb_problem* p, hjb_stats* stats) {
         stats->status = HJB_OK;
     }
     return HJB_OK;
+}
+
+int hjb_set_uhat(hjb_problem* p, const float* uhat) {
+    g_last_error.clear();
+    if (!p || !uhat) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!p->built) return fail(HJB_ERR_STATE, "hjb_build_patches has not run");
+    std::vector<uint8_t> m(p->N);
+    CU(cudaMemcpyAsync(m.data(), p->mask, p->N, cudaMemcpyDeviceToHost, p->st));
+    CU(cudaStreamSynchronize(p->st));
+    std::vector<float> v(uhat, uhat + p->N);
+    for (int k = 0; k < p->N; ++k) {
+        if (m[k] == HJB_MASK_FREE) {
+            if (!std::isfinite(v[k])) return fail(HJB_ERR_INVALID_ARG, "uhat[%d] is not finite", k);
+        } else {
+            v[k] = m[k] == HJB_MASK_TARGET ? 0.0f : (float)p->uob;
+        }
+    }
+    CU(cudaMemcpyAsync(p->uhat, v.data(), sizeof(float) * p->N, cudaMemcpyHostToDevice, p->st));
+    Timer tm(p->st);
+    tm.mark();
+    return precompute_from_uhat(p, tm);
 }
 
 int hjb_set_feedback(hjb_problem* p, const uint8_t* a) {

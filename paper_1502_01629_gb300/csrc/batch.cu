@@ -47,6 +47,7 @@ struct BatchInst {
     int R;               // halo of the fine operator
     float lambda;        // band map
     float band_w;
+    BandMap bm;          // exact band keys (edges into the batch's edge array)
     float uc0;           // coarse initial value on free nodes: l/lambda + h_c l
     float uob32;         // value held on obstacle nodes
     float sigma;
@@ -95,7 +96,7 @@ __global__ void k_b_synthesis(const BatchInst* __restrict__ I, const int2* __res
         } else {
             auto C = [&](int m) { return sctrl[m]; };
             B.a[k] = (uint8_t)synthesis_node(g, k, B.uhat, C);
-            kk = band_of(B.uhat[k], B.lambda, B.band_w, band_cap);
+            kk = band_key(B.uhat[k], B.bm);
             B.key[k] = kk;
         }
     }
@@ -462,6 +463,7 @@ struct hjb_batch {
     float* u32 = nullptr;
     float* u32b = nullptr;
     double* u64 = nullptr;
+    double* band_e = nullptr;            // every instance's band edges, concatenated
     float* uhat = nullptr;
     uint8_t* a = nullptr;
     int32_t* key = nullptr;
@@ -824,6 +826,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     std::vector<long long> fcount(count), ccount(count);
     long long nt_cap = 0;
     int nc_max = 0;
+    std::vector<double> edges;
     for (int i = 0; i < count; ++i) {
         const hjb_batch_inst& x = insts[i];
         const int n = x.n, nc = x.coarse_n;
@@ -894,6 +897,17 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         B.R = R;
         B.lambda = (float)x.lambda;
         B.band_w = (float)(b->band_width * h);
+        {
+            std::vector<double> e;
+            band_edges(x.lambda, b->band_width * h, kBandCap, e);
+            B.bm.lambda = B.lambda;
+            B.bm.w64 = b->band_width * h;
+            B.bm.w32 = B.band_w;
+            B.bm.n_edges = (int)e.size();
+            B.bm.cap = kBandCap;
+            B.bm.edges = reinterpret_cast<const double*>((uintptr_t)edges.size());   // offset until upload
+            edges.insert(edges.end(), e.begin(), e.end());
+        }
         B.uc0 = (float)uob_c;
         B.uob32 = (float)uob;
         B.sigma = (float)x.sigma;
@@ -916,6 +930,13 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         nc_max = std::max(nc_max, nc);
     }
     b->nt_cap = nt_cap;
+    if (!edges.empty()) {
+        BCUP(dalloc(b->band_e, edges.size(), b->st));
+        BCUP(cudaMemcpyAsync(b->band_e, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice,
+                             b->st));
+    }
+    for (int i = 0; i < count; ++i)
+        b->hinst[i].bm.edges = b->band_e ? b->band_e + (uintptr_t)b->hinst[i].bm.edges : nullptr;
     BCUP(dalloc(b->dinst, count, b->st));
     BCUP(dalloc(b->dtile, count, b->st));
     BCUP(cudaMemcpyAsync(b->dinst, b->hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice,
@@ -1021,7 +1042,7 @@ void hjb_batch_destroy(hjb_batch* b) {
     dfree(b->scan_tmp, b->st);
     if (b->st) cudaStreamSynchronize(b->st);
     dfree(b->dinst, b->st); dfree(b->dtile, b->st);
-    dfree(b->speed, b->st); dfree(b->mask, b->st); dfree(b->sector, b->st); dfree(b->u32, b->st); dfree(b->u32b, b->st); dfree(b->u64, b->st);
+    dfree(b->speed, b->st); dfree(b->mask, b->st); dfree(b->sector, b->st); dfree(b->u32, b->st); dfree(b->u32b, b->st); dfree(b->u64, b->st); dfree(b->band_e, b->st);
     dfree(b->uhat, b->st); dfree(b->a, b->st); dfree(b->key, b->st); dfree(b->succ, b->st); dfree(b->jump_a, b->st); dfree(b->jump_b, b->st);
     dfree(b->label, b->st); dfree(b->speed_c, b->st); dfree(b->mask_c, b->st); dfree(b->uc, b->st); dfree(b->ctrl32, b->st); dfree(b->ctrl64, b->st);
     dfree(b->fblk, b->st); dfree(b->cblk, b->st); dfree(b->rblk, b->st); dfree(b->corder, b->st);

@@ -41,6 +41,17 @@ struct GridView {
     float h32;   double h64;     // h
 };
 
+// The causal band map of the ordering (Section 4.2): band edges in FP64 (see
+// band_key in precompute_device.cuh).
+struct BandMap {
+    float lambda;
+    float w32;             // band width w = band_width h, FP32 (the estimate)
+    double w64;            // the same in FP64
+    const double* edges;   // L entries, edges[0] = 0 (unused)
+    int n_edges;           // L (0 when lambda = 0)
+    int cap;               // keys are capped at cap - 1
+};
+
 template <typename T> struct RealOf;
 template <typename T> struct V2Of_;
 template <> struct V2Of_<float> { using type = float2; };

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cmath>
 #include <stdint.h>
+#include <vector>
 
 #include "hjb_device.cuh"
 
@@ -112,12 +113,16 @@ cudaError_t launch_coarse_data(int n, int nc, const float* speed, const float2* 
                                uint8_t* mask_c, cudaStream_t st);
 cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, float u_obst,
                           float* uhat, cudaStream_t st);
-cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda, float band_w,
-                             int band_cap, uint8_t* a, int32_t* key, int* max_key, cudaStream_t st);
+// Band edges of the causal ordering, host FP64: with lambda > 0,
+// e[k] = (1 - exp(-(lambda (k w)))) / lambda for k = 1 .. L-1 (e[0] = 0), where
+// L = min(cap, floor(log(1e6) / (lambda w)) + 2) (travel times up to log(1e6) /
+// lambda, lambda u <= 1 - 1e-6); empty when lambda = 0.
+void band_edges(double lambda, double w, int cap, std::vector<double>& e);
+cudaError_t launch_synthesis(const GridView& g, const float* uhat, const BandMap& bm, uint8_t* a,
+                             int32_t* key, int* max_key, cudaStream_t st);
 // Band key from the current value (re-sorting), same mapping as the synthesis.
-cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, float lambda,
-                                    float band_w, int band_cap, int32_t* key, int* max_key,
-                                    cudaStream_t st);
+cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, const BandMap& bm,
+                                    int32_t* key, int* max_key, cudaStream_t st);
 cudaError_t launch_successors(const GridView& g, const uint8_t* a, int32_t* succ, cudaStream_t st);
 cudaError_t launch_labels(int N, const int32_t* succ, const uint8_t* mask, const int8_t* sector,
                           int n_patches, int32_t* jump_a, int32_t* jump_b, int8_t* label,
@@ -270,6 +275,12 @@ struct TileArgs {
     int n_waves;
     int period;                // D
     int local_sweeps;
+    int node_lanes;            // warp tiles, FP32: 1 = 32 nodes at a time (a node per lane,
+                               // every control in the lane), 0 = one node at a time
+                               // (a control per lane, warp minimum)
+    int no_self;               // warp tiles, FP32: 2 = no candidate has a self weight (scheme 2),
+                               // 1 = none in interior tiles (diffusion offset > 1 + the drift's
+                               // reach in cells), 0 = compute it
     int max_steps;
     float tol;
     GridSync* sync;

@@ -36,8 +36,8 @@ __global__ void k_interp(int nc, const float* __restrict__ uc, int n,
 
 // Synthesis a* and the causal band key of every free node; the largest key is
 // folded into *max_key.
-__global__ void k_synthesis(GridView g, const float* __restrict__ uhat, float lambda, float band_w,
-                            int band_cap, uint8_t* a_out, int32_t* key, int* max_key) {
+__global__ void k_synthesis(GridView g, const float* __restrict__ uhat, BandMap bm, uint8_t* a_out,
+                            int32_t* key, int* max_key) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* sctrl = reinterpret_cast<float2*>(smem);
     const int n = g.n;
@@ -52,7 +52,7 @@ __global__ void k_synthesis(GridView g, const float* __restrict__ uhat, float la
         } else {
             auto C = [&](int m) { return sctrl[m]; };
             a_out[k] = (uint8_t)synthesis_node(g, k, uhat, C);
-            kk = band_of(uhat[k], lambda, band_w, band_cap);
+            kk = band_key(uhat[k], bm);
             key[k] = kk;
         }
     }
@@ -65,15 +65,15 @@ __global__ void k_synthesis(GridView g, const float* __restrict__ uhat, float la
 
 // Band key of the current value (same mapping as in k_synthesis).
 __global__ void k_keys_from_values(int N, const uint8_t* __restrict__ mask,
-                                   const float* __restrict__ u, float lambda, float band_w,
-                                   int band_cap, int32_t* key, int* max_key) {
+                                   const float* __restrict__ u, BandMap bm, int32_t* key,
+                                   int* max_key) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int kk = -1;
     if (k < N) {
         if (mask[k] != kFree) {
             key[k] = -1;
         } else {
-            kk = band_of(u[k], lambda, band_w, band_cap);
+            kk = band_key(u[k], bm);
             key[k] = kk;
         }
     }
@@ -228,21 +228,28 @@ cudaError_t launch_interp(int nc, const float* uc, int n, const uint8_t* mask, f
     return cudaGetLastError();
 }
 
-cudaError_t launch_synthesis(const GridView& g, const float* uhat, float lambda, float band_w,
-                             int band_cap, uint8_t* a, int32_t* key, int* max_key, cudaStream_t st) {
+void band_edges(double lambda, double w, int cap, std::vector<double>& e) {
+    e.clear();
+    if (!(lambda > 0.0)) return;
+    const double span = std::floor(std::log(1e6) / (lambda * w));
+    const int L = span + 2.0 < (double)cap ? (int)span + 2 : cap;
+    e.resize(L);
+    e[0] = 0.0;
+    for (int k = 1; k < L; ++k) e[k] = (1.0 - std::exp(-(lambda * ((double)k * w)))) / lambda;
+}
+
+cudaError_t launch_synthesis(const GridView& g, const float* uhat, const BandMap& bm, uint8_t* a,
+                             int32_t* key, int* max_key, cudaStream_t st) {
     const size_t smem = (size_t)g.na * sizeof(float2);
     count_launches(1);
-    k_synthesis<<<blocks_for((long long)g.n * g.n), kThreads, smem, st>>>(g, uhat, lambda, band_w,
-                                                                          band_cap, a, key, max_key);
+    k_synthesis<<<blocks_for((long long)g.n * g.n), kThreads, smem, st>>>(g, uhat, bm, a, key, max_key);
     return cudaGetLastError();
 }
 
-cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, float lambda,
-                                    float band_w, int band_cap, int32_t* key, int* max_key,
-                                    cudaStream_t st) {
+cudaError_t launch_keys_from_values(int N, const uint8_t* mask, const float* u, const BandMap& bm,
+                                    int32_t* key, int* max_key, cudaStream_t st) {
     count_launches(1);
-    k_keys_from_values<<<blocks_for(N), kThreads, 0, st>>>(N, mask, u, lambda, band_w, band_cap,
-                                                             key, max_key);
+    k_keys_from_values<<<blocks_for(N), kThreads, 0, st>>>(N, mask, u, bm, key, max_key);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,26 @@ __device__ __forceinline__ int band_of(float u, float lambda, float band_w, int 
     return min((int)floorf(T / band_w), band_cap - 1);
 }
 
+// The causal band key of a value, exactly: with lambda > 0 the band edges are
+// e_k = (1 - exp(-(lambda (k w)))) / lambda, k = 1 .. L-1 (the values whose travel
+// time T(u) = -log(1 - lambda u)/lambda is k w), computed in FP64 on the host;
+// the key of u is the number of edges <= u (the value widened to FP64, compared
+// exactly).  With lambda = 0 the key is floor(u / w) in FP64.  Capped at cap - 1.
+// The float estimate band_of starts the search, which then moves to the exact
+// count (edges are increasing, so it ends).
+__device__ __forceinline__ int band_key(float u, const BandMap& bm) {
+    u = fmaxf(u, 0.0f);
+    const double ud = (double)u;
+    if (bm.n_edges == 0) {
+        const double b = floor(ud / bm.w64);
+        return b >= (double)(bm.cap - 1) ? bm.cap - 1 : (int)b;
+    }
+    int k = min(band_of(u, bm.lambda, bm.w32, bm.cap), bm.n_edges - 1);
+    while (k + 1 < bm.n_edges && __ldg(bm.edges + k + 1) <= ud) ++k;
+    while (k > 0 && __ldg(bm.edges + k) > ud) --k;
+    return min(k, bm.cap - 1);
+}
+
 // Synthesis a*(x_i) = argmin_a beta u_hat(x_i + h f(x_i, a)) + h l (sigma = 0,
 // self vertex included, ties to the lowest index) at free node k = (i, j).
 template <typename CtrlFn>

@@ -199,7 +199,14 @@ k_tiles(TileArgs a, T* u) {
 // fractions and the reciprocal of the denominator D = 1 - beta L (scheme 3;
 // -1 marks an excluded candidate, D <= 0).  Split out so the geometry of the
 // next node can be formed while the current node's gathers, warp reduction and
-// store are in flight.  Same arithmetic as control_terms4 and candidate().
+// store are in flight.  Same arithmetic as control_terms4 and candidate(), with
+// the foot's displacement sc a in cells (sc = s c, or s for a drift already in a)
+// and 1/D from the approximate reciprocal: a candidate's relative error stays a
+// few ulp, the minimum picks among candidates within that, and the increment
+// it gives is a few ulp of itself off (it vanishes at the fixed point).
+// NOL: no point's cell has the node as a vertex (the diffusion offset reaches
+// past the foot by more than a cell, or scheme 2, which keeps the self weight
+// in the sum): L = 0, D = 1, no reciprocal.
 template <bool SIG>
 struct Geo32 {
     int o[SIG ? 4 : 1];       // SIG: (xp, y0), (xm, y0), (x0, yp), (x0, ym)
@@ -208,14 +215,20 @@ struct Geo32 {
     float rD;
 };
 
-template <bool SIG, bool CLAMP>
-__device__ __forceinline__ Geo32<SIG> geo32(const GridView& g, int scheme, float s, float bq, int i,
-                                            int j, int kb, int W, float c, float2 a) {
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <bool SIG, bool CLAMP, bool NOL>
+__device__ __forceinline__ Geo32<SIG> geo32(const GridView& g, int scheme, float sc, float bq, int i,
+                                            int j, int kb, int W, float2 a) {
     Geo32<SIG> r;
     const NodeBox<float> box = node_box<float>(i, j, g.n);
-    const float fx = s * (c * a.x);
-    const float fy = s * (c * a.y);
-    float L;
+    const float fx = sc * a.x;
+    const float fy = sc * a.y;
+    float L = 0.0f;
     if constexpr (SIG) {
         const float d = g.d32;
         const Axis<float> xm = axis_cell<float, CLAMP>(fx - d, box.lox, box.hix, box.capx);
@@ -230,17 +243,21 @@ __device__ __forceinline__ Geo32<SIG> geo32(const GridView& g, int scheme, float
         r.o[3] = kb + ym.off * W + x0.off;
         r.fx[0] = xp.fr; r.fx[1] = xm.fr; r.fx[2] = x0.fr;
         r.fy[0] = y0.fr; r.fy[1] = yp.fr; r.fy[2] = ym.fr;
-        L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
+        if constexpr (!NOL) L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
     } else {
         const Axis<float> x0 = axis_cell<float, CLAMP>(fx, box.lox, box.hix, box.capx);
         const Axis<float> y0 = axis_cell<float, CLAMP>(fy, box.loy, box.hiy, box.capy);
         r.o[0] = kb + y0.off * W + x0.off;
         r.fx[0] = x0.fr;
         r.fy[0] = y0.fr;
-        L = x0.sw * y0.sw;
+        if constexpr (!NOL) L = x0.sw * y0.sw;
     }
-    const float D = scheme == 3 ? fmaf(-bq, L, 1.0f) : 1.0f;
-    r.rD = D > 0.0f ? __frcp_rn(D) : -1.0f;
+    if constexpr (NOL) {
+        r.rD = 1.0f;
+    } else {
+        const float D = scheme == 3 ? fmaf(-bq, L, 1.0f) : 1.0f;
+        r.rD = D > 0.0f ? rcp_approx(D) : -1.0f;
+    }
     return r;
 }
 
@@ -412,8 +429,9 @@ k_wtiles(TileArgs a) {
             };
             // FP32, no drift, at most one control per lane: the geometry of node
             // q + 1 is formed during node q (software pipelining)
-            auto visit32 = [&](auto clamp_tag) {
+            auto visit32 = [&](auto clamp_tag, auto nol_tag) {
               constexpr bool CL = decltype(clamp_tag)::value;
+              constexpr bool NOL = decltype(nol_tag)::value;
               const float s = g.s32, beta = g.beta32, hl = g.hl32;
               const float bq = SIG ? beta * 0.25f : beta;
               const float omb = 1.0f - beta;
@@ -424,7 +442,7 @@ k_wtiles(TileArgs a) {
                   const float c = __shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
                   const int ex = e % TW, ey = e / TW;
                   kb = (R + ey) * W + (R + ex);
-                  return geo32<SIG, CL>(g, a.scheme, s, bq, bi + ex, bj + ey, kb, W, c, ac);
+                  return geo32<SIG, CL, NOL>(g, a.scheme, s * c, bq, bi + ex, bj + ey, kb, W, ac);
               };
               float* sf = reinterpret_cast<float*>(su);
               for (int sw = 0; sw < a.local_sweeps; ++sw) {
@@ -446,7 +464,11 @@ k_wtiles(TileArgs a) {
                         Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
                     }
                     const float N = fmaf(bq, Sd, cc0);
-                    const float v = (has && gc.rD > 0.0f) ? N * gc.rD : INFINITY;
+                    float v;
+                    if constexpr (NOL)
+                        v = has ? N : INFINITY;
+                    else
+                        v = (has && gc.rD > 0.0f) ? N * gc.rD : INFINITY;
                     const float du = order_val(__reduce_min_sync(0xffffffffu, order_key(v)));
                     if (lane == 0) sf[kb] = uk + du;
                     __syncwarp();
@@ -455,14 +477,93 @@ k_wtiles(TileArgs a) {
                 }
               }
             };
+            // FP32, constant coefficients: the tile's nodes 32 at a time, one per
+            // lane, each lane evaluating every control itself (no cross-lane
+            // reduction on the chain).  The 32 nodes of a group read each other's
+            // previous values; the groups follow each other in u_hat order.
+            auto visit_ln = [&](auto clamp_tag, auto nol_tag) {
+              constexpr bool CL = decltype(clamp_tag)::value;
+              constexpr bool NOL = decltype(nol_tag)::value;
+              const float s = g.s32, beta = g.beta32, hl = g.hl32;
+              const float bq = SIG ? beta * 0.25f : beta;
+              const float omb = 1.0f - beta;
+              float* sf = reinterpret_cast<float*>(su);
+              const float2* sc = reinterpret_cast<const float2*>(sctrl);
+              for (int sw = 0; sw < a.local_sweeps; ++sw) {
+                for (int hg = 0; hg * 32 < nn; ++hg) {
+                    const bool act = lane + 32 * hg < nn;
+                    const int e = hg ? e1 : e0;
+                    const float c = hg ? c1 : c0;
+                    const int ex = e % TW, ey = e / TW;
+                    const int kb = (R + ey) * W + (R + ex);
+                    float uk = 0.0f, du = 0.0f;
+                    if (act) {
+                        uk = sf[kb];
+                        const float cc0 = fmaf(-omb, uk, hl);
+                        float bx = 0.0f, by = 0.0f;
+                        if (g.drift) {
+                            const float2 bb = g.drift[(bj + ey) * n + bi + ex];
+                            bx = bb.x;
+                            by = bb.y;
+                        }
+                        float best = INFINITY;
+#pragma unroll 2
+                        for (int m = 0; m < na; ++m) {
+                            const float2 am = sc[m];
+                            // the foot's drift c a + b, formed as in the other visits
+                            const float2 f = make_float2(fmaf(c, am.x, bx), fmaf(c, am.y, by));
+                            const Geo32<SIG> gc = geo32<SIG, CL, NOL>(g, a.scheme, s, bq, bi + ex,
+                                                                      bj + ey, kb, W, f);
+                            float Sd;
+                            if constexpr (SIG) {
+                                Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
+                                      bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
+                                     (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
+                                      bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
+                            } else {
+                                Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
+                            }
+                            const float N = fmaf(bq, Sd, cc0);
+                            if constexpr (NOL)
+                                best = fminf(best, N);
+                            else
+                                best = fminf(best, gc.rD > 0.0f ? N * gc.rD : INFINITY);
+                        }
+                        du = best;
+                    }
+                    __syncwarp();
+                    if (act) sf[kb] = uk + du;
+                    __syncwarp();
+                    // |du| >= 0: its bits order like the values
+                    const float gm = __uint_as_float(__reduce_max_sync(0xffffffffu,
+                                                                       __float_as_uint(fabsf(du))));
+                    tmax = fmaxf(tmax, gm);
+                    if (!claimed && tmax > a.tol) claim();
+                }
+              }
+            };
             bool piped = false;
             if constexpr (sizeof(T) == 4) {
-                if (g.drift == nullptr && na <= 32 && !g.gen) {
+                // no self weight: scheme 2 everywhere, a wide diffusion in interior tiles
+                const bool nol = a.no_self == 2 || (a.no_self == 1 && interior);
+                if (a.node_lanes && !g.gen) {
                     piped = true;
-                    if (interior)
-                        visit32(std::false_type{});
-                    else
-                        visit32(std::true_type{});
+                    if (interior) {
+                        if (nol) visit_ln(std::false_type{}, std::true_type{});
+                        else visit_ln(std::false_type{}, std::false_type{});
+                    } else {
+                        if (nol) visit_ln(std::true_type{}, std::true_type{});
+                        else visit_ln(std::true_type{}, std::false_type{});
+                    }
+                } else if (g.drift == nullptr && na <= 32 && !g.gen) {
+                    piped = true;
+                    if (interior) {
+                        if (nol) visit32(std::false_type{}, std::true_type{});
+                        else visit32(std::false_type{}, std::false_type{});
+                    } else {
+                        if (nol) visit32(std::true_type{}, std::true_type{});
+                        else visit32(std::true_type{}, std::false_type{});
+                    }
                 }
             }
             if (!piped) {

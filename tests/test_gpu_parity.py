@@ -56,6 +56,48 @@ def instance_variants():
 VARIANTS = instance_variants()
 
 
+BAND_CASES = {
+    "lambda1": lambda: hi.patchy_1025(0.02, n=257, coarse_n=33),
+    "lambda0.7-drift": lambda: _drift_case(),
+    "no-discount": lambda: hi.zermelo_instance(97, eps=0.01, coarse_n=25),
+}
+
+
+def _drift_case():
+    inst = hi.disc_instance(161, 0.05, n_controls=32, speed=hi.speed_sine(161), lam=0.7,
+                            coarse_n=21)
+    rng = np.random.default_rng(11)
+    inst.drift = rng.uniform(-0.3, 0.3, 2 * 161 * 161).astype(np.float32)
+    return inst
+
+
+@pytest.mark.parametrize("case", list(BAND_CASES))
+def test_band_keys_bit_exact_given_the_same_uhat(case):
+    """Section 4.2 orders the nodes by increasing u_hat; the causal band key of a
+    value is an exact comparison with FP64 band edges on both sides, so given the
+    same u_hat (the oracle's, rounded to FP32) the keys agree node for node, and
+    the ordering groups every band's nodes by patch."""
+    inst = BAND_CASES[case]()
+    ref = oracle.patchy_precompute(inst, tol_c=1e-9)
+    O = ref["fine"]
+    u32 = ref["uhat"].astype(np.float32)
+    free = np.flatnonzero(inst.mask == 0)
+    with P_gpu(inst) as G:
+        G.coarse_solve(tol_c=1e-7)
+        G.build_patches()
+        G.set_uhat(u32)
+        keys, order, off = G.get_order()
+        np.testing.assert_array_equal(G.get_uhat()[free], u32[free])
+    key_or = oracle.band_keys(u32.astype(np.float64), inst.mask, inst.lam, O.h, 1 << 20)
+    np.testing.assert_array_equal(keys[free], key_or[free])
+    assert (keys[inst.mask != 0] == -1).all()
+    kk = keys[order]
+    assert np.array_equal(np.sort(order), free)
+    for b in range(len(off) - 1):
+        assert (kk[off[b]:off[b + 1]] == b).all()
+    assert len(off) - 1 == key_or[free].max() + 1
+
+
 @pytest.mark.parametrize("name,inst", VARIANTS, ids=[v[0] for v in VARIANTS])
 @pytest.mark.parametrize("scheme", [3, 2])
 def test_operator_parity_fp64(name, inst, scheme):
