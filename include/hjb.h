@@ -442,6 +442,16 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
                      const float* speed, const uint8_t* mask, const int8_t* sector,
                      const double* controls, void* cuda_stream, hjb_batch** out);
 
+/* hjb_batch_create_lists -- hjb_batch_create with one host array per instance:
+ * speed[i], mask[i] (and sector[i], when sector is not NULL; a NULL sector list
+ * or entry gives sector 0 on target nodes, -1 elsewhere) hold instance i's
+ * n_i x n_i field.  The library copies each into its place on the device, so the
+ * caller never concatenates the instances.  Same checks and errors. */
+int hjb_batch_create_lists(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst* insts,
+                           const float* const* speed, const uint8_t* const* mask,
+                           const int8_t* const* sector, const double* controls, void* cuda_stream,
+                           hjb_batch** out);
+
 /* hjb_batch_solve -- the whole patchy pipeline for every instance: coarse solves
  * until the sup-increment is <= tol_c, pre-computation, FP32 warp-tile passes
  * until no tile changes by more than tol32, the FP64 sup-residual ||T2 u - u||

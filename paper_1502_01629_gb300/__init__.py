@@ -290,16 +290,26 @@ class Batch:
         d.n_controls, d.scheme, d.tile_shape = controls.shape[0], scheme, tile_shape
         d.tile_waves, d.tile_period, d.reserved = tile_waves, tile_period, 0
         d.cost, d.band_width = cost, band_width
-        speed = _c(np.concatenate([np.asarray(x.speed).reshape(-1) for x in insts]), np.float32)
-        mask = _c(np.concatenate([np.asarray(x.mask).reshape(-1) for x in insts]), np.uint8)
-        sector = _c(np.concatenate([np.asarray(x.sector).reshape(-1) for x in insts]), np.int8)
+        # one host array per instance (hjb_batch_create_lists): the library copies
+        # each into its place on the device, nothing is concatenated here
+        keep = [(_c(x.speed, np.float32).reshape(-1), _c(x.mask, np.uint8).reshape(-1),
+                 None if x.sector is None else _c(x.sector, np.int8).reshape(-1)) for x in insts]
+        for (sp, mk, sc), n in zip(keep, self.ns):
+            if sp.size != n * n or mk.size != n * n or (sc is not None and sc.size != n * n):
+                raise ValueError("speed, mask and sector must have n*n entries")
+        ptrs = lambda k: (ctypes.c_void_p * self.count)(*[a[k].ctypes.data if a[k] is not None else None
+                                                          for a in keep])
+        speed_l, mask_l = ptrs(0), ptrs(1)
+        sector_l = None if any(a[2] is None for a in keep) else ptrs(2)
         h = ctypes.c_void_p()
         st = None
         if stream is not None:
             st = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
-        check(lib().hjb_batch_create(ctypes.byref(d), self.count, ctypes.cast(arr, ctypes.c_void_p),
-                                     _p(speed), _p(mask), _p(sector), _p(controls), st,
-                                     ctypes.byref(h)), "hjb_batch_create")
+        check(lib().hjb_batch_create_lists(ctypes.byref(d), self.count, ctypes.cast(arr, ctypes.c_void_p),
+                                           ctypes.cast(speed_l, ctypes.c_void_p),
+                                           ctypes.cast(mask_l, ctypes.c_void_p),
+                                           None if sector_l is None else ctypes.cast(sector_l, ctypes.c_void_p),
+                                           _p(controls), st, ctypes.byref(h)), "hjb_batch_create_lists")
         self._h = h
 
     @classmethod

@@ -119,6 +119,8 @@ _SIGNATURES = {
                                             _PTR]),
     "hjb_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _PTR, _PTR, _PTR, _PTR, _PTR,
                                         _PTR, ctypes.POINTER(_P)]),
+    "hjb_batch_create_lists": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _PTR, _PTR, _PTR, _PTR, _PTR,
+                                        _PTR, ctypes.POINTER(_P)]),
     "hjb_batch_solve": (ctypes.c_int, [_P, _D, _D, _D, _I32, ctypes.POINTER(Stats), _PTR]),
     "hjb_batch_solve_full": (ctypes.c_int, [_P, _D, _D, _I32, ctypes.POINTER(Stats), _PTR]),
     "hjb_batch_autotune": (ctypes.c_int, [_P, _D, _D, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _PTR]),

@@ -287,6 +287,11 @@ struct hjb_problem {
     int32_t* wt_count = nullptr;
     float* wt_speed = nullptr;     // speed per node slot (warp tiles)
     int32_t* wt_stamp = nullptr;   // per-tile queue stamps (warp tiles)
+    bool async = false;            // schedule 3: the asynchronous worklist for the FP32 phase
+    int32_t* a_state = nullptr;    // worklist: per-tile state and first-visit counters
+    int32_t* a_deps = nullptr;
+    unsigned long long* a_queue = nullptr;
+    int a_cap = 0;
     int32_t* wt_queue = nullptr;   // (tile_period + 2) x nt queued tiles
     int32_t* wt_qcount = nullptr;  // tile_period + 2 queue lengths
     int32_t* cb_wave = nullptr;    // warm restart: checkerboard wave (0/1) of each tile
@@ -411,6 +416,7 @@ struct Scalars {
     CoarseResult coarse;
     WaveResult wave;
     GridSync sync;
+    AsyncCtl actl;
 };
 
 static_assert(sizeof(Scalars) <= kPinnedSlot, "a problem's pinned scalars must fit one pinned slot");
@@ -437,7 +443,7 @@ int validate_desc(const hjb_desc* d) {
     }
     if (!std::isfinite(d->band_width)) return fail(HJB_ERR_INVALID_ARG, "bad band_width");
     if (d->resort_passes < 0) return fail(HJB_ERR_INVALID_ARG, "resort_passes must be >= 0");
-    if (d->schedule < 0 || d->schedule > 2) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0, 1 or 2");
+    if (d->schedule < 0 || d->schedule > 3) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0, 1, 2 or 3");
     if (d->tile_shape < -1 || d->tile_shape > 2)
         return fail(HJB_ERR_INVALID_ARG, "tile_shape must be -1 (auto), 0 (8x8), 1 (8x4) or 2 (4x4)");
     if (d->visit < 0 || d->visit > 2)
@@ -574,6 +580,11 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         return bail(fail(HJB_ERR_INVALID_ARG, "obstacles need lambda > 0 (their value is l/lambda + h l)"));
 
     p->desc = *desc;
+    if (p->desc.schedule == 3) {
+        // the warp tiles of schedule 0, the FP32 phase from the asynchronous worklist
+        p->async = true;
+        p->desc.schedule = 0;
+    }
     if (p->desc.scheme == 0) p->desc.scheme = 3;
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
@@ -792,8 +803,12 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         ti.nty = p->nty;
         ti.tile_off = 0;
         ti.act_radius = p->act_radius;
-        p->max_wh = (tw + 2 * p->halo) * (th + 2 * p->halo);
+        const int wv = tw + 2 * p->halo;
+        p->max_wh = (p->desc.visit == 2 ? tile_pitch(wv) : wv) * (th + 2 * p->halo);
         CUP(cudaMemcpyAsync(p->tinst, &ti, sizeof(ti), cudaMemcpyHostToDevice, p->st));
+        // blocks per SM with the (padded) staging slices the launches use
+        p->tile_blocks32 = std::max(1, wtile_blocks_per_sm(false, sig, na, p->max_wh, p->shape)) * p->num_sms;
+        p->tile_blocks64 = std::max(1, wtile_blocks_per_sm(true, sig, na, p->max_wh, p->shape)) * p->num_sms;
     }
     p->wave_blocks32 = std::max(1, wave_blocks_per_sm(false, sig, na)) * p->num_sms;
     p->wave_blocks64 = std::max(1, wave_blocks_per_sm(true, sig, na)) * p->num_sms;
@@ -1122,6 +1137,43 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
         const int want = (p->desc.wave_warps + wpb - 1) / wpb;
         blocks = std::max(1, std::min(blocks, want));
     }
+    if (p->desc.schedule == 0 && p->async && !f64 && !warm) {
+        // the asynchronous worklist: ring sized above the tiles plus one waiting
+        // ticket per warp
+        const int warps = blocks * (tile_threads(false, p->shape) / 32);
+        int cap = 1024;
+        while (cap < p->nt + warps + 64) cap <<= 1;
+        if (cap > p->a_cap) {
+            pfree(p->a_state, p->st); pfree(p->a_deps, p->st); pfree(p->a_queue, p->st);
+            CU(palloc(&p->a_state, sizeof(int32_t) * (size_t)p->nt, p->st));
+            CU(palloc(&p->a_deps, sizeof(int32_t) * (size_t)p->nt, p->st));
+            CU(palloc(&p->a_queue, sizeof(unsigned long long) * (size_t)cap, p->st));
+            p->a_cap = cap;
+        }
+        CU(cudaMemsetAsync(p->a_queue, 0, sizeof(unsigned long long) * (size_t)p->a_cap, p->st));
+        CU(cudaMemsetAsync(&ds->actl, 0, sizeof(AsyncCtl), p->st));
+        a.astate = p->a_state;
+        a.adeps = p->a_deps;
+        a.aqueue = p->a_queue;
+        a.aq_cap = p->a_cap;
+        a.actl = &ds->actl;
+        a.max_visits = (long long)max_passes * p->nt;
+        CU(launch_wtiles_async(a, sig, blocks, p->st));
+        CU(cudaMemcpyAsync(&hscal(p)->actl, &ds->actl, sizeof(AsyncCtl), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaMemcpyAsync(&hscal(p)->sync, &ds->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, p->st));
+        CU(cudaStreamSynchronize(p->st));
+        if (hscal(p)->sync.err == HJB_ERR_TIMEOUT)
+            return fail(HJB_ERR_TIMEOUT, "tile worklist: a wait exceeded its limit");
+        if (hscal(p)->sync.err != 0) return fail(hscal(p)->sync.err, "tile worklist: internal error");
+        *out = hscal(p)->wave;
+        // passes = visits per tile with free nodes (the worklist has no steps)
+        const long long tiles = std::max(1, p->nt);
+        out->passes = (int)((hscal(p)->actl.visits + tiles - 1) / tiles);
+        out->converged = hscal(p)->actl.stop ? 0 : 1;
+        out->last_increment = (float)tol;
+        return HJB_OK;
+    }
     if (p->desc.schedule == 0) {
         CU(launch_wtiles(a, f64, sig, blocks, p->st));
     } else if (f64) {
@@ -1272,6 +1324,7 @@ void hjb_destroy(hjb_problem* p) {
     pfree(p->tile_inc, p->st); pfree(p->tile_key2, p->st); pfree(p->tile_nodes, p->st); pfree(p->tile_bin_count, p->st);
     pfree(p->tile_bin_off, p->st); pfree(p->wt_nodes, p->st); pfree(p->wt_count, p->st); pfree(p->wt_speed, p->st);
     pfree(p->wt_stamp, p->st); pfree(p->wt_queue, p->st); pfree(p->wt_qcount, p->st);
+    pfree(p->a_state, p->st); pfree(p->a_deps, p->st); pfree(p->a_queue, p->st);
     pfree(p->cb_wave, p->st); pfree(p->cb_key, p->st); pfree(p->cb_list, p->st); pfree(p->cb_off, p->st); pfree(p->cb_count, p->st);
     pfree(p->tinst, p->st); pfree(p->rank_flags, p->st); pfree(p->rank_scan, p->st); pfree(p->rank_boff, p->st); pfree(p->sched_count, p->st); pfree(p->sched_off, p->st); pfree(p->res_off, p->st);
     pfree(p->step_inc, p->st);

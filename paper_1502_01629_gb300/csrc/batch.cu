@@ -678,18 +678,35 @@ int validate_batch(const hjb_batch_desc* d, int32_t count, const hjb_batch_inst*
 
 }  // namespace
 
-extern "C" {
+// The host inputs of a batch: either concatenated arrays (instance i's nodes
+// after those of instances 0 .. i-1) or one array per instance.
+struct BatchHostInputs {
+    const float* speed = nullptr;
+    const uint8_t* mask = nullptr;
+    const int8_t* sector = nullptr;
+    const float* const* speed_list = nullptr;
+    const uint8_t* const* mask_list = nullptr;
+    const int8_t* const* sector_list = nullptr;
+    bool lists() const { return speed_list != nullptr; }
+};
 
-int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst* insts,
-                     const float* speed, const uint8_t* mask, const int8_t* sector,
-                     const double* controls, void* cuda_stream, hjb_batch** out) {
+int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst* insts,
+                 const BatchHostInputs& in, const double* controls, void* cuda_stream,
+                 hjb_batch** out) {
     clear_last_error();
     if (!out) return bfail(HJB_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     int rc = validate_batch(desc, count, insts);
     if (rc) return rc;
-    if (!speed || !mask || !controls)
+    if (!controls) return bfail(HJB_ERR_INVALID_ARG, "controls are required");
+    if (in.lists()) {
+        if (!in.mask_list) return bfail(HJB_ERR_INVALID_ARG, "speed and mask lists are required");
+        for (int i = 0; i < count; ++i)
+            if (!in.speed_list[i] || !in.mask_list[i])
+                return bfail(HJB_ERR_INVALID_ARG, "instance %d: speed / mask is NULL", i);
+    } else if (!in.speed || !in.mask) {
         return bfail(HJB_ERR_INVALID_ARG, "speed, mask and controls are required");
+    }
     const int na = desc->n_controls;
     double amax = 0.0;
     for (int m = 0; m < na; ++m) {
@@ -757,16 +774,26 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     BCUP(dalloc(b->uc, Nc, b->st));
     BCUP(dalloc(b->ctrl32, na, b->st));
     BCUP(dalloc(b->ctrl64, na, b->st));
-    BCUP(cudaMemcpyAsync(b->speed, speed, N * sizeof(float), cudaMemcpyHostToDevice, b->st));
-    BCUP(cudaMemcpyAsync(b->mask, mask, N, cudaMemcpyHostToDevice, b->st));
-    if (sector) {
-        BCUP(cudaMemcpyAsync(b->sector, sector, N, cudaMemcpyHostToDevice, b->st));
-    } else {
-        std::vector<int8_t> sec(N);
-        for (size_t k = 0; k < N; ++k) sec[k] = mask[k] == HJB_MASK_TARGET ? 0 : -1;
-        BCUP(cudaMemcpyAsync(b->sector, sec.data(), N, cudaMemcpyHostToDevice, b->st));
-        BCUP(cudaStreamSynchronize(b->st));
+    // uploads: one copy per array, or per instance and array (no host-side
+    // concatenation); absent sectors: sector 0 on target nodes, -1 elsewhere
+    for (int i = 0; i < (in.lists() ? count : 1); ++i) {
+        const long long o = in.lists() ? b->node_off[i] : 0;
+        const size_t Ni = in.lists() ? (size_t)(b->node_off[i + 1] - o) : N;
+        const float* sp = in.lists() ? in.speed_list[i] : in.speed;
+        const uint8_t* mk = in.lists() ? in.mask_list[i] : in.mask;
+        const int8_t* sc = in.lists() ? (in.sector_list ? in.sector_list[i] : nullptr) : in.sector;
+        BCUP(cudaMemcpyAsync(b->speed + o, sp, Ni * sizeof(float), cudaMemcpyHostToDevice, b->st));
+        BCUP(cudaMemcpyAsync(b->mask + o, mk, Ni, cudaMemcpyHostToDevice, b->st));
+        if (sc) {
+            BCUP(cudaMemcpyAsync(b->sector + o, sc, Ni, cudaMemcpyHostToDevice, b->st));
+        } else {
+            std::vector<int8_t> sec(Ni);
+            for (size_t k = 0; k < Ni; ++k) sec[k] = mk[k] == HJB_MASK_TARGET ? 0 : -1;
+            BCUP(cudaMemcpyAsync(b->sector + o, sec.data(), Ni, cudaMemcpyHostToDevice, b->st));
+            BCUP(cudaStreamSynchronize(b->st));
+        }
     }
+    const bool has_sector = in.lists() ? in.sector_list != nullptr : in.sector != nullptr;
     {
         // per-instance checks and speed maxima on the device, after the upload
         // (the host never walks the concatenated arrays)
@@ -779,7 +806,7 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
         for (int i = 0; i < count; ++i) {
             const long long o = b->node_off[i], Ni = b->node_off[i + 1] - o;
             nbk[i] = std::min(kScanBlocks, scan_inputs_blocks(Ni));
-            BCUP(launch_scan_inputs(Ni, b->speed + o, b->mask + o, sector ? b->sector + o : nullptr,
+            BCUP(launch_scan_inputs(Ni, b->speed + o, b->mask + o, has_sector ? b->sector + o : nullptr,
                                     insts[i].n_patches, nullptr, 1.0f, rec + (size_t)i * kScanBlocks,
                                     bad + 4 * (size_t)i, nbk[i], b->st));
         }
@@ -790,12 +817,14 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
                              b->st));
         BCUP(cudaStreamSynchronize(b->st));
         dfree(b->scan_tmp, b->st);
+        b->n_free.assign(count, 0);
         for (int i = 0; i < count; ++i) {
             unsigned flags = 0;
             for (int q = 0; q < nbk[i]; ++q) {
                 const InputScan& r = hr[(size_t)i * kScanBlocks + q];
                 flags |= r.flags;
                 cmax[i] = std::max(cmax[i], r.cmax);
+                b->n_free[i] += (long long)r.nfree;
             }
             if (flags & 1u)
                 return bail(bfail(HJB_ERR_INVALID_ARG, "instance %d: speed[%llu] is negative or not finite", i,
@@ -1021,19 +1050,45 @@ int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_
     if (rc) return bail(rc);
     BCUP(cudaStreamSynchronize(b->st));
     {
-        b->n_free.assign(count, 0);
+        // free coarse nodes (the fine ones came with the input scan)
         b->n_free_c.assign(count, 0);
         std::vector<uint8_t> mc((size_t)b->Nc);
         BCUP(cudaMemcpyAsync(mc.data(), b->mask_c, (size_t)b->Nc, cudaMemcpyDeviceToHost, b->st));
         BCUP(cudaStreamSynchronize(b->st));
-        for (int i = 0; i < count; ++i) {
-            for (long long k = b->node_off[i]; k < b->node_off[i + 1]; ++k) b->n_free[i] += mask[k] == 0;
+        for (int i = 0; i < count; ++i)
             for (long long k = b->coarse_off[i]; k < b->coarse_off[i + 1]; ++k) b->n_free_c[i] += mc[k] == 0;
-        }
     }
 #undef BCUP
     *out = b;
     return HJB_OK;
+}
+
+extern "C" {
+
+int hjb_batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst* insts,
+                     const float* speed, const uint8_t* mask, const int8_t* sector,
+                     const double* controls, void* cuda_stream, hjb_batch** out) {
+    BatchHostInputs in;
+    in.speed = speed;
+    in.mask = mask;
+    in.sector = sector;
+    return batch_create(desc, count, insts, in, controls, cuda_stream, out);
+}
+
+int hjb_batch_create_lists(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst* insts,
+                           const float* const* speed, const uint8_t* const* mask,
+                           const int8_t* const* sector, const double* controls, void* cuda_stream,
+                           hjb_batch** out) {
+    if (!speed || !mask) {
+        clear_last_error();
+        if (out) *out = nullptr;
+        return bfail(HJB_ERR_INVALID_ARG, "speed and mask lists are required");
+    }
+    BatchHostInputs in;
+    in.speed_list = speed;
+    in.mask_list = mask;
+    in.sector_list = sector;
+    return batch_create(desc, count, insts, in, controls, cuda_stream, out);
 }
 
 void hjb_batch_destroy(hjb_batch* b) {

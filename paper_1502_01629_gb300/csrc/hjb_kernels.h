@@ -246,6 +246,18 @@ struct TileInst {
     int pad;
 };
 
+// Control words of the asynchronous tile worklist (each on its own 128-byte line).
+struct AsyncCtl {
+    unsigned long long head;        // next ticket to take
+    unsigned long long pad0[15];
+    unsigned long long tail;        // next position to fill
+    unsigned long long pad1[15];
+    int pending;                    // tiles queued or being visited
+    int stop;                       // set on the visit cap or an error
+    unsigned long long visits;      // tile visits so far
+    unsigned long long pad2[14];
+};
+
 struct TileArgs {
     GridView g;
     int scheme;
@@ -283,12 +295,26 @@ struct TileArgs {
                                // reach in cells), 0 = compute it
     int max_steps;
     float tol;
+    // asynchronous worklist (schedule 3): per-tile state 0 idle, 1 queued,
+    // 2 being visited, 3 being visited and queued again; per-tile count of
+    // lower-wave neighbours whose first visit is still to come (-1 once the tile's
+    // own first visit has started); a ring of aq_cap tagged entries
+    int32_t* astate;
+    int32_t* adeps;
+    unsigned long long* aqueue;
+    int aq_cap;                // power of two > nt + warps in flight
+    AsyncCtl* actl;
+    long long max_visits;
     GridSync* sync;
     WaveResult* res;
     unsigned long long timeout_ns;
 };
 
 void wtile_dims(int shape, int* tw, int* th);
+// Row pitch of a staged warp-tile window of width w for node-per-lane visits:
+// the smallest 16 k + 8 >= w (8 or 24 mod 32: rows 0..3 of an 8-wide block of
+// nodes map to distinct shared-memory banks).
+__host__ __device__ inline int tile_pitch(int w) { return w <= 8 ? 8 : ((w - 8 + 15) / 16) * 16 + 8; }
 size_t tile_smem(bool f64, int na, int halo, int shape);
 // launch of the warp-tile kernel with the slices sized by a.max_wh
 size_t wtile_smem(bool f64, int na, int max_wh);
@@ -305,6 +331,10 @@ cudaError_t launch_checker_waves(const TileInst* insts, const int32_t* tile_inst
                                  const int32_t* count, int32_t* wave, int32_t* key, cudaStream_t st);
 // The warp-tile kernel (shape 1..3) over a.insts / a.tile_inst.
 cudaError_t launch_wtiles(const TileArgs& a, bool f64, bool sig, int blocks, cudaStream_t st);
+// The asynchronous worklist form (FP32): initialises the per-tile state and the
+// queue (the released tiles in tile_list order) and runs the persistent kernel.
+// a.aqueue (aq_cap entries) and a.actl must be zeroed by the caller.
+cudaError_t launch_wtiles_async(const TileArgs& a, bool sig, int blocks, cudaStream_t st);
 int wtile_blocks_per_sm(bool f64, bool sig, int na, int max_wh, int shape);
 // Dense tile waves (warp tiles): within each instance the distinct lowest bands
 // of its tiles are ranked in increasing order and wave = rank / band_group, so

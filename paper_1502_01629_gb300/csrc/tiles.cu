@@ -269,6 +269,321 @@ __device__ __forceinline__ float bil32(const float* su, int o, int W, float frx,
     return fmaf(fry, b - a, a);
 }
 
+// One visit of warp tile t (global index, instance from a.tile_inst): the warp
+// stages the tile and a halo of R cells from u into its slice su, updates the
+// tile's free nodes in increasing u_hat (the forms below), and writes them back.
+// `hook` runs once, as soon as some node has changed by more than a.tol, so a
+// schedule can queue the neighbours while the rest of the tile is visited.
+// Returns the largest |increment|; *nn_out = the tile's free nodes.
+template <typename T, bool SIG, int TW, int TH, typename Hook>
+__device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
+                                          const typename RealOf<T>::V2* sctrl, int na, int lane,
+                                          Hook& hook, int* nn_out) {
+    const int b = a.tile_inst ? a.tile_inst[t] : 0;
+    const TileInst& I = a.insts[b];
+    auto C = [&](int m) { return sctrl[m]; };
+    const GridView& g = I.g;
+    const int n = g.n;
+    const int R = I.R;
+    const int Wv = TW + 2 * R;       // staged window width
+    // row pitch of the staged window: with node-per-lane visits, 8 or 24
+    // (mod 32), so that 4 rows x 8 nodes fall in 32 distinct banks
+    const int W = a.node_lanes ? tile_pitch(Wv) : Wv;
+    const int H = TH + 2 * R;
+    T* u;
+    if constexpr (sizeof(T) == 4) u = I.u32; else u = I.u64;
+    const int tl = t - I.tile_off;
+    const int tcx = tl % I.ntx, tcy = tl / I.ntx;
+    const int bi = tcx * TW, bj = tcy * TH;
+    const int gx0 = bi - R, gy0 = bj - R;
+    for (int e = lane; e < Wv * H; e += 32) {
+        const int ey = e / Wv, ex = e - ey * Wv;
+        const int gx = min(max(gx0 + ex, 0), n - 1);
+        const int gy = min(max(gy0 + ey, 0), n - 1);
+        su[ey * W + ex] = ld_l2(u + (size_t)gy * n + gx);
+    }
+    const int nn = a.wt_count[t];
+    const int* tn = a.nodes + (size_t)t * kWarpTileNodes;
+    const float* tsp = a.slot_speed + (size_t)t * kWarpTileNodes;
+    // tile-local indices e (row-major TW x TH) of the nodes, in visiting order
+    const int e0 = lane < nn ? tn[lane] : 0;
+    const int e1 = lane + 32 < nn ? tn[lane + 32] : 0;
+    const float c0 = lane < nn ? tsp[lane] : 0.0f;
+    const float c1 = lane + 32 < nn ? tsp[lane + 32] : 0.0f;
+    __syncwarp();
+    float tmax = 0.0f;
+    bool claimed = false;
+    auto claim = [&]() {
+        claimed = true;
+        hook();
+    };
+    // staged window inside the grid: the projection is the identity
+    const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + Wv <= n && gy0 + H <= n;
+    auto visit = [&](auto clamp_tag) {
+      constexpr bool CL = decltype(clamp_tag)::value;
+      for (int sw = 0; sw < a.local_sweeps; ++sw) {
+        for (int q = 0; q < nn; ++q) {
+            const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
+            const T c = (T)__shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
+            const int ex = e % TW, ey = e / TW;
+            const int i = bi + ex, j = bj + ey;
+            T* base = su + (R + ey) * W + (R + ex);
+            const T uk = base[0];
+            T bx = T(0), by = T(0);
+            if (g.drift) {
+                const float2 bb = g.drift[j * n + i];
+                bx = (T)bb.x;
+                by = (T)bb.y;
+            }
+            auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
+            T N, Dn;
+            int M;
+            best_over_controls<T, SIG, CL>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C,
+                                           U, N, Dn, M);
+            T du;
+            if constexpr (sizeof(T) == 4) {
+                du = warp_min_increment(N, Dn, M);
+            } else {
+                warp_argmin<T>(N, Dn, M);
+                du = N / Dn;
+            }
+            if (lane == 0) base[0] = uk + du;
+            __syncwarp();
+            tmax = fmaxf(tmax, inc_to_float(fabs(du)));
+            if (!claimed && tmax > a.tol) claim();
+        }
+      }
+    };
+    // FP32, no drift, at most one control per lane: the geometry of node
+    // q + 1 is formed during node q (software pipelining)
+    auto visit32 = [&](auto clamp_tag, auto nol_tag) {
+      constexpr bool CL = decltype(clamp_tag)::value;
+      constexpr bool NOL = decltype(nol_tag)::value;
+      const float s = g.s32, beta = g.beta32, hl = g.hl32;
+      const float bq = SIG ? beta * 0.25f : beta;
+      const float omb = 1.0f - beta;
+      const bool has = lane < na;
+      const float2 ac = has ? g.ctrl32[lane] : make_float2(0.0f, 0.0f);
+      auto node_geo = [&](int q, int& kb) {
+          const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
+          const float c = __shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
+          const int ex = e % TW, ey = e / TW;
+          kb = (R + ey) * W + (R + ex);
+          return geo32<SIG, CL, NOL>(g, a.scheme, s * c, bq, bi + ex, bj + ey, kb, W, ac);
+      };
+      float* sf = reinterpret_cast<float*>(su);
+      for (int sw = 0; sw < a.local_sweeps; ++sw) {
+        int kbn;
+        Geo32<SIG> gn = node_geo(0, kbn);
+        for (int q = 0; q < nn; ++q) {
+            const Geo32<SIG> gc = gn;
+            const int kb = kbn;
+            gn = node_geo(min(q + 1, nn - 1), kbn);
+            const float uk = sf[kb];
+            const float cc0 = fmaf(-omb, uk, hl);
+            float Sd;
+            if constexpr (SIG) {
+                Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
+                      bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
+                     (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
+                      bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
+            } else {
+                Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
+            }
+            const float N = fmaf(bq, Sd, cc0);
+            float v;
+            if constexpr (NOL)
+                v = has ? N : INFINITY;
+            else
+                v = (has && gc.rD > 0.0f) ? N * gc.rD : INFINITY;
+            const float du = order_val(__reduce_min_sync(0xffffffffu, order_key(v)));
+            if (lane == 0) sf[kb] = uk + du;
+            __syncwarp();
+            tmax = fmaxf(tmax, fabsf(du));
+            if (!claimed && tmax > a.tol) claim();
+        }
+      }
+    };
+    // FP32, constant coefficients: the tile's nodes 32 at a time, one per
+    // lane, each lane evaluating every control itself (no cross-lane
+    // reduction on the chain).  A group is 32 consecutive tile positions
+    // (4 rows of 8), so a gather of the warp hits 32 distinct banks; the
+    // nodes of a group read each other's previous values, and the group
+    // holding the tile's lowest u_hat goes first.
+    auto visit_ln = [&](auto clamp_tag, auto nol_tag) {
+      constexpr bool CL = decltype(clamp_tag)::value;
+      constexpr bool NOL = decltype(nol_tag)::value;
+      constexpr int NG = (TW * TH + 31) / 32;
+      const float s = g.s32, beta = g.beta32, hl = g.hl32;
+      const float bq = SIG ? beta * 0.25f : beta;
+      const float omb = 1.0f - beta;
+      float* sf = reinterpret_cast<float*>(su);
+      const float2* sc = reinterpret_cast<const float2*>(sctrl);
+      // free positions of the tile, from its node slots
+      unsigned long long fm = 0ull;
+      if (lane < nn) fm |= 1ull << e0;
+      if (lane + 32 < nn) fm |= 1ull << e1;
+      const unsigned flo = __reduce_or_sync(0xffffffffu, (unsigned)fm);
+      const unsigned fhi = __reduce_or_sync(0xffffffffu, (unsigned)(fm >> 32));
+      const int g0 = __shfl_sync(0xffffffffu, e0, 0) >> 5;   // group of the lowest u_hat
+      static_assert(NG <= 2, "tiles of at most 64 nodes");
+      // this lane's node in each group: free?, speed (registers, no indexing)
+      const bool fr0 = lane < TW * TH && ((flo >> lane) & 1u);
+      const bool fr1 = NG > 1 && ((fhi >> lane) & 1u);
+      const float cg0 = fr0 ? g.speed[(size_t)(bj + lane / TW) * n + bi + lane % TW] : 0.0f;
+      const float cg1 = fr1 ? g.speed[(size_t)(bj + (32 + lane) / TW) * n + bi + (32 + lane) % TW]
+                            : 0.0f;
+      for (int sw = 0; sw < a.local_sweeps; ++sw) {
+#pragma unroll
+        for (int t2 = 0; t2 < NG; ++t2) {
+            const int gi = NG == 1 ? 0 : (g0 + t2) & 1;
+            const bool act = gi ? fr1 : fr0;
+            const int e = gi * 32 + lane;
+            const float c = gi ? cg1 : cg0;
+            const int ex = e % TW, ey = e / TW;
+            const int kb = (R + ey) * W + (R + ex);
+            float uk = 0.0f, du = 0.0f;
+            if (act) {
+                uk = sf[kb];
+                const float cc0 = fmaf(-omb, uk, hl);
+                float bx = 0.0f, by = 0.0f;
+                if (g.drift) {
+                    const float2 bb = g.drift[(size_t)(bj + ey) * n + bi + ex];
+                    bx = bb.x;
+                    by = bb.y;
+                }
+                float best = INFINITY;
+#pragma unroll 2
+                for (int m = 0; m < na; ++m) {
+                    const float2 am = sc[m];
+                    // the foot's drift c a + b, formed as in the other visits
+                    const float2 f = make_float2(fmaf(c, am.x, bx), fmaf(c, am.y, by));
+                    const Geo32<SIG> gc = geo32<SIG, CL, NOL>(g, a.scheme, s, bq, bi + ex,
+                                                              bj + ey, kb, W, f);
+                    float Sd;
+                    if constexpr (SIG) {
+                        Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
+                              bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
+                             (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
+                              bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
+                    } else {
+                        Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
+                    }
+                    const float N = fmaf(bq, Sd, cc0);
+                    if constexpr (NOL)
+                        best = fminf(best, N);
+                    else
+                        best = fminf(best, gc.rD > 0.0f ? N * gc.rD : INFINITY);
+                }
+                du = best;
+            }
+            __syncwarp();
+            if (act) sf[kb] = uk + du;
+            __syncwarp();
+            // |du| >= 0: its bits order like the values
+            const float gm = __uint_as_float(__reduce_max_sync(0xffffffffu,
+                                                               __float_as_uint(fabsf(du))));
+            tmax = fmaxf(tmax, gm);
+            if (!claimed && tmax > a.tol) claim();
+        }
+      }
+    };
+    // FP32, no drift, 33..64 controls: two controls per lane (m = lane and
+    // lane + 32), both geometries formed at the node, the lane's smaller
+    // candidate into the warp minimum
+    auto visit32k2 = [&](auto clamp_tag, auto nol_tag) {
+      constexpr bool CL = decltype(clamp_tag)::value;
+      constexpr bool NOL = decltype(nol_tag)::value;
+      const float s = g.s32, beta = g.beta32, hl = g.hl32;
+      const float bq = SIG ? beta * 0.25f : beta;
+      const float omb = 1.0f - beta;
+      const bool has1 = lane + 32 < na;
+      const float2 ac0 = g.ctrl32[lane];
+      const float2 ac1 = has1 ? g.ctrl32[lane + 32] : make_float2(0.0f, 0.0f);
+      float* sf = reinterpret_cast<float*>(su);
+      auto cand = [&](const Geo32<SIG>& gc, float uk, float cc0) {
+          float Sd;
+          if constexpr (SIG) {
+              Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
+                    bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
+                   (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
+                    bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
+          } else {
+              Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
+          }
+          const float N = fmaf(bq, Sd, cc0);
+          if constexpr (NOL) return N;
+          return gc.rD > 0.0f ? N * gc.rD : INFINITY;
+      };
+      for (int sw = 0; sw < a.local_sweeps; ++sw) {
+        for (int q = 0; q < nn; ++q) {
+            const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
+            const float c = __shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
+            const int ex = e % TW, ey = e / TW;
+            const int kb = (R + ey) * W + (R + ex);
+            const float sc2 = s * c;
+            const Geo32<SIG> ga = geo32<SIG, CL, NOL>(g, a.scheme, sc2, bq, bi + ex, bj + ey, kb, W, ac0);
+            const Geo32<SIG> gb = geo32<SIG, CL, NOL>(g, a.scheme, sc2, bq, bi + ex, bj + ey, kb, W, ac1);
+            const float uk = sf[kb];
+            const float cc0 = fmaf(-omb, uk, hl);
+            const float va = cand(ga, uk, cc0);
+            const float vb = has1 ? cand(gb, uk, cc0) : INFINITY;
+            const float du = order_val(__reduce_min_sync(0xffffffffu, order_key(fminf(va, vb))));
+            if (lane == 0) sf[kb] = uk + du;
+            __syncwarp();
+            tmax = fmaxf(tmax, fabsf(du));
+            if (!claimed && tmax > a.tol) claim();
+        }
+      }
+    };
+    bool piped = false;
+    if constexpr (sizeof(T) == 4) {
+        // no self weight: scheme 2 everywhere, a wide diffusion in interior tiles
+        const bool nol = a.no_self == 2 || (a.no_self == 1 && interior);
+        if (a.node_lanes && !g.gen) {
+            piped = true;
+            if (interior) {
+                if (nol) visit_ln(std::false_type{}, std::true_type{});
+                else visit_ln(std::false_type{}, std::false_type{});
+            } else {
+                if (nol) visit_ln(std::true_type{}, std::true_type{});
+                else visit_ln(std::true_type{}, std::false_type{});
+            }
+        } else if (g.drift == nullptr && na <= 32 && !g.gen) {
+            piped = true;
+            if (interior) {
+                if (nol) visit32(std::false_type{}, std::true_type{});
+                else visit32(std::false_type{}, std::false_type{});
+            } else {
+                if (nol) visit32(std::true_type{}, std::true_type{});
+                else visit32(std::true_type{}, std::false_type{});
+            }
+        } else if (g.drift == nullptr && na <= 64 && !g.gen) {
+            piped = true;
+            if (interior) {
+                if (nol) visit32k2(std::false_type{}, std::true_type{});
+                else visit32k2(std::false_type{}, std::false_type{});
+            } else {
+                if (nol) visit32k2(std::true_type{}, std::true_type{});
+                else visit32k2(std::true_type{}, std::false_type{});
+            }
+        }
+    }
+    if (!piped) {
+        if (interior)
+            visit(std::false_type{});
+        else
+            visit(std::true_type{});
+    }
+    // write back this tile's free nodes
+    if (lane < nn) st_l2(u + (size_t)(bj + e0 / TW) * n + bi + e0 % TW,
+                         su[(R + e0 / TW) * W + (R + e0 % TW)]);
+    if (lane + 32 < nn) st_l2(u + (size_t)(bj + e1 / TW) * n + bi + e1 % TW,
+                              su[(R + e1 / TW) * W + (R + e1 % TW)]);
+    *nn_out = nn;
+    return tmax;
+}
+
 // ------------------------------------------------- one warp per TW x TH tile
 // Each warp owns one tile per visit: it stages the tile and its halo in its own
 // slice of shared memory and updates the tile's free nodes one after another in
@@ -337,34 +652,11 @@ k_wtiles(TileArgs a) {
             const int b = a.tile_inst ? a.tile_inst[t] : 0;
             if (a.inst_active && !a.inst_active[b]) continue;
             const TileInst& I = a.insts[b];
-            const GridView& g = I.g;
-            const int n = g.n;
-            const int R = I.R;
-            const int W = TW + 2 * R;
-            const int H = TH + 2 * R;
-            T* u;
-            if constexpr (sizeof(T) == 4) u = I.u32; else u = I.u64;
             const int ar = I.act_radius;
             const int aw = 2 * ar + 1;
             const int nnb = aw * aw;
             const int tl = t - I.tile_off;
             const int tcx = tl % I.ntx, tcy = tl / I.ntx;
-            const int bi = tcx * TW, bj = tcy * TH;
-            const int gx0 = bi - R, gy0 = bj - R;
-            for (int e = lane; e < W * H; e += 32) {
-                const int ey = e / W, ex = e - ey * W;
-                const int gx = min(max(gx0 + ex, 0), n - 1);
-                const int gy = min(max(gy0 + ey, 0), n - 1);
-                su[e] = ld_l2(u + (size_t)gy * n + gx);
-            }
-            const int nn = a.wt_count[t];
-            const int* tn = a.nodes + (size_t)t * kWarpTileNodes;
-            const float* tsp = a.slot_speed + (size_t)t * kWarpTileNodes;
-            // tile-local indices e (row-major TW x TH) of the nodes, in visiting order
-            const int e0 = lane < nn ? tn[lane] : 0;
-            const int e1 = lane + 32 < nn ? tn[lane + 32] : 0;
-            const float c0 = lane < nn ? tsp[lane] : 0.0f;
-            const float c1 = lane + 32 < nn ? tsp[lane + 32] : 0.0f;
             // this lane's neighbour tile (lane < nnb): its wave decides the step it
             // would be queued for; -1 = none
             int nbw = -1;
@@ -375,8 +667,6 @@ k_wtiles(TileArgs a) {
                     if (w <= step) nbw = w;
                 }
             }
-            __syncwarp();
-            float tmax = 0.0f;
             int old = 0x7fffffff;    // stamp before this visit claimed the neighbour
             bool claimed = false;
             auto claim = [&]() {
@@ -390,193 +680,8 @@ k_wtiles(TileArgs a) {
                     old = atomicMax(a.stamp + I.tile_off + ny * I.ntx + nx, tgt);
                 }
             };
-            // staged window inside the grid: the projection is the identity
-            const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + W <= n && gy0 + H <= n;
-            auto visit = [&](auto clamp_tag) {
-              constexpr bool CL = decltype(clamp_tag)::value;
-              for (int sw = 0; sw < a.local_sweeps; ++sw) {
-                for (int q = 0; q < nn; ++q) {
-                    const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
-                    const T c = (T)__shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
-                    const int ex = e % TW, ey = e / TW;
-                    const int i = bi + ex, j = bj + ey;
-                    T* base = su + (R + ey) * W + (R + ex);
-                    const T uk = base[0];
-                    T bx = T(0), by = T(0);
-                    if (g.drift) {
-                        const float2 bb = g.drift[j * n + i];
-                        bx = (T)bb.x;
-                        by = (T)bb.y;
-                    }
-                    auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
-                    T N, Dn;
-                    int M;
-                    best_over_controls<T, SIG, CL>(g, a.scheme, i, j, uk, c, bx, by, lane, 32, C,
-                                                   U, N, Dn, M);
-                    T du;
-                    if constexpr (sizeof(T) == 4) {
-                        du = warp_min_increment(N, Dn, M);
-                    } else {
-                        warp_argmin<T>(N, Dn, M);
-                        du = N / Dn;
-                    }
-                    if (lane == 0) base[0] = uk + du;
-                    __syncwarp();
-                    tmax = fmaxf(tmax, inc_to_float(fabs(du)));
-                    if (!claimed && tmax > a.tol) claim();
-                }
-              }
-            };
-            // FP32, no drift, at most one control per lane: the geometry of node
-            // q + 1 is formed during node q (software pipelining)
-            auto visit32 = [&](auto clamp_tag, auto nol_tag) {
-              constexpr bool CL = decltype(clamp_tag)::value;
-              constexpr bool NOL = decltype(nol_tag)::value;
-              const float s = g.s32, beta = g.beta32, hl = g.hl32;
-              const float bq = SIG ? beta * 0.25f : beta;
-              const float omb = 1.0f - beta;
-              const bool has = lane < na;
-              const float2 ac = has ? g.ctrl32[lane] : make_float2(0.0f, 0.0f);
-              auto node_geo = [&](int q, int& kb) {
-                  const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
-                  const float c = __shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
-                  const int ex = e % TW, ey = e / TW;
-                  kb = (R + ey) * W + (R + ex);
-                  return geo32<SIG, CL, NOL>(g, a.scheme, s * c, bq, bi + ex, bj + ey, kb, W, ac);
-              };
-              float* sf = reinterpret_cast<float*>(su);
-              for (int sw = 0; sw < a.local_sweeps; ++sw) {
-                int kbn;
-                Geo32<SIG> gn = node_geo(0, kbn);
-                for (int q = 0; q < nn; ++q) {
-                    const Geo32<SIG> gc = gn;
-                    const int kb = kbn;
-                    gn = node_geo(min(q + 1, nn - 1), kbn);
-                    const float uk = sf[kb];
-                    const float cc0 = fmaf(-omb, uk, hl);
-                    float Sd;
-                    if constexpr (SIG) {
-                        Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
-                              bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
-                             (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
-                              bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
-                    } else {
-                        Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
-                    }
-                    const float N = fmaf(bq, Sd, cc0);
-                    float v;
-                    if constexpr (NOL)
-                        v = has ? N : INFINITY;
-                    else
-                        v = (has && gc.rD > 0.0f) ? N * gc.rD : INFINITY;
-                    const float du = order_val(__reduce_min_sync(0xffffffffu, order_key(v)));
-                    if (lane == 0) sf[kb] = uk + du;
-                    __syncwarp();
-                    tmax = fmaxf(tmax, fabsf(du));
-                    if (!claimed && tmax > a.tol) claim();
-                }
-              }
-            };
-            // FP32, constant coefficients: the tile's nodes 32 at a time, one per
-            // lane, each lane evaluating every control itself (no cross-lane
-            // reduction on the chain).  The 32 nodes of a group read each other's
-            // previous values; the groups follow each other in u_hat order.
-            auto visit_ln = [&](auto clamp_tag, auto nol_tag) {
-              constexpr bool CL = decltype(clamp_tag)::value;
-              constexpr bool NOL = decltype(nol_tag)::value;
-              const float s = g.s32, beta = g.beta32, hl = g.hl32;
-              const float bq = SIG ? beta * 0.25f : beta;
-              const float omb = 1.0f - beta;
-              float* sf = reinterpret_cast<float*>(su);
-              const float2* sc = reinterpret_cast<const float2*>(sctrl);
-              for (int sw = 0; sw < a.local_sweeps; ++sw) {
-                for (int hg = 0; hg * 32 < nn; ++hg) {
-                    const bool act = lane + 32 * hg < nn;
-                    const int e = hg ? e1 : e0;
-                    const float c = hg ? c1 : c0;
-                    const int ex = e % TW, ey = e / TW;
-                    const int kb = (R + ey) * W + (R + ex);
-                    float uk = 0.0f, du = 0.0f;
-                    if (act) {
-                        uk = sf[kb];
-                        const float cc0 = fmaf(-omb, uk, hl);
-                        float bx = 0.0f, by = 0.0f;
-                        if (g.drift) {
-                            const float2 bb = g.drift[(bj + ey) * n + bi + ex];
-                            bx = bb.x;
-                            by = bb.y;
-                        }
-                        float best = INFINITY;
-#pragma unroll 2
-                        for (int m = 0; m < na; ++m) {
-                            const float2 am = sc[m];
-                            // the foot's drift c a + b, formed as in the other visits
-                            const float2 f = make_float2(fmaf(c, am.x, bx), fmaf(c, am.y, by));
-                            const Geo32<SIG> gc = geo32<SIG, CL, NOL>(g, a.scheme, s, bq, bi + ex,
-                                                                      bj + ey, kb, W, f);
-                            float Sd;
-                            if constexpr (SIG) {
-                                Sd = (bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk) +
-                                      bil32(sf, gc.o[1], W, gc.fx[1], gc.fy[0], uk)) +
-                                     (bil32(sf, gc.o[2], W, gc.fx[2], gc.fy[1], uk) +
-                                      bil32(sf, gc.o[3], W, gc.fx[2], gc.fy[2], uk));
-                            } else {
-                                Sd = bil32(sf, gc.o[0], W, gc.fx[0], gc.fy[0], uk);
-                            }
-                            const float N = fmaf(bq, Sd, cc0);
-                            if constexpr (NOL)
-                                best = fminf(best, N);
-                            else
-                                best = fminf(best, gc.rD > 0.0f ? N * gc.rD : INFINITY);
-                        }
-                        du = best;
-                    }
-                    __syncwarp();
-                    if (act) sf[kb] = uk + du;
-                    __syncwarp();
-                    // |du| >= 0: its bits order like the values
-                    const float gm = __uint_as_float(__reduce_max_sync(0xffffffffu,
-                                                                       __float_as_uint(fabsf(du))));
-                    tmax = fmaxf(tmax, gm);
-                    if (!claimed && tmax > a.tol) claim();
-                }
-              }
-            };
-            bool piped = false;
-            if constexpr (sizeof(T) == 4) {
-                // no self weight: scheme 2 everywhere, a wide diffusion in interior tiles
-                const bool nol = a.no_self == 2 || (a.no_self == 1 && interior);
-                if (a.node_lanes && !g.gen) {
-                    piped = true;
-                    if (interior) {
-                        if (nol) visit_ln(std::false_type{}, std::true_type{});
-                        else visit_ln(std::false_type{}, std::false_type{});
-                    } else {
-                        if (nol) visit_ln(std::true_type{}, std::true_type{});
-                        else visit_ln(std::true_type{}, std::false_type{});
-                    }
-                } else if (g.drift == nullptr && na <= 32 && !g.gen) {
-                    piped = true;
-                    if (interior) {
-                        if (nol) visit32(std::false_type{}, std::true_type{});
-                        else visit32(std::false_type{}, std::false_type{});
-                    } else {
-                        if (nol) visit32(std::true_type{}, std::true_type{});
-                        else visit32(std::true_type{}, std::false_type{});
-                    }
-                }
-            }
-            if (!piped) {
-                if (interior)
-                    visit(std::false_type{});
-                else
-                    visit(std::true_type{});
-            }
-            // write back this tile's free nodes
-            if (lane < nn) st_l2(u + (size_t)(bj + e0 / TW) * n + bi + e0 % TW,
-                                 su[(R + e0 / TW) * W + (R + e0 % TW)]);
-            if (lane + 32 < nn) st_l2(u + (size_t)(bj + e1 / TW) * n + bi + e1 % TW,
-                                      su[(R + e1 / TW) * W + (R + e1 % TW)]);
+            int nn = 0;
+            const float tmax = wt_visit<T, SIG, TW, TH>(a, t, su, sctrl, na, lane, claim, &nn);
             if (claimed) {
                 // lanes 0..31 claimed above; tiles past the 32nd neighbour (radius > 2)
                 // are claimed here
@@ -640,6 +745,234 @@ k_wtiles(TileArgs a) {
             a.res->last_increment = last_max;
         }
     }
+}
+
+// ---------------------------------------- asynchronous worklist (schedule 3)
+// The same tile visits without a grid-wide barrier: warps take tiles from one
+// FIFO ring and put tiles back as their inputs change, so no warp idles while
+// there is work.  The causal order of Section 4.2 is kept for the first visits:
+// a tile is released for its first visit once every neighbour within the
+// interpolation reach (act_radius tiles) with a lower wave has made its first
+// visit (a counter per tile).  After that, a visit that changed some node by
+// more than tol puts back every released neighbour and itself; a tile is in
+// the ring at most once (per-tile state: idle, queued, being visited, being
+// visited and put back again).  The solve ends when no tile is queued or being
+// visited.  Every wait is bounded by a.timeout_ns of global time.
+
+__device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acq_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// tag of ring position pos (never 0, so 0 marks an empty entry)
+__device__ __forceinline__ unsigned int aq_tag(unsigned long long pos) {
+    return (unsigned int)(pos & 0x7fffffffull) | 0x80000000u;
+}
+
+__device__ __forceinline__ void aq_fail(const TileArgs& a, int code) {
+    atomicCAS(&a.sync->err, 0, code);
+    atomicExch(&a.actl->stop, 1);
+}
+
+// append tile t (its state already says queued)
+__device__ __forceinline__ void aq_enqueue(const TileArgs& a, int t) {
+    const unsigned long long pos = atomicAdd(&a.actl->tail, 1ull);
+    unsigned long long* slot = a.aqueue + (pos & (unsigned long long)(a.aq_cap - 1));
+    // the entry cap positions back has been taken by now (at most nt entries are
+    // queued and at most one ticket per warp waits ahead of the tail)
+    const unsigned long long t0 = global_ns();
+    while (ld_acq_u64(slot) != 0ull) {
+        if (global_ns() - t0 > a.timeout_ns) {
+            aq_fail(a, HJB_ERR_TIMEOUT);
+            return;
+        }
+        __nanosleep(32);
+    }
+    st_rel_u64(slot, ((unsigned long long)aq_tag(pos) << 32) | (unsigned int)t);
+}
+
+// tile t needs a visit: idle -> queued (appended), being visited -> put back
+// after the visit; already queued: nothing
+__device__ __forceinline__ void aq_push(const TileArgs& a, int t) {
+    int s = ld_acq_s32(a.astate + t);
+    for (int it = 0; it < 64; ++it) {
+        if (s == 0) {
+            const int o = atomicCAS(a.astate + t, 0, 1);
+            if (o == 0) {
+                atomicAdd(&a.actl->pending, 1);
+                aq_enqueue(a, t);
+                return;
+            }
+            s = o;
+        } else if (s == 2) {
+            const int o = atomicCAS(a.astate + t, 2, 3);
+            if (o == 2) return;
+            s = o;
+        } else {
+            return;
+        }
+    }
+}
+
+// next ticket's tile, or -1 when nothing is queued or being visited (or on stop)
+__device__ __forceinline__ int aq_pop(const TileArgs& a) {
+    if (ld_acq_s32(&a.actl->stop)) return -1;
+    const unsigned long long pos = atomicAdd(&a.actl->head, 1ull);
+    unsigned long long* slot = a.aqueue + (pos & (unsigned long long)(a.aq_cap - 1));
+    const unsigned int tag = aq_tag(pos);
+    const unsigned long long t0 = global_ns();
+    // poll the own entry; the shared words only every 8th time, with a growing
+    // pause (the waiting warps must not crowd L2 while others compute)
+    for (unsigned int spin = 0;; ++spin) {
+        const unsigned long long v = ld_acq_u64(slot);
+        if ((unsigned int)(v >> 32) == tag) {
+            st_rel_u64(slot, 0ull);
+            return (int)(unsigned int)v;
+        }
+        if ((spin & 7u) == 7u) {
+            if (ld_acq_s32(&a.actl->pending) == 0 || ld_acq_s32(&a.actl->stop)) return -1;
+            if (global_ns() - t0 > a.timeout_ns) {
+                aq_fail(a, HJB_ERR_TIMEOUT);
+                return -1;
+            }
+        }
+        __nanosleep(spin < 8 ? 64u : (spin < 32 ? 256u : 1024u));
+    }
+}
+
+// per tile: state idle; first-visit counter = neighbours (act box) of lower wave
+__global__ void k_async_deps(TileArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nt) return;
+    a.astate[t] = 0;
+    const int wt = a.tile_wave[t];
+    if (wt == 0x7fffffff) {        // no free node: never visited
+        a.adeps[t] = -2;
+        return;
+    }
+    const TileInst& I = a.insts[a.tile_inst ? a.tile_inst[t] : 0];
+    const int ar = I.act_radius;
+    const int tl = t - I.tile_off;
+    const int tcx = tl % I.ntx, tcy = tl / I.ntx;
+    int cnt = 0;
+    for (int dy = -ar; dy <= ar; ++dy)
+        for (int dx = -ar; dx <= ar; ++dx) {
+            const int nx = tcx + dx, ny = tcy + dy;
+            if (nx < 0 || ny < 0 || nx >= I.ntx || ny >= I.nty) continue;
+            const int wn = a.tile_wave[I.tile_off + ny * I.ntx + nx];
+            if (wn != 0x7fffffff && wn < wt) ++cnt;
+        }
+    a.adeps[t] = cnt;
+}
+
+// queue the tiles released from the start, in tile_list (wave) order per warp
+__global__ void k_async_seed(TileArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int listed = a.wave_off[a.n_waves];
+    int t = -1;
+    if (i < listed) {
+        t = a.tile_list[i];
+        if (a.adeps[t] != 0 || (a.inst_active && !a.inst_active[a.tile_inst ? a.tile_inst[t] : 0])) t = -1;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, t >= 0);
+    if (m == 0u) return;
+    unsigned long long base = 0;
+    if (lane == 0) {
+        base = atomicAdd(&a.actl->tail, (unsigned long long)__popc(m));
+        atomicAdd(&a.actl->pending, __popc(m));
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (t >= 0) {
+        const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+        a.astate[t] = 1;
+        st_rel_u64(a.aqueue + (pos & (unsigned long long)(a.aq_cap - 1)),
+                   ((unsigned long long)aq_tag(pos) << 32) | (unsigned int)t);
+    }
+}
+
+template <bool SIG, int TW, int TH>
+__global__ void __launch_bounds__(WTBlock<float>::threads)
+k_wtiles_async(TileArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int na = a.insts[0].g.na;
+    float2* sctrl = reinterpret_cast<float2*>(smem);
+    const size_t ctrl_bytes = ((size_t)na * sizeof(float2) + 15) & ~(size_t)15;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float* su = reinterpret_cast<float*>(smem + ctrl_bytes) + (size_t)warp * a.max_wh;
+    __shared__ unsigned long long s_nodes;
+    for (int m = threadIdx.x; m < na; m += blockDim.x) sctrl[m] = a.insts[0].g.ctrl32[m];
+    if (threadIdx.x == 0) s_nodes = 0ull;
+    __syncthreads();
+    unsigned long long cnt = 0;
+    auto nohook = [] {};
+    while (true) {
+        int t = -1;
+        if (lane == 0) {
+            t = aq_pop(a);
+            if (t >= 0) {
+                if (atomicAdd(&a.actl->visits, 1ull) >= (unsigned long long)a.max_visits) {
+                    atomicExch(&a.actl->stop, 1);   // the visit cap: not converged
+                    t = -1;
+                } else {
+                    atomicExch(a.astate + t, 2);
+                }
+            }
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t < 0) break;
+        int first = 0;
+        if (lane == 0) first = atomicExch(a.adeps + t, -1) == 0;
+        first = __shfl_sync(0xffffffffu, first, 0);
+        int nn = 0;
+        const float tmax = wt_visit<float, SIG, TW, TH>(a, t, su, sctrl, na, lane, nohook, &nn);
+        // the tile's new values are in L2 before any neighbour is put back
+        __threadfence();
+        const bool changed = tmax > a.tol;
+        const TileInst& I = a.insts[a.tile_inst ? a.tile_inst[t] : 0];
+        const int ar = I.act_radius;
+        const int aw = 2 * ar + 1;
+        const int tl = t - I.tile_off;
+        const int tcx = tl % I.ntx, tcy = tl / I.ntx;
+        const int wt = a.tile_wave[t];
+        if (first || changed) {
+            for (int q = lane; q < aw * aw; q += 32) {
+                const int nx = tcx + q % aw - ar, ny = tcy + q / aw - ar;
+                if (nx < 0 || ny < 0 || nx >= I.ntx || ny >= I.nty) continue;
+                const int nb = I.tile_off + ny * I.ntx + nx;
+                const int wn = a.tile_wave[nb];
+                if (wn == 0x7fffffff) continue;
+                // release: this was the last lower-wave neighbour's first visit
+                if (first && nb != t && wn > wt && atomicSub(a.adeps + nb, 1) == 1) aq_push(a, nb);
+                // put back the released neighbours (and this tile) after a change
+                if (changed && ld_acq_s32(a.adeps + nb) <= 0) aq_push(a, nb);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int o = atomicCAS(a.astate + t, 2, 0);
+            if (o == 3) {
+                atomicExch(a.astate + t, 1);
+                aq_enqueue(a, t);
+            } else {
+                atomicSub(&a.actl->pending, 1);
+            }
+            cnt += (unsigned long long)nn * a.local_sweeps;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && cnt) atomicAdd(&s_nodes, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&a.res->nodes, s_nodes);
 }
 
 // Build of the warp tiles: one warp per tile gathers the tile's free nodes,
@@ -967,6 +1300,32 @@ cudaError_t launch_wtiles(const TileArgs& a, bool f64, bool sig, int blocks, cud
                         : launch_wtiles_impl<double, false>(a, blocks, st);
     return sig ? launch_wtiles_impl<float, true>(a, blocks, st)
                : launch_wtiles_impl<float, false>(a, blocks, st);
+}
+
+template <bool SIG>
+auto wtile_async_kernel(int shape) -> void (*)(TileArgs) {
+    switch (shape) {
+        case 2: return k_wtiles_async<SIG, 8, 4>;
+        case 3: return k_wtiles_async<SIG, 4, 4>;
+        default: return k_wtiles_async<SIG, 8, 8>;
+    }
+}
+
+cudaError_t launch_wtiles_async(const TileArgs& a, bool sig, int blocks, cudaStream_t st) {
+    count_launches(3);
+    k_async_deps<<<(a.nt + 255) / 256, 256, 0, st>>>(a);
+    k_async_seed<<<(a.nt + 255) / 256, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = wtile_smem(false, a.g.na, a.max_wh);
+    auto kern = sig ? wtile_async_kernel<true>(a.warp_tiles) : wtile_async_kernel<false>(a.warp_tiles);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {(void*)&a};
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(WTBlock<float>::threads), args,
+                                       smem, st);
 }
 
 cudaError_t launch_wtile_build(int shape, const TileInst* insts, const int32_t* tile_inst, int nt,

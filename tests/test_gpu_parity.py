@@ -318,7 +318,11 @@ SCHEDULES = [dict(schedule=0, tile_shape=0), dict(schedule=0, tile_shape=1),
              dict(schedule=0, tile_shape=2), dict(schedule=0, tile_shape=0, tile_waves=8, tile_period=4),
              dict(schedule=0, resort_passes=1), dict(schedule=0, local_sweeps=2),
              dict(schedule=1, band_group=1), dict(schedule=1, band_group=4, wave_warps=1024),
-             dict(schedule=2, tile_waves=8, tile_period=4)]
+             dict(schedule=2, tile_waves=8, tile_period=4),
+             dict(schedule=0, visit=1), dict(schedule=0, visit=2, local_sweeps=2),
+             dict(schedule=0, tile_shape=1, visit=2),
+             dict(schedule=3), dict(schedule=3, tile_shape=1), dict(schedule=3, visit=2, local_sweeps=3),
+             dict(schedule=3, tile_shape=2)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES, ids=[str(s) for s in SCHEDULES])
