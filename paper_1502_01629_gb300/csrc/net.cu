@@ -15,8 +15,8 @@
 // FP32 in tensor memory) and commits to an mbarrier; the epilogue reads the
 // accumulator with tcgen05.ld and applies bias, ReLU or the ReLU mask of the
 // backward pass.  The input gradient (dgrad) is the same kernel with the
-// weights flipped and transposed; the weight gradient (wgrad) is a blocked
-// reduction over pixels on the FP32 cores.
+// weights flipped and transposed; the weight gradient (wgrad) is a third
+// implicit GEMM on the tensor cores whose reduction runs over the pixels.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -203,6 +203,138 @@ k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int tot
     if (tid < cout && db && bacc != 0.0f) atomicAdd(db + tid, bacc);
 }
 
+// --------------------------------------------------- wgrad on tensor cores
+// dW[n, m] = sum_p X[p, m] dy[p, n] with X the 3x3 (dilated) im2col of x
+// (m = t * CIN + ci) is a GEMM whose reduction runs over the pixels:
+// D[m, n] = sum_p A[m, p] B[n, p] with A = X^T and B = dy^T.  A CTA takes a chunk
+// of pixels in tiles of 128; per tile its threads transpose x and dy into the
+// canonical K-major layout of A (MT tiles of 128 rows m, the pixels along K) and
+// B (NPAD rows n), one thread issues MT x 8 tcgen05.mma (K = 16 pixels each)
+// accumulating D in tensor memory across the chunk, and the epilogue adds the
+// chunk's partial dW (and, from a row of ones in A, the bias gradient
+// sum_p dy[p, n]) to dw / db with FP32 atomics.
+template <int CIN, int NPAD>
+struct WgradShape {
+    static constexpr int K = 9 * CIN;                 // dW row length (taps x channels)
+    static constexpr int MT = (K + 1 + 127) / 128;    // 128-row tiles of A (row K: ones)
+    static constexpr int TMC = MT * NPAD <= 64 ? 64 : (MT * NPAD <= 128 ? 128 : 256);
+    static constexpr size_t smem = (size_t)MT * 128 * 128 * 2 + (size_t)NPAD * 128 * 2;
+};
+
+template <int CIN, int NPAD>
+__global__ void __launch_bounds__(kConvThreads)
+k_conv3x3_wgrad_tc(const bf16* __restrict__ x, const bf16* __restrict__ dy, int total, int H, int W,
+                   int dil, int chunk, int cout, float* dw, float* db, int* err) {
+    using S = WgradShape<CIN, NPAD>;
+    constexpr int K = S::K, MT = S::MT;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                               // MT x [128 x 128] bf16
+    unsigned char* sB = smem + (size_t)MT * 128 * 128 * 2;  // NPAD x 128 bf16
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_taddr;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int HW = H * W;
+    const long long pbeg = (long long)blockIdx.x * chunk;
+    const long long pend = pbeg + chunk < total ? pbeg + chunk : (long long)total;
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    if (warp == 0) tc::tmem_alloc<S::TMC>(&s_taddr);
+    // rows past K + 1 stay zero for the whole chunk
+    for (int i = tid; i < (int)(S::smem / 16); i += kConvThreads)
+        reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = s_taddr;
+    const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NPAD);
+    bool ok = true;
+    uint32_t phase = 0;
+    int tiles = 0;
+    for (long long s = pbeg; s < pend; s += 128, ++tiles) {
+        // A: element (m, q) = x at pixel s + q shifted by tap t = m / CIN, channel
+        // m % CIN (0 outside the image or past the chunk); row K = 1 for a pixel
+        for (int e = tid; e < 128 * 9 * (CIN / 8); e += kConvThreads) {
+            const int q = e % 128, rest = e / 128;
+            const int t = rest / (CIN / 8), cc = rest - t * (CIN / 8);
+            const long long p = s + q;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (p < pend) {
+                const int b = (int)(p / HW), r = (int)(p - (long long)b * HW);
+                const int yy = r / W + (t / 3 - 1) * dil, xq = r % W + (t % 3 - 1) * dil;
+                if (yy >= 0 && yy < H && xq >= 0 && xq < W)
+                    v = *reinterpret_cast<const uint4*>(x + ((size_t)b * HW + (size_t)yy * W + xq) * CIN + cc * 8);
+            }
+            const bf16* hv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int m = t * CIN + cc * 8 + j;
+                *reinterpret_cast<bf16*>(sA + (size_t)(m >> 7) * 128 * 128 * 2 + tc::canon_offset(m & 127, q, 128)) =
+                    hv[j];
+            }
+        }
+        if (tid < 128) {
+            const int m = K;
+            *reinterpret_cast<bf16*>(sA + (size_t)(m >> 7) * 128 * 128 * 2 + tc::canon_offset(m & 127, tid, 128)) =
+                __float2bfloat16(s + tid < pend ? 1.0f : 0.0f);
+        }
+        // B: element (n, q) = dy[s + q, n]
+        for (int e = tid; e < 128 * (NPAD / 8); e += kConvThreads) {
+            const int q = e % 128, c8 = e / 128;
+            const long long p = s + q;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (p < pend) v = *reinterpret_cast<const uint4*>(dy + (size_t)p * NPAD + c8 * 8);
+            const bf16* hv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<bf16*>(sB + tc::canon_offset(c8 * 8 + j, q, 128)) = hv[j];
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            for (int mt = 0; mt < MT; ++mt)
+                for (int ks = 0; ks < 8; ++ks) {
+                    const uint64_t ad =
+                        tc::desc_noswizzle(a0 + mt * 128 * 128 * 2 + ks * 256, 128, 16 * 128);
+                    const uint64_t bd = tc::desc_noswizzle(b0 + ks * 256, 128, 16 * 128);
+                    tc::mma_bf16(taddr + mt * NPAD, ad, bd, idesc, (tiles > 0 || ks > 0) ? 1u : 0u);
+                }
+            tc::mma_commit(&mbar);
+        }
+        // the operands are overwritten by the next tile: wait for the MMAs
+        ok = ok && tc::mbar_wait(&mbar, phase, kMmaWaitIters);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (!ok) break;
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+    if (ok && tiles > 0) {
+        // D rows m = mt * 128 + warp * 32 + lane, columns n
+        for (int mt = 0; mt < MT; ++mt) {
+            const int m = mt * 128 + warp * 32 + lane;
+            for (int c = 0; c < NPAD / 16; ++c) {
+                uint32_t r[16];
+                tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + mt * NPAD + c * 16, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int n = c * 16 + q;
+                    const float v = __uint_as_float(r[q]);
+                    if (n >= cout || v == 0.0f) continue;
+                    if (m < K)
+                        atomicAdd(dw + (size_t)n * K + m, v);
+                    else if (m == K && db)
+                        atomicAdd(db + n, v);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc<S::TMC>(taddr);
+}
+
 // -------------------------------------------------------- weight packing
 // forward B operand: (n, k = t * CINP + ci) = w[n, t, ci] (w: [cout][9][cin]), zero padded
 __global__ void k_pack_fwd(const float* __restrict__ w, int cout, int cin, int CINP, int NPAD,
@@ -331,7 +463,19 @@ cudaError_t conv_launch(int cinp, int npad, bool f32, const bf16* x, const uint8
 
 template <int CIN, int NPAD>
 cudaError_t wgrad_impl(const bf16* x, const bf16* dy, int total, int H, int W, int dil, int cout, float* dw,
-                       float* db, cudaStream_t st) {
+                       float* db, int* err, cudaStream_t st) {
+    if (err) {
+        // tensor cores: D = X^T dy accumulated in tensor memory over a chunk of pixels
+        using S = WgradShape<CIN, NPAD>;
+        auto kern = k_conv3x3_wgrad_tc<CIN, NPAD>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+        if (e != cudaSuccess) return e;
+        const int chunk = 4096;
+        count_launches(1);
+        kern<<<(total + chunk - 1) / chunk, kConvThreads, S::smem, st>>>(x, dy, total, H, W, dil, chunk, cout,
+                                                                         dw, db, err);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)32 * (NPAD + 9 * CIN) * sizeof(float);
     auto kern = k_conv3x3_wgrad<CIN, NPAD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -342,10 +486,12 @@ cudaError_t wgrad_impl(const bf16* x, const bf16* dy, int total, int H, int W, i
     return cudaGetLastError();
 }
 
+// err != nullptr: the tensor-core kernel (its bounded MMA wait sets *err on
+// expiry); nullptr: the FP32 CUDA-core reduction
 cudaError_t wgrad_launch(int cinp, int npad, const bf16* x, const bf16* dy, int total, int H, int W, int dil,
-                         int cout, float* dw, float* db, cudaStream_t st) {
+                         int cout, float* dw, float* db, int* err, cudaStream_t st) {
 #define HJB_WG(C, N) \
-    if (cinp == C && npad == N) return wgrad_impl<C, N>(x, dy, total, H, W, dil, cout, dw, db, st);
+    if (cinp == C && npad == N) return wgrad_impl<C, N>(x, dy, total, H, W, dil, cout, dw, db, err, st);
     HJB_WG(16, 32) HJB_WG(16, 48) HJB_WG(32, 32) HJB_WG(32, 48) HJB_WG(48, 32) HJB_WG(48, 48)
 #undef HJB_WG
     return cudaErrorInvalidValue;
@@ -607,7 +753,7 @@ int hjb_net_train_step(hjb_net* nt, int32_t batch, const void* x, const float* t
         const LayerShape& L = kShape[l];
         const bf16* xin = l == 0 ? x0 : nt->act[l];
         NCU(wgrad_launch(L.cinp, L.npad, xin, dzl, total, nt->H, nt->W, L.dil, L.cout,
-                         nt->grads + param_offset_w(l), nt->grads + param_offset_b(l), nt->st));
+                         nt->grads + param_offset_w(l), nt->grads + param_offset_b(l), nt->err, nt->st));
         if (l > 0) {
             bf16* dnext = nt->dz[l & 1];
             NCU(conv_launch(L.npad, 32, false, dzl, nt->wdgr[l], nullptr, 0, 0, nt->act[l], total, nt->H,
@@ -794,9 +940,14 @@ int hjb_conv3x3_wgrad(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t 
     NCU(cudaMalloc(&B.b, sizeof(float) * cout));
     NCU(cudaMemset(B.w, 0, sizeof(float) * cout * 9 * cinp));
     NCU(cudaMemset(B.b, 0, sizeof(float) * cout));
-    NCU(wgrad_launch(cinp, npad, B.x, B.y, (int)P, H, W, dil, cout, B.w, B.b, nullptr));
+    NCU(cudaMalloc(&B.err, sizeof(int)));
+    NCU(cudaMemset(B.err, 0, sizeof(int)));
+    NCU(wgrad_launch(cinp, npad, B.x, B.y, (int)P, H, W, dil, cout, B.w, B.b, B.err, nullptr));
     std::vector<float> h((size_t)cout * 9 * cinp);
     NCU(cudaMemcpy(h.data(), B.w, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    int e = 0;
+    NCU(cudaMemcpy(&e, B.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return nfail(HJB_ERR_TIMEOUT, "tensor-core wait exceeded its limit");
     for (int n = 0; n < cout; ++n)
         for (int t = 0; t < 9; ++t)
             for (int q = 0; q < cin; ++q) dw[((size_t)n * 9 + t) * cin + q] = h[((size_t)n * 9 + t) * cinp + q];

@@ -6,6 +6,7 @@ Calls only ``oracle/`` (the FP64 CPU oracle) and the seeded input generators of
 
     python tests/golden/make_full_size.py patchy1025    # three files, one per sigma
     python tests/golden/make_full_size.py large4097     # sampled nodes only
+    python tests/golden/make_full_size.py batched512    # 256 sampled nodes per instance
 
 What is solved: the fixed point u* of eq. SLscheme3 (Section 3; the same fixed
 point as eq. SLscheme2 by the Section 3 proof) on the workload's grid, by the
@@ -40,7 +41,8 @@ import numpy as np  # noqa: E402
 
 TOL = 1e-13
 SIGMAS_1025 = (0.0, 0.02, 0.1)
-N_SAMPLES = {"patchy1025": 8192, "large4097": 65536}
+N_SAMPLES = {"patchy1025": 8192, "large4097": 65536, "batched512": 256}
+BATCH_COUNT = 512
 
 
 def golden_path(name: str) -> str:
@@ -91,14 +93,49 @@ def solve_one(job):
     return f"{name}: {sweeps} sweeps, last increment {last:.2e}, residual {res:.2e}, {time.time() - t0:.0f} s"
 
 
+def solve_batch_instance(k):
+    """Instance k of the 512-instance workload (seed 1000 + k): the oracle's
+    solution at a seeded sample of its free nodes."""
+    import hjb_inputs as hi
+    import oracle
+    inst = hi.batched_instance(1000 + k)
+    pre = oracle.patchy_precompute(inst, tol_c=1e-10)
+    O = pre["fine"]
+    order = np.argsort(pre["uhat"], kind="stable")
+    u, sweeps, last = O.solve(u0=O.fix_nonfree(pre["uhat"]), scheme=3, method="gs",
+                              order=order, tol=TOL, max_sweeps=200000)
+    if sweeps < 0:
+        raise RuntimeError(f"batched instance {k}: the oracle did not reach {TOL}")
+    idx = sample_nodes(inst.mask, N_SAMPLES["batched512"], seed=20260 + k)
+    return k, idx, u[idx], sweeps, O.residual(u)
+
+
+def main_batched(workers: int):
+    t0 = time.time()
+    res = [None] * BATCH_COUNT
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for k, idx, vals, sweeps, r in pool.imap_unordered(solve_batch_instance, range(BATCH_COUNT)):
+            res[k] = (idx, vals, sweeps, r)
+    counts = np.array([r[0].size for r in res], np.int64)
+    np.savez_compressed(golden_path("batched512"),
+                        counts=counts, idx=np.concatenate([r[0] for r in res]),
+                        u64=np.concatenate([r[1] for r in res]),
+                        sweeps=np.array([r[2] for r in res], np.int64),
+                        residual=np.array([r[3] for r in res]))
+    print(f"batched512: {BATCH_COUNT} instances, max residual {max(r[3] for r in res):.2e}, "
+          f"{time.time() - t0:.0f} s", flush=True)
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "patchy1025"
     if which == "patchy1025":
         jobs = [("patchy1025", s) for s in SIGMAS_1025]
     elif which == "large4097":
         jobs = [("large4097", 0.01)]
+    elif which == "batched512":
+        return main_batched(int(argv[2]) if len(argv) > 2 else max(1, (os.cpu_count() or 2) - 1))
     else:
-        raise SystemExit("usage: make_full_size.py patchy1025|large4097")
+        raise SystemExit("usage: make_full_size.py patchy1025|large4097|batched512 [workers]")
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         for line in pool.imap_unordered(solve_one, jobs):
             print(line, flush=True)

@@ -232,20 +232,24 @@ def test_network_training_step_matches_reference_gradients(L):
     assert abs(loss[0] - lv) <= 1e-3 * max(1.0, lv) and abs(loss[1] - lc) <= 1e-3 * max(1.0, lc)
     dz = cn.bf16_round(g[..., :33])
     grads = [None] * 6
+    mags = [None] * 6
     for li in range(5, -1, -1):
         w, b = layers[li]
         grads[li] = cn.conv3x3_wgrad(acts[li], dz, dil=NET_DIL[li])
+        # sum_p |a_p| |dz_p| of every gradient entry: the scale of its rounding error
+        mags[li] = cn.conv3x3_wgrad(np.abs(acts[li]), np.abs(dz), dil=NET_DIL[li])
         if li > 0:
             dz = cn.bf16_round(cn.conv3x3_dgrad(dz, cn.bf16_round(w), acts[li], dil=NET_DIL[li]))
     ref_grad = net.pack([(gw, gb) for gw, gb in grads])
+    mag = net.pack([(mw, mb) for mw, mb in mags])
     got = net.get_grads()
-    # per layer: the gradients agree up to the bf16 rounding of the activations
-    o = 0
-    for (cin, cout) in [(16, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 33)]:
-        n = cout * 9 * cin + cout
-        a, r = got[o:o + n], ref_grad[o:o + n]
-        assert np.linalg.norm(a - r) <= 2e-2 * np.linalg.norm(r) + 1e-12, (o, np.linalg.norm(a - r), np.linalg.norm(r))
-        o += n
+    # element by element: an activation or gradient stored in BF16 may round the
+    # other way on the GPU (FP32 sums in another order), one BF16 ulp = 2^-8
+    # relative; a few such flips along the layers give at most 2^-6 of the
+    # magnitude sum of the entry, plus FP32 summation error
+    tol = 2.0 ** -6 * mag + 1e-6 * np.abs(ref_grad).max()
+    bad = np.abs(got - ref_grad) > tol
+    assert not bad.any(), (int(bad.sum()), float(np.abs(got - ref_grad)[bad].max()))
     # first Adam step: update = lr * g / (sqrt(g^2) + eps) with the GPU's own gradient
     ref_new = params - lr * got / (np.abs(got) + 1e-8)
     np.testing.assert_allclose(new, ref_new, rtol=0, atol=2e-6)
