@@ -89,12 +89,15 @@ typedef struct {
                              warp)                                                             */
     int32_t resort_passes;/* after each of the first k FP32 passes, re-sort the free nodes by
                              the current value instead of u_hat (0: never)                    */
-    int32_t schedule;     /* patch-solve schedule: 0 warp tiles (default), 1 band waves,
-                             2 block tiles                                                    */
+    int32_t schedule;     /* patch-solve schedule: 0 warp tiles (default; the FP32 phase as
+                             in 4 up to n = 3073, as in 3 above), 1 band waves, 2 block
+                             tiles, 3 warp tiles from an asynchronous worklist (no grid-wide
+                             barrier), 4 warp tiles in barrier-separated steps             */
     int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: automatic, 1 when the
                              diffusion offset sqrt(2h) sigma exceeds one cell, else 2)        */
     int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 2)         */
-    int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: 1)      */
+    int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: automatic,
+                             3 with 32-node warp-tile visits, else 1)                        */
     int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (8x8 when the
                              diffusion offset exceeds one cell, n > 2049 or more than 32
                              controls, else 8x4)                                              */
@@ -427,7 +430,9 @@ typedef struct {
     int32_t tile_shape;   /* warp tiles: 0 8x8, 1 8x4, 2 4x4, -1: 8x4 until tuned          */
     int32_t tile_waves;   /* bands per tile wave B (<= 0: 2 until tuned)                   */
     int32_t tile_period;  /* period D of the tile schedule (<= 1: 2)                       */
-    int32_t reserved;     /* must be 0                                                     */
+    int32_t schedule;     /* FP32 passes: 0 barrier-separated steps (hjb_batch_autotune may
+                             switch to 3), 3 the asynchronous worklist of hjb_desc.schedule 3,
+                             4 barrier-separated steps, never switched                       */
     double cost;          /* running cost l (> 0)                                          */
     double band_width;    /* causal band width in units of h (<= 0: 1)                    */
 } hjb_batch_desc;
@@ -479,10 +484,12 @@ int hjb_batch_solve_full(hjb_batch* b, double tol32, double tol64, int32_t max_s
                          hjb_stats* stats, double* residuals);
 
 /* hjb_batch_autotune -- runs the pre-computation once, then the FP32 patch solve
- * for each candidate schedule (tile shapes 8x8, 8x4, 4x4 x bands per wave 1, 2),
- * times each with CUDA events and keeps the fastest for later solves.  ms_out
- * (nullable, 6 doubles) gets the candidates' times in that order; shape_out /
- * waves_out (nullable) the choice. */
+ * for each candidate schedule (barrier steps with tile shapes 8x8, 8x4, 4x4 x bands
+ * per wave 1, 2; with desc.schedule 0 also the asynchronous worklist with each
+ * shape), times each with CUDA events and keeps the fastest for later solves.
+ * ms_out (nullable, 9 doubles) gets the candidates' times in that order (entries
+ * 6..8: the worklist, 0 when not tried); shape_out / waves_out (nullable) the
+ * choice (the worklist was chosen when the smallest time is among entries 6..8). */
 int hjb_batch_autotune(hjb_batch* b, double tol_c, double tol32, int32_t* shape_out,
                        int32_t* waves_out, double* ms_out);
 

@@ -70,7 +70,7 @@ class Problem:
                  scheme: int = 3, band_width: float = 1.0, band_window: int = 8,
                  band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
                  schedule: int = 0, tile_waves: int = 0, tile_period: int = 2,
-                 local_sweeps: int = 1, tile_shape: int = -1, visit: int = 0,
+                 local_sweeps: int = 0, tile_shape: int = -1, visit: int = 0,
                  drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False,
                  sigma_field: Optional[np.ndarray] = None, diffusion: int = 0,
                  cost_field: Optional[np.ndarray] = None,
@@ -276,7 +276,7 @@ class Batch:
 
     def __init__(self, instances, controls: np.ndarray, *, cost: float = 1.0, scheme: int = 3,
                  tile_shape: int = -1, tile_waves: int = 0, tile_period: int = 2,
-                 band_width: float = 1.0, stream=None):
+                 band_width: float = 1.0, schedule: int = 0, stream=None):
         self._h = None
         insts = list(instances)
         self.count = len(insts)
@@ -288,7 +288,7 @@ class Batch:
         d = BatchDesc()
         controls = _c(controls, np.float64).reshape(-1, 2)
         d.n_controls, d.scheme, d.tile_shape = controls.shape[0], scheme, tile_shape
-        d.tile_waves, d.tile_period, d.reserved = tile_waves, tile_period, 0
+        d.tile_waves, d.tile_period, d.schedule = tile_waves, tile_period, int(schedule)
         d.cost, d.band_width = cost, band_width
         # one host array per instance (hjb_batch_create_lists): the library copies
         # each into its place on the device, nothing is concatenated here
@@ -356,11 +356,15 @@ class Batch:
     def autotune(self, tol_c: float = 1e-6, tol32: float = 2.5e-7) -> dict:
         """Time the candidate tile schedules; returns the choice and the times."""
         shape, waves = ctypes.c_int32(), ctypes.c_int32()
-        ms = np.zeros(6)
+        ms = np.zeros(9)
         check(lib().hjb_batch_autotune(self._h, tol_c, tol32, ctypes.byref(shape), ctypes.byref(waves),
                                        _p(ms)), "hjb_batch_autotune")
         names = [f"{s}/B{b}" for s in ("8x8", "8x4", "4x4") for b in (1, 2)]
-        return {"tile_shape": shape.value, "tile_waves": waves.value, "ms": dict(zip(names, ms.tolist()))}
+        names += [f"{s}/worklist" for s in ("8x8", "8x4", "4x4")]
+        tried = {k: v for k, v in zip(names, ms.tolist()) if v > 0}
+        best = min(tried, key=tried.get)
+        return {"tile_shape": shape.value, "tile_waves": waves.value,
+                "schedule": 3 if best.endswith("worklist") else 4, "ms": tried}
 
     def get_value(self, index: int) -> np.ndarray:
         out = np.empty(self.ns[index] ** 2)

@@ -75,7 +75,7 @@ class BatchInst(ctypes.Structure):
 class BatchDesc(ctypes.Structure):
     _fields_ = [("n_controls", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("tile_shape", ctypes.c_int32), ("tile_waves", ctypes.c_int32),
-                ("tile_period", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tile_period", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("cost", ctypes.c_double), ("band_width", ctypes.c_double)]
 
 

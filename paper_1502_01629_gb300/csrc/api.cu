@@ -443,7 +443,7 @@ int validate_desc(const hjb_desc* d) {
     }
     if (!std::isfinite(d->band_width)) return fail(HJB_ERR_INVALID_ARG, "bad band_width");
     if (d->resort_passes < 0) return fail(HJB_ERR_INVALID_ARG, "resort_passes must be >= 0");
-    if (d->schedule < 0 || d->schedule > 3) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0, 1, 2 or 3");
+    if (d->schedule < 0 || d->schedule > 4) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0 .. 4");
     if (d->tile_shape < -1 || d->tile_shape > 2)
         return fail(HJB_ERR_INVALID_ARG, "tile_shape must be -1 (auto), 0 (8x8), 1 (8x4) or 2 (4x4)");
     if (d->visit < 0 || d->visit > 2)
@@ -580,9 +580,13 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         return bail(fail(HJB_ERR_INVALID_ARG, "obstacles need lambda > 0 (their value is l/lambda + h l)"));
 
     p->desc = *desc;
-    if (p->desc.schedule == 3) {
-        // the warp tiles of schedule 0, the FP32 phase from the asynchronous worklist
-        p->async = true;
+    // warp tiles: the FP32 phase steps through waves between grid-wide barriers
+    // (schedule 4) or runs from the asynchronous worklist (schedule 3); schedule 0
+    // takes the worklist above 3073 nodes per side, where the steps hold enough
+    // tiles that barrier waits and idle warps outweigh its extra visits (measured
+    // on the 64-control obstacle workload: 4097^2 241 vs 302 ms, 2049^2 66 vs 55 ms)
+    if (p->desc.schedule == 3 || p->desc.schedule == 4 || p->desc.schedule == 0) {
+        p->async = p->desc.schedule == 3 || (p->desc.schedule == 0 && desc->n > 3073);
         p->desc.schedule = 0;
     }
     if (p->desc.scheme == 0) p->desc.scheme = 3;
@@ -590,7 +594,6 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
     if (p->desc.band_group <= 0) p->desc.band_group = 1;
     if (p->desc.tile_period <= 1) p->desc.tile_period = 2;
-    if (p->desc.local_sweeps <= 0) p->desc.local_sweeps = 1;
     p->n = n;
     p->N = (int)N;
     p->na = na;
@@ -638,6 +641,11 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         // a wide diffusion reaches past the tile's own nodes, so ordering them
         // within a visit gains little: update 32 of them at a time
         if (p->desc.visit == 0) p->desc.visit = wide ? 2 : 1;
+        // node-per-lane visits sweep a tile three times per visit (the group of
+        // 32 is a Jacobi step; repeating it at the tile costs less than more
+        // pipeline steps: 1025^2, sigma 0.1: 1, 2, 3 sweeps 47.5, 41.4, 41.7 ms)
+        if (p->desc.local_sweeps <= 0)
+            p->desc.local_sweeps = (p->desc.schedule == 0 && p->desc.visit == 2) ? 3 : 1;
     }
     p->shape = p->desc.schedule == 0 ? 1 + p->desc.tile_shape : 0;
     if (p->desc.schedule != 1 && p->desc.coarse_n > 0 &&

@@ -464,6 +464,13 @@ struct hjb_batch {
     float* u32b = nullptr;
     double* u64 = nullptr;
     double* band_e = nullptr;            // every instance's band edges, concatenated
+    int sched_mode = 0;                  // hjb_batch_desc.schedule (0, 3, 4)
+    bool async = false;                  // FP32 passes from the asynchronous worklist
+    int32_t* a_state = nullptr;          // worklist: per-tile state and first-visit counters
+    int32_t* a_deps = nullptr;
+    unsigned long long* a_queue = nullptr;
+    int a_cap = 0;
+    AsyncCtl* a_ctl = nullptr;
     float* uhat = nullptr;
     uint8_t* a = nullptr;
     int32_t* key = nullptr;
@@ -649,7 +656,8 @@ int validate_batch(const hjb_batch_desc* d, int32_t count, const hjb_batch_inst*
         return bfail(HJB_ERR_INVALID_ARG, "scheme must be 2 or 3");
     if (d->tile_shape < -1 || d->tile_shape > 2)
         return bfail(HJB_ERR_INVALID_ARG, "tile_shape must be -1, 0, 1 or 2");
-    if (d->reserved != 0) return bfail(HJB_ERR_INVALID_ARG, "reserved field must be 0");
+    if (d->schedule != 0 && d->schedule != 3 && d->schedule != 4)
+        return bfail(HJB_ERR_INVALID_ARG, "schedule must be 0, 3 or 4");
     if (!(d->cost > 0.0) || !std::isfinite(d->cost)) return bfail(HJB_ERR_INVALID_ARG, "cost must be > 0");
     if (!std::isfinite(d->band_width)) return bfail(HJB_ERR_INVALID_ARG, "bad band_width");
     long long N = 0;
@@ -728,6 +736,8 @@ int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst
     b->tuned = desc->tile_shape >= 0 && desc->tile_waves > 0;
     b->cost = desc->cost;
     b->band_width = desc->band_width > 0.0 ? desc->band_width : 1.0;
+    b->sched_mode = desc->schedule;
+    b->async = desc->schedule == 3;
     b->desc.assign(insts, insts + count);
     b->node_off.assign(count + 1, 0);
     b->coarse_off.assign(count + 1, 0);
@@ -1098,6 +1108,7 @@ void hjb_batch_destroy(hjb_batch* b) {
     if (b->st) cudaStreamSynchronize(b->st);
     dfree(b->dinst, b->st); dfree(b->dtile, b->st);
     dfree(b->speed, b->st); dfree(b->mask, b->st); dfree(b->sector, b->st); dfree(b->u32, b->st); dfree(b->u32b, b->st); dfree(b->u64, b->st); dfree(b->band_e, b->st);
+    dfree(b->a_state, b->st); dfree(b->a_deps, b->st); dfree(b->a_queue, b->st); dfree(b->a_ctl, b->st);
     dfree(b->uhat, b->st); dfree(b->a, b->st); dfree(b->key, b->st); dfree(b->succ, b->st); dfree(b->jump_a, b->st); dfree(b->jump_b, b->st);
     dfree(b->label, b->st); dfree(b->speed_c, b->st); dfree(b->mask_c, b->st); dfree(b->uc, b->st); dfree(b->ctrl32, b->st); dfree(b->ctrl64, b->st);
     dfree(b->fblk, b->st); dfree(b->cblk, b->st); dfree(b->rblk, b->st); dfree(b->corder, b->st);
@@ -1265,6 +1276,42 @@ int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_ac
     a.max_wh = b->max_wh;
     const int per_sm = wtile_blocks_per_sm(f64, b->any_sigma, b->na, b->max_wh, b->shape);
     if (per_sm < 1) return bfail(HJB_ERR_INVALID_ARG, "warp-tile kernel does not fit on an SM");
+    if (b->async && !f64 && !warm) {
+        // the asynchronous worklist (see hjb_desc.schedule 3)
+        const int warps = per_sm * b->num_sms * (tile_threads(false, b->shape) / 32);
+        int cap = 1024;
+        while (cap < b->NT + warps + 64) cap <<= 1;
+        if (cap > b->a_cap) {
+            dfree(b->a_state, b->st); dfree(b->a_deps, b->st); dfree(b->a_queue, b->st);
+            BCU(dalloc(b->a_state, (size_t)b->NT, b->st));
+            BCU(dalloc(b->a_deps, (size_t)b->NT, b->st));
+            BCU(dalloc(b->a_queue, (size_t)cap, b->st));
+            b->a_cap = cap;
+        }
+        if (!b->a_ctl) BCU(dalloc(b->a_ctl, 1, b->st));
+        BCU(cudaMemsetAsync(b->a_queue, 0, sizeof(unsigned long long) * (size_t)b->a_cap, b->st));
+        BCU(cudaMemsetAsync(b->a_ctl, 0, sizeof(AsyncCtl), b->st));
+        a.astate = b->a_state;
+        a.adeps = b->a_deps;
+        a.aqueue = b->a_queue;
+        a.aq_cap = b->a_cap;
+        a.actl = b->a_ctl;
+        a.max_visits = (long long)max_passes * b->NT;
+        BCU(launch_wtiles_async(a, b->any_sigma, per_sm * b->num_sms, b->st));
+        AsyncCtl hc{};
+        GridSync hs{};
+        BCU(cudaMemcpyAsync(b->h_wres, b->wres, sizeof(WaveResult), cudaMemcpyDeviceToHost, b->st));
+        BCU(cudaMemcpyAsync(&hc, b->a_ctl, sizeof(AsyncCtl), cudaMemcpyDeviceToHost, b->st));
+        BCU(cudaMemcpyAsync(&hs, b->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, b->st));
+        BCU(cudaStreamSynchronize(b->st));
+        if (hs.err == HJB_ERR_TIMEOUT) return bfail(HJB_ERR_TIMEOUT, "batch tile worklist: a wait exceeded its limit");
+        if (hs.err != 0) return bfail(hs.err, "batch tile worklist: internal error");
+        *out = *b->h_wres;
+        out->passes = (int)((hc.visits + b->NT - 1) / std::max(1, b->NT));
+        out->converged = hc.stop ? 0 : 1;
+        out->last_increment = (float)tol;
+        return HJB_OK;
+    }
     BCU(launch_wtiles(a, f64, b->any_sigma, per_sm * b->num_sms, b->st));
     GridSync hs{};
     BCU(cudaMemcpyAsync(b->h_wres, b->wres, sizeof(WaveResult), cudaMemcpyDeviceToHost, b->st));
@@ -1499,8 +1546,36 @@ int hjb_batch_autotune(hjb_batch* b, double tol_c, double tol32, int32_t* shape_
             }
         }
     }
+    // the asynchronous worklist with each shape (one band per wave)
+    bool ba = b->sched_mode == 3;
+    const bool was_async = b->async;
+    if (b->sched_mode == 0) {
+        for (int si = 0; si < 3; ++si, ++c) {
+            b->shape = shapes[si];
+            b->B = 1;
+            b->async = true;
+            rc = stage_tiles(b);
+            if (rc) return rc;
+            BCU(cudaMemcpyAsync(b->u32, b->uhat, sizeof(float) * (size_t)b->N, cudaMemcpyDeviceToDevice,
+                                b->st));
+            BTimer t(b->st);
+            WaveResult w{};
+            rc = stage_passes(b, false, tol32, 100000, false, &w);
+            b->async = was_async;
+            if (rc) return rc;
+            const double ms = t.stop();
+            if (ms_out) ms_out[c] = ms;
+            if (w.converged && ms < best) {
+                best = ms;
+                bs = b->shape;
+                bw = 1;
+                ba = true;
+            }
+        }
+    }
     b->shape = bs;
     b->B = bw;
+    b->async = ba;
     b->tuned = true;
     b->built = false;
     if (shape_out) *shape_out = bs - 1;

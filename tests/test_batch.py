@@ -28,7 +28,7 @@ def _create(L, insts, **kw):
             if i == kw.get("at", 0):
                 setattr(arr[i], k, v)
     d = L.BatchDesc()
-    d.n_controls, d.scheme, d.tile_shape, d.tile_waves, d.tile_period, d.reserved = 32, 3, -1, 0, 2, 0
+    d.n_controls, d.scheme, d.tile_shape, d.tile_waves, d.tile_period, d.schedule = 32, 3, -1, 0, 2, 0
     d.cost, d.band_width = 1.0, 1.0
     for k, v in kw.get("desc", {}).items():
         setattr(d, k, v)
