@@ -48,7 +48,7 @@ def _create(L, insts, **kw):
 
 @pytest.mark.parametrize("bad", [
     dict(count=0), dict(desc=dict(n_controls=0)), dict(desc=dict(scheme=5)),
-    dict(desc=dict(tile_shape=4)), dict(desc=dict(reserved=2)), dict(desc=dict(cost=0.0)),
+    dict(desc=dict(tile_shape=4)), dict(desc=dict(schedule=2)), dict(desc=dict(cost=0.0)),
     dict(inst=dict(n=5)), dict(inst=dict(coarse_n=7), at=1), dict(inst=dict(lam=0.0), at=2),
     dict(inst=dict(sigma=-1.0)), dict(inst=dict(n_patches=0), at=3), dict(inst=dict(reserved=1)),
 ])
