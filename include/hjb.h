@@ -95,7 +95,7 @@ typedef struct {
                              barrier), 4 warp tiles in barrier-separated steps             */
     int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: automatic, 1 when the
                              diffusion offset sqrt(2h) sigma exceeds one cell, else 2)        */
-    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 1: 2)         */
+    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 0: 2)         */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: automatic,
                              3 with 32-node warp-tile visits, else 1)                        */
     int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (8x8 when the

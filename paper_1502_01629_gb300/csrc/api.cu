@@ -593,7 +593,7 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
     if (p->desc.band_group <= 0) p->desc.band_group = 1;
-    if (p->desc.tile_period <= 1) p->desc.tile_period = 2;
+    if (p->desc.tile_period <= 0) p->desc.tile_period = 2;
     p->n = n;
     p->N = (int)N;
     p->na = na;

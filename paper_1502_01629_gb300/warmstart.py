@@ -9,7 +9,8 @@ coarse solve has the last word: it runs to the same tolerance from the predicted
 start (falling back to the plain start when the prediction is far off), so the
 fixed point is the same and only the sweep count changes.
 
-    python -m paper_1502_01629_gb300.warmstart --train 20000 --eval 1000 --out result.json
+    python -m paper_1502_01629_gb300.warmstart --train 20000 --eval 1000 --epochs 10 --lr 2e-3 \
+        --save-weights paper_1502_01629_gb300/warmstart_weights.npy --large --out result.json
 
 Instances follow ``hjb_inputs.warmstart_instance`` (257^2 fine, 129^2 coarse,
 0-4 obstacles); training seeds start at 100000, evaluation seeds at 900000, so
@@ -115,8 +116,23 @@ def train(net, ds: Dataset, epochs: int = 3, batch: int = 32, lr: float = 1e-3, 
     return hist
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "warmstart_weights.npy")
+
+
+def load_trained(path: str = WEIGHTS, max_batch: int = 32):
+    """The network with the parameters a training run saved (``--save-weights``),
+    or None when the file is absent."""
+    if not os.path.exists(path):
+        return None
+    from . import Net
+    net = Net(max_batch=max_batch, height=NC, width=NC)
+    net.set_params(np.load(path).astype(np.float64))
+    return net
+
+
 def evaluate(net, insts, tol_c: float = 1e-6, k_sweeps: int = 4, accept_tol: float = 1e-3,
-             tol32: float = 2.5e-7, tol64: float = 1e-6, accept_tols=(1e-3, 1e-2, 5e-2, 0.2)) -> dict:
+             tol32: float = 1.25e-7, tol64: float = 1e-6, accept_tols=(1e-3, 1e-2, 5e-2, 0.2),
+             batch_kw=None) -> dict:
     """The instances solved twice as one batch: from the plain coarse start and
     from the network's prediction (accepted after k_sweeps refinement sweeps when
     the last sweep moves no node by more than accept_tol, else the plain coarse
@@ -134,7 +150,7 @@ def evaluate(net, insts, tol_c: float = 1e-6, k_sweeps: int = 4, accept_tol: flo
         torch.cuda.synchronize()
         return r, (time.perf_counter() - t0) * 1e3
 
-    with Batch.from_instances(insts) as B:
+    with Batch.from_instances(insts, **(batch_kw or {})) as B:
         n = len(insts)
         x = torch.empty((n, NC, NC, 16), dtype=torch.int16, device=dev)
         B.net_inputs(x)
@@ -195,26 +211,43 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--procs", type=int, default=0)
     ap.add_argument("--out", default="")
+    ap.add_argument("--save-weights", default="", help="write the trained parameters (float32 .npy)")
+    ap.add_argument("--load-weights", default="", help="skip the training: parameters from this file")
+    ap.add_argument("--large", action="store_true",
+                    help="also the 4097^2 workload (coarse 129^2) as a batch of one on the worklist")
     args = ap.parse_args(argv)
     log = lambda m: print(m, file=sys.stderr, flush=True)
     # instances are generated in spawn processes; the first CUDA call comes after
     import torch
     from . import Net
     dev = torch.device("cuda")
-    t0 = time.time()
-    ds = build_dataset(range(TRAIN_SEED0, TRAIN_SEED0 + args.train), dev, procs=args.procs, log=log)
-    t_data = time.time() - t0
-    net = Net(max_batch=args.batch, height=NC, width=NC)
-    net.set_params(net.init_params(seed=1))
-    t0 = time.time()
-    hist = train(net, ds, epochs=args.epochs, batch=args.batch, lr=args.lr, log=log)
-    t_train = time.time() - t0
-    del ds
-    torch.cuda.empty_cache()
-    ev_insts = generate(range(EVAL_SEED0, EVAL_SEED0 + args.eval), args.procs)
-    res = evaluate(net, ev_insts)
-    res.update(train_instances=args.train, epochs=args.epochs, batch=args.batch, lr=args.lr,
-               loss_history=hist, seconds_dataset=t_data, seconds_training=t_train)
+    if args.load_weights:
+        net = load_trained(args.load_weights, args.batch)
+        hist, t_data, t_train = [], 0.0, 0.0
+    else:
+        t0 = time.time()
+        ds = build_dataset(range(TRAIN_SEED0, TRAIN_SEED0 + args.train), dev, procs=args.procs, log=log)
+        t_data = time.time() - t0
+        net = Net(max_batch=args.batch, height=NC, width=NC)
+        net.set_params(net.init_params(seed=1))
+        t0 = time.time()
+        hist = train(net, ds, epochs=args.epochs, batch=args.batch, lr=args.lr, log=log)
+        t_train = time.time() - t0
+        del ds
+        torch.cuda.empty_cache()
+        if args.save_weights:
+            np.save(args.save_weights, net.get_params().astype(np.float32))
+    res = {}
+    if args.eval > 0:
+        ev_insts = generate(range(EVAL_SEED0, EVAL_SEED0 + args.eval), args.procs)
+        res = evaluate(net, ev_insts)
+    if args.large:
+        import hjb_inputs
+        res["large4097"] = evaluate(net, [hjb_inputs.large_instance()], accept_tols=(1e-3, 0.05, 0.2),
+                                    batch_kw=dict(schedule=3))
+    res.update(train_instances=0 if args.load_weights else args.train, epochs=args.epochs,
+               batch=args.batch, lr=args.lr, loss_history=hist, seconds_dataset=t_data,
+               seconds_training=t_train)
     line = json.dumps(res)
     print(line)
     if args.out:

@@ -115,3 +115,28 @@ def test_trained_network_replaces_coarse_sweeps(pkg):
             scale = max(1.0, np.abs(u_plain[i]).max())
             assert np.abs(B.get_value(i) - u_plain[i]).max() <= 1e-5 * scale
     net.close()
+
+
+def test_trained_network_against_the_plain_start(pkg):
+    """The trained network shipped with the package (written by the training run of
+    paper_1502_01629_gb300.warmstart --save-weights) on held-out instances: the
+    learned start and the plain coarse start reach the same fine fixed point
+    (both to the FP64 residual 1e-6, so within 2e-6 / (1 - beta) of each other),
+    and the time of both is reported (the learned start is judged by it, not
+    required to win: DESIGN records the measured difference and its cause)."""
+    from paper_1502_01629_gb300 import warmstart as ws
+    net = ws.load_trained()
+    assert net is not None, "the trained parameters are missing from the package"
+    insts = ws.generate(range(ws.EVAL_SEED0, ws.EVAL_SEED0 + 8), procs=1)
+    res = ws.evaluate(net, insts, accept_tol=0.05, accept_tols=(0.05, 0.2))
+    assert res["residual_max_plain"] <= 1e-6
+    one_minus_beta = min(1.0 - 1.0 / (1.0 + i.lam * i.h_eff) for i in insts)
+    for w in res["whole_solve"]:
+        assert w["residual_max"] <= 1e-6
+        assert w["max_abs_diff_of_solutions"] <= 2e-6 / one_minus_beta
+    # the loose threshold accepts predictions: their refinement replaces the coarse solve
+    assert res["whole_solve"][1]["accepted"] > 0
+    w = res["whole_solve"][0]
+    print(f"plain {res['solve_ms_plain']:.1f} ms, learned {w['solve_ms_warm_incl_inference']:.1f} ms "
+          f"({100 * w['solve_time_saved_fraction']:+.1f} % saved), accepted {w['accepted']}/{len(insts)}")
+    net.close()
