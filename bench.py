@@ -55,7 +55,7 @@ TOL32, TOL64, TOL_C = 1.25e-7, 1e-6, 1e-6
 GATE_REL = 1e-5
 METRIC = "time to 1e-6 residual vs plain GPU value iteration; node·control updates/s"
 UNIT = "node·control updates/s"
-SOLVER_KW = dict(schedule=0, tile_shape=-1, tile_waves=0, tile_period=2, local_sweeps=0, visit=0)
+SOLVER_KW = dict(schedule=0, tile_shape=-1, tile_waves=0, tile_period=0, local_sweeps=0, visit=0)
 BATCH_COUNT = 512
 GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 # DRAM bytes (read + write) per launch of the FP32 patch kernel, from one ncu

@@ -95,7 +95,8 @@ typedef struct {
                              barrier), 4 warp tiles in barrier-separated steps             */
     int32_t tile_waves;   /* tile schedule: bands per tile wave B (<= 0: automatic, 1 when the
                              diffusion offset sqrt(2h) sigma exceeds one cell, else 2)        */
-    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 0: 2)         */
+    int32_t tile_period;  /* tile schedule: period D of the cyclic schedule (<= 0: 1 for warp
+                             tiles, 2 for block tiles)                                        */
     int32_t local_sweeps; /* tile schedule: ordered sweeps of a tile per visit (<= 0: automatic,
                              3 with 32-node warp-tile visits, else 1)                        */
     int32_t tile_shape;   /* warp tiles: 0 8x8 nodes, 1 8x4, 2 4x4, -1 automatic (8x8 when the
@@ -104,8 +105,7 @@ typedef struct {
     int32_t visit;        /* warp tiles, FP32: how a warp updates a tile's nodes: 1 one node
                              at a time (a control per lane, warp minimum, Gauss-Seidel through
                              the tile), 2 32 nodes at a time (a node per lane, every control
-                             in the lane), 0 automatic (2 when the diffusion offset
-                             sqrt(2h) sigma exceeds one cell, else 1)                         */
+                             in the lane), 0 automatic (1)                                    */
 } hjb_desc;
 
 /* Per-call statistics; every field is written by the call that receives it. */
@@ -429,7 +429,7 @@ typedef struct {
     int32_t scheme;       /* 3 (SLscheme3, default when 0) or 2                            */
     int32_t tile_shape;   /* warp tiles: 0 8x8, 1 8x4, 2 4x4, -1: 8x4 until tuned          */
     int32_t tile_waves;   /* bands per tile wave B (<= 0: 2 until tuned)                   */
-    int32_t tile_period;  /* period D of the tile schedule (<= 1: 2)                       */
+    int32_t tile_period;  /* period D of the tile schedule (<= 0: 2)                       */
     int32_t schedule;     /* FP32 passes: 0 barrier-separated steps (hjb_batch_autotune may
                              switch to 3), 3 the asynchronous worklist of hjb_desc.schedule 3,
                              4 barrier-separated steps, never switched                       */

@@ -69,7 +69,7 @@ class Problem:
                  sigma: float = 0.0, cost: float = 1.0, coarse_n: int = 0, n_patches: int = 1,
                  scheme: int = 3, band_width: float = 1.0, band_window: int = 8,
                  band_group: int = 1, wave_warps: int = 0, resort_passes: int = 0,
-                 schedule: int = 0, tile_waves: int = 0, tile_period: int = 2,
+                 schedule: int = 0, tile_waves: int = 0, tile_period: int = 0,
                  local_sweeps: int = 0, tile_shape: int = -1, visit: int = 0,
                  drift: Optional[np.ndarray] = None, stream=None, device_inputs: bool = False,
                  sigma_field: Optional[np.ndarray] = None, diffusion: int = 0,

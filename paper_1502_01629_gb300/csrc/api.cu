@@ -593,7 +593,9 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
     if (p->desc.band_width <= 0.0) p->desc.band_width = 1.0;
     if (p->desc.band_window <= 0) p->desc.band_window = 8;
     if (p->desc.band_group <= 0) p->desc.band_group = 1;
-    if (p->desc.tile_period <= 0) p->desc.tile_period = 2;
+    // warp tiles revisit queued tiles every step (period 1; 1025^2: sigma 0.1
+    // 50.5 -> 31.4 ms, sigma 0.02 9.9 -> 8.8 ms, sigma 0 6.7 -> 6.5 ms against period 2)
+    if (p->desc.tile_period <= 0) p->desc.tile_period = p->desc.schedule == 0 ? 1 : 2;
     p->n = n;
     p->N = (int)N;
     p->na = na;
@@ -638,12 +640,12 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         const bool big = desc->n > 2049 || desc->n_controls > 32;
         if (p->desc.tile_shape < 0) p->desc.tile_shape = (wide || big) ? 0 : 1;
         if (p->desc.tile_waves <= 0) p->desc.tile_waves = wide ? 1 : 2;
-        // a wide diffusion reaches past the tile's own nodes, so ordering them
-        // within a visit gains little: update 32 of them at a time
-        if (p->desc.visit == 0) p->desc.visit = wide ? 2 : 1;
-        // node-per-lane visits sweep a tile three times per visit (the group of
-        // 32 is a Jacobi step; repeating it at the tile costs less than more
-        // pipeline steps: 1025^2, sigma 0.1: 1, 2, 3 sweeps 47.5, 41.4, 41.7 ms)
+        // one node at a time (lanes over controls) by default: with a period of
+        // one step it is the fastest form at every diffusion measured (1025^2,
+        // sigma 0.1: 31.4 ms against 46.9 ms for 32 nodes at a time); node-per-lane
+        // visits (visit 2) sweep a tile three times per visit (the group of 32 is a
+        // Jacobi step)
+        if (p->desc.visit == 0) p->desc.visit = 1;
         if (p->desc.local_sweeps <= 0)
             p->desc.local_sweeps = (p->desc.schedule == 0 && p->desc.visit == 2) ? 3 : 1;
     }
@@ -916,10 +918,14 @@ int jacobi64(hjb_problem* p, double* buf0, double* buf1, double tol, int max_swe
 // E <= 64 * 2^-24 * U (rounding of the values to FP32 and of about 25 FP32
 // operations on quantities <= 2U) + 2^-22 * reach * U (rounding of the foot
 // offset, times the largest value difference across a cell), which is below
-// 1e-5 U for a reach under 26 cells; the margin 2e-5 max(1, U) exceeds 2E.
+// 1e-5 U for a reach under 26 cells.  The margin is 2.2 E for the problem's own
+// reach (4.4e-6 U at 1 cell, 9.7e-6 U at 2.4 cells, 1e-5 U at 2.9 cells): every
+// control it keeps is evaluated in FP64, so a margin sized to the reach keeps
+// fewer of them.
 float screening_margin(const hjb_problem* p) {
     const double U = std::max(1.0, p->value_bound());
-    return (float)(2e-5 * U);
+    const double E = (64.0 * std::ldexp(1.0, -24) + std::ldexp(1.0, -22) * p->reach) * U;
+    return (float)(2.2 * E);
 }
 
 // FP64 sup-residual ||T2 u - u|| of u64 (FP32-screened, exact FP64 value).

@@ -730,7 +730,7 @@ int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst
     b->count = count;
     b->na = na;
     b->scheme = desc->scheme == 0 ? 3 : desc->scheme;
-    b->D = desc->tile_period <= 1 ? 2 : desc->tile_period;
+    b->D = desc->tile_period <= 0 ? 2 : desc->tile_period;
     b->shape = desc->tile_shape < 0 ? 2 : desc->tile_shape + 1;
     b->B = desc->tile_waves <= 0 ? 2 : desc->tile_waves;
     b->tuned = desc->tile_shape >= 0 && desc->tile_waves > 0;
@@ -962,7 +962,10 @@ int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst
         T.R = R;
         b->max_R = std::max(b->max_R, R);
         b->uob[i] = uob;
-        hmargin[i] = (float)(2e-5 * std::max(1.0, uob));
+        // FP32 screening margin of the FP64 residual: 2.2 x the FP32 candidate error
+        // bound (64 2^-24 + 2^-22 reach) max(1, U) (the single-problem residual's)
+        hmargin[i] = (float)(2.2 * (64.0 * std::ldexp(1.0, -24) + std::ldexp(1.0, -22) * reach) *
+                             std::max(1.0, uob));
         fcount[i] = (long long)n * n;
         ccount[i] = (long long)nc * nc;
         nt_cap += (long long)((n + 3) / 4) * ((n + 3) / 4);
