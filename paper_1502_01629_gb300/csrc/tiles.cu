@@ -278,7 +278,7 @@ __device__ __forceinline__ float bil32(const float* su, int o, int W, float frx,
 template <typename T, bool SIG, int TW, int TH, typename Hook>
 __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
                                           const typename RealOf<T>::V2* sctrl, int na, int lane,
-                                          Hook& hook, int* nn_out) {
+                                          Hook& hook, int* nn_out, int4* changed = nullptr) {
     const int b = a.tile_inst ? a.tile_inst[t] : 0;
     const TileInst& I = a.insts[b];
     auto C = [&](int m) { return sctrl[m]; };
@@ -317,6 +317,18 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
         claimed = true;
         hook();
     };
+    // tile-local box of the nodes that changed by more than tol (warp-uniform:
+    // the increment and the node of the one-node forms are the same in every lane)
+    int cx0 = TW, cx1 = -1, cy0 = TH, cy1 = -1;
+    auto mark = [&](int e, float adu) {
+        if (adu > a.tol) {
+            const int ex = e % TW, ey = e / TW;
+            cx0 = min(cx0, ex);
+            cx1 = max(cx1, ex);
+            cy0 = min(cy0, ey);
+            cy1 = max(cy1, ey);
+        }
+    };
     // staged window inside the grid: the projection is the identity
     const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + Wv <= n && gy0 + H <= n;
     auto visit = [&](auto clamp_tag) {
@@ -350,6 +362,7 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             if (lane == 0) base[0] = uk + du;
             __syncwarp();
             tmax = fmaxf(tmax, inc_to_float(fabs(du)));
+            mark(e, inc_to_float(fabs(du)));
             if (!claimed && tmax > a.tol) claim();
         }
       }
@@ -364,8 +377,8 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
       const float omb = 1.0f - beta;
       const bool has = lane < na;
       const float2 ac = has ? g.ctrl32[lane] : make_float2(0.0f, 0.0f);
-      auto node_geo = [&](int q, int& kb) {
-          const int e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
+      auto node_geo = [&](int q, int& kb, int& e) {
+          e = __shfl_sync(0xffffffffu, q < 32 ? e0 : e1, q & 31);
           const float c = __shfl_sync(0xffffffffu, q < 32 ? c0 : c1, q & 31);
           const int ex = e % TW, ey = e / TW;
           kb = (R + ey) * W + (R + ex);
@@ -373,12 +386,13 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
       };
       float* sf = reinterpret_cast<float*>(su);
       for (int sw = 0; sw < a.local_sweeps; ++sw) {
-        int kbn;
-        Geo32<SIG> gn = node_geo(0, kbn);
+        int kbn, en;
+        Geo32<SIG> gn = node_geo(0, kbn, en);
         for (int q = 0; q < nn; ++q) {
             const Geo32<SIG> gc = gn;
             const int kb = kbn;
-            gn = node_geo(min(q + 1, nn - 1), kbn);
+            const int ecur = en;
+            gn = node_geo(min(q + 1, nn - 1), kbn, en);
             const float uk = sf[kb];
             const float cc0 = fmaf(-omb, uk, hl);
             float Sd;
@@ -400,6 +414,7 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             if (lane == 0) sf[kb] = uk + du;
             __syncwarp();
             tmax = fmaxf(tmax, fabsf(du));
+            mark(ecur, fabsf(du));
             if (!claimed && tmax > a.tol) claim();
         }
       }
@@ -484,6 +499,13 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             const float gm = __uint_as_float(__reduce_max_sync(0xffffffffu,
                                                                __float_as_uint(fabsf(du))));
             tmax = fmaxf(tmax, gm);
+            if (gm > a.tol) {
+                const bool ch = fabsf(du) > a.tol;
+                cx0 = min(cx0, (int)__reduce_min_sync(0xffffffffu, ch ? (unsigned)ex : 0xffffu));
+                cx1 = max(cx1, (int)__reduce_max_sync(0xffffffffu, ch ? (unsigned)ex : 0u));
+                cy0 = min(cy0, (int)__reduce_min_sync(0xffffffffu, ch ? (unsigned)ey : 0xffffu));
+                cy1 = max(cy1, (int)__reduce_max_sync(0xffffffffu, ch ? (unsigned)ey : 0u));
+            }
             if (!claimed && tmax > a.tol) claim();
         }
       }
@@ -532,6 +554,7 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             if (lane == 0) sf[kb] = uk + du;
             __syncwarp();
             tmax = fmaxf(tmax, fabsf(du));
+            mark(e, fabsf(du));
             if (!claimed && tmax > a.tol) claim();
         }
       }
@@ -581,6 +604,7 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
     if (lane + 32 < nn) st_l2(u + (size_t)(bj + e1 / TW) * n + bi + e1 % TW,
                               su[(R + e1 / TW) * W + (R + e1 % TW)]);
     *nn_out = nn;
+    if (changed) *changed = make_int4(cx0, cx1, cy0, cy1);
     return tmax;
 }
 
@@ -934,7 +958,8 @@ k_wtiles_async(TileArgs a) {
         if (lane == 0) first = atomicExch(a.adeps + t, -1) == 0;
         first = __shfl_sync(0xffffffffu, first, 0);
         int nn = 0;
-        const float tmax = wt_visit<float, SIG, TW, TH>(a, t, su, sctrl, na, lane, nohook, &nn);
+        int4 chg;
+        const float tmax = wt_visit<float, SIG, TW, TH>(a, t, su, sctrl, na, lane, nohook, &nn, &chg);
         // the tile's new values are in L2 before any neighbour is put back
         __threadfence();
         const bool changed = tmax > a.tol;
@@ -953,8 +978,15 @@ k_wtiles_async(TileArgs a) {
                 if (wn == 0x7fffffff) continue;
                 // release: this was the last lower-wave neighbour's first visit
                 if (first && nb != t && wn > wt && atomicSub(a.adeps + nb, 1) == 1) aq_push(a, nb);
-                // put back the released neighbours (and this tile) after a change
-                if (changed && ld_acq_s32(a.adeps + nb) <= 0) aq_push(a, nb);
+                // put back the released neighbours (and this tile) after a change,
+                // those whose nodes read a changed node: within the staged halo R
+                // of the box of changed nodes along both axes
+                if (changed) {
+                    const int ox = (q % aw - ar) * TW, oy = (q / aw - ar) * TH;
+                    const int gx = max(0, max(ox - chg.y, chg.x - (ox + TW - 1)));
+                    const int gy = max(0, max(oy - chg.w, chg.z - (oy + TH - 1)));
+                    if (gx <= I.R && gy <= I.R && ld_acq_s32(a.adeps + nb) <= 0) aq_push(a, nb);
+                }
             }
         }
         __syncwarp();
