@@ -122,7 +122,8 @@ typedef struct {
     int32_t fp64_passes;           /* passes (sweeps) in FP64                                     */
     int64_t fp64_node_updates;     /* the part of node_updates done in FP64                       */
     int32_t residual_evals;        /* FP64 residual evaluations (full-grid operator applications) */
-    int32_t pad;
+    int32_t corr_sweeps;           /* solve_patches: FP32 sweeps of the FP64 stage's correction
+                                      equation (one control per node; part of node_updates)     */
 } hjb_stats;
 
 /* Regime of the upwind diffusion-ball condition (Section 4.1, eqs. upper-bound,
@@ -287,9 +288,15 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
  * max(1, U) A, at most two more FP32 phases run from the current value with
  * the tolerance divided by 4 each time while it stays >= 2^-21 max(1, U) A
  * (schedule 0, every tile visited in the first two steps in checkerboard
- * order); then FP64 passes until the FP64
- * sup-residual is <= tol64.  max_passes caps each phase.
- * ms_stage: [0] FP32 passes, [1] promotion + residuals, [2] FP64 passes.
+ * order); then, for constant coefficients with a discount (lambda > 0) and
+ * scheme 3, at most 12 rounds of mixed-precision correction: from the FP64
+ * residual r = T2 u - u and its minimising control a per node, FP32 Jacobi
+ * sweeps of e = beta P_a e + r (one control per node), u += e in FP64, the FP64
+ * residual again (Howard's policy iteration; stops at tol64, after two rounds
+ * in a row that do not halve the residual, or if it grows 1e3-fold); then FP64
+ * passes until the FP64 sup-residual is <= tol64.  max_passes caps each phase.
+ * ms_stage: [0] FP32 passes, [1] promotion + residuals, [2] correction rounds
+ * and FP64 passes.
  * Errors: HJB_ERR_STATE (build_patches not run), HJB_ERR_NOT_CONVERGED,
  * HJB_ERR_TIMEOUT (a grid-wide wait exceeded its limit). */
 int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_passes,

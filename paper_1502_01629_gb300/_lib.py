@@ -43,7 +43,7 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_stage", ctypes.c_double * 8),
                 ("fp32_passes", ctypes.c_int32), ("fp64_passes", ctypes.c_int32),
                 ("fp64_node_updates", ctypes.c_int64), ("residual_evals", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("corr_sweeps", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "ms_stage"}

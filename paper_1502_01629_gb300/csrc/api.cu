@@ -288,6 +288,8 @@ struct hjb_problem {
     float* wt_speed = nullptr;     // speed per node slot (warp tiles)
     int32_t* wt_stamp = nullptr;   // per-tile queue stamps (warp tiles)
     bool async = false;            // schedule 3: the asynchronous worklist for the FP32 phase
+    float* corr_r = nullptr;       // FP64 stage by correction: residual field (FP32) ...
+    uint8_t* corr_a = nullptr;     // ... and its minimising control per node
     int32_t* a_state = nullptr;    // worklist: per-tile state and first-visit counters
     int32_t* a_deps = nullptr;
     unsigned long long* a_queue = nullptr;
@@ -929,11 +931,16 @@ float screening_margin(const hjb_problem* p) {
 }
 
 // FP64 sup-residual ||T2 u - u|| of u64 (FP32-screened, exact FP64 value).
-int residual64(hjb_problem* p, double* out) {
+int residual64(hjb_problem* p, double* out, bool fields = false) {
     Scalars* ds = dscal(p);
+    if (fields && !p->corr_r) {
+        CU(palloc(&p->corr_r, sizeof(float) * (size_t)p->N, p->st));
+        CU(palloc(&p->corr_a, (size_t)p->N, p->st));
+    }
     CU(cudaMemsetAsync(&ds->inc64, 0, sizeof(unsigned long long), p->st));
     CU(launch_residual_screened(p->fine_view(), p->sigma > 0.0, p->halo, p->u64,
-                                screening_margin(p), &ds->inc64, p->st));
+                                screening_margin(p), &ds->inc64, p->st,
+                                fields ? p->corr_r : nullptr, fields ? p->corr_a : nullptr));
     unsigned long long bits = 0;
     CU(cudaMemcpyAsync(&hscal(p)->inc64, &ds->inc64, sizeof(bits), cudaMemcpyDeviceToHost, p->st));
     CU(cudaStreamSynchronize(p->st));
@@ -1159,6 +1166,7 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
         while (cap < p->nt + warps + 64) cap <<= 1;
         if (cap > p->a_cap) {
             pfree(p->a_state, p->st); pfree(p->a_deps, p->st); pfree(p->a_queue, p->st);
+    pfree(p->corr_r, p->st); pfree(p->corr_a, p->st);
             CU(palloc(&p->a_state, sizeof(int32_t) * (size_t)p->nt, p->st));
             CU(palloc(&p->a_deps, sizeof(int32_t) * (size_t)p->nt, p->st));
             CU(palloc(&p->a_queue, sizeof(unsigned long long) * (size_t)cap, p->st));
@@ -1524,6 +1532,61 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a) {
     return HJB_OK;
 }
 
+namespace {
+
+// The FP64 stage by mixed-precision correction (iterative refinement): with the
+// FP64 residual r = T2 u - u and its minimising control a per node (written by
+// the last residual64(p, &res, true)), solve the linear correction equation
+// e = beta P_a e + r in FP32 by Jacobi sweeps to a sup-increment of tol_in, add
+// e to u in FP64 and take the FP64 residual again; each round is one policy
+// evaluation of the linearised scheme, so the residual falls by orders of
+// magnitude per round while every sweep is FP32 with one control per node.
+// The rounds are Howard's policy iteration on the FP64 values: where the
+// minimising control switches (sigma = 0, ties along shocks) a round can raise
+// the residual, and the next round, with the new controls, brings it down.
+// Stops at res <= tol64, after `rounds`, after two rounds in a row that fail
+// to halve the residual, or when it grows past 1e3 times the stage's first
+// one (the FP64 passes then take over).  *sweeps / *nodes count the correction
+// sweeps and their node updates (one control each).
+int correction_stage(hjb_problem* p, double tol64, int rounds, double* res, int* sweeps,
+                     unsigned long long* nodes, int* n_res) {
+    const GridView g = p->fine_view();
+    const bool sig = p->sigma > 0.0;
+    constexpr int kMaxSweeps = 20000;
+    int rc = ensure_hist(p, kMaxSweeps + 8);
+    if (rc) return rc;
+    const double res0 = *res;
+    int stalled = 0;
+    for (int it = 0; it < rounds && *res > tol64; ++it) {
+        const double before = *res;
+        CU(cudaMemsetAsync(p->u32, 0, sizeof(float) * (size_t)p->N, p->st));
+        int sw = 0;
+        double last = 0.0;
+        bool conv = false;
+        // the correction is at most res / (1 - beta); its FP32 increments cannot
+        // resolve much below 2^-21 of that, so the round stops there at the latest
+        // (the next round starts from a residual that much smaller)
+        const double tol_in = std::max(0.2 * tol64, std::ldexp(*res / (1.0 - p->beta), -21));
+        rc = jacobi_loop_impl<float>(p, p->inc_hist32, p->u32, p->u32b, p->N, tol_in, kMaxSweeps, &sw,
+                                     &last, &conv, [&](const float* a, float* b, unsigned int* inc) {
+                                         return launch_correction_sweep(g, sig, p->halo, p->corr_a, p->corr_r,
+                                                                        a, b, inc, p->st);
+                                     });
+        if (rc) return rc;
+        *sweeps += sw;
+        *nodes += (unsigned long long)sw * (unsigned long long)p->n_free;
+        CU(launch_add_correction(p->N, p->mask, p->u32, p->u64, p->st));
+        rc = residual64(p, res, true);
+        if (rc) return rc;
+        ++*n_res;
+        stalled = *res < 0.5 * before ? 0 : stalled + 1;
+        if (stalled >= 2 || !(*res <= 1e3 * res0)) break;
+    }
+    return HJB_OK;
+}
+
+}  // namespace
+
 int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_passes,
                       hjb_stats* stats) {
     g_last_error.clear();
@@ -1575,12 +1638,16 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
     int passes64 = 0;
     int n_res = 0;
     double last = w32.last_increment;
+    int corr_sweeps = 0;
+    unsigned long long corr_nodes = 0;
+    // the FP64 stage by correction: constant coefficients, a discount, scheme 3
+    const bool corr = !p->gen && p->lambda > 0.0 && p->desc.scheme == 3;
     if (tol64 > 0.0 && rc == HJB_OK) {
         Timer t2(p->st);
         t2.mark();
         CU(launch_promote(p->N, p->u32, p->mask, p->uob, p->u64, p->st));
         p->value_f64 = true;
-        int r2 = residual64(p, &res);
+        int r2 = residual64(p, &res, corr);
         if (r2) return r2;
         ++n_res;
         t2.mark();
@@ -1608,12 +1675,20 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
             last = ww.last_increment;
             tw.mark();
             CU(launch_promote(p->N, p->u32, p->mask, p->uob, p->u64, p->st));
-            r2 = residual64(p, &res);
+            r2 = residual64(p, &res, corr);
             if (r2) return r2;
             ++n_res;
             tw.mark();
             ms_warm32 += tw.ms(0, 1);
             ms_promote += tw.ms(1, 2);
+        }
+        if (corr && res > tol64) {
+            Timer tc(p->st);
+            tc.mark();
+            r2 = correction_stage(p, tol64, 12, &res, &corr_sweeps, &corr_nodes, &n_res);
+            if (r2) return r2;
+            tc.mark();
+            ms64 += tc.ms(0, 1);
         }
         double tol_pass = tol64;
         while (res > tol64 && passes64 < max_passes) {
@@ -1639,8 +1714,10 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         stats->fp32_passes = w32.passes;
         stats->fp64_passes = passes64;
         stats->sweeps = w32.passes + passes64;
-        stats->node_updates = (long long)(w32.nodes + nodes64);
-        stats->node_control_updates = stats->node_updates * p->na;
+        stats->node_updates = (long long)(w32.nodes + nodes64 + corr_nodes);
+        // a correction sweep evaluates one control per node
+        stats->node_control_updates = (long long)(w32.nodes + nodes64) * p->na + (long long)corr_nodes;
+        stats->corr_sweeps = corr_sweeps;
         stats->fp64_node_updates = (long long)nodes64;
         stats->residual_evals = n_res;
         stats->residual = res;

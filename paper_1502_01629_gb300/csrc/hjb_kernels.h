@@ -99,7 +99,14 @@ cudaError_t launch_sweep_f64(const GridView& g, bool sig, int scheme, int halo, 
 // FP64 residual with exact FP32 screening of the controls (see sweep.cu);
 // margin must exceed twice the largest |FP32 - FP64| candidate difference.
 cudaError_t launch_residual_screened(const GridView& g, bool sig, int halo, const double* u,
-                                     float margin, unsigned long long* incmax, cudaStream_t st);
+                                     float margin, unsigned long long* incmax, cudaStream_t st,
+                                     float* rfield = nullptr, uint8_t* afield = nullptr);
+// The FP64 stage by correction: one FP32 Jacobi sweep of e = beta P_a e + r (a, r
+// from the residual field), and u += e on free nodes.
+cudaError_t launch_correction_sweep(const GridView& g, bool sig, int halo, const uint8_t* act,
+                                    const float* r, const float* ein, float* eout, unsigned int* incmax,
+                                    cudaStream_t st);
+cudaError_t launch_add_correction(long long N, const uint8_t* mask, const float* e, double* u, cudaStream_t st);
 size_t residual_screened_smem(int na, int R);
 
 // ------------------------------------------------------------ precompute.cu

@@ -114,7 +114,7 @@ cudaError_t launch_sweep_impl(const GridView& g, int scheme, int R, const T* uin
 template <bool SIG>
 __global__ void __launch_bounds__(kTileX * kBlockY)
 k_residual_screened(GridView g, int R, const double* __restrict__ u, float margin,
-                    unsigned long long* incmax) {
+                    unsigned long long* incmax, float* rfield, uint8_t* afield) {
     extern __shared__ __align__(16) unsigned char smem[];
     double2* c64 = reinterpret_cast<double2*>(smem);
     const size_t cb64 = ((size_t)g.na * sizeof(double2) + 15) & ~(size_t)15;
@@ -151,12 +151,96 @@ k_residual_screened(GridView g, int R, const double* __restrict__ u, float margi
         const int j = blockIdx.y * kTileY + threadIdx.y + r * kBlockY;
         if (i >= n || j >= n) continue;
         const size_t k = (size_t)j * n + i;
-        if (g.mask[k] != kFree) continue;
+        if (g.mask[k] != kFree) {
+            if (rfield) {
+                rfield[k] = 0.0f;
+                afield[k] = 0;
+            }
+            continue;
+        }
         const int off = (j - gy0) * W + (i - gx0);
-        lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin));
+        if (rfield) {
+            double v;
+            int m;
+            lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin, &v, &m));
+            rfield[k] = (float)v;
+            afield[k] = (uint8_t)m;
+        } else {
+            lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin));
+        }
     }
     const double bm = block_max<double>(lmax, red);
     if (tid == 0) atomic_max_nonneg(incmax, bm);
+}
+
+// One Jacobi sweep of the correction equation of the FP64 stage: with the
+// residual r = T2 u - u (eq. SLscheme2) and its minimising control a fixed per
+// node, the correction e solves e = beta P_a e + r (P_a: the Markov-chain
+// transition of eq. SLscheme2 under control a), i.e. one policy evaluation of
+// the linearised scheme; it is swept in the self-weight-free form of eq.
+// SLscheme3, e_i <- e_i + (beta S'_a + r_i - (1 - beta) e_i) / (1 - beta Lambda0_a),
+// in FP32 (e is small: its rounding is relative to e, not to u).  Non-free
+// nodes hold e = 0.
+template <bool SIG>
+__global__ void __launch_bounds__(kTileX * kBlockY)
+k_correction_sweep(GridView g, int R, const uint8_t* __restrict__ act, const float* __restrict__ r,
+                   const float* __restrict__ ein, float* __restrict__ eout, unsigned int* incmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* tile = reinterpret_cast<float*>(smem);
+    __shared__ float red[32];
+    const int n = g.n;
+    const int W = kTileX + 2 * R;
+    const int H = kTileY + 2 * R;
+    const int gx0 = blockIdx.x * kTileX - R;
+    const int gy0 = blockIdx.y * kTileY - R;
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    for (int t = tid; t < W * H; t += kTileX * kBlockY) {
+        const int ty = t / W;
+        const int tx = t - ty * W;
+        const int gx = min(max(gx0 + tx, 0), n - 1);
+        const int gy = min(max(gy0 + ty, 0), n - 1);
+        tile[t] = ein[(size_t)gy * n + gx];
+    }
+    __syncthreads();
+    const float beta = g.beta32, s = g.s32;
+    const float bq = SIG ? beta * 0.25f : beta;
+    float lmax = 0.0f;
+#pragma unroll 1
+    for (int rr = 0; rr < kTileY / kBlockY; ++rr) {
+        const int i = blockIdx.x * kTileX + threadIdx.x;
+        const int j = blockIdx.y * kTileY + threadIdx.y + rr * kBlockY;
+        if (i >= n || j >= n) continue;
+        const size_t k = (size_t)j * n + i;
+        if (g.mask[k] != kFree) {
+            eout[k] = 0.0f;
+            continue;
+        }
+        const float* base = tile + (j - gy0) * W + (i - gx0);
+        const float ek = base[0];
+        auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
+        float bx = 0.0f, by = 0.0f;
+        if (g.drift) {
+            const float2 b = g.drift[k];
+            bx = b.x;
+            by = b.y;
+        }
+        const NodeBox<float> box = node_box<float>(i, j, n);
+        const float c0 = fmaf(-(1.0f - beta), ek, r[k]);
+        float N, D;
+        candidate<float, SIG, true>(g, 3, box, s, bq, c0, ek, g.speed[k], bx, by, g.ctrl32[act[k]], U, N, D);
+        const float de = N / D;
+        eout[k] = ek + de;
+        lmax = fmaxf(lmax, fabsf(de));
+    }
+    const float bm = block_max<float>(lmax, red);
+    if (tid == 0) atomicMax(incmax, __float_as_uint(bm));
+}
+
+// u <- u + e on free nodes (FP64 values, FP32 correction)
+__global__ void k_add_correction(long long N, const uint8_t* __restrict__ mask, const float* __restrict__ e,
+                                 double* u) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N && mask[k] == kFree) u[k] += (double)e[k];
 }
 
 }  // namespace
@@ -175,7 +259,8 @@ size_t residual_screened_smem(int na, int R) {
 }
 
 cudaError_t launch_residual_screened(const GridView& g, bool sig, int halo, const double* u,
-                                     float margin, unsigned long long* incmax, cudaStream_t st) {
+                                     float margin, unsigned long long* incmax, cudaStream_t st,
+                                     float* rfield, uint8_t* afield) {
     const size_t smem = residual_screened_smem(g.na, halo);
     auto kern = sig ? k_residual_screened<true> : k_residual_screened<false>;
     if (smem > 48 * 1024) {
@@ -185,7 +270,29 @@ cudaError_t launch_residual_screened(const GridView& g, bool sig, int halo, cons
     dim3 block(kTileX, kBlockY);
     dim3 grid((g.n + kTileX - 1) / kTileX, (g.n + kTileY - 1) / kTileY);
     count_launches(1);
-    kern<<<grid, block, smem, st>>>(g, halo, u, margin, incmax);
+    kern<<<grid, block, smem, st>>>(g, halo, u, margin, incmax, rfield, afield);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correction_sweep(const GridView& g, bool sig, int halo, const uint8_t* act,
+                                    const float* r, const float* ein, float* eout, unsigned int* incmax,
+                                    cudaStream_t st) {
+    const size_t smem = (size_t)(kTileX + 2 * halo) * (kTileY + 2 * halo) * sizeof(float);
+    auto kern = sig ? k_correction_sweep<true> : k_correction_sweep<false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 block(kTileX, kBlockY);
+    dim3 grid((g.n + kTileX - 1) / kTileX, (g.n + kTileY - 1) / kTileY);
+    count_launches(1);
+    kern<<<grid, block, smem, st>>>(g, halo, act, r, ein, eout, incmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_correction(long long N, const uint8_t* mask, const float* e, double* u, cudaStream_t st) {
+    count_launches(1);
+    k_add_correction<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, mask, e, u);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,8 @@ template <bool SIG>
 __device__ __forceinline__ double residual_node(const GridView& g, int i, int j, size_t k,
                                                 const float* t32, const double* t64, int off,
                                                 int W, const float2* c32, const double2* c64,
-                                                float margin) {
+                                                float margin, double* vbest = nullptr,
+                                                int* mbest = nullptr) {
     const int n = g.n;
     const float* b32 = t32 + off;
     const double* b64 = t64 + off;
@@ -60,6 +61,8 @@ __device__ __forceinline__ double residual_node(const GridView& g, int i, int j,
         int M;
         best_over_controls<double, SIG>(g, 2, i, j, uk64, (double)ck32, (double)bx32, (double)by32,
                                         0, 1, C64, U64, N, D, M);
+        if (vbest) *vbest = N / D;
+        if (mbest) *mbest = M;
         return fabs(N / D);
     }
     // FP32 screening pass
@@ -82,6 +85,7 @@ __device__ __forceinline__ double residual_node(const GridView& g, int i, int j,
     const NodeBox<double> box64 = node_box<double>(i, j, n);
     const double ck64 = (double)ck32, bx64 = (double)bx32, by64 = (double)by32;
     double best = INFINITY;
+    int bm = 0;
     for (int m = 0; m < g.na; ++m) {
         const float2 a = c32[m];
         const float fx = s32 * fmaf(ck32, a.x, bx32);
@@ -94,8 +98,14 @@ __device__ __forceinline__ double residual_node(const GridView& g, int i, int j,
         const double fy64 = s64 * fma(ck64, a64.y, by64);
         double Sd64, L64;
         control_terms<double, SIG>(g, box64, fx64, fy64, uk64, U64, Sd64, L64);
-        best = fmin(best, fma(beta64, Sd64, c0_64));
+        const double v = fma(beta64, Sd64, c0_64);
+        if (v < best) {
+            best = v;
+            bm = m;
+        }
     }
+    if (vbest) *vbest = best;
+    if (mbest) *mbest = bm;
     return fabs(best);
 }
 
