@@ -66,8 +66,12 @@ k_conv3x3_tc(const bf16* __restrict__ x, const uint8_t* __restrict__ wpack,
         uint4* dst = reinterpret_cast<uint4*>(sB);
         for (int i = tid; i < NPAD * KC; i += kConvThreads) dst[i] = src[i];
     }
+    // e -> (m & 7) fastest, then the chunk kc, then m >> 3: a warp writes four
+    // whole 128-byte core-matrix blocks (no bank conflicts) and reads the same
+    // tap of 8 consecutive pixels (contiguous in NHWC)
     for (int e = tid; e < 128 * KC; e += kConvThreads) {
-        const int m = e / KC, kc = e - (e / KC) * KC;
+        const int rest = e >> 3, mh = rest / KC;
+        const int kc = rest - mh * KC, m = mh * 8 + (e & 7);
         const int t = kc / (CIN / 8), cc = kc - t * (CIN / 8);
         const long long p = p0 + m;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
