@@ -296,8 +296,13 @@ int hjb_set_feedback(hjb_problem* p, const uint8_t* a);
  * in a row that do not halve the residual, or if it grows 1e3-fold); then FP64
  * passes until the FP64 sup-residual is <= tol64.  max_passes caps each phase.
  * ms_stage: [0] FP32 passes, [1] promotion + residuals, [2] correction rounds
- * and FP64 passes.
- * Errors: HJB_ERR_STATE (build_patches not run), HJB_ERR_NOT_CONVERGED,
+ * and FP64 passes.  The worklist (schedule 3) stops putting back a tile after
+ * min(max_passes, 4096) visits of it (FP32 rounding can keep a few tiles
+ * changing by more than a tol32 below what FP32 resolves there); the FP32 phase
+ * then counts as not converged.  With tol64 > 0 the FP64 stage runs whether or
+ * not the FP32 phase converged, and the FP64 residual decides the status.
+ * Errors: HJB_ERR_STATE (build_patches not run), HJB_ERR_NOT_CONVERGED (tol64 = 0
+ * and the FP32 phase did not converge, or the FP64 residual stays above tol64),
  * HJB_ERR_TIMEOUT (a grid-wide wait exceeded its limit). */
 int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_passes,
                       hjb_stats* stats);
@@ -476,8 +481,11 @@ int hjb_batch_create_lists(const hjb_batch_desc* desc, int32_t count, const hjb_
  * passes, [1] residuals, [2] FP64 passes, [3] coarse solves, [4] pre-computation.
  * An instance above tol64 first gets at most two more FP32 phases (tolerance /4
  * each, while above the FP32 floor), then FP64 passes; both start warm (that
- * instance's tiles visited once in checkerboard order, then the queues).
- * Errors: HJB_ERR_NOT_CONVERGED (a cap was hit; values valid), HJB_ERR_TIMEOUT. */
+ * instance's tiles visited once in checkerboard order, then the queues).  The
+ * worklist schedule caps the visits of one tile as hjb_solve_patches does; with
+ * tol64 > 0 the FP64 residuals decide the status.
+ * Errors: HJB_ERR_NOT_CONVERGED (a cap was hit, or an FP64 residual stays above
+ * tol64; values valid), HJB_ERR_TIMEOUT. */
 int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int32_t max_passes,
                     hjb_stats* stats, double* residuals);
 

@@ -1180,6 +1180,7 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
         a.aq_cap = p->a_cap;
         a.actl = &ds->actl;
         a.max_visits = (long long)max_passes * p->nt;
+        a.tile_cap = std::min(max_passes, kTileVisitCap);
         CU(launch_wtiles_async(a, sig, blocks, p->st));
         CU(cudaMemcpyAsync(&hscal(p)->actl, &ds->actl, sizeof(AsyncCtl), cudaMemcpyDeviceToHost, p->st));
         CU(cudaMemcpyAsync(&hscal(p)->wave, &ds->wave, sizeof(WaveResult), cudaMemcpyDeviceToHost, p->st));
@@ -1192,7 +1193,7 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
         // passes = visits per tile with free nodes (the worklist has no steps)
         const long long tiles = std::max(1, p->nt);
         out->passes = (int)((hscal(p)->actl.visits + tiles - 1) / tiles);
-        out->converged = hscal(p)->actl.stop ? 0 : 1;
+        out->converged = (hscal(p)->actl.stop || hscal(p)->actl.capped) ? 0 : 1;
         out->last_increment = (float)tol;
         return HJB_OK;
     }
@@ -1631,7 +1632,10 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         w32.nodes = nodes;
     }
     tm.mark();
-    if (!w32.converged) rc = HJB_ERR_NOT_CONVERGED;
+    // Without an FP64 stage the FP32 phase must converge; with one, the FP64
+    // residual decides (the FP32 phase may stop at its visit caps where FP32
+    // rounding keeps a few tiles changing, and the FP64 stage resolves them).
+    if (!w32.converged && !(tol64 > 0.0)) rc = HJB_ERR_NOT_CONVERGED;
     double res = -1.0;
     double ms_promote = 0.0, ms64 = 0.0, ms_warm32 = 0.0;
     unsigned long long nodes64 = 0;
@@ -1661,7 +1665,7 @@ int hjb_solve_patches(hjb_problem* p, double tol32, double tol64, int32_t max_pa
         // noise of a converged FP32 field every tile would keep re-queueing.
         const double floor32 = std::ldexp(std::max(1.0, p->value_bound()), -22) * p->amp32;
         double tol_w = tol32;
-        for (int tries = 0; tries < 2 && res > tol64 && tol64 >= floor32 &&
+        for (int tries = 0; tries < 2 && w32.converged && res > tol64 && tol64 >= floor32 &&
                             0.25 * tol_w >= 2.0 * floor32 && p->desc.schedule == 0 &&
                             w32.passes < max_passes; ++tries) {
             Timer tw(p->st);

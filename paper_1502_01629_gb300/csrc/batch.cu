@@ -1300,6 +1300,7 @@ int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_ac
         a.aq_cap = b->a_cap;
         a.actl = b->a_ctl;
         a.max_visits = (long long)max_passes * b->NT;
+        a.tile_cap = std::min(max_passes, kTileVisitCap);
         BCU(launch_wtiles_async(a, b->any_sigma, per_sm * b->num_sms, b->st));
         AsyncCtl hc{};
         GridSync hs{};
@@ -1311,7 +1312,7 @@ int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_ac
         if (hs.err != 0) return bfail(hs.err, "batch tile worklist: internal error");
         *out = *b->h_wres;
         out->passes = (int)((hc.visits + b->NT - 1) / std::max(1, b->NT));
-        out->converged = hc.stop ? 0 : 1;
+        out->converged = (hc.stop || hc.capped) ? 0 : 1;
         out->last_increment = (float)tol;
         return HJB_OK;
     }
@@ -1478,7 +1479,9 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
         }
     }
     double rmax = 0.0;
-    bool ok = conv_c && w32.converged;
+    // with tol64 > 0 the FP64 residual decides (the FP32 phase may stop at its
+    // visit caps and leave the rest to the FP64 stage)
+    bool ok = conv_c && (tol64 > 0.0 || w32.converged);
     for (int i = 0; i < b->count; ++i) {
         rmax = std::max(rmax, res[i]);
         if (tol64 > 0.0 && res[i] > tol64) ok = false;

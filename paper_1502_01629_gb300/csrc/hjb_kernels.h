@@ -81,6 +81,11 @@ struct GraphCache {
 
 constexpr int kBandCap = 1 << 20;                          // causal bands per problem
 constexpr unsigned long long kTimeoutNs = 4000000000ull;   // grid-wide wait limit: 4 s
+// visits of one tile in one worklist solve after which it is not put back: the
+// 4097^2 workload with sigma = 0.01 needs 44 visits per tile on average and
+// between 1024 and 2048 at its busiest tile; with sigma = 0 a few tiles keep
+// changing by FP32 rounding (6.6e-7 > tol) and run into the cap (~10 us a visit)
+constexpr int kTileVisitCap = 4096;
 
 // ---------------------------------------------------------------- sweep.cu
 // Halo (cells) a tile needs so that every Q1 vertex of every point lies inside.
@@ -261,6 +266,8 @@ struct AsyncCtl {
     unsigned long long pad1[15];
     int pending;                    // tiles queued or being visited
     int stop;                       // set on the visit cap or an error
+    int capped;                     // a tile reached tile_cap visits (not put back)
+    int pad3;
     unsigned long long visits;      // tile visits so far
     unsigned long long pad2[14];
 };
@@ -312,6 +319,8 @@ struct TileArgs {
     int aq_cap;                // power of two > nt + warps in flight
     AsyncCtl* actl;
     long long max_visits;
+    int tile_cap;              // visits of one tile after which it is not put back
+                               // (<= 0: no cap)
     GridSync* sync;
     WaveResult* res;
     unsigned long long timeout_ns;

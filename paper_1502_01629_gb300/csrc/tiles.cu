@@ -777,11 +777,15 @@ k_wtiles(TileArgs a) {
 // there is work.  The causal order of Section 4.2 is kept for the first visits:
 // a tile is released for its first visit once every neighbour within the
 // interpolation reach (act_radius tiles) with a lower wave has made its first
-// visit (a counter per tile).  After that, a visit that changed some node by
-// more than tol puts back every released neighbour and itself; a tile is in
-// the ring at most once (per-tile state: idle, queued, being visited, being
-// visited and put back again).  The solve ends when no tile is queued or being
-// visited.  Every wait is bounded by a.timeout_ns of global time.
+// visit (a counter per tile, which then counts the tile's visits down from -1).
+// After that, a visit that changed some node by more than tol puts back every
+// released neighbour and itself; a tile is in the ring at most once (per-tile
+// state: idle, queued, being visited, being visited and put back again).  A
+// tile visited tile_cap times is not put back again (FP32 rounding can keep a
+// few tiles changing by more than a tol below what FP32 resolves there; the
+// solve then reports no convergence and leaves those nodes to the FP64 stage).
+// The solve ends when no tile is queued or being visited.  Every wait is
+// bounded by a.timeout_ns of global time.
 
 __device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -955,7 +959,7 @@ k_wtiles_async(TileArgs a) {
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t < 0) break;
         int first = 0;
-        if (lane == 0) first = atomicExch(a.adeps + t, -1) == 0;
+        if (lane == 0) first = atomicSub(a.adeps + t, 1) == 0;
         first = __shfl_sync(0xffffffffu, first, 0);
         int nn = 0;
         int4 chg;
@@ -985,7 +989,15 @@ k_wtiles_async(TileArgs a) {
                     const int ox = (q % aw - ar) * TW, oy = (q / aw - ar) * TH;
                     const int gx = max(0, max(ox - chg.y, chg.x - (ox + TW - 1)));
                     const int gy = max(0, max(oy - chg.w, chg.z - (oy + TH - 1)));
-                    if (gx <= I.R && gy <= I.R && ld_acq_s32(a.adeps + nb) <= 0) aq_push(a, nb);
+                    if (gx <= I.R && gy <= I.R) {
+                        const int d = ld_acq_s32(a.adeps + nb);
+                        if (d <= 0) {
+                            if (a.tile_cap <= 0 || d > -a.tile_cap)
+                                aq_push(a, nb);
+                            else
+                                atomicExch(&a.actl->capped, 1);
+                        }
+                    }
                 }
             }
         }
