@@ -6,6 +6,7 @@ Calls only ``oracle/`` (the FP64 CPU oracle) and the seeded input generators of
 
     python tests/golden/make_full_size.py patchy1025    # three files, one per sigma
     python tests/golden/make_full_size.py large4097     # sampled nodes only
+    python tests/golden/make_full_size.py large4097 --allcore   # the same on every core
     python tests/golden/make_full_size.py batched512    # 256 sampled nodes per instance
 
 What is solved: the fixed point u* of eq. SLscheme3 (Section 3; the same fixed
@@ -15,6 +16,17 @@ nodes ordered by the interpolated coarse solution; the order changes the speed
 only), started from u_hat and stopped at a sup-increment <= 1e-13.  For
 Gauss-Seidel of a beta-contraction the error after a sweep whose increment is
 d is at most d beta / (1 - beta): 5e-11 at 1025^2, 2e-10 at 4097^2.
+
+``--allcore`` (4097^2): the same iteration on every host core
+(oracle/cpu_parallel.c: one node list per block of rows, each in increasing
+order of the start value, the lists relaxed concurrently in place, a chaotic
+relaxation of the same contraction), by nested grids: the same recipe at 257^2
+from the oracle's u_hat, then 1025^2 and 4097^2, each started from (and ordered
+by) the bilinear interpolation of the previous level's solution (the start and
+order change the speed only; from the 129^2 coarse u_hat the 4097^2
+Gauss-Seidel has a slow phase of hundreds of sweeps).  Then the single-threaded
+oracle's residual r = ||T2 u - u|| of the result, which bounds the error by
+r / (1 - beta) whatever the order of the updates was; the file records r.
 
 Stored per workload and sigma (``tests/golden/<name>.npz``):
   u32        -- u* rounded to float32, every node (1025^2 only): enough for the
@@ -93,6 +105,53 @@ def solve_one(job):
     return f"{name}: {sweeps} sweeps, last increment {last:.2e}, residual {res:.2e}, {time.time() - t0:.0f} s"
 
 
+def _allcore_gs(inst, u0, key, tol, name, t0):
+    from oracle import cpu_parallel as cp
+    A = cp.AllCore(inst)
+    u = A.fix(u0)
+    nodes, off = A.gs_lists(key)
+    sweeps, last = 0, np.inf
+    while last > tol and sweeps < 200000:
+        last = A.gs(u, nodes, off)
+        sweeps += 1
+        if sweeps % 25 == 0:
+            print(f"  {name} n={inst.n}: sweep {sweeps}, increment {last:.3e}, {time.time() - t0:.0f} s",
+                  flush=True)
+    if last > tol:
+        raise RuntimeError(f"{name}: no convergence to {tol} at n={inst.n}")
+    return u, sweeps, last
+
+
+def solve_large_allcore(levels=(257, 1025, 4097)):
+    """large4097 on every core by nested grids; the stored residual is the
+    scalar oracle's."""
+    import hjb_inputs as hi
+    import oracle
+    from oracle import cpu_parallel as cp
+    name = large4097_name()
+    t0 = time.time()
+    u, prev = None, None
+    for n in levels:
+        inst = hi.large_instance(n=n, coarse_n=(n - 1) // 32 + 1 if n > 257 else (n - 1) // 8 + 1)
+        O = oracle.Problem.from_instance(inst)
+        if prev is None:
+            start = oracle.patchy_precompute(inst, tol_c=1e-10)["uhat"]
+        else:
+            start = oracle.interp_coarse(prev.n, u, n, inst.mask, O.u_obstacle)
+        tol = TOL if n == levels[-1] else 1e-10
+        u, sweeps, last = _allcore_gs(inst, O.fix_nonfree(start), start, tol, name, t0)
+        print(f"  {name}: level n={n} done, {sweeps} sweeps, {time.time() - t0:.0f} s", flush=True)
+        prev = inst
+    res = O.residual(u)
+    idx = sample_nodes(inst.mask, N_SAMPLES["large4097"])
+    np.savez_compressed(golden_path(name), idx=idx, u64=u[idx], sum64=np.float64(u.sum()),
+                        sweeps=np.int64(sweeps), last_increment=np.float64(last),
+                        residual=np.float64(res), n=np.int64(inst.n), sigma=np.float64(inst.sigma),
+                        allcore=np.int64(cp.threads()), levels=np.array(levels, np.int64))
+    print(f"{name}: {sweeps} all-core sweeps at n={inst.n} on {cp.threads()} threads, last increment "
+          f"{last:.2e}, oracle residual {res:.2e}, {time.time() - t0:.0f} s", flush=True)
+
+
 def solve_batch_instance(k):
     """Instance k of the 512-instance workload (seed 1000 + k): the oracle's
     solution at a seeded sample of its free nodes."""
@@ -130,12 +189,14 @@ def main(argv):
     which = argv[1] if len(argv) > 1 else "patchy1025"
     if which == "patchy1025":
         jobs = [("patchy1025", s) for s in SIGMAS_1025]
+    elif which == "large4097" and "--allcore" in argv:
+        return solve_large_allcore()
     elif which == "large4097":
         jobs = [("large4097", 0.01)]
     elif which == "batched512":
         return main_batched(int(argv[2]) if len(argv) > 2 else max(1, (os.cpu_count() or 2) - 1))
     else:
-        raise SystemExit("usage: make_full_size.py patchy1025|large4097|batched512 [workers]")
+        raise SystemExit("usage: make_full_size.py patchy1025|large4097 [--allcore]|batched512 [workers]")
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         for line in pool.imap_unordered(solve_one, jobs):
             print(line, flush=True)
