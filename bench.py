@@ -296,7 +296,7 @@ def certify_tol(inst) -> float:
 
 def golden_name(workload: str, inst) -> str:
     if workload == "large4097":
-        return "large4097_sigma0.01"
+        return f"large{inst.n}_sigma0.01"
     return f"patchy1025_sigma{inst.sigma:g}"
 
 
@@ -519,7 +519,7 @@ def single_summary(workload: str, insts, labels, R: dict, peaks: dict) -> dict:
 # ------------------------------------------------------------ the batch
 
 def bench_batched(*, steps: int, warmup: int, plain_reps: int, e2e_reps: int, ws: int, device,
-                  stream, peaks: dict, sample_clocks: bool = True):
+                  stream, peaks: dict, sample_clocks: bool = True, certify: bool = True):
     """The many-instance workload: 512 independent problems (n = 8k + 1 in 65..513,
     random Fourier speeds, 1-3 target discs, sigma ~ U[0, 0.1], lambda ~ U[0.5, 2],
     32 controls, 4-16 patches) solved as one batch per step; the comparator is the
@@ -566,18 +566,36 @@ def bench_batched(*, steps: int, warmup: int, plain_reps: int, e2e_reps: int, ws
     umax = np.array([i.h_eff * i.cost / (1.0 - beta_of(i)) for i in insts])
     # error against the oracle at its stored sample of every instance (outside the
     # timed region; tests/golden/batched512.npz, written by the oracle-only script)
-    gate_oracle = None
     gp = os.path.join(GOLDEN_DIR, "batched512.npz")
-    if os.path.exists(gp):
-        g = np.load(gp)
-        vals = B.get_values()
+    g = np.load(gp) if os.path.exists(gp) else None
+
+    def oracle_gate(vals):
+        if g is None:
+            return None
         off = np.concatenate([[0], np.cumsum(g["counts"])])
         errs = np.array([np.abs(vals[k][g["idx"][off[k]:off[k + 1]]] - g["u64"][off[k]:off[k + 1]]).max()
                          for k in range(len(insts))])
         gates = GATE_REL * np.maximum(1.0, np.array([np.abs(v).max() for v in vals]))
-        gate_oracle = {"max_oracle_err": float(errs.max()), "max_err_over_gate": float((errs / gates).max()),
-                       "instances_within_gate": int((errs <= gates).sum()),
-                       "compared": f"{int(g['counts'][0])} seeded free nodes per instance (oracle FP64)"}
+        return {"max_oracle_err": float(errs.max()), "max_err_over_gate": float((errs / gates).max()),
+                "instances_within_gate": int((errs <= gates).sum()),
+                "compared": f"{int(g['counts'][0])} seeded free nodes per instance (oracle FP64)"}
+
+    vals = B.get_values()
+    gate_oracle = oracle_gate(vals)
+    certified = None
+    if certify:
+        # the solve to the one residual that certifies the gate of every instance,
+        # min_i 0.99 gate_i (1 - beta_i), outside the timed region
+        tol_cert = min(0.99 * GATE_REL * max(1.0, float(np.abs(v).max())) * (1.0 - beta_of(i))
+                       for i, v in zip(insts, vals))
+        e0, e1 = event_pair(torch, stream)
+        e0.record(stream)
+        cst, cres = B.solve(tol_c=TOL_C, tol32=TOL32, tol64=tol_cert, check_conv=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        certified = {"tol64_residual": tol_cert, "ms": e0.elapsed_time(e1), "status": cst["status"],
+                     "fp64_passes": cst["fp64_passes"], "max_residual": float(cres.max()),
+                     "oracle": oracle_gate(B.get_values())}
     plain_ms = []
     for _ in range(max(1, plain_reps)):
         flush_l2(flush)
@@ -616,6 +634,7 @@ def bench_batched(*, steps: int, warmup: int, plain_reps: int, e2e_reps: int, ws
             "value_gate": {"rule": "max |u - u_oracle| <= 1e-5 max(1, |u|) per instance at the oracle's "
                                    "stored sample; beside it the certified bound r / (1 - beta)",
                            "oracle": gate_oracle,
+                           "certified_solve": certified,
                            "max_err_bound": float(bounds.max()),
                            "max_residual": float(res.max()),
                            "instances_within_bound": int((bounds <= GATE_REL * np.maximum(1.0, umax)).sum()),
@@ -797,7 +816,8 @@ def ours(args, ws, rank, local):
     peaks = load_peaks()
     if args.workload == "batched512":
         B = bench_batched(steps=args.steps, warmup=args.warmup, plain_reps=args.plain_reps,
-                          e2e_reps=args.e2e_reps, ws=ws, device=device, stream=stream, peaks=peaks)
+                          e2e_reps=args.e2e_reps, ws=ws, device=device, stream=stream, peaks=peaks,
+                          certify=not args.no_certify)
         if rank != 0:
             return None
         out = line(args, ws, B["value"], B["step_ms"],
@@ -833,7 +853,8 @@ def ours(args, ws, rank, local):
                                 **single_summary("patchy1025", [i for _, i in lab1],
                                                  [lb for lb, _ in lab1], P1, peaks))
         B = bench_batched(steps=min(args.steps, 5), warmup=3, plain_reps=1, e2e_reps=1, ws=ws,
-                          device=device, stream=stream, peaks=peaks, sample_clocks=False)
+                          device=device, stream=stream, peaks=peaks, sample_clocks=False,
+                          certify=not args.no_certify)
         ex["batched512"] = dict(config=dict(batched_config(B["insts"], B["n_free"], ws), autotune=B["tune"]),
                                 value=B["value"], ms_per_step=sum(B["step_ms"]) / len(B["step_ms"]),
                                 steps=len(B["step_ms"]), gpu_launches=B["launches"], **B["summary"])
