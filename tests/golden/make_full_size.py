@@ -7,6 +7,7 @@ Calls only ``oracle/`` (the FP64 CPU oracle) and the seeded input generators of
     python tests/golden/make_full_size.py patchy1025    # three files, one per sigma
     python tests/golden/make_full_size.py large4097     # sampled nodes only
     python tests/golden/make_full_size.py large4097 --allcore   # the same on every core
+    python tests/golden/make_full_size.py large2049     # the large recipe at 2049^2, every core
     python tests/golden/make_full_size.py batched512    # 256 sampled nodes per instance
 
 What is solved: the fixed point u* of eq. SLscheme3 (Section 3; the same fixed
@@ -21,8 +22,8 @@ d is at most d beta / (1 - beta): 5e-11 at 1025^2, 2e-10 at 4097^2.
 (oracle/cpu_parallel.c: one node list per block of rows, each in increasing
 order of the start value, the lists relaxed concurrently in place, a chaotic
 relaxation of the same contraction), by nested grids: the same recipe at 257^2
-from the oracle's u_hat, then 1025^2 and 4097^2, each started from (and ordered
-by) the bilinear interpolation of the previous level's solution (the start and
+from the oracle's u_hat, then 1025^2, 2049^2 and 4097^2, each started from (and
+ordered by) the bilinear interpolation of the previous level's solution (the start and
 order change the speed only; from the 129^2 coarse u_hat the 4097^2
 Gauss-Seidel has a slow phase of hundreds of sweeps).  Then the single-threaded
 oracle's residual r = ||T2 u - u|| of the result, which bounds the error by
@@ -67,6 +68,10 @@ def patchy1025_name(sigma: float) -> str:
 
 def large4097_name() -> str:
     return "large4097_sigma0.01"
+
+
+def large_name(n: int) -> str:
+    return f"large{n}_sigma0.01"
 
 
 def sample_nodes(mask: np.ndarray, count: int, seed: int = 20260) -> np.ndarray:
@@ -123,12 +128,12 @@ def _allcore_gs(inst, u0, key, tol, name, t0):
 
 
 def solve_large_allcore(levels=(257, 1025, 4097)):
-    """large4097 on every core by nested grids; the stored residual is the
-    scalar oracle's."""
+    """The large recipe at levels[-1]^2 on every core by nested grids; the
+    stored residual is the scalar oracle's."""
     import hjb_inputs as hi
     import oracle
     from oracle import cpu_parallel as cp
-    name = large4097_name()
+    name = large_name(levels[-1])
     t0 = time.time()
     u, prev = None, None
     for n in levels:
@@ -147,7 +152,8 @@ def solve_large_allcore(levels=(257, 1025, 4097)):
     np.savez_compressed(golden_path(name), idx=idx, u64=u[idx], sum64=np.float64(u.sum()),
                         sweeps=np.int64(sweeps), last_increment=np.float64(last),
                         residual=np.float64(res), n=np.int64(inst.n), sigma=np.float64(inst.sigma),
-                        allcore=np.int64(cp.threads()), levels=np.array(levels, np.int64))
+                        allcore=np.int64(cp.threads()), levels=np.array(levels, np.int64),
+                        coarse_n=np.int64(inst.coarse_n))
     print(f"{name}: {sweeps} all-core sweeps at n={inst.n} on {cp.threads()} threads, last increment "
           f"{last:.2e}, oracle residual {res:.2e}, {time.time() - t0:.0f} s", flush=True)
 
@@ -190,13 +196,15 @@ def main(argv):
     if which == "patchy1025":
         jobs = [("patchy1025", s) for s in SIGMAS_1025]
     elif which == "large4097" and "--allcore" in argv:
-        return solve_large_allcore()
+        return solve_large_allcore((257, 1025, 2049, 4097))
+    elif which == "large2049":
+        return solve_large_allcore((257, 1025, 2049))
     elif which == "large4097":
         jobs = [("large4097", 0.01)]
     elif which == "batched512":
         return main_batched(int(argv[2]) if len(argv) > 2 else max(1, (os.cpu_count() or 2) - 1))
     else:
-        raise SystemExit("usage: make_full_size.py patchy1025|large4097 [--allcore]|batched512 [workers]")
+        raise SystemExit("usage: make_full_size.py patchy1025|large4097 [--allcore]|large2049|batched512 [workers]")
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         for line in pool.imap_unordered(solve_one, jobs):
             print(line, flush=True)
