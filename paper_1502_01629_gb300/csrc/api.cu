@@ -219,6 +219,7 @@ struct hjb_problem {
     bool has_drift = false;
     // general terms (Section 5.3)
     bool gen = false, along = false;
+    bool ctrl_sym = false;         // 64 controls, a_{m+32} = -a_m in FP32
     float* sigf = nullptr;         // sigma(x), n*n
     float* costf = nullptr;        // l(x), n*n
     float* costf_c = nullptr;      // l(x) at the coarse nodes
@@ -685,6 +686,14 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
             c32[m] = make_float2((float)controls[2 * m], (float)controls[2 * m + 1]);
             c64[m] = make_double2(controls[2 * m], controls[2 * m + 1]);
         }
+        // opposite pairs a_{m+32} = -a_m up to 1e-12 (evenly spaced directions
+        // from cos/sin: components near zero differ by ~1e-16); the foot points
+        // of such a pair then mirror each other to far below the FP32 rounding
+        // of the cell fractions (6e-8 of a cell)
+        p->ctrl_sym = na == 64;
+        for (int m = 0; m < 32 && p->ctrl_sym; ++m)
+            p->ctrl_sym = std::fabs(controls[2 * (m + 32)] + controls[2 * m]) <= 1e-12 &&
+                          std::fabs(controls[2 * (m + 32) + 1] + controls[2 * m + 1]) <= 1e-12;
         CUP(palloc(&p->ctrl32, na * sizeof(float2), p->st));
         CUP(palloc(&p->ctrl64, na * sizeof(double2), p->st));
         CUP(cudaMemcpyAsync(p->ctrl32, c32.data(), na * sizeof(float2), cudaMemcpyHostToDevice, p->st));
@@ -1133,6 +1142,7 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
     a.period = D;
     a.local_sweeps = p->desc.local_sweeps;
     a.node_lanes = p->desc.visit == 2 ? 1 : 0;
+    a.ctrl_sym = p->ctrl_sym && !p->gen && p->drift == nullptr ? 1 : 0;
     {
         // the self weight of eq. self-dependency is zero for every candidate when
         // each diffusion point lies more than a cell from the node: offset d

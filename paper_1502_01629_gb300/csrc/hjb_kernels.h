@@ -307,6 +307,8 @@ struct TileArgs {
     int no_self;               // warp tiles, FP32: 2 = no candidate has a self weight (scheme 2),
                                // 1 = none in interior tiles (diffusion offset > 1 + the drift's
                                // reach in cells), 0 = compute it
+    int ctrl_sym;              // 1: 64 controls with a_{m+32} = -a_m (to 1e-12): the second
+                               // control of a lane takes the mirror of the first's geometry
     int max_steps;
     float tol;
     // asynchronous worklist (schedule 3): per-tile state 0 idle, 1 queued,

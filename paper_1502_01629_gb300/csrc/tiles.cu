@@ -261,6 +261,78 @@ __device__ __forceinline__ Geo32<SIG> geo32(const GridView& g, int scheme, float
     return r;
 }
 
+// The geometry of a control a and of its opposite -a together (interior tiles:
+// no projection).  The points of -a are the mirror images of those of a, so
+// each axis cell of -a follows from one of a: floor(-y) = -floor(y) - 1 and
+// frac(-y) = 1 - frac(y) when y is not an integer (-floor(y) and 0 when it is);
+// the self weights, and with them D, are the same.  Same cells as geo32 on -a
+// (the floors are exact); the fractions agree to an ulp.
+__device__ __forceinline__ void mirror_cell(const Axis<float>& c, int& off, float& fr) {
+    const bool f = c.fr > 0.0f;
+    off = f ? -c.off - 1 : -c.off;
+    fr = f ? 1.0f - c.fr : 0.0f;
+}
+
+template <bool SIG, bool NOL>
+__device__ __forceinline__ void geo32_pair(const GridView& g, int scheme, float sc, float bq, int kb,
+                                           int W, float2 a, Geo32<SIG>& ra, Geo32<SIG>& rb) {
+    const float fx = sc * a.x;
+    const float fy = sc * a.y;
+    float L = 0.0f;
+    if constexpr (SIG) {
+        const float d = g.d32;
+        const Axis<float> xm = axis_cell<float, false>(fx - d, 0.0f, 0.0f, 0.0f);
+        const Axis<float> x0 = axis_cell<float, false>(fx, 0.0f, 0.0f, 0.0f);
+        const Axis<float> xp = axis_cell<float, false>(fx + d, 0.0f, 0.0f, 0.0f);
+        const Axis<float> ym = axis_cell<float, false>(fy - d, 0.0f, 0.0f, 0.0f);
+        const Axis<float> y0 = axis_cell<float, false>(fy, 0.0f, 0.0f, 0.0f);
+        const Axis<float> yp = axis_cell<float, false>(fy + d, 0.0f, 0.0f, 0.0f);
+        ra.o[0] = kb + y0.off * W + xp.off;
+        ra.o[1] = kb + y0.off * W + xm.off;
+        ra.o[2] = kb + yp.off * W + x0.off;
+        ra.o[3] = kb + ym.off * W + x0.off;
+        ra.fx[0] = xp.fr; ra.fx[1] = xm.fr; ra.fx[2] = x0.fr;
+        ra.fy[0] = y0.fr; ra.fy[1] = yp.fr; ra.fy[2] = ym.fr;
+        // -a: its +d point mirrors a's -d point and so on
+        int oxp, oxm, ox0, oyp, oym, oy0;
+        float fxp, fxm, fx0, fyp, fym, fy0;
+        mirror_cell(xm, oxp, fxp);
+        mirror_cell(xp, oxm, fxm);
+        mirror_cell(x0, ox0, fx0);
+        mirror_cell(ym, oyp, fyp);
+        mirror_cell(yp, oym, fym);
+        mirror_cell(y0, oy0, fy0);
+        rb.o[0] = kb + oy0 * W + oxp;
+        rb.o[1] = kb + oy0 * W + oxm;
+        rb.o[2] = kb + oyp * W + ox0;
+        rb.o[3] = kb + oym * W + ox0;
+        rb.fx[0] = fxp; rb.fx[1] = fxm; rb.fx[2] = fx0;
+        rb.fy[0] = fy0; rb.fy[1] = fyp; rb.fy[2] = fym;
+        if constexpr (!NOL) L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
+    } else {
+        const Axis<float> x0 = axis_cell<float, false>(fx, 0.0f, 0.0f, 0.0f);
+        const Axis<float> y0 = axis_cell<float, false>(fy, 0.0f, 0.0f, 0.0f);
+        ra.o[0] = kb + y0.off * W + x0.off;
+        ra.fx[0] = x0.fr;
+        ra.fy[0] = y0.fr;
+        int ox, oy;
+        float frx, fry;
+        mirror_cell(x0, ox, frx);
+        mirror_cell(y0, oy, fry);
+        rb.o[0] = kb + oy * W + ox;
+        rb.fx[0] = frx;
+        rb.fy[0] = fry;
+        if constexpr (!NOL) L = x0.sw * y0.sw;
+    }
+    if constexpr (NOL) {
+        ra.rD = 1.0f;
+    } else {
+        const float D = scheme == 3 ? fmaf(-bq, L, 1.0f) : 1.0f;
+        ra.rD = D > 0.0f ? rcp_approx(D) : -1.0f;
+    }
+    rb.rD = ra.rD;
+}
+
 // Q1 value at a point minus uk from the vertex block at su[o] (row stride W).
 __device__ __forceinline__ float bil32(const float* su, int o, int W, float frx, float fry, float uk) {
     const float v00 = su[o], v10 = su[o + 1], v01 = su[o + W], v11 = su[o + W + 1];
@@ -513,9 +585,10 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
     // FP32, no drift, 33..64 controls: two controls per lane (m = lane and
     // lane + 32), both geometries formed at the node, the lane's smaller
     // candidate into the warp minimum
-    auto visit32k2 = [&](auto clamp_tag, auto nol_tag) {
+    auto visit32k2 = [&](auto clamp_tag, auto nol_tag, auto sym_tag) {
       constexpr bool CL = decltype(clamp_tag)::value;
       constexpr bool NOL = decltype(nol_tag)::value;
+      constexpr bool SYM = decltype(sym_tag)::value && !CL;
       const float s = g.s32, beta = g.beta32, hl = g.hl32;
       const float bq = SIG ? beta * 0.25f : beta;
       const float omb = 1.0f - beta;
@@ -544,8 +617,13 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             const int ex = e % TW, ey = e / TW;
             const int kb = (R + ey) * W + (R + ex);
             const float sc2 = s * c;
-            const Geo32<SIG> ga = geo32<SIG, CL, NOL>(g, a.scheme, sc2, bq, bi + ex, bj + ey, kb, W, ac0);
-            const Geo32<SIG> gb = geo32<SIG, CL, NOL>(g, a.scheme, sc2, bq, bi + ex, bj + ey, kb, W, ac1);
+            Geo32<SIG> ga, gb;
+            if constexpr (SYM) {
+                geo32_pair<SIG, NOL>(g, a.scheme, sc2, bq, kb, W, ac0, ga, gb);
+            } else {
+                ga = geo32<SIG, CL, NOL>(g, a.scheme, sc2, bq, bi + ex, bj + ey, kb, W, ac0);
+                gb = geo32<SIG, CL, NOL>(g, a.scheme, sc2, bq, bi + ex, bj + ey, kb, W, ac1);
+            }
             const float uk = sf[kb];
             const float cc0 = fmaf(-omb, uk, hl);
             const float va = cand(ga, uk, cc0);
@@ -584,11 +662,16 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
         } else if (g.drift == nullptr && na <= 64 && !g.gen) {
             piped = true;
             if (interior) {
-                if (nol) visit32k2(std::false_type{}, std::true_type{});
-                else visit32k2(std::false_type{}, std::false_type{});
+                if (a.ctrl_sym) {
+                    if (nol) visit32k2(std::false_type{}, std::true_type{}, std::true_type{});
+                    else visit32k2(std::false_type{}, std::false_type{}, std::true_type{});
+                } else {
+                    if (nol) visit32k2(std::false_type{}, std::true_type{}, std::false_type{});
+                    else visit32k2(std::false_type{}, std::false_type{}, std::false_type{});
+                }
             } else {
-                if (nol) visit32k2(std::true_type{}, std::true_type{});
-                else visit32k2(std::true_type{}, std::false_type{});
+                if (nol) visit32k2(std::true_type{}, std::true_type{}, std::false_type{});
+                else visit32k2(std::true_type{}, std::false_type{}, std::false_type{});
             }
         }
     }
