@@ -480,8 +480,12 @@ int hjb_batch_create_lists(const hjb_batch_desc* desc, int32_t count, const hjb_
  * pipeline steps; ms_stage: [0] FP32
  * passes, [1] residuals, [2] FP64 passes, [3] coarse solves, [4] pre-computation.
  * An instance above tol64 first gets at most two more FP32 phases (tolerance /4
- * each, while above the FP32 floor), then FP64 passes; both start warm (that
- * instance's tiles visited once in checkerboard order, then the queues).  The
+ * each, while above the FP32 floor), then (scheme 3) at most 12 rounds of the
+ * mixed-precision correction of hjb_solve_patches, per instance (an instance
+ * leaves after two rounds in a row that do not halve its residual), then FP64
+ * passes; the FP32 phases and FP64 passes start warm (that instance's tiles
+ * visited once in checkerboard order, then the queues).  stats->corr_sweeps:
+ * the correction sweeps (each instance's count, the largest per round, summed).  The
  * worklist schedule caps the visits of one tile as hjb_solve_patches does; with
  * tol64 > 0 the FP64 residuals decide the status.
  * Errors: HJB_ERR_NOT_CONVERGED (a cap was hit, or an FP64 residual stays above

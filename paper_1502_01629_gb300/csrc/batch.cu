@@ -271,7 +271,8 @@ template <bool SIG>
 __global__ void __launch_bounds__(kRX * kRBY)
 k_b_residual(const BatchInst* __restrict__ I, const int4* __restrict__ rblk,
              const double* __restrict__ u_all, const float* __restrict__ margin,
-             const uint8_t* __restrict__ active, unsigned long long* res_bits) {
+             const uint8_t* __restrict__ active, unsigned long long* res_bits,
+             float* __restrict__ rfield, uint8_t* __restrict__ afield) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int4 bl = rblk[blockIdx.x];
     if (active && !active[bl.x]) return;
@@ -313,9 +314,25 @@ k_b_residual(const BatchInst* __restrict__ I, const int4* __restrict__ rblk,
         const int j = bl.z * kRY + threadIdx.y + r * kRBY;
         if (i >= n || j >= n) continue;
         const size_t k = (size_t)j * n + i;
-        if (g.mask[k] != kFree) continue;
+        if (g.mask[k] != kFree) {
+            if (rfield) {
+                rfield[B.node_off + k] = 0.0f;
+                afield[B.node_off + k] = 0;
+            }
+            continue;
+        }
         const int off = (j - gy0) * W + (i - gx0);
-        lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin[bl.x]));
+        if (rfield) {
+            // the residual r = T2 u - u and its minimising control, for the
+            // correction rounds of the FP64 stage
+            double v;
+            int m;
+            lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin[bl.x], &v, &m));
+            rfield[B.node_off + k] = (float)v;
+            afield[B.node_off + k] = (uint8_t)m;
+        } else {
+            lmax = fmax(lmax, residual_node<SIG>(g, i, j, k, t32, t64, off, W, c32, c64, margin[bl.x]));
+        }
     }
     const double bm = block_max<double>(lmax, red);
     if (tid == 0) atomic_max_nonneg(res_bits + bl.x, bm);
@@ -394,6 +411,106 @@ __global__ void k_b_jacobi_mark(int count, float tol, int sweep, uint8_t* active
     } else {
         atomicAdd(n_active, 1);
     }
+}
+
+// One Jacobi sweep of the correction equation e = beta P_a e + r of the FP64
+// stage (the residual r = T2 u - u and its minimising control a per node, from
+// k_b_residual with fields) over the tiles of the active instances, in the
+// self-weight-free form of eq. SLscheme3 (one control per node); per-instance
+// sup-increment in inc_bits.  Non-free nodes hold e = 0.
+template <bool SIG>
+__global__ void __launch_bounds__(kRX * kRBY)
+k_b_corr_sweep(const BatchInst* __restrict__ I, const int4* __restrict__ rblk,
+               const float* __restrict__ r_all, const uint8_t* __restrict__ a_all,
+               const float* __restrict__ ein_all, float* __restrict__ eout_all,
+               const uint8_t* __restrict__ active, unsigned int* inc_bits) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int4 bl = rblk[blockIdx.x];
+    if (!active[bl.x]) return;
+    const BatchInst& B = I[bl.x];
+    const GridView& g = B.g;
+    float* tile = reinterpret_cast<float*>(smem);
+    __shared__ float red[32];
+    const int n = g.n;
+    const int R = B.R;
+    const int W = kRX + 2 * R;
+    const int H = kRY + 2 * R;
+    const float* ein = ein_all + B.node_off;
+    float* eout = eout_all + B.node_off;
+    const float* r = r_all + B.node_off;
+    const uint8_t* act = a_all + B.node_off;
+    const int gx0 = bl.y * kRX - R;
+    const int gy0 = bl.z * kRY - R;
+    const int tid = threadIdx.y * kRX + threadIdx.x;
+    for (int t = tid; t < W * H; t += kRX * kRBY) {
+        const int ty = t / W;
+        const int tx = t - ty * W;
+        const int gx = min(max(gx0 + tx, 0), n - 1);
+        const int gy = min(max(gy0 + ty, 0), n - 1);
+        tile[t] = ein[(size_t)gy * n + gx];
+    }
+    __syncthreads();
+    const float beta = g.beta32, s = g.s32;
+    const float bq = SIG ? beta * 0.25f : beta;
+    float lmax = 0.0f;
+    for (int rr = 0; rr < kRY / kRBY; ++rr) {
+        const int i = bl.y * kRX + threadIdx.x;
+        const int j = bl.z * kRY + threadIdx.y + rr * kRBY;
+        if (i >= n || j >= n) continue;
+        const size_t k = (size_t)j * n + i;
+        if (g.mask[k] != kFree) {
+            eout[k] = 0.0f;
+            continue;
+        }
+        const float* base = tile + (j - gy0) * W + (i - gx0);
+        const float ek = base[0];
+        auto U = [&](int dx, int dy) { return base[dy * W + dx]; };
+        float bx = 0.0f, by = 0.0f;
+        if (g.drift) {
+            const float2 b2 = g.drift[k];
+            bx = b2.x;
+            by = b2.y;
+        }
+        const NodeBox<float> box = node_box<float>(i, j, n);
+        const float c0 = fmaf(-(1.0f - beta), ek, r[k]);
+        float N, D;
+        candidate<float, SIG, true>(g, 3, box, s, bq, c0, ek, g.speed[k], bx, by, g.ctrl32[act[k]], U, N, D);
+        const float de = N / D;
+        eout[k] = ek + de;
+        lmax = fmaxf(lmax, fabsf(de));
+    }
+    const float bm = block_max<float>(lmax, red);
+    if (tid == 0 && bm > 0.0f) atomicMax(inc_bits + bl.x, __float_as_uint(bm));
+}
+
+// After a correction sweep: instances whose sup-increment is <= their own
+// tolerance stop (sweep count recorded: its parity tells the buffer).
+__global__ void k_b_corr_mark(int count, const float* __restrict__ tol, int sweep, uint8_t* active,
+                              unsigned int* inc_bits, int* sweeps, int* n_active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count || !active[b]) return;
+    const float inc = __uint_as_float(inc_bits[b]);
+    inc_bits[b] = 0u;
+    if (inc <= tol[b]) {
+        active[b] = 0;
+        sweeps[b] = sweep;
+    } else {
+        atomicAdd(n_active, 1);
+    }
+}
+
+// u64 += e on the free nodes of the instances flagged in `sel` (e from buffer a
+// or b by the parity of the instance's sweep count)
+__global__ void k_b_add_corr(const BatchInst* __restrict__ I, const int2* __restrict__ blk,
+                             const float* __restrict__ ea, const float* __restrict__ eb,
+                             const int* __restrict__ sweeps, const uint8_t* __restrict__ sel, double* u64) {
+    const int2 bl = blk[blockIdx.x];
+    if (!sel[bl.x]) return;
+    const BatchInst& B = I[bl.x];
+    const int k = bl.y + threadIdx.x;
+    if (k >= B.g.n * B.g.n || B.g.mask[k] != kFree) return;
+    const float* src = (sweeps[bl.x] & 1) ? eb : ea;
+    u64[B.node_off + k] += (double)src[B.node_off + k];
 }
 
 // u64 = u (FP32 result of each instance, from buffer a or b by the parity of
@@ -531,6 +648,11 @@ struct hjb_batch {
     unsigned long long* res_bits = nullptr;
     float* margin = nullptr;
     uint8_t* active = nullptr;
+    // correction rounds of the FP64 stage (allocated on first use)
+    float* corr_r = nullptr;             // N: residual field
+    uint8_t* corr_a = nullptr;           // N: its minimising control
+    float* corr_tol = nullptr;           // count: inner tolerances
+    uint8_t* corr_sel = nullptr;         // count: instances of the round
     unsigned int* inc_bits = nullptr;
     int* j_sweeps = nullptr;
     int* n_active = nullptr;
@@ -1119,6 +1241,7 @@ void hjb_batch_destroy(hjb_batch* b) {
     dfree(b->tile_wave, b->st); dfree(b->tile_key, b->st); dfree(b->tile_list, b->st); dfree(b->tile_inc, b->st); dfree(b->stamp, b->st);
     dfree(b->queue, b->st); dfree(b->qcount, b->st); dfree(b->step_inc, b->st); dfree(b->sched_count, b->st); dfree(b->sched_off, b->st);
     dfree(b->max_key, b->st); dfree(b->c_sweeps, b->st); dfree(b->c_inc, b->st); dfree(b->res_bits, b->st); dfree(b->margin, b->st);
+    dfree(b->corr_r, b->st); dfree(b->corr_a, b->st); dfree(b->corr_tol, b->st); dfree(b->corr_sel, b->st);
     dfree(b->active, b->st); dfree(b->inc_bits, b->st); dfree(b->j_sweeps, b->st); dfree(b->n_active, b->st); dfree(b->sync, b->st);
     dfree(b->coarse_init, b->st); dfree(b->d_coarse_off, b->st); dfree(b->c_fallback, b->st);
     dfree(b->cb_wave, b->st); dfree(b->cb_key, b->st); dfree(b->cb_list, b->st); dfree(b->cb_off, b->st); dfree(b->cb_count, b->st);
@@ -1329,7 +1452,7 @@ int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_ac
 
 // FP64 residuals of the instances (all, or those flagged in b->active); u64
 // must hold the values.  res[i] is updated for the evaluated instances.
-int stage_residual(hjb_batch* b, bool use_active, std::vector<double>& res) {
+int stage_residual(hjb_batch* b, bool use_active, std::vector<double>& res, bool fields = false) {
     BCU(cudaMemsetAsync(b->res_bits, 0, sizeof(unsigned long long) * b->count, b->st));
     const size_t smem = residual_screened_smem(b->na, b->max_R);
     auto kern = b->any_sigma ? k_b_residual<true> : k_b_residual<false>;
@@ -1337,7 +1460,9 @@ int stage_residual(hjb_batch* b, bool use_active, std::vector<double>& res) {
         BCU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     count_launches(1);
     kern<<<b->nrblk, dim3(kRX, kRBY), smem, b->st>>>(b->dinst, b->rblk, b->u64, b->margin,
-                                                      use_active ? b->active : nullptr, b->res_bits);
+                                                      use_active ? b->active : nullptr, b->res_bits,
+                                                      fields ? b->corr_r : nullptr,
+                                                      fields ? b->corr_a : nullptr);
     BCU(cudaGetLastError());
     std::vector<unsigned long long> bits(b->count);
     std::vector<uint8_t> act;
@@ -1354,6 +1479,108 @@ int stage_residual(hjb_batch* b, bool use_active, std::vector<double>& res) {
         double v;
         std::memcpy(&v, &bits[i], sizeof(v));
         res[i] = v;
+    }
+    return HJB_OK;
+}
+
+// The FP64 stage by mixed-precision correction for the instances above tol64
+// (scheme 3; every batch instance has a discount): per round, with the FP64
+// residual r = T2 u - u and its minimising controls a (residual fields), FP32
+// Jacobi sweeps of e = beta P_a e + r until each instance's sup-increment is below
+// max(0.2 tol64, 2^-21 r_i / (1 - beta_i)), u += e in FP64, the residual again.
+// Howard's policy iteration per instance: a round can raise an instance's
+// residual where its minimising controls switch; an instance leaves after two
+// rounds in a row that do not halve its residual, or if it grows past 1e3 times
+// its first value (the FP64 passes then take it over).  The e buffers are the
+// FP32 value arrays (u32, u32b), free once the values are in u64.
+int stage_correction(hjb_batch* b, double tol64, int rounds, std::vector<double>& res, int* sweeps_out,
+                     long long* nodes_out, int* n_res) {
+    const int count = b->count;
+    const size_t N = (size_t)b->N;
+    if (!b->corr_r) {
+        BCU(dalloc(b->corr_r, N, b->st));
+        BCU(dalloc(b->corr_a, N, b->st));
+        BCU(dalloc(b->corr_tol, (size_t)count, b->st));
+        BCU(dalloc(b->corr_sel, (size_t)count, b->st));
+    }
+    constexpr int kMaxSweeps = 20000;
+    const int big = 0x7fffffff;
+    const std::vector<double> res0 = res;
+    std::vector<int> stalled(count, 0);
+    std::vector<uint8_t> sel(count);
+    std::vector<float> tin(count);
+    const size_t smem = (size_t)(kRX + 2 * b->max_R) * (kRY + 2 * b->max_R) * sizeof(float);
+    auto kern = b->any_sigma ? k_b_corr_sweep<true> : k_b_corr_sweep<false>;
+    if (smem > 48 * 1024)
+        BCU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bool fields = false;
+    for (int round = 0; round < rounds; ++round) {
+        int n_sel = 0;
+        for (int i = 0; i < count; ++i) {
+            sel[i] = res[i] > tol64 && stalled[i] < 2 && res[i] <= 1e3 * res0[i];
+            n_sel += sel[i];
+            const double omb = 1.0 - b->hinst[i].g.beta64;
+            tin[i] = (float)std::max(0.2 * tol64, std::ldexp(res[i] / omb, -21));
+        }
+        if (n_sel == 0) break;
+        BCU(cudaMemcpyAsync(b->corr_sel, sel.data(), count, cudaMemcpyHostToDevice, b->st));
+        BCU(cudaMemcpyAsync(b->active, sel.data(), count, cudaMemcpyHostToDevice, b->st));
+        if (!fields) {
+            // residual fields of the selected instances (their residuals unchanged)
+            std::vector<double> r2 = res;
+            int rc = stage_residual(b, true, r2, true);
+            if (rc) return rc;
+            ++*n_res;
+            fields = true;
+        }
+        BCU(cudaMemcpyAsync(b->corr_tol, tin.data(), sizeof(float) * count, cudaMemcpyHostToDevice, b->st));
+        BCU(cudaMemsetAsync(b->u32, 0, sizeof(float) * N, b->st));
+        BCU(cudaMemsetAsync(b->u32b, 0, sizeof(float) * N, b->st));
+        BCU(cudaMemsetAsync(b->inc_bits, 0, sizeof(unsigned int) * count, b->st));
+        std::vector<int> init(count, big);
+        BCU(cudaMemcpyAsync(b->j_sweeps, init.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->st));
+        int sweep = 0, h_active = n_sel;
+        while (sweep < kMaxSweeps && h_active > 0) {
+            const float* ein = (sweep & 1) ? b->u32b : b->u32;
+            float* eout = (sweep & 1) ? b->u32 : b->u32b;
+            count_launches(1);
+            kern<<<b->nrblk, dim3(kRX, kRBY), smem, b->st>>>(b->dinst, b->rblk, b->corr_r, b->corr_a, ein, eout,
+                                                              b->active, b->inc_bits);
+            ++sweep;
+            BCU(cudaMemsetAsync(b->n_active, 0, sizeof(int), b->st));
+            count_launches(1);
+            k_b_corr_mark<<<(count + 255) / 256, 256, 0, b->st>>>(count, b->corr_tol, sweep, b->active,
+                                                                b->inc_bits, b->j_sweeps, b->n_active);
+            BCU(cudaGetLastError());
+            if ((sweep & 15) == 0 || sweep == kMaxSweeps) {
+                BCU(cudaMemcpyAsync(&h_active, b->n_active, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+                BCU(cudaStreamSynchronize(b->st));
+            }
+        }
+        std::vector<int> sw(count);
+        BCU(cudaMemcpyAsync(sw.data(), b->j_sweeps, sizeof(int) * count, cudaMemcpyDeviceToHost, b->st));
+        BCU(cudaStreamSynchronize(b->st));
+        int smax = 0;
+        for (int i = 0; i < count; ++i) {
+            if (!sel[i]) continue;
+            if (sw[i] == big) sw[i] = sweep;     // still moving: the last sweep's values
+            smax = std::max(smax, sw[i]);
+            *nodes_out += (long long)sw[i] * b->n_free[i];
+        }
+        *sweeps_out += smax;
+        BCU(cudaMemcpyAsync(b->j_sweeps, sw.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->st));
+        count_launches(1);
+        k_b_add_corr<<<b->nfblk, kBT, 0, b->st>>>(b->dinst, b->fblk, b->u32, b->u32b, b->j_sweeps, b->corr_sel,
+                                                  b->u64);
+        BCU(cudaGetLastError());
+        // the new residuals (and fields) of the round's instances
+        BCU(cudaMemcpyAsync(b->active, sel.data(), count, cudaMemcpyHostToDevice, b->st));
+        const std::vector<double> before = res;
+        int rc = stage_residual(b, true, res, true);
+        if (rc) return rc;
+        ++*n_res;
+        for (int i = 0; i < count; ++i)
+            if (sel[i]) stalled[i] = res[i] < 0.5 * before[i] ? 0 : stalled[i] + 1;
     }
     return HJB_OK;
 }
@@ -1411,6 +1638,8 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
     int n_res = 0;
     unsigned long long nodes64 = 0;
     int passes64 = 0;
+    int corr_sweeps = 0;
+    long long corr_nodes = 0;
     if (tol64 > 0.0) {
         BTimer t(b->st);
         count_launches(1);
@@ -1450,6 +1679,13 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
             if (rc) return rc;
             ++n_res;
             ms_res += tr.stop();
+        }
+        // mixed-precision correction rounds (scheme 3)
+        if (b->scheme == 3) {
+            BTimer tc(b->st);
+            rc = stage_correction(b, tol64, 12, res, &corr_sweeps, &corr_nodes, &n_res);
+            if (rc) return rc;
+            ms64 += tc.stop();
         }
         // FP64 passes for the instances still above tol64
         double tol_pass = tol64;
@@ -1494,9 +1730,12 @@ int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int3
         stats->sweeps = w32.passes + passes64;
         stats->fp32_passes = w32.passes;
         stats->fp64_passes = passes64;
-        stats->node_updates = (long long)w32.nodes + (long long)nodes64;
+        stats->node_updates = (long long)w32.nodes + (long long)nodes64 + corr_nodes;
         stats->fp64_node_updates = (long long)nodes64;
-        stats->node_control_updates = (nodes_c + stats->node_updates + (long long)n_res * nf) * b->na;
+        // a correction sweep evaluates one control per node
+        stats->node_control_updates =
+            (nodes_c + (long long)w32.nodes + (long long)nodes64 + (long long)n_res * nf) * b->na + corr_nodes;
+        stats->corr_sweeps = corr_sweeps;
         stats->residual_evals = n_res;
         stats->residual = tol64 > 0.0 ? rmax : -1.0;
         stats->increment = w32.last_increment;
