@@ -66,22 +66,28 @@ k_conv3x3_tc(const bf16* __restrict__ x, const uint8_t* __restrict__ wpack,
         uint4* dst = reinterpret_cast<uint4*>(sB);
         for (int i = tid; i < NPAD * KC; i += kConvThreads) dst[i] = src[i];
     }
-    // e -> (m & 7) fastest, then the chunk kc, then m >> 3: a warp writes four
-    // whole 128-byte core-matrix blocks (no bank conflicts) and reads the same
-    // tap of 8 consecutive pixels (contiguous in NHWC)
-    for (int e = tid; e < 128 * KC; e += kConvThreads) {
-        const int rest = e >> 3, mh = rest / KC;
-        const int kc = rest - mh * KC, m = mh * 8 + (e & 7);
-        const int t = kc / (CIN / 8), cc = kc - t * (CIN / 8);
+    // thread m gathers pixel p0 + m (its image coordinates formed once), chunk by
+    // chunk: at a given chunk a warp writes four whole 128-byte core-matrix
+    // blocks (no bank conflicts) and reads the same tap of 32 consecutive pixels
+    {
+        const int m = tid;
         const long long p = p0 + m;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (p < total) {
-            const int b = (int)(p / HW), r = (int)(p - (long long)b * HW);
-            const int yy = r / W + (t / 3 - 1) * dil, xq = r % W + (t % 3 - 1) * dil;
-            if (yy >= 0 && yy < H && xq >= 0 && xq < W)
-                v = *reinterpret_cast<const uint4*>(x + ((size_t)b * HW + (size_t)yy * W + xq) * CIN + cc * 8);
+        const bool pv = p < total;
+        int py = 0, px = 0;
+        if (pv) {
+            const int r = (int)(p % HW);
+            py = r / W;
+            px = r - py * W;
         }
-        *reinterpret_cast<uint4*>(sA + ((m >> 3) * KC + kc) * 128 + (m & 7) * 16) = v;
+        for (int kc = 0; kc < KC; ++kc) {
+            const int t = kc / (CIN / 8), cc = kc - t * (CIN / 8);
+            const int dyt = (t / 3 - 1) * dil, dxt = (t % 3 - 1) * dil;
+            const int yy = py + dyt, xq = px + dxt;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (pv && yy >= 0 && yy < H && xq >= 0 && xq < W)
+                v = *reinterpret_cast<const uint4*>(x + (size_t)(p + (long long)dyt * W + dxt) * CIN + cc * 8);
+            *reinterpret_cast<uint4*>(sA + ((m >> 3) * KC + kc) * 128 + (m & 7) * 16) = v;
+        }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -254,27 +260,49 @@ k_conv3x3_wgrad_tc(const bf16* __restrict__ x, const bf16* __restrict__ dy, int 
     bool ok = true;
     uint32_t phase = 0;
     int tiles = 0;
+    // the transposes into the K-major layout (pixels along K) go through
+    // stmatrix.trans: a warp takes 32 pixels q0 .. q0 + 31 and one 8-channel
+    // chunk as four 8x8 matrices (rows = pixels, lane L holding channels
+    // 2(L%4), +1 of pixel q0 + 8i + L/4 in matrix i) and stores each transposed:
+    // row j = channel j of the chunk over 8 consecutive pixels, one 16-byte
+    // canonical row (whole 128-byte core-matrix blocks, no bank conflicts)
+    const int fr = lane >> 2, fc = lane & 3;       // fragment row (pixel), column pair
+    const int sm = lane >> 3, sj = lane & 7;       // stored matrix, row (channel)
+    const int q0 = warp * 32;                      // the warp's 32 pixels of a tile
     for (long long s = pbeg; s < pend; s += 128, ++tiles) {
+        // the lane's four fragment pixels s + q0 + 8i + fr, coordinates formed once
+        long long pp[4];
+        int py[4], px[4];
+        bool pv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            pp[i] = s + q0 + 8 * i + fr;
+            pv[i] = pp[i] < pend;
+            py[i] = px[i] = 0;
+            if (pv[i]) {
+                const int r = (int)(pp[i] % HW);
+                py[i] = r / W;
+                px[i] = r - py[i] * W;
+            }
+        }
         // A: element (m, q) = x at pixel s + q shifted by tap t = m / CIN, channel
         // m % CIN (0 outside the image or past the chunk); row K = 1 for a pixel
-        for (int e = tid; e < 128 * 9 * (CIN / 8); e += kConvThreads) {
-            const int q = e % 128, rest = e / 128;
-            const int t = rest / (CIN / 8), cc = rest - t * (CIN / 8);
-            const long long p = s + q;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < pend) {
-                const int b = (int)(p / HW), r = (int)(p - (long long)b * HW);
-                const int yy = r / W + (t / 3 - 1) * dil, xq = r % W + (t % 3 - 1) * dil;
-                if (yy >= 0 && yy < H && xq >= 0 && xq < W)
-                    v = *reinterpret_cast<const uint4*>(x + ((size_t)b * HW + (size_t)yy * W + xq) * CIN + cc * 8);
-            }
-            const bf16* hv = reinterpret_cast<const bf16*>(&v);
+        for (int it = 0; it < 9 * (CIN / 8); ++it) {
+            const int t = it / (CIN / 8), cc = it - t * (CIN / 8);
+            const int dyt = (t / 3 - 1) * dil, dxt = (t % 3 - 1) * dil;
+            uint32_t rv[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int m = t * CIN + cc * 8 + j;
-                *reinterpret_cast<bf16*>(sA + (size_t)(m >> 7) * 128 * 128 * 2 + tc::canon_offset(m & 127, q, 128)) =
-                    hv[j];
+            for (int i = 0; i < 4; ++i) {
+                const int yy = py[i] + dyt, xq = px[i] + dxt;
+                rv[i] = (pv[i] && yy >= 0 && yy < H && xq >= 0 && xq < W)
+                            ? *reinterpret_cast<const uint32_t*>(
+                                  x + (size_t)(pp[i] + (long long)dyt * W + dxt) * CIN + cc * 8 + 2 * fc)
+                            : 0u;
             }
+            const int m = t * CIN + cc * 8 + sj;
+            const uint32_t dst = a0 + (uint32_t)((m >> 7) * 128 * 128 * 2) +
+                                 tc::canon_offset(m & 127, q0 + 8 * sm, 128);
+            tc::stmatrix_x4_trans(dst, rv[0], rv[1], rv[2], rv[3]);
         }
         if (tid < 128) {
             const int m = K;
@@ -282,15 +310,14 @@ k_conv3x3_wgrad_tc(const bf16* __restrict__ x, const bf16* __restrict__ dy, int 
                 __float2bfloat16(s + tid < pend ? 1.0f : 0.0f);
         }
         // B: element (n, q) = dy[s + q, n]
-        for (int e = tid; e < 128 * (NPAD / 8); e += kConvThreads) {
-            const int q = e % 128, c8 = e / 128;
-            const long long p = s + q;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < pend) v = *reinterpret_cast<const uint4*>(dy + (size_t)p * NPAD + c8 * 8);
-            const bf16* hv = reinterpret_cast<const bf16*>(&v);
+        for (int c8 = 0; c8 < NPAD / 8; ++c8) {
+            uint32_t rv[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<bf16*>(sB + tc::canon_offset(c8 * 8 + j, q, 128)) = hv[j];
+            for (int i = 0; i < 4; ++i)
+                rv[i] = pv[i] ? *reinterpret_cast<const uint32_t*>(dy + (size_t)pp[i] * NPAD + c8 * 8 + 2 * fc)
+                              : 0u;
+            const uint32_t dst = b0 + tc::canon_offset(c8 * 8 + sj, q0 + 8 * sm, 128);
+            tc::stmatrix_x4_trans(dst, rv[0], rv[1], rv[2], rv[3]);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();

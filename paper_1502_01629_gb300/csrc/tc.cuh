@@ -25,6 +25,16 @@ __device__ __forceinline__ uint32_t canon_offset(int r, int k, int K) {
     return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Four 8x8 b16 matrices stored transposed: lane t holds element (t/4, 2(t%4)) and
+// (t/4, 2(t%4)+1) of matrix i in r_i (lower half the smaller column); lane 8i + j
+// gives the address of the 16-byte row j of stored matrix i, which receives
+// column j of matrix i.
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t saddr, uint32_t r0, uint32_t r1, uint32_t r2,
+                                                  uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};"
+                 :: "r"(saddr), "r"(r0), "r"(r1), "r"(r2), "r"(r3) : "memory");
+}
+
 // shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), version 1,
 // no swizzle
 __device__ __forceinline__ uint64_t desc_noswizzle(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
