@@ -220,8 +220,13 @@ class Problem:
         u = _c(u, np.float64).reshape(-1)
         check(lib().hjb_set_value(self._h, _p(u)), "hjb_set_value")
 
-    def get_value(self) -> np.ndarray:
-        out = np.empty(self.N)
+    def get_value(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """The fine value (float64, n^2); into `out` when given (e.g. a buffer in
+        pinned host memory reused across solves)."""
+        if out is None:
+            out = np.empty(self.N)
+        elif out.dtype != np.float64 or out.size != self.N or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of n^2 elements")
         check(lib().hjb_get_value(self._h, _p(out)), "hjb_get_value")
         return out
 
@@ -371,11 +376,15 @@ class Batch:
         check(lib().hjb_batch_get_value(self._h, index, _p(out)), "hjb_batch_get_value")
         return out
 
-    def get_values(self) -> list:
+    def get_values(self, out: Optional[np.ndarray] = None) -> list:
         """Every instance's value from one read-back (``hjb_batch_get_values``): a
-        list of n_i^2 arrays, views of one buffer."""
+        list of n_i^2 arrays, views of one buffer (`out`, sum n_i^2 float64, when
+        given: e.g. pinned host memory reused across solves)."""
         sizes = [n * n for n in self.ns]
-        out = np.empty(sum(sizes))
+        if out is None:
+            out = np.empty(sum(sizes))
+        elif out.dtype != np.float64 or out.size != sum(sizes) or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of sum n_i^2 elements")
         check(lib().hjb_batch_get_values(self._h, _p(out)), "hjb_batch_get_values")
         return np.split(out, np.cumsum(sizes)[:-1])
 
