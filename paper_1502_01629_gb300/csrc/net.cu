@@ -287,6 +287,7 @@ k_conv3x3_wgrad_tc(const bf16* __restrict__ x, const bf16* __restrict__ dy, int 
         }
         // A: element (m, q) = x at pixel s + q shifted by tap t = m / CIN, channel
         // m % CIN (0 outside the image or past the chunk); row K = 1 for a pixel
+#pragma unroll 2
         for (int it = 0; it < 9 * (CIN / 8); ++it) {
             const int t = it / (CIN / 8), cc = it - t * (CIN / 8);
             const int dyt = (t / 3 - 1) * dil, dxt = (t % 3 - 1) * dil;
