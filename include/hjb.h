@@ -105,7 +105,12 @@ typedef struct {
     int32_t visit;        /* warp tiles, FP32: how a warp updates a tile's nodes: 1 one node
                              at a time (a control per lane, warp minimum, Gauss-Seidel through
                              the tile), 2 32 nodes at a time (a node per lane, every control
-                             in the lane), 0 automatic (1)                                    */
+                             in the lane), 3 two nodes at a time (16 lanes each; interior
+                             tiles, 1 elsewhere): four controls a lane with 64 controls closed
+                             under quarter turns (a_{m+16} = (-a_m.y, a_m.x), a_{m+32} = -a_m,
+                             to 1e-12), two with 32 in opposite pairs (a_{m+16} = -a_m), 1 for
+                             other control sets; 0 automatic (3 for such 64 controls, and for
+                             such 32 where the candidates carry a self weight, else 1)        */
 } hjb_desc;
 
 /* Per-call statistics; every field is written by the call that receives it. */

@@ -555,6 +555,7 @@ struct hjb_batch {
     int count = 0;
     int na = 0;
     int scheme = 3;
+    bool ctrl_sym32 = false;     // 32 controls in opposite pairs (two-node visits)
     int D = 2;
     int shape = 2;               // warp-tile shape code: 1 8x8, 2 8x4, 3 4x4
     int B = 2;                   // bands per tile wave
@@ -975,6 +976,12 @@ int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst
             c32[m] = make_float2((float)controls[2 * m], (float)controls[2 * m + 1]);
             c64[m] = make_double2(controls[2 * m], controls[2 * m + 1]);
         }
+        // 32 controls in opposite pairs a_{m+16} = -a_m (to 1e-12): the FP32 warp
+        // tiles update two nodes at a time, two controls a lane (mirrored geometry)
+        b->ctrl_sym32 = na == 32;
+        for (int m = 0; m < 16 && b->ctrl_sym32; ++m)
+            b->ctrl_sym32 = std::fabs(controls[2 * (m + 16)] + controls[2 * m]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 16) + 1] + controls[2 * m + 1]) <= 1e-12;
         BCUP(cudaMemcpyAsync(b->ctrl32, c32.data(), sizeof(float2) * na, cudaMemcpyHostToDevice, b->st));
         BCUP(cudaMemcpyAsync(b->ctrl64, c64.data(), sizeof(double2) * na, cudaMemcpyHostToDevice, b->st));
         BCUP(cudaStreamSynchronize(b->st));
@@ -1400,6 +1407,7 @@ int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_ac
     a.tile_inst = b->tile_inst;
     a.inst_active = use_active ? b->active : nullptr;
     a.max_wh = b->max_wh;
+    a.node_pairs = !f64 && b->ctrl_sym32 ? 2 : 0;
     const int per_sm = wtile_blocks_per_sm(f64, b->any_sigma, b->na, b->max_wh, b->shape);
     if (per_sm < 1) return bfail(HJB_ERR_INVALID_ARG, "warp-tile kernel does not fit on an SM");
     if (b->async && !f64 && !warm) {

@@ -309,6 +309,10 @@ struct TileArgs {
                                // reach in cells), 0 = compute it
     int ctrl_sym;              // 1: 64 controls with a_{m+32} = -a_m (to 1e-12): the second
                                // control of a lane takes the mirror of the first's geometry
+    int node_pairs;            // two nodes at a time (16 lanes each), interior tiles: 1 with
+                               // 64 controls, four per lane (m, m+16, m+32, m+48: one
+                               // geometry, its mirror and quarter turns); 2 with 32 controls,
+                               // two per lane (m and its mirror m+16)
     int max_steps;
     float tol;
     // asynchronous worklist (schedule 3): per-tile state 0 idle, 1 queued,

@@ -637,6 +637,137 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
         }
       }
     };
+    // FP32, no drift, 64 controls closed under quarter turns, interior tiles: two
+    // nodes at a time (q and q + 1 of the visiting order, 16 lanes each; the
+    // second reads the first's value of before the pair), four controls per lane
+    // (m, m + 16, m + 32, m + 48 for m = lane % 16).  The six axis cells of a_m give
+    // every point of the four controls: -a_m takes their mirror images, the quarter
+    // turns (-a.y, a.x) and (a.y, -a.x) swap the axes with one of them mirrored;
+    // the self weight, and with it 1/D, is the same for all four.  Each
+    // control's four points are summed in the order geo32 uses for it.
+    auto visit_pairs = [&](auto nol_tag, auto quad_tag) {
+      constexpr bool NOL = decltype(nol_tag)::value;
+      constexpr bool QUAD = decltype(quad_tag)::value;   // 64 controls; else 32 (m, m + 16 = -a_m)
+      const float s = g.s32, beta = g.beta32, hl = g.hl32;
+      const float bq = SIG ? beta * 0.25f : beta;
+      const float omb = 1.0f - beta;
+      const int half = lane >> 4;
+      const float2 ac = g.ctrl32[lane & 15];
+      float* sf = reinterpret_cast<float*>(su);
+      auto N4 = [&](int o0, float fx0, float fy0, int o1, float fx1, float fy1, int o2, float fx2, float fy2,
+                    int o3, float fx3, float fy3, float uk, float cc0) {
+          float Sd;
+          if constexpr (SIG) {
+              Sd = (bil32(sf, o0, W, fx0, fy0, uk) + bil32(sf, o1, W, fx1, fy1, uk)) +
+                   (bil32(sf, o2, W, fx2, fy2, uk) + bil32(sf, o3, W, fx3, fy3, uk));
+          } else {
+              Sd = bil32(sf, o0, W, fx0, fy0, uk);
+          }
+          return fmaf(bq, Sd, cc0);
+      };
+      for (int sw = 0; sw < a.local_sweeps; ++sw) {
+        for (int q = 0; q < nn; q += 2) {
+            const int qq = q + half;
+            const bool valid = qq < nn;
+            const int src = qq & 31;
+            const int ev0 = __shfl_sync(0xffffffffu, e0, src), ev1 = __shfl_sync(0xffffffffu, e1, src);
+            const float cv0 = __shfl_sync(0xffffffffu, c0, src), cv1 = __shfl_sync(0xffffffffu, c1, src);
+            const int e = valid ? (qq < 32 ? ev0 : ev1) : 0;
+            const float c = valid ? (qq < 32 ? cv0 : cv1) : 0.0f;
+            const int ex = e % TW, ey = e / TW;
+            const int kb = (R + ey) * W + (R + ex);
+            const float sc = s * c;
+            const float fx = sc * ac.x, fy = sc * ac.y;
+            const float uk = sf[kb];
+            const float cc0 = fmaf(-omb, uk, hl);
+            float v;
+            if constexpr (SIG) {
+                const float d = g.d32;
+                const Axis<float> xm = axis_cell<float, false>(fx - d, 0.0f, 0.0f, 0.0f);
+                const Axis<float> x0 = axis_cell<float, false>(fx, 0.0f, 0.0f, 0.0f);
+                const Axis<float> xp = axis_cell<float, false>(fx + d, 0.0f, 0.0f, 0.0f);
+                const Axis<float> ym = axis_cell<float, false>(fy - d, 0.0f, 0.0f, 0.0f);
+                const Axis<float> y0 = axis_cell<float, false>(fy, 0.0f, 0.0f, 0.0f);
+                const Axis<float> yp = axis_cell<float, false>(fy + d, 0.0f, 0.0f, 0.0f);
+                // mirror images: M(c) is the cell of -y for the cell c of y
+                int mxm, mx0, mxp, mym, my0, myp;
+                float fmxm, fmx0, fmxp, fmym, fmy0, fmyp;
+                mirror_cell(xm, mxm, fmxm);
+                mirror_cell(x0, mx0, fmx0);
+                mirror_cell(xp, mxp, fmxp);
+                mirror_cell(ym, mym, fmym);
+                mirror_cell(y0, my0, fmy0);
+                mirror_cell(yp, myp, fmyp);
+                // a: (x+d, y), (x-d, y), (x, y+d), (x, y-d)
+                const float va = N4(kb + y0.off * W + xp.off, xp.fr, y0.fr, kb + y0.off * W + xm.off, xm.fr, y0.fr,
+                                    kb + yp.off * W + x0.off, x0.fr, yp.fr, kb + ym.off * W + x0.off, x0.fr, ym.fr,
+                                    uk, cc0);
+                // -a: foot (-x, -y)
+                const float vb = N4(kb + my0 * W + mxm, fmxm, fmy0, kb + my0 * W + mxp, fmxp, fmy0,
+                                    kb + mym * W + mx0, fmx0, fmym, kb + myp * W + mx0, fmx0, fmyp, uk, cc0);
+                v = fminf(va, vb);
+                if constexpr (QUAD) {
+                    // quarter turn (-a.y, a.x): foot (-y, x)
+                    const float vc = N4(kb + x0.off * W + mym, fmym, x0.fr, kb + x0.off * W + myp, fmyp, x0.fr,
+                                        kb + xp.off * W + my0, fmy0, xp.fr, kb + xm.off * W + my0, fmy0, xm.fr, uk,
+                                        cc0);
+                    // quarter turn (a.y, -a.x): foot (y, -x)
+                    const float vd = N4(kb + mx0 * W + yp.off, yp.fr, fmx0, kb + mx0 * W + ym.off, ym.fr, fmx0,
+                                        kb + mxm * W + y0.off, y0.fr, fmxm, kb + mxp * W + y0.off, y0.fr, fmxp, uk,
+                                        cc0);
+                    v = fminf(v, fminf(vc, vd));
+                }
+                if constexpr (!NOL) {
+                    const float L = y0.sw * (xp.sw + xm.sw) + x0.sw * (yp.sw + ym.sw);
+                    const float D = a.scheme == 3 ? fmaf(-bq, L, 1.0f) : 1.0f;
+                    // the same positive D for the four: the minimum of N / D is
+                    // the minimum of N divided by D
+                    v = D > 0.0f ? v * rcp_approx(D) : INFINITY;
+                }
+            } else {
+                const Axis<float> x0 = axis_cell<float, false>(fx, 0.0f, 0.0f, 0.0f);
+                const Axis<float> y0 = axis_cell<float, false>(fy, 0.0f, 0.0f, 0.0f);
+                int mx0, my0;
+                float fmx0, fmy0;
+                mirror_cell(x0, mx0, fmx0);
+                mirror_cell(y0, my0, fmy0);
+                const float va = N4(kb + y0.off * W + x0.off, x0.fr, y0.fr, 0, 0.f, 0.f, 0, 0.f, 0.f, 0, 0.f, 0.f, uk, cc0);
+                const float vb = N4(kb + my0 * W + mx0, fmx0, fmy0, 0, 0.f, 0.f, 0, 0.f, 0.f, 0, 0.f, 0.f, uk, cc0);
+                v = fminf(va, vb);
+                if constexpr (QUAD) {
+                    const float vc =
+                        N4(kb + x0.off * W + my0, fmy0, x0.fr, 0, 0.f, 0.f, 0, 0.f, 0.f, 0, 0.f, 0.f, uk, cc0);
+                    const float vd =
+                        N4(kb + mx0 * W + y0.off, y0.fr, fmx0, 0, 0.f, 0.f, 0, 0.f, 0.f, 0, 0.f, 0.f, uk, cc0);
+                    v = fminf(v, fminf(vc, vd));
+                }
+                if constexpr (!NOL) {
+                    const float L = x0.sw * y0.sw;
+                    const float D = a.scheme == 3 ? fmaf(-bq, L, 1.0f) : 1.0f;
+                    v = D > 0.0f ? v * rcp_approx(D) : INFINITY;
+                }
+            }
+            // minimum over the 16 lanes of the half (order-preserving bits)
+            unsigned int key = order_key(valid ? v : INFINITY);
+#pragma unroll
+            for (int o = 8; o >= 1; o >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+            const float du = order_val(key);
+            __syncwarp();
+            if ((lane & 15) == 0 && valid) sf[kb] = uk + du;
+            __syncwarp();
+            const float du0 = __shfl_sync(0xffffffffu, du, 0), du1 = __shfl_sync(0xffffffffu, du, 16);
+            const int e_0 = __shfl_sync(0xffffffffu, e, 0), e_1 = __shfl_sync(0xffffffffu, e, 16);
+            const bool v1 = q + 1 < nn;
+            tmax = fmaxf(tmax, fabsf(du0));
+            mark(e_0, fabsf(du0));
+            if (v1) {
+                tmax = fmaxf(tmax, fabsf(du1));
+                mark(e_1, fabsf(du1));
+            }
+            if (!claimed && tmax > a.tol) claim();
+        }
+      }
+    };
     bool piped = false;
     if constexpr (sizeof(T) == 4) {
         // no self weight: scheme 2 everywhere, a wide diffusion in interior tiles
@@ -650,6 +781,10 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
                 if (nol) visit_ln(std::true_type{}, std::true_type{});
                 else visit_ln(std::true_type{}, std::false_type{});
             }
+        } else if (g.drift == nullptr && na == 32 && !g.gen && a.node_pairs == 2 && interior) {
+            piped = true;
+            if (nol) visit_pairs(std::true_type{}, std::false_type{});
+            else visit_pairs(std::false_type{}, std::false_type{});
         } else if (g.drift == nullptr && na <= 32 && !g.gen) {
             piped = true;
             if (interior) {
@@ -659,6 +794,10 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
                 if (nol) visit32(std::true_type{}, std::true_type{});
                 else visit32(std::true_type{}, std::false_type{});
             }
+        } else if (g.drift == nullptr && na == 64 && !g.gen && a.node_pairs == 1 && interior) {
+            piped = true;
+            if (nol) visit_pairs(std::true_type{}, std::true_type{});
+            else visit_pairs(std::false_type{}, std::true_type{});
         } else if (g.drift == nullptr && na <= 64 && !g.gen) {
             piped = true;
             if (interior) {
