@@ -59,9 +59,10 @@ SOLVER_KW = dict(schedule=0, tile_shape=-1, tile_waves=0, tile_period=0, local_s
 BATCH_COUNT = 512
 GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 # DRAM bytes (read + write) per launch of the FP32 patch kernel, from one ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum),
-# per workload; None where no capture of the current kernel exists
-WTILES_DRAM_BYTES = {"patchy1025": None, "large4097": None, "batched512": None}
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum;
+# profiles/dram_traffic_wtiles.md), per workload: 4097^2 one launch per solve;
+# 1025^2 the mean of a step's three launches; None where no capture exists
+WTILES_DRAM_BYTES = {"patchy1025": 14.25e6, "large4097": 257.23e6, "batched512": None}
 
 
 def ops_per_node_control(sigma: float) -> int:
