@@ -322,7 +322,8 @@ SCHEDULES = [dict(schedule=0, tile_shape=0), dict(schedule=0, tile_shape=1),
              dict(schedule=0, visit=1), dict(schedule=0, visit=2, local_sweeps=2),
              dict(schedule=0, tile_shape=1, visit=2),
              dict(schedule=3), dict(schedule=3, tile_shape=1), dict(schedule=3, visit=2, local_sweeps=3),
-             dict(schedule=3, tile_shape=2)]
+             dict(schedule=3, tile_shape=2),
+             dict(schedule=0, visit=3), dict(schedule=0, tile_shape=0, visit=3), dict(schedule=3, visit=3)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES, ids=[str(s) for s in SCHEDULES])
@@ -345,17 +346,20 @@ def test_every_patch_schedule_reaches_the_oracle_fixed_point(sched, sigma):
         np.testing.assert_allclose(G.get_value(), u_ref, rtol=0, atol=1e-10)
 
 
-def test_large_recipe_matches_oracle():
+@pytest.mark.parametrize("visit", [0, 1, 3])
+def test_large_recipe_matches_oracle(visit):
     """The large workload's recipe (random Fourier speed, 64 controls, six
     rectangular obstacles held at the obstacle value, sigma = 0.01, 64 sectors)
     at 129^2 with a 33^2 coarse grid: the patchy solve with the automatic tile
     schedule (8x8 tiles: more than 32 controls) meets the FP32 gate, then the
-    FP64 gate after polishing."""
+    FP64 gate after polishing -- with the automatic visits (two nodes at a time:
+    the 64 controls are closed under quarter turns), one node at a time, and two
+    nodes at a time by request."""
     inst = hi.large_instance(n=129, coarse_n=33)
     O = oracle.Problem.from_instance(inst)
     u_ref, _, _ = O.solve(scheme=3, tol=1e-13)
     scale = max(1.0, np.abs(u_ref).max())
-    with P_gpu(inst) as G:
+    with P_gpu(inst, visit=visit) as G:
         G.coarse_solve(tol_c=1e-7)
         G.build_patches()
         G.solve_patches(tol32=3e-7, tol64=0.0)
