@@ -123,7 +123,9 @@ def test_trained_network_against_the_plain_start(pkg):
     learned start and the plain coarse start reach the same fine fixed point
     (both to the FP64 residual 1e-6, so within 2e-6 / (1 - beta) of each other),
     and the time of both is reported (the learned start is judged by it, not
-    required to win: DESIGN records the measured difference and its cause)."""
+    required to win: on these workloads it loses a few per cent, the cost of its
+    trial sweeps and of the fine work an accepted, less accurate coarse value
+    causes)."""
     from paper_1502_01629_gb300 import warmstart as ws
     net = ws.load_trained()
     assert net is not None, "the trained parameters are missing from the package"
