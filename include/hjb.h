@@ -109,8 +109,9 @@ typedef struct {
                              tiles, 1 elsewhere): four controls a lane with 64 controls closed
                              under quarter turns (a_{m+16} = (-a_m.y, a_m.x), a_{m+32} = -a_m,
                              to 1e-12), two with 32 in opposite pairs (a_{m+16} = -a_m), 1 for
-                             other control sets; 0 automatic (3 for such 64 controls, and for
-                             such 32 where the candidates carry a self weight, else 1)        */
+                             other control sets; 4 four nodes at a time (8 lanes each, four
+                             controls a lane: 32 controls closed under quarter turns); 0
+                             automatic (4 for such 32 controls, 3 for such 64, else 1)        */
 } hjb_desc;
 
 /* Per-call statistics; every field is written by the call that receives it. */

@@ -222,6 +222,7 @@ struct hjb_problem {
     bool ctrl_sym = false;         // 64 controls, a_{m+32} = -a_m
     bool ctrl_rot = false;         // and a_{m+16}, a_{m+48} the quarter turns of a_m
     bool ctrl_sym32 = false;       // 32 controls, a_{m+16} = -a_m
+    bool ctrl_rot32 = false;       // and a_{m+8}, a_{m+24} the quarter turns of a_m
     bool visit_auto = false;       // desc.visit was 0 (automatic)
     float* sigf = nullptr;         // sigma(x), n*n
     float* costf = nullptr;        // l(x), n*n
@@ -452,9 +453,10 @@ int validate_desc(const hjb_desc* d) {
     if (d->schedule < 0 || d->schedule > 4) return fail(HJB_ERR_INVALID_ARG, "schedule must be 0 .. 4");
     if (d->tile_shape < -1 || d->tile_shape > 2)
         return fail(HJB_ERR_INVALID_ARG, "tile_shape must be -1 (auto), 0 (8x8), 1 (8x4) or 2 (4x4)");
-    if (d->visit < 0 || d->visit > 3)
+    if (d->visit < 0 || d->visit > 4)
         return fail(HJB_ERR_INVALID_ARG,
-                    "visit must be 0 (auto), 1 (a node at a time), 2 (32 nodes at a time) or 3 (two nodes at a time)");
+                    "visit must be 0 (auto), 1 (a node at a time), 2 (32 nodes at a time), 3 (two nodes at a "
+                    "time) or 4 (four nodes at a time)");
     return HJB_OK;
 }
 
@@ -707,6 +709,13 @@ int create_common(const hjb_desc* desc, const float* speed, const uint8_t* mask,
         for (int m = 0; m < 16 && p->ctrl_sym32; ++m)
             p->ctrl_sym32 = std::fabs(controls[2 * (m + 16)] + controls[2 * m]) <= 1e-12 &&
                             std::fabs(controls[2 * (m + 16) + 1] + controls[2 * m + 1]) <= 1e-12;
+        // and quarter turns: a_{m+8} = (-a_m.y, a_m.x), a_{m+24} = (a_m.y, -a_m.x)
+        p->ctrl_rot32 = p->ctrl_sym32;
+        for (int m = 0; m < 8 && p->ctrl_rot32; ++m)
+            p->ctrl_rot32 = std::fabs(controls[2 * (m + 8)] + controls[2 * m + 1]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 8) + 1] - controls[2 * m]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 24)] - controls[2 * m + 1]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 24) + 1] + controls[2 * m]) <= 1e-12;
         // quarter turns as well: a_{m+16} = (-a_m.y, a_m.x), a_{m+48} = (a_m.y, -a_m.x)
         p->ctrl_rot = p->ctrl_sym;
         for (int m = 0; m < 16 && p->ctrl_rot; ++m)
@@ -1173,14 +1182,18 @@ int run_tiles(hjb_problem* p, bool f64, double tol, int max_passes, WaveResult* 
         a.no_self = p->desc.scheme == 2 ? 2 : (p->sigma > 0.0 && dcell >= 1.0 + drift_cells + 1e-3 ? 1 : 0);
     }
     {
-        // two nodes at a time (visit 3): automatic with 64 controls closed under
-        // quarter turns (4097^2: FP32 passes 235 -> 210 ms) and with 32 opposite
-        // pairs where candidates carry a self weight (1025^2: sigma 0 6.55 -> 6.25
-        // ms, 0.02 8.90 -> 8.37 ms; sigma 0.1, without self weights, 31.7 -> 32.0 ms)
-        const bool pairs = !p->gen && p->drift == nullptr && (p->desc.visit == 3 || p->visit_auto);
-        if (pairs && p->ctrl_sym && p->ctrl_rot)
+        // node groups, automatic where the control set allows them: 64 controls
+        // closed under quarter turns two nodes at a time (visit 3; 4097^2: FP32
+        // passes 235 -> 210 ms), 32 closed under quarter turns four at a time
+        // (visit 4; 1025^2: sigma 0 6.62 -> 5.83 ms, 0.02 8.90 -> 8.14 ms, 0.1
+        // 31.7 -> 29.1 ms), 32 opposite pairs only two at a time (visit 3)
+        const bool plain = !p->gen && p->drift == nullptr;
+        const bool aut = p->visit_auto;
+        if (plain && (p->desc.visit == 3 || aut) && p->ctrl_sym && p->ctrl_rot)
             a.node_pairs = 1;
-        else if (pairs && p->ctrl_sym32 && (p->desc.visit == 3 || a.no_self == 0))
+        else if (plain && (p->desc.visit == 4 || aut) && p->ctrl_rot32)
+            a.node_pairs = 3;
+        else if (plain && (p->desc.visit == 3 || (aut && a.no_self == 0)) && p->ctrl_sym32)
             a.node_pairs = 2;
         else
             a.node_pairs = 0;

@@ -556,6 +556,7 @@ struct hjb_batch {
     int na = 0;
     int scheme = 3;
     bool ctrl_sym32 = false;     // 32 controls in opposite pairs (two-node visits)
+    bool ctrl_rot32 = false;     // and closed under quarter turns (four-node visits)
     int D = 2;
     int shape = 2;               // warp-tile shape code: 1 8x8, 2 8x4, 3 4x4
     int B = 2;                   // bands per tile wave
@@ -982,6 +983,13 @@ int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst
         for (int m = 0; m < 16 && b->ctrl_sym32; ++m)
             b->ctrl_sym32 = std::fabs(controls[2 * (m + 16)] + controls[2 * m]) <= 1e-12 &&
                             std::fabs(controls[2 * (m + 16) + 1] + controls[2 * m + 1]) <= 1e-12;
+        // closed under quarter turns as well: four nodes at a time, four controls a lane
+        b->ctrl_rot32 = b->ctrl_sym32;
+        for (int m = 0; m < 8 && b->ctrl_rot32; ++m)
+            b->ctrl_rot32 = std::fabs(controls[2 * (m + 8)] + controls[2 * m + 1]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 8) + 1] - controls[2 * m]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 24)] - controls[2 * m + 1]) <= 1e-12 &&
+                            std::fabs(controls[2 * (m + 24) + 1] + controls[2 * m]) <= 1e-12;
         BCUP(cudaMemcpyAsync(b->ctrl32, c32.data(), sizeof(float2) * na, cudaMemcpyHostToDevice, b->st));
         BCUP(cudaMemcpyAsync(b->ctrl64, c64.data(), sizeof(double2) * na, cudaMemcpyHostToDevice, b->st));
         BCUP(cudaStreamSynchronize(b->st));
@@ -1407,7 +1415,7 @@ int stage_passes(hjb_batch* b, bool f64, double tol, int max_passes, bool use_ac
     a.tile_inst = b->tile_inst;
     a.inst_active = use_active ? b->active : nullptr;
     a.max_wh = b->max_wh;
-    a.node_pairs = !f64 && b->ctrl_sym32 ? 2 : 0;
+    a.node_pairs = f64 ? 0 : (b->ctrl_rot32 ? 3 : (b->ctrl_sym32 ? 2 : 0));
     const int per_sm = wtile_blocks_per_sm(f64, b->any_sigma, b->na, b->max_wh, b->shape);
     if (per_sm < 1) return bfail(HJB_ERR_INVALID_ARG, "warp-tile kernel does not fit on an SM");
     if (b->async && !f64 && !warm) {

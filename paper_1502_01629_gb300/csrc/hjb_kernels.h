@@ -312,7 +312,8 @@ struct TileArgs {
     int node_pairs;            // two nodes at a time (16 lanes each), interior tiles: 1 with
                                // 64 controls, four per lane (m, m+16, m+32, m+48: one
                                // geometry, its mirror and quarter turns); 2 with 32 controls,
-                               // two per lane (m and its mirror m+16)
+                               // two per lane (m and its mirror m+16); 3: four nodes at a
+                               // time (8 lanes each), 32 controls, four per lane
     int max_steps;
     float tol;
     // asynchronous worklist (schedule 3): per-tile state 0 idle, 1 queued,

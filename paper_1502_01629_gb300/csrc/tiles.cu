@@ -637,22 +637,28 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
         }
       }
     };
-    // FP32, no drift, 64 controls closed under quarter turns, interior tiles: two
-    // nodes at a time (q and q + 1 of the visiting order, 16 lanes each; the
-    // second reads the first's value of before the pair), four controls per lane
-    // (m, m + 16, m + 32, m + 48 for m = lane % 16).  The six axis cells of a_m give
-    // every point of the four controls: -a_m takes their mirror images, the quarter
+    // FP32, no drift, interior tiles: NG nodes at a time (q .. q + NG - 1 of the
+    // visiting order on 32 / NG lanes each; a node reads the group's other nodes'
+    // values of before the group).  With the NA controls closed under quarter
+    // turns a lane takes four (m, m + NA/4, m + NA/2, m + 3NA/4 for m = lane %
+    // (32 / NG): 64 controls two nodes at a time, 32 four at a time); with
+    // opposite pairs only, two (m, m + NA/2).  The six axis cells of a_m give every
+    // point of the four controls: -a_m takes their mirror images, the quarter
     // turns (-a.y, a.x) and (a.y, -a.x) swap the axes with one of them mirrored;
     // the self weight, and with it 1/D, is the same for all four.  Each
     // control's four points are summed in the order geo32 uses for it.
-    auto visit_pairs = [&](auto nol_tag, auto quad_tag) {
+    auto visit_pairs = [&](auto nol_tag, auto quad_tag, auto group_tag) {
       constexpr bool NOL = decltype(nol_tag)::value;
-      constexpr bool QUAD = decltype(quad_tag)::value;   // 64 controls; else 32 (m, m + 16 = -a_m)
+      // QUAD: four controls a lane (a_m and its mirror and quarter turns), else two
+      // (a_m and its mirror); NG nodes at a time on 32 / NG lanes each
+      constexpr bool QUAD = decltype(quad_tag)::value;
+      constexpr int NG = decltype(group_tag)::value;
+      constexpr int LPN = 32 / NG;                  // lanes per node
       const float s = g.s32, beta = g.beta32, hl = g.hl32;
       const float bq = SIG ? beta * 0.25f : beta;
       const float omb = 1.0f - beta;
-      const int half = lane >> 4;
-      const float2 ac = g.ctrl32[lane & 15];
+      const int half = lane / LPN;
+      const float2 ac = g.ctrl32[lane % LPN];
       float* sf = reinterpret_cast<float*>(su);
       auto N4 = [&](int o0, float fx0, float fy0, int o1, float fx1, float fy1, int o2, float fx2, float fy2,
                     int o3, float fx3, float fy3, float uk, float cc0) {
@@ -666,7 +672,7 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
           return fmaf(bq, Sd, cc0);
       };
       for (int sw = 0; sw < a.local_sweeps; ++sw) {
-        for (int q = 0; q < nn; q += 2) {
+        for (int q = 0; q < nn; q += NG) {
             const int qq = q + half;
             const bool valid = qq < nn;
             const int src = qq & 31;
@@ -747,22 +753,22 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
                     v = D > 0.0f ? v * rcp_approx(D) : INFINITY;
                 }
             }
-            // minimum over the 16 lanes of the half (order-preserving bits)
+            // minimum over the node's lanes (order-preserving bits)
             unsigned int key = order_key(valid ? v : INFINITY);
 #pragma unroll
-            for (int o = 8; o >= 1; o >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+            for (int o = LPN / 2; o >= 1; o >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
             const float du = order_val(key);
             __syncwarp();
-            if ((lane & 15) == 0 && valid) sf[kb] = uk + du;
+            if (lane % LPN == 0 && valid) sf[kb] = uk + du;
             __syncwarp();
-            const float du0 = __shfl_sync(0xffffffffu, du, 0), du1 = __shfl_sync(0xffffffffu, du, 16);
-            const int e_0 = __shfl_sync(0xffffffffu, e, 0), e_1 = __shfl_sync(0xffffffffu, e, 16);
-            const bool v1 = q + 1 < nn;
-            tmax = fmaxf(tmax, fabsf(du0));
-            mark(e_0, fabsf(du0));
-            if (v1) {
-                tmax = fmaxf(tmax, fabsf(du1));
-                mark(e_1, fabsf(du1));
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                const float duk = __shfl_sync(0xffffffffu, du, k * LPN);
+                const int ek = __shfl_sync(0xffffffffu, e, k * LPN);
+                if (q + k < nn) {
+                    tmax = fmaxf(tmax, fabsf(duk));
+                    mark(ek, fabsf(duk));
+                }
             }
             if (!claimed && tmax > a.tol) claim();
         }
@@ -783,8 +789,12 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             }
         } else if (g.drift == nullptr && na == 32 && !g.gen && a.node_pairs == 2 && interior) {
             piped = true;
-            if (nol) visit_pairs(std::true_type{}, std::false_type{});
-            else visit_pairs(std::false_type{}, std::false_type{});
+            if (nol) visit_pairs(std::true_type{}, std::false_type{}, std::integral_constant<int, 2>{});
+            else visit_pairs(std::false_type{}, std::false_type{}, std::integral_constant<int, 2>{});
+        } else if (g.drift == nullptr && na == 32 && !g.gen && a.node_pairs == 3 && interior) {
+            piped = true;
+            if (nol) visit_pairs(std::true_type{}, std::true_type{}, std::integral_constant<int, 4>{});
+            else visit_pairs(std::false_type{}, std::true_type{}, std::integral_constant<int, 4>{});
         } else if (g.drift == nullptr && na <= 32 && !g.gen) {
             piped = true;
             if (interior) {
@@ -796,8 +806,8 @@ __device__ __forceinline__ float wt_visit(const TileArgs& a, int t, T* su,
             }
         } else if (g.drift == nullptr && na == 64 && !g.gen && a.node_pairs == 1 && interior) {
             piped = true;
-            if (nol) visit_pairs(std::true_type{}, std::true_type{});
-            else visit_pairs(std::false_type{}, std::true_type{});
+            if (nol) visit_pairs(std::true_type{}, std::true_type{}, std::integral_constant<int, 2>{});
+            else visit_pairs(std::false_type{}, std::true_type{}, std::integral_constant<int, 2>{});
         } else if (g.drift == nullptr && na <= 64 && !g.gen) {
             piped = true;
             if (interior) {

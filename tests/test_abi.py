@@ -61,7 +61,7 @@ def _desc(L, **kw):
 @pytest.mark.parametrize("bad", [
     dict(n=2), dict(n_controls=0), dict(n_controls=300), dict(lam=-1.0), dict(sigma=-0.1),
     dict(cost=0.0), dict(scheme=4), dict(n_patches=0), dict(coarse_n=4),
-    dict(lam=float("nan")), dict(visit=4), dict(visit=-1), dict(resort_passes=-1), dict(schedule=5), dict(tile_shape=3), dict(tile_shape=-2),
+    dict(lam=float("nan")), dict(visit=5), dict(visit=-1), dict(resort_passes=-1), dict(schedule=5), dict(tile_shape=3), dict(tile_shape=-2),
 ])
 def test_invalid_descriptions_are_rejected_on_host(L, bad):
     d = _desc(L, **bad)

@@ -323,7 +323,8 @@ SCHEDULES = [dict(schedule=0, tile_shape=0), dict(schedule=0, tile_shape=1),
              dict(schedule=0, tile_shape=1, visit=2),
              dict(schedule=3), dict(schedule=3, tile_shape=1), dict(schedule=3, visit=2, local_sweeps=3),
              dict(schedule=3, tile_shape=2),
-             dict(schedule=0, visit=3), dict(schedule=0, tile_shape=0, visit=3), dict(schedule=3, visit=3)]
+             dict(schedule=0, visit=3), dict(schedule=0, tile_shape=0, visit=3), dict(schedule=3, visit=3),
+             dict(schedule=0, visit=4), dict(schedule=0, tile_shape=0, visit=4), dict(schedule=3, visit=4)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES, ids=[str(s) for s in SCHEDULES])
