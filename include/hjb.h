@@ -493,7 +493,9 @@ int hjb_batch_create_lists(const hjb_batch_desc* desc, int32_t count, const hjb_
  * visited once in checkerboard order, then the queues).  stats->corr_sweeps:
  * the correction sweeps (each instance's count, the largest per round, summed).  The
  * worklist schedule caps the visits of one tile as hjb_solve_patches does; with
- * tol64 > 0 the FP64 residuals decide the status.
+ * tol64 > 0 the FP64 residuals decide the status.  The FP32 passes update the
+ * nodes of interior tiles in groups as hjb_desc.visit 4 (32 controls closed under
+ * quarter turns) or 3 (32 in opposite pairs) does, else one at a time.
  * Errors: HJB_ERR_NOT_CONVERGED (a cap was hit, or an FP64 residual stays above
  * tol64; values valid), HJB_ERR_TIMEOUT. */
 int hjb_batch_solve(hjb_batch* b, double tol_c, double tol32, double tol64, int32_t max_passes,
