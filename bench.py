@@ -868,7 +868,7 @@ def ours(args, ws, rank, local):
         ex = {}
         lab1 = make_instances("patchy1025")
         P1 = bench_single("patchy1025", [i for _, i in lab1], [lb for lb, _ in lab1],
-                          steps=min(args.steps, 10), warmup=args.warmup, plain_reps=1, e2e_reps=1,
+                          steps=min(args.steps, 10), warmup=args.warmup, plain_reps=1, e2e_reps=3,
                           certify=not args.no_certify, ws=ws, device=device, stream=stream,
                           sample_clocks=False)
         ex["patchy1025"] = dict(config=workload_config("patchy1025", [i for _, i in lab1], ws),
@@ -876,7 +876,7 @@ def ours(args, ws, rank, local):
                                 steps=len(P1["step_ms"]), gpu_launches=P1["launches"],
                                 **single_summary("patchy1025", [i for _, i in lab1],
                                                  [lb for lb, _ in lab1], P1, peaks))
-        B = bench_batched(steps=min(args.steps, 5), warmup=3, plain_reps=1, e2e_reps=1, ws=ws,
+        B = bench_batched(steps=min(args.steps, 5), warmup=3, plain_reps=1, e2e_reps=3, ws=ws,
                           device=device, stream=stream, peaks=peaks, sample_clocks=False,
                           certify=not args.no_certify)
         ex["batched512"] = dict(config=dict(batched_config(B["insts"], B["n_free"], ws), autotune=B["tune"]),
