@@ -954,17 +954,22 @@ int jacobi64(hjb_problem* p, double* buf0, double* buf1, double tol, int max_swe
 }
 
 // Screening margin of the FP64 residual.  With every value in [0, U]
-// (U = l/lambda + h l), an FP32 candidate differs from the FP64 one by at most
-// E <= 64 * 2^-24 * U (rounding of the values to FP32 and of about 25 FP32
-// operations on quantities <= 2U) + 2^-22 * reach * U (rounding of the foot
-// offset, times the largest value difference across a cell), which is below
-// 1e-5 U for a reach under 26 cells.  The margin is 2.2 E for the problem's own
-// reach (4.4e-6 U at 1 cell, 9.7e-6 U at 2.4 cells, 1e-5 U at 2.9 cells): every
-// control it keeps is evaluated in FP64, so a margin sized to the reach keeps
-// fewer of them.
+// (U = l/lambda + h l; eps = 2^-24), an FP32 candidate beta Sd + c0 differs from
+// the FP64 one by at most E = (20 + 10 reach) eps U:
+//  - the FP32 copies of the values: 2 eps U in Sd (a node's and a vertex's);
+//  - the arithmetic on the differences v - uk (each of magnitude <= U): 9 eps U
+//    per bilinear point, 12 eps U for the four points' sums and the quarter, about
+//    6 eps U for beta, c0 = h l - (1 - beta) uk and the last FMA: 18 eps U;
+//  - the point positions: the foot s c a and the offset d carry at most 5 eps
+//    reach cells of rounding per axis, and the interpolant moves by at most U per
+//    cell along each axis: 10 eps reach U.
+// The margin is 2.2 E (the FP64 candidates' own rounding is far below the 0.2 E
+// left over): every control within it of the FP32 minimum is evaluated in FP64,
+// so the FP64 minimiser always survives and the result is the full FP64
+// residual; at the 4097^2 workload's reach (2.4 cells) 5.8e-6 U.
 float screening_margin(const hjb_problem* p) {
     const double U = std::max(1.0, p->value_bound());
-    const double E = (64.0 * std::ldexp(1.0, -24) + std::ldexp(1.0, -22) * p->reach) * U;
+    const double E = (20.0 + 10.0 * p->reach) * std::ldexp(1.0, -24) * U;
     return (float)(2.2 * E);
 }
 

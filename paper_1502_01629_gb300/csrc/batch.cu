@@ -1100,9 +1100,8 @@ int batch_create(const hjb_batch_desc* desc, int32_t count, const hjb_batch_inst
         b->max_R = std::max(b->max_R, R);
         b->uob[i] = uob;
         // FP32 screening margin of the FP64 residual: 2.2 x the FP32 candidate error
-        // bound (64 2^-24 + 2^-22 reach) max(1, U) (the single-problem residual's)
-        hmargin[i] = (float)(2.2 * (64.0 * std::ldexp(1.0, -24) + std::ldexp(1.0, -22) * reach) *
-                             std::max(1.0, uob));
+        // bound (20 + 10 reach) 2^-24 max(1, U) (the single-problem residual's)
+        hmargin[i] = (float)(2.2 * (20.0 + 10.0 * reach) * std::ldexp(1.0, -24) * std::max(1.0, uob));
         fcount[i] = (long long)n * n;
         ccount[i] = (long long)nc * nc;
         nt_cap += (long long)((n + 3) / 4) * ((n + 3) / 4);
